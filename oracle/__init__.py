@@ -1,0 +1,260 @@
+"""CPU FP64 oracle for the five-equation diffuse-interface right-hand side.
+
+TEST INFRASTRUCTURE ONLY.  Only ``tests/``, ``__graft_entry__.smoke()`` and the
+CPU-baseline leg of ``bench.py`` may import this package.  The CUDA product
+path never imports, links or calls it, and it imports nothing from the product
+package.
+
+Contents (each cites the passage of arXiv 2305.09163 it follows):
+  * ``mfc_oracle.c`` (loaded with ctypes): EOS (Sec. 2.1, Eq. "soe"), WENO5-JS
+    (Sec. 3.2), HLLC (Sec. 3.2.1), ghost cells (Sec. 3.3), the semi-discrete
+    operator (Sec. 3.1, Eq. "fvmdis") and the CFL rate.
+  * this module: SSP-RK3 (Sec. 3.4, Gottlieb & Shu TVD Runge-Kutta) and the
+    CFL time step, in plain numpy on top of the C right-hand side.
+  * ``exact_riemann``: exact two-material stiffened-gas Riemann solution used to
+    judge shock-tube runs.
+  * ``mlp``: FP64 forward/backward of the learned-weight network.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "mfc_oracle.c")
+_LIB = os.path.join(_HERE, "libmfc_oracle.so")
+_lock = threading.Lock()
+_lib = None
+
+BC_PERIODIC, BC_TRANSMISSIVE, BC_REFLECTIVE = 0, 1, 2
+
+
+def build(force: bool = False) -> str:
+    """Compile the C oracle with gcc (no fused multiply-add, OpenMP)."""
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + ".tmp%d" % os.getpid()
+        cmd = ["gcc", "-O2", "-ffp-contract=off", "-fopenmp", "-fPIC", "-shared",
+               "-std=c11", "-o", tmp, _SRC, "-lm"]
+        subprocess.check_call(cmd)
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+class Params(ctypes.Structure):
+    _fields_ = [
+        ("n", ctypes.c_int * 3),
+        ("ndim", ctypes.c_int),
+        ("nf", ctypes.c_int),
+        ("dx", ctypes.c_double * 3),
+        ("bc", ctypes.c_int * 6),
+        ("gamma", ctypes.c_double * 3),
+        ("pi_inf", ctypes.c_double * 3),
+        ("eps", ctypes.c_double),
+        ("fallback", ctypes.c_int),
+    ]
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            lib = ctypes.CDLL(build())
+            P = ctypes.POINTER(Params)
+            dp = ctypes.POINTER(ctypes.c_double)
+            lp = ctypes.POINTER(ctypes.c_long)
+            lib.oracle_sys_size.argtypes = [P]
+            lib.oracle_sys_size.restype = ctypes.c_int
+            lib.oracle_cons_to_prim.argtypes = [P, dp, dp]
+            lib.oracle_prim_to_cons.argtypes = [P, dp, dp]
+            lib.oracle_prim_to_cons_array.argtypes = [P, dp, dp, ctypes.c_long]
+            lib.oracle_cons_to_prim_array.argtypes = [P, dp, dp, ctypes.c_long]
+            lib.oracle_weno5.argtypes = [dp, ctypes.c_double]
+            lib.oracle_weno5.restype = ctypes.c_double
+            lib.oracle_weno5_weights.argtypes = [dp, ctypes.c_double, dp, dp]
+            lib.oracle_weno5_beta.argtypes = [dp, dp]
+            lib.oracle_hllc.argtypes = [P, ctypes.c_int, dp, dp, dp, dp]
+            lib.oracle_face.argtypes = [P, dp, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                        ctypes.c_int, dp, dp]
+            lib.oracle_face.restype = ctypes.c_int
+            lib.oracle_rhs.argtypes = [P, dp, dp, dp]
+            lib.oracle_rhs.restype = ctypes.c_long
+            lib.oracle_rhs_cells.argtypes = [P, dp, ctypes.c_long, lp, dp]
+            lib.oracle_max_rate.argtypes = [P, dp, lp]
+            lib.oracle_max_rate.restype = ctypes.c_double
+            _lib = lib
+    return _lib
+
+
+def _dp(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+class Problem:
+    """Grid, boundary types and fluids of one problem (Sec. 3.1 uniform grid)."""
+
+    def __init__(self, n, lo, hi, bc, gamma, pi_inf, eps=1e-6, fallback=False):
+        n = list(n) + [1] * (3 - len(n))
+        self.n = tuple(int(v) for v in n)
+        self.ndim = 3 if self.n[2] > 1 else (2 if self.n[1] > 1 else 1)
+        self.nf = len(gamma)
+        self.lo = tuple(float(v) for v in (list(lo) + [0.0] * (3 - len(lo))))
+        self.hi = tuple(float(v) for v in (list(hi) + [1.0] * (3 - len(hi))))
+        self.dx = tuple((self.hi[d] - self.lo[d]) / self.n[d] for d in range(3))
+        self.bc = tuple(int(b) for b in bc) + (1,) * (6 - len(bc))
+        self.gamma = tuple(float(g) for g in gamma)
+        self.pi_inf = tuple(float(p) for p in pi_inf)
+        self.eps = float(eps)
+        self.fallback = bool(fallback)
+        self.sys_size = 2 * self.nf + self.ndim
+        self.ncell = self.n[0] * self.n[1] * self.n[2]
+
+    def params(self) -> Params:
+        p = Params()
+        for d in range(3):
+            p.n[d] = self.n[d]
+            p.dx[d] = self.dx[d]
+        p.ndim = self.ndim
+        p.nf = self.nf
+        for i in range(6):
+            p.bc[i] = self.bc[i]
+        for k in range(self.nf):
+            p.gamma[k] = self.gamma[k]
+            p.pi_inf[k] = self.pi_inf[k]
+        p.eps = self.eps
+        p.fallback = 1 if self.fallback else 0
+        return p
+
+    def shape(self):
+        """Array shape of a state: [sys_size][nz][ny][nx]."""
+        return (self.sys_size, self.n[2], self.n[1], self.n[0])
+
+
+def _state(pb: Problem, q) -> np.ndarray:
+    q = np.ascontiguousarray(q, dtype=np.float64)
+    assert q.size == pb.sys_size * pb.ncell, (q.shape, pb.shape())
+    return q
+
+
+def cons_from_prims(pb: Problem, w) -> np.ndarray:
+    w = _state(pb, w)
+    q = np.empty_like(w)
+    _load().oracle_prim_to_cons_array(ctypes.byref(pb.params()), _dp(w), _dp(q), pb.ncell)
+    return q.reshape(pb.shape())
+
+
+def prims_from_cons(pb: Problem, q) -> np.ndarray:
+    q = _state(pb, q)
+    w = np.empty_like(q)
+    _load().oracle_cons_to_prim_array(ctypes.byref(pb.params()), _dp(q), _dp(w), pb.ncell)
+    return w.reshape(pb.shape())
+
+
+def rhs(pb: Problem, q, return_info: bool = False):
+    """R(q) of Eq. "fvmdis"; with return_info also (per-variable max |F|, fallback faces)."""
+    q = _state(pb, q)
+    out = np.empty_like(q)
+    fmax = np.zeros(pb.sys_size)
+    nfb = _load().oracle_rhs(ctypes.byref(pb.params()), _dp(q), _dp(out), _dp(fmax))
+    out = out.reshape(pb.shape())
+    if return_info:
+        return out, fmax, int(nfb)
+    return out
+
+
+def rhs_cells(pb: Problem, q, cells) -> np.ndarray:
+    """R at the given flat cell indices; result [len(cells)][sys_size]."""
+    q = _state(pb, q)
+    cells = np.ascontiguousarray(cells, dtype=np.int64)
+    out = np.empty((cells.size, pb.sys_size))
+    _load().oracle_rhs_cells(ctypes.byref(pb.params()), _dp(q), cells.size,
+                             cells.ctypes.data_as(ctypes.POINTER(ctypes.c_long)), _dp(out))
+    return out
+
+
+def weno5(v, eps=1e-6) -> float:
+    v = np.ascontiguousarray(v, dtype=np.float64)
+    return _load().oracle_weno5(_dp(v), eps)
+
+
+def weno5_weights(v, eps=1e-6):
+    v = np.ascontiguousarray(v, dtype=np.float64)
+    om = np.zeros(3)
+    cand = np.zeros(3)
+    _load().oracle_weno5_weights(_dp(v), eps, _dp(om), _dp(cand))
+    return om, cand
+
+
+def weno5_beta(v):
+    v = np.ascontiguousarray(v, dtype=np.float64)
+    b = np.zeros(3)
+    _load().oracle_weno5_beta(_dp(v), _dp(b))
+    return b
+
+
+def hllc(pb: Problem, d: int, wL, wR):
+    wL = np.ascontiguousarray(wL, dtype=np.float64)
+    wR = np.ascontiguousarray(wR, dtype=np.float64)
+    F = np.zeros(pb.sys_size)
+    ut = np.zeros(1)
+    _load().oracle_hllc(ctypes.byref(pb.params()), d, _dp(wL), _dp(wR), _dp(F), _dp(ut))
+    return F, float(ut[0])
+
+
+def cons_from_prim_cell(pb: Problem, w):
+    w = np.ascontiguousarray(w, dtype=np.float64)
+    q = np.zeros(pb.sys_size)
+    _load().oracle_prim_to_cons(ctypes.byref(pb.params()), _dp(w), _dp(q))
+    return q
+
+
+def prim_from_cons_cell(pb: Problem, q):
+    q = np.ascontiguousarray(q, dtype=np.float64)
+    w = np.zeros(pb.sys_size)
+    _load().oracle_cons_to_prim(ctypes.byref(pb.params()), _dp(q), _dp(w))
+    return w
+
+
+def max_rate(pb: Problem, q):
+    """max_cells max_d (|u_d| + c)/dx_d and the number of non-physical cells."""
+    q = _state(pb, q)
+    bad = ctypes.c_long(0)
+    m = _load().oracle_max_rate(ctypes.byref(pb.params()), _dp(q), ctypes.byref(bad))
+    return m, int(bad.value)
+
+
+def cfl_dt(pb: Problem, q, cfl: float) -> float:
+    """Time step from the CFL condition: dt = CFL / max_d max_cells (|u_d|+c)/dx_d."""
+    m, bad = max_rate(pb, q)
+    if bad:
+        raise FloatingPointError("non-physical state in %d cells" % bad)
+    return cfl / m
+
+
+def rk3_step(pb: Problem, q, dt: float, rhs_fn=None):
+    """One SSP-RK3 step in Shu-Osher form (Gottlieb & Shu 1998; Sec. 3.4):
+    q1 = q + dt R(q); q2 = 3/4 q + 1/4 (q1 + dt R(q1)); q' = 1/3 q + 2/3 (q2 + dt R(q2)).
+    """
+    f = rhs_fn if rhs_fn is not None else (lambda s: rhs(pb, s))
+    q = np.asarray(q, dtype=np.float64)
+    q1 = q + dt * f(q)
+    q2 = 0.75 * q + 0.25 * (q1 + dt * f(q1))
+    return q / 3.0 + (2.0 / 3.0) * (q2 + dt * f(q2))
+
+
+def run(pb: Problem, q, t_end: float, cfl: float, max_steps: int = 10 ** 7):
+    """March to t_end with CFL time steps, clipping the last step to hit t_end."""
+    t = 0.0
+    steps = 0
+    q = np.array(q, dtype=np.float64)
+    while t < t_end and steps < max_steps:
+        dt = cfl_dt(pb, q, cfl)
+        if t + dt > t_end:
+            dt = t_end - t
+        q = rk3_step(pb, q, dt)
+        t += dt
+        steps += 1
+    return q, t, steps

@@ -1,0 +1,449 @@
+/*
+ * Plain, slow CPU FP64 oracle for the right-hand side of the five-equation
+ * (Allaire) diffuse-interface model with stiffened-gas fluids.
+ *
+ * TEST INFRASTRUCTURE ONLY.  Nothing in the product path may link, load or
+ * call this file; it exists so tests, the smoke check and the CPU baseline can
+ * compare the CUDA path against an independent definition.  It shares no code,
+ * header, table or constant with the CUDA sources.
+ *
+ * What it computes (arXiv 2305.09163):
+ *   - Model (Sec. 2.1, "5-equation models"): partial densities a_k r_k, mixture
+ *     momentum r u, total energy r E and volume fractions a_k, with the Kapila
+ *     source K div(u) dropped (the Allaire reduction stated at the end of
+ *     Sec. 2.1).  N fluids carry N-1 transported volume fractions; a_N = 1 - sum.
+ *   - EOS (Sec. 2.1, Eq. "soe"): stiffened gas.  Mixture closure
+ *     r E = Gamma p + Pi + 0.5 r |u|^2, Gamma = sum a_k/(g_k-1),
+ *     Pi = sum a_k g_k pinf_k/(g_k-1); sound speed c^2 = ((Gamma+1)p+Pi)/(Gamma r).
+ *   - Finite volumes (Sec. 3.1, Eqs. "fvm" and "fvmdis"):
+ *     dq/dt = sum_d (F_{-1/2} - F_{+1/2})/dx_d - h(q) div(u), with h = -a_k in the
+ *     volume-fraction rows and div(u) from face velocities (Sec. 3.1, last eq.).
+ *   - Reconstruction (Sec. 3.2): WENO5-JS on the primitive variables
+ *     (a_k r_k, u, p, a_k), one variable at a time, textbook Jiang-Shu
+ *     candidates, smoothness indicators and ideal weights (0.1, 0.6, 0.3).
+ *   - Riemann solver (Sec. 3.2.1): HLLC, Davis wave-speed estimates, star states
+ *     with continuity of normal velocity and pressure, four-branch flux.
+ *     Face velocity = HLLC flux of a volume fraction divided by that fraction.
+ *   - Boundaries (Sec. 3.3): ghost cells three deep (WENO5 order); periodic,
+ *     transmissive (copy of the nearest interior cell) and reflective (mirror,
+ *     normal momentum negated).
+ *
+ * Optional first-order fallback (Sec. 3.2, first-order reconstruction): when a
+ * reconstructed face state has a negative partial density, a volume fraction
+ * outside [0,1] or (Gamma+1)p+Pi <= 0, both sides of that face use the cell
+ * values instead.  Off unless params->fallback is set.
+ *
+ * Built with -O2 -ffp-contract=off so that no multiply-add is fused.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define OR_MAXF 3             /* fluids */
+#define OR_MAXV (2 * OR_MAXF + 3) /* conserved variables */
+
+typedef struct {
+    int n[3];          /* cells per direction; 1 for an inactive direction */
+    int ndim;          /* 1, 2 or 3: directions 0..ndim-1 are active */
+    int nf;            /* number of fluids, 1..3 */
+    double dx[3];      /* uniform cell widths */
+    int bc[6];         /* -x,+x,-y,+y,-z,+z: 0 periodic, 1 transmissive, 2 reflective */
+    double gamma[OR_MAXF];
+    double pi_inf[OR_MAXF];
+    double eps;        /* WENO epsilon */
+    int fallback;      /* first-order fallback at non-physical faces */
+} oracle_params;
+
+/* ---- variable indexing (conserved and primitive share positions) ---- */
+static int sys_size(const oracle_params *P) { return 2 * P->nf + P->ndim; }
+static int i_mom(const oracle_params *P, int d) { return P->nf + d; }
+static int i_E(const oracle_params *P) { return P->nf + P->ndim; }
+static int i_alpha(const oracle_params *P, int k) { return P->nf + P->ndim + 1 + k; }
+
+int oracle_sys_size(const oracle_params *P) { return sys_size(P); }
+
+/* Volume fractions of all N fluids from the N-1 transported ones. */
+static void all_alphas(const oracle_params *P, const double *v, double *a) {
+    double s = 0.0;
+    for (int k = 0; k < P->nf - 1; ++k) { a[k] = v[i_alpha(P, k)]; s += a[k]; }
+    a[P->nf - 1] = 1.0 - s;
+}
+
+/* Mixture Gamma = sum a_k/(g_k-1) and Pi = sum a_k g_k pinf_k/(g_k-1). */
+static void mixture(const oracle_params *P, const double *v, double *Gam, double *Pi) {
+    double a[OR_MAXF];
+    all_alphas(P, v, a);
+    double G = 0.0, Q = 0.0;
+    for (int k = 0; k < P->nf; ++k) {
+        G += a[k] / (P->gamma[k] - 1.0);
+        Q += a[k] * P->gamma[k] * P->pi_inf[k] / (P->gamma[k] - 1.0);
+    }
+    *Gam = G; *Pi = Q;
+}
+
+static double density(const oracle_params *P, const double *v) {
+    double r = 0.0;
+    for (int k = 0; k < P->nf; ++k) r += v[k];
+    return r;
+}
+
+/* Conserved -> primitive for one cell (EOS solved for p). */
+void oracle_cons_to_prim(const oracle_params *P, const double *q, double *w) {
+    int ns = sys_size(P);
+    double r = density(P, q);
+    double ke = 0.0;
+    for (int k = 0; k < ns; ++k) w[k] = q[k];
+    for (int d = 0; d < P->ndim; ++d) {
+        double u = q[i_mom(P, d)] / r;
+        w[i_mom(P, d)] = u;
+        ke += 0.5 * r * u * u;
+    }
+    double G, Q;
+    mixture(P, q, &G, &Q);
+    w[i_E(P)] = (q[i_E(P)] - ke - Q) / G;
+}
+
+/* Primitive -> conserved for one cell. */
+void oracle_prim_to_cons(const oracle_params *P, const double *w, double *q) {
+    int ns = sys_size(P);
+    double r = density(P, w);
+    double ke = 0.0;
+    for (int k = 0; k < ns; ++k) q[k] = w[k];
+    for (int d = 0; d < P->ndim; ++d) {
+        double u = w[i_mom(P, d)];
+        q[i_mom(P, d)] = r * u;
+        ke += 0.5 * r * u * u;
+    }
+    double G, Q;
+    mixture(P, w, &G, &Q);
+    q[i_E(P)] = G * w[i_E(P)] + Q + ke;
+}
+
+void oracle_prim_to_cons_array(const oracle_params *P, const double *w, double *q, long ncell) {
+    int ns = sys_size(P);
+#pragma omp parallel for schedule(static)
+    for (long c = 0; c < ncell; ++c) {
+        double wc[OR_MAXV], qc[OR_MAXV];
+        for (int v = 0; v < ns; ++v) wc[v] = w[(long)v * ncell + c];
+        oracle_prim_to_cons(P, wc, qc);
+        for (int v = 0; v < ns; ++v) q[(long)v * ncell + c] = qc[v];
+    }
+}
+
+void oracle_cons_to_prim_array(const oracle_params *P, const double *q, double *w, long ncell) {
+    int ns = sys_size(P);
+#pragma omp parallel for schedule(static)
+    for (long c = 0; c < ncell; ++c) {
+        double wc[OR_MAXV], qc[OR_MAXV];
+        for (int v = 0; v < ns; ++v) qc[v] = q[(long)v * ncell + c];
+        oracle_cons_to_prim(P, qc, wc);
+        for (int v = 0; v < ns; ++v) w[(long)v * ncell + c] = wc[v];
+    }
+}
+
+/* Squared sound speed ((Gamma+1)p + Pi)/(Gamma rho) of a primitive state. */
+static double sound_speed_sq(const oracle_params *P, const double *w) {
+    double G, Q;
+    mixture(P, w, &G, &Q);
+    return ((G + 1.0) * w[i_E(P)] + Q) / (G * density(P, w));
+}
+
+/* ---- WENO5-JS (Jiang & Shu 1996; Sec. 3.2) ----
+ * v[0..4] = values of cells i-2..i+2; returns the left-biased value at i+1/2.
+ * The value at i-1/2 seen from cell i is the same call on the reversed stencil.
+ */
+void oracle_weno5_weights(const double *v, double eps, double *omega, double *cand) {
+    double p0 = (2.0 * v[0] - 7.0 * v[1] + 11.0 * v[2]) / 6.0;
+    double p1 = (-v[1] + 5.0 * v[2] + 2.0 * v[3]) / 6.0;
+    double p2 = (2.0 * v[2] + 5.0 * v[3] - v[4]) / 6.0;
+    double t;
+    double b0, b1, b2;
+    t = v[0] - 2.0 * v[1] + v[2];
+    b0 = 13.0 / 12.0 * t * t;
+    t = v[0] - 4.0 * v[1] + 3.0 * v[2];
+    b0 += 0.25 * t * t;
+    t = v[1] - 2.0 * v[2] + v[3];
+    b1 = 13.0 / 12.0 * t * t;
+    t = v[1] - v[3];
+    b1 += 0.25 * t * t;
+    t = v[2] - 2.0 * v[3] + v[4];
+    b2 = 13.0 / 12.0 * t * t;
+    t = 3.0 * v[2] - 4.0 * v[3] + v[4];
+    b2 += 0.25 * t * t;
+    double a0 = 0.1 / ((eps + b0) * (eps + b0));
+    double a1 = 0.6 / ((eps + b1) * (eps + b1));
+    double a2 = 0.3 / ((eps + b2) * (eps + b2));
+    double s = a0 + a1 + a2;
+    omega[0] = a0 / s; omega[1] = a1 / s; omega[2] = a2 / s;
+    if (cand) { cand[0] = p0; cand[1] = p1; cand[2] = p2; }
+}
+
+double oracle_weno5(const double *v, double eps) {
+    double om[3], c[3];
+    oracle_weno5_weights(v, eps, om, c);
+    return om[0] * c[0] + om[1] * c[1] + om[2] * c[2];
+}
+
+/* Smoothness indicators alone (for tests against their integral definition). */
+void oracle_weno5_beta(const double *v, double *beta) {
+    double t;
+    t = v[0] - 2.0 * v[1] + v[2]; beta[0] = 13.0 / 12.0 * t * t;
+    t = v[0] - 4.0 * v[1] + 3.0 * v[2]; beta[0] += 0.25 * t * t;
+    t = v[1] - 2.0 * v[2] + v[3]; beta[1] = 13.0 / 12.0 * t * t;
+    t = v[1] - v[3]; beta[1] += 0.25 * t * t;
+    t = v[2] - 2.0 * v[3] + v[4]; beta[2] = 13.0 / 12.0 * t * t;
+    t = 3.0 * v[2] - 4.0 * v[3] + v[4]; beta[2] += 0.25 * t * t;
+}
+
+/* ---- physical flux in direction d of a primitive state (Sec. 2.1 equations) ---- */
+static void physical_flux(const oracle_params *P, int d, const double *w, double *F) {
+    int ns = sys_size(P);
+    double r = density(P, w);
+    double un = w[i_mom(P, d)];
+    double p = w[i_E(P)];
+    double G, Q;
+    mixture(P, w, &G, &Q);
+    double ke = 0.0;
+    for (int e = 0; e < P->ndim; ++e) ke += 0.5 * r * w[i_mom(P, e)] * w[i_mom(P, e)];
+    double rE = G * p + Q + ke;
+    for (int k = 0; k < P->nf; ++k) F[k] = w[k] * un;
+    for (int e = 0; e < P->ndim; ++e) F[i_mom(P, e)] = r * w[i_mom(P, e)] * un;
+    F[i_mom(P, d)] += p;
+    F[i_E(P)] = (rE + p) * un;
+    for (int k = 0; k < P->nf - 1; ++k) F[i_alpha(P, k)] = w[i_alpha(P, k)] * un;
+    (void)ns;
+}
+
+/* Conserved vector of a primitive state (local helper for the star states). */
+static void cons_of(const oracle_params *P, const double *w, double *q) {
+    oracle_prim_to_cons(P, w, q);
+}
+
+/* HLLC star state q*_K (Sec. 3.2.1): continuity of u_n and p across s*. */
+static void star_state(const oracle_params *P, int d, const double *w, double sK, double ss,
+                       double *qs) {
+    int ns = sys_size(P);
+    double q[OR_MAXV];
+    cons_of(P, w, q);
+    double r = density(P, w);
+    double un = w[i_mom(P, d)];
+    double p = w[i_E(P)];
+    double xi = (sK - un) / (sK - ss);
+    for (int k = 0; k < P->nf; ++k) qs[k] = xi * w[k];
+    for (int e = 0; e < P->ndim; ++e) qs[i_mom(P, e)] = xi * r * w[i_mom(P, e)];
+    qs[i_mom(P, d)] = xi * r * ss;
+    qs[i_E(P)] = xi * (q[i_E(P)] + (ss - un) * (r * ss + p / (sK - un)));
+    for (int k = 0; k < P->nf - 1; ++k) qs[i_alpha(P, k)] = xi * w[i_alpha(P, k)];
+    (void)ns;
+}
+
+/* HLLC flux F and face velocity ut between primitive states wL | wR, normal d. */
+void oracle_hllc(const oracle_params *P, int d, const double *wL, const double *wR,
+                 double *F, double *ut) {
+    int ns = sys_size(P);
+    double rL = density(P, wL), rR = density(P, wR);
+    double uL = wL[i_mom(P, d)], uR = wR[i_mom(P, d)];
+    double pL = wL[i_E(P)], pR = wR[i_E(P)];
+    double cL = sqrt(sound_speed_sq(P, wL));
+    double cR = sqrt(sound_speed_sq(P, wR));
+    /* Davis direct wave-speed estimates */
+    double sL = fmin(uL - cL, uR - cR);
+    double sR = fmax(uL + cL, uR + cR);
+    double ss = (pR - pL + rL * uL * (sL - uL) - rR * uR * (sR - uR)) /
+                (rL * (sL - uL) - rR * (sR - uR));
+    if (0.0 <= sL) {
+        physical_flux(P, d, wL, F);
+        *ut = uL;
+    } else if (0.0 <= ss) {
+        double FL[OR_MAXV], qL[OR_MAXV], qs[OR_MAXV];
+        physical_flux(P, d, wL, FL);
+        cons_of(P, wL, qL);
+        star_state(P, d, wL, sL, ss, qs);
+        for (int v = 0; v < ns; ++v) F[v] = FL[v] + sL * (qs[v] - qL[v]);
+        *ut = uL + sL * ((sL - uL) / (sL - ss) - 1.0);
+    } else if (0.0 < sR) {
+        double FR[OR_MAXV], qR[OR_MAXV], qs[OR_MAXV];
+        physical_flux(P, d, wR, FR);
+        cons_of(P, wR, qR);
+        star_state(P, d, wR, sR, ss, qs);
+        for (int v = 0; v < ns; ++v) F[v] = FR[v] + sR * (qs[v] - qR[v]);
+        *ut = uR + sR * ((sR - uR) / (sR - ss) - 1.0);
+    } else {
+        physical_flux(P, d, wR, F);
+        *ut = uR;
+    }
+}
+
+/* ---- ghost cells by index mapping (Sec. 3.3) ---- */
+/* Fetch the conserved vector of cell (i,j,k); indices may lie in the ghost
+ * layers of at most one direction. */
+static void fetch_cell(const oracle_params *P, const double *q, int idx[3], double *qc) {
+    int ns = sys_size(P);
+    int flip = -1;
+    int ii[3] = {idx[0], idx[1], idx[2]};
+    for (int d = 0; d < 3; ++d) {
+        int n = P->n[d];
+        if (ii[d] < 0) {
+            int bc = P->bc[2 * d];
+            if (bc == 0) ii[d] += n;
+            else if (bc == 1) ii[d] = 0;
+            else { ii[d] = -ii[d] - 1; flip = d; }
+        } else if (ii[d] >= n) {
+            int bc = P->bc[2 * d + 1];
+            if (bc == 0) ii[d] -= n;
+            else if (bc == 1) ii[d] = n - 1;
+            else { ii[d] = 2 * n - 1 - ii[d]; flip = d; }
+        }
+    }
+    long ncell = (long)P->n[0] * P->n[1] * P->n[2];
+    long c = ((long)ii[2] * P->n[1] + ii[1]) * P->n[0] + ii[0];
+    for (int v = 0; v < ns; ++v) qc[v] = q[(long)v * ncell + c];
+    if (flip >= 0) qc[i_mom(P, flip)] = -qc[i_mom(P, flip)];
+}
+
+static int face_state_ok(const oracle_params *P, const double *w) {
+    for (int k = 0; k < P->nf; ++k)
+        if (!(w[k] >= 0.0)) return 0;
+    double a[OR_MAXF];
+    all_alphas(P, w, a);
+    for (int k = 0; k < P->nf; ++k)
+        if (!(a[k] >= 0.0 && a[k] <= 1.0)) return 0;
+    if (!(density(P, w) > 0.0)) return 0;
+    double G, Q;
+    mixture(P, w, &G, &Q);
+    if (!((G + 1.0) * w[i_E(P)] + Q > 0.0)) return 0;
+    return 1;
+}
+
+/* Flux through the face on the low side of cell (i,j,k) in direction d, i.e.
+ * between cells idx - e_d and idx.  Returns 1 if the first-order fallback was
+ * used at this face. */
+int oracle_face(const oracle_params *P, const double *q, int d, int i, int j, int k,
+                double *F, double *ut) {
+    int ns = sys_size(P);
+    double w[6][OR_MAXV];
+    for (int s = 0; s < 6; ++s) {
+        int idx[3] = {i, j, k};
+        idx[d] += s - 3; /* cells -3..+2 relative to the face's high side */
+        double qc[OR_MAXV];
+        fetch_cell(P, q, idx, qc);
+        oracle_cons_to_prim(P, qc, w[s]);
+    }
+    double wL[OR_MAXV], wR[OR_MAXV];
+    for (int v = 0; v < ns; ++v) {
+        double st[5];
+        for (int s = 0; s < 5; ++s) st[s] = w[s][v];       /* cells -3..+1, centre -1 */
+        wL[v] = oracle_weno5(st, P->eps);
+        for (int s = 0; s < 5; ++s) st[s] = w[5 - s][v];   /* cells +2..-2, centre 0 */
+        wR[v] = oracle_weno5(st, P->eps);
+    }
+    int fb = 0;
+    if (P->fallback && !(face_state_ok(P, wL) && face_state_ok(P, wR))) {
+        for (int v = 0; v < ns; ++v) { wL[v] = w[2][v]; wR[v] = w[3][v]; }
+        fb = 1;
+    }
+    oracle_hllc(P, d, wL, wR, F, ut);
+    return fb;
+}
+
+/* Full right-hand side R(q), Eq. "fvmdis".  Also returns, per variable, the
+ * largest |F| over all faces (a scale for relative error measures), and the
+ * number of faces that used the first-order fallback. */
+long oracle_rhs(const oracle_params *P, const double *q, double *rhs, double *fmax) {
+    int ns = sys_size(P);
+    int nx = P->n[0], ny = P->n[1], nz = P->n[2];
+    long ncell = (long)nx * ny * nz;
+    long nfb = 0;
+    for (int v = 0; v < ns; ++v) fmax[v] = 0.0;
+    memset(rhs, 0, sizeof(double) * (size_t)ns * (size_t)ncell);
+    for (int d = 0; d < P->ndim; ++d) {
+        int m[3] = {nx, ny, nz};
+        m[d] += 1; /* faces along d */
+        long nface = (long)m[0] * m[1] * m[2];
+        double *Ff = (double *)malloc(sizeof(double) * (size_t)(ns + 1) * (size_t)nface);
+#pragma omp parallel for schedule(static) reduction(+ : nfb)
+        for (long f = 0; f < nface; ++f) {
+            int i = (int)(f % m[0]);
+            int j = (int)((f / m[0]) % m[1]);
+            int k = (int)(f / ((long)m[0] * m[1]));
+            double F[OR_MAXV], ut;
+            nfb += oracle_face(P, q, d, i, j, k, F, &ut);
+            for (int v = 0; v < ns; ++v) Ff[(long)v * nface + f] = F[v];
+            Ff[(long)ns * nface + f] = ut;
+        }
+        for (int v = 0; v < ns; ++v)
+            for (long f = 0; f < nface; ++f)
+                if (fabs(Ff[(long)v * nface + f]) > fmax[v]) fmax[v] = fabs(Ff[(long)v * nface + f]);
+        double inv = 1.0 / P->dx[d];
+#pragma omp parallel for schedule(static)
+        for (long c = 0; c < ncell; ++c) {
+            int ci[3] = {(int)(c % nx), (int)((c / nx) % ny), (int)(c / ((long)nx * ny))};
+            int hi[3] = {ci[0], ci[1], ci[2]};
+            hi[d] += 1;
+            long flo = ((long)ci[2] * m[1] + ci[1]) * m[0] + ci[0];
+            long fhi = ((long)hi[2] * m[1] + hi[1]) * m[0] + hi[0];
+            for (int v = 0; v < ns; ++v)
+                rhs[(long)v * ncell + c] += (Ff[(long)v * nface + flo] - Ff[(long)v * nface + fhi]) * inv;
+            double divu = (Ff[(long)ns * nface + fhi] - Ff[(long)ns * nface + flo]) * inv;
+            for (int a = 0; a < P->nf - 1; ++a) {
+                long o = (long)i_alpha(P, a) * ncell + c;
+                rhs[o] += q[o] * divu;
+            }
+        }
+        free(Ff);
+    }
+    return nfb;
+}
+
+/* R at selected cells only (flat cell indices), computed face by face from the
+ * same definitions; out is [ncells][sys_size]. */
+void oracle_rhs_cells(const oracle_params *P, const double *q, long nsel, const long *cells,
+                      double *out) {
+    int ns = sys_size(P);
+    int nx = P->n[0], ny = P->n[1];
+    long ncell = (long)nx * ny * P->n[2];
+#pragma omp parallel for schedule(dynamic, 16)
+    for (long s = 0; s < nsel; ++s) {
+        long c = cells[s];
+        int ci[3] = {(int)(c % nx), (int)((c / nx) % ny), (int)(c / ((long)nx * ny))};
+        double *o = out + s * ns;
+        for (int v = 0; v < ns; ++v) o[v] = 0.0;
+        for (int d = 0; d < P->ndim; ++d) {
+            double Flo[OR_MAXV], Fhi[OR_MAXV], ulo, uhi;
+            oracle_face(P, q, d, ci[0], ci[1], ci[2], Flo, &ulo);
+            int hi[3] = {ci[0], ci[1], ci[2]};
+            hi[d] += 1;
+            oracle_face(P, q, d, hi[0], hi[1], hi[2], Fhi, &uhi);
+            double inv = 1.0 / P->dx[d];
+            for (int v = 0; v < ns; ++v) o[v] += (Flo[v] - Fhi[v]) * inv;
+            double divu = (uhi - ulo) * inv;
+            for (int a = 0; a < P->nf - 1; ++a)
+                o[i_alpha(P, a)] += q[(long)i_alpha(P, a) * ncell + c] * divu;
+        }
+    }
+}
+
+/* max over cells of max_d (|u_d| + c)/dx_d; *bad counts cells with a
+ * non-finite state or c^2 <= 0. */
+double oracle_max_rate(const oracle_params *P, const double *q, long *bad) {
+    int ns = sys_size(P);
+    long ncell = (long)P->n[0] * P->n[1] * P->n[2];
+    double m = 0.0;
+    long nbad = 0;
+#pragma omp parallel for schedule(static) reduction(max : m) reduction(+ : nbad)
+    for (long c = 0; c < ncell; ++c) {
+        double qc[OR_MAXV], w[OR_MAXV];
+        for (int v = 0; v < ns; ++v) qc[v] = q[(long)v * ncell + c];
+        oracle_cons_to_prim(P, qc, w);
+        double c2 = sound_speed_sq(P, w);
+        if (!(c2 > 0.0) || !isfinite(c2)) { nbad += 1; continue; }
+        double cs = sqrt(c2);
+        for (int d = 0; d < P->ndim; ++d) {
+            double r = (fabs(w[i_mom(P, d)]) + cs) / P->dx[d];
+            if (r > m) m = r;
+        }
+    }
+    *bad = nbad;
+    return m;
+}
