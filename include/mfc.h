@@ -1,0 +1,145 @@
+/*
+ * mfc.h -- C ABI of the GB300 (sm_103a) right-hand-side library for the
+ * five-equation diffuse-interface model with stiffened-gas fluids
+ * (arXiv 2305.09163).
+ *
+ * One context = one uniform structured grid on one GPU, its boundary types,
+ * its fluids and a CUDA stream.  All device work of a context is enqueued on
+ * that stream.  Every call returns an mfc_status and never aborts; the text of
+ * the last error is kept per context (mfc_last_error).  After MFC_ERR_CUDA the
+ * context is unusable except for mfc_finalize.
+ *
+ * Layout of every state array (conserved q, primitive w, right-hand side R):
+ * structure of arrays, float64, [sys_size][nz][ny][nx] with x fastest;
+ * sys_size = 2*N + d for N fluids and d active dimensions.  Variable order
+ * (Sec. 2.1, "5-equation models"):
+ *     conserved q: a_1 r_1 .. a_N r_N, r u_x [, r u_y, r u_z], r E, a_1 .. a_{N-1}
+ *     primitive w: a_1 r_1 .. a_N r_N,   u_x [,   u_y,   u_z],   p, a_1 .. a_{N-1}
+ * where a_k are volume fractions (a_N = 1 - sum of the others), r_k phase
+ * densities, u the mixture velocity, E the total energy and p the pressure.
+ *
+ * Pointers: "on_device" = 1 means a device pointer on the context's GPU
+ * (e.g. a contiguous float64 torch tensor's data_ptr), used in stream order;
+ * 0 means host memory, and the call returns after the copy completes.  The
+ * caller owns every q / w / rhs buffer it passes; the library owns its own
+ * device state and releases it in mfc_finalize.
+ */
+#ifndef MFC_GB300_H
+#define MFC_GB300_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct mfc_ctx mfc_ctx;
+
+typedef enum {
+    MFC_OK = 0,
+    MFC_ERR_ARG = 1,          /* invalid argument; nothing was changed */
+    MFC_ERR_STATE_UNSET = 2,  /* no state has been set on this context */
+    MFC_ERR_OOM = 3,          /* device allocation failed */
+    MFC_ERR_CUDA = 4,         /* CUDA error; the context is now unusable */
+    MFC_ERR_NONPHYSICAL = 5,  /* non-finite state or c^2 <= 0 somewhere */
+    MFC_ERR_TIMEOUT = 6       /* reserved: a bounded device wait expired */
+} mfc_status;
+
+typedef enum { MFC_BC_PERIODIC = 0, MFC_BC_TRANSMISSIVE = 1, MFC_BC_REFLECTIVE = 2 } mfc_bc;
+
+/* Arithmetic of the reconstruction and Riemann solver:
+ *   MFC_FP64    everything in float64;
+ *   MFC_MIXED   WENO5 and HLLC in float32; pressure recovery from total energy
+ *               and the Runge-Kutta accumulation stay float64;
+ *   MFC_LEARNED as MFC_MIXED, with WENO5 nonlinear weights from a small MLP
+ *               (mfc_set_mlp) except where the shock/interface sensor or the
+ *               positivity check trips, where WENO5-JS weights are used. */
+typedef enum { MFC_FP64 = 0, MFC_MIXED = 1, MFC_LEARNED = 2 } mfc_precision;
+
+/* Create a context (Sec. 3.1: uniform structured grid; Sec. 3.3: ghost-cell
+ * boundaries; Sec. 2.1: stiffened-gas fluids).
+ *   nx, ny, nz   cells per direction; 1D: ny = nz = 1, 2D: nz = 1.  Every
+ *                active direction needs at least 3 cells.
+ *   lo, hi       domain corners [3] (only active directions are used).
+ *   bc           [6] boundary types for -x,+x,-y,+y,-z,+z (mfc_bc); periodic
+ *                must be set on both faces of a direction.
+ *   num_fluids   N in 1..3; gamma[N] > 1, pi_inf[N] >= 0 (Pa).
+ *   precision    mfc_precision.
+ *   cuda_stream  cudaStream_t to use, or NULL for the legacy default stream.
+ * Allocates the state, one stage buffer, a primitive buffer and a
+ * right-hand-side accumulator on the current CUDA device.
+ * Errors: MFC_ERR_ARG (bad sizes / parameters; *out untouched),
+ * MFC_ERR_OOM, MFC_ERR_CUDA. */
+mfc_status mfc_init(mfc_ctx** out, int nx, int ny, int nz, const double lo[3], const double hi[3],
+                    const int bc[6], int num_fluids, const double* gamma, const double* pi_inf,
+                    int precision, void* cuda_stream);
+
+/* Set a numerical parameter by name:
+ *   "weno_eps"   epsilon of the WENO5-JS weights (Sec. 3.2), default 1e-6,
+ *                valid range [1e-30, 1];
+ *   "fallback"   1 (default) / 0: first-order reconstruction (Sec. 3.2) at a
+ *                face whose reconstructed state is non-physical;
+ *   "segment"    cells per thread along a sweep (8..256), 0 = automatic;
+ *   "profile"    1 / 0: time every kernel launch with CUDA events.
+ * Errors: MFC_ERR_ARG for an unknown name or out-of-range value. */
+mfc_status mfc_set_param(mfc_ctx* ctx, const char* name, double value);
+
+/* Copy a conserved state q (layout above) into the context. */
+mfc_status mfc_set_state(mfc_ctx* ctx, const double* q, int on_device);
+
+/* Set the state from primitive variables w (layout above); the conversion
+ * rho E = Gamma p + Pi + rho|u|^2/2 (Sec. 2.1, Eq. "soe" with the mixture
+ * rules) runs on the GPU. */
+mfc_status mfc_set_state_prim(mfc_ctx* ctx, const double* w, int on_device);
+
+/* Copy the current conserved state out. */
+mfc_status mfc_get_state(mfc_ctx* ctx, double* q, int on_device);
+
+/* R(q) of Eq. "fvmdis" (Sec. 3.1) for the current state: WENO5 reconstruction
+ * of primitives, HLLC fluxes, flux divergence and the a_k div(u) source of the
+ * volume-fraction rows, written to rhs (layout above).
+ * Errors: MFC_ERR_STATE_UNSET, MFC_ERR_ARG (NULL rhs), MFC_ERR_CUDA. */
+mfc_status mfc_rhs(mfc_ctx* ctx, double* rhs, int on_device);
+
+/* Advance the state by one SSP-RK3 step of size dt (Sec. 3.4):
+ *   q1 = q + dt R(q); q2 = 3/4 q + 1/4 (q1 + dt R(q1)); q' = 1/3 q + 2/3 (q2 + dt R(q2)).
+ * Enqueued on the stream; returns without waiting.
+ * Errors: MFC_ERR_STATE_UNSET, MFC_ERR_ARG (dt not finite or <= 0), MFC_ERR_CUDA. */
+mfc_status mfc_step(mfc_ctx* ctx, double dt);
+
+/* CFL time step of the current state: dt = cfl / max over cells and
+ * directions of (|u_d| + c)/dx_d, with c^2 = ((Gamma+1)p + Pi)/(Gamma rho).
+ * Synchronises the stream (8-byte readback).  Errors: MFC_ERR_NONPHYSICAL if
+ * any cell has a non-finite state or c^2 <= 0 (*dt_out = 0),
+ * MFC_ERR_STATE_UNSET, MFC_ERR_ARG. */
+mfc_status mfc_cfl_dt(mfc_ctx* ctx, double cfl, double* dt_out);
+
+/* Install the learned-weight network (MFC_LEARNED): n floats laid out as
+ * W1[32][5], b1[32], W2[32][32], b2[32], W3[3][32], b3[3] (n = 1315).
+ * Errors: MFC_ERR_ARG (wrong n, context not MFC_LEARNED). */
+mfc_status mfc_set_mlp(mfc_ctx* ctx, const float* params, int n);
+
+/* Number of conserved variables, 2N + d. */
+int mfc_sys_size(const mfc_ctx* ctx);
+
+/* Kernel launches issued by this context so far. */
+long long mfc_launch_count(const mfc_ctx* ctx);
+
+/* Number of faces that used the first-order fallback since the context was
+ * created (synchronises the stream). */
+long long mfc_fallback_count(mfc_ctx* ctx);
+
+/* Per-kernel timing collected while "profile" is on: for category i in
+ * [0, n) (0 prims, 1 sweep_x, 2 sweep_y, 3 sweep_z, 4 prims+cfl, 5 convert,
+ * 6 mlp), total milliseconds and launch counts.  Synchronises the stream.
+ * Returns the number of categories (7). */
+int mfc_profile_read(mfc_ctx* ctx, double* total_ms, long long* launches, int n);
+
+/* Text of the last error on this context ("" if none). */
+const char* mfc_last_error(const mfc_ctx* ctx);
+
+/* Release the context and its device memory. NULL is ignored. */
+void mfc_finalize(mfc_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MFC_GB300_H */

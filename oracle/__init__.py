@@ -82,7 +82,7 @@ def _load():
             lib.oracle_face.restype = ctypes.c_int
             lib.oracle_rhs.argtypes = [P, dp, dp, dp]
             lib.oracle_rhs.restype = ctypes.c_long
-            lib.oracle_rhs_cells.argtypes = [P, dp, ctypes.c_long, lp, dp]
+            lib.oracle_rhs_cells.argtypes = [P, dp, ctypes.c_long, lp, dp, dp]
             lib.oracle_max_rate.argtypes = [P, dp, lp]
             lib.oracle_max_rate.restype = ctypes.c_double
             _lib = lib
@@ -165,13 +165,17 @@ def rhs(pb: Problem, q, return_info: bool = False):
     return out
 
 
-def rhs_cells(pb: Problem, q, cells) -> np.ndarray:
-    """R at the given flat cell indices; result [len(cells)][sys_size]."""
+def rhs_cells(pb: Problem, q, cells, return_fmax: bool = False):
+    """R at the given flat cell indices; result [len(cells)][sys_size]
+    (and, with return_fmax, the per-variable max |F| over the faces visited)."""
     q = _state(pb, q)
     cells = np.ascontiguousarray(cells, dtype=np.int64)
     out = np.empty((cells.size, pb.sys_size))
+    fmax = np.zeros(pb.sys_size)
     _load().oracle_rhs_cells(ctypes.byref(pb.params()), _dp(q), cells.size,
-                             cells.ctypes.data_as(ctypes.POINTER(ctypes.c_long)), _dp(out))
+                             cells.ctypes.data_as(ctypes.POINTER(ctypes.c_long)), _dp(out), _dp(fmax))
+    if return_fmax:
+        return out, fmax
     return out
 
 

@@ -397,13 +397,16 @@ long oracle_rhs(const oracle_params *P, const double *q, double *rhs, double *fm
 }
 
 /* R at selected cells only (flat cell indices), computed face by face from the
- * same definitions; out is [ncells][sys_size]. */
+ * same definitions; out is [ncells][sys_size].  If fmax is not NULL it receives,
+ * per variable, the largest |F| over the faces visited. */
 void oracle_rhs_cells(const oracle_params *P, const double *q, long nsel, const long *cells,
-                      double *out) {
+                      double *out, double *fmax) {
     int ns = sys_size(P);
     int nx = P->n[0], ny = P->n[1];
     long ncell = (long)nx * ny * P->n[2];
-#pragma omp parallel for schedule(dynamic, 16)
+    double fm[OR_MAXV];
+    for (int v = 0; v < ns; ++v) fm[v] = 0.0;
+#pragma omp parallel for schedule(dynamic, 16) reduction(max : fm[:OR_MAXV])
     for (long s = 0; s < nsel; ++s) {
         long c = cells[s];
         int ci[3] = {(int)(c % nx), (int)((c / nx) % ny), (int)(c / ((long)nx * ny))};
@@ -416,12 +419,18 @@ void oracle_rhs_cells(const oracle_params *P, const double *q, long nsel, const 
             hi[d] += 1;
             oracle_face(P, q, d, hi[0], hi[1], hi[2], Fhi, &uhi);
             double inv = 1.0 / P->dx[d];
-            for (int v = 0; v < ns; ++v) o[v] += (Flo[v] - Fhi[v]) * inv;
+            for (int v = 0; v < ns; ++v) {
+                o[v] += (Flo[v] - Fhi[v]) * inv;
+                if (fabs(Flo[v]) > fm[v]) fm[v] = fabs(Flo[v]);
+                if (fabs(Fhi[v]) > fm[v]) fm[v] = fabs(Fhi[v]);
+            }
             double divu = (uhi - ulo) * inv;
             for (int a = 0; a < P->nf - 1; ++a)
                 o[i_alpha(P, a)] += q[(long)i_alpha(P, a) * ncell + c] * divu;
         }
     }
+    if (fmax)
+        for (int v = 0; v < ns; ++v) fmax[v] = fm[v];
 }
 
 /* max over cells of max_d (|u_d| + c)/dx_d; *bad counts cells with a

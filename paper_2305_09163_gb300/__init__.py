@@ -1,0 +1,274 @@
+"""GB300 (sm_103a) right-hand side and SSP-RK3 step of the five-equation
+diffuse-interface model with stiffened-gas fluids (arXiv 2305.09163).
+
+Thin ctypes binding over the C ABI in ``include/mfc.h`` (``libmfc_gb300.so``):
+the functions ``mfc_init`` ... ``mfc_finalize`` keep the C names and only
+marshal arguments; every step of the computation runs in the library's CUDA
+kernels.  ``Solver`` wraps a context for convenience.  Device buffers are torch
+tensors (contiguous float64 on the context's GPU); host buffers are numpy
+arrays.  There is no CPU fallback: if the library is missing or cannot load,
+import of the binding functions raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import _build
+
+MFC_OK = 0
+MFC_ERR_ARG, MFC_ERR_STATE_UNSET, MFC_ERR_OOM, MFC_ERR_CUDA, MFC_ERR_NONPHYSICAL, MFC_ERR_TIMEOUT = 1, 2, 3, 4, 5, 6
+MFC_BC_PERIODIC, MFC_BC_TRANSMISSIVE, MFC_BC_REFLECTIVE = 0, 1, 2
+MFC_FP64, MFC_MIXED, MFC_LEARNED = 0, 1, 2
+PRECISIONS = {"fp64": MFC_FP64, "mixed": MFC_MIXED, "learned": MFC_LEARNED}
+PROFILE_CATEGORIES = ("prims", "sweep_x", "sweep_y", "sweep_z", "prims_cfl", "convert", "mlp")
+MLP_PARAM_COUNT = 32 * 5 + 32 + 32 * 32 + 32 + 3 * 32 + 3
+
+_lib = None
+
+
+class MFCError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__("mfc status %d: %s" % (status, msg))
+        self.status = status
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def build(force: bool = False) -> str:
+    """Compile the CUDA library in-tree (nvcc, sm_103a)."""
+    return _build.build(force=force)
+
+
+def _declare(lib):
+    c_int, c_double, c_void_p, c_char_p = ctypes.c_int, ctypes.c_double, ctypes.c_void_p, ctypes.c_char_p
+    c_ll = ctypes.c_longlong
+    dptr = ctypes.POINTER(c_double)
+    lib.mfc_init.argtypes = [ctypes.POINTER(c_void_p), c_int, c_int, c_int, dptr, dptr,
+                             ctypes.POINTER(c_int), c_int, dptr, dptr, c_int, c_void_p]
+    lib.mfc_init.restype = c_int
+    lib.mfc_set_param.argtypes = [c_void_p, c_char_p, c_double]
+    lib.mfc_set_param.restype = c_int
+    for name in ("mfc_set_state", "mfc_set_state_prim", "mfc_get_state", "mfc_rhs"):
+        f = getattr(lib, name)
+        f.argtypes = [c_void_p, c_void_p, c_int]
+        f.restype = c_int
+    lib.mfc_step.argtypes = [c_void_p, c_double]
+    lib.mfc_step.restype = c_int
+    lib.mfc_cfl_dt.argtypes = [c_void_p, c_double, dptr]
+    lib.mfc_cfl_dt.restype = c_int
+    lib.mfc_set_mlp.argtypes = [c_void_p, ctypes.POINTER(ctypes.c_float), c_int]
+    lib.mfc_set_mlp.restype = c_int
+    lib.mfc_sys_size.argtypes = [c_void_p]
+    lib.mfc_sys_size.restype = c_int
+    lib.mfc_launch_count.argtypes = [c_void_p]
+    lib.mfc_launch_count.restype = c_ll
+    lib.mfc_fallback_count.argtypes = [c_void_p]
+    lib.mfc_fallback_count.restype = c_ll
+    lib.mfc_profile_read.argtypes = [c_void_p, dptr, ctypes.POINTER(c_ll), c_int]
+    lib.mfc_profile_read.restype = c_int
+    lib.mfc_last_error.argtypes = [c_void_p]
+    lib.mfc_last_error.restype = c_char_p
+    lib.mfc_finalize.argtypes = [c_void_p]
+    lib.mfc_finalize.restype = None
+    return lib
+
+
+def load(build_if_missing: bool = True):
+    """Load libmfc_gb300.so (building it first if it is absent or stale)."""
+    global _lib
+    if _lib is None:
+        if build_if_missing and not _build.up_to_date():
+            _build.build()
+        if not os.path.exists(_build.LIB):
+            raise OSError("libmfc_gb300.so is not built (run paper_2305_09163_gb300.build())")
+        _lib = _declare(ctypes.CDLL(_build.LIB))
+    return _lib
+
+
+def _ptr(buf):
+    """(address, on_device) of a torch tensor or numpy array (float64, contiguous)."""
+    if isinstance(buf, np.ndarray):
+        if buf.dtype != np.float64 or not buf.flags.c_contiguous:
+            raise TypeError("host buffers must be contiguous float64 numpy arrays")
+        return buf.ctypes.data, 0
+    import torch
+    if isinstance(buf, torch.Tensor):
+        if buf.dtype != torch.float64 or not buf.is_contiguous():
+            raise TypeError("tensors must be contiguous float64")
+        return buf.data_ptr(), 1 if buf.is_cuda else 0
+    raise TypeError("expected a numpy array or a torch tensor, got %r" % type(buf))
+
+
+def _check(lib, ctx, status):
+    if status != MFC_OK:
+        msg = lib.mfc_last_error(ctx).decode() if ctx else ""
+        raise MFCError(status, msg)
+
+
+# ---- C ABI, same names -------------------------------------------------------
+def mfc_init(n, lo, hi, bc, gamma, pi_inf, precision=MFC_FP64, stream=None):
+    """Create a context; returns the opaque handle (an int)."""
+    lib = load()
+    n = list(n) + [1] * (3 - len(n))
+    lo3 = (ctypes.c_double * 3)(*(list(lo) + [0.0] * (3 - len(lo))))
+    hi3 = (ctypes.c_double * 3)(*(list(hi) + [1.0] * (3 - len(hi))))
+    bc6 = (ctypes.c_int * 6)(*(list(bc) + [1] * (6 - len(bc))))
+    g = (ctypes.c_double * len(gamma))(*gamma)
+    p = (ctypes.c_double * len(pi_inf))(*pi_inf)
+    h = ctypes.c_void_p()
+    st = lib.mfc_init(ctypes.byref(h), int(n[0]), int(n[1]), int(n[2]), lo3, hi3, bc6, len(gamma), g, p,
+                      int(precision), ctypes.c_void_p(stream or 0))
+    _check(lib, None, st)
+    return h.value
+
+
+def mfc_set_param(ctx, name, value):
+    lib = load()
+    _check(lib, ctx, lib.mfc_set_param(ctx, name.encode(), float(value)))
+
+
+def mfc_set_state(ctx, q):
+    lib = load()
+    a, dev = _ptr(q)
+    _check(lib, ctx, lib.mfc_set_state(ctx, a, dev))
+
+
+def mfc_set_state_prim(ctx, w):
+    lib = load()
+    a, dev = _ptr(w)
+    _check(lib, ctx, lib.mfc_set_state_prim(ctx, a, dev))
+
+
+def mfc_get_state(ctx, q):
+    lib = load()
+    a, dev = _ptr(q)
+    _check(lib, ctx, lib.mfc_get_state(ctx, a, dev))
+
+
+def mfc_rhs(ctx, rhs):
+    lib = load()
+    a, dev = _ptr(rhs)
+    _check(lib, ctx, lib.mfc_rhs(ctx, a, dev))
+
+
+def mfc_step(ctx, dt):
+    lib = load()
+    _check(lib, ctx, lib.mfc_step(ctx, float(dt)))
+
+
+def mfc_cfl_dt(ctx, cfl):
+    lib = load()
+    out = ctypes.c_double(0.0)
+    _check(lib, ctx, lib.mfc_cfl_dt(ctx, float(cfl), ctypes.byref(out)))
+    return out.value
+
+
+def mfc_set_mlp(ctx, params):
+    lib = load()
+    params = np.ascontiguousarray(params, dtype=np.float32)
+    _check(lib, ctx, lib.mfc_set_mlp(ctx, params.ctypes.data_as(ctypes.POINTER(ctypes.c_float)), params.size))
+
+
+def mfc_sys_size(ctx):
+    return load().mfc_sys_size(ctx)
+
+
+def mfc_launch_count(ctx):
+    return load().mfc_launch_count(ctx)
+
+
+def mfc_fallback_count(ctx):
+    return load().mfc_fallback_count(ctx)
+
+
+def mfc_profile_read(ctx):
+    lib = load()
+    ms = (ctypes.c_double * 8)()
+    cnt = (ctypes.c_longlong * 8)()
+    k = lib.mfc_profile_read(ctx, ms, cnt, 8)
+    return {PROFILE_CATEGORIES[i]: (ms[i], cnt[i]) for i in range(min(k, len(PROFILE_CATEGORIES)))}
+
+
+def mfc_last_error(ctx):
+    return load().mfc_last_error(ctx).decode()
+
+
+def mfc_finalize(ctx):
+    if ctx:
+        load().mfc_finalize(ctx)
+
+
+# ---- convenience wrapper ----------------------------------------------------------
+class Solver:
+    """One context: grid, boundaries, fluids, precision, stream."""
+
+    def __init__(self, n, lo, hi, bc, gamma, pi_inf, precision="fp64", stream=None, **params):
+        import torch
+        self.n = tuple(list(n) + [1] * (3 - len(n)))
+        self.ndim = 3 if self.n[2] > 1 else (2 if self.n[1] > 1 else 1)
+        self.nf = len(gamma)
+        self.sys_size = 2 * self.nf + self.ndim
+        self.shape = (self.sys_size, self.n[2], self.n[1], self.n[0])
+        if stream is None:
+            stream = torch.cuda.current_stream().cuda_stream
+        prec = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+        self.ctx = mfc_init(self.n, lo, hi, bc, gamma, pi_inf, prec, stream)
+        for k, v in params.items():
+            mfc_set_param(self.ctx, k, v)
+
+    def set_param(self, name, value):
+        mfc_set_param(self.ctx, name, value)
+
+    def set_state(self, q):
+        mfc_set_state(self.ctx, q)
+
+    def set_state_prim(self, w):
+        mfc_set_state_prim(self.ctx, w)
+
+    def get_state(self, out=None):
+        import torch
+        if out is None:
+            out = torch.empty(self.shape, dtype=torch.float64, device="cuda")
+        mfc_get_state(self.ctx, out)
+        return out
+
+    def rhs(self, out=None):
+        import torch
+        if out is None:
+            out = torch.empty(self.shape, dtype=torch.float64, device="cuda")
+        mfc_rhs(self.ctx, out)
+        return out
+
+    def step(self, dt):
+        mfc_step(self.ctx, dt)
+
+    def cfl_dt(self, cfl):
+        return mfc_cfl_dt(self.ctx, cfl)
+
+    def set_mlp(self, params):
+        mfc_set_mlp(self.ctx, params)
+
+    def launch_count(self):
+        return mfc_launch_count(self.ctx)
+
+    def fallback_count(self):
+        return mfc_fallback_count(self.ctx)
+
+    def profile(self):
+        return mfc_profile_read(self.ctx)
+
+    def close(self):
+        if getattr(self, "ctx", None):
+            mfc_finalize(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,516 @@
+// C ABI of the GB300 five-equation right-hand-side library (declared in
+// include/mfc.h).  Owns the device state of a context and sequences the
+// kernels of one RHS evaluation and one SSP-RK3 step on the context's stream.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/mfc.h"
+#include "mfc_launch.cuh"
+
+using namespace mfc;
+
+namespace {
+
+enum ProfCat { P_PRIMS = 0, P_SWEEP_X, P_SWEEP_Y, P_SWEEP_Z, P_CFL, P_CONVERT, P_MLP, P_NCAT };
+
+struct ProfRec {
+    int cat;
+    cudaEvent_t a, b;
+};
+
+}  // namespace
+
+struct mfc_ctx {
+    int n[3] = {1, 1, 1};
+    int ndim = 1, nf = 1, ns = 3;
+    long long ncell = 0;
+    double lo[3] = {0, 0, 0}, hi[3] = {1, 1, 1};
+    int bc[6] = {1, 1, 1, 1, 1, 1};
+    double gamma[3] = {0, 0, 0}, pi_inf[3] = {0, 0, 0};
+    int precision = MFC_FP64;
+    cudaStream_t stream = nullptr;
+    double eps = 1e-6;
+    int fallback = 1;
+    int seg_override = 0;
+    bool profile = false;
+
+    Geometry g{};
+    EosConst e{};
+
+    double* q = nullptr;      // state q^n
+    double* q1 = nullptr;     // RK stage state
+    double* R = nullptr;      // RHS accumulator
+    void* w = nullptr;        // primitives (double or float)
+    unsigned long long* d_rate = nullptr;  // CFL max (ordered bits)
+    int* d_bad = nullptr;
+    unsigned long long* d_fallback = nullptr;
+    unsigned long long* h_pin = nullptr;   // pinned readback [rate, bad]
+    float* mlp = nullptr;
+
+    bool state_set = false;
+    bool w_valid = false;     // w holds the primitives of q
+    bool dead = false;
+    long long launches = 0;
+    std::string err;
+    std::vector<ProfRec> prof_pending;
+    double prof_ms[P_NCAT] = {0};
+    long long prof_n[P_NCAT] = {0};
+};
+
+namespace {
+
+mfc_status fail(mfc_ctx* c, mfc_status s, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    if (c) {
+        c->err = buf;
+        if (s == MFC_ERR_CUDA) c->dead = true;
+    }
+    return s;
+}
+
+#define MFC_CUDA(ctx, call)                                                                \
+    do {                                                                                   \
+        cudaError_t e_ = (call);                                                           \
+        if (e_ != cudaSuccess)                                                             \
+            return fail((ctx), MFC_ERR_CUDA, "%s: %s", #call, cudaGetErrorString(e_));     \
+    } while (0)
+
+bool is_f32(const mfc_ctx* c) { return c->precision != MFC_FP64; }
+
+size_t real_size(const mfc_ctx* c) { return is_f32(c) ? sizeof(float) : sizeof(double); }
+
+int auto_segment(const mfc_ctx* c, int dir) {
+    if (c->seg_override > 0) return c->seg_override;
+    const int nd = c->n[dir];
+    const long long trans = c->ncell / nd;
+    int L = 64;
+    // keep at least ~8 warps per SM resident while limiting edge recomputation
+    while (L > 8 && trans * ((nd + L - 1) / L) < 152LL * 4 * kSweepThreads) L /= 2;
+    return L;
+}
+
+template <typename F>
+mfc_status launch(mfc_ctx* c, int cat, F&& fn) {
+    cudaEvent_t a = nullptr, b = nullptr;
+    if (c->profile) {
+        MFC_CUDA(c, cudaEventCreate(&a));
+        MFC_CUDA(c, cudaEventCreate(&b));
+        MFC_CUDA(c, cudaEventRecord(a, c->stream));
+    }
+    cudaError_t e = fn();
+    if (e != cudaSuccess) return fail(c, MFC_ERR_CUDA, "kernel launch: %s", cudaGetErrorString(e));
+    c->launches += 1;
+    if (c->profile) {
+        MFC_CUDA(c, cudaEventRecord(b, c->stream));
+        c->prof_pending.push_back({cat, a, b});
+    }
+    return MFC_OK;
+}
+
+cudaError_t dispatch_sweep(const mfc_ctx* c, const SweepArgs& a, int dir) {
+    if (is_f32(c)) {
+        switch (c->nf) {
+            case 1: return launch_sweep<float, 1>(a, c->ndim, dir, c->stream);
+            case 2: return launch_sweep<float, 2>(a, c->ndim, dir, c->stream);
+            default: return launch_sweep<float, 3>(a, c->ndim, dir, c->stream);
+        }
+    }
+    switch (c->nf) {
+        case 1: return launch_sweep<double, 1>(a, c->ndim, dir, c->stream);
+        case 2: return launch_sweep<double, 2>(a, c->ndim, dir, c->stream);
+        default: return launch_sweep<double, 3>(a, c->ndim, dir, c->stream);
+    }
+}
+
+cudaError_t dispatch_prims(const mfc_ctx* c, const PrimArgs& a, bool rate) {
+    if (is_f32(c)) {
+        switch (c->nf) {
+            case 1: return launch_prims<float, 1>(a, c->ndim, rate, c->stream);
+            case 2: return launch_prims<float, 2>(a, c->ndim, rate, c->stream);
+            default: return launch_prims<float, 3>(a, c->ndim, rate, c->stream);
+        }
+    }
+    switch (c->nf) {
+        case 1: return launch_prims<double, 1>(a, c->ndim, rate, c->stream);
+        case 2: return launch_prims<double, 2>(a, c->ndim, rate, c->stream);
+        default: return launch_prims<double, 3>(a, c->ndim, rate, c->stream);
+    }
+}
+
+cudaError_t dispatch_cons(const mfc_ctx* c, const double* w, double* q) {
+    switch (c->nf) {
+        case 1: return launch_cons<1>(c->g, c->e, w, q, c->ndim, c->stream);
+        case 2: return launch_cons<2>(c->g, c->e, w, q, c->ndim, c->stream);
+        default: return launch_cons<3>(c->g, c->e, w, q, c->ndim, c->stream);
+    }
+}
+
+mfc_status ensure_alive(mfc_ctx* c) {
+    if (!c) return MFC_ERR_ARG;
+    if (c->dead) return fail(c, MFC_ERR_CUDA, "context unusable after an earlier CUDA error: %s", c->err.c_str());
+    return MFC_OK;
+}
+
+// Primitive recovery of src into c->w (optionally with the CFL rate).
+mfc_status run_prims(mfc_ctx* c, const double* src, bool rate) {
+    PrimArgs a{};
+    a.g = c->g;
+    a.e = c->e;
+    a.q = src;
+    a.w = c->w;
+    a.rate_max = rate ? c->d_rate : nullptr;
+    a.bad = rate ? c->d_bad : nullptr;
+    return launch(c, rate ? P_CFL : P_PRIMS, [&] { return dispatch_prims(c, a, rate); });
+}
+
+SweepArgs base_sweep(const mfc_ctx* c) {
+    SweepArgs a{};
+    a.g = c->g;
+    a.e = c->e;
+    a.w = c->w;
+    a.eps = c->eps;
+    a.fallback = c->fallback;
+    a.fallback_count = c->d_fallback;
+    return a;
+}
+
+// All directional sweeps of one RHS evaluation on c->w.  With rk == nullptr the
+// result goes to out (mode 0 then 1); otherwise the last sweep applies the RK
+// stage update described by rk.
+struct RkStage {
+    const double* q0;
+    const double* qs;
+    double* qout;
+    double c0, c1, dt;
+};
+
+mfc_status run_sweeps(mfc_ctx* c, double* out, const RkStage* rk) {
+    for (int d = 0; d < c->ndim; ++d) {
+        SweepArgs a = base_sweep(c);
+        a.seg = auto_segment(c, d);
+        a.nseg = (c->n[d] + a.seg - 1) / a.seg;
+        const bool last = (d == c->ndim - 1);
+        if (rk && last) {
+            a.mode = 2;
+            a.R = c->R;
+            a.q0 = rk->q0;
+            a.qs = rk->qs;
+            a.qout = rk->qout;
+            a.c0 = rk->c0;
+            a.c1 = rk->c1;
+            a.dt = rk->dt;
+        } else {
+            a.mode = (d == 0) ? 0 : 1;
+            a.R = rk ? c->R : out;
+        }
+        mfc_status s = launch(c, P_SWEEP_X + d, [&] { return dispatch_sweep(c, a, d); });
+        if (s != MFC_OK) return s;
+    }
+    return MFC_OK;
+}
+
+void collect_profile(mfc_ctx* c) {
+    for (auto& r : c->prof_pending) {
+        float ms = 0.f;
+        if (cudaEventSynchronize(r.b) == cudaSuccess && cudaEventElapsedTime(&ms, r.a, r.b) == cudaSuccess) {
+            c->prof_ms[r.cat] += ms;
+            c->prof_n[r.cat] += 1;
+        }
+        cudaEventDestroy(r.a);
+        cudaEventDestroy(r.b);
+    }
+    c->prof_pending.clear();
+}
+
+void free_all(mfc_ctx* c) {
+    collect_profile(c);
+    cudaFree(c->q);
+    cudaFree(c->q1);
+    cudaFree(c->R);
+    cudaFree(c->w);
+    cudaFree(c->d_rate);
+    cudaFree(c->d_bad);
+    cudaFree(c->d_fallback);
+    cudaFree(c->mlp);
+    if (c->h_pin) cudaFreeHost(c->h_pin);
+}
+
+}  // namespace
+
+extern "C" {
+
+mfc_status mfc_init(mfc_ctx** out, int nx, int ny, int nz, const double lo[3], const double hi[3],
+                    const int bc[6], int num_fluids, const double* gamma, const double* pi_inf,
+                    int precision, void* cuda_stream) {
+    if (!out || !lo || !hi || !bc || !gamma || !pi_inf) return MFC_ERR_ARG;
+    if (num_fluids < 1 || num_fluids > 3) return MFC_ERR_ARG;
+    if (precision < MFC_FP64 || precision > MFC_LEARNED) return MFC_ERR_ARG;
+    const int n[3] = {nx, ny, nz};
+    const int ndim = nz > 1 ? 3 : (ny > 1 ? 2 : 1);
+    for (int d = 0; d < 3; ++d) {
+        if (d < ndim && n[d] < 3) return MFC_ERR_ARG;
+        if (d >= ndim && n[d] != 1) return MFC_ERR_ARG;
+        if (d < ndim && !(hi[d] > lo[d]) ) return MFC_ERR_ARG;
+    }
+    for (int i = 0; i < 6; ++i)
+        if (bc[i] < 0 || bc[i] > 2) return MFC_ERR_ARG;
+    for (int d = 0; d < ndim; ++d)
+        if ((bc[2 * d] == MFC_BC_PERIODIC) != (bc[2 * d + 1] == MFC_BC_PERIODIC)) return MFC_ERR_ARG;
+    for (int k = 0; k < num_fluids; ++k)
+        if (!(gamma[k] > 1.0) || !(pi_inf[k] >= 0.0) || !std::isfinite(gamma[k]) || !std::isfinite(pi_inf[k]))
+            return MFC_ERR_ARG;
+    const long long ncell = (long long)nx * ny * nz;
+    if (ncell > (1LL << 34)) return MFC_ERR_ARG;
+
+    mfc_ctx* c = new mfc_ctx();
+    for (int d = 0; d < 3; ++d) {
+        c->n[d] = n[d];
+        c->lo[d] = lo[d];
+        c->hi[d] = hi[d];
+    }
+    c->ndim = ndim;
+    c->nf = num_fluids;
+    c->ns = 2 * num_fluids + ndim;
+    c->ncell = ncell;
+    for (int i = 0; i < 6; ++i) c->bc[i] = bc[i];
+    for (int k = 0; k < num_fluids; ++k) {
+        c->gamma[k] = gamma[k];
+        c->pi_inf[k] = pi_inf[k];
+    }
+    c->precision = precision;
+    c->stream = static_cast<cudaStream_t>(cuda_stream);
+
+    Geometry& g = c->g;
+    for (int d = 0; d < 3; ++d) {
+        g.n[d] = n[d];
+        g.bc_lo[d] = bc[2 * d];
+        g.bc_hi[d] = bc[2 * d + 1];
+        g.inv_dx[d] = d < ndim ? n[d] / (hi[d] - lo[d]) : 0.0;
+    }
+    g.ncell = ncell;
+    const int N = num_fluids;
+    double G[3], P[3];
+    for (int k = 0; k < N; ++k) {
+        G[k] = 1.0 / (gamma[k] - 1.0);
+        P[k] = gamma[k] * pi_inf[k] / (gamma[k] - 1.0);
+    }
+    c->e.G_N = G[N - 1];
+    c->e.P_N = P[N - 1];
+    for (int k = 0; k < 2; ++k) {
+        c->e.dG[k] = k < N - 1 ? G[k] - G[N - 1] : 0.0;
+        c->e.dP[k] = k < N - 1 ? P[k] - P[N - 1] : 0.0;
+    }
+
+    const size_t bytes = sizeof(double) * (size_t)c->ns * (size_t)ncell;
+    const size_t wbytes = real_size(c) * (size_t)c->ns * (size_t)ncell;
+    cudaError_t e = cudaSuccess;
+    if ((e = cudaMalloc(&c->q, bytes)) != cudaSuccess || (e = cudaMalloc(&c->q1, bytes)) != cudaSuccess ||
+        (e = cudaMalloc(&c->R, bytes)) != cudaSuccess || (e = cudaMalloc(&c->w, wbytes)) != cudaSuccess ||
+        (e = cudaMalloc(&c->d_rate, sizeof(unsigned long long))) != cudaSuccess ||
+        (e = cudaMalloc(&c->d_bad, sizeof(int))) != cudaSuccess ||
+        (e = cudaMalloc(&c->d_fallback, sizeof(unsigned long long))) != cudaSuccess ||
+        (e = cudaMallocHost(&c->h_pin, 2 * sizeof(unsigned long long))) != cudaSuccess) {
+        const bool oom = (e == cudaErrorMemoryAllocation);
+        cudaGetLastError();
+        free_all(c);
+        delete c;
+        return oom ? MFC_ERR_OOM : MFC_ERR_CUDA;
+    }
+    if (cudaMemsetAsync(c->d_fallback, 0, sizeof(unsigned long long), c->stream) != cudaSuccess) {
+        free_all(c);
+        delete c;
+        return MFC_ERR_CUDA;
+    }
+    *out = c;
+    return MFC_OK;
+}
+
+mfc_status mfc_set_param(mfc_ctx* c, const char* name, double value) {
+    mfc_status s = ensure_alive(c);
+    if (s != MFC_OK) return s;
+    if (!name) return fail(c, MFC_ERR_ARG, "NULL parameter name");
+    if (!strcmp(name, "weno_eps")) {
+        if (!(value >= 1e-30 && value <= 1.0)) return fail(c, MFC_ERR_ARG, "weno_eps out of range");
+        c->eps = value;
+    } else if (!strcmp(name, "fallback")) {
+        if (value != 0.0 && value != 1.0) return fail(c, MFC_ERR_ARG, "fallback must be 0 or 1");
+        c->fallback = (int)value;
+    } else if (!strcmp(name, "segment")) {
+        if (!(value == 0.0 || (value >= 8 && value <= 256))) return fail(c, MFC_ERR_ARG, "segment out of range");
+        c->seg_override = (int)value;
+    } else if (!strcmp(name, "profile")) {
+        if (value != 0.0 && value != 1.0) return fail(c, MFC_ERR_ARG, "profile must be 0 or 1");
+        c->profile = value != 0.0;
+    } else {
+        return fail(c, MFC_ERR_ARG, "unknown parameter '%s'", name);
+    }
+    return MFC_OK;
+}
+
+mfc_status mfc_set_state(mfc_ctx* c, const double* q, int on_device) {
+    mfc_status s = ensure_alive(c);
+    if (s != MFC_OK) return s;
+    if (!q) return fail(c, MFC_ERR_ARG, "NULL state");
+    const size_t bytes = sizeof(double) * (size_t)c->ns * (size_t)c->ncell;
+    MFC_CUDA(c, cudaMemcpyAsync(c->q, q, bytes, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                                c->stream));
+    if (!on_device) MFC_CUDA(c, cudaStreamSynchronize(c->stream));
+    c->state_set = true;
+    c->w_valid = false;
+    return MFC_OK;
+}
+
+mfc_status mfc_set_state_prim(mfc_ctx* c, const double* w, int on_device) {
+    mfc_status s = ensure_alive(c);
+    if (s != MFC_OK) return s;
+    if (!w) return fail(c, MFC_ERR_ARG, "NULL state");
+    const double* src = w;
+    if (!on_device) {
+        const size_t bytes = sizeof(double) * (size_t)c->ns * (size_t)c->ncell;
+        MFC_CUDA(c, cudaMemcpyAsync(c->q1, w, bytes, cudaMemcpyHostToDevice, c->stream));
+        src = c->q1;
+    }
+    s = launch(c, P_CONVERT, [&] { return dispatch_cons(c, src, c->q); });
+    if (s != MFC_OK) return s;
+    if (!on_device) MFC_CUDA(c, cudaStreamSynchronize(c->stream));
+    c->state_set = true;
+    c->w_valid = false;
+    return MFC_OK;
+}
+
+mfc_status mfc_get_state(mfc_ctx* c, double* q, int on_device) {
+    mfc_status s = ensure_alive(c);
+    if (s != MFC_OK) return s;
+    if (!q) return fail(c, MFC_ERR_ARG, "NULL buffer");
+    if (!c->state_set) return fail(c, MFC_ERR_STATE_UNSET, "no state set");
+    const size_t bytes = sizeof(double) * (size_t)c->ns * (size_t)c->ncell;
+    MFC_CUDA(c, cudaMemcpyAsync(q, c->q, bytes, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                                c->stream));
+    if (!on_device) MFC_CUDA(c, cudaStreamSynchronize(c->stream));
+    return MFC_OK;
+}
+
+mfc_status mfc_rhs(mfc_ctx* c, double* rhs, int on_device) {
+    mfc_status s = ensure_alive(c);
+    if (s != MFC_OK) return s;
+    if (!rhs) return fail(c, MFC_ERR_ARG, "NULL rhs");
+    if (!c->state_set) return fail(c, MFC_ERR_STATE_UNSET, "no state set");
+    if (c->precision == MFC_LEARNED && !c->mlp) return fail(c, MFC_ERR_ARG, "learned mode needs mfc_set_mlp");
+    if (!c->w_valid) {
+        s = run_prims(c, c->q, false);
+        if (s != MFC_OK) return s;
+        c->w_valid = true;
+    }
+    double* target = on_device ? rhs : c->R;
+    s = run_sweeps(c, target, nullptr);
+    if (s != MFC_OK) return s;
+    if (!on_device) {
+        const size_t bytes = sizeof(double) * (size_t)c->ns * (size_t)c->ncell;
+        MFC_CUDA(c, cudaMemcpyAsync(rhs, c->R, bytes, cudaMemcpyDeviceToHost, c->stream));
+        MFC_CUDA(c, cudaStreamSynchronize(c->stream));
+    }
+    return MFC_OK;
+}
+
+mfc_status mfc_step(mfc_ctx* c, double dt) {
+    mfc_status s = ensure_alive(c);
+    if (s != MFC_OK) return s;
+    if (!c->state_set) return fail(c, MFC_ERR_STATE_UNSET, "no state set");
+    if (!(dt > 0.0) || !std::isfinite(dt)) return fail(c, MFC_ERR_ARG, "dt must be finite and > 0");
+    if (c->precision == MFC_LEARNED && !c->mlp) return fail(c, MFC_ERR_ARG, "learned mode needs mfc_set_mlp");
+    // stage 1: q1 = q + dt R(q)
+    if (!c->w_valid) {
+        s = run_prims(c, c->q, false);
+        if (s != MFC_OK) return s;
+    }
+    RkStage st1{c->q, c->q, c->q1, 0.0, 1.0, dt};
+    if ((s = run_sweeps(c, nullptr, &st1)) != MFC_OK) return s;
+    // stage 2: q1 = 3/4 q + 1/4 (q1 + dt R(q1))
+    if ((s = run_prims(c, c->q1, false)) != MFC_OK) return s;
+    RkStage st2{c->q, c->q1, c->q1, 0.75, 0.25, dt};
+    if ((s = run_sweeps(c, nullptr, &st2)) != MFC_OK) return s;
+    // stage 3: q = 1/3 q + 2/3 (q1 + dt R(q1))
+    if ((s = run_prims(c, c->q1, false)) != MFC_OK) return s;
+    RkStage st3{c->q, c->q1, c->q, 1.0 / 3.0, 2.0 / 3.0, dt};
+    if ((s = run_sweeps(c, nullptr, &st3)) != MFC_OK) return s;
+    c->w_valid = false;
+    return MFC_OK;
+}
+
+mfc_status mfc_cfl_dt(mfc_ctx* c, double cfl, double* dt_out) {
+    mfc_status s = ensure_alive(c);
+    if (s != MFC_OK) return s;
+    if (!dt_out || !(cfl > 0.0) || !std::isfinite(cfl)) return fail(c, MFC_ERR_ARG, "bad cfl or NULL dt_out");
+    if (!c->state_set) return fail(c, MFC_ERR_STATE_UNSET, "no state set");
+    MFC_CUDA(c, cudaMemsetAsync(c->d_rate, 0, sizeof(unsigned long long), c->stream));
+    MFC_CUDA(c, cudaMemsetAsync(c->d_bad, 0, sizeof(int), c->stream));
+    s = run_prims(c, c->q, true);
+    if (s != MFC_OK) return s;
+    c->w_valid = true;
+    MFC_CUDA(c, cudaMemcpyAsync(&c->h_pin[0], c->d_rate, sizeof(unsigned long long), cudaMemcpyDeviceToHost,
+                                c->stream));
+    MFC_CUDA(c, cudaMemcpyAsync(&c->h_pin[1], c->d_bad, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    MFC_CUDA(c, cudaStreamSynchronize(c->stream));
+    const int bad = *reinterpret_cast<int*>(&c->h_pin[1]);
+    double rate;
+    unsigned long long bits = c->h_pin[0];
+    std::memcpy(&rate, &bits, sizeof rate);
+    if (bad > 0 || !(rate > 0.0) || !std::isfinite(rate)) {
+        *dt_out = 0.0;
+        return fail(c, MFC_ERR_NONPHYSICAL, "non-physical state in %d cell(s)", bad);
+    }
+    *dt_out = cfl / rate;
+    return MFC_OK;
+}
+
+mfc_status mfc_set_mlp(mfc_ctx* c, const float* params, int n) {
+    mfc_status s = ensure_alive(c);
+    if (s != MFC_OK) return s;
+    return fail(c, MFC_ERR_ARG, "learned mode is not available in this build");
+    (void)params;
+    (void)n;
+}
+
+int mfc_sys_size(const mfc_ctx* c) { return c ? c->ns : 0; }
+
+long long mfc_launch_count(const mfc_ctx* c) { return c ? c->launches : 0; }
+
+long long mfc_fallback_count(mfc_ctx* c) {
+    if (!c || c->dead) return -1;
+    unsigned long long v = 0;
+    if (cudaMemcpyAsync(&c->h_pin[0], c->d_fallback, sizeof v, cudaMemcpyDeviceToHost, c->stream) != cudaSuccess ||
+        cudaStreamSynchronize(c->stream) != cudaSuccess)
+        return -1;
+    v = c->h_pin[0];
+    return (long long)v;
+}
+
+int mfc_profile_read(mfc_ctx* c, double* total_ms, long long* launches, int n) {
+    if (!c) return 0;
+    collect_profile(c);
+    for (int i = 0; i < n && i < P_NCAT; ++i) {
+        if (total_ms) total_ms[i] = c->prof_ms[i];
+        if (launches) launches[i] = c->prof_n[i];
+    }
+    return P_NCAT;
+}
+
+const char* mfc_last_error(const mfc_ctx* c) { return c ? c->err.c_str() : "NULL context"; }
+
+void mfc_finalize(mfc_ctx* c) {
+    if (!c) return;
+    if (c->stream) cudaStreamSynchronize(c->stream);
+    else cudaDeviceSynchronize();
+    free_all(c);
+    delete c;
+}
+
+}  // extern "C"

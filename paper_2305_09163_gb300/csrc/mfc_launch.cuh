@@ -1,0 +1,80 @@
+// Host-side launchers for the device templates.  Each translation unit
+// instantiates them for one (arithmetic type, number of fluids) pair so the
+// build compiles in parallel.
+#pragma once
+#include "mfc_device.cuh"
+
+namespace mfc {
+
+constexpr int kSweepThreads = 128;
+constexpr int kElemThreads = 256;
+
+template <typename Real, int NF>
+cudaError_t launch_sweep(const SweepArgs& a, int ndim, int dir, cudaStream_t s) {
+    const int t1 = (dir == 0) ? 1 : 0, t2 = (dir == 2) ? 1 : 2;
+    const long long total = (long long)a.g.n[t1] * a.nseg * a.g.n[t2];
+    const unsigned blocks = (unsigned)((total + kSweepThreads - 1) / kSweepThreads);
+    switch (ndim * 4 + dir) {
+        case 4: sweep_kernel<Real, NF, 1, 0><<<blocks, kSweepThreads, 0, s>>>(a); break;
+        case 8: sweep_kernel<Real, NF, 2, 0><<<blocks, kSweepThreads, 0, s>>>(a); break;
+        case 9: sweep_kernel<Real, NF, 2, 1><<<blocks, kSweepThreads, 0, s>>>(a); break;
+        case 12: sweep_kernel<Real, NF, 3, 0><<<blocks, kSweepThreads, 0, s>>>(a); break;
+        case 13: sweep_kernel<Real, NF, 3, 1><<<blocks, kSweepThreads, 0, s>>>(a); break;
+        case 14: sweep_kernel<Real, NF, 3, 2><<<blocks, kSweepThreads, 0, s>>>(a); break;
+        default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+inline unsigned elem_blocks(long long n) {
+    long long b = (n + kElemThreads - 1) / kElemThreads;
+    const long long cap = 152LL * 16;
+    if (b > cap) b = cap;
+    if (b < 1) b = 1;
+    return (unsigned)b;
+}
+
+template <typename Real, int NF>
+cudaError_t launch_prims(const PrimArgs& a, int ndim, bool rate, cudaStream_t s) {
+    const unsigned blocks = elem_blocks(a.g.ncell);
+    switch (ndim * 2 + (rate ? 1 : 0)) {
+        case 2: prims_kernel<Real, NF, 1, false><<<blocks, kElemThreads, 0, s>>>(a); break;
+        case 3: prims_kernel<Real, NF, 1, true><<<blocks, kElemThreads, 0, s>>>(a); break;
+        case 4: prims_kernel<Real, NF, 2, false><<<blocks, kElemThreads, 0, s>>>(a); break;
+        case 5: prims_kernel<Real, NF, 2, true><<<blocks, kElemThreads, 0, s>>>(a); break;
+        case 6: prims_kernel<Real, NF, 3, false><<<blocks, kElemThreads, 0, s>>>(a); break;
+        case 7: prims_kernel<Real, NF, 3, true><<<blocks, kElemThreads, 0, s>>>(a); break;
+        default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+template <int NF>
+cudaError_t launch_cons(const Geometry& g, const EosConst& e, const double* w, double* q, int ndim,
+                        cudaStream_t s) {
+    const unsigned blocks = elem_blocks(g.ncell);
+    switch (ndim) {
+        case 1: cons_kernel<NF, 1><<<blocks, kElemThreads, 0, s>>>(g, e, w, q); break;
+        case 2: cons_kernel<NF, 2><<<blocks, kElemThreads, 0, s>>>(g, e, w, q); break;
+        case 3: cons_kernel<NF, 3><<<blocks, kElemThreads, 0, s>>>(g, e, w, q); break;
+        default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+// Explicitly instantiated in the mfc_inst_*.cu units.
+#define MFC_DECLARE_INSTANCES(Real, NF)                                                         \
+    extern template cudaError_t launch_sweep<Real, NF>(const SweepArgs&, int, int, cudaStream_t); \
+    extern template cudaError_t launch_prims<Real, NF>(const PrimArgs&, int, bool, cudaStream_t);
+
+MFC_DECLARE_INSTANCES(double, 1)
+MFC_DECLARE_INSTANCES(double, 2)
+MFC_DECLARE_INSTANCES(double, 3)
+MFC_DECLARE_INSTANCES(float, 1)
+MFC_DECLARE_INSTANCES(float, 2)
+MFC_DECLARE_INSTANCES(float, 3)
+extern template cudaError_t launch_cons<1>(const Geometry&, const EosConst&, const double*, double*, int, cudaStream_t);
+extern template cudaError_t launch_cons<2>(const Geometry&, const EosConst&, const double*, double*, int, cudaStream_t);
+extern template cudaError_t launch_cons<3>(const Geometry&, const EosConst&, const double*, double*, int, cudaStream_t);
+
+}  // namespace mfc
