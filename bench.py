@@ -1,0 +1,350 @@
+"""Throughput of the five-equation RHS / SSP-RK3 step on GB300.
+
+Default workload: the 256^3 two-fluid water/air shock-bubble in FP64 (a step =
+one CFL reduction + three RHS evaluations + three RK stage updates).  The metric
+is the grind time t_RHS / (cells * equations) in ns/(cell*eqn*RHS) (lower is
+better), with cell-updates/s beside it; the mixed-precision (and, when built,
+learned-weight) forms are timed on the same workload and reported under "forms".
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+--impl reference times the CPU FP64 oracle (plain C, OpenMP over the host
+cores) on a bounded slab of the same workload.  With torchrun (N > 1) every rank
+runs an independent replica (the path needs no exchange on one GPU); the
+reference arm runs on rank 0 only.
+"""
+from __future__ import annotations
+
+import argparse
+import csv
+import io
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import workloads  # noqa: E402
+
+METRIC = "grind time ns/(cell·eqn·RHS) & cell-updates/s, FP64 vs mixed vs learned"
+UNIT = "ns/(cell*eqn*RHS)"
+CFL = 0.3
+
+# Algorithmic FP64 operations of one directional sweep per cell (3D, two fluids,
+# seven equations), counted from the formulation the kernels evaluate with
+# FMA = 2 and every add, multiply, divide, square root, min and max = 1:
+#   WENO5 edges (both sides of a cell) 74 per variable x 7, HLLC 88 per face,
+#   flux difference + alpha div(u) source 18 per cell.
+FLOP_SWEEP_CELL_3D_2F = 74 * 7 + 88 + 18
+# RK3 stage epilogue in the last sweep: 6 per variable (stages 2, 3), 4 in stage 1
+FLOP_RK_CELL_2F = 7 * (6 + 6 + 4) / 3.0
+# Nominal FP64 peak: 152 SMs x 4 FP64 FLOP/clk/SM (2 DFMA) x 2.07 GHz
+FP64_PEAK_TFLOPS = 152 * 4 * 2.07e9 / 1e12
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+class ClockSampler:
+    """nvidia-smi clocks/throttle reasons sampled during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        self.out = ""
+        if self.proc is not None:
+            time.sleep(0.25)
+            self.proc.terminate()
+            try:
+                self.out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                self.out, _ = self.proc.communicate()
+        return False
+
+    def summary(self):
+        rows = [r for r in csv.reader(io.StringIO(self.out or "")) if len(r) >= 9]
+        sm, mx, reasons = [], [], set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for r in rows:
+            try:
+                sm.append(float(r[1]))
+                mx.append(float(r[2]))
+            except ValueError:
+                continue
+            for name, val in zip(names, r[5:9]):
+                if val.strip().lower() == "active":
+                    reasons.add(name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def _sweep_profile(prof):
+    ms = sum(prof[k][0] for k in ("sweep_x", "sweep_y", "sweep_z"))
+    n = sum(prof[k][1] for k in ("sweep_x", "sweep_y", "sweep_z"))
+    return ms, n
+
+
+def time_form(m, torch, wl, w_dev, precision, steps, warmup, dist_barrier, sampler_gpu=None, mlp=None):
+    """Warm up, then time `steps` steps (CFL + SSP-RK3) with CUDA events on the
+    solver's stream.  Returns a dict of measurements."""
+    stream = torch.cuda.current_stream()
+    s = m.Solver(wl.n, wl.lo, wl.hi, wl.bc, wl.gamma, wl.pi_inf, precision=precision, fallback=1)
+    if mlp is not None:
+        s.set_mlp(mlp)
+    s.set_state_prim(w_dev)
+    for _ in range(warmup):
+        s.step(s.cfl_dt(CFL))
+    torch.cuda.synchronize()
+    dist_barrier()
+    torch.cuda.synchronize()
+    s.set_param("profile", 1)
+    s.profile()  # clear anything pending
+    prof0 = s.profile()
+    l0 = s.launch_count()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    sampler = ClockSampler(sampler_gpu) if sampler_gpu is not None else None
+    if sampler:
+        sampler.__enter__()
+    e0.record(stream)
+    for _ in range(steps):
+        s.step(s.cfl_dt(CFL))
+    e1.record(stream)
+    torch.cuda.synchronize()
+    if sampler:
+        sampler.__exit__(None, None, None)
+    dist_barrier()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    prof1 = s.profile()
+    s.set_param("profile", 0)
+    launches = s.launch_count() - l0
+    sweep_ms = _sweep_profile(prof1)[0] - _sweep_profile(prof0)[0]
+    sweep_n = _sweep_profile(prof1)[1] - _sweep_profile(prof0)[1]
+    kern = {k: (prof1[k][0] - prof0[k][0], prof1[k][1] - prof0[k][1]) for k in prof1}
+    fb = s.fallback_count()
+    s.close()
+    return {"ms_per_step": ms, "launches": launches, "sweep_ms": sweep_ms, "sweep_launches": sweep_n,
+            "kernels": kern, "clocks": sampler.summary() if sampler else None, "fallback_faces": fb}
+
+
+def e2e_form(m, torch, wl, w_host, precision, steps, warmup):
+    """Same metric through the C ABI with HOST buffers: every step copies the
+    state in from pinned host memory, steps, and reads the state back."""
+    s = m.Solver(wl.n, wl.lo, wl.hi, wl.bc, wl.gamma, wl.pi_inf, precision=precision, fallback=1)
+    s.set_state_prim(w_host)
+    q_host = torch.empty(s.shape, dtype=torch.float64, pin_memory=True)
+    m.mfc_get_state(s.ctx, q_host)
+    for _ in range(warmup):
+        m.mfc_set_state(s.ctx, q_host)
+        s.step(s.cfl_dt(CFL))
+        m.mfc_get_state(s.ctx, q_host)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        m.mfc_set_state(s.ctx, q_host)
+        s.step(s.cfl_dt(CFL))
+        m.mfc_get_state(s.ctx, q_host)
+    torch.cuda.synchronize()
+    dt = (time.perf_counter() - t0) / steps
+    nbytes = q_host.numel() * 8
+    s.close()
+    return dt, nbytes
+
+
+def cpu_baseline_sample(wl, w_host, min_seconds=10.0, min_calls=2):
+    """The oracle as it stands (C, OpenMP over all host cores) on a 32-plane slab
+    through the bubble centre of the same workload; returns grind time."""
+    import oracle
+    nz = 32
+    z0 = wl.n[2] // 2 - nz // 2
+    sub = np.ascontiguousarray(w_host[:, z0:z0 + nz])
+    h = (wl.hi[2] - wl.lo[2]) / wl.n[2]
+    pb = oracle.Problem((wl.n[0], wl.n[1], nz), wl.lo, (wl.hi[0], wl.hi[1], wl.lo[2] + nz * h), wl.bc,
+                        wl.gamma, wl.pi_inf, fallback=True)
+    q = oracle.cons_from_prims(pb, sub)
+    oracle.rhs(pb, q)  # warm (page-in, thread pool)
+    calls = 0
+    t0 = time.perf_counter()
+    while calls < min_calls or time.perf_counter() - t0 < min_seconds:
+        oracle.rhs(pb, q)
+        calls += 1
+    el = time.perf_counter() - t0
+    grind = el / calls / (pb.ncell * pb.sys_size) * 1e9
+    cores = os.environ.get("OMP_NUM_THREADS") or str(os.cpu_count())
+    return {"value": grind, "unit": UNIT, "cores": int(cores), "kind": "oracle",
+            "sample": "%d oracle RHS calls on a %dx%dx%d slab (z planes %d..%d) of the %s initial state, %.1f s"
+                      % (calls, wl.n[0], wl.n[1], nz, z0, z0 + nz - 1, wl.name, el)}
+
+
+def run_reference(args, wl):
+    import oracle as orc  # test infrastructure: the reference arm is the CPU oracle
+    w_host = wl.prims()
+    nz = 32
+    z0 = wl.n[2] // 2 - nz // 2
+    sub = np.ascontiguousarray(w_host[:, z0:z0 + nz])
+    h = (wl.hi[2] - wl.lo[2]) / wl.n[2]
+    pb = orc.Problem((wl.n[0], wl.n[1], nz), wl.lo, (wl.hi[0], wl.hi[1], wl.lo[2] + nz * h), wl.bc,
+                     wl.gamma, wl.pi_inf, fallback=True)
+    q = orc.cons_from_prims(pb, sub)
+    for _ in range(max(args.warmup, 0)):
+        orc.rk3_step(pb, q, orc.cfl_dt(pb, q, CFL))
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        q = orc.rk3_step(pb, q, orc.cfl_dt(pb, q, CFL))
+    el = time.perf_counter() - t0
+    ms = el / args.steps * 1e3
+    grind = el / args.steps / (3 * pb.ncell * pb.sys_size) * 1e9
+    cores = int(os.environ.get("OMP_NUM_THREADS") or os.cpu_count())
+    sample = ("%d oracle SSP-RK3 steps (CFL + 3 RHS) on a %dx%dx%d slab (z planes %d..%d) of the %s initial state"
+              % (args.steps, wl.n[0], wl.n[1], nz, z0, z0 + nz - 1, wl.name))
+    line = {"impl": "reference", "metric": METRIC, "value": grind, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": False,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": wl.name, "cells": pb.ncell, "sys_size": pb.sys_size, "form": "fp64",
+                       "sample": sample},
+            "cell_updates_per_s": pb.ncell / (el / args.steps),
+            "cpu_baseline": {"value": grind, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+            "e2e": {"value": grind, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
+    ap.add_argument("--n", type=int, default=256, help="cells per direction of the shock-bubble cube")
+    ap.add_argument("--forms", default="fp64,mixed", help="comma list of fp64,mixed,learned")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    args = ap.parse_args()
+    ws, rank, local = _dist()
+    wl = workloads.shock_bubble(args.n)
+
+    if args.impl == "reference":
+        if rank == 0:
+            run_reference(args, wl)
+        return
+
+    import torch
+    import paper_2305_09163_gb300 as m
+    torch.cuda.set_device(local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+        barrier = lambda: dist.barrier()
+    else:
+        barrier = lambda: None
+    m.build() if rank == 0 else None
+    if ws > 1:
+        barrier()
+    m.load()
+
+    w_host = wl.prims()
+    w_dev = torch.from_numpy(w_host).cuda()
+    cells = wl.ncell
+    ns = wl.sys_size
+    forms = [f.strip() for f in args.forms.split(",") if f.strip()]
+    results = {}
+    for form in forms:
+        if form == "learned":
+            results[form] = None  # reported once the learned kernels are built
+            continue
+        r = time_form(m, torch, wl, w_dev, form, args.steps, args.warmup, barrier,
+                      sampler_gpu=local if form == "fp64" else None)
+        t = torch.tensor([r["ms_per_step"]], device="cuda")
+        if ws > 1:
+            import torch.distributed as dist
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        r["ms_max"] = float(t.item())
+        results[form] = r
+
+    fp = results["fp64"]
+    ms = fp["ms_max"]
+    grind = ms * 1e-3 / (ws * cells * ns * 3) * 1e9
+    flops_per_sweep_launch = (FLOP_SWEEP_CELL_3D_2F + FLOP_RK_CELL_2F / 3.0) * cells
+    achieved = flops_per_sweep_launch * fp["sweep_launches"] / (fp["sweep_ms"] * 1e-3) / 1e12
+
+    line = {
+        "metric": METRIC, "value": grind, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": False, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": wl.name + " (FP64, 2 fluids, 7 equations)", "cells": cells, "sys_size": ns,
+                   "rhs_per_step": 3, "cfl": CFL, "parallelism": "replicas" if ws > 1 else "single-gpu",
+                   "l2": "inputs larger than L2 (state %.2f GB per array)" % (cells * ns * 8 / 1e9)},
+        "cell_updates_per_s": ws * cells / (ms * 1e-3),
+        "roofline": {"bound": "alu", "kernel": "sweep (x, y, z)", "achieved": achieved,
+                     "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS,
+                     "peak_note": "nominal FP64: 152 SMs x 4 FLOP/clk x 2.07 GHz",
+                     "flop_per_cell_per_sweep": FLOP_SWEEP_CELL_3D_2F, "traffic": None},
+        "gpu_launches": fp["launches"],
+        "kernels_ms": {k: v[0] for k, v in fp["kernels"].items() if v[1]},
+        "fallback_faces": fp["fallback_faces"],
+        "clocks": fp["clocks"],
+        "forms": {},
+    }
+    for form, r in results.items():
+        if form == "fp64":
+            continue
+        if r is None:
+            line["forms"][form] = None
+            continue
+        g = r["ms_max"] * 1e-3 / (ws * cells * ns * 3) * 1e9
+        line["forms"][form] = {"grind": g, "unit": UNIT, "ms_per_step": r["ms_max"],
+                               "cell_updates_per_s": ws * cells / (r["ms_max"] * 1e-3),
+                               "speedup_vs_fp64": ms / r["ms_max"], "gpu_launches": r["launches"],
+                               "kernels_ms": {k: v[0] for k, v in r["kernels"].items() if v[1]}}
+    if not args.no_e2e:
+        k = max(2, min(args.steps, 5))
+        dt, nbytes = e2e_form(m, torch, wl, w_host, "fp64", k, 1)
+        t = torch.tensor([dt], device="cuda")
+        if ws > 1:
+            import torch.distributed as dist
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        dt = float(t.item())
+        line["e2e"] = {"value": dt / (ws * cells * ns * 3) * 1e9, "unit": UNIT,
+                       "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes, "steps": k,
+                       "note": "C ABI with pinned host buffers: set_state + CFL + step + get_state per step"}
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline_sample(wl, w_host)
+    if rank == 0:
+        print(json.dumps(line))
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()
