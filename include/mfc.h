@@ -133,6 +133,36 @@ long long mfc_fallback_count(mfc_ctx* ctx);
  * Returns the number of categories (7). */
 int mfc_profile_read(mfc_ctx* ctx, double* total_ms, long long* launches, int n);
 
+/* Largest grid (in cells) that mfc_rhs_noalloc accepts. */
+#define MFC_NOALLOC_MAX_CELLS 262144LL
+
+/* Allocation-free right-hand side.  The paper has no counterpart: this entry
+ * point exists for callers that cannot let a library call cudaMalloc, such as
+ * host applications or frameworks that hand out all device memory from their
+ * own pool or fixed budget, and time-critical loops that cannot absorb the
+ * device synchronisation an allocation may take.  It computes the same R(q) as
+ * mfc_rhs for a stateless problem description and allocates nothing: no
+ * cudaMalloc, cudaFree or allocating library routine.
+ *   q          device pointer, conserved state (layout above), caller-owned;
+ *   rhs        device pointer, output R(q) (layout above), caller-owned;
+ *   nx..pi_inf as in mfc_init; nx*ny*nz must not exceed MFC_NOALLOC_MAX_CELLS;
+ *   weno_eps   WENO epsilon in [1e-30, 1]; fallback 0/1 as in mfc_set_param;
+ *   cuda_stream the stream to enqueue on (NULL = legacy default stream);
+ *   err, err_len optional caller buffer for an error message (may be NULL).
+ * FP64 arithmetic.  Enqueued on the stream; returns without waiting.
+ * The only scratch (the primitive variables, at most MFC_NOALLOC_MAX_CELLS x 9
+ * doubles = 18.9 MB) is a static device array of the library, held by every GPU
+ * that loads the library until the process exits.  The first call on a device,
+ * with that device current, looks up the array's device address once; make that
+ * first call before any stream capture.  All calls share the array: calls that
+ * overlap on the GPU race on it and must be serialised by the caller.
+ * Errors: MFC_ERR_ARG (bad arguments, or a grid larger than
+ * MFC_NOALLOC_MAX_CELLS, with the reason in err), MFC_ERR_CUDA. */
+mfc_status mfc_rhs_noalloc(const double* q, double* rhs, int nx, int ny, int nz, const double lo[3],
+                           const double hi[3], const int bc[6], int num_fluids, const double* gamma,
+                           const double* pi_inf, double weno_eps, int fallback, void* cuda_stream,
+                           char* err, int err_len);
+
 /* Text of the last error on this context ("" if none). */
 const char* mfc_last_error(const mfc_ctx* ctx);
 

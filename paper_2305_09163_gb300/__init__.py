@@ -71,6 +71,9 @@ def _declare(lib):
     lib.mfc_fallback_count.restype = c_ll
     lib.mfc_profile_read.argtypes = [c_void_p, dptr, ctypes.POINTER(c_ll), c_int]
     lib.mfc_profile_read.restype = c_int
+    lib.mfc_rhs_noalloc.argtypes = [c_void_p, c_void_p, c_int, c_int, c_int, dptr, dptr, ctypes.POINTER(c_int),
+                                    c_int, dptr, dptr, c_double, c_int, c_void_p, c_char_p, c_int]
+    lib.mfc_rhs_noalloc.restype = c_int
     lib.mfc_last_error.argtypes = [c_void_p]
     lib.mfc_last_error.restype = c_char_p
     lib.mfc_finalize.argtypes = [c_void_p]
@@ -192,6 +195,30 @@ def mfc_profile_read(ctx):
     cnt = (ctypes.c_longlong * 8)()
     k = lib.mfc_profile_read(ctx, ms, cnt, 8)
     return {PROFILE_CATEGORIES[i]: (ms[i], cnt[i]) for i in range(min(k, len(PROFILE_CATEGORIES)))}
+
+
+NOALLOC_MAX_CELLS = 262144
+
+
+def mfc_rhs_noalloc(q, rhs, n, lo, hi, bc, gamma, pi_inf, weno_eps=1e-6, fallback=1, stream=None):
+    """Allocation-free R(q) for callers that cannot let the library allocate
+    device memory; q and rhs are device tensors (float64, contiguous)."""
+    lib = load()
+    qa, qdev = _ptr(q)
+    ra, rdev = _ptr(rhs)
+    if not (qdev and rdev):
+        raise TypeError("mfc_rhs_noalloc takes device buffers")
+    n = list(n) + [1] * (3 - len(n))
+    lo3 = (ctypes.c_double * 3)(*(list(lo) + [0.0] * (3 - len(lo))))
+    hi3 = (ctypes.c_double * 3)(*(list(hi) + [1.0] * (3 - len(hi))))
+    bc6 = (ctypes.c_int * 6)(*(list(bc) + [1] * (6 - len(bc))))
+    g = (ctypes.c_double * len(gamma))(*gamma)
+    p = (ctypes.c_double * len(pi_inf))(*pi_inf)
+    err = ctypes.create_string_buffer(512)
+    st = lib.mfc_rhs_noalloc(qa, ra, int(n[0]), int(n[1]), int(n[2]), lo3, hi3, bc6, len(gamma), g, p,
+                             float(weno_eps), int(fallback), ctypes.c_void_p(stream or 0), err, 512)
+    if st != MFC_OK:
+        raise MFCError(st, err.value.decode())
 
 
 def mfc_last_error(ctx):
