@@ -43,7 +43,7 @@ struct mfc_ctx {
 
     double* q = nullptr;      // state q^n
     double* q1 = nullptr;     // RK stage state
-    double* R = nullptr;      // RHS accumulator
+    void* R = nullptr;        // RHS accumulator (double or float)
     void* w = nullptr;        // primitives (double or float)
     unsigned long long* d_rate = nullptr;  // CFL max (ordered bits)
     int* d_bad = nullptr;
@@ -182,9 +182,10 @@ SweepArgs base_sweep(const mfc_ctx* c) {
     return a;
 }
 
-// All directional sweeps of one RHS evaluation on c->w.  With rk == nullptr the
-// result goes to out (mode 0 then 1); otherwise the last sweep applies the RK
-// stage update described by rk.
+// All directional sweeps of one RHS evaluation on c->w.  The accumulator R has
+// the arithmetic type of the path (float64 or float32).  With rk == nullptr the
+// last sweep writes the float64 right-hand side to out; otherwise it applies
+// the RK stage update described by rk.
 struct RkStage {
     const double* q0;
     const double* qs;
@@ -197,19 +198,22 @@ mfc_status run_sweeps(mfc_ctx* c, double* out, const RkStage* rk) {
         SweepArgs a = base_sweep(c);
         a.seg = auto_segment(c, d);
         a.nseg = (c->n[d] + a.seg - 1) / a.seg;
+        a.R = c->R;
         const bool last = (d == c->ndim - 1);
-        if (rk && last) {
+        a.acc_in = c->ndim > 1 ? 1 : 0;
+        if (last && rk) {
             a.mode = 2;
-            a.R = c->R;
             a.q0 = rk->q0;
             a.qs = rk->qs;
             a.qout = rk->qout;
             a.c0 = rk->c0;
             a.c1 = rk->c1;
             a.dt = rk->dt;
+        } else if (last) {
+            a.mode = 3;
+            a.out = out;
         } else {
             a.mode = (d == 0) ? 0 : 1;
-            a.R = rk ? c->R : out;
         }
         mfc_status s = launch(c, P_SWEEP_X + d, [&] { return dispatch_sweep(c, a, d); });
         if (s != MFC_OK) return s;
@@ -313,7 +317,7 @@ mfc_status mfc_init(mfc_ctx** out, int nx, int ny, int nz, const double lo[3], c
     const size_t wbytes = real_size(c) * (size_t)c->ns * (size_t)ncell;
     cudaError_t e = cudaSuccess;
     if ((e = cudaMalloc(&c->q, bytes)) != cudaSuccess || (e = cudaMalloc(&c->q1, bytes)) != cudaSuccess ||
-        (e = cudaMalloc(&c->R, bytes)) != cudaSuccess || (e = cudaMalloc(&c->w, wbytes)) != cudaSuccess ||
+        (e = cudaMalloc(&c->R, wbytes)) != cudaSuccess || (e = cudaMalloc(&c->w, wbytes)) != cudaSuccess ||
         (e = cudaMalloc(&c->d_rate, sizeof(unsigned long long))) != cudaSuccess ||
         (e = cudaMalloc(&c->d_bad, sizeof(int))) != cudaSuccess ||
         (e = cudaMalloc(&c->d_fallback, sizeof(unsigned long long))) != cudaSuccess ||
@@ -409,12 +413,14 @@ mfc_status mfc_rhs(mfc_ctx* c, double* rhs, int on_device) {
         if (s != MFC_OK) return s;
         c->w_valid = true;
     }
-    double* target = on_device ? rhs : c->R;
+    // the float64 result goes to the caller's device buffer, or through the
+    // stage buffer to host memory
+    double* target = on_device ? rhs : c->q1;
     s = run_sweeps(c, target, nullptr);
     if (s != MFC_OK) return s;
     if (!on_device) {
         const size_t bytes = sizeof(double) * (size_t)c->ns * (size_t)c->ncell;
-        MFC_CUDA(c, cudaMemcpyAsync(rhs, c->R, bytes, cudaMemcpyDeviceToHost, c->stream));
+        MFC_CUDA(c, cudaMemcpyAsync(rhs, c->q1, bytes, cudaMemcpyDeviceToHost, c->stream));
         MFC_CUDA(c, cudaStreamSynchronize(c->stream));
     }
     return MFC_OK;

@@ -1,6 +1,6 @@
 // Device code for the five-equation (Allaire) diffuse-interface right-hand side
-// on GB300 (sm_103a).  Templates over the arithmetic type (double for the FP64
-// path, float for the mixed path), the number of fluids NF, the number of
+// on GB300 (sm_103a).  Templates over the arithmetic type Real (double for the
+// FP64 path, float for the mixed path), the number of fluids NF, the number of
 // dimensions NDIM and the sweep direction DIR.
 //
 // Method (arXiv 2305.09163):
@@ -12,13 +12,15 @@
 //   Sec. 3.4      SSP (TVD) Runge-Kutta 3 update
 //
 // GB300 design: the FP64 pipe issues about 2 DFMA per SM clock, ~1/58 of FP32,
-// so the FP64 path is bound by double-precision instructions, not by HBM.  The
-// sweep kernel therefore (a) computes each cell's two WENO edge values from one
-// shared set of smoothness indicators, (b) folds the six weight divisions of a
-// cell into one reciprocal, (c) computes every face flux once, marching along a
-// pencil so the neighbouring cell's edge and flux stay in registers, and (d) does
-// the flux difference, the alpha div(u) source and the RK3 stage update in the
-// same pass.  No atomics touch the state, so results are bitwise reproducible.
+// and FP64 compares run on it too, while FP32<->FP64 conversions and integer
+// work do not.  The FP64 path is therefore bound by FP64 instructions, not by
+// HBM, and the kernels minimise them: each cell's two WENO edge values share one
+// set of smoothness indicators and one reciprocal (a Newton-Raphson refinement
+// of an FP32 seed), the ideal weights are folded into the candidate constants,
+// positivity tests are integer tests on bit patterns, and every face flux is
+// computed once.  Flux difference, alpha div(u) source and the RK3 stage update
+// are applied in the same pass.  No atomics touch the state, so results are
+// bitwise reproducible.
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -47,16 +49,19 @@ struct SweepArgs {
     Geometry g;
     EosConst e;
     const void* w;          // primitives [NS][ncell], Real
-    double* R;              // right-hand side accumulator [NS][ncell]
-    int mode;               // 0: R = sweep; 1: R += sweep; 2: RK stage update
+    void* R;                // right-hand side accumulator [NS][ncell], Real
+    int mode;               // 0: R = s; 1: R += s; 2: RK stage update; 3: out = R + s
+    int acc_in;             // modes 2/3: add the accumulator R (earlier sweeps)
     const double* q0;       // RK: state at t^n
     const double* qs;       // RK: current stage state
     double* qout;           // RK: output stage state (may alias qs or q0)
-    double c0, c1, dt;      // RK: qout = c0 q0 + c1 (qs + dt (R + sweep))
+    double* out;            // mode 3: float64 right-hand side output
+    double c0, c1, dt;      // RK: qout = c0 q0 + c1 (qs + dt (R + s))
     double eps;             // WENO epsilon
     int fallback;           // first-order fallback at non-physical faces
-    int seg;                // cells per thread along the sweep direction
-    int nseg;               // pencil segments along the sweep direction
+    int seg;                // marching kernels: cells per thread along DIR
+    int nseg;               // marching kernels: segments along DIR
+    long long slots_per_block;  // x-stream kernel: edge slots owned by one CTA
     unsigned long long* fallback_count;  // optional counter of fallback faces
 };
 
@@ -99,54 +104,82 @@ __device__ __forceinline__ int ghost_map(int i, int n, int bclo, int bchi, bool*
 }
 
 // ---------------------------------------------------------------------------
+// FP64 reciprocal by Newton-Raphson refinement (third-order step
+// y <- y + y (e + e^2), e = 1 - d y) of an FP32 hardware estimate.  The seed
+// is formed with integer operations only: the top 23 mantissa bits of d are
+// placed in a float in [1,2), its approximate reciprocal is taken, and the
+// exponent of d is subtracted back in.  The seed is good to ~2^-22, one step
+// gives full FP64 precision (within 1 ulp of the correctly rounded 1/d).
+// Valid for finite normal d; zero and subnormal inputs return +-inf.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ double rcp_nr(double d) {
+    const long long bits = __double_as_longlong(d);
+    const int hi = (int)(bits >> 32);
+    const int e = (hi >> 20) & 0x7FF;
+    const unsigned sign = (unsigned)hi & 0x80000000u;
+    const unsigned m23 = (((unsigned)hi & 0xFFFFFu) << 3) | ((unsigned)bits >> 29);
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(__uint_as_float(0x3F800000u | m23)));
+    const unsigned rb = __float_as_uint(r);
+    const int ed = (int)((rb >> 23) & 0xFF) - 127 - (e - 1023) + 1023;
+    const unsigned mr = rb & 0x7FFFFFu;
+    const double y = __hiloint2double((int)(sign | ((unsigned)ed << 20) | (mr >> 3)), (int)(mr << 29));
+    const double err = fma(-d, y, 1.0);
+    const double res = fma(y, fma(err, err, err), y);
+    return e == 0 ? __longlong_as_double((long long)((unsigned long long)sign << 32) | 0x7FF0000000000000LL) : res;
+}
+
+// ---------------------------------------------------------------------------
 // WENO5-JS edge values of one cell (Sec. 3.2).  D[k] = v_{c+k-1} - v_{c+k-2},
 // k = 0..3, i.e. the four differences across the five-cell stencil c-2..c+2.
 // Returns eR (value at c-1/2) and eL (value at c+1/2).
 //
-// Smoothness indicators as quadratic forms of the differences:
-//   b0 = 10/3 D1^2 - 11/3 D1 D0 + 4/3 D0^2      (stencil c-2..c)
-//   b1 =  4/3 (D1^2 + D2^2) - 5/3 D1 D2         (stencil c-1..c+1)
-//   b2 = 10/3 D2^2 - 11/3 D2 D3 + 4/3 D3^2      (stencil c..c+2)
-// Candidates as increments over v_c, so constant data reconstructs exactly.  Both edges share
-// the indicators; the mirrored edge uses the ideal weights reversed.
+// The Jiang-Shu smoothness indicators as quadratic forms of the differences,
+//   b0 = 4/3 [ 5/2 D1^2 - 11/4 D1 D0 + D0^2 ]   (stencil c-2..c)
+//   b1 = 4/3 [ D1^2 + D2^2 - 5/4 D1 D2 ]        (stencil c-1..c+1)
+//   b2 = 4/3 [ 5/2 D2^2 - 11/4 D2 D3 + D3^2 ]   (stencil c..c+2),
+// are evaluated without the common factor 4/3, with eps scaled by 3/4 so every
+// (eps + b_r) carries the same factor and the weights are unchanged.  The
+// candidates are increments over v_c (constant data reconstructs exactly), the
+// ideal weights 1/10, 6/10, 3/10 are folded into their constants, and the two
+// weight normalisations share one reciprocal.  eps34 = 3/4 eps.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ void weno5_edges(double vc, const double D[4], double eps,
+__device__ __forceinline__ void weno5_edges(double vc, const double D[4], double eps34,
                                             double& eR, double& eL) {
     const double S0 = D[0] * D[0], S1 = D[1] * D[1], S2 = D[2] * D[2], S3 = D[3] * D[3];
-    const double b0 = fma(10.0 / 3.0, S1, fma(-11.0 / 3.0, D[1] * D[0], (4.0 / 3.0) * S0));
-    const double b1 = fma(4.0 / 3.0, S1 + S2, (-5.0 / 3.0) * (D[1] * D[2]));
-    const double b2 = fma(10.0 / 3.0, S2, fma(-11.0 / 3.0, D[2] * D[3], (4.0 / 3.0) * S3));
-    const double t0 = eps + b0, t1 = eps + b1, t2 = eps + b2;
+    const double b0 = fma(2.5, S1, fma(-2.75, D[1] * D[0], S0));
+    const double b1 = fma(-1.25, D[1] * D[2], S1 + S2);
+    const double b2 = fma(2.5, S2, fma(-2.75, D[2] * D[3], S3));
+    const double t0 = eps34 + b0, t1 = eps34 + b1, t2 = eps34 + b2;
     const double a0 = t0 * t0, a1 = t1 * t1, a2 = t2 * t2;
-    // alpha_r = d_r / a_r; multiplied through by 10 a0 a1 a2
-    const double P12 = a1 * a2, P02x6 = 6.0 * (a0 * a2), P01 = a0 * a1;
-    const double P01x3 = 3.0 * P01, P12x3 = 3.0 * P12;
-    // candidate increments p_r - v_c at c+1/2 (exact zero on constant data)
+    // weights d_r/a_r multiplied through by 10 a0 a1 a2
+    const double P12 = a1 * a2, P02 = a0 * a2, P01 = a0 * a1;
+    // increments at c+1/2: 1x (stencil c-2..c), 6x (c-1..c+1), 3x (c..c+2)
     const double p0 = fma(5.0 / 6.0, D[1], (-1.0 / 3.0) * D[0]);
-    const double p1 = fma(1.0 / 6.0, D[1], (1.0 / 3.0) * D[2]);
-    const double p2 = fma(2.0 / 3.0, D[2], (-1.0 / 6.0) * D[3]);
-    // mirrored increments at c-1/2: stencils c..c+2, c-1..c+1, c-2..c
+    const double p1 = fma(2.0, D[2], D[1]);
+    const double p2 = fma(2.0, D[2], -0.5 * D[3]);
+    // mirrored increments at c-1/2: 1x (c..c+2), 6x (c-1..c+1), 3x (c-2..c)
     const double m0 = fma(-5.0 / 6.0, D[2], (1.0 / 3.0) * D[3]);
-    const double m1 = fma(-1.0 / 6.0, D[2], (-1.0 / 3.0) * D[1]);
-    const double m2 = fma(-2.0 / 3.0, D[1], (1.0 / 6.0) * D[0]);
-    const double numL = fma(P12, p0, fma(P02x6, p1, P01x3 * p2));
-    const double denL = P12 + P02x6 + P01x3;
-    const double numR = fma(P01, m0, fma(P02x6, m1, P12x3 * m2));
-    const double denR = P01 + P02x6 + P12x3;
-    const double x = 1.0 / (denL * denR);
+    const double m1 = fma(-2.0, D[1], -D[2]);
+    const double m2 = fma(-2.0, D[1], 0.5 * D[0]);
+    const double numL = fma(P12, p0, fma(P02, p1, P01 * p2));
+    const double denL = fma(6.0, P02, fma(3.0, P01, P12));
+    const double numR = fma(P01, m0, fma(P02, m1, P12 * m2));
+    const double denR = fma(6.0, P02, fma(3.0, P12, P01));
+    const double x = rcp_nr(denL * denR);
     eL = fma(numL, denR * x, vc);
     eR = fma(numR, denL * x, vc);
 }
 
-// FP32 variant for the mixed path: the weights are normalised by the smallest
-// eps+beta so no intermediate overflows FP32 (beta of a 1e9 Pa jump is ~1e19).
-__device__ __forceinline__ void weno5_edges(float vc, const float D[4], float eps,
+// FP32 variant for the mixed path.  The weights are normalised by the smallest
+// eps+beta, so no intermediate overflows FP32 (beta of a 1e9 Pa jump is ~1e19).
+__device__ __forceinline__ void weno5_edges(float vc, const float D[4], float eps34,
                                             float& eR, float& eL) {
     const float S0 = D[0] * D[0], S1 = D[1] * D[1], S2 = D[2] * D[2], S3 = D[3] * D[3];
-    const float b0 = fmaf(10.f / 3.f, S1, fmaf(-11.f / 3.f, D[1] * D[0], (4.f / 3.f) * S0));
-    const float b1 = fmaf(4.f / 3.f, S1 + S2, (-5.f / 3.f) * (D[1] * D[2]));
-    const float b2 = fmaf(10.f / 3.f, S2, fmaf(-11.f / 3.f, D[2] * D[3], (4.f / 3.f) * S3));
-    const float t0 = eps + b0, t1 = eps + b1, t2 = eps + b2;
+    const float b0 = fmaf(2.5f, S1, fmaf(-2.75f, D[1] * D[0], S0));
+    const float b1 = fmaf(-1.25f, D[1] * D[2], S1 + S2);
+    const float b2 = fmaf(2.5f, S2, fmaf(-2.75f, D[2] * D[3], S3));
+    const float t0 = eps34 + b0, t1 = eps34 + b1, t2 = eps34 + b2;
     const float m = fminf(t0, fminf(t1, t2));
     float g0 = __fdividef(m, t0), g1 = __fdividef(m, t1), g2 = __fdividef(m, t2);
     g0 *= g0; g1 *= g1; g2 *= g2;
@@ -171,7 +204,7 @@ template <typename Real> struct EosR {
     }
 };
 
-__device__ __forceinline__ double real_rcp(double x) { return 1.0 / x; }
+__device__ __forceinline__ double real_rcp(double x) { return rcp_nr(x); }
 __device__ __forceinline__ float real_rcp(float x) { return __fdividef(1.0f, x); }
 __device__ __forceinline__ double real_sqrt(double x) { return sqrt(x); }
 __device__ __forceinline__ float real_sqrt(float x) { return sqrtf(x); }
@@ -180,30 +213,65 @@ __device__ __forceinline__ float real_min(float a, float b) { return fminf(a, b)
 __device__ __forceinline__ double real_max(double a, double b) { return fmax(a, b); }
 __device__ __forceinline__ float real_max(float a, float b) { return fmaxf(a, b); }
 
+// Sign tests on the bit pattern (integer pipe), equal to the IEEE comparisons
+// for every input including -0, +-inf and NaN.
+__device__ __forceinline__ bool nonneg(double x) {          // x >= 0
+    const unsigned long long u = (unsigned long long)__double_as_longlong(x);
+    return u <= 0x7FF0000000000000ULL || u == 0x8000000000000000ULL;
+}
+__device__ __forceinline__ bool unit_interval(double x) {   // 0 <= x <= 1
+    const unsigned long long u = (unsigned long long)__double_as_longlong(x);
+    return u <= 0x3FF0000000000000ULL || u == 0x8000000000000000ULL;
+}
+__device__ __forceinline__ bool positive(double x) {        // x > 0
+    const unsigned long long u = (unsigned long long)__double_as_longlong(x);
+    return u - 1ULL < 0x7FF0000000000000ULL;
+}
+__device__ __forceinline__ bool nonneg(float x) { return x >= 0.f; }
+__device__ __forceinline__ bool unit_interval(float x) { return x >= 0.f && x <= 1.f; }
+__device__ __forceinline__ bool positive(float x) { return x > 0.f; }
+
+// Mixture quantities of one face state: rho, Gamma, Pi and (Gamma+1)p + Pi.
+template <typename Real> struct Mix {
+    Real r, G, P, n;
+};
+
+template <typename Real, int NF, int NDIM>
+__device__ __forceinline__ Mix<Real> mixture(const Real* s, const EosR<Real>& e) {
+    using Lay = Layout<NF, NDIM>;
+    Mix<Real> m;
+    m.r = s[0];
+#pragma unroll
+    for (int k = 1; k < NF; ++k) m.r += s[k];
+    m.G = e.G_N;
+    m.P = e.P_N;
+#pragma unroll
+    for (int k = 0; k < NF - 1; ++k) {
+        m.G = fma(s[Lay::IA + k], e.dG[k], m.G);
+        m.P = fma(s[Lay::IA + k], e.dP[k], m.P);
+    }
+    m.n = fma(m.G + (Real)1, s[Lay::IE], m.P);
+    return m;
+}
+
 // A reconstructed face state is physical when every partial density is
 // non-negative, every volume fraction (including alpha_N) lies in [0,1], the
 // density is positive and (Gamma+1)p + Pi > 0.
 template <typename Real, int NF, int NDIM>
-__device__ __forceinline__ bool face_state_ok(const Real* s, const EosR<Real>& e) {
+__device__ __forceinline__ bool face_state_ok(const Real* s, const Mix<Real>& m) {
     using Lay = Layout<NF, NDIM>;
-    bool ok = true;
-    Real rho = s[0];
-    ok = ok && (s[0] >= (Real)0);
+    bool ok = positive(m.r) && positive(m.n);
 #pragma unroll
-    for (int k = 1; k < NF; ++k) { rho += s[k]; ok = ok && (s[k] >= (Real)0); }
-    Real asum = 0, G = e.G_N, P = e.P_N;
+    for (int k = 0; k < NF; ++k) ok = ok && nonneg(s[k]);
+    if (NF > 1) {
+        Real asum = s[Lay::IA];
 #pragma unroll
-    for (int k = 0; k < NF - 1; ++k) {
-        const Real a = s[Lay::IA + k];
-        ok = ok && (a >= (Real)0) && (a <= (Real)1);
-        asum += a;
-        G = fma(a, e.dG[k], G);
-        P = fma(a, e.dP[k], P);
+        for (int k = 0; k < NF - 1; ++k) {
+            ok = ok && unit_interval(s[Lay::IA + k]);
+            if (k > 0) asum += s[Lay::IA + k];
+        }
+        ok = ok && unit_interval((Real)1 - asum);
     }
-    const Real aN = (Real)1 - asum;
-    ok = ok && (aN >= (Real)0) && (aN <= (Real)1);
-    ok = ok && (rho > (Real)0);
-    ok = ok && (fma(G + (Real)1, s[Lay::IE], P) > (Real)0);
     return ok;
 }
 
@@ -211,36 +279,26 @@ __device__ __forceinline__ bool face_state_ok(const Real* s, const EosR<Real>& e
 // normal direction DIR; Davis wave-speed estimates.  The branch order matches
 // the four cases of the paper: 0<=sL; sL<0<=s*; s*<0<sR; sR<=0.
 template <typename Real, int NF, int NDIM, int DIR>
-__device__ __forceinline__ void hllc(const Real* L, const Real* R, const EosR<Real>& e,
+__device__ __forceinline__ void hllc(const Real* L, const Real* R, const Mix<Real>& mL, const Mix<Real>& mR,
                                      Real* F, Real& ut) {
     using Lay = Layout<NF, NDIM>;
     constexpr int IM = Lay::IM, IE = Lay::IE, IA = Lay::IA;
-    Real rL = L[0], rR = R[0];
-#pragma unroll
-    for (int k = 1; k < NF; ++k) { rL += L[k]; rR += R[k]; }
-    Real GL = e.G_N, PL = e.P_N, GR = e.G_N, PR = e.P_N;
-#pragma unroll
-    for (int k = 0; k < NF - 1; ++k) {
-        GL = fma(L[IA + k], e.dG[k], GL); PL = fma(L[IA + k], e.dP[k], PL);
-        GR = fma(R[IA + k], e.dG[k], GR); PR = fma(R[IA + k], e.dP[k], PR);
-    }
     const Real uL = L[IM + DIR], uR = R[IM + DIR], pL = L[IE], pR = R[IE];
     // c^2 = ((Gamma+1)p + Pi)/(Gamma rho); one reciprocal for both sides
-    const Real nL = fma(GL + (Real)1, pL, PL), nR = fma(GR + (Real)1, pR, PR);
-    const Real dL = GL * rL, dR = GR * rR;
+    const Real dL = mL.G * mL.r, dR = mR.G * mR.r;
     const Real xd = real_rcp(dL * dR);
-    const Real cL = real_sqrt(nL * (dR * xd)), cR = real_sqrt(nR * (dL * xd));
+    const Real cL = real_sqrt(mL.n * (dR * xd)), cR = real_sqrt(mR.n * (dL * xd));
     const Real sL = real_min(uL - cL, uR - cR);
     const Real sR = real_max(uL + cL, uR + cR);
-    const Real aL = rL * (sL - uL), aR = rR * (sR - uR);
+    const Real aL = mL.r * (sL - uL), aR = mR.r * (sR - uR);
     const Real sS = (pR - pL + aL * uL - aR * uR) * real_rcp(aL - aR);
     const bool useL = ((Real)0 <= sL) || ((Real)0 <= sS);
     const bool star = useL ? !((Real)0 <= sL) : ((Real)0 < sR);
     Real K[Lay::NS];
 #pragma unroll
     for (int v = 0; v < Lay::NS; ++v) K[v] = useL ? L[v] : R[v];
-    const Real rK = useL ? rL : rR, uK = useL ? uL : uR, pK = useL ? pL : pR;
-    const Real GK = useL ? GL : GR, PK = useL ? PL : PR, sK = useL ? sL : sR;
+    const Real rK = useL ? mL.r : mR.r, uK = useL ? uL : uR, pK = useL ? pL : pR;
+    const Real GK = useL ? mL.G : mR.G, PK = useL ? mL.P : mR.P, sK = useL ? sL : sR;
     // xi - 1 = (s* - u_K)/(s_K - s*) taken directly, so a contact (s* = u_K)
     // gives the face velocity u_K exactly
     Real rr = 0, xm1 = 0, sKe = 0;
@@ -267,16 +325,80 @@ __device__ __forceinline__ void hllc(const Real* L, const Real* R, const EosR<Re
     for (int k = 0; k < NF - 1; ++k) F[IA + k] = K[IA + k] * ut;
 }
 
+// Face flux between reconstructed states (with the optional first-order
+// fallback to the two cell values cl | cr).
+template <typename Real, int NF, int NDIM, int DIR>
+__device__ __forceinline__ void face_flux(const SweepArgs& a, const EosR<Real>& e, const Real* eLs, const Real* eRs,
+                                          const Real* cl, const Real* cr, Real* F, Real& ut) {
+    constexpr int NS = Layout<NF, NDIM>::NS;
+    Mix<Real> mL = mixture<Real, NF, NDIM>(eLs, e);
+    Mix<Real> mR = mixture<Real, NF, NDIM>(eRs, e);
+    bool first = false;
+    if (a.fallback) {
+        first = !(face_state_ok<Real, NF, NDIM>(eLs, mL) && face_state_ok<Real, NF, NDIM>(eRs, mR));
+    }
+    if (first) {
+        if (a.fallback_count) atomicAdd(a.fallback_count, 1ULL);
+        Real fl[NS], fr[NS];
+#pragma unroll
+        for (int v = 0; v < NS; ++v) { fl[v] = cl[v]; fr[v] = cr[v]; }
+        mL = mixture<Real, NF, NDIM>(fl, e);
+        mR = mixture<Real, NF, NDIM>(fr, e);
+        hllc<Real, NF, NDIM, DIR>(fl, fr, mL, mR, F, ut);
+    } else {
+        hllc<Real, NF, NDIM, DIR>(eLs, eRs, mL, mR, F, ut);
+    }
+}
+
+// Finish one cell: flux difference + alpha div(u) source, then the epilogue
+// selected by a.mode.
+template <typename Real, int NF, int NDIM>
+__device__ __forceinline__ void finish_cell(const SweepArgs& a, long long idx, const Real* Fm, const Real* Fp,
+                                            Real um, Real up, const Real* cell, Real inv_dx) {
+    using Lay = Layout<NF, NDIM>;
+    constexpr int NS = Lay::NS, IA = Lay::IA;
+    Real out[NS];
+#pragma unroll
+    for (int v = 0; v < NS; ++v) out[v] = (Fm[v] - Fp[v]) * inv_dx;
+    const Real du = (up - um) * inv_dx;
+#pragma unroll
+    for (int k = 0; k < NF - 1; ++k) out[IA + k] = fma(cell[IA + k], du, out[IA + k]);
+    const long long nc = a.g.ncell;
+    Real* R = static_cast<Real*>(a.R);
+    if (a.mode == 0) {
+#pragma unroll
+        for (int v = 0; v < NS; ++v) R[v * nc + idx] = out[v];
+    } else if (a.mode == 1) {
+#pragma unroll
+        for (int v = 0; v < NS; ++v) R[v * nc + idx] += out[v];
+    } else if (a.mode == 2) {
+#pragma unroll
+        for (int v = 0; v < NS; ++v) {
+            const Real rv = a.acc_in ? R[v * nc + idx] + out[v] : out[v];
+            const double s = fma(a.dt, (double)rv, a.qs[v * nc + idx]);
+            double o = a.c1 * s;
+            if (a.c0 != 0.0) o = fma(a.c0, a.q0[v * nc + idx], o);
+            a.qout[v * nc + idx] = o;
+        }
+    } else {
+#pragma unroll
+        for (int v = 0; v < NS; ++v) {
+            const Real rv = a.acc_in ? R[v * nc + idx] + out[v] : out[v];
+            a.out[v * nc + idx] = (double)rv;
+        }
+    }
+}
+
 // ---------------------------------------------------------------------------
-// Directional sweep.  One thread marches along one pencil segment of `seg`
-// cells in direction DIR: it reconstructs the edges of cells s0-1..s1, forms
-// faces s0-1/2..s1-1/2 and finishes cells s0..s1-1.  For DIR = y, z the lanes
+// Directional sweep for y and z.  One thread marches along one pencil segment
+// of `seg` cells in direction DIR: it reconstructs the edges of cells
+// s0-1..s1, forms faces s0-1/2..s1-1/2 and finishes cells s0..s1-1.  The lanes
 // of a warp are consecutive x, so every load and store is coalesced.
 // ---------------------------------------------------------------------------
 template <typename Real, int NF, int NDIM, int DIR>
 __global__ void __launch_bounds__(128) sweep_kernel(const SweepArgs a) {
     using Lay = Layout<NF, NDIM>;
-    constexpr int NS = Lay::NS, IM = Lay::IM, IA = Lay::IA;
+    constexpr int NS = Lay::NS, IM = Lay::IM;
     constexpr int T1 = (DIR == 0) ? 1 : 0;
     constexpr int T2 = (DIR == 2) ? 1 : 2;
     const Real* __restrict__ w = static_cast<const Real*>(a.w);
@@ -294,9 +416,9 @@ __global__ void __launch_bounds__(128) sweep_kernel(const SweepArgs a) {
     const int s0 = sg * a.seg;
     const int s1 = min(s0 + a.seg, nd);
     const int bclo = a.g.bc_lo[DIR], bchi = a.g.bc_hi[DIR];
-    const Real eps = (Real)a.eps;
+    const Real eps34 = (Real)(0.75 * a.eps);
     const EosR<Real> e(a.e);
-    const double inv_dx = a.g.inv_dx[DIR];
+    const Real inv_dx = (Real)a.g.inv_dx[DIR];
 
     auto load = [&](int i, Real* out) {
         bool flip = false;
@@ -307,75 +429,37 @@ __global__ void __launch_bounds__(128) sweep_kernel(const SweepArgs a) {
         if (flip) out[IM + DIR] = -out[IM + DIR];
     };
 
-    // Window around the cell c being reconstructed: vm1 = c-1, vc = c,
-    // vp1 = c+1, vp2 = c+2 and the four differences across c-2..c+2.
-    Real vm1[NS], vc[NS], vp1[NS], vp2[NS], D[NS][4];
+    // Window around the cell c being reconstructed: vc = c, vp1 = c+1,
+    // vp2 = c+2, the four differences across c-2..c+2, and cm1 = c-1.
+    Real vc[NS], vp1[NS], vp2[NS], D[NS][4], cm1[NS];
     {
         Real t[NS];
         load(s0 - 3, t);
-        load(s0 - 2, vm1);
+        load(s0 - 2, cm1);
         load(s0 - 1, vc);
         load(s0, vp1);
         load(s0 + 1, vp2);
 #pragma unroll
         for (int v = 0; v < NS; ++v) {
-            D[v][0] = vm1[v] - t[v];
-            D[v][1] = vc[v] - vm1[v];
+            D[v][0] = cm1[v] - t[v];
+            D[v][1] = vc[v] - cm1[v];
             D[v][2] = vp1[v] - vc[v];
             D[v][3] = vp2[v] - vp1[v];
         }
     }
     Real eLprev[NS], Fprev[NS], utprev = 0;
-    Real cm1[NS];  // cell c-1 values (for the fallback and the alpha source)
 #pragma unroll
-    for (int v = 0; v < NS; ++v) { eLprev[v] = 0; Fprev[v] = 0; cm1[v] = vm1[v]; }
+    for (int v = 0; v < NS; ++v) { eLprev[v] = 0; Fprev[v] = 0; }
 
     for (int c = s0 - 1; c <= s1; ++c) {
         Real eR[NS], eL[NS];
 #pragma unroll
-        for (int v = 0; v < NS; ++v) weno5_edges(vc[v], D[v], eps, eR[v], eL[v]);
+        for (int v = 0; v < NS; ++v) weno5_edges(vc[v], D[v], eps34, eR[v], eL[v]);
         if (c >= s0) {
             Real F[NS], ut;
-            bool first = false;
-            if (a.fallback) {
-                first = !(face_state_ok<Real, NF, NDIM>(eLprev, e) && face_state_ok<Real, NF, NDIM>(eR, e));
-                if (first && a.fallback_count) atomicAdd(a.fallback_count, 1ULL);
-            }
-            Real fl[NS], fr[NS];
-#pragma unroll
-            for (int v = 0; v < NS; ++v) {
-                fl[v] = first ? cm1[v] : eLprev[v];
-                fr[v] = first ? vc[v] : eR[v];
-            }
-            hllc<Real, NF, NDIM, DIR>(fl, fr, e, F, ut);
-            if (c >= s0 + 1) {
-                // finish cell c-1: flux difference and alpha div(u) source
-                double out[NS];
-#pragma unroll
-                for (int v = 0; v < NS; ++v) out[v] = (double)(Fprev[v] - F[v]) * inv_dx;
-                const double du = (double)(ut - utprev) * inv_dx;
-#pragma unroll
-                for (int k = 0; k < NF - 1; ++k) out[IA + k] = fma((double)cm1[IA + k], du, out[IA + k]);
-                const long long idx = base + (long long)(c - 1) * sd;
-                if (a.mode == 0) {
-#pragma unroll
-                    for (int v = 0; v < NS; ++v) a.R[v * nc + idx] = out[v];
-                } else if (a.mode == 1) {
-#pragma unroll
-                    for (int v = 0; v < NS; ++v) a.R[v * nc + idx] += out[v];
-                } else {
-                    const bool acc = (NDIM > 1);
-#pragma unroll
-                    for (int v = 0; v < NS; ++v) {
-                        double r = out[v];
-                        if (acc) r += a.R[v * nc + idx];
-                        double s = fma(a.dt, r, a.qs[v * nc + idx]);
-                        double o = a.c1 * s;
-                        if (a.c0 != 0.0) o = fma(a.c0, a.q0[v * nc + idx], o);
-                        a.qout[v * nc + idx] = o;
-                    }
-                }
-            }
+            face_flux<Real, NF, NDIM, DIR>(a, e, eLprev, eR, cm1, vc, F, ut);
+            if (c >= s0 + 1)
+                finish_cell<Real, NF, NDIM>(a, base + (long long)(c - 1) * sd, Fprev, F, utprev, ut, cm1, inv_dx);
 #pragma unroll
             for (int v = 0; v < NS; ++v) Fprev[v] = F[v];
             utprev = ut;
@@ -401,56 +485,197 @@ __global__ void __launch_bounds__(128) sweep_kernel(const SweepArgs a) {
 }
 
 // ---------------------------------------------------------------------------
-// Conserved -> primitive (Sec. 2.1): rho = sum a_k r_k, u = (rho u)/rho,
-// p = (rho E - rho|u|^2/2 - Pi)/Gamma, always in FP64 (the water Pi ~ 7.8e8 Pa
-// cancels against rho E).  Optionally the CFL rate max_d (|u_d| + c)/dx_d with
-// c^2 = ((Gamma+1)p + Pi)/(Gamma rho), reduced to one max per launch with an
-// order-preserving integer atomic (non-negative doubles), so it is exact and
-// independent of scheduling.
+// x sweep as a coalesced stream.  Every x-row of n cells is laid out as n+2
+// "slots" for edge cells c = -1..n; the rows are concatenated and each CTA
+// owns `slots_per_block` consecutive slots.  A chunk of 128 slots is one slot
+// per lane: lane s reconstructs the edges of its cell c (five-cell stencil read
+// straight from global memory, consecutive lanes = consecutive x), forms the
+// face c-1/2 from its own right-side value and the left-side value of slot s-1
+// (shared memory), and finishes cell c-1 from faces c-3/2 and c-1/2.  The last
+// slot's left-side value and flux carry to the next chunk, and each CTA starts
+// two slots early so that its first cell has both faces.
 // ---------------------------------------------------------------------------
+constexpr int kStreamThreads = 128;
+
+template <typename Real, int NF, int NDIM>
+__global__ void __launch_bounds__(kStreamThreads) sweep_x_stream_kernel(const SweepArgs a) {
+    using Lay = Layout<NF, NDIM>;
+    constexpr int NS = Lay::NS, IM = Lay::IM;
+    __shared__ Real sh_eL[NS][kStreamThreads + 1];
+    __shared__ Real sh_F[NS + 1][kStreamThreads + 1];
+    const Real* __restrict__ w = static_cast<const Real*>(a.w);
+    const int n = a.g.n[0];
+    const long long rowlen = (long long)n + 2;
+    const long long nrows = a.g.ncell / n;
+    const long long total = rowlen * nrows;
+    const long long own0 = (long long)blockIdx.x * a.slots_per_block;
+    const long long own1 = min(own0 + a.slots_per_block, total);
+    const long long nc = a.g.ncell;
+    const int bclo = a.g.bc_lo[0], bchi = a.g.bc_hi[0];
+    const Real eps34 = (Real)(0.75 * a.eps);
+    const EosR<Real> e(a.e);
+    const Real inv_dx = (Real)a.g.inv_dx[0];
+    const int t = threadIdx.x;
+
+    for (long long base = own0 - 2; base < own1; base += kStreamThreads) {
+        const long long s = base + t;
+        const bool live = (s >= 0) && (s < own1);
+        const long long row = live ? s / rowlen : 0;
+        const int c = live ? (int)(s - row * rowlen) - 1 : -1;
+        const long long rowoff = row * n;
+        Real cell[NS], cm1[NS], eL[NS], eR[NS];
+        if (live) {
+            Real v[5][NS];
+#pragma unroll
+            for (int k = 0; k < 5; ++k) {
+                bool flip = false;
+                const int m = ghost_map(c + k - 2, n, bclo, bchi, &flip);
+#pragma unroll
+                for (int q = 0; q < NS; ++q) v[k][q] = __ldg(w + q * nc + rowoff + m);
+                if (flip) v[k][IM] = -v[k][IM];
+            }
+#pragma unroll
+            for (int q = 0; q < NS; ++q) {
+                const Real D[4] = {v[1][q] - v[0][q], v[2][q] - v[1][q], v[3][q] - v[2][q], v[4][q] - v[3][q]};
+                weno5_edges(v[2][q], D, eps34, eR[q], eL[q]);
+                cell[q] = v[2][q];
+                cm1[q] = v[1][q];
+            }
+        }
+        // left-side values of this chunk; slot 0 holds the carry from the last chunk
+        if (live) {
+#pragma unroll
+            for (int q = 0; q < NS; ++q) sh_eL[q][t + 1] = eL[q];
+        }
+        __syncthreads();
+        Real F[NS], ut = 0;
+        const bool has_face = live && c >= 0 && s >= own0 - 1;
+        if (has_face) {
+            Real lft[NS];
+#pragma unroll
+            for (int q = 0; q < NS; ++q) lft[q] = sh_eL[q][t];
+            face_flux<Real, NF, NDIM, 0>(a, e, lft, eR, cm1, cell, F, ut);
+#pragma unroll
+            for (int q = 0; q < NS; ++q) sh_F[q][t + 1] = F[q];
+            sh_F[NS][t + 1] = ut;
+        }
+        __syncthreads();
+        if (has_face && s >= own0 && c >= 1) {
+            Real Fm[NS];
+#pragma unroll
+            for (int q = 0; q < NS; ++q) Fm[q] = sh_F[q][t];
+            finish_cell<Real, NF, NDIM>(a, rowoff + (c - 1), Fm, F, sh_F[NS][t], ut, cm1, inv_dx);
+        }
+        __syncthreads();
+        // carry the last slot of the chunk into position 0
+        if (t == kStreamThreads - 1) {
+#pragma unroll
+            for (int q = 0; q < NS; ++q) {
+                sh_eL[q][0] = sh_eL[q][kStreamThreads];
+                sh_F[q][0] = sh_F[q][kStreamThreads];
+            }
+            sh_F[NS][0] = sh_F[NS][kStreamThreads];
+        }
+        __syncthreads();
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Conserved -> primitive (Sec. 2.1): rho = sum a_k r_k, u = (rho u)/rho,
+// p = (rho E - rho|u|^2/2 - Pi)/Gamma.  FP64 path: all in FP64.  Mixed path:
+// rho E - Pi (the water Pi ~ 7.8e8 Pa cancels against rho E) and the kinetic
+// energy subtraction stay FP64, the rest is FP32.  Optionally the CFL rate
+// max_d (|u_d| + c)/dx_d with c^2 = ((Gamma+1)p + Pi)/(Gamma rho), reduced to one
+// max per launch with an order-preserving integer atomic (non-negative
+// doubles), so it is exact and independent of scheduling.
+// ---------------------------------------------------------------------------
+template <int NF, int NDIM>
+__device__ __forceinline__ void prims_cell(const double* q, const EosConst& e, double* wv, double& c2) {
+    using Lay = Layout<NF, NDIM>;
+    constexpr int IM = Lay::IM, IE = Lay::IE, IA = Lay::IA;
+    double rho = q[0];
+#pragma unroll
+    for (int k = 1; k < NF; ++k) rho += q[k];
+    double G = e.G_N, P = e.P_N;
+#pragma unroll
+    for (int k = 0; k < NF - 1; ++k) {
+        G = fma(q[IA + k], e.dG[k], G);
+        P = fma(q[IA + k], e.dP[k], P);
+    }
+    const double x = 1.0 / (rho * G);
+    const double irho = G * x, iG = rho * x;
+    double ke = 0.0;
+#pragma unroll
+    for (int d = 0; d < NDIM; ++d) { wv[IM + d] = q[IM + d] * irho; ke = fma(q[IM + d], wv[IM + d], ke); }
+    const double p = (q[IE] - 0.5 * ke - P) * iG;
+#pragma unroll
+    for (int k = 0; k < NF; ++k) wv[k] = q[k];
+    wv[IE] = p;
+#pragma unroll
+    for (int k = 0; k < NF - 1; ++k) wv[IA + k] = q[IA + k];
+    c2 = fma(G + 1.0, p, P) * iG * irho;
+}
+
+template <int NF, int NDIM>
+__device__ __forceinline__ void prims_cell(const double* q, const EosConst& e, float* wv, float& c2) {
+    using Lay = Layout<NF, NDIM>;
+    constexpr int IM = Lay::IM, IE = Lay::IE, IA = Lay::IA;
+    float rho = (float)q[0];
+#pragma unroll
+    for (int k = 1; k < NF; ++k) rho += (float)q[k];
+    float G = (float)e.G_N;
+    double P = e.P_N;
+#pragma unroll
+    for (int k = 0; k < NF - 1; ++k) {
+        G = fmaf((float)q[IA + k], (float)e.dG[k], G);
+        P = fma(q[IA + k], e.dP[k], P);
+    }
+    const float irho = __fdividef(1.0f, rho);
+    float ke = 0.f;
+#pragma unroll
+    for (int d = 0; d < NDIM; ++d) {
+        const float m = (float)q[IM + d];
+        wv[IM + d] = m * irho;
+        ke = fmaf(m, wv[IM + d], ke);
+    }
+    const double eint = fma(-0.5, (double)ke, q[IE] - P);
+    const float p = __fdividef((float)eint, G);
+#pragma unroll
+    for (int k = 0; k < NF; ++k) wv[k] = (float)q[k];
+    wv[IE] = p;
+#pragma unroll
+    for (int k = 0; k < NF - 1; ++k) wv[IA + k] = (float)q[IA + k];
+    c2 = __fdividef(fmaf(G + 1.0f, p, (float)P), G * rho);
+}
+
 template <typename Real, int NF, int NDIM, bool RATE>
 __global__ void __launch_bounds__(256) prims_kernel(const PrimArgs a) {
     using Lay = Layout<NF, NDIM>;
-    constexpr int NS = Lay::NS, IM = Lay::IM, IE = Lay::IE, IA = Lay::IA;
+    constexpr int NS = Lay::NS, IM = Lay::IM;
     const long long nc = a.g.ncell;
     double rate = 0.0;
     int bad = 0;
+    Real* w = static_cast<Real*>(a.w);
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < nc;
          i += (long long)gridDim.x * blockDim.x) {
         double q[NS];
 #pragma unroll
         for (int v = 0; v < NS; ++v) q[v] = __ldg(a.q + v * nc + i);
-        double rho = q[0];
+        Real wv[NS], c2;
+        prims_cell<NF, NDIM>(q, a.e, wv, c2);
 #pragma unroll
-        for (int k = 1; k < NF; ++k) rho += q[k];
-        double G = a.e.G_N, P = a.e.P_N;
-#pragma unroll
-        for (int k = 0; k < NF - 1; ++k) {
-            G = fma(q[IA + k], a.e.dG[k], G);
-            P = fma(q[IA + k], a.e.dP[k], P);
-        }
-        const double x = 1.0 / (rho * G);
-        const double irho = G * x, iG = rho * x;
-        double u[NDIM], ke = 0.0;
-#pragma unroll
-        for (int d = 0; d < NDIM; ++d) { u[d] = q[IM + d] * irho; ke = fma(q[IM + d], u[d], ke); }
-        const double p = (q[IE] - 0.5 * ke - P) * iG;
-        Real* w = static_cast<Real*>(a.w);
-#pragma unroll
-        for (int k = 0; k < NF; ++k) w[k * nc + i] = (Real)q[k];
-#pragma unroll
-        for (int d = 0; d < NDIM; ++d) w[(IM + d) * nc + i] = (Real)u[d];
-        w[IE * nc + i] = (Real)p;
-#pragma unroll
-        for (int k = 0; k < NF - 1; ++k) w[(IA + k) * nc + i] = (Real)q[IA + k];
+        for (int v = 0; v < NS; ++v) w[v * nc + i] = wv[v];
         if (RATE) {
-            const double c2 = fma(G + 1.0, p, P) * iG * irho;
-            if (!(c2 > 0.0) || !(c2 < 1e300) || !(ke == ke)) {
+            double us = 0.0;
+#pragma unroll
+            for (int d = 0; d < NDIM; ++d) us += (double)wv[IM + d];
+            const double c2d = (double)c2;
+            if (!(c2d > 0.0) || !(c2d < 1e300) || !(us - us == 0.0)) {
                 bad += 1;
             } else {
-                const double cs = sqrt(c2);
+                const double cs = sqrt(c2d);
 #pragma unroll
-                for (int d = 0; d < NDIM; ++d) rate = fmax(rate, (fabs(u[d]) + cs) * a.g.inv_dx[d]);
+                for (int d = 0; d < NDIM; ++d) rate = fmax(rate, (fabs((double)wv[IM + d]) + cs) * a.g.inv_dx[d]);
             }
         }
     }

@@ -2,7 +2,7 @@
 // and 3 fluid(s).
 #include "mfc_launch.cuh"
 namespace mfc {
-template cudaError_t launch_sweep<float, 3>(const SweepArgs&, int, int, cudaStream_t);
+template cudaError_t launch_sweep<float, 3>(SweepArgs, int, int, cudaStream_t);
 template cudaError_t launch_prims<float, 3>(const PrimArgs&, int, bool, cudaStream_t);
 
 }  // namespace mfc

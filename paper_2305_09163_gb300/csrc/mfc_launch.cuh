@@ -9,16 +9,29 @@ namespace mfc {
 constexpr int kSweepThreads = 128;
 constexpr int kElemThreads = 256;
 
+// Slots (edge cells) owned by one CTA of the x-stream kernel: 16 chunks of 128,
+// so the two recomputed slots at its start cost about 0.1%.
+constexpr long long kStreamSlotsPerBlock = 16LL * kStreamThreads;
+
 template <typename Real, int NF>
-cudaError_t launch_sweep(const SweepArgs& a, int ndim, int dir, cudaStream_t s) {
+cudaError_t launch_sweep(SweepArgs a, int ndim, int dir, cudaStream_t s) {
+    if (dir == 0) {
+        const long long total = (long long)(a.g.n[0] + 2) * (a.g.ncell / a.g.n[0]);
+        a.slots_per_block = kStreamSlotsPerBlock;
+        const unsigned blocks = (unsigned)((total + kStreamSlotsPerBlock - 1) / kStreamSlotsPerBlock);
+        switch (ndim) {
+            case 1: sweep_x_stream_kernel<Real, NF, 1><<<blocks, kStreamThreads, 0, s>>>(a); break;
+            case 2: sweep_x_stream_kernel<Real, NF, 2><<<blocks, kStreamThreads, 0, s>>>(a); break;
+            case 3: sweep_x_stream_kernel<Real, NF, 3><<<blocks, kStreamThreads, 0, s>>>(a); break;
+            default: return cudaErrorInvalidValue;
+        }
+        return cudaGetLastError();
+    }
     const int t1 = (dir == 0) ? 1 : 0, t2 = (dir == 2) ? 1 : 2;
     const long long total = (long long)a.g.n[t1] * a.nseg * a.g.n[t2];
     const unsigned blocks = (unsigned)((total + kSweepThreads - 1) / kSweepThreads);
     switch (ndim * 4 + dir) {
-        case 4: sweep_kernel<Real, NF, 1, 0><<<blocks, kSweepThreads, 0, s>>>(a); break;
-        case 8: sweep_kernel<Real, NF, 2, 0><<<blocks, kSweepThreads, 0, s>>>(a); break;
         case 9: sweep_kernel<Real, NF, 2, 1><<<blocks, kSweepThreads, 0, s>>>(a); break;
-        case 12: sweep_kernel<Real, NF, 3, 0><<<blocks, kSweepThreads, 0, s>>>(a); break;
         case 13: sweep_kernel<Real, NF, 3, 1><<<blocks, kSweepThreads, 0, s>>>(a); break;
         case 14: sweep_kernel<Real, NF, 3, 2><<<blocks, kSweepThreads, 0, s>>>(a); break;
         default: return cudaErrorInvalidValue;
@@ -64,7 +77,7 @@ cudaError_t launch_cons(const Geometry& g, const EosConst& e, const double* w, d
 
 // Explicitly instantiated in the mfc_inst_*.cu units.
 #define MFC_DECLARE_INSTANCES(Real, NF)                                                         \
-    extern template cudaError_t launch_sweep<Real, NF>(const SweepArgs&, int, int, cudaStream_t); \
+    extern template cudaError_t launch_sweep<Real, NF>(SweepArgs, int, int, cudaStream_t); \
     extern template cudaError_t launch_prims<Real, NF>(const PrimArgs&, int, bool, cudaStream_t);
 
 MFC_DECLARE_INSTANCES(double, 1)
