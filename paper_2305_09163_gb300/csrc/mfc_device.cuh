@@ -666,16 +666,18 @@ __global__ void __launch_bounds__(256) prims_kernel(const PrimArgs a) {
 #pragma unroll
         for (int v = 0; v < NS; ++v) w[v * nc + i] = wv[v];
         if (RATE) {
-            double us = 0.0;
+            // in the arithmetic of the path: FP64, or FP32 for the mixed path
+            Real us = 0;
 #pragma unroll
-            for (int d = 0; d < NDIM; ++d) us += (double)wv[IM + d];
-            const double c2d = (double)c2;
-            if (!(c2d > 0.0) || !(c2d < 1e300) || !(us - us == 0.0)) {
+            for (int d = 0; d < NDIM; ++d) us += wv[IM + d];
+            if (!(c2 > (Real)0) || !(c2 - c2 == (Real)0) || !(us - us == (Real)0)) {
                 bad += 1;
             } else {
-                const double cs = sqrt(c2d);
+                const Real cs = real_sqrt(c2);
+                Real r = 0;
 #pragma unroll
-                for (int d = 0; d < NDIM; ++d) rate = fmax(rate, (fabs((double)wv[IM + d]) + cs) * a.g.inv_dx[d]);
+                for (int d = 0; d < NDIM; ++d) r = real_max(r, (fabs(wv[IM + d]) + cs) * (Real)a.g.inv_dx[d]);
+                rate = fmax(rate, (double)r);
             }
         }
     }
