@@ -78,6 +78,10 @@ mfc_status mfc_init(mfc_ctx** out, int nx, int ny, int nz, const double lo[3], c
  *   "fallback"   1 (default) / 0: first-order reconstruction (Sec. 3.2) at a
  *                face whose reconstructed state is non-physical;
  *   "segment"    cells per thread along a sweep (8..256), 0 = automatic;
+ *   "sensor_tau" learned form: the discontinuity sensor trips (WENO5-JS
+ *                weights are used) where max_r b_r > tau (min_r b_r + 1e-6 s^2),
+ *                b the smoothness indicators without their 4/3 factor and s the
+ *                stencil scale; default 1e3, range [1, 1e30];
  *   "profile"    1 / 0: time every kernel launch with CUDA events.
  * Errors: MFC_ERR_ARG for an unknown name or out-of-range value. */
 mfc_status mfc_set_param(mfc_ctx* ctx, const char* name, double value);
@@ -112,10 +116,67 @@ mfc_status mfc_step(mfc_ctx* ctx, double dt);
  * MFC_ERR_STATE_UNSET, MFC_ERR_ARG. */
 mfc_status mfc_cfl_dt(mfc_ctx* ctx, double cfl, double* dt_out);
 
-/* Install the learned-weight network (MFC_LEARNED): n floats laid out as
- * W1[32][5], b1[32], W2[32][32], b2[32], W3[3][32], b3[3] (n = 1315).
- * Errors: MFC_ERR_ARG (wrong n, context not MFC_LEARNED). */
+/* Number of float32 parameters of the learned-weight network. */
+#define MFC_MLP_PARAMS 1347
+
+/* Install the learned-weight network (MFC_LEARNED): host array of
+ * MFC_MLP_PARAMS floats laid out as W1[32][5], b1[32], W2[32][32], b2[32],
+ * W3[3][32], b3[3] (inputs 5 normalised stencil differences, two ReLU layers of
+ * 32, softmax over the 3 WENO5 candidates; see mfc_mlp_forward).  The library
+ * keeps a device copy.  Errors: MFC_ERR_ARG (NULL, wrong n, or the context is
+ * not MFC_LEARNED), MFC_ERR_CUDA. */
 mfc_status mfc_set_mlp(mfc_ctx* ctx, const float* params, int n);
+
+/* Primitive variables of the current state (layout above), float64.  Errors:
+ * MFC_ERR_STATE_UNSET, MFC_ERR_ARG, MFC_ERR_CUDA. */
+mfc_status mfc_get_prims(mfc_ctx* ctx, double* w, int on_device);
+
+/* ---- Learned WENO weights: network kernels (the paper has no learned part;
+ * the network replaces the WENO5-JS nonlinear weights of Sec. 3.2).  All
+ * pointers are device pointers; work is enqueued on `stream` (NULL = legacy
+ * default stream).  For a five-cell stencil v_{i-2..i+2} and the edge at i+1/2
+ * the inputs are x_k = (v_{i+k} - v_i)/s, k = -2..2, s = max_k |v_{i+k} - v_i|
+ * (+1e-30); the outputs are softmax weights omega of the three WENO5
+ * candidates; the edge value is v_i + sum_r omega_r (p_r - v_i).  Matrix
+ * products run on BF16 tensor cores with FP32 accumulation. ---- */
+
+/* omega[batch][3] of inputs x[batch][5] with parameters params[MFC_MLP_PARAMS]. */
+mfc_status mfc_mlp_forward(const float* params, const float* x, long long batch, float* omega, void* stream);
+
+/* Thread blocks of mfc_mlp_grad and the size of its caller-owned workspace. */
+#define MFC_MLP_GRAD_BLOCKS 608
+#define MFC_MLP_WORK_FLOATS (608LL * 4 * 1348)
+
+/* Loss and gradient of a batch:
+ *   L = (1/B) sum_b [ (sum_r omega_br phat_br - target_b)^2
+ *                     + lam * mask_b * sum_r (omega_br - d_r)^2 ],  d = (0.1, 0.6, 0.3),
+ * with x[B][5], phat[B][3] the normalised candidate increments (p_r - v_i)/s,
+ * target[B] the normalised target edge value and mask[B] (1 in smooth
+ * regions).  Writes grad[MFC_MLP_PARAMS] and *loss (loss may be NULL); work is
+ * a caller-owned buffer of MFC_MLP_WORK_FLOATS floats.  Deterministic. */
+mfc_status mfc_mlp_grad(const float* params, const float* x, const float* phat, const float* target,
+                        const float* mask, long long batch, float lam, float* grad, float* loss, float* work,
+                        void* stream);
+
+/* One Adam step (bias-corrected, step >= 1) on params[n] with moments m[n], v[n]. */
+mfc_status mfc_mlp_adam(float* params, const float* grad, float* m, float* v, int n, float lr, float beta1,
+                        float beta2, float eps, int step, void* stream);
+
+/* Training samples from a fine primitive field w_fine (float64, layout above,
+ * nxf x nyf x nzf cells, every active size even and >= 16).  Sample k (a
+ * counter-based hash of seed and k) picks an active direction, a face of the
+ * 2x-restricted grid, a variable and a side, and writes: x[k][5] normalised
+ * coarse stencil, phat[k][3] normalised candidate increments, target[k] the
+ * normalised fine-grid face value (mean of the fine WENO5-JS left and right
+ * values at the coincident fine faces), smooth[k] = 1 unless the
+ * discontinuity sensor trips (max_r b_r > tau (min_r b_r + 1e-6 s^2) on the
+ * smoothness indicators without their 4/3 factor), js[k] the normalised
+ * coarse WENO5-JS value.  Samples whose stencil is flat to FP32 resolution of
+ * its centre value (s <= 1e-7 |v_i|), or whose normalised target exceeds 8 in
+ * magnitude, are written as zeros with smooth[k] = 0. */
+mfc_status mfc_harvest(const double* w_fine, int nxf, int nyf, int nzf, int num_fluids, double weno_eps, double tau,
+                       long long n_samples, unsigned long long seed, float* x, float* phat, float* target,
+                       float* smooth, float* js, void* stream);
 
 /* Number of conserved variables, 2N + d. */
 int mfc_sys_size(const mfc_ctx* ctx);

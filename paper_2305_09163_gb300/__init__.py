@@ -24,7 +24,7 @@ MFC_BC_PERIODIC, MFC_BC_TRANSMISSIVE, MFC_BC_REFLECTIVE = 0, 1, 2
 MFC_FP64, MFC_MIXED, MFC_LEARNED = 0, 1, 2
 PRECISIONS = {"fp64": MFC_FP64, "mixed": MFC_MIXED, "learned": MFC_LEARNED}
 PROFILE_CATEGORIES = ("prims", "sweep_x", "sweep_y", "sweep_z", "prims_cfl", "convert", "mlp")
-MLP_PARAM_COUNT = 32 * 5 + 32 + 32 * 32 + 32 + 3 * 32 + 3
+MLP_PARAMS = 32 * 5 + 32 + 32 * 32 + 32 + 3 * 32 + 3
 
 _lib = None
 
@@ -74,6 +74,19 @@ def _declare(lib):
     lib.mfc_rhs_noalloc.argtypes = [c_void_p, c_void_p, c_int, c_int, c_int, dptr, dptr, ctypes.POINTER(c_int),
                                     c_int, dptr, dptr, c_double, c_int, c_void_p, c_char_p, c_int]
     lib.mfc_rhs_noalloc.restype = c_int
+    lib.mfc_get_prims.argtypes = [c_void_p, c_void_p, c_int]
+    lib.mfc_get_prims.restype = c_int
+    lib.mfc_mlp_forward.argtypes = [c_void_p, c_void_p, c_ll, c_void_p, c_void_p]
+    lib.mfc_mlp_forward.restype = c_int
+    lib.mfc_mlp_grad.argtypes = [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_ll, ctypes.c_float,
+                                 c_void_p, c_void_p, c_void_p, c_void_p]
+    lib.mfc_mlp_grad.restype = c_int
+    lib.mfc_mlp_adam.argtypes = [c_void_p, c_void_p, c_void_p, c_void_p, c_int, ctypes.c_float, ctypes.c_float,
+                                 ctypes.c_float, ctypes.c_float, c_int, c_void_p]
+    lib.mfc_mlp_adam.restype = c_int
+    lib.mfc_harvest.argtypes = [c_void_p, c_int, c_int, c_int, c_int, c_double, c_double, c_ll, ctypes.c_ulonglong,
+                                c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]
+    lib.mfc_harvest.restype = c_int
     lib.mfc_last_error.argtypes = [c_void_p]
     lib.mfc_last_error.restype = c_char_p
     lib.mfc_finalize.argtypes = [c_void_p]
@@ -197,6 +210,72 @@ def mfc_profile_read(ctx):
     return {PROFILE_CATEGORIES[i]: (ms[i], cnt[i]) for i in range(min(k, len(PROFILE_CATEGORIES)))}
 
 
+def mfc_get_prims(ctx, w):
+    lib = load()
+    a, dev = _ptr(w)
+    _check(lib, ctx, lib.mfc_get_prims(ctx, a, dev))
+
+
+MLP_GRAD_BLOCKS = 608
+MLP_WORK_FLOATS = 608 * 4 * 1348
+
+
+def _dev32(t, name):
+    import torch
+    if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.float32 and t.is_contiguous()):
+        raise TypeError("%s must be a contiguous float32 CUDA tensor" % name)
+    return t.data_ptr()
+
+
+def _stream(stream):
+    if stream is not None:
+        return stream
+    import torch
+    return torch.cuda.current_stream().cuda_stream
+
+
+def mfc_mlp_forward(params, x, omega, stream=None):
+    """omega[B,3] = softmax weights of the network for inputs x[B,5] (device float32)."""
+    lib = load()
+    st = lib.mfc_mlp_forward(_dev32(params, "params"), _dev32(x, "x"), x.shape[0], _dev32(omega, "omega"),
+                             _stream(stream))
+    if st != MFC_OK:
+        raise MFCError(st, "mfc_mlp_forward")
+
+
+def mfc_mlp_grad(params, x, phat, target, mask, lam, grad, loss, work, stream=None):
+    lib = load()
+    st = lib.mfc_mlp_grad(_dev32(params, "params"), _dev32(x, "x"), _dev32(phat, "phat"), _dev32(target, "target"),
+                          _dev32(mask, "mask"), x.shape[0], float(lam), _dev32(grad, "grad"),
+                          _dev32(loss, "loss") if loss is not None else None, _dev32(work, "work"), _stream(stream))
+    if st != MFC_OK:
+        raise MFCError(st, "mfc_mlp_grad")
+
+
+def mfc_mlp_adam(params, grad, m, v, lr, beta1, beta2, eps, step, stream=None):
+    lib = load()
+    st = lib.mfc_mlp_adam(_dev32(params, "params"), _dev32(grad, "grad"), _dev32(m, "m"), _dev32(v, "v"),
+                          params.numel(), float(lr), float(beta1), float(beta2), float(eps), int(step),
+                          _stream(stream))
+    if st != MFC_OK:
+        raise MFCError(st, "mfc_mlp_adam")
+
+
+def mfc_harvest(w_fine, n_fine, num_fluids, weno_eps, tau, n_samples, seed, x, phat, target, smooth, js,
+                stream=None):
+    """Training samples from a fine primitive field (device float64 tensor)."""
+    lib = load()
+    wa, dev = _ptr(w_fine)
+    if not dev:
+        raise TypeError("w_fine must be a device tensor")
+    n = list(n_fine) + [1] * (3 - len(n_fine))
+    st = lib.mfc_harvest(wa, int(n[0]), int(n[1]), int(n[2]), int(num_fluids), float(weno_eps), float(tau),
+                         int(n_samples), int(seed) & 0xFFFFFFFFFFFFFFFF, _dev32(x, "x"), _dev32(phat, "phat"),
+                         _dev32(target, "target"), _dev32(smooth, "smooth"), _dev32(js, "js"), _stream(stream))
+    if st != MFC_OK:
+        raise MFCError(st, "mfc_harvest")
+
+
 NOALLOC_MAX_CELLS = 262144
 
 
@@ -279,6 +358,13 @@ class Solver:
 
     def set_mlp(self, params):
         mfc_set_mlp(self.ctx, params)
+
+    def get_prims(self, out=None):
+        import torch
+        if out is None:
+            out = torch.empty(self.shape, dtype=torch.float64, device="cuda")
+        mfc_get_prims(self.ctx, out)
+        return out
 
     def launch_count(self):
         return mfc_launch_count(self.ctx)

@@ -13,6 +13,9 @@
 
 using namespace mfc;
 
+cudaError_t mfc_launch_prims_out(const double* q, double* w, long long nc, int nf, int ndim, const EosConst& e,
+                                 cudaStream_t s);
+
 namespace {
 
 enum ProfCat { P_PRIMS = 0, P_SWEEP_X, P_SWEEP_Y, P_SWEEP_Z, P_CFL, P_CONVERT, P_MLP, P_NCAT };
@@ -37,6 +40,7 @@ struct mfc_ctx {
     int fallback = 1;
     int seg_override = 0;
     bool profile = false;
+    double tau = 1e3;         // learned form: sensor threshold
 
     Geometry g{};
     EosConst e{};
@@ -116,6 +120,13 @@ mfc_status launch(mfc_ctx* c, int cat, F&& fn) {
 }
 
 cudaError_t dispatch_sweep(const mfc_ctx* c, const SweepArgs& a, int dir) {
+    if (c->precision == MFC_LEARNED) {
+        switch (c->nf) {
+            case 1: return launch_sweep<float, 1, true>(a, c->ndim, dir, c->stream);
+            case 2: return launch_sweep<float, 2, true>(a, c->ndim, dir, c->stream);
+            default: return launch_sweep<float, 3, true>(a, c->ndim, dir, c->stream);
+        }
+    }
     if (is_f32(c)) {
         switch (c->nf) {
             case 1: return launch_sweep<float, 1>(a, c->ndim, dir, c->stream);
@@ -179,6 +190,8 @@ SweepArgs base_sweep(const mfc_ctx* c) {
     a.eps = c->eps;
     a.fallback = c->fallback;
     a.fallback_count = c->d_fallback;
+    a.mlp = c->mlp;
+    a.tau = (float)c->tau;
     return a;
 }
 
@@ -350,6 +363,9 @@ mfc_status mfc_set_param(mfc_ctx* c, const char* name, double value) {
     } else if (!strcmp(name, "segment")) {
         if (!(value == 0.0 || (value >= 8 && value <= 256))) return fail(c, MFC_ERR_ARG, "segment out of range");
         c->seg_override = (int)value;
+    } else if (!strcmp(name, "sensor_tau")) {
+        if (!(value >= 1.0 && value <= 1e30)) return fail(c, MFC_ERR_ARG, "sensor_tau must lie in [1, 1e30]");
+        c->tau = value;
     } else if (!strcmp(name, "profile")) {
         if (value != 0.0 && value != 1.0) return fail(c, MFC_ERR_ARG, "profile must be 0 or 1");
         c->profile = value != 0.0;
@@ -480,9 +496,35 @@ mfc_status mfc_cfl_dt(mfc_ctx* c, double cfl, double* dt_out) {
 mfc_status mfc_set_mlp(mfc_ctx* c, const float* params, int n) {
     mfc_status s = ensure_alive(c);
     if (s != MFC_OK) return s;
-    return fail(c, MFC_ERR_ARG, "learned mode is not available in this build");
-    (void)params;
-    (void)n;
+    if (!params || n != MFC_MLP_PARAMS) return fail(c, MFC_ERR_ARG, "need %d parameters", MFC_MLP_PARAMS);
+    if (c->precision != MFC_LEARNED) return fail(c, MFC_ERR_ARG, "context is not MFC_LEARNED");
+    if (!c->mlp) {
+        cudaError_t e = cudaMalloc(&c->mlp, sizeof(float) * MFC_MLP_PARAMS);
+        if (e != cudaSuccess) {
+            c->mlp = nullptr;
+            return fail(c, e == cudaErrorMemoryAllocation ? MFC_ERR_OOM : MFC_ERR_CUDA, "cudaMalloc: %s",
+                        cudaGetErrorString(e));
+        }
+    }
+    MFC_CUDA(c, cudaMemcpyAsync(c->mlp, params, sizeof(float) * MFC_MLP_PARAMS, cudaMemcpyHostToDevice, c->stream));
+    MFC_CUDA(c, cudaStreamSynchronize(c->stream));
+    return MFC_OK;
+}
+
+mfc_status mfc_get_prims(mfc_ctx* c, double* w, int on_device) {
+    mfc_status s = ensure_alive(c);
+    if (s != MFC_OK) return s;
+    if (!w) return fail(c, MFC_ERR_ARG, "NULL buffer");
+    if (!c->state_set) return fail(c, MFC_ERR_STATE_UNSET, "no state set");
+    double* dst = on_device ? w : c->q1;
+    s = launch(c, P_CONVERT, [&] { return mfc_launch_prims_out(c->q, dst, c->ncell, c->nf, c->ndim, c->e, c->stream); });
+    if (s != MFC_OK) return s;
+    if (!on_device) {
+        const size_t bytes = sizeof(double) * (size_t)c->ns * (size_t)c->ncell;
+        MFC_CUDA(c, cudaMemcpyAsync(w, c->q1, bytes, cudaMemcpyDeviceToHost, c->stream));
+        MFC_CUDA(c, cudaStreamSynchronize(c->stream));
+    }
+    return MFC_OK;
 }
 
 int mfc_sys_size(const mfc_ctx* c) { return c ? c->ns : 0; }

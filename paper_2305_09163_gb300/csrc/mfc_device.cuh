@@ -25,6 +25,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "mfc_mlp.cuh"
+
 namespace mfc {
 
 enum { BC_PERIODIC = 0, BC_TRANSMISSIVE = 1, BC_REFLECTIVE = 2 };
@@ -63,6 +65,8 @@ struct SweepArgs {
     int nseg;               // marching kernels: segments along DIR
     long long slots_per_block;  // x-stream kernel: edge slots owned by one CTA
     unsigned long long* fallback_count;  // optional counter of fallback faces
+    const float* mlp;       // learned form: network parameters (device)
+    float tau;              // learned form: discontinuity-sensor threshold
 };
 
 struct PrimArgs {
@@ -350,6 +354,145 @@ __device__ __forceinline__ void face_flux(const SweepArgs& a, const EosR<Real>& 
     }
 }
 
+// ---------------------------------------------------------------------------
+// Learned form (the paper has no learned part; the network replaces the
+// WENO5-JS nonlinear weights of Sec. 3.2).  Per cell and variable the FP32
+// WENO5 pieces are formed as in the mixed path; the five-cell stencil,
+// normalised by s = max_k |v_{c+k} - v_c|, goes to shared memory as BF16; the
+// warp then evaluates the network for its 32 cells x NS variables on the
+// tensor cores (16 stencils per tile) and each lane combines its candidates
+// with the returned weights.  WENO5-JS weights are kept where the
+// discontinuity sensor trips (max_r b_r > tau (min_r b_r + 1e-6 s^2), b the
+// smoothness indicators without their 4/3 factor) or the stencil is flat to
+// FP32 resolution (s <= 1e-7 |v_c|).  All 32 lanes must call these functions.
+// ---------------------------------------------------------------------------
+template <int NS> struct LearnSmem {
+    uint32_t x[NS][32][4];   // BF16 inputs, columns 0..4 used
+    float om[NS][32][3];     // network weights of each stencil
+};
+
+// Network over the NS x 32 stencils staged in sm.x (one side of the cells).
+template <int NS>
+__device__ __forceinline__ void learned_side(const MlpWeights& W, LearnSmem<NS>& sm, int lane) {
+    const int g = lane >> 2, t = lane & 3;
+    __syncwarp();
+#pragma unroll 1
+    for (int v = 0; v < NS; ++v) {
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const uint32_t a_in[2] = {sm.x[v][16 * h + g][t], sm.x[v][16 * h + g + 8][t]};
+            float c1[4][4], c2[4][4], z[4];
+            uint32_t a1[2][4], a2[2][4];
+            mlp_tile_forward(W, a_in, c1, a1, c2, a2, z);
+            float og[3], og8[3];
+            mlp_softmax_rows(z, og, og8);
+            if (t == 0) {
+#pragma unroll
+                for (int q = 0; q < 3; ++q) {
+                    sm.om[v][16 * h + g][q] = og[q];
+                    sm.om[v][16 * h + g + 8][q] = og8[q];
+                }
+            }
+        }
+    }
+    __syncwarp();
+}
+
+// Edge values of one cell for all NS variables: WENO5-JS (eRjs, eLjs) and the
+// learned form (eR, eL; equal to the JS values where the sensor trips).
+template <int NS>
+__device__ __forceinline__ void learned_cell_edges(const float (&vc)[NS], const float (&D)[NS][4], float eps34,
+                                                   float tau, const MlpWeights& W, LearnSmem<NS>& sm, int lane,
+                                                   float (&eRjs)[NS], float (&eLjs)[NS], float (&eR)[NS],
+                                                   float (&eL)[NS]) {
+    bool usejs[NS];
+    float inv_s[NS];
+#pragma unroll
+    for (int v = 0; v < NS; ++v) {
+        const float* d = D[v];
+        weno5_edges(vc[v], d, eps34, eRjs[v], eLjs[v]);
+        const float S0 = d[0] * d[0], S1 = d[1] * d[1], S2 = d[2] * d[2], S3 = d[3] * d[3];
+        const float b0 = fmaf(2.5f, S1, fmaf(-2.75f, d[1] * d[0], S0));
+        const float b1 = fmaf(-1.25f, d[1] * d[2], S1 + S2);
+        const float b2 = fmaf(2.5f, S2, fmaf(-2.75f, d[2] * d[3], S3));
+        const float xm2 = -(d[0] + d[1]), xm1 = -d[1], xp1 = d[2], xp2 = d[2] + d[3];
+        const float sc = fmaxf(fmaxf(fabsf(xm2), fabsf(xm1)), fmaxf(fabsf(xp1), fabsf(xp2)));
+        const float bmax = fmaxf(b0, fmaxf(b1, b2)), bmin = fminf(b0, fminf(b1, b2));
+        usejs[v] = !(sc > 1e-7f * fabsf(vc[v])) || (bmax > tau * fmaf(1e-6f * sc, sc, bmin));
+        inv_s[v] = __fdividef(1.0f, sc + 1e-30f);
+        const float is = inv_s[v];
+        sm.x[v][lane][0] = pack_bf16(xm2 * is, xm1 * is);
+        sm.x[v][lane][1] = pack_bf16(0.f, xp1 * is);
+        sm.x[v][lane][2] = pack_bf16(xp2 * is, 0.f);
+        sm.x[v][lane][3] = 0u;
+    }
+    learned_side<NS>(W, sm, lane);
+#pragma unroll
+    for (int v = 0; v < NS; ++v) {
+        const float* d = D[v];
+        // increments at c+1/2 of the stencils c-2..c, c-1..c+1, c..c+2
+        const float p0 = fmaf(5.f / 6.f, d[1], (-1.f / 3.f) * d[0]);
+        const float p1 = fmaf(1.f / 6.f, d[1], (1.f / 3.f) * d[2]);
+        const float p2 = fmaf(2.f / 3.f, d[2], (-1.f / 6.f) * d[3]);
+        const float* om = sm.om[v][lane];
+        const float el = vc[v] + fmaf(om[0], p0, fmaf(om[1], p1, om[2] * p2));
+        eL[v] = usejs[v] ? eLjs[v] : el;
+        // reversed stencil for the edge at c-1/2
+        const float is = inv_s[v];
+        const float xm2 = -(d[0] + d[1]), xm1 = -d[1], xp1 = d[2], xp2 = d[2] + d[3];
+        sm.x[v][lane][0] = pack_bf16(xp2 * is, xp1 * is);
+        sm.x[v][lane][1] = pack_bf16(0.f, xm1 * is);
+        sm.x[v][lane][2] = pack_bf16(xm2 * is, 0.f);
+    }
+    learned_side<NS>(W, sm, lane);
+#pragma unroll
+    for (int v = 0; v < NS; ++v) {
+        const float* d = D[v];
+        // increments at c-1/2 of the stencils c..c+2, c-1..c+1, c-2..c
+        const float m0 = fmaf(-5.f / 6.f, d[2], (1.f / 3.f) * d[3]);
+        const float m1 = fmaf(-1.f / 6.f, d[2], (-1.f / 3.f) * d[1]);
+        const float m2 = fmaf(-2.f / 3.f, d[1], (1.f / 6.f) * d[0]);
+        const float* om = sm.om[v][lane];
+        const float er = vc[v] + fmaf(om[0], m0, fmaf(om[1], m1, om[2] * m2));
+        eR[v] = usejs[v] ? eRjs[v] : er;
+    }
+}
+
+// Face flux of the learned form: the learned face states, else (non-physical)
+// the WENO5-JS states, else the first-order cell values.
+template <int NF, int NDIM, int DIR>
+__device__ __forceinline__ void face_flux_learned(const SweepArgs& a, const EosR<float>& e, const float* Ll,
+                                                  const float* Rl, const float* Lj, const float* Rj, const float* cl,
+                                                  const float* cr, float* F, float& ut) {
+    constexpr int NS = Layout<NF, NDIM>::NS;
+    Mix<float> mL = mixture<float, NF, NDIM>(Ll, e);
+    Mix<float> mR = mixture<float, NF, NDIM>(Rl, e);
+    int choice = 0;
+    if (a.fallback) {
+        if (!(face_state_ok<float, NF, NDIM>(Ll, mL) && face_state_ok<float, NF, NDIM>(Rl, mR))) {
+            const Mix<float> jL = mixture<float, NF, NDIM>(Lj, e);
+            const Mix<float> jR = mixture<float, NF, NDIM>(Rj, e);
+            if (face_state_ok<float, NF, NDIM>(Lj, jL) && face_state_ok<float, NF, NDIM>(Rj, jR)) {
+                choice = 1;
+                mL = jL;
+                mR = jR;
+            } else {
+                choice = 2;
+                mL = mixture<float, NF, NDIM>(cl, e);
+                mR = mixture<float, NF, NDIM>(cr, e);
+                if (a.fallback_count) atomicAdd(a.fallback_count, 1ULL);
+            }
+        }
+    }
+    float fl[NS], fr[NS];
+#pragma unroll
+    for (int v = 0; v < NS; ++v) {
+        fl[v] = choice == 0 ? Ll[v] : (choice == 1 ? Lj[v] : cl[v]);
+        fr[v] = choice == 0 ? Rl[v] : (choice == 1 ? Rj[v] : cr[v]);
+    }
+    hllc<float, NF, NDIM, DIR>(fl, fr, mL, mR, F, ut);
+}
+
 // Finish one cell: flux difference + alpha div(u) source, then the epilogue
 // selected by a.mode.
 template <typename Real, int NF, int NDIM>
@@ -392,24 +535,32 @@ __device__ __forceinline__ void finish_cell(const SweepArgs& a, long long idx, c
 // ---------------------------------------------------------------------------
 // Directional sweep for y and z.  One thread marches along one pencil segment
 // of `seg` cells in direction DIR: it reconstructs the edges of cells
-// s0-1..s1, forms faces s0-1/2..s1-1/2 and finishes cells s0..s1-1.  The lanes
-// of a warp are consecutive x, so every load and store is coalesced.
+// s0-1..s1, forms faces s0-1/2..s1-1/2 and finishes cells s0..s1-1.  A warp
+// covers 32 consecutive x of one segment (lanes past the end of a row work on
+// a clamped copy and store nothing), so loads and stores are coalesced and all
+// lanes of a warp run the same number of iterations, which the tensor-core
+// network of the learned form (LEARNED) requires.
 // ---------------------------------------------------------------------------
-template <typename Real, int NF, int NDIM, int DIR>
+template <typename Real, int NF, int NDIM, int DIR, bool LEARNED = false>
 __global__ void __launch_bounds__(128) sweep_kernel(const SweepArgs a) {
+    static_assert(!LEARNED || sizeof(Real) == 4, "the learned form runs in FP32");
     using Lay = Layout<NF, NDIM>;
     constexpr int NS = Lay::NS, IM = Lay::IM;
     constexpr int T1 = (DIR == 0) ? 1 : 0;
     constexpr int T2 = (DIR == 2) ? 1 : 2;
     const Real* __restrict__ w = static_cast<const Real*>(a.w);
-    const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const int lane = threadIdx.x & 31;
+    const long long wid = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int n1 = a.g.n[T1], n2 = a.g.n[T2], nd = a.g.n[DIR];
-    const long long total = (long long)n1 * a.nseg * n2;
-    if (tid >= total) return;
-    const int t1 = (int)(tid % n1);
-    const long long rest = tid / n1;
+    const int nxc = (n1 + 31) >> 5;
+    if (wid >= (long long)nxc * a.nseg * n2) return;  // whole warps only
+    const int xc = (int)(wid % nxc);
+    const long long rest = wid / nxc;
     const int sg = (int)(rest % a.nseg);
     const int t2 = (int)(rest / a.nseg);
+    const bool active = xc * 32 + lane < n1;
+    if (!LEARNED && !active) return;
+    const int t1 = active ? xc * 32 + lane : n1 - 1;
     const long long sd = stride_of(a.g, DIR);
     const long long base = (long long)t1 * stride_of(a.g, T1) + (long long)t2 * stride_of(a.g, T2);
     const long long nc = a.g.ncell;
@@ -419,6 +570,13 @@ __global__ void __launch_bounds__(128) sweep_kernel(const SweepArgs a) {
     const Real eps34 = (Real)(0.75 * a.eps);
     const EosR<Real> e(a.e);
     const Real inv_dx = (Real)a.g.inv_dx[DIR];
+    MlpWeights W;
+    LearnSmem<NS>* lsm = nullptr;
+    if constexpr (LEARNED) {
+        __shared__ LearnSmem<NS> lbuf[4];
+        lsm = &lbuf[threadIdx.x >> 5];
+        mlp_load_weights(a.mlp, W, lane);
+    }
 
     auto load = [&](int i, Real* out) {
         bool flip = false;
@@ -447,18 +605,25 @@ __global__ void __launch_bounds__(128) sweep_kernel(const SweepArgs a) {
             D[v][3] = vp2[v] - vp1[v];
         }
     }
-    Real eLprev[NS], Fprev[NS], utprev = 0;
+    Real eLprev[NS], eLprevJ[NS], Fprev[NS], utprev = 0;
 #pragma unroll
-    for (int v = 0; v < NS; ++v) { eLprev[v] = 0; Fprev[v] = 0; }
+    for (int v = 0; v < NS; ++v) { eLprev[v] = 0; eLprevJ[v] = 0; Fprev[v] = 0; }
 
     for (int c = s0 - 1; c <= s1; ++c) {
-        Real eR[NS], eL[NS];
+        Real eR[NS], eL[NS], eRJ[NS], eLJ[NS];
+        if constexpr (LEARNED) {
+            learned_cell_edges<NS>(vc, D, eps34, a.tau, W, *lsm, lane, eRJ, eLJ, eR, eL);
+        } else {
 #pragma unroll
-        for (int v = 0; v < NS; ++v) weno5_edges(vc[v], D[v], eps34, eR[v], eL[v]);
+            for (int v = 0; v < NS; ++v) weno5_edges(vc[v], D[v], eps34, eR[v], eL[v]);
+        }
         if (c >= s0) {
             Real F[NS], ut;
-            face_flux<Real, NF, NDIM, DIR>(a, e, eLprev, eR, cm1, vc, F, ut);
-            if (c >= s0 + 1)
+            if constexpr (LEARNED)
+                face_flux_learned<NF, NDIM, DIR>(a, e, eLprev, eR, eLprevJ, eRJ, cm1, vc, F, ut);
+            else
+                face_flux<Real, NF, NDIM, DIR>(a, e, eLprev, eR, cm1, vc, F, ut);
+            if (c >= s0 + 1 && active)
                 finish_cell<Real, NF, NDIM>(a, base + (long long)(c - 1) * sd, Fprev, F, utprev, ut, cm1, inv_dx);
 #pragma unroll
             for (int v = 0; v < NS; ++v) Fprev[v] = F[v];
@@ -466,7 +631,11 @@ __global__ void __launch_bounds__(128) sweep_kernel(const SweepArgs a) {
         }
         // advance the window by one cell
 #pragma unroll
-        for (int v = 0; v < NS; ++v) { eLprev[v] = eL[v]; cm1[v] = vc[v]; }
+        for (int v = 0; v < NS; ++v) {
+            eLprev[v] = eL[v];
+            if constexpr (LEARNED) eLprevJ[v] = eLJ[v];
+            cm1[v] = vc[v];
+        }
         if (c < s1) {
             Real nw[NS];
             load(c + 3, nw);
@@ -493,15 +662,19 @@ __global__ void __launch_bounds__(128) sweep_kernel(const SweepArgs a) {
 // face c-1/2 from its own right-side value and the left-side value of slot s-1
 // (shared memory), and finishes cell c-1 from faces c-3/2 and c-1/2.  The last
 // slot's left-side value and flux carry to the next chunk, and each CTA starts
-// two slots early so that its first cell has both faces.
+// two slots early so that its first cell has both faces.  Every lane takes part
+// in every chunk, as the learned form's warp-level network needs.
 // ---------------------------------------------------------------------------
 constexpr int kStreamThreads = 128;
 
-template <typename Real, int NF, int NDIM>
+template <typename Real, int NF, int NDIM, bool LEARNED = false>
 __global__ void __launch_bounds__(kStreamThreads) sweep_x_stream_kernel(const SweepArgs a) {
+    static_assert(!LEARNED || sizeof(Real) == 4, "the learned form runs in FP32");
     using Lay = Layout<NF, NDIM>;
     constexpr int NS = Lay::NS, IM = Lay::IM;
+    constexpr int NJ = LEARNED ? NS : 1;
     __shared__ Real sh_eL[NS][kStreamThreads + 1];
+    __shared__ Real sh_eLJ[NJ][kStreamThreads + 1];
     __shared__ Real sh_F[NS + 1][kStreamThreads + 1];
     const Real* __restrict__ w = static_cast<const Real*>(a.w);
     const int n = a.g.n[0];
@@ -516,6 +689,13 @@ __global__ void __launch_bounds__(kStreamThreads) sweep_x_stream_kernel(const Sw
     const EosR<Real> e(a.e);
     const Real inv_dx = (Real)a.g.inv_dx[0];
     const int t = threadIdx.x;
+    MlpWeights W;
+    LearnSmem<NS>* lsm = nullptr;
+    if constexpr (LEARNED) {
+        __shared__ LearnSmem<NS> lbuf[kStreamThreads / 32];
+        lsm = &lbuf[t >> 5];
+        mlp_load_weights(a.mlp, W, t & 31);
+    }
 
     for (long long base = own0 - 2; base < own1; base += kStreamThreads) {
         const long long s = base + t;
@@ -523,7 +703,14 @@ __global__ void __launch_bounds__(kStreamThreads) sweep_x_stream_kernel(const Sw
         const long long row = live ? s / rowlen : 0;
         const int c = live ? (int)(s - row * rowlen) - 1 : -1;
         const long long rowoff = row * n;
-        Real cell[NS], cm1[NS], eL[NS], eR[NS];
+        Real cell[NS], cm1[NS], eL[NS], eR[NS], eLJ[NS], eRJ[NS];
+        Real vcv[NS], Dv[NS][4];
+#pragma unroll
+        for (int q = 0; q < NS; ++q) {
+            vcv[q] = 0;
+            cm1[q] = 0;
+            Dv[q][0] = Dv[q][1] = Dv[q][2] = Dv[q][3] = 0;
+        }
         if (live) {
             Real v[5][NS];
 #pragma unroll
@@ -536,16 +723,29 @@ __global__ void __launch_bounds__(kStreamThreads) sweep_x_stream_kernel(const Sw
             }
 #pragma unroll
             for (int q = 0; q < NS; ++q) {
-                const Real D[4] = {v[1][q] - v[0][q], v[2][q] - v[1][q], v[3][q] - v[2][q], v[4][q] - v[3][q]};
-                weno5_edges(v[2][q], D, eps34, eR[q], eL[q]);
-                cell[q] = v[2][q];
+                Dv[q][0] = v[1][q] - v[0][q];
+                Dv[q][1] = v[2][q] - v[1][q];
+                Dv[q][2] = v[3][q] - v[2][q];
+                Dv[q][3] = v[4][q] - v[3][q];
+                vcv[q] = v[2][q];
                 cm1[q] = v[1][q];
             }
         }
+        if constexpr (LEARNED) {
+            learned_cell_edges<NS>(vcv, Dv, eps34, a.tau, W, *lsm, t & 31, eRJ, eLJ, eR, eL);
+        } else if (live) {
+#pragma unroll
+            for (int q = 0; q < NS; ++q) weno5_edges(vcv[q], Dv[q], eps34, eR[q], eL[q]);
+        }
+#pragma unroll
+        for (int q = 0; q < NS; ++q) cell[q] = vcv[q];
         // left-side values of this chunk; slot 0 holds the carry from the last chunk
         if (live) {
 #pragma unroll
-            for (int q = 0; q < NS; ++q) sh_eL[q][t + 1] = eL[q];
+            for (int q = 0; q < NS; ++q) {
+                sh_eL[q][t + 1] = eL[q];
+                if constexpr (LEARNED) sh_eLJ[q][t + 1] = eLJ[q];
+            }
         }
         __syncthreads();
         Real F[NS], ut = 0;
@@ -554,7 +754,14 @@ __global__ void __launch_bounds__(kStreamThreads) sweep_x_stream_kernel(const Sw
             Real lft[NS];
 #pragma unroll
             for (int q = 0; q < NS; ++q) lft[q] = sh_eL[q][t];
-            face_flux<Real, NF, NDIM, 0>(a, e, lft, eR, cm1, cell, F, ut);
+            if constexpr (LEARNED) {
+                Real lftJ[NS];
+#pragma unroll
+                for (int q = 0; q < NS; ++q) lftJ[q] = sh_eLJ[q][t];
+                face_flux_learned<NF, NDIM, 0>(a, e, lft, eR, lftJ, eRJ, cm1, cell, F, ut);
+            } else {
+                face_flux<Real, NF, NDIM, 0>(a, e, lft, eR, cm1, cell, F, ut);
+            }
 #pragma unroll
             for (int q = 0; q < NS; ++q) sh_F[q][t + 1] = F[q];
             sh_F[NS][t + 1] = ut;
@@ -572,6 +779,7 @@ __global__ void __launch_bounds__(kStreamThreads) sweep_x_stream_kernel(const Sw
 #pragma unroll
             for (int q = 0; q < NS; ++q) {
                 sh_eL[q][0] = sh_eL[q][kStreamThreads];
+                if constexpr (LEARNED) sh_eLJ[q][0] = sh_eLJ[q][kStreamThreads];
                 sh_F[q][0] = sh_F[q][kStreamThreads];
             }
             sh_F[NS][0] = sh_F[NS][kStreamThreads];

@@ -1,0 +1,6 @@
+// Instantiates the learned-form sweep kernels (FP32, tensor-core network) for
+// 2 fluid(s).
+#include "mfc_launch.cuh"
+namespace mfc {
+template cudaError_t launch_sweep<float, 2, true>(SweepArgs, int, int, cudaStream_t);
+}  // namespace mfc

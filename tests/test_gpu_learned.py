@@ -1,0 +1,116 @@
+"""The learned-weight form: fused tensor-core inference in the sweeps, training
+on the GPU, and what the trained network gains over WENO5-JS."""
+import numpy as np
+import pytest
+
+import oracle
+import workloads
+from parity_util import rhs_error
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def m():
+    import paper_2305_09163_gb300 as mm
+    mm.build()
+    mm.load()
+    return mm
+
+
+def _ideal_params():
+    from paper_2305_09163_gb300 import learned
+    p = learned.init_params(3).astype(np.float64)
+    # W3 = 0 and b3 = log(d): the network returns the ideal weights for any input
+    p[1248:1344] = 0.0
+    p[1344:1347] = np.log([0.1, 0.6, 0.3])
+    return p.astype(np.float32)
+
+
+@pytest.mark.parametrize("n,nf,bc", [((37, 23, 19), 2, 1), ((41,), 2, 0), ((29, 17), 3, 2), ((19, 24, 13), 3, 1)])
+def test_ideal_weight_network_reproduces_linear_weno5(m, n, nf, bc):
+    """With constant ideal weights the learned reconstruction is the linear
+    fifth-order scheme, i.e. WENO5 with epsilon -> infinity: compare with the
+    FP64 oracle at that epsilon, to FP32 accuracy, in all three kernels."""
+    gam, pin = workloads.fluids(nf)
+    pb = oracle.Problem(n, (0,) * 3, (1,) * 3, (bc,) * 6, gam, pin, eps=1e30, fallback=False)
+    w = workloads.random_prims(n, nf, seed=17, noise=0.0)
+    q = oracle.cons_from_prims(pb, w)
+    R_cpu, fmax, _ = oracle.rhs(pb, q, return_info=True)
+    s = m.Solver(pb.n, pb.lo, pb.hi, pb.bc, gam, pin, precision="learned", fallback=0, sensor_tau=1e30)
+    s.set_mlp(_ideal_params())
+    s.set_state_prim(torch.from_numpy(w).cuda())
+    R = s.rhs().cpu().numpy()
+    err = rhs_error(pb, q, R, R_cpu, fmax)
+    assert err.max() <= 2e-5, err
+
+
+def test_learned_form_steps_and_falls_back_safely(m):
+    """A trained network on the shock-bubble: finite, physical states over a few
+    steps, and some faces take the first-order fallback or the JS weights."""
+    from paper_2305_09163_gb300 import learned
+    samples = learned.harvest_run(workloads.shock_bubble(64, steps=20), 20, {10, 20}, 400_000, 1)
+    P, hist = learned.train(samples, epochs=4, batch=32768)
+    assert hist[-1] < hist[0]
+    wl = workloads.shock_bubble(48)
+    s = m.Solver(wl.n, wl.lo, wl.hi, wl.bc, wl.gamma, wl.pi_inf, precision="learned", fallback=1)
+    s.set_mlp(P.cpu().numpy())
+    s.set_state_prim(torch.from_numpy(wl.prims()).cuda())
+    for _ in range(10):
+        s.step(s.cfl_dt(0.3))
+    q = s.get_state()
+    assert torch.isfinite(q).all()
+    assert s.cfl_dt(0.3) > 0
+
+
+def _restrict(w, f=2):
+    ns, nz, ny, nx = w.shape
+    return w.reshape(ns, nz // f, f, ny // f, f, nx // f, f).mean(axis=(2, 4, 6))
+
+
+def _run(m, wl, precision, t_end, params=None):
+    s = m.Solver(wl.n, wl.lo, wl.hi, wl.bc, wl.gamma, wl.pi_inf, precision=precision, fallback=1)
+    if params is not None:
+        s.set_mlp(params)
+    s.set_state_prim(torch.from_numpy(wl.prims()).cuda())
+    t = 0.0
+    while t < t_end:
+        dt = min(s.cfl_dt(0.3), t_end - t)
+        s.step(dt)
+        t += dt
+    return s.get_prims().cpu().numpy()
+
+
+def test_trained_network_gain_over_weno5_js(m, capsys):
+    """Train on stencils of the shock-bubble and bubble-cloud runs (2x grids),
+    then measure on a held-out bubble cloud: the face-value error against the
+    2x-resolution target must drop below WENO5-JS's; the solution-level L1
+    errors (rho, p, alpha vs the restricted 2x FP64 run) are reported."""
+    from paper_2305_09163_gb300 import learned
+    parts = [learned.harvest_run(workloads.shock_bubble(96, steps=40), 40, {10, 20, 30, 40}, 500_000, 1),
+             learned.harvest_run(workloads.bubble_cloud(96, steps=40, seed=230509163), 40, {10, 20, 30, 40},
+                                 500_000, 2)]
+    P, hist = learned.train(learned.Samples.cat(parts), epochs=10, batch=65536)
+    held = learned.harvest_run(workloads.bubble_cloud(96, steps=30, seed=4242), 30, {15, 30}, 200_000, 9)
+    e_net, e_js = learned.evaluate(P, held)
+    # solution level: coarse 48^3 learned and JS (mixed) against the 96^3 FP64 run
+    n = 48
+    fine = workloads.bubble_cloud(2 * n, seed=4242)
+    coarse = workloads.bubble_cloud(n, seed=4242)
+    coarse.prims = lambda: _restrict(fine.prims())
+    t_end = 2.5e-5
+    ref = _restrict(_run(m, fine, "fp64", t_end))
+    wl_ = _run(m, coarse, "learned", t_end, P.cpu().numpy())
+    wj = _run(m, coarse, "mixed", t_end)
+    def l1(w):
+        rho = lambda a: a[0] + a[1]
+        return [float(np.abs(rho(w) - rho(ref)).mean() / np.abs(rho(ref)).mean()),
+                float(np.abs(w[5] - ref[5]).mean() / np.abs(ref[5]).mean()),
+                float(np.abs(w[6] - ref[6]).mean())]
+    e_l, e_j = l1(wl_), l1(wj)
+    with capsys.disabled():
+        print("\nlearned gain: face MSE net %.5g vs JS %.5g (%.1f%%); solution L1 (rho, p, alpha) "
+              "learned %s vs JS %s" % (e_net, e_js, 100 * (1 - e_net / e_js), np.round(e_l, 6), np.round(e_j, 6)))
+    assert e_net < e_js
+    assert all(np.isfinite(e_l))
