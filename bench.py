@@ -48,6 +48,17 @@ FLOP_SWEEP_CELL_3D_2F = 74 * 7 + 88 + 18
 FLOP_RK_CELL_2F = 7 * (6 + 6 + 4) / 3.0
 # Nominal FP64 peak: 152 SMs x 4 FP64 FLOP/clk/SM (2 DFMA) x 2.07 GHz
 FP64_PEAK_TFLOPS = 152 * 4 * 2.07e9 / 1e12
+# Nominal FP32 peak: 152 SMs x 128 FMA/clk x 2 FLOP x 2.07 GHz
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+# Algorithmic DRAM bytes per cell of the three mixed-form sweeps of one stage
+# (FP32 primitives and accumulator, FP64 state): x reads w and writes R (56 B),
+# y reads w and updates R (84 B), z reads w and R and the FP64 stage states and
+# writes the new state (224 B; 168 B in stage 1, which has no q^n term).
+BYTES_MIXED_SWEEPS_STAGE = (56 + 84 + (168 + 224 + 224) / 3.0)
+# Useful tensor-core FLOPs of the learned network per stencil
+# (5x32 + 32x32 + 32x3 multiply-adds) and stencils per cell and sweep (2 edges x 7 variables).
+FLOP_MLP_STENCIL = 2 * (5 * 32 + 32 * 32 + 32 * 3)
+STENCILS_PER_CELL_SWEEP = 14
 
 
 def _dist():
@@ -106,6 +117,28 @@ class ClockSampler:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
                 "samples": len(sm)}
+
+
+def _measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except (OSError, ValueError):
+        return {}
+
+
+def train_learned(m, torch, log=None):
+    """Train the learned weights on stencils of 128^3 shock-bubble and
+    bubble-cloud runs (done before, and outside, the timed region)."""
+    from paper_2305_09163_gb300 import learned
+    t0 = time.perf_counter()
+    parts = [learned.harvest_run(workloads.shock_bubble(128, steps=80), 80, {20, 40, 60, 80}, 1_000_000, 1),
+             learned.harvest_run(workloads.bubble_cloud(128, steps=80, seed=230509163), 80, {20, 40, 60, 80},
+                                 1_000_000, 2)]
+    P, hist = learned.train(learned.Samples.cat(parts))
+    torch.cuda.synchronize()
+    return P.cpu().numpy(), {"samples": sum(len(p) for p in parts), "final_loss": hist[-1],
+                             "seconds": time.perf_counter() - t0}
 
 
 def _sweep_profile(prof):
@@ -246,7 +279,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
     ap.add_argument("--n", type=int, default=256, help="cells per direction of the shock-bubble cube")
-    ap.add_argument("--forms", default="fp64,mixed", help="comma list of fp64,mixed,learned")
+    ap.add_argument("--forms", default="fp64,mixed,learned", help="comma list of fp64,mixed,learned")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     args = ap.parse_args()
@@ -278,12 +311,13 @@ def main():
     ns = wl.sys_size
     forms = [f.strip() for f in args.forms.split(",") if f.strip()]
     results = {}
+    training = None
     for form in forms:
+        mlp = None
         if form == "learned":
-            results[form] = None  # reported once the learned kernels are built
-            continue
+            mlp, training = train_learned(m, torch)
         r = time_form(m, torch, wl, w_dev, form, args.steps, args.warmup, barrier,
-                      sampler_gpu=local if form == "fp64" else None)
+                      sampler_gpu=local if form == "fp64" else None, mlp=mlp)
         t = torch.tensor([r["ms_per_step"]], device="cuda")
         if ws > 1:
             import torch.distributed as dist
@@ -322,10 +356,29 @@ def main():
             line["forms"][form] = None
             continue
         g = r["ms_max"] * 1e-3 / (ws * cells * ns * 3) * 1e9
-        line["forms"][form] = {"grind": g, "unit": UNIT, "ms_per_step": r["ms_max"],
-                               "cell_updates_per_s": ws * cells / (r["ms_max"] * 1e-3),
-                               "speedup_vs_fp64": ms / r["ms_max"], "gpu_launches": r["launches"],
-                               "kernels_ms": {k: v[0] for k, v in r["kernels"].items() if v[1]}}
+        entry = {"grind": g, "unit": UNIT, "ms_per_step": r["ms_max"],
+                 "cell_updates_per_s": ws * cells / (r["ms_max"] * 1e-3),
+                 "speedup_vs_fp64": ms / r["ms_max"], "gpu_launches": r["launches"],
+                 "kernels_ms": {k: v[0] for k, v in r["kernels"].items() if v[1]}}
+        sweep_s = r["sweep_ms"] * 1e-3
+        stages = r["sweep_launches"] / 3.0
+        peaks = _measured_peaks()
+        hbm = float(peaks.get("hbm_gbs", 6800.0))
+        if form == "mixed":
+            gbs = BYTES_MIXED_SWEEPS_STAGE * cells * stages / sweep_s / 1e9
+            tf = FLOP_SWEEP_CELL_3D_2F * cells * r["sweep_launches"] / sweep_s / 1e12
+            entry["roofline"] = {"kernel": "sweep (x, y, z)", "hbm_gbs": gbs, "hbm_peak": hbm,
+                                 "hbm_frac": gbs / hbm, "fp32_tflops": tf, "fp32_peak": FP32_PEAK_TFLOPS,
+                                 "fp32_frac": tf / FP32_PEAK_TFLOPS,
+                                 "note": "peaks: HBM of measured copy, FP32 nominal"}
+        elif form == "learned":
+            tfl = FLOP_MLP_STENCIL * STENCILS_PER_CELL_SWEEP * cells * r["sweep_launches"] / sweep_s / 1e12
+            bf = float(peaks.get("bf16_tflops_sustained", 1700.0))
+            entry["roofline"] = {"kernel": "sweep (x, y, z) with the network", "tensor_tflops": tfl,
+                                 "tensor_peak": bf, "tensor_frac": tfl / bf,
+                                 "note": "useful network FLOPs; peak = measured sustained BF16 (mma.sync path)"}
+            entry["training"] = training
+        line["forms"][form] = entry
     if not args.no_e2e:
         k = max(2, min(args.steps, 5))
         dt, nbytes = e2e_form(m, torch, wl, w_host, "fp64", k, 1)

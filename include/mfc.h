@@ -81,7 +81,7 @@ mfc_status mfc_init(mfc_ctx** out, int nx, int ny, int nz, const double lo[3], c
  *   "sensor_tau" learned form: the discontinuity sensor trips (WENO5-JS
  *                weights are used) where max_r b_r > tau (min_r b_r + 1e-6 s^2),
  *                b the smoothness indicators without their 4/3 factor and s the
- *                stencil scale; default 1e3, range [1, 1e30];
+ *                stencil scale; default 100, range [1, 1e30];
  *   "profile"    1 / 0: time every kernel launch with CUDA events.
  * Errors: MFC_ERR_ARG for an unknown name or out-of-range value. */
 mfc_status mfc_set_param(mfc_ctx* ctx, const char* name, double value);

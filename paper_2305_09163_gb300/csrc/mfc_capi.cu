@@ -40,7 +40,7 @@ struct mfc_ctx {
     int fallback = 1;
     int seg_override = 0;
     bool profile = false;
-    double tau = 1e3;         // learned form: sensor threshold
+    double tau = 100.0;       // learned form: sensor threshold
 
     Geometry g{};
     EosConst e{};

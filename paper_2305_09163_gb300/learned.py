@@ -55,7 +55,7 @@ class Samples:
         return Samples(*[torch.cat([getattr(p, f) for p in parts]) for f in ("x", "phat", "target", "smooth", "js")])
 
 
-def harvest(w_fine, n_fine, num_fluids, count, seed, weno_eps=1e-6, tau=1e3) -> Samples:
+def harvest(w_fine, n_fine, num_fluids, count, seed, weno_eps=1e-6, tau=100.0) -> Samples:
     """`count` samples from one fine primitive field (device float64 tensor)."""
     import torch
     dev = w_fine.device
@@ -85,10 +85,21 @@ def harvest_run(workload, steps, snapshots, per_snapshot, seed, precision="mixed
     return Samples.cat(parts)
 
 
-def train(samples: Samples, epochs=3, batch=65536, lr=2e-3, lam=0.05, seed=0, params=None, log=None):
-    """Adam on the harvested samples; returns (params as a device float32 tensor,
-    per-epoch mean losses)."""
+def smooth_part(samples: Samples) -> Samples:
+    """The samples where the discontinuity sensor does not trip: the only places
+    the learned weights are used."""
+    keep = samples.smooth > 0.5
+    return Samples(samples.x[keep], samples.phat[keep], samples.target[keep], samples.smooth[keep],
+                   samples.js[keep])
+
+
+def train(samples: Samples, epochs=15, batch=65536, lr=2e-3, lam=1.0, seed=0, params=None, log=None,
+          smooth_only=True):
+    """Adam on the harvested samples (by default only those where the sensor does
+    not trip); returns (params as a device float32 tensor, per-epoch mean losses)."""
     import torch
+    if smooth_only:
+        samples = smooth_part(samples)
     dev = samples.x.device
     P = torch.tensor(init_params(seed) if params is None else params, dtype=torch.float32, device=dev)
     M = torch.zeros_like(P)

@@ -51,7 +51,7 @@ def test_learned_form_steps_and_falls_back_safely(m):
     steps, and some faces take the first-order fallback or the JS weights."""
     from paper_2305_09163_gb300 import learned
     samples = learned.harvest_run(workloads.shock_bubble(64, steps=20), 20, {10, 20}, 400_000, 1)
-    P, hist = learned.train(samples, epochs=4, batch=32768)
+    P, hist = learned.train(samples, epochs=4, batch=32768, smooth_only=False, lam=0.05)
     assert hist[-1] < hist[0]
     wl = workloads.shock_bubble(48)
     s = m.Solver(wl.n, wl.lo, wl.hi, wl.bc, wl.gamma, wl.pi_inf, precision="learned", fallback=1)
@@ -83,34 +83,36 @@ def _run(m, wl, precision, t_end, params=None):
 
 
 def test_trained_network_gain_over_weno5_js(m, capsys):
-    """Train on stencils of the shock-bubble and bubble-cloud runs (2x grids),
-    then measure on a held-out bubble cloud: the face-value error against the
-    2x-resolution target must drop below WENO5-JS's; the solution-level L1
-    errors (rho, p, alpha vs the restricted 2x FP64 run) are reported."""
+    """Train on stencils of 128^3 shock-bubble and bubble-cloud runs, then measure
+    on a held-out bubble cloud (different seed): the face-value error against
+    the 2x-resolution target, and the solution-level L1 errors of rho, p and
+    alpha of a 64^3 run at t = 1e-4 s against the restricted 128^3 FP64 run.
+    The learned form (sensor threshold 100) must beat WENO5-JS at the same
+    resolution in both."""
     from paper_2305_09163_gb300 import learned
-    parts = [learned.harvest_run(workloads.shock_bubble(96, steps=40), 40, {10, 20, 30, 40}, 500_000, 1),
-             learned.harvest_run(workloads.bubble_cloud(96, steps=40, seed=230509163), 40, {10, 20, 30, 40},
-                                 500_000, 2)]
-    P, hist = learned.train(learned.Samples.cat(parts), epochs=10, batch=65536)
+    parts = [learned.harvest_run(workloads.shock_bubble(128, steps=80), 80, {20, 40, 60, 80}, 1_000_000, 1),
+             learned.harvest_run(workloads.bubble_cloud(128, steps=80, seed=230509163), 80, {20, 40, 60, 80},
+                                 1_000_000, 2)]
+    P, hist = learned.train(learned.Samples.cat(parts))
     held = learned.harvest_run(workloads.bubble_cloud(96, steps=30, seed=4242), 30, {15, 30}, 200_000, 9)
     e_net, e_js = learned.evaluate(P, held)
-    # solution level: coarse 48^3 learned and JS (mixed) against the 96^3 FP64 run
-    n = 48
+    n = 64
     fine = workloads.bubble_cloud(2 * n, seed=4242)
     coarse = workloads.bubble_cloud(n, seed=4242)
-    coarse.prims = lambda: _restrict(fine.prims())
-    t_end = 2.5e-5
+    init = _restrict(fine.prims())
+    coarse.prims = lambda: init
+    t_end = 1.0e-4
     ref = _restrict(_run(m, fine, "fp64", t_end))
     wl_ = _run(m, coarse, "learned", t_end, P.cpu().numpy())
     wj = _run(m, coarse, "mixed", t_end)
+
     def l1(w):
         rho = lambda a: a[0] + a[1]
-        return [float(np.abs(rho(w) - rho(ref)).mean() / np.abs(rho(ref)).mean()),
-                float(np.abs(w[5] - ref[5]).mean() / np.abs(ref[5]).mean()),
-                float(np.abs(w[6] - ref[6]).mean())]
+        return np.array([np.abs(rho(w) - rho(ref)).mean() / np.abs(rho(ref)).mean(),
+                         np.abs(w[5] - ref[5]).mean() / np.abs(ref[5]).mean(), np.abs(w[6] - ref[6]).mean()])
     e_l, e_j = l1(wl_), l1(wj)
     with capsys.disabled():
-        print("\nlearned gain: face MSE net %.5g vs JS %.5g (%.1f%%); solution L1 (rho, p, alpha) "
-              "learned %s vs JS %s" % (e_net, e_js, 100 * (1 - e_net / e_js), np.round(e_l, 6), np.round(e_j, 6)))
+        print("\nlearned gain: face MSE net %.5g vs JS %.5g (%.1f%% lower); solution L1 (rho, p, alpha) "
+              "learned %s vs JS %s" % (e_net, e_js, 100 * (1 - e_net / e_js), np.round(e_l, 7), np.round(e_j, 7)))
     assert e_net < e_js
-    assert all(np.isfinite(e_l))
+    assert (e_l < e_j).all(), (e_l, e_j)
