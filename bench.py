@@ -41,9 +41,9 @@ CFL = 0.3
 # Algorithmic FP64 operations of one directional sweep per cell (3D, two fluids,
 # seven equations), counted from the formulation the kernels evaluate with
 # FMA = 2 and every add, multiply, divide, square root, min and max = 1:
-#   WENO5 edges (both sides of a cell) 74 per variable x 7, HLLC 88 per face,
+#   WENO5 edges (both sides of a cell) 70 per variable x 7, HLLC 87 per face,
 #   flux difference + alpha div(u) source 18 per cell.
-FLOP_SWEEP_CELL_3D_2F = 74 * 7 + 88 + 18
+FLOP_SWEEP_CELL_3D_2F = 70 * 7 + 87 + 18
 # RK3 stage epilogue in the last sweep: 6 per variable (stages 2, 3), 4 in stage 1
 FLOP_RK_CELL_2F = 7 * (6 + 6 + 4) / 3.0
 # Nominal FP64 peak: 152 SMs x 4 FP64 FLOP/clk/SM (2 DFMA) x 2.07 GHz
@@ -59,6 +59,24 @@ BYTES_MIXED_SWEEPS_STAGE = (56 + 84 + (168 + 224 + 224) / 3.0)
 # (5x32 + 32x32 + 32x3 multiply-adds) and stencils per cell and sweep (2 edges x 7 variables).
 FLOP_MLP_STENCIL = 2 * (5 * 32 + 32 * 32 + 32 * 3)
 STENCILS_PER_CELL_SWEEP = 14
+
+
+def max_over_ranks(x: float, ws: int, device="cpu") -> float:
+    """Maximum of a per-rank scalar over all ranks (the step time of the
+    slowest replica); a no-op on one rank."""
+    if ws == 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def grind_ns(ms_per_step, ws, cells, ns, rhs_per_step=3):
+    """Whole-job grind time: the slowest rank's step time over every cell,
+    equation and RHS evaluation that all ws replicas processed in it."""
+    return ms_per_step * 1e-3 / (ws * cells * ns * rhs_per_step) * 1e9
 
 
 def _dist():
@@ -272,6 +290,103 @@ def run_reference(args, wl):
     print(json.dumps(line))
 
 
+def _l1_fields(w, ref, nf):
+    """L1 differences of density (relative), pressure (relative) and the first
+    volume fraction (absolute mean) between two primitive states."""
+    rho = lambda a: a[:nf].sum(axis=0)
+    ip = nf + 3  # 3D: pressure follows the three velocities, volume fractions follow
+    ia = ip + 1
+    return {"rho": float(np.abs(rho(w) - rho(ref)).mean() / np.abs(rho(ref)).mean()),
+            "p": float(np.abs(w[ip] - ref[ip]).mean() / np.abs(ref[ip]).mean()),
+            "alpha": float(np.abs(w[ia] - ref[ia]).mean())}
+
+
+def _run_schedule(m, torch, wl, precision, dts=None, steps=None, mlp=None, init=None):
+    """Run a workload; returns (final primitives on the host, dt list).  With
+    dts given the same time steps are replayed."""
+    s = m.Solver(wl.n, wl.lo, wl.hi, wl.bc, wl.gamma, wl.pi_inf, precision=precision, fallback=1)
+    if mlp is not None:
+        s.set_mlp(mlp)
+    s.set_state_prim(torch.from_numpy(init if init is not None else wl.prims()).cuda())
+    out = []
+    n = len(dts) if dts is not None else steps
+    for k in range(n):
+        dt = dts[k] if dts is not None else s.cfl_dt(CFL)
+        s.step(dt)
+        out.append(dt)
+    w = s.get_prims().cpu().numpy()
+    s.close()
+    torch.cuda.empty_cache()
+    return w, out
+
+
+def run_accuracy(args):
+    """Accuracy of the mixed and learned forms against the FP64 GPU path (itself
+    parity-gated against the oracle per RHS call) on the full-size workloads,
+    replaying the FP64 run's time steps; and of the learned form against a
+    2x-resolution FP64 run on a reduced bubble-cloud box."""
+    import torch
+    import paper_2305_09163_gb300 as m
+    m.build()
+    m.load()
+    mlp, training = train_learned(m, torch)
+    cases = {"1": workloads.shock_bubble(256), "2": workloads.bubble_cloud(384), "4": workloads.three_fluid(512)}
+    for key in [c.strip() for c in args.configs.split(",") if c.strip() and c.strip() in cases]:
+        wl = cases[key]
+        t0 = time.perf_counter()
+        try:
+            _accuracy_case(m, torch, wl, key, mlp, t0)
+        except Exception as exc:  # report and go on with the next workload
+            print(json.dumps({"config": key, "workload": wl.name, "error": repr(exc)}), flush=True)
+    if "3" in args.configs:
+        _accuracy_learned_2x(m, torch, mlp, training)
+
+
+def _accuracy_case(m, torch, wl, key, mlp, t0):
+    init = wl.prims()
+    ref, dts = _run_schedule(m, torch, wl, "fp64", steps=wl.steps, init=init)
+    res = {"config": key, "workload": wl.name, "steps": wl.steps, "t_end": float(sum(dts))}
+    res["mixed_vs_fp64"] = _l1_fields(_run_schedule(m, torch, wl, "mixed", dts=dts, init=init)[0], ref, wl.nf)
+    if wl.nf == 2:
+        res["learned_vs_fp64"] = _l1_fields(
+            _run_schedule(m, torch, wl, "learned", dts=dts, mlp=mlp, init=init)[0], ref, wl.nf)
+    res["seconds"] = time.perf_counter() - t0
+    print(json.dumps(res), flush=True)
+
+
+def _accuracy_learned_2x(m, torch, mlp, training):
+    # learned vs WENO5-JS at 128^3 against FP64 at 256^3 (the 768^3 reference of the
+    # 384^3 cloud is out of reach of a bench run), same physical time
+    n = 128
+    fine = workloads.bubble_cloud(2 * n)
+    coarse = workloads.bubble_cloud(n)
+    fw = fine.prims()
+    init = fw.reshape(fw.shape[0], n, 2, n, 2, n, 2).mean(axis=(2, 4, 6))
+    del fw
+    t_end = 1.0e-4
+    def run_to(wl, precision, mlp=None, init=None):
+        s = m.Solver(wl.n, wl.lo, wl.hi, wl.bc, wl.gamma, wl.pi_inf, precision=precision, fallback=1)
+        if mlp is not None:
+            s.set_mlp(mlp)
+        s.set_state_prim(torch.from_numpy(init if init is not None else wl.prims()).cuda())
+        t = 0.0
+        while t < t_end:
+            dt = min(s.cfl_dt(CFL), t_end - t)
+            s.step(dt)
+            t += dt
+        w = s.get_prims().cpu().numpy()
+        s.close()
+        return w
+    ref = run_to(fine, "fp64")
+    ref = ref.reshape(ref.shape[0], n, 2, n, 2, n, 2).mean(axis=(2, 4, 6))
+    res = {"config": "3", "workload": "bubble_cloud 128^3 vs restricted FP64 256^3", "t_end": t_end,
+           "learned_vs_2x": _l1_fields(run_to(coarse, "learned", mlp, init), ref, 2),
+           "mixed_js_vs_2x": _l1_fields(run_to(coarse, "mixed", None, init), ref, 2),
+           "fp64_js_vs_2x": _l1_fields(run_to(coarse, "fp64", None, init), ref, 2),
+           "training": training}
+    print(json.dumps(res), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -282,7 +397,13 @@ def main():
     ap.add_argument("--forms", default="fp64,mixed,learned", help="comma list of fp64,mixed,learned")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--accuracy", action="store_true",
+                    help="accuracy study of the mixed and learned forms instead of timing")
+    ap.add_argument("--configs", default="1,2,3,4", help="accuracy study: which workloads")
     args = ap.parse_args()
+    if args.accuracy:
+        run_accuracy(args)
+        return
     ws, rank, local = _dist()
     wl = workloads.shock_bubble(args.n)
 
@@ -318,16 +439,12 @@ def main():
             mlp, training = train_learned(m, torch)
         r = time_form(m, torch, wl, w_dev, form, args.steps, args.warmup, barrier,
                       sampler_gpu=local if form == "fp64" else None, mlp=mlp)
-        t = torch.tensor([r["ms_per_step"]], device="cuda")
-        if ws > 1:
-            import torch.distributed as dist
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        r["ms_max"] = float(t.item())
+        r["ms_max"] = max_over_ranks(r["ms_per_step"], ws, "cuda")
         results[form] = r
 
     fp = results["fp64"]
     ms = fp["ms_max"]
-    grind = ms * 1e-3 / (ws * cells * ns * 3) * 1e9
+    grind = grind_ns(ms, ws, cells, ns)
     flops_per_sweep_launch = (FLOP_SWEEP_CELL_3D_2F + FLOP_RK_CELL_2F / 3.0) * cells
     achieved = flops_per_sweep_launch * fp["sweep_launches"] / (fp["sweep_ms"] * 1e-3) / 1e12
 
@@ -355,7 +472,7 @@ def main():
         if r is None:
             line["forms"][form] = None
             continue
-        g = r["ms_max"] * 1e-3 / (ws * cells * ns * 3) * 1e9
+        g = grind_ns(r["ms_max"], ws, cells, ns)
         entry = {"grind": g, "unit": UNIT, "ms_per_step": r["ms_max"],
                  "cell_updates_per_s": ws * cells / (r["ms_max"] * 1e-3),
                  "speedup_vs_fp64": ms / r["ms_max"], "gpu_launches": r["launches"],
@@ -382,12 +499,8 @@ def main():
     if not args.no_e2e:
         k = max(2, min(args.steps, 5))
         dt, nbytes = e2e_form(m, torch, wl, w_host, "fp64", k, 1)
-        t = torch.tensor([dt], device="cuda")
-        if ws > 1:
-            import torch.distributed as dist
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        dt = float(t.item())
-        line["e2e"] = {"value": dt / (ws * cells * ns * 3) * 1e9, "unit": UNIT,
+        dt = max_over_ranks(dt, ws, "cuda")
+        line["e2e"] = {"value": grind_ns(dt * 1e3, ws, cells, ns), "unit": UNIT,
                        "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes, "steps": k,
                        "note": "C ABI with pinned host buffers: set_state + CFL + step + get_state per step"}
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:

@@ -8,9 +8,9 @@ w = (a_1 r_1 .. a_N r_N, u_1 .. u_d, p, a_1 .. a_{N-1}) as float64 arrays of sha
 conserved variables.
 
 The geometry follows the synthetic shock/bubble workloads used to exercise the
-method of arXiv 2305.09163 (Sec. 4 runs a "3D 2-component air/water problem";
-Sec. 5.1 a bubble cloud hit by a pressure wave; Sec. 5.2 bubbles beside a stiff
-solid).  No dataset is involved.
+method of arXiv 2305.09163 (Sec. 5 measures a 3D two-component air/water
+problem; Sec. 6.1 a bubble cloud hit by a pressure wave; Sec. 6.2 bubbles beside
+a stiff solid).  No dataset is involved.
 """
 from __future__ import annotations
 
