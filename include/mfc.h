@@ -50,8 +50,11 @@ typedef enum { MFC_BC_PERIODIC = 0, MFC_BC_TRANSMISSIVE = 1, MFC_BC_REFLECTIVE =
  *   MFC_MIXED   WENO5 and HLLC in float32; pressure recovery from total energy
  *               and the Runge-Kutta accumulation stay float64;
  *   MFC_LEARNED as MFC_MIXED, with WENO5 nonlinear weights from a small MLP
- *               (mfc_set_mlp) except where the shock/interface sensor or the
- *               positivity check trips, where WENO5-JS weights are used. */
+ *               (mfc_set_mlp) except where the shock/interface sensor trips or
+ *               the learned edge value would leave the range of the cell and
+ *               its two neighbours, where WENO5-JS weights are used; a
+ *               non-physical learned face state falls back to WENO5-JS, then
+ *               to first order. */
 typedef enum { MFC_FP64 = 0, MFC_MIXED = 1, MFC_LEARNED = 2 } mfc_precision;
 
 /* Create a context (Sec. 3.1: uniform structured grid; Sec. 3.3: ghost-cell
@@ -78,10 +81,15 @@ mfc_status mfc_init(mfc_ctx** out, int nx, int ny, int nz, const double lo[3], c
  *   "fallback"   1 (default) / 0: first-order reconstruction (Sec. 3.2) at a
  *                face whose reconstructed state is non-physical;
  *   "segment"    cells per thread along a sweep (8..256), 0 = automatic;
+ *   "yz_kernel"  y/z sweep kernel: -1 automatic (default: stream kernel for the
+ *                FP32 paths, pencil marching for FP64), 0 marching, 1 stream;
  *   "sensor_tau" learned form: the discontinuity sensor trips (WENO5-JS
  *                weights are used) where max_r b_r > tau (min_r b_r + 1e-6 s^2),
  *                b the smoothness indicators without their 4/3 factor and s the
- *                stencil scale; default 100, range [1, 1e30];
+ *                stencil scale; default 30, range [1, 1e30];
+ *   "learned_bound" learned form: 1 (default) / 0: keep a learned edge value
+ *                only inside the range of the cell and its two neighbours
+ *                (WENO5-JS value otherwise);
  *   "profile"    1 / 0: time every kernel launch with CUDA events.
  * Errors: MFC_ERR_ARG for an unknown name or out-of-range value. */
 mfc_status mfc_set_param(mfc_ctx* ctx, const char* name, double value);

@@ -40,7 +40,9 @@ struct mfc_ctx {
     int fallback = 1;
     int seg_override = 0;
     bool profile = false;
-    double tau = 100.0;       // learned form: sensor threshold
+    double tau = 30.0;        // learned form: sensor threshold
+    int yz_stream = -1;       // y/z sweep kernel: -1 automatic, 0 marching, 1 stream
+    int bound = 1;            // learned form: range safeguard
 
     Geometry g{};
     EosConst e{};
@@ -192,6 +194,10 @@ SweepArgs base_sweep(const mfc_ctx* c) {
     a.fallback_count = c->d_fallback;
     a.mlp = c->mlp;
     a.tau = (float)c->tau;
+    // FP32 paths use the y/z stream kernel; the FP64 path marches pencils so
+    // consecutive cells share their stencil differences (fewer FP64 instructions)
+    a.yz_stream = c->yz_stream >= 0 ? c->yz_stream : (is_f32(c) ? 1 : 0);
+    a.bound = c->bound;
     return a;
 }
 
@@ -363,6 +369,12 @@ mfc_status mfc_set_param(mfc_ctx* c, const char* name, double value) {
     } else if (!strcmp(name, "segment")) {
         if (!(value == 0.0 || (value >= 8 && value <= 256))) return fail(c, MFC_ERR_ARG, "segment out of range");
         c->seg_override = (int)value;
+    } else if (!strcmp(name, "yz_kernel")) {
+        if (value != -1.0 && value != 0.0 && value != 1.0) return fail(c, MFC_ERR_ARG, "yz_kernel must be -1, 0 or 1");
+        c->yz_stream = (int)value;
+    } else if (!strcmp(name, "learned_bound")) {
+        if (value != 0.0 && value != 1.0) return fail(c, MFC_ERR_ARG, "learned_bound must be 0 or 1");
+        c->bound = (int)value;
     } else if (!strcmp(name, "sensor_tau")) {
         if (!(value >= 1.0 && value <= 1e30)) return fail(c, MFC_ERR_ARG, "sensor_tau must lie in [1, 1e30]");
         c->tau = value;

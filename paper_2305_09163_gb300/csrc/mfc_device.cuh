@@ -67,6 +67,8 @@ struct SweepArgs {
     unsigned long long* fallback_count;  // optional counter of fallback faces
     const float* mlp;       // learned form: network parameters (device)
     float tau;              // learned form: discontinuity-sensor threshold
+    int yz_stream;          // y/z sweeps: 1 = stream kernel, 0 = pencil marching
+    int bound;              // learned form: range safeguard on learned edge values
 };
 
 struct PrimArgs {
@@ -363,8 +365,9 @@ __device__ __forceinline__ void face_flux(const SweepArgs& a, const EosR<Real>& 
 // tensor cores (16 stencils per tile) and each lane combines its candidates
 // with the returned weights.  WENO5-JS weights are kept where the
 // discontinuity sensor trips (max_r b_r > tau (min_r b_r + 1e-6 s^2), b the
-// smoothness indicators without their 4/3 factor) or the stencil is flat to
-// FP32 resolution (s <= 1e-7 |v_c|).  All 32 lanes must call these functions.
+// smoothness indicators without their 4/3 factor), where the stencil is flat
+// to FP32 resolution (s <= 1e-7 |v_c|), and where the learned edge value would
+// leave the range of cells c-1, c, c+1.  All 32 lanes must call these functions.
 // ---------------------------------------------------------------------------
 template <int NS> struct LearnSmem {
     uint32_t x[NS][32][4];   // BF16 inputs, columns 0..4 used
@@ -402,7 +405,8 @@ __device__ __forceinline__ void learned_side(const MlpWeights& W, LearnSmem<NS>&
 // learned form (eR, eL; equal to the JS values where the sensor trips).
 template <int NS>
 __device__ __forceinline__ void learned_cell_edges(const float (&vc)[NS], const float (&D)[NS][4], float eps34,
-                                                   float tau, const MlpWeights& W, LearnSmem<NS>& sm, int lane,
+                                                   float tau, bool bound, const MlpWeights& W, LearnSmem<NS>& sm,
+                                                   int lane,
                                                    float (&eRjs)[NS], float (&eLjs)[NS], float (&eR)[NS],
                                                    float (&eL)[NS]) {
     bool usejs[NS];
@@ -435,8 +439,10 @@ __device__ __forceinline__ void learned_cell_edges(const float (&vc)[NS], const 
         const float p1 = fmaf(1.f / 6.f, d[1], (1.f / 3.f) * d[2]);
         const float p2 = fmaf(2.f / 3.f, d[2], (-1.f / 6.f) * d[3]);
         const float* om = sm.om[v][lane];
-        const float el = vc[v] + fmaf(om[0], p0, fmaf(om[1], p1, om[2] * p2));
-        eL[v] = usejs[v] ? eLjs[v] : el;
+        const float il = fmaf(om[0], p0, fmaf(om[1], p1, om[2] * p2));
+        // accept a learned value only inside the range of cells c-1, c, c+1
+        const float lo = fminf(0.f, fminf(-d[1], d[2])), hi = fmaxf(0.f, fmaxf(-d[1], d[2]));
+        eL[v] = (usejs[v] || (bound && (il < lo || il > hi))) ? eLjs[v] : vc[v] + il;
         // reversed stencil for the edge at c-1/2
         const float is = inv_s[v];
         const float xm2 = -(d[0] + d[1]), xm1 = -d[1], xp1 = d[2], xp2 = d[2] + d[3];
@@ -453,8 +459,9 @@ __device__ __forceinline__ void learned_cell_edges(const float (&vc)[NS], const 
         const float m1 = fmaf(-1.f / 6.f, d[2], (-1.f / 3.f) * d[1]);
         const float m2 = fmaf(-2.f / 3.f, d[1], (1.f / 6.f) * d[0]);
         const float* om = sm.om[v][lane];
-        const float er = vc[v] + fmaf(om[0], m0, fmaf(om[1], m1, om[2] * m2));
-        eR[v] = usejs[v] ? eRjs[v] : er;
+        const float ir = fmaf(om[0], m0, fmaf(om[1], m1, om[2] * m2));
+        const float lo = fminf(0.f, fminf(-d[1], d[2])), hi = fmaxf(0.f, fmaxf(-d[1], d[2]));
+        eR[v] = (usejs[v] || (bound && (ir < lo || ir > hi))) ? eRjs[v] : vc[v] + ir;
     }
 }
 
@@ -612,7 +619,7 @@ __global__ void __launch_bounds__(128) sweep_kernel(const SweepArgs a) {
     for (int c = s0 - 1; c <= s1; ++c) {
         Real eR[NS], eL[NS], eRJ[NS], eLJ[NS];
         if constexpr (LEARNED) {
-            learned_cell_edges<NS>(vc, D, eps34, a.tau, W, *lsm, lane, eRJ, eLJ, eR, eL);
+            learned_cell_edges<NS>(vc, D, eps34, a.tau, a.bound != 0, W, *lsm, lane, eRJ, eLJ, eR, eL);
         } else {
 #pragma unroll
             for (int v = 0; v < NS; ++v) weno5_edges(vc[v], D[v], eps34, eR[v], eL[v]);
@@ -732,7 +739,7 @@ __global__ void __launch_bounds__(kStreamThreads) sweep_x_stream_kernel(const Sw
             }
         }
         if constexpr (LEARNED) {
-            learned_cell_edges<NS>(vcv, Dv, eps34, a.tau, W, *lsm, t & 31, eRJ, eLJ, eR, eL);
+            learned_cell_edges<NS>(vcv, Dv, eps34, a.tau, a.bound != 0, W, *lsm, t & 31, eRJ, eLJ, eR, eL);
         } else if (live) {
 #pragma unroll
             for (int q = 0; q < NS; ++q) weno5_edges(vcv[q], Dv[q], eps34, eR[q], eL[q]);
@@ -783,6 +790,139 @@ __global__ void __launch_bounds__(kStreamThreads) sweep_x_stream_kernel(const Sw
                 sh_F[q][0] = sh_F[q][kStreamThreads];
             }
             sh_F[NS][0] = sh_F[NS][kStreamThreads];
+        }
+        __syncthreads();
+    }
+}
+
+// ---------------------------------------------------------------------------
+// y or z sweep as a coalesced stream (FP32 paths).  A CTA of 4 warps covers 32
+// consecutive x (lanes) of one pencil segment s0..s1-1 along DIR and walks it
+// in chunks of 4 edge cells, one per warp: warp r of a chunk reconstructs the
+// edges of cell c = base + r from its five-cell stencil (loaded straight from
+// global memory; the chunk's rows overlap in L1), forms the face c-1/2 with the
+// left-side value of the previous row (shared memory, or the carry from the
+// previous chunk) and finishes cell c-1.  Unlike the marching kernel no
+// per-thread window is kept, so more warps stay resident to hide load and
+// tensor-core latency.
+// ---------------------------------------------------------------------------
+constexpr int kRowsPerChunk = 4;
+
+template <typename Real, int NF, int NDIM, int DIR, bool LEARNED = false>
+__global__ void __launch_bounds__(32 * kRowsPerChunk) sweep_yz_stream_kernel(const SweepArgs a) {
+    static_assert(DIR == 1 || DIR == 2, "y or z");
+    static_assert(!LEARNED || sizeof(Real) == 4, "the learned form runs in FP32");
+    using Lay = Layout<NF, NDIM>;
+    constexpr int NS = Lay::NS, IM = Lay::IM;
+    constexpr int NJ = LEARNED ? NS : 1;
+    constexpr int T1 = 0;
+    constexpr int T2 = (DIR == 2) ? 1 : 2;
+    __shared__ Real sh_eL[NS][kRowsPerChunk + 1][32];
+    __shared__ Real sh_eLJ[NJ][kRowsPerChunk + 1][32];
+    __shared__ Real sh_F[NS + 1][kRowsPerChunk + 1][32];
+    const Real* __restrict__ w = static_cast<const Real*>(a.w);
+    const int lane = threadIdx.x & 31, row = threadIdx.x >> 5;
+    const int n1 = a.g.n[T1], n2 = a.g.n[T2], nd = a.g.n[DIR];
+    const int nxc = (n1 + 31) >> 5;
+    const long long bid = blockIdx.x;
+    const int xc = (int)(bid % nxc);
+    const long long rest = bid / nxc;
+    const int sg = (int)(rest % a.nseg);
+    const int t2 = (int)(rest / a.nseg);
+    if (t2 >= n2) return;  // whole CTA
+    const bool active = xc * 32 + lane < n1;
+    const int t1 = active ? xc * 32 + lane : n1 - 1;
+    const long long sd = stride_of(a.g, DIR);
+    const long long basei = (long long)t1 * stride_of(a.g, T1) + (long long)t2 * stride_of(a.g, T2);
+    const long long nc = a.g.ncell;
+    const int s0 = sg * a.seg;
+    const int s1 = min(s0 + a.seg, nd);
+    const int bclo = a.g.bc_lo[DIR], bchi = a.g.bc_hi[DIR];
+    const Real eps34 = (Real)(0.75 * a.eps);
+    const EosR<Real> e(a.e);
+    const Real inv_dx = (Real)a.g.inv_dx[DIR];
+    MlpWeights W;
+    LearnSmem<NS>* lsm = nullptr;
+    if constexpr (LEARNED) {
+        __shared__ LearnSmem<NS> lbuf[kRowsPerChunk];
+        lsm = &lbuf[row];
+        mlp_load_weights(a.mlp, W, lane);
+    }
+
+    for (int base = s0 - 1; base <= s1; base += kRowsPerChunk) {
+        const int c = base + row;       // edge cell of this warp (warp-uniform)
+        const bool live = c <= s1;
+        Real cell[NS], cm1[NS], eL[NS], eR[NS], eLJ[NS], eRJ[NS];
+        if (live) {
+            Real v[5][NS];
+#pragma unroll
+            for (int k = 0; k < 5; ++k) {
+                bool flip = false;
+                const int m = ghost_map(c + k - 2, nd, bclo, bchi, &flip);
+                const long long idx = basei + (long long)m * sd;
+#pragma unroll
+                for (int q = 0; q < NS; ++q) v[k][q] = __ldg(w + q * nc + idx);
+                if (flip) v[k][IM + DIR] = -v[k][IM + DIR];
+            }
+            Real Dv[NS][4];
+#pragma unroll
+            for (int q = 0; q < NS; ++q) {
+                Dv[q][0] = v[1][q] - v[0][q];
+                Dv[q][1] = v[2][q] - v[1][q];
+                Dv[q][2] = v[3][q] - v[2][q];
+                Dv[q][3] = v[4][q] - v[3][q];
+                cell[q] = v[2][q];
+                cm1[q] = v[1][q];
+            }
+            if constexpr (LEARNED) {
+                learned_cell_edges<NS>(cell, Dv, eps34, a.tau, a.bound != 0, W, *lsm, lane, eRJ, eLJ, eR, eL);
+            } else {
+#pragma unroll
+                for (int q = 0; q < NS; ++q) weno5_edges(cell[q], Dv[q], eps34, eR[q], eL[q]);
+            }
+#pragma unroll
+            for (int q = 0; q < NS; ++q) {
+                sh_eL[q][row + 1][lane] = eL[q];
+                if constexpr (LEARNED) sh_eLJ[q][row + 1][lane] = eLJ[q];
+            }
+        }
+        __syncthreads();
+        Real F[NS], ut = 0;
+        const bool has_face = live && c >= s0;
+        if (has_face) {
+            Real lft[NS];
+#pragma unroll
+            for (int q = 0; q < NS; ++q) lft[q] = sh_eL[q][row][lane];
+            if constexpr (LEARNED) {
+                Real lftJ[NS];
+#pragma unroll
+                for (int q = 0; q < NS; ++q) lftJ[q] = sh_eLJ[q][row][lane];
+                face_flux_learned<NF, NDIM, DIR>(a, e, lft, eR, lftJ, eRJ, cm1, cell, F, ut);
+            } else {
+                face_flux<Real, NF, NDIM, DIR>(a, e, lft, eR, cm1, cell, F, ut);
+            }
+#pragma unroll
+            for (int q = 0; q < NS; ++q) sh_F[q][row + 1][lane] = F[q];
+            sh_F[NS][row + 1][lane] = ut;
+        }
+        __syncthreads();
+        if (has_face && c >= s0 + 1 && active) {
+            Real Fm[NS];
+#pragma unroll
+            for (int q = 0; q < NS; ++q) Fm[q] = sh_F[q][row][lane];
+            finish_cell<Real, NF, NDIM>(a, basei + (long long)(c - 1) * sd, Fm, F, sh_F[NS][row][lane], ut, cm1,
+                                        inv_dx);
+        }
+        __syncthreads();
+        // carry the last row of the chunk into row 0
+        if (row == kRowsPerChunk - 1) {
+#pragma unroll
+            for (int q = 0; q < NS; ++q) {
+                sh_eL[q][0][lane] = sh_eL[q][kRowsPerChunk][lane];
+                if constexpr (LEARNED) sh_eLJ[q][0][lane] = sh_eLJ[q][kRowsPerChunk][lane];
+                sh_F[q][0][lane] = sh_F[q][kRowsPerChunk][lane];
+            }
+            sh_F[NS][0][lane] = sh_F[NS][kRowsPerChunk][lane];
         }
         __syncthreads();
     }

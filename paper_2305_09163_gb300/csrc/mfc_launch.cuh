@@ -28,6 +28,17 @@ cudaError_t launch_sweep(SweepArgs a, int ndim, int dir, cudaStream_t s) {
         return cudaGetLastError();
     }
     const int t1 = (dir == 0) ? 1 : 0, t2 = (dir == 2) ? 1 : 2;
+    if (a.yz_stream) {
+        // y/z stream kernel, one CTA per 32 x-lanes of a segment
+        const unsigned blocks = (unsigned)((long long)((a.g.n[t1] + 31) / 32) * a.nseg * a.g.n[t2]);
+        switch (ndim * 4 + dir) {
+            case 9: sweep_yz_stream_kernel<Real, NF, 2, 1, LEARNED><<<blocks, 32 * kRowsPerChunk, 0, s>>>(a); break;
+            case 13: sweep_yz_stream_kernel<Real, NF, 3, 1, LEARNED><<<blocks, 32 * kRowsPerChunk, 0, s>>>(a); break;
+            case 14: sweep_yz_stream_kernel<Real, NF, 3, 2, LEARNED><<<blocks, 32 * kRowsPerChunk, 0, s>>>(a); break;
+            default: return cudaErrorInvalidValue;
+        }
+        return cudaGetLastError();
+    }
     const long long warps = (long long)((a.g.n[t1] + 31) / 32) * a.nseg * a.g.n[t2];
     const unsigned blocks = (unsigned)((warps * 32 + kSweepThreads - 1) / kSweepThreads);
     switch (ndim * 4 + dir) {

@@ -83,16 +83,17 @@ def test_rhs_parity_fp64_mixed_bcs(mfc):
     assert rhs_error(pb, q, R_gpu, R_cpu, fmax).max() <= TOL_FP64
 
 
-@pytest.mark.parametrize("seg", [8, 16, 64])
-def test_rhs_parity_independent_of_segment_length(mfc, seg):
-    """Several pencil segments per direction with a ragged last segment."""
+@pytest.mark.parametrize("seg,yz", [(8, 0), (16, 0), (64, 0), (8, 1), (64, 1)])
+def test_rhs_parity_independent_of_segment_length(mfc, seg, yz):
+    """Several pencil segments per direction with a ragged last segment, with
+    either y/z kernel (pencil marching or the stream kernel)."""
     n = (70, 33, 21)
     gam, pin = workloads.fluids(2)
     pb = _problem(n, (1,) * 6, gam, pin, True)
     w = workloads.random_prims(n, 2, seed=7)
     q = oracle.cons_from_prims(pb, w)
     R_cpu, fmax, _ = oracle.rhs(pb, q, return_info=True)
-    s = _solver(mfc, pb, segment=seg)
+    s = _solver(mfc, pb, segment=seg, yz_kernel=yz)
     s.set_state_prim(torch.from_numpy(w).cuda())
     R_gpu = s.rhs().cpu().numpy()
     assert rhs_error(pb, q, R_gpu, R_cpu, fmax).max() <= TOL_FP64
