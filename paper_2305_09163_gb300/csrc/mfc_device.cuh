@@ -704,12 +704,30 @@ __global__ void __launch_bounds__(kStreamThreads) sweep_x_stream_kernel(const Sw
         mlp_load_weights(a.mlp, W, t & 31);
     }
 
+    // (row, column) of this lane's slot: one 64-bit division when the slot first
+    // becomes valid, then advanced by 128 slots per chunk with additions (a
+    // 64-bit division per chunk would run on the FP64 pipe)
+    long long srow = 0;
+    int scol = 0;  // slot index within its row, 0..n+1
+    bool placed = false;
     for (long long base = own0 - 2; base < own1; base += kStreamThreads) {
         const long long s = base + t;
+        if (s >= 0 && !placed) {
+            srow = s / rowlen;
+            scol = (int)(s - srow * rowlen);
+            placed = true;
+        }
         const bool live = (s >= 0) && (s < own1);
-        const long long row = live ? s / rowlen : 0;
-        const int c = live ? (int)(s - row * rowlen) - 1 : -1;
+        const long long row = srow;
+        const int c = live ? scol - 1 : -1;
         const long long rowoff = row * n;
+        if (placed) {
+            scol += kStreamThreads;
+            while (scol >= rowlen) {
+                scol -= (int)rowlen;
+                ++srow;
+            }
+        }
         Real cell[NS], cm1[NS], eL[NS], eR[NS], eLJ[NS], eRJ[NS];
         Real vcv[NS], Dv[NS][4];
 #pragma unroll
@@ -799,12 +817,13 @@ __global__ void __launch_bounds__(kStreamThreads) sweep_x_stream_kernel(const Sw
 // y or z sweep as a coalesced stream (FP32 paths).  A CTA of 4 warps covers 32
 // consecutive x (lanes) of one pencil segment s0..s1-1 along DIR and walks it
 // in chunks of 4 edge cells, one per warp: warp r of a chunk reconstructs the
-// edges of cell c = base + r from its five-cell stencil (loaded straight from
-// global memory; the chunk's rows overlap in L1), forms the face c-1/2 with the
-// left-side value of the previous row (shared memory, or the carry from the
-// previous chunk) and finishes cell c-1.  Unlike the marching kernel no
-// per-thread window is kept, so more warps stay resident to hide load and
-// tensor-core latency.
+// edges of cell c = base + r from its five-cell stencil, read from a shared
+// ring of the 8 rows base-2..base+5 (each warp loads one new row per chunk,
+// prefetched into registers during the previous chunk's arithmetic), forms the
+// face c-1/2 with the left-side value of the previous row (shared memory, or
+// the carry from the previous chunk) and finishes cell c-1.  Unlike the
+// marching kernel no per-thread window is kept, so more warps stay resident to
+// hide load and tensor-core latency.
 // ---------------------------------------------------------------------------
 constexpr int kRowsPerChunk = 4;
 
@@ -817,6 +836,8 @@ __global__ void __launch_bounds__(32 * kRowsPerChunk) sweep_yz_stream_kernel(con
     constexpr int NJ = LEARNED ? NS : 1;
     constexpr int T1 = 0;
     constexpr int T2 = (DIR == 2) ? 1 : 2;
+    constexpr int RING = 2 * kRowsPerChunk;  // rows base-2 .. base+5 of a chunk
+    __shared__ Real ring[RING][NS][32];
     __shared__ Real sh_eL[NS][kRowsPerChunk + 1][32];
     __shared__ Real sh_eLJ[NJ][kRowsPerChunk + 1][32];
     __shared__ Real sh_F[NS + 1][kRowsPerChunk + 1][32];
@@ -848,31 +869,51 @@ __global__ void __launch_bounds__(32 * kRowsPerChunk) sweep_yz_stream_kernel(con
         lsm = &lbuf[row];
         mlp_load_weights(a.mlp, W, lane);
     }
+    // cell i along DIR (ghost-mapped) of this lane's column
+    auto load = [&](int i, Real* out) {
+        bool flip = false;
+        const int m = ghost_map(i, nd, bclo, bchi, &flip);
+        const long long idx = basei + (long long)m * sd;
+#pragma unroll
+        for (int q = 0; q < NS; ++q) out[q] = __ldg(w + q * nc + idx);
+        if (flip) out[IM + DIR] = -out[IM + DIR];
+    };
+    auto slot = [](int i) { return ((i % RING) + RING) % RING; };
+    // prologue: rows s0-3 .. s0+4 (cells base-2 .. base+5 of the first chunk)
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        const int i = s0 - 3 + row + kRowsPerChunk * h;
+        if (i <= s1 + 2) {
+            Real v[NS];
+            load(i, v);
+#pragma unroll
+            for (int q = 0; q < NS; ++q) ring[slot(i)][q][lane] = v[q];
+        }
+    }
+    __syncthreads();
 
     for (int base = s0 - 1; base <= s1; base += kRowsPerChunk) {
+        // prefetch the row the next chunk adds (cell base+6+row) while this one computes
+        const int inext = base + RING - 2 + row;
+        const bool pf = inext <= s1 + 2;
+        Real nxt[NS];
+        if (pf) load(inext, nxt);
         const int c = base + row;       // edge cell of this warp (warp-uniform)
         const bool live = c <= s1;
         Real cell[NS], cm1[NS], eL[NS], eR[NS], eLJ[NS], eRJ[NS];
         if (live) {
-            Real v[5][NS];
-#pragma unroll
-            for (int k = 0; k < 5; ++k) {
-                bool flip = false;
-                const int m = ghost_map(c + k - 2, nd, bclo, bchi, &flip);
-                const long long idx = basei + (long long)m * sd;
-#pragma unroll
-                for (int q = 0; q < NS; ++q) v[k][q] = __ldg(w + q * nc + idx);
-                if (flip) v[k][IM + DIR] = -v[k][IM + DIR];
-            }
             Real Dv[NS][4];
 #pragma unroll
             for (int q = 0; q < NS; ++q) {
-                Dv[q][0] = v[1][q] - v[0][q];
-                Dv[q][1] = v[2][q] - v[1][q];
-                Dv[q][2] = v[3][q] - v[2][q];
-                Dv[q][3] = v[4][q] - v[3][q];
-                cell[q] = v[2][q];
-                cm1[q] = v[1][q];
+                const Real v0 = ring[slot(c - 2)][q][lane], v1 = ring[slot(c - 1)][q][lane];
+                const Real v2 = ring[slot(c)][q][lane], v3 = ring[slot(c + 1)][q][lane];
+                const Real v4 = ring[slot(c + 2)][q][lane];
+                Dv[q][0] = v1 - v0;
+                Dv[q][1] = v2 - v1;
+                Dv[q][2] = v3 - v2;
+                Dv[q][3] = v4 - v3;
+                cell[q] = v2;
+                cm1[q] = v1;
             }
             if constexpr (LEARNED) {
                 learned_cell_edges<NS>(cell, Dv, eps34, a.tau, a.bound != 0, W, *lsm, lane, eRJ, eLJ, eR, eL);
@@ -887,6 +928,11 @@ __global__ void __launch_bounds__(32 * kRowsPerChunk) sweep_yz_stream_kernel(con
             }
         }
         __syncthreads();
+        // rows base-2 .. base+1 are no longer needed: the prefetched rows replace them
+        if (pf) {
+#pragma unroll
+            for (int q = 0; q < NS; ++q) ring[slot(inext)][q][lane] = nxt[q];
+        }
         Real F[NS], ut = 0;
         const bool has_face = live && c >= s0;
         if (has_face) {
