@@ -442,7 +442,8 @@ def main():
         r["ms_max"] = max_over_ranks(r["ms_per_step"], ws, "cuda")
         results[form] = r
 
-    fp = results["fp64"]
+    head = "fp64" if "fp64" in results else forms[0]
+    fp = results[head]
     ms = fp["ms_max"]
     grind = grind_ns(ms, ws, cells, ns)
     flops_per_sweep_launch = (FLOP_SWEEP_CELL_3D_2F + FLOP_RK_CELL_2F / 3.0) * cells
@@ -467,7 +468,7 @@ def main():
         "forms": {},
     }
     for form, r in results.items():
-        if form == "fp64":
+        if form == head:
             continue
         if r is None:
             line["forms"][form] = None
