@@ -359,46 +359,63 @@ __device__ __forceinline__ void face_flux(const SweepArgs& a, const EosR<Real>& 
 // ---------------------------------------------------------------------------
 // Learned form (the paper has no learned part; the network replaces the
 // WENO5-JS nonlinear weights of Sec. 3.2).  Per cell and variable the FP32
-// WENO5 pieces are formed as in the mixed path; the five-cell stencil,
-// normalised by s = max_k |v_{c+k} - v_c|, goes to shared memory as BF16; the
-// warp then evaluates the network for its 32 cells x NS variables on the
-// tensor cores (16 stencils per tile) and each lane combines its candidates
-// with the returned weights.  WENO5-JS weights are kept where the
-// discontinuity sensor trips (max_r b_r > tau (min_r b_r + 1e-6 s^2), b the
-// smoothness indicators without their 4/3 factor), where the stencil is flat
-// to FP32 resolution (s <= 1e-7 |v_c|), and where the learned edge value would
-// leave the range of cells c-1, c, c+1.  All 32 lanes must call these functions.
+// WENO5 pieces are formed as in the mixed path.  WENO5-JS weights are kept
+// where the discontinuity sensor trips (max_r b_r > tau (min_r b_r + 1e-6 s^2),
+// b the smoothness indicators without their 4/3 factor), where the stencil is
+// flat to FP32 resolution (s <= 1e-7 |v_c|), and where the learned edge value
+// would leave the range of cells c-1, c, c+1.  Only the stencils whose learned
+// value can be used go to the network: the warp packs them (ballot and prefix
+// count) into shared memory as BF16 rows of the five normalised differences,
+// one row per edge, evaluates the network on the tensor cores 16 rows per
+// tile, and each lane turns its rows' logits into weights and edge values.
+// All 32 lanes must call these functions.
 // ---------------------------------------------------------------------------
 template <int NS> struct LearnSmem {
-    uint32_t x[NS][32][4];   // BF16 inputs, columns 0..4 used
-    float om[NS][32][3];     // network weights of each stencil
+    // one row per network evaluation (both edges of up to 32 cells x NS
+    // variables): BF16 inputs in columns 0..4, then overwritten by the logits
+    uint4 row[2 * NS * 32];
 };
 
-// Network over the NS x 32 stencils staged in sm.x (one side of the cells).
+// Network over rows 0..nrows-1 of sm; each row's inputs are replaced by its
+// three logits (FP32, words 0..2).
 template <int NS>
-__device__ __forceinline__ void learned_side(const MlpWeights& W, LearnSmem<NS>& sm, int lane) {
+__device__ __forceinline__ void learned_logits(const MlpWeights& W, LearnSmem<NS>& sm, int nrows, int lane) {
     const int g = lane >> 2, t = lane & 3;
+    const int nt = (nrows + 15) >> 4;
+    const uint32_t* rw = reinterpret_cast<const uint32_t*>(sm.row);
+    float* rf = reinterpret_cast<float*>(sm.row);
     __syncwarp();
+    // groups of four independent tiles so their tensor-core chains overlap
 #pragma unroll 1
-    for (int v = 0; v < NS; ++v) {
+    for (int t0 = 0; t0 < nt; t0 += 4) {
+        float z[4][4];
 #pragma unroll
-        for (int h = 0; h < 2; ++h) {
-            const uint32_t a_in[2] = {sm.x[v][16 * h + g][t], sm.x[v][16 * h + g + 8][t]};
-            float c1[4][4], c2[4][4], z[4];
-            uint32_t a1[2][4], a2[2][4];
-            mlp_tile_forward(W, a_in, c1, a1, c2, a2, z);
-            float og[3], og8[3];
-            mlp_softmax_rows(z, og, og8);
-            if (t == 0) {
+        for (int u = 0; u < 4; ++u) {
+            if (t0 + u < nt) {
+                const int r0 = 16 * (t0 + u);
+                const uint32_t a_in[2] = {rw[4 * (r0 + g) + t], rw[4 * (r0 + g + 8) + t]};
+                mlp_tile_logits(W, a_in, z[u]);
+            }
+        }
 #pragma unroll
-                for (int q = 0; q < 3; ++q) {
-                    sm.om[v][16 * h + g][q] = og[q];
-                    sm.om[v][16 * h + g + 8][q] = og8[q];
-                }
+        for (int u = 0; u < 4; ++u) {
+            if (t0 + u < nt && t < 2) {
+                const int r0 = 16 * (t0 + u);
+                *reinterpret_cast<float2*>(rf + 4 * (r0 + g) + 2 * t) = make_float2(z[u][0], z[u][1]);
+                *reinterpret_cast<float2*>(rf + 4 * (r0 + g + 8) + 2 * t) = make_float2(z[u][2], z[u][3]);
             }
         }
     }
     __syncwarp();
+}
+
+// Increment sum_r omega_r d_r with omega the softmax of the logits in words
+// 0..2 of a row.
+__device__ __forceinline__ float learned_increment(const uint4& row, float d0, float d1, float d2) {
+    const float z0 = __uint_as_float(row.x), z1 = __uint_as_float(row.y), z2 = __uint_as_float(row.z);
+    const float m = fmaxf(z0, fmaxf(z1, z2));
+    const float e0 = __expf(z0 - m), e1 = __expf(z1 - m), e2 = __expf(z2 - m);
+    return __fdividef(fmaf(e0, d0, fmaf(e1, d1, e2 * d2)), e0 + e1 + e2);
 }
 
 // Edge values of one cell for all NS variables: WENO5-JS (eRjs, eLjs) and the
@@ -409,8 +426,10 @@ __device__ __forceinline__ void learned_cell_edges(const float (&vc)[NS], const 
                                                    int lane,
                                                    float (&eRjs)[NS], float (&eLjs)[NS], float (&eR)[NS],
                                                    float (&eL)[NS]) {
-    bool usejs[NS];
-    float inv_s[NS];
+    const unsigned below = (1u << lane) - 1u;
+    unsigned need[NS];
+    int nrows = 0;
+    __syncwarp();   // the previous call's logits are read before rows are rewritten
 #pragma unroll
     for (int v = 0; v < NS; ++v) {
         const float* d = D[v];
@@ -422,46 +441,44 @@ __device__ __forceinline__ void learned_cell_edges(const float (&vc)[NS], const 
         const float xm2 = -(d[0] + d[1]), xm1 = -d[1], xp1 = d[2], xp2 = d[2] + d[3];
         const float sc = fmaxf(fmaxf(fabsf(xm2), fabsf(xm1)), fmaxf(fabsf(xp1), fabsf(xp2)));
         const float bmax = fmaxf(b0, fmaxf(b1, b2)), bmin = fminf(b0, fminf(b1, b2));
-        usejs[v] = !(sc > 1e-7f * fabsf(vc[v])) || (bmax > tau * fmaf(1e-6f * sc, sc, bmin));
-        inv_s[v] = __fdividef(1.0f, sc + 1e-30f);
-        const float is = inv_s[v];
-        sm.x[v][lane][0] = pack_bf16(xm2 * is, xm1 * is);
-        sm.x[v][lane][1] = pack_bf16(0.f, xp1 * is);
-        sm.x[v][lane][2] = pack_bf16(xp2 * is, 0.f);
-        sm.x[v][lane][3] = 0u;
+        const bool usejs = !(sc > 1e-7f * fabsf(vc[v])) || (bmax > tau * fmaf(1e-6f * sc, sc, bmin));
+        need[v] = __ballot_sync(0xffffffffu, !usejs);
+        if (!usejs) {
+            const float is = __fdividef(1.0f, sc + 1e-30f);
+            const int r = nrows + 2 * __popc(need[v] & below);
+            // edge at c+1/2: stencil c-2..c+2; edge at c-1/2: the mirrored stencil
+            sm.row[r] = make_uint4(pack_bf16(xm2 * is, xm1 * is), pack_bf16(0.f, xp1 * is),
+                                   pack_bf16(xp2 * is, 0.f), 0u);
+            sm.row[r + 1] = make_uint4(pack_bf16(xp2 * is, xp1 * is), pack_bf16(0.f, xm1 * is),
+                                       pack_bf16(xm2 * is, 0.f), 0u);
+        }
+        nrows += 2 * __popc(need[v]);
     }
-    learned_side<NS>(W, sm, lane);
+    learned_logits<NS>(W, sm, nrows, lane);
+    int r = 0;
 #pragma unroll
     for (int v = 0; v < NS; ++v) {
-        const float* d = D[v];
-        // increments at c+1/2 of the stencils c-2..c, c-1..c+1, c..c+2
-        const float p0 = fmaf(5.f / 6.f, d[1], (-1.f / 3.f) * d[0]);
-        const float p1 = fmaf(1.f / 6.f, d[1], (1.f / 3.f) * d[2]);
-        const float p2 = fmaf(2.f / 3.f, d[2], (-1.f / 6.f) * d[3]);
-        const float* om = sm.om[v][lane];
-        const float il = fmaf(om[0], p0, fmaf(om[1], p1, om[2] * p2));
-        // accept a learned value only inside the range of cells c-1, c, c+1
-        const float lo = fminf(0.f, fminf(-d[1], d[2])), hi = fmaxf(0.f, fmaxf(-d[1], d[2]));
-        eL[v] = (usejs[v] || (bound && (il < lo || il > hi))) ? eLjs[v] : vc[v] + il;
-        // reversed stencil for the edge at c-1/2
-        const float is = inv_s[v];
-        const float xm2 = -(d[0] + d[1]), xm1 = -d[1], xp1 = d[2], xp2 = d[2] + d[3];
-        sm.x[v][lane][0] = pack_bf16(xp2 * is, xp1 * is);
-        sm.x[v][lane][1] = pack_bf16(0.f, xm1 * is);
-        sm.x[v][lane][2] = pack_bf16(xm2 * is, 0.f);
-    }
-    learned_side<NS>(W, sm, lane);
-#pragma unroll
-    for (int v = 0; v < NS; ++v) {
-        const float* d = D[v];
-        // increments at c-1/2 of the stencils c..c+2, c-1..c+1, c-2..c
-        const float m0 = fmaf(-5.f / 6.f, d[2], (1.f / 3.f) * d[3]);
-        const float m1 = fmaf(-1.f / 6.f, d[2], (-1.f / 3.f) * d[1]);
-        const float m2 = fmaf(-2.f / 3.f, d[1], (1.f / 6.f) * d[0]);
-        const float* om = sm.om[v][lane];
-        const float ir = fmaf(om[0], m0, fmaf(om[1], m1, om[2] * m2));
-        const float lo = fminf(0.f, fminf(-d[1], d[2])), hi = fmaxf(0.f, fmaxf(-d[1], d[2]));
-        eR[v] = (usejs[v] || (bound && (ir < lo || ir > hi))) ? eRjs[v] : vc[v] + ir;
+        eL[v] = eLjs[v];
+        eR[v] = eRjs[v];
+        if (need[v] & (1u << lane)) {
+            const float* d = D[v];
+            const int rr = r + 2 * __popc(need[v] & below);
+            // increments at c+1/2 of the stencils c-2..c, c-1..c+1, c..c+2
+            const float p0 = fmaf(5.f / 6.f, d[1], (-1.f / 3.f) * d[0]);
+            const float p1 = fmaf(1.f / 6.f, d[1], (1.f / 3.f) * d[2]);
+            const float p2 = fmaf(2.f / 3.f, d[2], (-1.f / 6.f) * d[3]);
+            // increments at c-1/2 of the stencils c..c+2, c-1..c+1, c-2..c
+            const float m0 = fmaf(-5.f / 6.f, d[2], (1.f / 3.f) * d[3]);
+            const float m1 = fmaf(-1.f / 6.f, d[2], (-1.f / 3.f) * d[1]);
+            const float m2 = fmaf(-2.f / 3.f, d[1], (1.f / 6.f) * d[0]);
+            const float il = learned_increment(sm.row[rr], p0, p1, p2);
+            const float ir = learned_increment(sm.row[rr + 1], m0, m1, m2);
+            // accept a learned value only inside the range of cells c-1, c, c+1
+            const float lo = fminf(0.f, fminf(-d[1], d[2])), hi = fmaxf(0.f, fmaxf(-d[1], d[2]));
+            if (!(bound && (il < lo || il > hi))) eL[v] = vc[v] + il;
+            if (!(bound && (ir < lo || ir > hi))) eR[v] = vc[v] + ir;
+        }
+        r += 2 * __popc(need[v]);
     }
 }
 

@@ -57,6 +57,24 @@ __device__ __forceinline__ void mma1688(float* d, const uint32_t* a, uint32_t b)
         : "r"(a[0]), "r"(a[1]), "r"(b));
 }
 
+// D = A(16x16, row) * B(16x8, col) + C with C = (c0, c1) in both row halves:
+// a bias enters as the accumulator input, with no register copies.
+__device__ __forceinline__ void mma16816_bias(float* d, const uint32_t* a, const uint32_t* b, float c0, float c1) {
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+        "{%10,%11,%10,%11};\n"
+        : "=f"(d[0]), "=f"(d[1]), "=f"(d[2]), "=f"(d[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]), "f"(c0), "f"(c1));
+}
+
+// D = A(16x8, row) * B(8x8, col) + C, C as in mma16816_bias.
+__device__ __forceinline__ void mma1688_bias(float* d, const uint32_t* a, uint32_t b, float c0, float c1) {
+    asm volatile(
+        "mma.sync.aligned.m16n8k8.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5}, {%6}, {%7,%8,%7,%8};\n"
+        : "=f"(d[0]), "=f"(d[1]), "=f"(d[2]), "=f"(d[3])
+        : "r"(a[0]), "r"(a[1]), "r"(b), "f"(c0), "f"(c1));
+}
+
 // Per-thread B fragments of the three layers and the biases of the columns
 // this thread accumulates.  Lane = 4 g + t: a thread holds accumulator rows g,
 // g+8 and columns 2t, 2t+1 of each n8 tile.
@@ -97,12 +115,19 @@ __device__ __forceinline__ void mlp_load_weights(const float* __restrict__ P, Ml
     W.b3[1] = 2 * t + 1 < kMlpOut ? P[kOffB3 + 2 * t + 1] : 0.f;
 }
 
+// max(lo, 0), max(hi, 0) rounded to BF16 and packed, in one conversion.
+__device__ __forceinline__ uint32_t pack_bf16_relu(float lo, float hi) {
+    uint32_t r;
+    asm("cvt.rn.relu.bf16x2.f32 %0, %1, %2;" : "=r"(r) : "f"(hi), "f"(lo));
+    return r;
+}
+
 // Accumulator pair (two adjacent n8 tiles) after ReLU -> A fragment of the next layer.
 __device__ __forceinline__ void relu_to_a(const float* c0, const float* c1, uint32_t* a) {
-    a[0] = pack_bf16(fmaxf(c0[0], 0.f), fmaxf(c0[1], 0.f));
-    a[1] = pack_bf16(fmaxf(c0[2], 0.f), fmaxf(c0[3], 0.f));
-    a[2] = pack_bf16(fmaxf(c1[0], 0.f), fmaxf(c1[1], 0.f));
-    a[3] = pack_bf16(fmaxf(c1[2], 0.f), fmaxf(c1[3], 0.f));
+    a[0] = pack_bf16_relu(c0[0], c0[1]);
+    a[1] = pack_bf16_relu(c0[2], c0[3]);
+    a[2] = pack_bf16_relu(c1[0], c1[1]);
+    a[3] = pack_bf16_relu(c1[2], c1[3]);
 }
 
 // Forward pass of one 16-stencil tile.  a_in is the m16n8k8 A fragment of the
@@ -132,6 +157,26 @@ __device__ __forceinline__ void mlp_tile_forward(const MlpWeights& W, const uint
     z[0] = z[2] = W.b3[0];
     z[1] = z[3] = W.b3[1];
     mma16816(z, a2[0], W.w3[0]);
+    mma16816(z, a2[1], W.w3[1]);
+}
+
+// Logits of one 16-stencil tile for inference (same arithmetic as
+// mlp_tile_forward, without keeping the intermediate layers).
+__device__ __forceinline__ void mlp_tile_logits(const MlpWeights& W, const uint32_t* a_in, float (&z)[4]) {
+    float c[4][4];
+    uint32_t a1[2][4], a2[2][4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) mma1688_bias(c[j], a_in, W.w1[j], W.b1[j][0], W.b1[j][1]);
+    relu_to_a(c[0], c[1], a1[0]);
+    relu_to_a(c[2], c[3], a1[1]);
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        mma16816_bias(c[j], a1[0], W.w2[0][j], W.b2[j][0], W.b2[j][1]);
+        mma16816(c[j], a1[1], W.w2[1][j]);
+    }
+    relu_to_a(c[0], c[1], a2[0]);
+    relu_to_a(c[2], c[3], a2[1]);
+    mma16816_bias(z, a2[0], W.w3[0], W.b3[0], W.b3[1]);
     mma16816(z, a2[1], W.w3[1]);
 }
 
