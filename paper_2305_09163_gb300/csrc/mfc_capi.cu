@@ -13,6 +13,12 @@
 
 using namespace mfc;
 
+// The learned form's device blob: MFC_MLP_PARAMS floats, then the packed
+// per-lane fragments the sweeps load (16-byte aligned).
+constexpr size_t kMlpFragOffset = 8192;
+static_assert(sizeof(float) * MFC_MLP_PARAMS <= kMlpFragOffset, "parameters fit before the fragments");
+
+cudaError_t mfc_launch_mlp_pack(const float* P, void* frag, cudaStream_t s);
 cudaError_t mfc_launch_prims_out(const double* q, double* w, long long nc, int nf, int ndim, const EosConst& e,
                                  cudaStream_t s);
 
@@ -55,7 +61,7 @@ struct mfc_ctx {
     int* d_bad = nullptr;
     unsigned long long* d_fallback = nullptr;
     unsigned long long* h_pin = nullptr;   // pinned readback [rate, bad]
-    float* mlp = nullptr;
+    float* mlp = nullptr;         // network parameters, then (at byte kMlpFragOffset) the packed fragments
 
     bool state_set = false;
     bool w_valid = false;     // w holds the primitives of q
@@ -192,7 +198,8 @@ SweepArgs base_sweep(const mfc_ctx* c) {
     a.eps = c->eps;
     a.fallback = c->fallback;
     a.fallback_count = c->d_fallback;
-    a.mlp = c->mlp;
+    a.mlp_frag = c->mlp ? reinterpret_cast<const uint4*>(reinterpret_cast<const char*>(c->mlp) + kMlpFragOffset)
+                        : nullptr;
     a.tau = (float)c->tau;
     // FP32 paths use the y/z stream kernel; the FP64 path marches pencils so
     // consecutive cells share their stencil differences (fewer FP64 instructions)
@@ -511,7 +518,7 @@ mfc_status mfc_set_mlp(mfc_ctx* c, const float* params, int n) {
     if (!params || n != MFC_MLP_PARAMS) return fail(c, MFC_ERR_ARG, "need %d parameters", MFC_MLP_PARAMS);
     if (c->precision != MFC_LEARNED) return fail(c, MFC_ERR_ARG, "context is not MFC_LEARNED");
     if (!c->mlp) {
-        cudaError_t e = cudaMalloc(&c->mlp, sizeof(float) * MFC_MLP_PARAMS);
+        cudaError_t e = cudaMalloc(&c->mlp, kMlpFragOffset + kMlpFragBytes);
         if (e != cudaSuccess) {
             c->mlp = nullptr;
             return fail(c, e == cudaErrorMemoryAllocation ? MFC_ERR_OOM : MFC_ERR_CUDA, "cudaMalloc: %s",
@@ -519,6 +526,8 @@ mfc_status mfc_set_mlp(mfc_ctx* c, const float* params, int n) {
         }
     }
     MFC_CUDA(c, cudaMemcpyAsync(c->mlp, params, sizeof(float) * MFC_MLP_PARAMS, cudaMemcpyHostToDevice, c->stream));
+    MFC_CUDA(c, mfc_launch_mlp_pack(c->mlp, reinterpret_cast<char*>(c->mlp) + kMlpFragOffset, c->stream));
+    ++c->launches;
     MFC_CUDA(c, cudaStreamSynchronize(c->stream));
     return MFC_OK;
 }

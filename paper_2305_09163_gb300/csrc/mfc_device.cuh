@@ -65,7 +65,7 @@ struct SweepArgs {
     int nseg;               // marching kernels: segments along DIR
     long long slots_per_block;  // x-stream kernel: edge slots owned by one CTA
     unsigned long long* fallback_count;  // optional counter of fallback faces
-    const float* mlp;       // learned form: network parameters (device)
+    const uint4* mlp_frag;  // learned form: packed per-lane network fragments (device)
     float tau;              // learned form: discontinuity-sensor threshold
     int yz_stream;          // y/z sweeps: 1 = stream kernel, 0 = pencil marching
     int bound;              // learned form: range safeguard on learned edge values
@@ -370,6 +370,11 @@ __device__ __forceinline__ void face_flux(const SweepArgs& a, const EosR<Real>& 
 // tile, and each lane turns its rows' logits into weights and edge values.
 // All 32 lanes must call these functions.
 // ---------------------------------------------------------------------------
+#ifndef MFC_LEARN_TILES
+#define MFC_LEARN_TILES 1
+#endif
+constexpr int kLearnTiles = MFC_LEARN_TILES;
+
 template <int NS> struct LearnSmem {
     // one row per network evaluation (both edges of up to 32 cells x NS
     // variables): BF16 inputs in columns 0..4, then overwritten by the logits
@@ -379,18 +384,22 @@ template <int NS> struct LearnSmem {
 // Network over rows 0..nrows-1 of sm; each row's inputs are replaced by its
 // three logits (FP32, words 0..2).
 template <int NS>
-__device__ __forceinline__ void learned_logits(const MlpWeights& W, LearnSmem<NS>& sm, int nrows, int lane) {
+__device__ __forceinline__ void learned_logits(const uint4* __restrict__ frag, LearnSmem<NS>& sm, int nrows,
+                                               int lane) {
     const int g = lane >> 2, t = lane & 3;
     const int nt = (nrows + 15) >> 4;
     const uint32_t* rw = reinterpret_cast<const uint32_t*>(sm.row);
     float* rf = reinterpret_cast<float*>(sm.row);
     __syncwarp();
-    // groups of four independent tiles so their tensor-core chains overlap
+    if (nt == 0) return;
+    MlpWeights W;
+    mlp_weights_from_frag(frag, W, lane);
+    // kLearnTiles independent tiles at a time so their tensor-core chains overlap
 #pragma unroll 1
-    for (int t0 = 0; t0 < nt; t0 += 4) {
-        float z[4][4];
+    for (int t0 = 0; t0 < nt; t0 += kLearnTiles) {
+        float z[kLearnTiles][4];
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
+        for (int u = 0; u < kLearnTiles; ++u) {
             if (t0 + u < nt) {
                 const int r0 = 16 * (t0 + u);
                 const uint32_t a_in[2] = {rw[4 * (r0 + g) + t], rw[4 * (r0 + g + 8) + t]};
@@ -398,7 +407,7 @@ __device__ __forceinline__ void learned_logits(const MlpWeights& W, LearnSmem<NS
             }
         }
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
+        for (int u = 0; u < kLearnTiles; ++u) {
             if (t0 + u < nt && t < 2) {
                 const int r0 = 16 * (t0 + u);
                 *reinterpret_cast<float2*>(rf + 4 * (r0 + g) + 2 * t) = make_float2(z[u][0], z[u][1]);
@@ -420,10 +429,13 @@ __device__ __forceinline__ float learned_increment(const uint4& row, float d0, f
 
 // Edge values of one cell for all NS variables: WENO5-JS (eRjs, eLjs) and the
 // learned form (eR, eL; equal to the JS values where the sensor trips).
-template <int NS>
-__device__ __forceinline__ void learned_cell_edges(const float (&vc)[NS], const float (&D)[NS][4], float eps34,
-                                                   float tau, bool bound, const MlpWeights& W, LearnSmem<NS>& sm,
-                                                   int lane,
+// stencil(v, d) returns the cell value of variable v and fills d with the four
+// differences across cells c-2..c+2; it is called once per variable, and again
+// for the variables whose stencils went to the network, so that the stencils
+// need not stay in registers across the network.
+template <int NS, typename Stencil>
+__device__ __forceinline__ void learned_cell_edges(const Stencil& stencil, float eps34, float tau, bool bound,
+                                                   const uint4* __restrict__ frag, LearnSmem<NS>& sm, int lane,
                                                    float (&eRjs)[NS], float (&eLjs)[NS], float (&eR)[NS],
                                                    float (&eL)[NS]) {
     const unsigned below = (1u << lane) - 1u;
@@ -432,8 +444,9 @@ __device__ __forceinline__ void learned_cell_edges(const float (&vc)[NS], const 
     __syncwarp();   // the previous call's logits are read before rows are rewritten
 #pragma unroll
     for (int v = 0; v < NS; ++v) {
-        const float* d = D[v];
-        weno5_edges(vc[v], d, eps34, eRjs[v], eLjs[v]);
+        float d[4];
+        const float vc = stencil(v, d);
+        weno5_edges(vc, d, eps34, eRjs[v], eLjs[v]);
         const float S0 = d[0] * d[0], S1 = d[1] * d[1], S2 = d[2] * d[2], S3 = d[3] * d[3];
         const float b0 = fmaf(2.5f, S1, fmaf(-2.75f, d[1] * d[0], S0));
         const float b1 = fmaf(-1.25f, d[1] * d[2], S1 + S2);
@@ -441,7 +454,7 @@ __device__ __forceinline__ void learned_cell_edges(const float (&vc)[NS], const 
         const float xm2 = -(d[0] + d[1]), xm1 = -d[1], xp1 = d[2], xp2 = d[2] + d[3];
         const float sc = fmaxf(fmaxf(fabsf(xm2), fabsf(xm1)), fmaxf(fabsf(xp1), fabsf(xp2)));
         const float bmax = fmaxf(b0, fmaxf(b1, b2)), bmin = fminf(b0, fminf(b1, b2));
-        const bool usejs = !(sc > 1e-7f * fabsf(vc[v])) || (bmax > tau * fmaf(1e-6f * sc, sc, bmin));
+        const bool usejs = !(sc > 1e-7f * fabsf(vc)) || (bmax > tau * fmaf(1e-6f * sc, sc, bmin));
         need[v] = __ballot_sync(0xffffffffu, !usejs);
         if (!usejs) {
             const float is = __fdividef(1.0f, sc + 1e-30f);
@@ -454,14 +467,15 @@ __device__ __forceinline__ void learned_cell_edges(const float (&vc)[NS], const 
         }
         nrows += 2 * __popc(need[v]);
     }
-    learned_logits<NS>(W, sm, nrows, lane);
+    learned_logits<NS>(frag, sm, nrows, lane);
     int r = 0;
 #pragma unroll
     for (int v = 0; v < NS; ++v) {
         eL[v] = eLjs[v];
         eR[v] = eRjs[v];
         if (need[v] & (1u << lane)) {
-            const float* d = D[v];
+            float d[4];
+            const float vc = stencil(v, d);
             const int rr = r + 2 * __popc(need[v] & below);
             // increments at c+1/2 of the stencils c-2..c, c-1..c+1, c..c+2
             const float p0 = fmaf(5.f / 6.f, d[1], (-1.f / 3.f) * d[0]);
@@ -475,8 +489,8 @@ __device__ __forceinline__ void learned_cell_edges(const float (&vc)[NS], const 
             const float ir = learned_increment(sm.row[rr + 1], m0, m1, m2);
             // accept a learned value only inside the range of cells c-1, c, c+1
             const float lo = fminf(0.f, fminf(-d[1], d[2])), hi = fmaxf(0.f, fmaxf(-d[1], d[2]));
-            if (!(bound && (il < lo || il > hi))) eL[v] = vc[v] + il;
-            if (!(bound && (ir < lo || ir > hi))) eR[v] = vc[v] + ir;
+            if (!(bound && (il < lo || il > hi))) eL[v] = vc + il;
+            if (!(bound && (ir < lo || ir > hi))) eR[v] = vc + ir;
         }
         r += 2 * __popc(need[v]);
     }
@@ -594,12 +608,10 @@ __global__ void __launch_bounds__(128) sweep_kernel(const SweepArgs a) {
     const Real eps34 = (Real)(0.75 * a.eps);
     const EosR<Real> e(a.e);
     const Real inv_dx = (Real)a.g.inv_dx[DIR];
-    MlpWeights W;
     LearnSmem<NS>* lsm = nullptr;
     if constexpr (LEARNED) {
         __shared__ LearnSmem<NS> lbuf[4];
         lsm = &lbuf[threadIdx.x >> 5];
-        mlp_load_weights(a.mlp, W, lane);
     }
 
     auto load = [&](int i, Real* out) {
@@ -636,7 +648,14 @@ __global__ void __launch_bounds__(128) sweep_kernel(const SweepArgs a) {
     for (int c = s0 - 1; c <= s1; ++c) {
         Real eR[NS], eL[NS], eRJ[NS], eLJ[NS];
         if constexpr (LEARNED) {
-            learned_cell_edges<NS>(vc, D, eps34, a.tau, a.bound != 0, W, *lsm, lane, eRJ, eLJ, eR, eL);
+            auto stencil = [&](int v, float (&dd)[4]) -> float {
+                dd[0] = D[v][0];
+                dd[1] = D[v][1];
+                dd[2] = D[v][2];
+                dd[3] = D[v][3];
+                return vc[v];
+            };
+            learned_cell_edges<NS>(stencil, eps34, a.tau, a.bound != 0, a.mlp_frag, *lsm, lane, eRJ, eLJ, eR, eL);
         } else {
 #pragma unroll
             for (int v = 0; v < NS; ++v) weno5_edges(vc[v], D[v], eps34, eR[v], eL[v]);
@@ -713,12 +732,10 @@ __global__ void __launch_bounds__(kStreamThreads) sweep_x_stream_kernel(const Sw
     const EosR<Real> e(a.e);
     const Real inv_dx = (Real)a.g.inv_dx[0];
     const int t = threadIdx.x;
-    MlpWeights W;
     LearnSmem<NS>* lsm = nullptr;
     if constexpr (LEARNED) {
         __shared__ LearnSmem<NS> lbuf[kStreamThreads / 32];
         lsm = &lbuf[t >> 5];
-        mlp_load_weights(a.mlp, W, t & 31);
     }
 
     // (row, column) of this lane's slot: one 64-bit division when the slot first
@@ -746,14 +763,49 @@ __global__ void __launch_bounds__(kStreamThreads) sweep_x_stream_kernel(const Sw
             }
         }
         Real cell[NS], cm1[NS], eL[NS], eR[NS], eLJ[NS], eRJ[NS];
-        Real vcv[NS], Dv[NS][4];
+        if constexpr (LEARNED) {
+            // the five cells of this lane's stencil, re-read (L1) per variable
+            int mk[5];
+            bool fk[5];
 #pragma unroll
-        for (int q = 0; q < NS; ++q) {
-            vcv[q] = 0;
-            cm1[q] = 0;
-            Dv[q][0] = Dv[q][1] = Dv[q][2] = Dv[q][3] = 0;
+            for (int k = 0; k < 5; ++k) {
+                fk[k] = false;
+                mk[k] = live ? ghost_map(c + k - 2, n, bclo, bchi, &fk[k]) : 0;
+            }
+            const Real* wr = w + rowoff;
+            auto stencil = [&](int q, float (&dd)[4]) -> float {
+                float v5[5];
+#pragma unroll
+                for (int k = 0; k < 5; ++k) {
+                    float x = live ? __ldg(wr + q * nc + mk[k]) : 0.f;
+                    if (q == IM && fk[k]) x = -x;
+                    v5[k] = x;
+                }
+#pragma unroll
+                for (int k = 0; k < 4; ++k) dd[k] = v5[k + 1] - v5[k];
+                return v5[2];
+            };
+            learned_cell_edges<NS>(stencil, eps34, a.tau, a.bound != 0, a.mlp_frag, *lsm, t & 31, eRJ, eLJ, eR, eL);
+#pragma unroll
+            for (int q = 0; q < NS; ++q) {
+                float x1 = live ? __ldg(wr + q * nc + mk[1]) : 0.f;
+                float x2 = live ? __ldg(wr + q * nc + mk[2]) : 0.f;
+                if (q == IM && fk[1]) x1 = -x1;
+                if (q == IM && fk[2]) x2 = -x2;
+                cm1[q] = x1;
+                cell[q] = x2;
+            }
         }
-        if (live) {
+        Real vcv[NS], Dv[NS][4];
+        if constexpr (!LEARNED) {
+#pragma unroll
+            for (int q = 0; q < NS; ++q) {
+                vcv[q] = 0;
+                cm1[q] = 0;
+                Dv[q][0] = Dv[q][1] = Dv[q][2] = Dv[q][3] = 0;
+            }
+        }
+        if (!LEARNED && live) {
             Real v[5][NS];
 #pragma unroll
             for (int k = 0; k < 5; ++k) {
@@ -773,14 +825,14 @@ __global__ void __launch_bounds__(kStreamThreads) sweep_x_stream_kernel(const Sw
                 cm1[q] = v[1][q];
             }
         }
-        if constexpr (LEARNED) {
-            learned_cell_edges<NS>(vcv, Dv, eps34, a.tau, a.bound != 0, W, *lsm, t & 31, eRJ, eLJ, eR, eL);
-        } else if (live) {
+        if (!LEARNED && live) {
 #pragma unroll
             for (int q = 0; q < NS; ++q) weno5_edges(vcv[q], Dv[q], eps34, eR[q], eL[q]);
         }
+        if constexpr (!LEARNED) {
 #pragma unroll
-        for (int q = 0; q < NS; ++q) cell[q] = vcv[q];
+            for (int q = 0; q < NS; ++q) cell[q] = vcv[q];
+        }
         // left-side values of this chunk; slot 0 holds the carry from the last chunk
         if (live) {
 #pragma unroll
@@ -879,12 +931,10 @@ __global__ void __launch_bounds__(32 * kRowsPerChunk) sweep_yz_stream_kernel(con
     const Real eps34 = (Real)(0.75 * a.eps);
     const EosR<Real> e(a.e);
     const Real inv_dx = (Real)a.g.inv_dx[DIR];
-    MlpWeights W;
     LearnSmem<NS>* lsm = nullptr;
     if constexpr (LEARNED) {
         __shared__ LearnSmem<NS> lbuf[kRowsPerChunk];
         lsm = &lbuf[row];
-        mlp_load_weights(a.mlp, W, lane);
     }
     // cell i along DIR (ghost-mapped) of this lane's column
     auto load = [&](int i, Real* out) {
@@ -919,22 +969,36 @@ __global__ void __launch_bounds__(32 * kRowsPerChunk) sweep_yz_stream_kernel(con
         const bool live = c <= s1;
         Real cell[NS], cm1[NS], eL[NS], eR[NS], eLJ[NS], eRJ[NS];
         if (live) {
-            Real Dv[NS][4];
-#pragma unroll
-            for (int q = 0; q < NS; ++q) {
-                const Real v0 = ring[slot(c - 2)][q][lane], v1 = ring[slot(c - 1)][q][lane];
-                const Real v2 = ring[slot(c)][q][lane], v3 = ring[slot(c + 1)][q][lane];
-                const Real v4 = ring[slot(c + 2)][q][lane];
-                Dv[q][0] = v1 - v0;
-                Dv[q][1] = v2 - v1;
-                Dv[q][2] = v3 - v2;
-                Dv[q][3] = v4 - v3;
-                cell[q] = v2;
-                cm1[q] = v1;
-            }
             if constexpr (LEARNED) {
-                learned_cell_edges<NS>(cell, Dv, eps34, a.tau, a.bound != 0, W, *lsm, lane, eRJ, eLJ, eR, eL);
+                auto stencil = [&](int q, float (&dd)[4]) -> float {
+                    float v5[5];
+#pragma unroll
+                    for (int k = 0; k < 5; ++k) v5[k] = ring[slot(c - 2 + k)][q][lane];
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) dd[k] = v5[k + 1] - v5[k];
+                    return v5[2];
+                };
+                learned_cell_edges<NS>(stencil, eps34, a.tau, a.bound != 0, a.mlp_frag, *lsm, lane, eRJ, eLJ, eR,
+                                       eL);
+#pragma unroll
+                for (int q = 0; q < NS; ++q) {
+                    cell[q] = ring[slot(c)][q][lane];
+                    cm1[q] = ring[slot(c - 1)][q][lane];
+                }
             } else {
+                Real Dv[NS][4];
+#pragma unroll
+                for (int q = 0; q < NS; ++q) {
+                    const Real v0 = ring[slot(c - 2)][q][lane], v1 = ring[slot(c - 1)][q][lane];
+                    const Real v2 = ring[slot(c)][q][lane], v3 = ring[slot(c + 1)][q][lane];
+                    const Real v4 = ring[slot(c + 2)][q][lane];
+                    Dv[q][0] = v1 - v0;
+                    Dv[q][1] = v2 - v1;
+                    Dv[q][2] = v3 - v2;
+                    Dv[q][3] = v4 - v3;
+                    cell[q] = v2;
+                    cm1[q] = v1;
+                }
 #pragma unroll
                 for (int q = 0; q < NS; ++q) weno5_edges(cell[q], Dv[q], eps34, eR[q], eL[q]);
             }

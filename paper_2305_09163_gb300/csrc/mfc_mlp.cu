@@ -517,7 +517,20 @@ __global__ void __launch_bounds__(256) prims_out_kernel(const double* __restrict
     }
 }
 
+// One warp: the per-lane MMA fragments of a parameter blob, for the sweeps.
+__global__ void __launch_bounds__(32) mlp_pack_kernel(const float* __restrict__ P, uint4* __restrict__ frag) {
+    MlpWeights W;
+    mlp_load_weights(P, W, threadIdx.x);
+    mlp_weights_to_frag(W, frag, threadIdx.x);
+}
+
 }  // namespace
+
+// Host launcher used by mfc_set_mlp: frag holds kMlpFragBytes.
+cudaError_t mfc_launch_mlp_pack(const float* P, void* frag, cudaStream_t s) {
+    mlp_pack_kernel<<<1, 32, 0, s>>>(P, static_cast<uint4*>(frag));
+    return cudaGetLastError();
+}
 
 // Host launcher used by mfc_get_prims in the context code.
 cudaError_t mfc_launch_prims_out(const double* q, double* w, long long nc, int nf, int ndim, const EosConst& e,

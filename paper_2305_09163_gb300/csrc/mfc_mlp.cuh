@@ -115,6 +115,35 @@ __device__ __forceinline__ void mlp_load_weights(const float* __restrict__ P, Ml
     W.b3[1] = 2 * t + 1 < kMlpOut ? P[kOffB3 + 2 * t + 1] : 0.f;
 }
 
+// The per-lane fragments of MlpWeights packed for one warp: word k of lane l
+// at frag[k / 4][l] component k % 4, so each lane reads 11 16-byte words and
+// a warp's 32 lanes read 512 contiguous bytes per word.  Built once per
+// parameter set; the sweeps load it only when a warp has stencils for the
+// network.
+constexpr int kMlpFragVec = 11;   // uint4 per lane (42 words used)
+constexpr int kMlpFragBytes = kMlpFragVec * 32 * 16;
+static_assert(sizeof(MlpWeights) == 42 * 4, "MlpWeights is 42 words");
+
+union MlpWeightsWords {
+    MlpWeights w;
+    uint4 v[kMlpFragVec];
+};
+
+__device__ __forceinline__ void mlp_weights_to_frag(const MlpWeights& W, uint4* __restrict__ F, int lane) {
+    MlpWeightsWords u;
+    u.v[kMlpFragVec - 1] = make_uint4(0u, 0u, 0u, 0u);
+    u.w = W;
+#pragma unroll
+    for (int k = 0; k < kMlpFragVec; ++k) F[k * 32 + lane] = u.v[k];
+}
+
+__device__ __forceinline__ void mlp_weights_from_frag(const uint4* __restrict__ F, MlpWeights& W, int lane) {
+    MlpWeightsWords u;
+#pragma unroll
+    for (int k = 0; k < kMlpFragVec; ++k) u.v[k] = __ldg(F + k * 32 + lane);
+    W = u.w;
+}
+
 // max(lo, 0), max(hi, 0) rounded to BF16 and packed, in one conversion.
 __device__ __forceinline__ uint32_t pack_bf16_relu(float lo, float hi) {
     uint32_t r;
