@@ -433,16 +433,16 @@ def main():
     forms = [f.strip() for f in args.forms.split(",") if f.strip()]
     results = {}
     training = None
+    head = "fp64" if "fp64" in forms else forms[0]
     for form in forms:
         mlp = None
         if form == "learned":
             mlp, training = train_learned(m, torch)
         r = time_form(m, torch, wl, w_dev, form, args.steps, args.warmup, barrier,
-                      sampler_gpu=local if form == "fp64" else None, mlp=mlp)
+                      sampler_gpu=local if form == head else None, mlp=mlp)
         r["ms_max"] = max_over_ranks(r["ms_per_step"], ws, "cuda")
         results[form] = r
 
-    head = "fp64" if "fp64" in results else forms[0]
     fp = results[head]
     ms = fp["ms_max"]
     grind = grind_ns(ms, ws, cells, ns)

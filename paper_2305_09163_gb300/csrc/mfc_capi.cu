@@ -205,6 +205,7 @@ SweepArgs base_sweep(const mfc_ctx* c) {
     // consecutive cells share their stencil differences (fewer FP64 instructions)
     a.yz_stream = c->yz_stream >= 0 ? c->yz_stream : (is_f32(c) ? 1 : 0);
     a.bound = c->bound;
+    sweep_set_f32_constants(a);
     return a;
 }
 

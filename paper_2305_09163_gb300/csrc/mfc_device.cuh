@@ -46,6 +46,14 @@ struct EosConst {
     double dG[2], dP[2];
 };
 
+// FP32 copies of the constants the FP32 kernels use, converted once on the
+// host (a conversion from FP64 in the kernel would run on the FP64 pipe, and
+// the compiler may repeat it at every use).
+struct EosConstF {
+    float G_N, P_N;
+    float dG[2], dP[2];
+};
+
 // Arguments of one directional sweep.
 struct SweepArgs {
     Geometry g;
@@ -69,7 +77,22 @@ struct SweepArgs {
     float tau;              // learned form: discontinuity-sensor threshold
     int yz_stream;          // y/z sweeps: 1 = stream kernel, 0 = pencil marching
     int bound;              // learned form: range safeguard on learned edge values
+    EosConstF ef;           // FP32 kernels: e, eps * 3/4 and g.inv_dx in FP32
+    float eps34f;
+    float inv_dxf[3];
 };
+
+// Fill the FP32 constants of a from its FP64 ones (host, after e, eps and g).
+inline void sweep_set_f32_constants(SweepArgs& a) {
+    a.ef.G_N = (float)a.e.G_N;
+    a.ef.P_N = (float)a.e.P_N;
+    for (int k = 0; k < 2; ++k) {
+        a.ef.dG[k] = (float)a.e.dG[k];
+        a.ef.dP[k] = (float)a.e.dP[k];
+    }
+    a.eps34f = (float)(0.75 * a.eps);
+    for (int d = 0; d < 3; ++d) a.inv_dxf[d] = (float)a.g.inv_dx[d];
+}
 
 struct PrimArgs {
     Geometry g;
@@ -208,7 +231,28 @@ template <typename Real> struct EosR {
         dG[0] = (Real)e.dG[0]; dG[1] = (Real)e.dG[1];
         dP[0] = (Real)e.dP[0]; dP[1] = (Real)e.dP[1];
     }
+    __device__ __forceinline__ explicit EosR(const EosConstF& e) : G_N(e.G_N), P_N(e.P_N) {
+        dG[0] = e.dG[0]; dG[1] = e.dG[1];
+        dP[0] = e.dP[0]; dP[1] = e.dP[1];
+    }
 };
+
+// The EOS constants, 3/4 eps and 1/dx of direction d in the sweep's precision.
+template <typename Real>
+__device__ __forceinline__ EosR<Real> sweep_eos(const SweepArgs& a) {
+    if constexpr (sizeof(Real) == 4) return EosR<Real>(a.ef);
+    else return EosR<Real>(a.e);
+}
+template <typename Real>
+__device__ __forceinline__ Real sweep_eps34(const SweepArgs& a) {
+    if constexpr (sizeof(Real) == 4) return a.eps34f;
+    else return (Real)(0.75 * a.eps);
+}
+template <typename Real>
+__device__ __forceinline__ Real sweep_inv_dx(const SweepArgs& a, int d) {
+    if constexpr (sizeof(Real) == 4) return a.inv_dxf[d];
+    else return (Real)a.g.inv_dx[d];
+}
 
 __device__ __forceinline__ double real_rcp(double x) { return rcp_nr(x); }
 __device__ __forceinline__ float real_rcp(float x) { return __fdividef(1.0f, x); }
@@ -605,9 +649,9 @@ __global__ void __launch_bounds__(128) sweep_kernel(const SweepArgs a) {
     const int s0 = sg * a.seg;
     const int s1 = min(s0 + a.seg, nd);
     const int bclo = a.g.bc_lo[DIR], bchi = a.g.bc_hi[DIR];
-    const Real eps34 = (Real)(0.75 * a.eps);
-    const EosR<Real> e(a.e);
-    const Real inv_dx = (Real)a.g.inv_dx[DIR];
+    const Real eps34 = sweep_eps34<Real>(a);
+    const EosR<Real> e = sweep_eos<Real>(a);
+    const Real inv_dx = sweep_inv_dx<Real>(a, DIR);
     LearnSmem<NS>* lsm = nullptr;
     if constexpr (LEARNED) {
         __shared__ LearnSmem<NS> lbuf[4];
@@ -728,9 +772,9 @@ __global__ void __launch_bounds__(kStreamThreads) sweep_x_stream_kernel(const Sw
     const long long own1 = min(own0 + a.slots_per_block, total);
     const long long nc = a.g.ncell;
     const int bclo = a.g.bc_lo[0], bchi = a.g.bc_hi[0];
-    const Real eps34 = (Real)(0.75 * a.eps);
-    const EosR<Real> e(a.e);
-    const Real inv_dx = (Real)a.g.inv_dx[0];
+    const Real eps34 = sweep_eps34<Real>(a);
+    const EosR<Real> e = sweep_eos<Real>(a);
+    const Real inv_dx = sweep_inv_dx<Real>(a, 0);
     const int t = threadIdx.x;
     LearnSmem<NS>* lsm = nullptr;
     if constexpr (LEARNED) {
@@ -896,8 +940,8 @@ __global__ void __launch_bounds__(kStreamThreads) sweep_x_stream_kernel(const Sw
 // ---------------------------------------------------------------------------
 constexpr int kRowsPerChunk = 4;
 
-template <typename Real, int NF, int NDIM, int DIR, bool LEARNED = false>
-__global__ void __launch_bounds__(32 * kRowsPerChunk) sweep_yz_stream_kernel(const SweepArgs a) {
+template <typename Real, int NF, int NDIM, int DIR, bool LEARNED>
+__device__ __forceinline__ void sweep_yz_stream_body(const SweepArgs& a) {
     static_assert(DIR == 1 || DIR == 2, "y or z");
     static_assert(!LEARNED || sizeof(Real) == 4, "the learned form runs in FP32");
     using Lay = Layout<NF, NDIM>;
@@ -928,9 +972,9 @@ __global__ void __launch_bounds__(32 * kRowsPerChunk) sweep_yz_stream_kernel(con
     const int s0 = sg * a.seg;
     const int s1 = min(s0 + a.seg, nd);
     const int bclo = a.g.bc_lo[DIR], bchi = a.g.bc_hi[DIR];
-    const Real eps34 = (Real)(0.75 * a.eps);
-    const EosR<Real> e(a.e);
-    const Real inv_dx = (Real)a.g.inv_dx[DIR];
+    const Real eps34 = sweep_eps34<Real>(a);
+    const EosR<Real> e = sweep_eos<Real>(a);
+    const Real inv_dx = sweep_inv_dx<Real>(a, DIR);
     LearnSmem<NS>* lsm = nullptr;
     if constexpr (LEARNED) {
         __shared__ LearnSmem<NS> lbuf[kRowsPerChunk];
@@ -1053,6 +1097,20 @@ __global__ void __launch_bounds__(32 * kRowsPerChunk) sweep_yz_stream_kernel(con
         }
         __syncthreads();
     }
+}
+
+// The y/z stream kernel of the FP32 forms.  The learned form gets its own
+// entry with a register bound (4 CTAs per SM for two fluids) so that enough
+// warps stay resident; the mixed form keeps the compiler's own allocation,
+// which schedules its loads better.
+template <typename Real, int NF, int NDIM, int DIR>
+__global__ void __launch_bounds__(32 * kRowsPerChunk) sweep_yz_stream_kernel(const SweepArgs a) {
+    sweep_yz_stream_body<Real, NF, NDIM, DIR, false>(a);
+}
+
+template <int NF, int NDIM, int DIR>
+__global__ void __launch_bounds__(32 * kRowsPerChunk, NF <= 2 ? 4 : 3) sweep_yz_stream_learned_kernel(const SweepArgs a) {
+    sweep_yz_stream_body<float, NF, NDIM, DIR, true>(a);
 }
 
 // ---------------------------------------------------------------------------

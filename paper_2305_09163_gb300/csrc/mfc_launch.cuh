@@ -31,11 +31,20 @@ cudaError_t launch_sweep(SweepArgs a, int ndim, int dir, cudaStream_t s) {
     if (a.yz_stream) {
         // y/z stream kernel, one CTA per 32 x-lanes of a segment
         const unsigned blocks = (unsigned)((long long)((a.g.n[t1] + 31) / 32) * a.nseg * a.g.n[t2]);
-        switch (ndim * 4 + dir) {
-            case 9: sweep_yz_stream_kernel<Real, NF, 2, 1, LEARNED><<<blocks, 32 * kRowsPerChunk, 0, s>>>(a); break;
-            case 13: sweep_yz_stream_kernel<Real, NF, 3, 1, LEARNED><<<blocks, 32 * kRowsPerChunk, 0, s>>>(a); break;
-            case 14: sweep_yz_stream_kernel<Real, NF, 3, 2, LEARNED><<<blocks, 32 * kRowsPerChunk, 0, s>>>(a); break;
-            default: return cudaErrorInvalidValue;
+        if constexpr (LEARNED) {
+            switch (ndim * 4 + dir) {
+                case 9: sweep_yz_stream_learned_kernel<NF, 2, 1><<<blocks, 32 * kRowsPerChunk, 0, s>>>(a); break;
+                case 13: sweep_yz_stream_learned_kernel<NF, 3, 1><<<blocks, 32 * kRowsPerChunk, 0, s>>>(a); break;
+                case 14: sweep_yz_stream_learned_kernel<NF, 3, 2><<<blocks, 32 * kRowsPerChunk, 0, s>>>(a); break;
+                default: return cudaErrorInvalidValue;
+            }
+        } else {
+            switch (ndim * 4 + dir) {
+                case 9: sweep_yz_stream_kernel<Real, NF, 2, 1><<<blocks, 32 * kRowsPerChunk, 0, s>>>(a); break;
+                case 13: sweep_yz_stream_kernel<Real, NF, 3, 1><<<blocks, 32 * kRowsPerChunk, 0, s>>>(a); break;
+                case 14: sweep_yz_stream_kernel<Real, NF, 3, 2><<<blocks, 32 * kRowsPerChunk, 0, s>>>(a); break;
+                default: return cudaErrorInvalidValue;
+            }
         }
         return cudaGetLastError();
     }

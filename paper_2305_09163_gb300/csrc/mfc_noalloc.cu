@@ -88,6 +88,7 @@ cudaError_t run(const Geometry& g, const EosConst& e, int ndim, const double* q,
         a.eps = eps;
         a.fallback = fallback;
         a.fallback_count = nullptr;
+        sweep_set_f32_constants(a);
         const long long trans = g.ncell / g.n[d];
         int L = 64;
         while (L > 8 && trans * ((g.n[d] + L - 1) / L) < 152LL * 4 * kSweepThreads) L /= 2;
