@@ -182,6 +182,7 @@ def time_form(m, torch, wl, w_dev, precision, steps, warmup, dist_barrier, sampl
     s.profile()  # clear anything pending
     prof0 = s.profile()
     l0 = s.launch_count()
+    r0 = s.network_rows()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     sampler = ClockSampler(sampler_gpu) if sampler_gpu is not None else None
@@ -200,13 +201,15 @@ def time_form(m, torch, wl, w_dev, precision, steps, warmup, dist_barrier, sampl
     prof1 = s.profile()
     s.set_param("profile", 0)
     launches = s.launch_count() - l0
+    rows = s.network_rows() - r0
     sweep_ms = _sweep_profile(prof1)[0] - _sweep_profile(prof0)[0]
     sweep_n = _sweep_profile(prof1)[1] - _sweep_profile(prof0)[1]
     kern = {k: (prof1[k][0] - prof0[k][0], prof1[k][1] - prof0[k][1]) for k in prof1}
     fb = s.fallback_count()
     s.close()
     return {"ms_per_step": ms, "launches": launches, "sweep_ms": sweep_ms, "sweep_launches": sweep_n,
-            "kernels": kern, "clocks": sampler.summary() if sampler else None, "fallback_faces": fb}
+            "kernels": kern, "clocks": sampler.summary() if sampler else None, "fallback_faces": fb,
+            "network_rows": rows}
 
 
 def e2e_form(m, torch, wl, w_host, precision, steps, warmup):
@@ -490,11 +493,21 @@ def main():
                                  "fp32_frac": tf / FP32_PEAK_TFLOPS,
                                  "note": "peaks: HBM of measured copy, FP32 nominal"}
         elif form == "learned":
-            tfl = FLOP_MLP_STENCIL * STENCILS_PER_CELL_SWEEP * cells * r["sweep_launches"] / sweep_s / 1e12
+            # the sweeps do the mixed form's work plus the sensor and, on the
+            # edges it does not trip, the network (counted on the device)
+            gbs = BYTES_MIXED_SWEEPS_STAGE * cells * stages / sweep_s / 1e9
+            tf = FLOP_SWEEP_CELL_3D_2F * cells * r["sweep_launches"] / sweep_s / 1e12
+            edges = STENCILS_PER_CELL_SWEEP * cells * r["sweep_launches"]
+            tfl = FLOP_MLP_STENCIL * r["network_rows"] / sweep_s / 1e12
             bf = float(peaks.get("bf16_tflops_sustained", 1700.0))
-            entry["roofline"] = {"kernel": "sweep (x, y, z) with the network", "tensor_tflops": tfl,
-                                 "tensor_peak": bf, "tensor_frac": tfl / bf,
-                                 "note": "useful network FLOPs; peak = measured sustained BF16 (mma.sync path)"}
+            entry["roofline"] = {"kernel": "sweep (x, y, z) with the network", "hbm_gbs": gbs, "hbm_peak": hbm,
+                                 "hbm_frac": gbs / hbm, "fp32_tflops": tf, "fp32_peak": FP32_PEAK_TFLOPS,
+                                 "fp32_frac": tf / FP32_PEAK_TFLOPS,
+                                 "network_edges": r["network_rows"], "network_fraction": r["network_rows"] / edges,
+                                 "tensor_tflops": tfl, "tensor_peak": bf, "tensor_frac": tfl / bf,
+                                 "note": "HBM/FP32 as the mixed form (its algorithmic bytes and FLOPs); network "
+                                         "FLOPs of the edges evaluated, averaged over the sweep time; peaks: HBM "
+                                         "of measured copy, FP32 nominal, BF16 measured sustained"}
             entry["training"] = training
         line["forms"][form] = entry
     if not args.no_e2e:

@@ -196,6 +196,11 @@ long long mfc_launch_count(const mfc_ctx* ctx);
  * created (synchronises the stream). */
 long long mfc_fallback_count(mfc_ctx* ctx);
 
+/* Learned form: number of edge values the network evaluated since the context
+ * was created (the rest kept their WENO5-JS weights: sensor trip or flat
+ * stencil).  0 for the other forms; -1 on error.  Synchronises the stream. */
+long long mfc_network_rows(mfc_ctx* ctx);
+
 /* Per-kernel timing collected while "profile" is on: for category i in
  * [0, n) (0 prims, 1 sweep_x, 2 sweep_y, 3 sweep_z, 4 prims+cfl, 5 convert,
  * 6 mlp), total milliseconds and launch counts.  Synchronises the stream.

@@ -69,6 +69,8 @@ def _declare(lib):
     lib.mfc_launch_count.restype = c_ll
     lib.mfc_fallback_count.argtypes = [c_void_p]
     lib.mfc_fallback_count.restype = c_ll
+    lib.mfc_network_rows.argtypes = [c_void_p]
+    lib.mfc_network_rows.restype = c_ll
     lib.mfc_profile_read.argtypes = [c_void_p, dptr, ctypes.POINTER(c_ll), c_int]
     lib.mfc_profile_read.restype = c_int
     lib.mfc_rhs_noalloc.argtypes = [c_void_p, c_void_p, c_int, c_int, c_int, dptr, dptr, ctypes.POINTER(c_int),
@@ -200,6 +202,10 @@ def mfc_launch_count(ctx):
 
 def mfc_fallback_count(ctx):
     return load().mfc_fallback_count(ctx)
+
+
+def mfc_network_rows(ctx):
+    return load().mfc_network_rows(ctx)
 
 
 def mfc_profile_read(ctx):
@@ -371,6 +377,9 @@ class Solver:
 
     def fallback_count(self):
         return mfc_fallback_count(self.ctx)
+
+    def network_rows(self):
+        return mfc_network_rows(self.ctx)
 
     def profile(self):
         return mfc_profile_read(self.ctx)

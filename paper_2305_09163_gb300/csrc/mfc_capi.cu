@@ -59,7 +59,7 @@ struct mfc_ctx {
     void* w = nullptr;        // primitives (double or float)
     unsigned long long* d_rate = nullptr;  // CFL max (ordered bits)
     int* d_bad = nullptr;
-    unsigned long long* d_fallback = nullptr;
+    unsigned long long* d_fallback = nullptr;  // [0] fallback faces, [1] learned-form network rows
     unsigned long long* h_pin = nullptr;   // pinned readback [rate, bad]
     float* mlp = nullptr;         // network parameters, then (at byte kMlpFragOffset) the packed fragments
 
@@ -198,6 +198,7 @@ SweepArgs base_sweep(const mfc_ctx* c) {
     a.eps = c->eps;
     a.fallback = c->fallback;
     a.fallback_count = c->d_fallback;
+    a.net_rows = c->d_fallback + 1;
     a.mlp_frag = c->mlp ? reinterpret_cast<const uint4*>(reinterpret_cast<const char*>(c->mlp) + kMlpFragOffset)
                         : nullptr;
     a.tau = (float)c->tau;
@@ -347,7 +348,7 @@ mfc_status mfc_init(mfc_ctx** out, int nx, int ny, int nz, const double lo[3], c
         (e = cudaMalloc(&c->R, wbytes)) != cudaSuccess || (e = cudaMalloc(&c->w, wbytes)) != cudaSuccess ||
         (e = cudaMalloc(&c->d_rate, sizeof(unsigned long long))) != cudaSuccess ||
         (e = cudaMalloc(&c->d_bad, sizeof(int))) != cudaSuccess ||
-        (e = cudaMalloc(&c->d_fallback, sizeof(unsigned long long))) != cudaSuccess ||
+        (e = cudaMalloc(&c->d_fallback, 2 * sizeof(unsigned long long))) != cudaSuccess ||
         (e = cudaMallocHost(&c->h_pin, 2 * sizeof(unsigned long long))) != cudaSuccess) {
         const bool oom = (e == cudaErrorMemoryAllocation);
         cudaGetLastError();
@@ -355,7 +356,7 @@ mfc_status mfc_init(mfc_ctx** out, int nx, int ny, int nz, const double lo[3], c
         delete c;
         return oom ? MFC_ERR_OOM : MFC_ERR_CUDA;
     }
-    if (cudaMemsetAsync(c->d_fallback, 0, sizeof(unsigned long long), c->stream) != cudaSuccess) {
+    if (cudaMemsetAsync(c->d_fallback, 0, 2 * sizeof(unsigned long long), c->stream) != cudaSuccess) {
         free_all(c);
         delete c;
         return MFC_ERR_CUDA;
@@ -561,6 +562,15 @@ long long mfc_fallback_count(mfc_ctx* c) {
         return -1;
     v = c->h_pin[0];
     return (long long)v;
+}
+
+long long mfc_network_rows(mfc_ctx* c) {
+    if (!c || c->dead) return -1;
+    if (cudaMemcpyAsync(&c->h_pin[0], c->d_fallback + 1, sizeof(unsigned long long), cudaMemcpyDeviceToHost,
+                        c->stream) != cudaSuccess ||
+        cudaStreamSynchronize(c->stream) != cudaSuccess)
+        return -1;
+    return (long long)c->h_pin[0];
 }
 
 int mfc_profile_read(mfc_ctx* c, double* total_ms, long long* launches, int n) {

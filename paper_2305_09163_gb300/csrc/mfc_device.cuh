@@ -73,6 +73,7 @@ struct SweepArgs {
     int nseg;               // marching kernels: segments along DIR
     long long slots_per_block;  // x-stream kernel: edge slots owned by one CTA
     unsigned long long* fallback_count;  // optional counter of fallback faces
+    unsigned long long* net_rows;        // learned form: optional counter of network evaluations
     const uint4* mlp_frag;  // learned form: packed per-lane network fragments (device)
     float tau;              // learned form: discontinuity-sensor threshold
     int yz_stream;          // y/z sweeps: 1 = stream kernel, 0 = pencil marching
@@ -476,9 +477,10 @@ __device__ __forceinline__ float learned_increment(const uint4& row, float d0, f
 // stencil(v, d) returns the cell value of variable v and fills d with the four
 // differences across cells c-2..c+2; it is called once per variable, and again
 // for the variables whose stencils went to the network, so that the stencils
-// need not stay in registers across the network.
+// need not stay in registers across the network.  Returns the number of
+// network rows (edges) the warp evaluated.
 template <int NS, typename Stencil>
-__device__ __forceinline__ void learned_cell_edges(const Stencil& stencil, float eps34, float tau, bool bound,
+__device__ __forceinline__ int learned_cell_edges(const Stencil& stencil, float eps34, float tau, bool bound,
                                                    const uint4* __restrict__ frag, LearnSmem<NS>& sm, int lane,
                                                    float (&eRjs)[NS], float (&eLjs)[NS], float (&eR)[NS],
                                                    float (&eL)[NS]) {
@@ -538,6 +540,7 @@ __device__ __forceinline__ void learned_cell_edges(const Stencil& stencil, float
         }
         r += 2 * __popc(need[v]);
     }
+    return nrows;
 }
 
 // Face flux of the learned form: the learned face states, else (non-physical)
@@ -657,6 +660,7 @@ __global__ void __launch_bounds__(128) sweep_kernel(const SweepArgs a) {
         __shared__ LearnSmem<NS> lbuf[4];
         lsm = &lbuf[threadIdx.x >> 5];
     }
+    unsigned long long net_rows = 0;  // learned form: network rows of this warp
 
     auto load = [&](int i, Real* out) {
         bool flip = false;
@@ -699,7 +703,8 @@ __global__ void __launch_bounds__(128) sweep_kernel(const SweepArgs a) {
                 dd[3] = D[v][3];
                 return vc[v];
             };
-            learned_cell_edges<NS>(stencil, eps34, a.tau, a.bound != 0, a.mlp_frag, *lsm, lane, eRJ, eLJ, eR, eL);
+            net_rows += learned_cell_edges<NS>(stencil, eps34, a.tau, a.bound != 0, a.mlp_frag, *lsm, lane, eRJ, eLJ, eR,
+                                                  eL);
         } else {
 #pragma unroll
             for (int v = 0; v < NS; ++v) weno5_edges(vc[v], D[v], eps34, eR[v], eL[v]);
@@ -737,6 +742,9 @@ __global__ void __launch_bounds__(128) sweep_kernel(const SweepArgs a) {
                 vp2[v] = nw[v];
             }
         }
+    }
+    if constexpr (LEARNED) {
+        if ((threadIdx.x & 31) == 0 && net_rows && a.net_rows) atomicAdd(a.net_rows, net_rows);
     }
 }
 
@@ -781,6 +789,7 @@ __global__ void __launch_bounds__(kStreamThreads) sweep_x_stream_kernel(const Sw
         __shared__ LearnSmem<NS> lbuf[kStreamThreads / 32];
         lsm = &lbuf[t >> 5];
     }
+    unsigned long long net_rows = 0;  // learned form: network rows of this warp
 
     // (row, column) of this lane's slot: one 64-bit division when the slot first
     // becomes valid, then advanced by 128 slots per chunk with additions (a
@@ -829,7 +838,8 @@ __global__ void __launch_bounds__(kStreamThreads) sweep_x_stream_kernel(const Sw
                 for (int k = 0; k < 4; ++k) dd[k] = v5[k + 1] - v5[k];
                 return v5[2];
             };
-            learned_cell_edges<NS>(stencil, eps34, a.tau, a.bound != 0, a.mlp_frag, *lsm, t & 31, eRJ, eLJ, eR, eL);
+            net_rows += learned_cell_edges<NS>(stencil, eps34, a.tau, a.bound != 0, a.mlp_frag, *lsm, t & 31, eRJ, eLJ,
+                                                  eR, eL);
 #pragma unroll
             for (int q = 0; q < NS; ++q) {
                 float x1 = live ? __ldg(wr + q * nc + mk[1]) : 0.f;
@@ -924,6 +934,9 @@ __global__ void __launch_bounds__(kStreamThreads) sweep_x_stream_kernel(const Sw
         }
         __syncthreads();
     }
+    if constexpr (LEARNED) {
+        if ((threadIdx.x & 31) == 0 && net_rows && a.net_rows) atomicAdd(a.net_rows, net_rows);
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -980,6 +993,7 @@ __device__ __forceinline__ void sweep_yz_stream_body(const SweepArgs& a) {
         __shared__ LearnSmem<NS> lbuf[kRowsPerChunk];
         lsm = &lbuf[row];
     }
+    unsigned long long net_rows = 0;  // learned form: network rows of this warp
     // cell i along DIR (ghost-mapped) of this lane's column
     auto load = [&](int i, Real* out) {
         bool flip = false;
@@ -1022,8 +1036,8 @@ __device__ __forceinline__ void sweep_yz_stream_body(const SweepArgs& a) {
                     for (int k = 0; k < 4; ++k) dd[k] = v5[k + 1] - v5[k];
                     return v5[2];
                 };
-                learned_cell_edges<NS>(stencil, eps34, a.tau, a.bound != 0, a.mlp_frag, *lsm, lane, eRJ, eLJ, eR,
-                                       eL);
+                net_rows += learned_cell_edges<NS>(stencil, eps34, a.tau, a.bound != 0, a.mlp_frag, *lsm, lane, eRJ,
+                                                   eLJ, eR, eL);
 #pragma unroll
                 for (int q = 0; q < NS; ++q) {
                     cell[q] = ring[slot(c)][q][lane];
@@ -1096,6 +1110,9 @@ __device__ __forceinline__ void sweep_yz_stream_body(const SweepArgs& a) {
             sh_F[NS][0][lane] = sh_F[NS][kRowsPerChunk][lane];
         }
         __syncthreads();
+    }
+    if constexpr (LEARNED) {
+        if ((threadIdx.x & 31) == 0 && net_rows && a.net_rows) atomicAdd(a.net_rows, net_rows);
     }
 }
 

@@ -48,6 +48,54 @@ def test_ideal_weight_network_reproduces_linear_weno5(m, n, nf, bc):
     assert err.max() <= 2e-5, err
 
 
+def _random_network(seed):
+    """A network whose weights depend strongly on the stencil (logits of order 1)."""
+    from oracle import mlp
+    p = mlp.unpack(mlp.init_params(seed))
+    rng = np.random.default_rng(seed + 100)
+    p["W3"] = rng.normal(0.0, 0.6, p["W3"].shape)
+    p["b3"] = rng.normal(0.0, 0.3, 3)
+    return mlp.pack(p).astype(np.float32)
+
+
+@pytest.mark.parametrize("n,nf", [((16, 16, 16), 2), ((37, 21), 3)])
+def test_fused_network_matches_reference_edge_by_edge(m, n, nf, capsys):
+    """Every edge through the network (sensor and range safeguard off) on a
+    noisy periodic field: the GPU learned RHS against the CPU reference that
+    rounds to BF16 where the tensor cores do.  The same reference with each
+    stencil given its neighbour's weights (an off-by-one in the warp's packing
+    of network rows) must miss by far more than the tolerance.
+
+    Tolerance: the GPU forms the inputs from FP32 primitives, the reference
+    from FP64 ones, so an input near a BF16 rounding boundary can round the
+    other way, moving it by one BF16 ulp.  The whole effect of BF16 rounding
+    (rounded against unrounded reference) is 1.5e-3 at 16^3 in this metric, so
+    2e-3 bounds any set of such flips; measured 4e-4 (16^3) and 2e-6 (37x21),
+    against 0.18 and 0.029 for the planted mistake."""
+    from learned_reference import learned_rhs
+    gam, pin = workloads.fluids(nf)
+    pb = oracle.Problem(n, (0,) * 3, (1,) * 3, (0,) * 6, gam, pin, eps=1e-6, fallback=False)
+    w = workloads.random_prims(n, nf, seed=31, jumps=False)
+    q = oracle.cons_from_prims(pb, w)
+    theta = _random_network(7)
+    R_ref, fmax = learned_rhs(pb, q, theta.astype(np.float64))
+    R_bad, _ = learned_rhs(pb, q, theta.astype(np.float64), shift=1)
+    s = m.Solver(pb.n, pb.lo, pb.hi, pb.bc, gam, pin, precision="learned", fallback=0, sensor_tau=1e30,
+                 learned_bound=0)
+    s.set_mlp(theta)
+    s.set_state(torch.from_numpy(q).cuda())
+    R = s.rhs().cpu().numpy()
+    rows = s.network_rows()
+    err = rhs_error(pb, q, R, R_ref, fmax)
+    err_bad = rhs_error(pb, q, R_bad, R_ref, fmax)
+    with capsys.disabled():
+        print("\nfused network vs reference: err %.3g (planted off-by-one %.3g), network rows %d"
+              % (err.max(), err_bad.max(), rows))
+    assert rows >= 2 * pb.sys_size * pb.ncell * pb.ndim
+    assert err.max() <= 2e-3, err
+    assert err_bad.max() >= 10 * 2e-3, err_bad
+
+
 def test_learned_form_steps_and_falls_back_safely(m):
     """A briefly trained network on the shock-bubble: finite, physical states
     over ten steps (the sensor, the range safeguard and the JS/first-order
