@@ -7,9 +7,9 @@ package.
 
 Contents (each cites the passage of arXiv 2305.09163 it follows):
   * ``mfc_oracle.c`` (loaded with ctypes): EOS (Sec. 2.1, Eq. "soe"), WENO5-JS
-    (Sec. 3.2), HLLC (Sec. 3.2.1), ghost cells (Sec. 3.3), the semi-discrete
+    and WENO3-JS (Sec. 3.2), HLLC (Sec. 3.2.1), ghost cells (Sec. 3.3), the semi-discrete
     operator (Sec. 3.1, Eq. "fvmdis") and the CFL rate.
-  * this module: SSP-RK3 (Sec. 3.4, Gottlieb & Shu TVD Runge-Kutta) and the
+  * this module: SSP-RK1/2/3 (Sec. 3.4, Gottlieb & Shu TVD Runge-Kutta) and the
     CFL time step, in plain numpy on top of the C right-hand side.
   * ``exact_riemann``: exact two-material stiffened-gas Riemann solution used to
     judge shock-tube runs.
@@ -55,6 +55,7 @@ class Params(ctypes.Structure):
         ("pi_inf", ctypes.c_double * 3),
         ("eps", ctypes.c_double),
         ("fallback", ctypes.c_int),
+        ("weno_order", ctypes.c_int),
     ]
 
 
@@ -76,6 +77,9 @@ def _load():
             lib.oracle_weno5.restype = ctypes.c_double
             lib.oracle_weno5_weights.argtypes = [dp, ctypes.c_double, dp, dp]
             lib.oracle_weno5_beta.argtypes = [dp, dp]
+            lib.oracle_weno3.argtypes = [dp, ctypes.c_double]
+            lib.oracle_weno3.restype = ctypes.c_double
+            lib.oracle_weno3_weights.argtypes = [dp, ctypes.c_double, dp, dp]
             lib.oracle_hllc.argtypes = [P, ctypes.c_int, dp, dp, dp, dp]
             lib.oracle_face.argtypes = [P, dp, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                         ctypes.c_int, dp, dp]
@@ -96,7 +100,7 @@ def _dp(a: np.ndarray):
 class Problem:
     """Grid, boundary types and fluids of one problem (Sec. 3.1 uniform grid)."""
 
-    def __init__(self, n, lo, hi, bc, gamma, pi_inf, eps=1e-6, fallback=False):
+    def __init__(self, n, lo, hi, bc, gamma, pi_inf, eps=1e-6, fallback=False, weno_order=5):
         n = list(n) + [1] * (3 - len(n))
         self.n = tuple(int(v) for v in n)
         self.ndim = 3 if self.n[2] > 1 else (2 if self.n[1] > 1 else 1)
@@ -109,6 +113,9 @@ class Problem:
         self.pi_inf = tuple(float(p) for p in pi_inf)
         self.eps = float(eps)
         self.fallback = bool(fallback)
+        if weno_order not in (3, 5):
+            raise ValueError("weno_order must be 3 or 5")
+        self.weno_order = int(weno_order)
         self.sys_size = 2 * self.nf + self.ndim
         self.ncell = self.n[0] * self.n[1] * self.n[2]
 
@@ -126,6 +133,7 @@ class Problem:
             p.pi_inf[k] = self.pi_inf[k]
         p.eps = self.eps
         p.fallback = 1 if self.fallback else 0
+        p.weno_order = self.weno_order
         return p
 
     def shape(self):
@@ -199,6 +207,20 @@ def weno5_beta(v):
     return b
 
 
+def weno3(v, eps=1e-6) -> float:
+    """Third-order WENO-JS value at i+1/2 from cells v = (i-1, i, i+1)."""
+    v = np.ascontiguousarray(v, dtype=np.float64)
+    return _load().oracle_weno3(_dp(v), eps)
+
+
+def weno3_weights(v, eps=1e-6):
+    v = np.ascontiguousarray(v, dtype=np.float64)
+    om = np.zeros(2)
+    cand = np.zeros(2)
+    _load().oracle_weno3_weights(_dp(v), eps, _dp(om), _dp(cand))
+    return om, cand
+
+
 def hllc(pb: Problem, d: int, wL, wR):
     wL = np.ascontiguousarray(wL, dtype=np.float64)
     wR = np.ascontiguousarray(wR, dtype=np.float64)
@@ -249,7 +271,23 @@ def rk3_step(pb: Problem, q, dt: float, rhs_fn=None):
     return q / 3.0 + (2.0 / 3.0) * (q2 + dt * f(q2))
 
 
-def run(pb: Problem, q, t_end: float, cfl: float, max_steps: int = 10 ** 7):
+def rk_step(pb: Problem, q, dt: float, order: int = 3, rhs_fn=None):
+    """One step of the SSP Runge-Kutta scheme of the given order (Sec. 3.4,
+    Gottlieb & Shu TVD Runge-Kutta family): 1 = forward Euler;
+    2 = q1 = q + dt R(q), q' = 1/2 q + 1/2 (q1 + dt R(q1)); 3 = rk3_step."""
+    f = rhs_fn if rhs_fn is not None else (lambda s: rhs(pb, s))
+    q = np.asarray(q, dtype=np.float64)
+    if order == 3:
+        return rk3_step(pb, q, dt, rhs_fn=f)
+    q1 = q + dt * f(q)
+    if order == 1:
+        return q1
+    if order == 2:
+        return 0.5 * q + 0.5 * (q1 + dt * f(q1))
+    raise ValueError("order must be 1, 2 or 3")
+
+
+def run(pb: Problem, q, t_end: float, cfl: float, max_steps: int = 10 ** 7, rk_order: int = 3):
     """March to t_end with CFL time steps, clipping the last step to hit t_end."""
     t = 0.0
     steps = 0
@@ -258,7 +296,7 @@ def run(pb: Problem, q, t_end: float, cfl: float, max_steps: int = 10 ** 7):
         dt = cfl_dt(pb, q, cfl)
         if t + dt > t_end:
             dt = t_end - t
-        q = rk3_step(pb, q, dt)
+        q = rk_step(pb, q, dt, rk_order)
         t += dt
         steps += 1
     return q, t, steps

@@ -20,7 +20,10 @@
  *     volume-fraction rows and div(u) from face velocities (Sec. 3.1, last eq.).
  *   - Reconstruction (Sec. 3.2): WENO5-JS on the primitive variables
  *     (a_k r_k, u, p, a_k), one variable at a time, textbook Jiang-Shu
- *     candidates, smoothness indicators and ideal weights (0.1, 0.6, 0.3).
+ *     candidates, smoothness indicators and ideal weights (0.1, 0.6, 0.3);
+ *     or, with weno_order = 3, the third-order variant the section also
+ *     names (k = 2 candidates of two cells, ideal weights (1/3, 2/3),
+ *     smoothness indicators the squared one-sided differences).
  *   - Riemann solver (Sec. 3.2.1): HLLC, Davis wave-speed estimates, star states
  *     with continuity of normal velocity and pressure, four-branch flux.
  *     Face velocity = HLLC flux of a volume fraction divided by that fraction.
@@ -53,6 +56,7 @@ typedef struct {
     double pi_inf[OR_MAXF];
     double eps;        /* WENO epsilon */
     int fallback;      /* first-order fallback at non-physical faces */
+    int weno_order;    /* 5 (default) or 3 */
 } oracle_params;
 
 /* ---- variable indexing (conserved and primitive share positions) ---- */
@@ -196,6 +200,32 @@ void oracle_weno5_beta(const double *v, double *beta) {
     t = 3.0 * v[2] - 4.0 * v[3] + v[4]; beta[2] += 0.25 * t * t;
 }
 
+/* ---- WENO3-JS (Sec. 3.2, the third-order variant: (2k-1)th order with k = 2) ----
+ * v[0..2] = values of cells i-1..i+1; returns the left-biased value at i+1/2.
+ * Candidates: the linear interpolants of cells (i-1, i) and (i, i+1) at
+ * i+1/2; ideal weights 1/3 and 2/3 (their combination is the third-order
+ * interpolant of the three cells); smoothness indicators the squares of the
+ * candidates' differences.  The value at i-1/2 is the same call on the
+ * reversed stencil.
+ */
+void oracle_weno3_weights(const double *v, double eps, double *omega, double *cand) {
+    double p0 = -0.5 * v[0] + 1.5 * v[1];
+    double p1 = 0.5 * v[1] + 0.5 * v[2];
+    double b0 = (v[1] - v[0]) * (v[1] - v[0]);
+    double b1 = (v[2] - v[1]) * (v[2] - v[1]);
+    double a0 = (1.0 / 3.0) / ((eps + b0) * (eps + b0));
+    double a1 = (2.0 / 3.0) / ((eps + b1) * (eps + b1));
+    double s = a0 + a1;
+    omega[0] = a0 / s; omega[1] = a1 / s;
+    if (cand) { cand[0] = p0; cand[1] = p1; }
+}
+
+double oracle_weno3(const double *v, double eps) {
+    double om[2], c[2];
+    oracle_weno3_weights(v, eps, om, c);
+    return om[0] * c[0] + om[1] * c[1];
+}
+
 /* ---- physical flux in direction d of a primitive state (Sec. 2.1 equations) ---- */
 static void physical_flux(const oracle_params *P, int d, const double *w, double *F) {
     int ns = sys_size(P);
@@ -333,10 +363,17 @@ int oracle_face(const oracle_params *P, const double *q, int d, int i, int j, in
     double wL[OR_MAXV], wR[OR_MAXV];
     for (int v = 0; v < ns; ++v) {
         double st[5];
-        for (int s = 0; s < 5; ++s) st[s] = w[s][v];       /* cells -3..+1, centre -1 */
-        wL[v] = oracle_weno5(st, P->eps);
-        for (int s = 0; s < 5; ++s) st[s] = w[5 - s][v];   /* cells +2..-2, centre 0 */
-        wR[v] = oracle_weno5(st, P->eps);
+        if (P->weno_order == 3) {
+            for (int s = 0; s < 3; ++s) st[s] = w[1 + s][v];   /* cells -2..0, centre -1 */
+            wL[v] = oracle_weno3(st, P->eps);
+            for (int s = 0; s < 3; ++s) st[s] = w[4 - s][v];   /* cells +1..-1, centre 0 */
+            wR[v] = oracle_weno3(st, P->eps);
+        } else {
+            for (int s = 0; s < 5; ++s) st[s] = w[s][v];       /* cells -3..+1, centre -1 */
+            wL[v] = oracle_weno5(st, P->eps);
+            for (int s = 0; s < 5; ++s) st[s] = w[5 - s][v];   /* cells +2..-2, centre 0 */
+            wR[v] = oracle_weno5(st, P->eps);
+        }
     }
     int fb = 0;
     if (P->fallback && !(face_state_ok(P, wL) && face_state_ok(P, wR))) {
