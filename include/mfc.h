@@ -76,8 +76,13 @@ mfc_status mfc_init(mfc_ctx** out, int nx, int ny, int nz, const double lo[3], c
                     int precision, void* cuda_stream);
 
 /* Set a numerical parameter by name:
- *   "weno_eps"   epsilon of the WENO5-JS weights (Sec. 3.2), default 1e-6,
+ *   "weno_eps"   epsilon of the WENO weights (Sec. 3.2), default 1e-6,
  *                valid range [1e-30, 1];
+ *   "weno_order" 5 (default): WENO5-JS; 3: WENO3-JS, the third-order variant
+ *                of Sec. 3.2 (FP64 and mixed forms; the learned form needs 5);
+ *   "rk_order"   order of the SSP Runge-Kutta step of mfc_step (Sec. 3.4):
+ *                3 (default), 2 (q1 = q + dt R(q), q' = 1/2 q + 1/2 (q1 + dt R(q1)))
+ *                or 1 (forward Euler);
  *   "fallback"   1 (default) / 0: first-order reconstruction (Sec. 3.2) at a
  *                face whose reconstructed state is non-physical;
  *   "segment"    cells per thread along a sweep (8..256), 0 = automatic;
@@ -111,9 +116,11 @@ mfc_status mfc_get_state(mfc_ctx* ctx, double* q, int on_device);
  * Errors: MFC_ERR_STATE_UNSET, MFC_ERR_ARG (NULL rhs), MFC_ERR_CUDA. */
 mfc_status mfc_rhs(mfc_ctx* ctx, double* rhs, int on_device);
 
-/* Advance the state by one SSP-RK3 step of size dt (Sec. 3.4):
+/* Advance the state by one SSP Runge-Kutta step of size dt (Sec. 3.4); with
+ * the default rk_order 3:
  *   q1 = q + dt R(q); q2 = 3/4 q + 1/4 (q1 + dt R(q1)); q' = 1/3 q + 2/3 (q2 + dt R(q2)).
- * Enqueued on the stream; returns without waiting.
+ * (rk_order 2 and 1: see mfc_set_param.)  Enqueued on the stream; returns
+ * without waiting.
  * Errors: MFC_ERR_STATE_UNSET, MFC_ERR_ARG (dt not finite or <= 0), MFC_ERR_CUDA. */
 mfc_status mfc_step(mfc_ctx* ctx, double dt);
 

@@ -49,6 +49,8 @@ struct mfc_ctx {
     double tau = 30.0;        // learned form: sensor threshold
     int yz_stream = -1;       // y/z sweep kernel: -1 automatic, 0 marching, 1 stream
     int bound = 1;            // learned form: range safeguard
+    int weno_order = 5;       // reconstruction: WENO5-JS or WENO3-JS
+    int rk_order = 3;         // SSP Runge-Kutta order of mfc_step: 1, 2 or 3
 
     Geometry g{};
     EosConst e{};
@@ -133,6 +135,20 @@ cudaError_t dispatch_sweep(const mfc_ctx* c, const SweepArgs& a, int dir) {
             case 1: return launch_sweep<float, 1, true>(a, c->ndim, dir, c->stream);
             case 2: return launch_sweep<float, 2, true>(a, c->ndim, dir, c->stream);
             default: return launch_sweep<float, 3, true>(a, c->ndim, dir, c->stream);
+        }
+    }
+    if (c->weno_order == 3) {
+        if (is_f32(c)) {
+            switch (c->nf) {
+                case 1: return launch_sweep<float, 1, false, 3>(a, c->ndim, dir, c->stream);
+                case 2: return launch_sweep<float, 2, false, 3>(a, c->ndim, dir, c->stream);
+                default: return launch_sweep<float, 3, false, 3>(a, c->ndim, dir, c->stream);
+            }
+        }
+        switch (c->nf) {
+            case 1: return launch_sweep<double, 1, false, 3>(a, c->ndim, dir, c->stream);
+            case 2: return launch_sweep<double, 2, false, 3>(a, c->ndim, dir, c->stream);
+            default: return launch_sweep<double, 3, false, 3>(a, c->ndim, dir, c->stream);
         }
     }
     if (is_f32(c)) {
@@ -387,6 +403,14 @@ mfc_status mfc_set_param(mfc_ctx* c, const char* name, double value) {
     } else if (!strcmp(name, "sensor_tau")) {
         if (!(value >= 1.0 && value <= 1e30)) return fail(c, MFC_ERR_ARG, "sensor_tau must lie in [1, 1e30]");
         c->tau = value;
+    } else if (!strcmp(name, "weno_order")) {
+        if (value != 3.0 && value != 5.0) return fail(c, MFC_ERR_ARG, "weno_order must be 3 or 5");
+        if (value == 3.0 && c->precision == MFC_LEARNED)
+            return fail(c, MFC_ERR_ARG, "the learned form replaces the WENO5 weights (weno_order 5)");
+        c->weno_order = (int)value;
+    } else if (!strcmp(name, "rk_order")) {
+        if (value != 1.0 && value != 2.0 && value != 3.0) return fail(c, MFC_ERR_ARG, "rk_order must be 1, 2 or 3");
+        c->rk_order = (int)value;
     } else if (!strcmp(name, "profile")) {
         if (value != 0.0 && value != 1.0) return fail(c, MFC_ERR_ARG, "profile must be 0 or 1");
         c->profile = value != 0.0;
@@ -469,11 +493,28 @@ mfc_status mfc_step(mfc_ctx* c, double dt) {
     if (!c->state_set) return fail(c, MFC_ERR_STATE_UNSET, "no state set");
     if (!(dt > 0.0) || !std::isfinite(dt)) return fail(c, MFC_ERR_ARG, "dt must be finite and > 0");
     if (c->precision == MFC_LEARNED && !c->mlp) return fail(c, MFC_ERR_ARG, "learned mode needs mfc_set_mlp");
-    // stage 1: q1 = q + dt R(q)
     if (!c->w_valid) {
         s = run_prims(c, c->q, false);
         if (s != MFC_OK) return s;
     }
+    if (c->rk_order == 1) {
+        // forward Euler, in place: q = q + dt R(q)
+        RkStage st{c->q, c->q, c->q, 0.0, 1.0, dt};
+        if ((s = run_sweeps(c, nullptr, &st)) != MFC_OK) return s;
+        c->w_valid = false;
+        return MFC_OK;
+    }
+    if (c->rk_order == 2) {
+        // SSP-RK2: q1 = q + dt R(q); q = 1/2 q + 1/2 (q1 + dt R(q1))
+        RkStage st1{c->q, c->q, c->q1, 0.0, 1.0, dt};
+        if ((s = run_sweeps(c, nullptr, &st1)) != MFC_OK) return s;
+        if ((s = run_prims(c, c->q1, false)) != MFC_OK) return s;
+        RkStage st2{c->q, c->q1, c->q, 0.5, 0.5, dt};
+        if ((s = run_sweeps(c, nullptr, &st2)) != MFC_OK) return s;
+        c->w_valid = false;
+        return MFC_OK;
+    }
+    // SSP-RK3, stage 1: q1 = q + dt R(q)
     RkStage st1{c->q, c->q, c->q1, 0.0, 1.0, dt};
     if ((s = run_sweeps(c, nullptr, &st1)) != MFC_OK) return s;
     // stage 2: q1 = 3/4 q + 1/4 (q1 + dt R(q1))

@@ -80,6 +80,7 @@ struct SweepArgs {
     int bound;              // learned form: range safeguard on learned edge values
     EosConstF ef;           // FP32 kernels: e, eps * 3/4 and g.inv_dx in FP32
     float eps34f;
+    float epsf;
     float inv_dxf[3];
 };
 
@@ -92,6 +93,7 @@ inline void sweep_set_f32_constants(SweepArgs& a) {
         a.ef.dP[k] = (float)a.e.dP[k];
     }
     a.eps34f = (float)(0.75 * a.eps);
+    a.epsf = (float)a.eps;
     for (int d = 0; d < 3; ++d) a.inv_dxf[d] = (float)a.g.inv_dx[d];
 }
 
@@ -225,6 +227,50 @@ __device__ __forceinline__ void weno5_edges(float vc, const float D[4], float ep
     eR = vc + __fdividef(fmaf(wr0, m0, fmaf(wl1, m1, wr2 * m2)), wr0 + wl1 + wr2);
 }
 
+// ---------------------------------------------------------------------------
+// WENO3-JS (the third-order variant of Sec. 3.2: k = 2 candidates) for the
+// edges at c+1/2 (eL) and c-1/2 (eR) from a = v_c - v_{c-1}, b = v_{c+1} - v_c.
+// With t0 = eps + a^2, t1 = eps + b^2 the weights of the candidates
+// v_c + a/2 (cells c-1, c; ideal 1/3) and v_c + b/2 (cells c, c+1; ideal 2/3)
+// are proportional to t1^2 and 2 t0^2, so
+//   eL = v_c + (t1^2 a + 2 t0^2 b) / (2 (t1^2 + 2 t0^2))
+// and, mirrored, eR = v_c - (t0^2 b + 2 t1^2 a) / (2 (t0^2 + 2 t1^2)).
+// FP64: one reciprocal of the product of the two denominators serves both
+// edges (t^2 <= ~1e40 for physical data, far inside the FP64 range).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void weno3_edges(double vc, double a, double b, double eps, double& eR, double& eL) {
+    const double t0 = fma(a, a, eps), t1 = fma(b, b, eps);
+    const double s0 = t0 * t0, s1 = t1 * t1;
+    const double dL = fma(2.0, s0, s1), dR = fma(2.0, s1, s0);
+    const double hr = 0.5 * rcp_nr(dL * dR);
+    const double nL = fma(2.0 * s0, b, s1 * a), nR = fma(2.0 * s1, a, s0 * b);
+    eL = fma(nL * dR, hr, vc);
+    eR = fma(-(nR * dL), hr, vc);
+}
+
+// FP32: t^2 can overflow FP32 (a pressure jump of 1e9 Pa gives t ~ 1e18), so
+// both t are scaled by their minimum first: g_r = min(t0, t1)/t_r <= 1.
+__device__ __forceinline__ void weno3_edges(float vc, float a, float b, float eps, float& eR, float& eL) {
+    const float t0 = fmaf(a, a, eps), t1 = fmaf(b, b, eps);
+    const float m = fminf(t0, t1);
+    float g0 = __fdividef(m, t0), g1 = __fdividef(m, t1);
+    g0 *= g0;
+    g1 *= g1;
+    // weights proportional to g0/3 and 2 g1/3 at c+1/2, g1/3 and 2 g0/3 at c-1/2
+    eL = vc + 0.5f * __fdividef(fmaf(2.f * g1, b, g0 * a), fmaf(2.f, g1, g0));
+    eR = vc - 0.5f * __fdividef(fmaf(2.f * g0, a, g1 * b), fmaf(2.f, g0, g1));
+}
+
+// Edge values of the reconstruction of order ORDER (3 or 5) from the four
+// differences D across cells c-2..c+2; epsw is the epsilon as the order's
+// edge function takes it (3/4 eps for WENO5, eps for WENO3).
+template <int ORDER, typename Real>
+__device__ __forceinline__ void weno_edges(Real vc, const Real D[4], Real epsw, Real& eR, Real& eL) {
+    static_assert(ORDER == 3 || ORDER == 5, "WENO3 or WENO5");
+    if constexpr (ORDER == 3) weno3_edges(vc, D[1], D[2], epsw, eR, eL);
+    else weno5_edges(vc, D, epsw, eR, eL);
+}
+
 template <typename Real> struct EosR {
     Real G_N, P_N, dG[2], dP[2];
     __device__ __forceinline__ explicit EosR(const EosConst& e)
@@ -248,6 +294,12 @@ template <typename Real>
 __device__ __forceinline__ Real sweep_eps34(const SweepArgs& a) {
     if constexpr (sizeof(Real) == 4) return a.eps34f;
     else return (Real)(0.75 * a.eps);
+}
+template <typename Real, int ORDER>
+__device__ __forceinline__ Real sweep_epsw(const SweepArgs& a) {
+    if constexpr (ORDER == 5) return sweep_eps34<Real>(a);
+    else if constexpr (sizeof(Real) == 4) return a.epsf;
+    else return (Real)a.eps;
 }
 template <typename Real>
 __device__ __forceinline__ Real sweep_inv_dx(const SweepArgs& a, int d) {
@@ -626,9 +678,10 @@ __device__ __forceinline__ void finish_cell(const SweepArgs& a, long long idx, c
 // lanes of a warp run the same number of iterations, which the tensor-core
 // network of the learned form (LEARNED) requires.
 // ---------------------------------------------------------------------------
-template <typename Real, int NF, int NDIM, int DIR, bool LEARNED = false>
+template <typename Real, int NF, int NDIM, int DIR, bool LEARNED = false, int ORDER = 5>
 __global__ void __launch_bounds__(128) sweep_kernel(const SweepArgs a) {
     static_assert(!LEARNED || sizeof(Real) == 4, "the learned form runs in FP32");
+    static_assert(!LEARNED || ORDER == 5, "the learned form replaces the WENO5 weights");
     using Lay = Layout<NF, NDIM>;
     constexpr int NS = Lay::NS, IM = Lay::IM;
     constexpr int T1 = (DIR == 0) ? 1 : 0;
@@ -652,7 +705,7 @@ __global__ void __launch_bounds__(128) sweep_kernel(const SweepArgs a) {
     const int s0 = sg * a.seg;
     const int s1 = min(s0 + a.seg, nd);
     const int bclo = a.g.bc_lo[DIR], bchi = a.g.bc_hi[DIR];
-    const Real eps34 = sweep_eps34<Real>(a);
+    const Real eps34 = sweep_epsw<Real, ORDER>(a);  // 3/4 eps (WENO5) or eps (WENO3)
     const EosR<Real> e = sweep_eos<Real>(a);
     const Real inv_dx = sweep_inv_dx<Real>(a, DIR);
     LearnSmem<NS>* lsm = nullptr;
@@ -707,7 +760,7 @@ __global__ void __launch_bounds__(128) sweep_kernel(const SweepArgs a) {
                                                   eL);
         } else {
 #pragma unroll
-            for (int v = 0; v < NS; ++v) weno5_edges(vc[v], D[v], eps34, eR[v], eL[v]);
+            for (int v = 0; v < NS; ++v) weno_edges<ORDER>(vc[v], D[v], eps34, eR[v], eL[v]);
         }
         if (c >= s0) {
             Real F[NS], ut;
@@ -762,9 +815,10 @@ __global__ void __launch_bounds__(128) sweep_kernel(const SweepArgs a) {
 // ---------------------------------------------------------------------------
 constexpr int kStreamThreads = 128;
 
-template <typename Real, int NF, int NDIM, bool LEARNED = false>
+template <typename Real, int NF, int NDIM, bool LEARNED = false, int ORDER = 5>
 __global__ void __launch_bounds__(kStreamThreads) sweep_x_stream_kernel(const SweepArgs a) {
     static_assert(!LEARNED || sizeof(Real) == 4, "the learned form runs in FP32");
+    static_assert(!LEARNED || ORDER == 5, "the learned form replaces the WENO5 weights");
     using Lay = Layout<NF, NDIM>;
     constexpr int NS = Lay::NS, IM = Lay::IM;
     constexpr int NJ = LEARNED ? NS : 1;
@@ -780,7 +834,7 @@ __global__ void __launch_bounds__(kStreamThreads) sweep_x_stream_kernel(const Sw
     const long long own1 = min(own0 + a.slots_per_block, total);
     const long long nc = a.g.ncell;
     const int bclo = a.g.bc_lo[0], bchi = a.g.bc_hi[0];
-    const Real eps34 = sweep_eps34<Real>(a);
+    const Real eps34 = sweep_epsw<Real, ORDER>(a);  // 3/4 eps (WENO5) or eps (WENO3)
     const EosR<Real> e = sweep_eos<Real>(a);
     const Real inv_dx = sweep_inv_dx<Real>(a, 0);
     const int t = threadIdx.x;
@@ -881,7 +935,7 @@ __global__ void __launch_bounds__(kStreamThreads) sweep_x_stream_kernel(const Sw
         }
         if (!LEARNED && live) {
 #pragma unroll
-            for (int q = 0; q < NS; ++q) weno5_edges(vcv[q], Dv[q], eps34, eR[q], eL[q]);
+            for (int q = 0; q < NS; ++q) weno_edges<ORDER>(vcv[q], Dv[q], eps34, eR[q], eL[q]);
         }
         if constexpr (!LEARNED) {
 #pragma unroll
@@ -953,8 +1007,9 @@ __global__ void __launch_bounds__(kStreamThreads) sweep_x_stream_kernel(const Sw
 // ---------------------------------------------------------------------------
 constexpr int kRowsPerChunk = 4;
 
-template <typename Real, int NF, int NDIM, int DIR, bool LEARNED>
+template <typename Real, int NF, int NDIM, int DIR, bool LEARNED, int ORDER>
 __device__ __forceinline__ void sweep_yz_stream_body(const SweepArgs& a) {
+    static_assert(!LEARNED || ORDER == 5, "the learned form replaces the WENO5 weights");
     static_assert(DIR == 1 || DIR == 2, "y or z");
     static_assert(!LEARNED || sizeof(Real) == 4, "the learned form runs in FP32");
     using Lay = Layout<NF, NDIM>;
@@ -985,7 +1040,7 @@ __device__ __forceinline__ void sweep_yz_stream_body(const SweepArgs& a) {
     const int s0 = sg * a.seg;
     const int s1 = min(s0 + a.seg, nd);
     const int bclo = a.g.bc_lo[DIR], bchi = a.g.bc_hi[DIR];
-    const Real eps34 = sweep_eps34<Real>(a);
+    const Real eps34 = sweep_epsw<Real, ORDER>(a);  // 3/4 eps (WENO5) or eps (WENO3)
     const EosR<Real> e = sweep_eos<Real>(a);
     const Real inv_dx = sweep_inv_dx<Real>(a, DIR);
     LearnSmem<NS>* lsm = nullptr;
@@ -1058,7 +1113,7 @@ __device__ __forceinline__ void sweep_yz_stream_body(const SweepArgs& a) {
                     cm1[q] = v1;
                 }
 #pragma unroll
-                for (int q = 0; q < NS; ++q) weno5_edges(cell[q], Dv[q], eps34, eR[q], eL[q]);
+                for (int q = 0; q < NS; ++q) weno_edges<ORDER>(cell[q], Dv[q], eps34, eR[q], eL[q]);
             }
 #pragma unroll
             for (int q = 0; q < NS; ++q) {
@@ -1120,14 +1175,14 @@ __device__ __forceinline__ void sweep_yz_stream_body(const SweepArgs& a) {
 // entry with a register bound (4 CTAs per SM for two fluids) so that enough
 // warps stay resident; the mixed form keeps the compiler's own allocation,
 // which schedules its loads better.
-template <typename Real, int NF, int NDIM, int DIR>
+template <typename Real, int NF, int NDIM, int DIR, int ORDER = 5>
 __global__ void __launch_bounds__(32 * kRowsPerChunk) sweep_yz_stream_kernel(const SweepArgs a) {
-    sweep_yz_stream_body<Real, NF, NDIM, DIR, false>(a);
+    sweep_yz_stream_body<Real, NF, NDIM, DIR, false, ORDER>(a);
 }
 
 template <int NF, int NDIM, int DIR>
 __global__ void __launch_bounds__(32 * kRowsPerChunk, NF <= 2 ? 4 : 3) sweep_yz_stream_learned_kernel(const SweepArgs a) {
-    sweep_yz_stream_body<float, NF, NDIM, DIR, true>(a);
+    sweep_yz_stream_body<float, NF, NDIM, DIR, true, 5>(a);
 }
 
 // ---------------------------------------------------------------------------
