@@ -44,6 +44,18 @@ CFL = 0.3
 #   WENO5 edges (both sides of a cell) 70 per variable x 7, HLLC 87 per face,
 #   flux difference + alpha div(u) source 18 per cell.
 FLOP_SWEEP_CELL_3D_2F = 70 * 7 + 87 + 18
+# The same with the third-order reconstruction: WENO3 edges (both sides) 31 per
+# variable (two differences, t = eps + d^2, t^2, the two weight denominators
+# and their product, one reciprocal, the two numerators and the two edges).
+FLOP_SWEEP_CELL_3D_2F_W3 = 31 * 7 + 87 + 18
+# Forms the bench can time: name -> (precision, extra solver parameters).
+FORMS = {
+    "fp64": ("fp64", {}),
+    "mixed": ("mixed", {}),
+    "learned": ("learned", {}),
+    "fp64_weno3": ("fp64", {"weno_order": 3}),
+    "mixed_weno3": ("mixed", {"weno_order": 3}),
+}
 # RK3 stage epilogue in the last sweep: 6 per variable (stages 2, 3), 4 in stage 1
 FLOP_RK_CELL_2F = 7 * (6 + 6 + 4) / 3.0
 # Nominal FP64 peak: 152 SMs x 4 FP64 FLOP/clk/SM (2 DFMA) x 2.07 GHz
@@ -171,11 +183,12 @@ def _sweep_profile(prof):
     return ms, n
 
 
-def time_form(m, torch, wl, w_dev, precision, steps, warmup, dist_barrier, sampler_gpu=None, mlp=None):
-    """Warm up, then time `steps` steps (CFL + SSP-RK3) with CUDA events on the
-    solver's stream.  Returns a dict of measurements."""
+def time_form(m, torch, wl, w_dev, form, steps, warmup, dist_barrier, sampler_gpu=None, mlp=None):
+    """Warm up, then time `steps` steps (CFL + SSP-RK3) of one form (FORMS) with
+    CUDA events on the solver's stream.  Returns a dict of measurements."""
     stream = torch.cuda.current_stream()
-    s = m.Solver(wl.n, wl.lo, wl.hi, wl.bc, wl.gamma, wl.pi_inf, precision=precision, fallback=1)
+    precision, params = FORMS[form]
+    s = m.Solver(wl.n, wl.lo, wl.hi, wl.bc, wl.gamma, wl.pi_inf, precision=precision, fallback=1, **params)
     if mlp is not None:
         s.set_mlp(mlp)
     s.set_state_prim(w_dev)
@@ -403,7 +416,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
     ap.add_argument("--n", type=int, default=256, help="cells per direction of the shock-bubble cube")
-    ap.add_argument("--forms", default="fp64,mixed,learned", help="comma list of fp64,mixed,learned")
+    ap.add_argument("--forms", default="fp64,mixed,learned,fp64_weno3,mixed_weno3",
+                    help="comma list of " + ",".join(FORMS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--accuracy", action="store_true",
@@ -440,6 +454,9 @@ def main():
     cells = wl.ncell
     ns = wl.sys_size
     forms = [f.strip() for f in args.forms.split(",") if f.strip()]
+    for f in forms:
+        if f not in FORMS:
+            raise SystemExit("unknown form %r (known: %s)" % (f, ", ".join(FORMS)))
     results = {}
     training = None
     head = "fp64" if "fp64" in forms else forms[0]
@@ -493,9 +510,16 @@ def main():
         stages = r["sweep_launches"] / 3.0
         peaks = _measured_peaks()
         hbm = float(peaks.get("hbm_gbs", 6800.0))
-        if form == "mixed":
+        if form == "fp64_weno3":
+            tf = (FLOP_SWEEP_CELL_3D_2F_W3 + FLOP_RK_CELL_2F / 3.0) * cells * r["sweep_launches"] / sweep_s / 1e12
+            entry["roofline"] = {"kernel": "sweep (x, y, z), WENO3", "bound": "alu", "achieved": tf,
+                                 "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": tf / FP64_PEAK_TFLOPS,
+                                 "flop_per_cell_per_sweep": FLOP_SWEEP_CELL_3D_2F_W3,
+                                 "note": "nominal FP64 peak as for the WENO5 form"}
+        elif form in ("mixed", "mixed_weno3"):
             gbs = BYTES_MIXED_SWEEPS_STAGE * cells * stages / sweep_s / 1e9
-            tf = FLOP_SWEEP_CELL_3D_2F * cells * r["sweep_launches"] / sweep_s / 1e12
+            fl = FLOP_SWEEP_CELL_3D_2F if form == "mixed" else FLOP_SWEEP_CELL_3D_2F_W3
+            tf = fl * cells * r["sweep_launches"] / sweep_s / 1e12
             entry["roofline"] = {"kernel": "sweep (x, y, z)", "hbm_gbs": gbs, "hbm_peak": hbm,
                                  "hbm_frac": gbs / hbm, "fp32_tflops": tf, "fp32_peak": FP32_PEAK_TFLOPS,
                                  "fp32_frac": tf / FP32_PEAK_TFLOPS,
