@@ -6,7 +6,8 @@ path never imports, links or calls it, and it imports nothing from the product
 package.
 
 Contents (each cites the passage of arXiv 2305.09163 it follows):
-  * ``mfc_oracle.c`` (loaded with ctypes): EOS (Sec. 2.1, Eq. "soe"), WENO5-JS
+  * ``mfc_oracle.c`` (loaded with ctypes): EOS (Sec. 2.1, Eq. "soe"), the Allaire
+    and Kapila five-equation models (Sec. 2.1), WENO5-JS
     and WENO3-JS (Sec. 3.2), HLLC (Sec. 3.2.1), ghost cells (Sec. 3.3), the semi-discrete
     operator (Sec. 3.1, Eq. "fvmdis") and the CFL rate.
   * this module: SSP-RK1/2/3 (Sec. 3.4, Gottlieb & Shu TVD Runge-Kutta) and the
@@ -56,6 +57,7 @@ class Params(ctypes.Structure):
         ("eps", ctypes.c_double),
         ("fallback", ctypes.c_int),
         ("weno_order", ctypes.c_int),
+        ("model", ctypes.c_int),
     ]
 
 
@@ -77,6 +79,7 @@ def _load():
             lib.oracle_weno5.restype = ctypes.c_double
             lib.oracle_weno5_weights.argtypes = [dp, ctypes.c_double, dp, dp]
             lib.oracle_weno5_beta.argtypes = [dp, dp]
+            lib.oracle_kapila_K.argtypes = [P, dp, dp]
             lib.oracle_weno3.argtypes = [dp, ctypes.c_double]
             lib.oracle_weno3.restype = ctypes.c_double
             lib.oracle_weno3_weights.argtypes = [dp, ctypes.c_double, dp, dp]
@@ -100,7 +103,9 @@ def _dp(a: np.ndarray):
 class Problem:
     """Grid, boundary types and fluids of one problem (Sec. 3.1 uniform grid)."""
 
-    def __init__(self, n, lo, hi, bc, gamma, pi_inf, eps=1e-6, fallback=False, weno_order=5):
+    MODELS = {"allaire": 0, "kapila": 1}
+
+    def __init__(self, n, lo, hi, bc, gamma, pi_inf, eps=1e-6, fallback=False, weno_order=5, model="allaire"):
         n = list(n) + [1] * (3 - len(n))
         self.n = tuple(int(v) for v in n)
         self.ndim = 3 if self.n[2] > 1 else (2 if self.n[1] > 1 else 1)
@@ -116,6 +121,9 @@ class Problem:
         if weno_order not in (3, 5):
             raise ValueError("weno_order must be 3 or 5")
         self.weno_order = int(weno_order)
+        if model not in self.MODELS:
+            raise ValueError("model must be 'allaire' or 'kapila'")
+        self.model = model
         self.sys_size = 2 * self.nf + self.ndim
         self.ncell = self.n[0] * self.n[1] * self.n[2]
 
@@ -134,6 +142,7 @@ class Problem:
         p.eps = self.eps
         p.fallback = 1 if self.fallback else 0
         p.weno_order = self.weno_order
+        p.model = self.MODELS[self.model]
         return p
 
     def shape(self):
@@ -205,6 +214,14 @@ def weno5_beta(v):
     b = np.zeros(3)
     _load().oracle_weno5_beta(_dp(v), _dp(b))
     return b
+
+
+def kapila_K(pb: Problem, w):
+    """Kapila coefficients K_k (k < N) of one primitive cell state (Sec. 2.1)."""
+    w = np.ascontiguousarray(w, dtype=np.float64)
+    K = np.zeros(3)
+    _load().oracle_kapila_K(ctypes.byref(pb.params()), _dp(w), _dp(K))
+    return K[:pb.nf - 1]
 
 
 def weno3(v, eps=1e-6) -> float:

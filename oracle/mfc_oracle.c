@@ -15,6 +15,8 @@
  *   - EOS (Sec. 2.1, Eq. "soe"): stiffened gas.  Mixture closure
  *     r E = Gamma p + Pi + 0.5 r |u|^2, Gamma = sum a_k/(g_k-1),
  *     Pi = sum a_k g_k pinf_k/(g_k-1); sound speed c^2 = ((Gamma+1)p+Pi)/(Gamma r).
+ *     With model = 1 the Kapila source is kept instead (the first model of
+ *     Sec. 2.1): the volume-fraction rows gain K_k div(u), see oracle_kapila_K.
  *   - Finite volumes (Sec. 3.1, Eqs. "fvm" and "fvmdis"):
  *     dq/dt = sum_d (F_{-1/2} - F_{+1/2})/dx_d - h(q) div(u), with h = -a_k in the
  *     volume-fraction rows and div(u) from face velocities (Sec. 3.1, last eq.).
@@ -57,6 +59,7 @@ typedef struct {
     double eps;        /* WENO epsilon */
     int fallback;      /* first-order fallback at non-physical faces */
     int weno_order;    /* 5 (default) or 3 */
+    int model;         /* 0: Allaire (K = 0); 1: Kapila (K div u in the alpha rows) */
 } oracle_params;
 
 /* ---- variable indexing (conserved and primitive share positions) ---- */
@@ -84,6 +87,29 @@ static void mixture(const oracle_params *P, const double *v, double *Gam, double
         Q += a[k] * P->gamma[k] * P->pi_inf[k] / (P->gamma[k] - 1.0);
     }
     *Gam = G; *Pi = Q;
+}
+
+/* ---- Kapila source coefficient (Sec. 2.1, 5-equation models) ----
+ * d(alpha_k)/dt + u . grad(alpha_k) = K_k div(u).  For two components the
+ * section gives K = (r2 c2^2 - r1 c1^2) / (r2 c2^2/a2 + r1 c1^2/a1) (its second
+ * term is printed with c2 where c1 belongs).  For N components the model of
+ * Kapila et al. (the section's reference) has
+ *     K_k = a_k (r c_W^2 / (r_k c_k^2) - 1),  1/(r c_W^2) = sum_j a_j / (r_j c_j^2),
+ * c_W the Wood mixture sound speed; for N = 2 this is the printed form.  For a
+ * stiffened gas r_k c_k^2 = g_k (p + pinf_k).  w is a primitive cell state;
+ * K receives the N-1 coefficients of the transported fractions.
+ */
+void oracle_kapila_K(const oracle_params *P, const double *w, double *K) {
+    double a[OR_MAXF], Z[OR_MAXF];
+    all_alphas(P, w, a);
+    double p = w[P->nf + P->ndim];
+    double s = 0.0;
+    for (int k = 0; k < P->nf; ++k) {
+        Z[k] = P->gamma[k] * (p + P->pi_inf[k]);
+        s += a[k] / Z[k];
+    }
+    double rcw2 = 1.0 / s;
+    for (int k = 0; k < P->nf - 1; ++k) K[k] = a[k] * (rcw2 / Z[k] - 1.0);
 }
 
 static double density(const oracle_params *P, const double *v) {
@@ -423,9 +449,16 @@ long oracle_rhs(const oracle_params *P, const double *q, double *rhs, double *fm
             for (int v = 0; v < ns; ++v)
                 rhs[(long)v * ncell + c] += (Ff[(long)v * nface + flo] - Ff[(long)v * nface + fhi]) * inv;
             double divu = (Ff[(long)ns * nface + fhi] - Ff[(long)ns * nface + flo]) * inv;
+            double K[OR_MAXF] = {0.0, 0.0, 0.0};
+            if (P->model == 1) {
+                double qc[OR_MAXV], wc[OR_MAXV];
+                for (int v = 0; v < ns; ++v) qc[v] = q[(long)v * ncell + c];
+                oracle_cons_to_prim(P, qc, wc);
+                oracle_kapila_K(P, wc, K);
+            }
             for (int a = 0; a < P->nf - 1; ++a) {
                 long o = (long)i_alpha(P, a) * ncell + c;
-                rhs[o] += q[o] * divu;
+                rhs[o] += (q[o] + K[a]) * divu;
             }
         }
         free(Ff);
@@ -462,8 +495,15 @@ void oracle_rhs_cells(const oracle_params *P, const double *q, long nsel, const 
                 if (fabs(Fhi[v]) > fm[v]) fm[v] = fabs(Fhi[v]);
             }
             double divu = (uhi - ulo) * inv;
+            double K[OR_MAXF] = {0.0, 0.0, 0.0};
+            if (P->model == 1) {
+                double qc[OR_MAXV], wc[OR_MAXV];
+                for (int v = 0; v < ns; ++v) qc[v] = q[(long)v * ncell + c];
+                oracle_cons_to_prim(P, qc, wc);
+                oracle_kapila_K(P, wc, K);
+            }
             for (int a = 0; a < P->nf - 1; ++a)
-                o[i_alpha(P, a)] += q[(long)i_alpha(P, a) * ncell + c] * divu;
+                o[i_alpha(P, a)] += (q[(long)i_alpha(P, a) * ncell + c] + K[a]) * divu;
         }
     }
     if (fmax)
