@@ -48,6 +48,9 @@ FLOP_SWEEP_CELL_3D_2F = 70 * 7 + 87 + 18
 # variable (two differences, t = eps + d^2, t^2, the two weight denominators
 # and their product, one reciprocal, the two numerators and the two edges).
 FLOP_SWEEP_CELL_3D_2F_W3 = 31 * 7 + 87 + 18
+# The Kapila model adds K (two Z_k = gamma_k (p + pinf_k), the weighted sum,
+# one reciprocal, K = alpha (Z_2/D - 1)) and its source term: 13 per cell and sweep.
+FLOP_SWEEP_CELL_3D_2F_KAPILA = FLOP_SWEEP_CELL_3D_2F + 13
 # Forms the bench can time: name -> (precision, extra solver parameters).
 FORMS = {
     "fp64": ("fp64", {}),
@@ -55,6 +58,7 @@ FORMS = {
     "learned": ("learned", {}),
     "fp64_weno3": ("fp64", {"weno_order": 3}),
     "mixed_weno3": ("mixed", {"weno_order": 3}),
+    "fp64_kapila": ("fp64", {"model": 1}),
 }
 # RK3 stage epilogue in the last sweep: 6 per variable (stages 2, 3), 4 in stage 1
 FLOP_RK_CELL_2F = 7 * (6 + 6 + 4) / 3.0
@@ -416,7 +420,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
     ap.add_argument("--n", type=int, default=256, help="cells per direction of the shock-bubble cube")
-    ap.add_argument("--forms", default="fp64,mixed,learned,fp64_weno3,mixed_weno3",
+    ap.add_argument("--forms", default="fp64,mixed,learned,fp64_weno3,mixed_weno3,fp64_kapila",
                     help="comma list of " + ",".join(FORMS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -510,11 +514,13 @@ def main():
         stages = r["sweep_launches"] / 3.0
         peaks = _measured_peaks()
         hbm = float(peaks.get("hbm_gbs", 6800.0))
-        if form == "fp64_weno3":
-            tf = (FLOP_SWEEP_CELL_3D_2F_W3 + FLOP_RK_CELL_2F / 3.0) * cells * r["sweep_launches"] / sweep_s / 1e12
-            entry["roofline"] = {"kernel": "sweep (x, y, z), WENO3", "bound": "alu", "achieved": tf,
+        if form in ("fp64_weno3", "fp64_kapila"):
+            fl = FLOP_SWEEP_CELL_3D_2F_W3 if form == "fp64_weno3" else FLOP_SWEEP_CELL_3D_2F_KAPILA
+            tf = (fl + FLOP_RK_CELL_2F / 3.0) * cells * r["sweep_launches"] / sweep_s / 1e12
+            entry["roofline"] = {"kernel": "sweep (x, y, z), " + ("WENO3" if form == "fp64_weno3" else "Kapila"),
+                                 "bound": "alu", "achieved": tf,
                                  "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": tf / FP64_PEAK_TFLOPS,
-                                 "flop_per_cell_per_sweep": FLOP_SWEEP_CELL_3D_2F_W3,
+                                 "flop_per_cell_per_sweep": fl,
                                  "note": "nominal FP64 peak as for the WENO5 form"}
         elif form in ("mixed", "mixed_weno3"):
             gbs = BYTES_MIXED_SWEEPS_STAGE * cells * stages / sweep_s / 1e9

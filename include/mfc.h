@@ -80,6 +80,10 @@ mfc_status mfc_init(mfc_ctx** out, int nx, int ny, int nz, const double lo[3], c
  *                valid range [1e-30, 1];
  *   "weno_order" 5 (default): WENO5-JS; 3: WENO3-JS, the third-order variant
  *                of Sec. 3.2 (FP64 and mixed forms; the learned form needs 5);
+ *   "model"      0 (default): Allaire five-equation model; 1: Kapila model
+ *                (Sec. 2.1), the volume-fraction rows gain K_k div(u) with
+ *                K_k = alpha_k (rho c_W^2/(rho_k c_k^2) - 1), c_W Wood's mixture
+ *                sound speed (two fluids: the formula of Sec. 2.1);
  *   "rk_order"   order of the SSP Runge-Kutta step of mfc_step (Sec. 3.4):
  *                3 (default), 2 (q1 = q + dt R(q), q' = 1/2 q + 1/2 (q1 + dt R(q1)))
  *                or 1 (forward Euler);

@@ -51,6 +51,7 @@ struct mfc_ctx {
     int bound = 1;            // learned form: range safeguard
     int weno_order = 5;       // reconstruction: WENO5-JS or WENO3-JS
     int rk_order = 3;         // SSP Runge-Kutta order of mfc_step: 1, 2 or 3
+    int kapila = 0;           // model: 0 Allaire, 1 Kapila (K div u source)
 
     Geometry g{};
     EosConst e{};
@@ -222,6 +223,11 @@ SweepArgs base_sweep(const mfc_ctx* c) {
     // consecutive cells share their stencil differences (fewer FP64 instructions)
     a.yz_stream = c->yz_stream >= 0 ? c->yz_stream : (is_f32(c) ? 1 : 0);
     a.bound = c->bound;
+    a.kapila = c->kapila;
+    for (int k = 0; k < 3; ++k) {
+        a.kgam[k] = k < c->nf ? c->gamma[k] : 1.0;
+        a.kpinf[k] = k < c->nf ? c->pi_inf[k] : 0.0;
+    }
     sweep_set_f32_constants(a);
     return a;
 }
@@ -411,6 +417,9 @@ mfc_status mfc_set_param(mfc_ctx* c, const char* name, double value) {
     } else if (!strcmp(name, "rk_order")) {
         if (value != 1.0 && value != 2.0 && value != 3.0) return fail(c, MFC_ERR_ARG, "rk_order must be 1, 2 or 3");
         c->rk_order = (int)value;
+    } else if (!strcmp(name, "model")) {
+        if (value != 0.0 && value != 1.0) return fail(c, MFC_ERR_ARG, "model must be 0 (Allaire) or 1 (Kapila)");
+        c->kapila = (int)value;
     } else if (!strcmp(name, "profile")) {
         if (value != 0.0 && value != 1.0) return fail(c, MFC_ERR_ARG, "profile must be 0 or 1");
         c->profile = value != 0.0;

@@ -78,6 +78,9 @@ struct SweepArgs {
     float tau;              // learned form: discontinuity-sensor threshold
     int yz_stream;          // y/z sweeps: 1 = stream kernel, 0 = pencil marching
     int bound;              // learned form: range safeguard on learned edge values
+    int kapila;             // 1: Kapila model, K div(u) in the volume-fraction rows
+    double kgam[3], kpinf[3];   // Kapila: gamma_k and pi_inf_k of every fluid
+    float kgamf[3], kpinff[3];
     EosConstF ef;           // FP32 kernels: e, eps * 3/4 and g.inv_dx in FP32
     float eps34f;
     float epsf;
@@ -94,6 +97,10 @@ inline void sweep_set_f32_constants(SweepArgs& a) {
     }
     a.eps34f = (float)(0.75 * a.eps);
     a.epsf = (float)a.eps;
+    for (int k = 0; k < 3; ++k) {
+        a.kgamf[k] = (float)a.kgam[k];
+        a.kpinff[k] = (float)a.kpinf[k];
+    }
     for (int d = 0; d < 3; ++d) a.inv_dxf[d] = (float)a.g.inv_dx[d];
 }
 
@@ -632,6 +639,48 @@ __device__ __forceinline__ void face_flux_learned(const SweepArgs& a, const EosR
 
 // Finish one cell: flux difference + alpha div(u) source, then the epilogue
 // selected by a.mode.
+// Kapila coefficients (Sec. 2.1, 5-equation models): the volume-fraction rows
+// carry (alpha_k + K_k) div(u) instead of alpha_k div(u), with
+//   K_k = alpha_k (rho c_W^2 / Z_k - 1),  1/(rho c_W^2) = sum_j alpha_j / Z_j,
+// Z_k = rho_k c_k^2 = gamma_k (p + pi_inf_k) for a stiffened gas (Kapila's
+// N-phase form; for two phases the formula the section prints).  Written
+// with one reciprocal: rho c_W^2 / Z_k = prod_{j != k} Z_j / sum_j alpha_j
+// prod_{i != j} Z_i.  w is the primitive state of the cell.  Not inlined:
+// the Allaire path of the sweeps keeps its instruction schedule.
+template <typename Real, int NF, int NDIM>
+__device__ __noinline__ void kapila_K(const SweepArgs& a, const Real* w, Real* K) {
+    using Lay = Layout<NF, NDIM>;
+    const Real p = w[Lay::IE];
+    Real al[NF], Z[NF];
+    Real last = (Real)1;
+#pragma unroll
+    for (int k = 0; k < NF - 1; ++k) {
+        al[k] = w[Lay::IA + k];
+        last -= al[k];
+    }
+    al[NF - 1] = last;
+#pragma unroll
+    for (int k = 0; k < NF; ++k) {
+        if constexpr (sizeof(Real) == 4) Z[k] = a.kgamf[k] * (p + a.kpinff[k]);
+        else Z[k] = a.kgam[k] * (p + a.kpinf[k]);
+    }
+    Real pe[NF];   // product of the other phases' Z
+#pragma unroll
+    for (int k = 0; k < NF; ++k) {
+        Real t = (Real)1;
+#pragma unroll
+        for (int j = 0; j < NF; ++j)
+            if (j != k) t *= Z[j];
+        pe[k] = t;
+    }
+    Real D = 0;
+#pragma unroll
+    for (int k = 0; k < NF; ++k) D = fma(al[k], pe[k], D);
+    const Real rD = real_rcp(D);
+#pragma unroll
+    for (int k = 0; k < NF - 1; ++k) K[k] = al[k] * fma(pe[k], rD, (Real)-1);
+}
+
 template <typename Real, int NF, int NDIM>
 __device__ __forceinline__ void finish_cell(const SweepArgs& a, long long idx, const Real* Fm, const Real* Fp,
                                             Real um, Real up, const Real* cell, Real inv_dx) {
@@ -641,8 +690,17 @@ __device__ __forceinline__ void finish_cell(const SweepArgs& a, long long idx, c
 #pragma unroll
     for (int v = 0; v < NS; ++v) out[v] = (Fm[v] - Fp[v]) * inv_dx;
     const Real du = (up - um) * inv_dx;
+    if constexpr (NF > 1) {
+        if (a.kapila) {
+            Real K[NF - 1];
+            kapila_K<Real, NF, NDIM>(a, cell, K);
 #pragma unroll
-    for (int k = 0; k < NF - 1; ++k) out[IA + k] = fma(cell[IA + k], du, out[IA + k]);
+            for (int k = 0; k < NF - 1; ++k) out[IA + k] = fma(cell[IA + k] + K[k], du, out[IA + k]);
+        } else {
+#pragma unroll
+            for (int k = 0; k < NF - 1; ++k) out[IA + k] = fma(cell[IA + k], du, out[IA + k]);
+        }
+    }
     const long long nc = a.g.ncell;
     Real* R = static_cast<Real*>(a.R);
     if (a.mode == 0) {
