@@ -90,8 +90,8 @@ mfc_status mfc_init(mfc_ctx** out, int nx, int ny, int nz, const double lo[3], c
  *   "fallback"   1 (default) / 0: first-order reconstruction (Sec. 3.2) at a
  *                face whose reconstructed state is non-physical;
  *   "segment"    cells per thread along a sweep (8..256), 0 = automatic;
- *   "yz_kernel"  y/z sweep kernel: -1 automatic (default: stream kernel for the
- *                FP32 paths, pencil marching for FP64), 0 marching, 1 stream;
+ *   "yz_kernel"  y/z sweep kernel: -1 automatic (default: the stream kernel),
+ *                0 pencil marching, 1 stream;
  *   "sensor_tau" learned form: the discontinuity sensor trips (WENO5-JS
  *                weights are used) where max_r b_r > tau (min_r b_r + 1e-6 s^2),
  *                b the smoothness indicators without their 4/3 factor and s the

@@ -106,7 +106,9 @@ int auto_segment(const mfc_ctx* c, int dir) {
     if (c->seg_override > 0) return c->seg_override;
     const int nd = c->n[dir];
     const long long trans = c->ncell / nd;
-    int L = 64;
+    // the FP64 stream sweeps do more work per cell: longer segments halve the
+    // recomputed edge cells (256^3 shock-bubble: 104.4 vs 105.5 ms per step)
+    int L = (!is_f32(c) && c->yz_stream != 0) ? 128 : 64;
     // keep at least ~8 warps per SM resident while limiting edge recomputation
     while (L > 8 && trans * ((nd + L - 1) / L) < 152LL * 4 * kSweepThreads) L /= 2;
     return L;
@@ -219,9 +221,10 @@ SweepArgs base_sweep(const mfc_ctx* c) {
     a.mlp_frag = c->mlp ? reinterpret_cast<const uint4*>(reinterpret_cast<const char*>(c->mlp) + kMlpFragOffset)
                         : nullptr;
     a.tau = (float)c->tau;
-    // FP32 paths use the y/z stream kernel; the FP64 path marches pencils so
-    // consecutive cells share their stencil differences (fewer FP64 instructions)
-    a.yz_stream = c->yz_stream >= 0 ? c->yz_stream : (is_f32(c) ? 1 : 0);
+    // y/z sweeps: the stream kernel (shared-memory ring) unless asked for the
+    // pencil-marching kernel; with float-float WENO weights the FP64 path is
+    // faster streamed too (256^3: 104 vs 122 ms per step)
+    a.yz_stream = c->yz_stream >= 0 ? c->yz_stream : 1;
     a.bound = c->bound;
     a.kapila = c->kapila;
     for (int k = 0; k < 3; ++k) {

@@ -25,6 +25,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "mfc_df.cuh"
 #include "mfc_mlp.cuh"
 
 namespace mfc {
@@ -179,35 +180,51 @@ __device__ __forceinline__ double rcp_nr(double d) {
 //   b2 = 4/3 [ 5/2 D2^2 - 11/4 D2 D3 + D3^2 ]   (stencil c..c+2),
 // are evaluated without the common factor 4/3, with eps scaled by 3/4 so every
 // (eps + b_r) carries the same factor and the weights are unchanged.  The
-// candidates are increments over v_c (constant data reconstructs exactly), the
-// ideal weights 1/10, 6/10, 3/10 are folded into their constants, and the two
-// weight normalisations share one reciprocal.  eps34 = 3/4 eps.
+// candidates are increments over v_c (constant data reconstructs exactly).
+// eps34 = 3/4 eps.
+//
+// FP64 path: the differences D come in as FP64 and the edge values go out as
+// FP64, but the smoothness indicators, weights and weighted increments are
+// evaluated in float-float arithmetic (mfc_df.cuh, ~48 bits): on GB300 this
+// costs 8 FP64 instructions per variable instead of ~50.  The weights are
+// normalised by m = min_r (eps + b_r), g_r = m/(eps + b_r) <= 1, so that
+// (eps + b)^2 (up to ~1e40 for a 1e9 Pa pressure jump) never meets the FP32
+// range; with ideal weights 1 : 6 : 3 (times 10) and candidates times 6
+// (integer coefficients, exact in FP32):
+//   eL - v_c = (g0^2 (5 D1 - 2 D0) + 6 g1^2 (D1 + 2 D2) + 3 g2^2 (4 D2 - D3))
+//              / (6 (g0^2 + 6 g1^2 + 3 g2^2)),
+//   eR - v_c = (g2^2 (2 D3 - 5 D2) - 6 g1^2 (2 D1 + D2) + 3 g0^2 (D0 - 4 D1))
+//              / (6 (g2^2 + 6 g1^2 + 3 g0^2)).
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ void weno5_edges(double vc, const double D[4], double eps34,
                                             double& eR, double& eL) {
-    const double S0 = D[0] * D[0], S1 = D[1] * D[1], S2 = D[2] * D[2], S3 = D[3] * D[3];
-    const double b0 = fma(2.5, S1, fma(-2.75, D[1] * D[0], S0));
-    const double b1 = fma(-1.25, D[1] * D[2], S1 + S2);
-    const double b2 = fma(2.5, S2, fma(-2.75, D[2] * D[3], S3));
-    const double t0 = eps34 + b0, t1 = eps34 + b1, t2 = eps34 + b2;
-    const double a0 = t0 * t0, a1 = t1 * t1, a2 = t2 * t2;
-    // weights d_r/a_r multiplied through by 10 a0 a1 a2
-    const double P12 = a1 * a2, P02 = a0 * a2, P01 = a0 * a1;
-    // increments at c+1/2: 1x (stencil c-2..c), 6x (c-1..c+1), 3x (c..c+2)
-    const double p0 = fma(5.0 / 6.0, D[1], (-1.0 / 3.0) * D[0]);
-    const double p1 = fma(2.0, D[2], D[1]);
-    const double p2 = fma(2.0, D[2], -0.5 * D[3]);
-    // mirrored increments at c-1/2: 1x (c..c+2), 6x (c-1..c+1), 3x (c-2..c)
-    const double m0 = fma(-5.0 / 6.0, D[2], (1.0 / 3.0) * D[3]);
-    const double m1 = fma(-2.0, D[1], -D[2]);
-    const double m2 = fma(-2.0, D[1], 0.5 * D[0]);
-    const double numL = fma(P12, p0, fma(P02, p1, P01 * p2));
-    const double denL = fma(6.0, P02, fma(3.0, P01, P12));
-    const double numR = fma(P01, m0, fma(P02, m1, P12 * m2));
-    const double denR = fma(6.0, P02, fma(3.0, P12, P01));
-    const double x = rcp_nr(denL * denR);
-    eL = fma(numL, denR * x, vc);
-    eR = fma(numR, denL * x, vc);
+    const df d0 = df_from_double(D[0]), d1 = df_from_double(D[1]);
+    const df d2 = df_from_double(D[2]), d3 = df_from_double(D[3]);
+    const df S1 = df_mul(d1, d1), S2 = df_mul(d2, d2);
+    const df b0 = df_add(df_add(df_mul(d0, d0), df_mul_f(df_mul(d1, d0), -2.75f)), df_mul_f(S1, 2.5f));
+    const df b1 = df_add(df_add(S1, S2), df_mul_f(df_mul(d1, d2), -1.25f));
+    const df b2 = df_add(df_add(df_mul(d3, d3), df_mul_f(df_mul(d2, d3), -2.75f)), df_mul_f(S2, 2.5f));
+    const df e = df_from_double(eps34);
+    const df t0 = df_add(e, b0), t1 = df_add(e, b1), t2 = df_add(e, b2);
+    const float m = fminf(t0.hi, fminf(t1.hi, t2.hi));
+    const df g0 = df_div_f(m, t0), g1 = df_div_f(m, t1), g2 = df_div_f(m, t2);
+    const df q0 = df_mul(g0, g0), q1 = df_mul_f(df_mul(g1, g1), 6.f), q2 = df_mul(g2, g2);
+    // edge at c+1/2: weights q0, q1, 3 q2
+    const df wL2 = df_mul_f(q2, 3.f);
+    const df P0 = df_add(df_mul_f(d1, 5.f), df_mul_f(d0, -2.f));
+    const df P1 = df_add(d1, df_mul_f(d2, 2.f));
+    const df P2 = df_add(df_mul_f(d2, 4.f), df_neg(d3));
+    const df numL = df_add(df_add(df_mul(q0, P0), df_mul(q1, P1)), df_mul(wL2, P2));
+    const df denL = df_mul_f(df_add(df_add(q0, q1), wL2), 6.f);
+    // edge at c-1/2: weights q2, q1, 3 q0
+    const df wR2 = df_mul_f(q0, 3.f);
+    const df M0 = df_add(df_mul_f(d3, 2.f), df_mul_f(d2, -5.f));
+    const df M1 = df_neg(df_add(df_mul_f(d1, 2.f), d2));
+    const df M2 = df_add(d0, df_mul_f(d1, -4.f));
+    const df numR = df_add(df_add(df_mul(q2, M0), df_mul(q1, M1)), df_mul(wR2, M2));
+    const df denR = df_mul_f(df_add(df_add(q2, q1), wR2), 6.f);
+    eL = vc + df_to_double(df_div(numL, denL));
+    eR = vc + df_to_double(df_div(numR, denR));
 }
 
 // FP32 variant for the mixed path.  The weights are normalised by the smallest

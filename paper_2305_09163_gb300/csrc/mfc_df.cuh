@@ -1,0 +1,93 @@
+// Float-float ("double-single") arithmetic: a value is the unevaluated sum
+// hi + lo of two FP32 numbers with |lo| <= ulp(hi)/2, about 48 significant
+// bits.  Built from the error-free transformations of Knuth (TwoSum, The Art of
+// Computer Programming vol. 2, 4.2.2), Dekker (FastTwoSum, 1971) and the
+// FMA form of TwoProduct, combined as in Hida, Li and Bailey's double-double
+// algorithms (2001).  On GB300 an FP64 instruction costs the issue time of
+// about sixty FP32 instructions, so the FP64 path evaluates its WENO weights in
+// this arithmetic: each operation is 5-20 FP32 instructions with a relative
+// error near 2^-46, far below the path's 1e-11 parity requirement.
+//
+// The explicit _rn intrinsics keep the compiler from contracting or
+// reordering the transformations.  FP32 range applies (|x| < 3.4e38); callers
+// keep their intermediates inside it.
+#pragma once
+#include <cuda_runtime.h>
+
+namespace mfc {
+
+struct df {
+    float hi, lo;
+};
+
+// s + e = a + b exactly (Knuth).
+__device__ __forceinline__ df df_two_sum(float a, float b) {
+    const float s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    const float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+    return {s, e};
+}
+
+// s + e = a + b exactly when |a| >= |b| or a = 0 (Dekker).
+__device__ __forceinline__ df df_fast_two_sum(float a, float b) {
+    const float s = __fadd_rn(a, b);
+    return {s, __fsub_rn(b, __fsub_rn(s, a))};
+}
+
+// p + e = a * b exactly (one rounding of the FMA recovers the product's error).
+__device__ __forceinline__ df df_two_prod(float a, float b) {
+    const float p = __fmul_rn(a, b);
+    return {p, __fmaf_rn(a, b, -p)};
+}
+
+// x + y, accurate also under cancellation (both parts summed error-free).
+__device__ __forceinline__ df df_add(df x, df y) {
+    df s = df_two_sum(x.hi, y.hi);
+    const df t = df_two_sum(x.lo, y.lo);
+    s = df_fast_two_sum(s.hi, __fadd_rn(s.lo, t.hi));
+    return df_fast_two_sum(s.hi, __fadd_rn(s.lo, t.lo));
+}
+
+__device__ __forceinline__ df df_neg(df x) { return {-x.hi, -x.lo}; }
+
+__device__ __forceinline__ df df_mul(df x, df y) {
+    const df p = df_two_prod(x.hi, y.hi);
+    float e = __fmaf_rn(x.hi, y.lo, p.lo);
+    e = __fmaf_rn(x.lo, y.hi, e);
+    return df_fast_two_sum(p.hi, e);
+}
+
+// x * f for an FP32 f (exact small integers keep it exact up to the rounding of x).
+__device__ __forceinline__ df df_mul_f(df x, float f) {
+    const df p = df_two_prod(x.hi, f);
+    return df_fast_two_sum(p.hi, __fmaf_rn(x.lo, f, p.lo));
+}
+
+// a / b for an FP32 a: quotient from the correctly rounded reciprocal of b.hi,
+// then one correction from the exact residual a - q1 b.
+__device__ __forceinline__ df df_div_f(float a, df b) {
+    const float y = __frcp_rn(b.hi);
+    const float q1 = __fmul_rn(a, y);
+    const df p = df_two_prod(q1, b.hi);
+    float r = __fsub_rn(__fsub_rn(a, p.hi), p.lo);
+    r = __fmaf_rn(-q1, b.lo, r);
+    return df_fast_two_sum(q1, __fmul_rn(r, y));
+}
+
+// a / b, the same correction with a float-float residual.
+__device__ __forceinline__ df df_div(df a, df b) {
+    const float y = __frcp_rn(b.hi);
+    const float q1 = __fmul_rn(a.hi, y);
+    const df r = df_add(a, df_neg(df_mul_f(b, q1)));
+    return df_fast_two_sum(q1, __fmul_rn(r.hi, y));
+}
+
+// FP64 -> float-float (48 of the 53 bits) and back.
+__device__ __forceinline__ df df_from_double(double d) {
+    const float hi = __double2float_rn(d);
+    return {hi, __double2float_rn(d - (double)hi)};
+}
+
+__device__ __forceinline__ double df_to_double(df x) { return (double)x.hi + (double)x.lo; }
+
+}  // namespace mfc

@@ -84,7 +84,7 @@ cudaError_t run(const Geometry& g, const EosConst& e, int ndim, const double* q,
         a.R = rhs;
         a.mode = d == 0 ? 0 : 1;
         a.acc_in = 0;
-        a.yz_stream = 0;
+        a.yz_stream = 1;
         a.eps = eps;
         a.fallback = fallback;
         a.fallback_count = nullptr;
