@@ -82,12 +82,32 @@ __device__ __forceinline__ df df_div(df a, df b) {
     return df_fast_two_sum(q1, __fmul_rn(r.hi, y));
 }
 
-// FP64 -> float-float (48 of the 53 bits) and back.
+// FP64 -> float-float by integer operations on the bit pattern (FP64<->FP32
+// conversion instructions run on the FP64 pipe, the scarce one on GB300): hi
+// takes the sign, the rebiased exponent and the top 23 stored significand bits
+// (a truncation, exact), lo the remaining 29 bits scaled by 2^(E-52), so
+// hi + lo equals d to ~2^-48 relative.  |d| < 2^-126 gives 0 and for
+// |d| < 2^-74 lo is dropped (absolute error < 2^-98); |d| must stay below
+// 2^128.
 __device__ __forceinline__ df df_from_double(double d) {
-    const float hi = __double2float_rn(d);
-    return {hi, __double2float_rn(d - (double)hi)};
+    const unsigned hw = (unsigned)__double2hiint(d), lw = (unsigned)__double2loint(d);
+    const unsigned sign = hw & 0x80000000u;
+    const int ef = (int)((hw >> 20) & 0x7FFu) - 1023 + 127;
+    const unsigned hb = sign | ((unsigned)ef << 23) | ((hw & 0xFFFFFu) << 3) | (lw >> 29);
+    const int es = ef - 52;
+    const float lo = __uint2float_rn(lw & 0x1FFFFFFFu) * __int_as_float(max(es, 1) << 23);
+    return {ef > 0 ? __int_as_float((int)hb) : 0.f, es > 0 ? __int_as_float(__float_as_int(lo) | (int)sign) : 0.f};
 }
 
-__device__ __forceinline__ double df_to_double(df x) { return (double)x.hi + (double)x.lo; }
+// FP32 -> FP64 by integer operations (exact for normal numbers; zero and FP32
+// subnormals give 0).
+__device__ __forceinline__ double df_widen(float f) {
+    const unsigned b = (unsigned)__float_as_int(f);
+    const unsigned ef = (b >> 23) & 0xFFu;
+    const unsigned hw = (b & 0x80000000u) | ((ef + (1023u - 127u)) << 20) | ((b & 0x7FFFFFu) >> 3);
+    return ef ? __hiloint2double((int)hw, (int)(b << 29)) : 0.0;
+}
+
+__device__ __forceinline__ double df_to_double(df x) { return df_widen(x.hi) + df_widen(x.lo); }
 
 }  // namespace mfc
