@@ -198,31 +198,34 @@ __device__ __forceinline__ double rcp_nr(double d) {
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ void weno5_edges(double vc, const double D[4], double eps34,
                                             double& eR, double& eL) {
+    // sums use the fast float-float addition: its error, ~2^-44 of the
+    // operands, is relative to the stencil's differences, far inside the
+    // path's parity tolerance; scalings by 2 and 4 are exact
     const df d0 = df_from_double(D[0]), d1 = df_from_double(D[1]);
     const df d2 = df_from_double(D[2]), d3 = df_from_double(D[3]);
     const df S1 = df_mul(d1, d1), S2 = df_mul(d2, d2);
-    const df b0 = df_add(df_add(df_mul(d0, d0), df_mul_f(df_mul(d1, d0), -2.75f)), df_mul_f(S1, 2.5f));
-    const df b1 = df_add(df_add(S1, S2), df_mul_f(df_mul(d1, d2), -1.25f));
-    const df b2 = df_add(df_add(df_mul(d3, d3), df_mul_f(df_mul(d2, d3), -2.75f)), df_mul_f(S2, 2.5f));
+    const df b0 = df_add_fast(df_add_fast(df_mul(d0, d0), df_mul_f(df_mul(d1, d0), -2.75f)), df_mul_f(S1, 2.5f));
+    const df b1 = df_add_fast(df_add_fast(S1, S2), df_mul_f(df_mul(d1, d2), -1.25f));
+    const df b2 = df_add_fast(df_add_fast(df_mul(d3, d3), df_mul_f(df_mul(d2, d3), -2.75f)), df_mul_f(S2, 2.5f));
     const df e = df_from_double(eps34);
-    const df t0 = df_add(e, b0), t1 = df_add(e, b1), t2 = df_add(e, b2);
+    const df t0 = df_add_fast(e, b0), t1 = df_add_fast(e, b1), t2 = df_add_fast(e, b2);
     const float m = fminf(t0.hi, fminf(t1.hi, t2.hi));
     const df g0 = df_div_f(m, t0), g1 = df_div_f(m, t1), g2 = df_div_f(m, t2);
     const df q0 = df_mul(g0, g0), q1 = df_mul_f(df_mul(g1, g1), 6.f), q2 = df_mul(g2, g2);
     // edge at c+1/2: weights q0, q1, 3 q2
     const df wL2 = df_mul_f(q2, 3.f);
-    const df P0 = df_add(df_mul_f(d1, 5.f), df_mul_f(d0, -2.f));
-    const df P1 = df_add(d1, df_mul_f(d2, 2.f));
-    const df P2 = df_add(df_mul_f(d2, 4.f), df_neg(d3));
-    const df numL = df_add(df_add(df_mul(q0, P0), df_mul(q1, P1)), df_mul(wL2, P2));
-    const df denL = df_mul_f(df_add(df_add(q0, q1), wL2), 6.f);
+    const df P0 = df_add_fast(df_mul_f(d1, 5.f), df_mul_pow2(d0, -2.f));
+    const df P1 = df_add_fast(d1, df_mul_pow2(d2, 2.f));
+    const df P2 = df_add_fast(df_mul_pow2(d2, 4.f), df_neg(d3));
+    const df numL = df_add_fast(df_add_fast(df_mul(q0, P0), df_mul(q1, P1)), df_mul(wL2, P2));
+    const df denL = df_mul_f(df_add_fast(df_add_fast(q0, q1), wL2), 6.f);
     // edge at c-1/2: weights q2, q1, 3 q0
     const df wR2 = df_mul_f(q0, 3.f);
-    const df M0 = df_add(df_mul_f(d3, 2.f), df_mul_f(d2, -5.f));
-    const df M1 = df_neg(df_add(df_mul_f(d1, 2.f), d2));
-    const df M2 = df_add(d0, df_mul_f(d1, -4.f));
-    const df numR = df_add(df_add(df_mul(q2, M0), df_mul(q1, M1)), df_mul(wR2, M2));
-    const df denR = df_mul_f(df_add(df_add(q2, q1), wR2), 6.f);
+    const df M0 = df_add_fast(df_mul_pow2(d3, 2.f), df_mul_f(d2, -5.f));
+    const df M1 = df_neg(df_add_fast(df_mul_pow2(d1, 2.f), d2));
+    const df M2 = df_add_fast(d0, df_mul_pow2(d1, -4.f));
+    const df numR = df_add_fast(df_add_fast(df_mul(q2, M0), df_mul(q1, M1)), df_mul(wR2, M2));
+    const df denR = df_mul_f(df_add_fast(df_add_fast(q2, q1), wR2), 6.f);
     eL = vc + df_to_double(df_div(numL, denL));
     eR = vc + df_to_double(df_div(numR, denR));
 }

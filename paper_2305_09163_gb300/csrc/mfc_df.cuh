@@ -48,7 +48,18 @@ __device__ __forceinline__ df df_add(df x, df y) {
     return df_fast_two_sum(s.hi, __fadd_rn(s.lo, t.lo));
 }
 
+// x + y with one error-free sum of the high parts ("sloppy" addition): error
+// below ~2^-44 (|x| + |y|), so relative accuracy is lost only under
+// cancellation.  Used where an absolute error of that size is harmless.
+__device__ __forceinline__ df df_add_fast(df x, df y) {
+    const df s = df_two_sum(x.hi, y.hi);
+    return df_fast_two_sum(s.hi, __fadd_rn(__fadd_rn(s.lo, x.lo), y.lo));
+}
+
 __device__ __forceinline__ df df_neg(df x) { return {-x.hi, -x.lo}; }
+
+// x * 2^k (f a power of two): exact while both parts stay normal.
+__device__ __forceinline__ df df_mul_pow2(df x, float f) { return {__fmul_rn(x.hi, f), __fmul_rn(x.lo, f)}; }
 
 __device__ __forceinline__ df df_mul(df x, df y) {
     const df p = df_two_prod(x.hi, y.hi);
