@@ -262,17 +262,23 @@ __device__ __forceinline__ void weno5_edges(float vc, const float D[4], float ep
 // are proportional to t1^2 and 2 t0^2, so
 //   eL = v_c + (t1^2 a + 2 t0^2 b) / (2 (t1^2 + 2 t0^2))
 // and, mirrored, eR = v_c - (t0^2 b + 2 t1^2 a) / (2 (t0^2 + 2 t1^2)).
-// FP64: one reciprocal of the product of the two denominators serves both
-// edges (t^2 <= ~1e40 for physical data, far inside the FP64 range).
+// FP64 path: a and b come in as FP64, the weights and weighted increments are
+// float-float (mfc_df.cuh), scaled as the FP32 variant below so nothing leaves
+// the FP32 range: g_r = min(t0, t1)/t_r <= 1, weights g0^2 and 2 g1^2 at
+// c+1/2, g1^2 and 2 g0^2 at c-1/2.
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ void weno3_edges(double vc, double a, double b, double eps, double& eR, double& eL) {
-    const double t0 = fma(a, a, eps), t1 = fma(b, b, eps);
-    const double s0 = t0 * t0, s1 = t1 * t1;
-    const double dL = fma(2.0, s0, s1), dR = fma(2.0, s1, s0);
-    const double hr = 0.5 * rcp_nr(dL * dR);
-    const double nL = fma(2.0 * s0, b, s1 * a), nR = fma(2.0 * s1, a, s0 * b);
-    eL = fma(nL * dR, hr, vc);
-    eR = fma(-(nR * dL), hr, vc);
+    const df A = df_from_double(a), Bd = df_from_double(b), E = df_from_double(eps);
+    const df t0 = df_add_fast(E, df_mul(A, A)), t1 = df_add_fast(E, df_mul(Bd, Bd));
+    const float m = fminf(t0.hi, t1.hi);
+    const df g0 = df_div_f(m, t0), g1 = df_div_f(m, t1);
+    const df s0 = df_mul(g0, g0), s1 = df_mul(g1, g1);
+    const df s0x2 = df_mul_pow2(s0, 2.f), s1x2 = df_mul_pow2(s1, 2.f);
+    const df numL = df_add_fast(df_mul(s0, A), df_mul(s1x2, Bd));
+    const df numR = df_add_fast(df_mul(s1, Bd), df_mul(s0x2, A));
+    const df denL = df_mul_pow2(df_add_fast(s0, s1x2), 2.f), denR = df_mul_pow2(df_add_fast(s1, s0x2), 2.f);
+    eL = vc + df_to_double(df_div(numL, denL));
+    eR = vc - df_to_double(df_div(numR, denR));
 }
 
 // FP32: t^2 can overflow FP32 (a pressure jump of 1e9 Pa gives t ~ 1e18), so
@@ -455,6 +461,14 @@ __device__ __forceinline__ void hllc(const Real* L, const Real* R, const Mix<Rea
     for (int k = 0; k < NF - 1; ++k) F[IA + k] = K[IA + k] * ut;
 }
 
+// Count one fallback face per calling lane with one atomic per converged
+// group of lanes (a single global counter takes every fallback of the grid).
+__device__ __forceinline__ void count_fallback(unsigned long long* counter) {
+    if (!counter) return;
+    const unsigned mask = __activemask();
+    if ((int)(threadIdx.x & 31) == __ffs((int)mask) - 1) atomicAdd(counter, (unsigned long long)__popc(mask));
+}
+
 // Face flux between reconstructed states (with the optional first-order
 // fallback to the two cell values cl | cr).
 template <typename Real, int NF, int NDIM, int DIR>
@@ -467,17 +481,39 @@ __device__ __forceinline__ void face_flux(const SweepArgs& a, const EosR<Real>& 
     if (a.fallback) {
         first = !(face_state_ok<Real, NF, NDIM>(eLs, mL) && face_state_ok<Real, NF, NDIM>(eRs, mR));
     }
-    if (first) {
-        if (a.fallback_count) atomicAdd(a.fallback_count, 1ULL);
-        Real fl[NS], fr[NS];
+    if constexpr (sizeof(Real) == 4) {
+        // FP32: a per-lane branch (the compiler schedules this form best)
+        if (first) {
+            count_fallback(a.fallback_count);
+            Real fl[NS], fr[NS];
 #pragma unroll
-        for (int v = 0; v < NS; ++v) { fl[v] = cl[v]; fr[v] = cr[v]; }
-        mL = mixture<Real, NF, NDIM>(fl, e);
-        mR = mixture<Real, NF, NDIM>(fr, e);
-        hllc<Real, NF, NDIM, DIR>(fl, fr, mL, mR, F, ut);
-    } else {
-        hllc<Real, NF, NDIM, DIR>(eLs, eRs, mL, mR, F, ut);
+            for (int v = 0; v < NS; ++v) { fl[v] = cl[v]; fr[v] = cr[v]; }
+            mL = mixture<Real, NF, NDIM>(fl, e);
+            mR = mixture<Real, NF, NDIM>(fr, e);
+            hllc<Real, NF, NDIM, DIR>(fl, fr, mL, mR, F, ut);
+        } else {
+            hllc<Real, NF, NDIM, DIR>(eLs, eRs, mL, mR, F, ut);
+        }
+        return;
     }
+    if (!__any_sync(__activemask(), first)) {
+        hllc<Real, NF, NDIM, DIR>(eLs, eRs, mL, mR, F, ut);
+        return;
+    }
+    // FP64: some lane of the warp falls back; select the states first so
+    // that the warp runs the (costly) solver once rather than once per branch
+    Real sl[NS], sr[NS];
+#pragma unroll
+    for (int v = 0; v < NS; ++v) {
+        sl[v] = first ? cl[v] : eLs[v];
+        sr[v] = first ? cr[v] : eRs[v];
+    }
+    if (first) {
+        count_fallback(a.fallback_count);
+        mL = mixture<Real, NF, NDIM>(sl, e);
+        mR = mixture<Real, NF, NDIM>(sr, e);
+    }
+    hllc<Real, NF, NDIM, DIR>(sl, sr, mL, mR, F, ut);
 }
 
 // ---------------------------------------------------------------------------
@@ -644,7 +680,7 @@ __device__ __forceinline__ void face_flux_learned(const SweepArgs& a, const EosR
                 choice = 2;
                 mL = mixture<float, NF, NDIM>(cl, e);
                 mR = mixture<float, NF, NDIM>(cr, e);
-                if (a.fallback_count) atomicAdd(a.fallback_count, 1ULL);
+                count_fallback(a.fallback_count);
             }
         }
     }
@@ -701,6 +737,44 @@ __device__ __noinline__ void kapila_K(const SweepArgs& a, const Real* w, Real* K
     for (int k = 0; k < NF - 1; ++k) K[k] = al[k] * fma(pe[k], rD, (Real)-1);
 }
 
+// The same coefficients for the FP64 path, in float-float arithmetic
+// (mfc_df.cuh) and inlined: the FP64 instructions of a reciprocal and the
+// call would cost more than the rest of the source term.
+template <int NF, int NDIM>
+__device__ __forceinline__ void kapila_K_df(const SweepArgs& a, const double* w, double* K) {
+    using Lay = Layout<NF, NDIM>;
+    const df p = df_from_double(w[Lay::IE]);
+    df al[NF], Z[NF];
+    double last = 1.0;
+#pragma unroll
+    for (int k = 0; k < NF - 1; ++k) {
+        al[k] = df_from_double(w[Lay::IA + k]);
+        last -= w[Lay::IA + k];
+    }
+    al[NF - 1] = df_from_double(last);
+#pragma unroll
+    for (int k = 0; k < NF; ++k)   // gamma_k as float-float: its FP32 rounding would show in K
+        Z[k] = df_mul(df_add(p, df_from_double(a.kpinf[k])), df_from_double(a.kgam[k]));
+    df pe[NF];   // product of the other phases' Z
+#pragma unroll
+    for (int k = 0; k < NF; ++k) {
+        df t = {1.f, 0.f};
+        bool first = true;
+#pragma unroll
+        for (int j = 0; j < NF; ++j) {
+            if (j == k) continue;
+            t = first ? Z[j] : df_mul(t, Z[j]);
+            first = false;
+        }
+        pe[k] = t;
+    }
+    df D = df_mul(al[0], pe[0]);
+#pragma unroll
+    for (int k = 1; k < NF; ++k) D = df_add(D, df_mul(al[k], pe[k]));
+#pragma unroll
+    for (int k = 0; k < NF - 1; ++k) K[k] = df_to_double(df_mul(al[k], df_add(df_div(pe[k], D), {-1.f, 0.f})));
+}
+
 template <typename Real, int NF, int NDIM>
 __device__ __forceinline__ void finish_cell(const SweepArgs& a, long long idx, const Real* Fm, const Real* Fp,
                                             Real um, Real up, const Real* cell, Real inv_dx) {
@@ -713,7 +787,8 @@ __device__ __forceinline__ void finish_cell(const SweepArgs& a, long long idx, c
     if constexpr (NF > 1) {
         if (a.kapila) {
             Real K[NF - 1];
-            kapila_K<Real, NF, NDIM>(a, cell, K);
+            if constexpr (sizeof(Real) == 8) kapila_K_df<NF, NDIM>(a, cell, K);
+            else kapila_K<Real, NF, NDIM>(a, cell, K);
 #pragma unroll
             for (int k = 0; k < NF - 1; ++k) out[IA + k] = fma(cell[IA + k] + K[k], du, out[IA + k]);
         } else {

@@ -1,0 +1,183 @@
+"""CPU check of the float-float arithmetic the FP64 path uses for its WENO5
+weights: a float32 model of the scheme (error-free transformations, the
+integer split of a double into hi + lo, the min-normalised weights) against
+the oracle's FP64 WENO5-JS on stencils of every kind the solver meets.  It
+models the arithmetic, not the kernel: the CUDA path's own parity is tested
+on the GPU.  Exact FMA is modelled by one rounding of a float64 product-sum
+(exact for float32 operands)."""
+
+import numpy as np
+import pytest
+
+import oracle
+
+f32 = np.float32
+
+
+def _fma(a, b, c):
+    return (a.astype(np.float64) * b.astype(np.float64) + c.astype(np.float64)).astype(f32)
+
+
+def _two_sum(a, b):
+    s = (a + b).astype(f32)
+    bb = (s - a).astype(f32)
+    return s, ((a - (s - bb).astype(f32)).astype(f32) + (b - bb).astype(f32)).astype(f32)
+
+
+def _fast_two_sum(a, b):
+    s = (a + b).astype(f32)
+    return s, (b - (s - a).astype(f32)).astype(f32)
+
+
+def _two_prod(a, b):
+    p = (a * b).astype(f32)
+    return p, _fma(a, b, -p)
+
+
+def add_fast(x, y):
+    s, e = _two_sum(x[0], y[0])
+    return _fast_two_sum(s, ((e + x[1]).astype(f32) + y[1]).astype(f32))
+
+
+def add(x, y):
+    s, e = _two_sum(x[0], y[0])
+    t, f = _two_sum(x[1], y[1])
+    s, e = _fast_two_sum(s, (e + t).astype(f32))
+    return _fast_two_sum(s, (e + f).astype(f32))
+
+
+def neg(x):
+    return -x[0], -x[1]
+
+
+def mul(x, y):
+    p, e = _two_prod(x[0], y[0])
+    e = _fma(x[1], y[0], _fma(x[0], y[1], e))
+    return _fast_two_sum(p, e)
+
+
+def mul_f(x, f):
+    f = np.full_like(x[0], f32(f))
+    p, e = _two_prod(x[0], f)
+    return _fast_two_sum(p, _fma(x[1], f, e))
+
+
+def mul_pow2(x, f):
+    return (x[0] * f32(f)).astype(f32), (x[1] * f32(f)).astype(f32)
+
+
+def div_f(a, b):
+    y = (f32(1) / b[0]).astype(f32)        # the correctly rounded reciprocal
+    q1 = (a * y).astype(f32)
+    p, pe = _two_prod(q1, b[0])
+    r = _fma(-q1, b[1], ((a - p).astype(f32) - pe).astype(f32))
+    return _fast_two_sum(q1, (r * y).astype(f32))
+
+
+def div(a, b):
+    y = (f32(1) / b[0]).astype(f32)
+    q1 = (a[0] * y).astype(f32)
+    r = add(a, neg(mul_f(b, q1)))
+    return _fast_two_sum(q1, (r[0] * y).astype(f32))
+
+
+def split(d):
+    """double -> (hi, lo) by integer operations on the bit pattern."""
+    u = d.astype(np.float64).view(np.uint64)
+    hw = (u >> np.uint64(32)).astype(np.uint64)
+    lw = (u & np.uint64(0xFFFFFFFF)).astype(np.uint64)
+    sign = hw & np.uint64(0x80000000)
+    ef = ((hw >> np.uint64(20)) & np.uint64(0x7FF)).astype(np.int64) - 1023 + 127
+    hb = sign | (np.clip(ef, 0, 255).astype(np.uint64) << np.uint64(23)) | \
+        ((hw & np.uint64(0xFFFFF)) << np.uint64(3)) | (lw >> np.uint64(29))
+    hi = np.where(ef > 0, hb.astype(np.uint32).view(np.float32), f32(0))
+    es = ef - 52
+    scale = (np.maximum(es, 1).astype(np.uint32) << np.uint32(23)).view(np.float32)
+    lo = ((lw & np.uint64(0x1FFFFFFF)).astype(f32) * scale).astype(f32)
+    lo = np.where(sign > 0, -lo, lo)
+    return hi.astype(f32), np.where(es > 0, lo, f32(0)).astype(f32)
+
+
+def to_double(x):
+    return x[0].astype(np.float64) + x[1].astype(np.float64)
+
+
+def weno5_float_float(vc, D, eps34):
+    """Edge values (eR at c-1/2, eL at c+1/2) as the FP64 path forms them."""
+    d0, d1, d2, d3 = (split(D[:, j]) for j in range(4))
+    S1, S2 = mul(d1, d1), mul(d2, d2)
+    b0 = add_fast(add_fast(mul(d0, d0), mul_f(mul(d1, d0), -2.75)), mul_f(S1, 2.5))
+    b1 = add_fast(add_fast(S1, S2), mul_f(mul(d1, d2), -1.25))
+    b2 = add_fast(add_fast(mul(d3, d3), mul_f(mul(d2, d3), -2.75)), mul_f(S2, 2.5))
+    e = split(np.full(len(vc), eps34))
+    t0, t1, t2 = add_fast(e, b0), add_fast(e, b1), add_fast(e, b2)
+    m = np.minimum(np.minimum(t0[0], t1[0]), t2[0])
+    g0, g1, g2 = div_f(m, t0), div_f(m, t1), div_f(m, t2)
+    q0, q1, q2 = mul(g0, g0), mul_f(mul(g1, g1), 6), mul(g2, g2)
+    wL2, wR2 = mul_f(q2, 3), mul_f(q0, 3)
+    P0 = add_fast(mul_f(d1, 5), mul_pow2(d0, -2))
+    P1 = add_fast(d1, mul_pow2(d2, 2))
+    P2 = add_fast(mul_pow2(d2, 4), neg(d3))
+    numL = add_fast(add_fast(mul(q0, P0), mul(q1, P1)), mul(wL2, P2))
+    denL = mul_f(add_fast(add_fast(q0, q1), wL2), 6)
+    M0 = add_fast(mul_pow2(d3, 2), mul_f(d2, -5))
+    M1 = neg(add_fast(mul_pow2(d1, 2), d2))
+    M2 = add_fast(d0, mul_pow2(d1, -4))
+    numR = add_fast(add_fast(mul(q2, M0), mul(q1, M1)), mul(wR2, M2))
+    denR = mul_f(add_fast(add_fast(q2, q1), wR2), 6)
+    return vc + to_double(div(numR, denR)), vc + to_double(div(numL, denL))
+
+
+def test_error_free_transformations_are_exact():
+    rng = np.random.default_rng(0)
+    a = (rng.standard_normal(10000) * 10.0 ** rng.uniform(-10, 10, 10000)).astype(f32)
+    b = (rng.standard_normal(10000) * 10.0 ** rng.uniform(-10, 10, 10000)).astype(f32)
+    s, e = _two_sum(a, b)
+    assert np.all(s.astype(np.float64) + e.astype(np.float64) == a.astype(np.float64) + b.astype(np.float64))
+    p, e = _two_prod(a, b)
+    assert np.all(p.astype(np.float64) + e.astype(np.float64) == a.astype(np.float64) * b.astype(np.float64))
+
+
+def test_integer_split_matches_the_double():
+    rng = np.random.default_rng(1)
+    d = rng.standard_normal(100000) * 10.0 ** rng.uniform(-22, 37, 100000)
+    hi, lo = split(d)
+    big = np.abs(d) >= 2.0 ** -74
+    assert np.all(np.abs(to_double((hi, lo))[big] - d[big]) <= 2.0 ** -47 * np.abs(d[big]))
+    assert np.all(np.abs(lo[big].astype(np.float64)) <= 2.0 ** -23 * np.abs(hi[big].astype(np.float64)))
+    # exact for doubles that are floats; zero and values below the FP32 range give zero
+    x = np.array([1.0, -3.5, 0.0, 1e-40, 2.0 ** -126])
+    hx, lx = split(x)
+    assert list(hx) == [1.0, -3.5, 0.0, 0.0, np.float32(2.0 ** -126)] and not lx.any()
+
+
+def _stencils(kind, rng, B=20000):
+    x = np.arange(-2, 3)[None, :]
+    if kind == "jumps":
+        k = rng.integers(0, 5, B)
+        return np.where(x >= k[:, None], 1e9, 1e5) * (1 + 1e-4 * rng.standard_normal((B, 5)))
+    if kind == "flat_next_to_jump":
+        k = rng.integers(0, 6, B)
+        return np.where(x >= k[:, None] - 2, 1e9, 1e5) + np.zeros((B, 5))
+    if kind == "sign_changing":
+        return rng.normal(0, 400, (B, 5))
+    scale, noise = {"smooth_pressure": (1e9, 1e-3), "noisy_pressure": (1e5, 0.05), "volume_fraction": (1.0, 0.01),
+                    "small": (1e-6, 0.1)}[kind]
+    return scale * (1 + noise * rng.standard_normal((B, 5)) + 0.01 * rng.standard_normal((B, 1)) * x)
+
+
+@pytest.mark.parametrize("kind", ["smooth_pressure", "noisy_pressure", "jumps", "flat_next_to_jump",
+                                  "volume_fraction", "small", "sign_changing"])
+def test_float_float_weno5_matches_the_oracle(kind):
+    """Edge values within 1e-13 of the stencil magnitude of the oracle's FP64
+    WENO5-JS (the FP64 path's parity tolerance is 1e-11 of much larger scales)."""
+    rng = np.random.default_rng(sum(map(ord, kind)))
+    v = _stencils(kind, rng, 2000)
+    eps = 1e-6
+    with np.errstate(all="ignore"):
+        eR, eL = weno5_float_float(v[:, 2], np.diff(v, axis=1), 0.75 * eps)
+    rL = np.array([oracle.weno5(s, eps) for s in v])
+    rR = np.array([oracle.weno5(s[::-1], eps) for s in v])
+    scale = np.abs(v).max(axis=1)
+    assert np.all(np.abs(eL - rL) <= 1e-13 * scale)
+    assert np.all(np.abs(eR - rR) <= 1e-13 * scale)
