@@ -808,7 +808,12 @@ __device__ __forceinline__ void finish_cell(const SweepArgs& a, long long idx, c
 #pragma unroll
         for (int v = 0; v < NS; ++v) {
             const Real rv = a.acc_in ? R[v * nc + idx] + out[v] : out[v];
-            const double s = fma(a.dt, (double)rv, a.qs[v * nc + idx]);
+            // FP32 accumulator widened by integer operations (a conversion
+            // instruction would take an FP64-pipe slot)
+            double rd;
+            if constexpr (sizeof(Real) == 4) rd = df_widen(rv);
+            else rd = rv;
+            const double s = fma(a.dt, rd, a.qs[v * nc + idx]);
             double o = a.c1 * s;
             if (a.c0 != 0.0) o = fma(a.c0, a.q0[v * nc + idx], o);
             a.qout[v * nc + idx] = o;
