@@ -15,6 +15,8 @@ Contents (each cites the passage of arXiv 2305.09163 it follows):
   * ``exact_riemann``: exact two-material stiffened-gas Riemann solution used to
     judge shock-tube runs.
   * ``mlp``: FP64 forward/backward of the learned-weight network.
+  * ``nonuniform``: WENO5 coefficient tables of a non-uniform grid (Sec. 3.3,
+    Listing 1) from their definitions, and the tanh stretching of Sec. 5.
 """
 from __future__ import annotations
 
@@ -58,6 +60,7 @@ class Params(ctypes.Structure):
         ("fallback", ctypes.c_int),
         ("weno_order", ctypes.c_int),
         ("model", ctypes.c_int),
+        ("tab", ctypes.POINTER(ctypes.c_double) * 3),
     ]
 
 
@@ -105,7 +108,12 @@ class Problem:
 
     MODELS = {"allaire": 0, "kapila": 1}
 
-    def __init__(self, n, lo, hi, bc, gamma, pi_inf, eps=1e-6, fallback=False, weno_order=5, model="allaire"):
+    def __init__(self, n, lo, hi, bc, gamma, pi_inf, eps=1e-6, fallback=False, weno_order=5, model="allaire",
+                 faces=None):
+        """faces: optional per-direction face coordinates (None or a sequence of up
+        to three arrays or None) for a non-uniform grid (WENO5 only); lo/hi of a
+        non-uniform direction are taken from its faces and dx[d] becomes its
+        smallest cell width."""
         n = list(n) + [1] * (3 - len(n))
         self.n = tuple(int(v) for v in n)
         self.ndim = 3 if self.n[2] > 1 else (2 if self.n[1] > 1 else 1)
@@ -126,6 +134,24 @@ class Problem:
         self.model = model
         self.sys_size = 2 * self.nf + self.ndim
         self.ncell = self.n[0] * self.n[1] * self.n[2]
+        self.faces = [None, None, None]
+        self._tabs = [None, None, None]
+        if faces is not None:
+            from . import nonuniform
+            if self.weno_order != 5:
+                raise ValueError("non-uniform grids need weno_order 5")
+            lo_l, hi_l, dx_l = list(self.lo), list(self.hi), list(self.dx)
+            for d, f in enumerate(list(faces)[:3]):
+                if f is None:
+                    continue
+                f = np.ascontiguousarray(f, dtype=np.float64)
+                if d >= self.ndim or f.size != self.n[d] + 1 or not np.all(np.diff(f) > 0):
+                    raise ValueError("faces[%d] must hold n+1 increasing coordinates of an active direction" % d)
+                periodic = self.bc[2 * d] == BC_PERIODIC
+                self.faces[d] = f
+                self._tabs[d] = nonuniform.direction_tables(f, periodic)
+                lo_l[d], hi_l[d], dx_l[d] = f[0], f[-1], float(np.diff(f).min())
+            self.lo, self.hi, self.dx = tuple(lo_l), tuple(hi_l), tuple(dx_l)
 
     def params(self) -> Params:
         p = Params()
@@ -143,6 +169,9 @@ class Problem:
         p.fallback = 1 if self.fallback else 0
         p.weno_order = self.weno_order
         p.model = self.MODELS[self.model]
+        for d in range(3):
+            if self._tabs[d] is not None:
+                p.tab[d] = _dp(self._tabs[d])
         return p
 
     def shape(self):

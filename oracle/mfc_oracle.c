@@ -29,6 +29,10 @@
  *   - Riemann solver (Sec. 3.2.1): HLLC, Davis wave-speed estimates, star states
  *     with continuity of normal velocity and pressure, four-branch flux.
  *     Face velocity = HLLC flux of a volume fraction divided by that fraction.
+ *   - Grid (Sec. 3.3): uniform, or non-uniform per direction with WENO5
+ *     coefficient tables (candidates, ideal weights, smoothness-indicator
+ *     quadratic forms per cell, as Listing 1's per-index tables) built by
+ *     oracle/nonuniform.py from the definitions.
  *   - Boundaries (Sec. 3.3): ghost cells three deep (WENO5 order); periodic,
  *     transmissive (copy of the nearest interior cell) and reflective (mirror,
  *     normal momentum negated).
@@ -60,7 +64,42 @@ typedef struct {
     int fallback;      /* first-order fallback at non-physical faces */
     int weno_order;    /* 5 (default) or 3 */
     int model;         /* 0: Allaire (K = 0); 1: Kapila (K div u in the alpha rows) */
+    const double *tab[3]; /* non-uniform grid: per-direction WENO5 tables (NULL: uniform) */
 } oracle_params;
+
+/* Layout of one table row (cell c of a direction, rows for c = -1..n), written
+ * by oracle/nonuniform.py from the definitions of the finite-volume WENO5
+ * construction: candidate values at c+1/2 and c-1/2 over the five-cell
+ * stencil, ideal weights of both edges, the smoothness-indicator quadratic
+ * forms over each candidate's three cells, and 1/dx_c. */
+#define TAB_CL 0
+#define TAB_CR 15
+#define TAB_DL 30
+#define TAB_DR 33
+#define TAB_B 36
+#define TAB_IDX 63
+#define TAB_ROW 64
+
+static const double *tab_row(const oracle_params *P, int d, int c) { return P->tab[d] + (long)(c + 1) * TAB_ROW; }
+
+/* WENO5-JS value at one edge of cell c from a table row (side 0: c+1/2,
+ * side 1: c-1/2); st = the five cell values c-2..c+2. */
+static double weno5_table(const double *row, int side, const double *st, double eps) {
+    const double *cand = row + (side ? TAB_CR : TAB_CL);
+    const double *dd = row + (side ? TAB_DR : TAB_DL);
+    double a[3], p[3], s = 0.0;
+    for (int r = 0; r < 3; ++r) {
+        p[r] = 0.0;
+        for (int j = 0; j < 5; ++j) p[r] += cand[5 * r + j] * st[j];
+        const double *B = row + TAB_B + 9 * r;
+        double b = 0.0;
+        for (int j = 0; j < 3; ++j)
+            for (int k = 0; k < 3; ++k) b += B[3 * j + k] * st[r + j] * st[r + k];
+        a[r] = dd[r] / ((eps + b) * (eps + b));
+        s += a[r];
+    }
+    return (a[0] * p[0] + a[1] * p[1] + a[2] * p[2]) / s;
+}
 
 /* ---- variable indexing (conserved and primitive share positions) ---- */
 static int sys_size(const oracle_params *P) { return 2 * P->nf + P->ndim; }
@@ -394,6 +433,12 @@ int oracle_face(const oracle_params *P, const double *q, int d, int i, int j, in
             wL[v] = oracle_weno3(st, P->eps);
             for (int s = 0; s < 3; ++s) st[s] = w[4 - s][v];   /* cells +1..-1, centre 0 */
             wR[v] = oracle_weno3(st, P->eps);
+        } else if (P->tab[d]) {
+            /* non-uniform grid: the tables of the two cells next to the face */
+            for (int s = 0; s < 5; ++s) st[s] = w[s][v];       /* cells -3..+1, centre -1 */
+            wL[v] = weno5_table(tab_row(P, d, (d == 0 ? i : d == 1 ? j : k) - 1), 0, st, P->eps);
+            for (int s = 0; s < 5; ++s) st[s] = w[1 + s][v];   /* cells -2..+2, centre 0 */
+            wR[v] = weno5_table(tab_row(P, d, d == 0 ? i : d == 1 ? j : k), 1, st, P->eps);
         } else {
             for (int s = 0; s < 5; ++s) st[s] = w[s][v];       /* cells -3..+1, centre -1 */
             wL[v] = oracle_weno5(st, P->eps);
@@ -438,10 +483,11 @@ long oracle_rhs(const oracle_params *P, const double *q, double *rhs, double *fm
         for (int v = 0; v < ns; ++v)
             for (long f = 0; f < nface; ++f)
                 if (fabs(Ff[(long)v * nface + f]) > fmax[v]) fmax[v] = fabs(Ff[(long)v * nface + f]);
-        double inv = 1.0 / P->dx[d];
+        const double inv_u = 1.0 / P->dx[d];
 #pragma omp parallel for schedule(static)
         for (long c = 0; c < ncell; ++c) {
             int ci[3] = {(int)(c % nx), (int)((c / nx) % ny), (int)(c / ((long)nx * ny))};
+            const double inv = P->tab[d] ? tab_row(P, d, ci[d])[TAB_IDX] : inv_u;
             int hi[3] = {ci[0], ci[1], ci[2]};
             hi[d] += 1;
             long flo = ((long)ci[2] * m[1] + ci[1]) * m[0] + ci[0];
@@ -488,7 +534,7 @@ void oracle_rhs_cells(const oracle_params *P, const double *q, long nsel, const 
             int hi[3] = {ci[0], ci[1], ci[2]};
             hi[d] += 1;
             oracle_face(P, q, d, hi[0], hi[1], hi[2], Fhi, &uhi);
-            double inv = 1.0 / P->dx[d];
+            double inv = P->tab[d] ? tab_row(P, d, ci[d])[TAB_IDX] : 1.0 / P->dx[d];
             for (int v = 0; v < ns; ++v) {
                 o[v] += (Flo[v] - Fhi[v]) * inv;
                 if (fabs(Flo[v]) > fm[v]) fm[v] = fabs(Flo[v]);
@@ -525,8 +571,10 @@ double oracle_max_rate(const oracle_params *P, const double *q, long *bad) {
         double c2 = sound_speed_sq(P, w);
         if (!(c2 > 0.0) || !isfinite(c2)) { nbad += 1; continue; }
         double cs = sqrt(c2);
+        int ci[3] = {(int)(c % P->n[0]), (int)((c / P->n[0]) % P->n[1]), (int)(c / ((long)P->n[0] * P->n[1]))};
         for (int d = 0; d < P->ndim; ++d) {
-            double r = (fabs(w[i_mom(P, d)]) + cs) / P->dx[d];
+            double r = P->tab[d] ? (fabs(w[i_mom(P, d)]) + cs) * tab_row(P, d, ci[d])[TAB_IDX]
+                                 : (fabs(w[i_mom(P, d)]) + cs) / P->dx[d];
             if (r > m) m = r;
         }
     }
