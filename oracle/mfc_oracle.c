@@ -83,22 +83,28 @@ typedef struct {
 static const double *tab_row(const oracle_params *P, int d, int c) { return P->tab[d] + (long)(c + 1) * TAB_ROW; }
 
 /* WENO5-JS value at one edge of cell c from a table row (side 0: c+1/2,
- * side 1: c-1/2); st = the five cell values c-2..c+2. */
+ * side 1: c-1/2); st = the five cell values c-2..c+2.  The candidates'
+ * coefficients sum to one and the smoothness indicators vanish on constants
+ * (they measure derivatives), so both are evaluated on the values relative to
+ * the cell value v_c: the same numbers, without the cancellation a quadratic
+ * form of raw values suffers when |v| is large and its variation small. */
 static double weno5_table(const double *row, int side, const double *st, double eps) {
     const double *cand = row + (side ? TAB_CR : TAB_CL);
     const double *dd = row + (side ? TAB_DR : TAB_DL);
+    double rel[5];
+    for (int j = 0; j < 5; ++j) rel[j] = st[j] - st[2];
     double a[3], p[3], s = 0.0;
     for (int r = 0; r < 3; ++r) {
         p[r] = 0.0;
-        for (int j = 0; j < 5; ++j) p[r] += cand[5 * r + j] * st[j];
+        for (int j = 0; j < 5; ++j) p[r] += cand[5 * r + j] * rel[j];
         const double *B = row + TAB_B + 9 * r;
         double b = 0.0;
         for (int j = 0; j < 3; ++j)
-            for (int k = 0; k < 3; ++k) b += B[3 * j + k] * st[r + j] * st[r + k];
+            for (int k = 0; k < 3; ++k) b += B[3 * j + k] * rel[r + j] * rel[r + k];
         a[r] = dd[r] / ((eps + b) * (eps + b));
         s += a[r];
     }
-    return (a[0] * p[0] + a[1] * p[1] + a[2] * p[2]) / s;
+    return st[2] + (a[0] * p[0] + a[1] * p[1] + a[2] * p[2]) / s;
 }
 
 /* ---- variable indexing (conserved and primitive share positions) ---- */
