@@ -103,6 +103,31 @@ mfc_status mfc_init(mfc_ctx** out, int nx, int ny, int nz, const double lo[3], c
  * Errors: MFC_ERR_ARG for an unknown name or out-of-range value. */
 mfc_status mfc_set_param(mfc_ctx* ctx, const char* name, double value);
 
+/* Non-uniform grid (Sec. 3.3: a structured mesh with non-uniform spacing,
+ * e.g. the tanh stretching of Sec. 5): faces[0..n_dir] are the strictly
+ * increasing face coordinates of the n_dir cells of direction dir (0 x, 1 y,
+ * 2 z; an active direction).  The library builds, on the host, the per-cell
+ * WENO5 coefficients of the finite-volume reconstruction on each five-cell
+ * stencil (candidates, ideal weights, smoothness indicators; Listing 1 keeps
+ * such per-index tables) and 1/dx per cell, used by the sweeps, the divergence
+ * and the CFL rate; ghost cells mirror (or, periodic, wrap) the interior
+ * widths.  The direction's lo/hi of mfc_init are then unused.  FP64 and mixed
+ * forms with weno_order 5 only; the y/z sweeps use the stream kernel.
+ * Host pointer, copied.  Errors: MFC_ERR_ARG (inactive direction, wrong
+ * count, non-increasing or non-finite faces, learned form, weno_order 3),
+ * MFC_ERR_OOM, MFC_ERR_CUDA. */
+mfc_status mfc_set_grid(mfc_ctx* ctx, int dir, const double* faces, int nfaces);
+
+/* The table mfc_set_grid uploads, on the host (no GPU needed): for the cells
+ * -1..n of a direction with faces[0..n], 28 values per cell, each as an FP32
+ * pair (hi, lo): candidate increments at c+1/2 (ea0, eb0, ea1, eb1, ea2, eb2;
+ * p_r - v_c = ea_r Da_r + eb_r Db_r, (Da, Db) = (D0, D1), (D1, D2), (D2, D3) with
+ * D_k = v_{c+k-1} - v_{c+k-2}), the same at c-1/2, the ideal weights at c+1/2
+ * and at c-1/2, beta_r = qa Da^2 + qab Da Db + qb Db^2 (qa, qab, qb per r), 1/dx.
+ * out receives (n + 2) * 56 floats.  Returns 0; the needed length if out is
+ * NULL or out_len is too small; -1 for bad faces. */
+int mfc_grid_table(const double* faces, int n, int periodic, float* out, long long out_len);
+
 /* Copy a conserved state q (layout above) into the context. */
 mfc_status mfc_set_state(mfc_ctx* ctx, const double* q, int on_device);
 

@@ -69,6 +69,10 @@ def _declare(lib):
     lib.mfc_launch_count.restype = c_ll
     lib.mfc_fallback_count.argtypes = [c_void_p]
     lib.mfc_fallback_count.restype = c_ll
+    lib.mfc_grid_table.argtypes = [c_void_p, c_int, c_int, c_void_p, ctypes.c_longlong]
+    lib.mfc_grid_table.restype = c_int
+    lib.mfc_set_grid.argtypes = [c_void_p, c_int, c_void_p, c_int]
+    lib.mfc_set_grid.restype = c_int
     lib.mfc_network_rows.argtypes = [c_void_p]
     lib.mfc_network_rows.restype = c_ll
     lib.mfc_profile_read.argtypes = [c_void_p, dptr, ctypes.POINTER(c_ll), c_int]
@@ -202,6 +206,26 @@ def mfc_launch_count(ctx):
 
 def mfc_fallback_count(ctx):
     return load().mfc_fallback_count(ctx)
+
+
+def mfc_set_grid(ctx, direction, faces):
+    """Face coordinates (n+1, increasing) of a non-uniform direction."""
+    import numpy as np
+    f = np.ascontiguousarray(faces, dtype=np.float64)
+    lib = load()
+    _check(lib, ctx, lib.mfc_set_grid(ctx, int(direction), f.ctypes.data, int(f.size)))
+
+
+def mfc_grid_table(faces, periodic=False):
+    """The per-cell WENO5 rows of a non-uniform direction as [n+2, 28, 2] float32."""
+    import numpy as np
+    f = np.ascontiguousarray(faces, dtype=np.float64)
+    n = f.size - 1
+    out = np.zeros((n + 2, 28, 2), dtype=np.float32)
+    st = load().mfc_grid_table(f.ctypes.data, n, 1 if periodic else 0, out.ctypes.data, out.size)
+    if st != 0:
+        raise MFCError(MFC_ERR_ARG, "faces must be finite and strictly increasing")
+    return out
 
 
 def mfc_network_rows(ctx):
@@ -377,6 +401,9 @@ class Solver:
 
     def fallback_count(self):
         return mfc_fallback_count(self.ctx)
+
+    def set_grid(self, direction, faces):
+        mfc_set_grid(self.ctx, direction, faces)
 
     def network_rows(self):
         return mfc_network_rows(self.ctx)

@@ -9,6 +9,7 @@
 #include <vector>
 
 #include "../../include/mfc.h"
+#include "mfc_grid.h"
 #include "mfc_launch.cuh"
 
 using namespace mfc;
@@ -52,6 +53,7 @@ struct mfc_ctx {
     int weno_order = 5;       // reconstruction: WENO5-JS or WENO3-JS
     int rk_order = 3;         // SSP Runge-Kutta order of mfc_step: 1, 2 or 3
     int kapila = 0;           // model: 0 Allaire, 1 Kapila (K div u source)
+    float* grid[3] = {nullptr, nullptr, nullptr};   // non-uniform directions: WENO5 rows (mfc_grid.cu)
 
     Geometry g{};
     EosConst e{};
@@ -132,7 +134,23 @@ mfc_status launch(mfc_ctx* c, int cat, F&& fn) {
     return MFC_OK;
 }
 
+bool nonuniform(const mfc_ctx* c) { return c->grid[0] || c->grid[1] || c->grid[2]; }
+
 cudaError_t dispatch_sweep(const mfc_ctx* c, const SweepArgs& a, int dir) {
+    if (nonuniform(c)) {
+        if (is_f32(c)) {
+            switch (c->nf) {
+                case 1: return launch_sweep<float, 1, false, 5, true>(a, c->ndim, dir, c->stream);
+                case 2: return launch_sweep<float, 2, false, 5, true>(a, c->ndim, dir, c->stream);
+                default: return launch_sweep<float, 3, false, 5, true>(a, c->ndim, dir, c->stream);
+            }
+        }
+        switch (c->nf) {
+            case 1: return launch_sweep<double, 1, false, 5, true>(a, c->ndim, dir, c->stream);
+            case 2: return launch_sweep<double, 2, false, 5, true>(a, c->ndim, dir, c->stream);
+            default: return launch_sweep<double, 3, false, 5, true>(a, c->ndim, dir, c->stream);
+        }
+    }
     if (c->precision == MFC_LEARNED) {
         switch (c->nf) {
             case 1: return launch_sweep<float, 1, true>(a, c->ndim, dir, c->stream);
@@ -206,6 +224,7 @@ mfc_status run_prims(mfc_ctx* c, const double* src, bool rate) {
     a.w = c->w;
     a.rate_max = rate ? c->d_rate : nullptr;
     a.bad = rate ? c->d_bad : nullptr;
+    for (int d = 0; d < 3; ++d) a.grid[d] = c->grid[d];
     return launch(c, rate ? P_CFL : P_PRIMS, [&] { return dispatch_prims(c, a, rate); });
 }
 
@@ -227,6 +246,7 @@ SweepArgs base_sweep(const mfc_ctx* c) {
     a.yz_stream = c->yz_stream >= 0 ? c->yz_stream : 1;
     a.bound = c->bound;
     a.kapila = c->kapila;
+    for (int d = 0; d < 3; ++d) a.grid[d] = c->grid[d];
     for (int k = 0; k < 3; ++k) {
         a.kgam[k] = k < c->nf ? c->gamma[k] : 1.0;
         a.kpinf[k] = k < c->nf ? c->pi_inf[k] : 0.0;
@@ -297,6 +317,7 @@ void free_all(mfc_ctx* c) {
     cudaFree(c->d_bad);
     cudaFree(c->d_fallback);
     cudaFree(c->mlp);
+    for (int d = 0; d < 3; ++d) cudaFree(c->grid[d]);
     if (c->h_pin) cudaFreeHost(c->h_pin);
 }
 
@@ -416,6 +437,7 @@ mfc_status mfc_set_param(mfc_ctx* c, const char* name, double value) {
         if (value != 3.0 && value != 5.0) return fail(c, MFC_ERR_ARG, "weno_order must be 3 or 5");
         if (value == 3.0 && c->precision == MFC_LEARNED)
             return fail(c, MFC_ERR_ARG, "the learned form replaces the WENO5 weights (weno_order 5)");
+        if (value == 3.0 && nonuniform(c)) return fail(c, MFC_ERR_ARG, "non-uniform grids need weno_order 5");
         c->weno_order = (int)value;
     } else if (!strcmp(name, "rk_order")) {
         if (value != 1.0 && value != 2.0 && value != 3.0) return fail(c, MFC_ERR_ARG, "rk_order must be 1, 2 or 3");
@@ -429,6 +451,31 @@ mfc_status mfc_set_param(mfc_ctx* c, const char* name, double value) {
     } else {
         return fail(c, MFC_ERR_ARG, "unknown parameter '%s'", name);
     }
+    return MFC_OK;
+}
+
+mfc_status mfc_set_grid(mfc_ctx* c, int dir, const double* faces, int nfaces) {
+    mfc_status s = ensure_alive(c);
+    if (s != MFC_OK) return s;
+    if (dir < 0 || dir >= c->ndim) return fail(c, MFC_ERR_ARG, "direction %d is not active", dir);
+    if (!faces || nfaces != c->n[dir] + 1) return fail(c, MFC_ERR_ARG, "need n+1 = %d face coordinates", c->n[dir] + 1);
+    if (c->precision == MFC_LEARNED) return fail(c, MFC_ERR_ARG, "non-uniform grids: FP64 and mixed forms only");
+    if (c->weno_order != 5) return fail(c, MFC_ERR_ARG, "non-uniform grids need weno_order 5");
+    const bool periodic = c->bc[2 * dir] == MFC_BC_PERIODIC;
+    std::vector<float> tab;
+    if (!grid_tables(faces, c->n[dir], periodic, tab))
+        return fail(c, MFC_ERR_ARG, "faces must be finite and strictly increasing");
+    if (!c->grid[dir]) {
+        cudaError_t e = cudaMalloc(&c->grid[dir], tab.size() * sizeof(float));
+        if (e != cudaSuccess) {
+            c->grid[dir] = nullptr;
+            return fail(c, e == cudaErrorMemoryAllocation ? MFC_ERR_OOM : MFC_ERR_CUDA, "cudaMalloc: %s",
+                        cudaGetErrorString(e));
+        }
+    }
+    MFC_CUDA(c, cudaMemcpyAsync(c->grid[dir], tab.data(), tab.size() * sizeof(float), cudaMemcpyHostToDevice,
+                                c->stream));
+    MFC_CUDA(c, cudaStreamSynchronize(c->stream));
     return MFC_OK;
 }
 

@@ -79,6 +79,7 @@ struct SweepArgs {
     float tau;              // learned form: discontinuity-sensor threshold
     int yz_stream;          // y/z sweeps: 1 = stream kernel, 0 = pencil marching
     int bound;              // learned form: range safeguard on learned edge values
+    const float* grid[3];   // non-uniform directions: WENO5 rows per cell (mfc_grid.cu), else null
     int kapila;             // 1: Kapila model, K div(u) in the volume-fraction rows
     double kgam[3], kpinf[3];   // Kapila: gamma_k and pi_inf_k of every fluid
     float kgamf[3], kpinff[3];
@@ -112,7 +113,13 @@ struct PrimArgs {
     void* w;                // primitives out [NS][ncell], Real
     unsigned long long* rate_max;  // optional: max (|u_d|+c)/dx_d as ordered bits
     int* bad;               // optional: count of non-physical cells
+    const float* grid[3];   // non-uniform directions: per-cell rows (1/dx at value 27), else null
 };
+
+// Values per non-uniform grid row (28 values, each an FP32 pair hi, lo) and
+// the position of 1/dx in a row.
+constexpr int kGridRowFloats = 56;
+constexpr int kGridInvDx = 27;
 
 template <int NF, int NDIM> struct Layout {
     static constexpr int NS = 2 * NF + NDIM;
@@ -302,6 +309,84 @@ __device__ __forceinline__ void weno_edges(Real vc, const Real D[4], Real epsw, 
     static_assert(ORDER == 3 || ORDER == 5, "WENO3 or WENO5");
     if constexpr (ORDER == 3) weno3_edges(vc, D[1], D[2], epsw, eR, eL);
     else weno5_edges(vc, D, epsw, eR, eL);
+}
+
+// ---------------------------------------------------------------------------
+// WENO5-JS on a non-uniform grid (Sec. 3.3, with per-cell coefficients as in
+// Listing 1): row = the cell's table row (mfc_grid.cu): candidate increments
+// ea_r Da_r + eb_r Db_r for both edges (values 0..11), ideal weights (12..17),
+// beta_r = qa Da^2 + qab Da Db + qb Db^2 (18..26), with (Da, Db) = (D0, D1),
+// (D1, D2), (D2, D3) for r = 0, 1, 2.  The indicators are the exact integrals
+// (no 4/3 scaling), so eps enters unscaled.  Weights normalised by
+// m = min_r (eps + beta_r) as in the uniform variants.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ df grid_df(const float* __restrict__ row, int k) {
+    return {__ldg(row + 2 * k), __ldg(row + 2 * k + 1)};
+}
+
+__device__ __forceinline__ void weno5_edges_nu(double vc, const double D[4], double eps,
+                                               const float* __restrict__ row, double& eR, double& eL) {
+    const df d0 = df_from_double(D[0]), d1 = df_from_double(D[1]);
+    const df d2 = df_from_double(D[2]), d3 = df_from_double(D[3]);
+    const df S0 = df_mul(d0, d0), S1 = df_mul(d1, d1), S2 = df_mul(d2, d2), S3 = df_mul(d3, d3);
+    const df X01 = df_mul(d0, d1), X12 = df_mul(d1, d2), X23 = df_mul(d2, d3);
+    const df b0 = df_add_fast(df_add_fast(df_mul(grid_df(row, 18), S0), df_mul(grid_df(row, 19), X01)),
+                              df_mul(grid_df(row, 20), S1));
+    const df b1 = df_add_fast(df_add_fast(df_mul(grid_df(row, 21), S1), df_mul(grid_df(row, 22), X12)),
+                              df_mul(grid_df(row, 23), S2));
+    const df b2 = df_add_fast(df_add_fast(df_mul(grid_df(row, 24), S2), df_mul(grid_df(row, 25), X23)),
+                              df_mul(grid_df(row, 26), S3));
+    const df e = df_from_double(eps);
+    const df t0 = df_add_fast(e, b0), t1 = df_add_fast(e, b1), t2 = df_add_fast(e, b2);
+    const float m = fminf(t0.hi, fminf(t1.hi, t2.hi));
+    const df g0 = df_div_f(m, t0), g1 = df_div_f(m, t1), g2 = df_div_f(m, t2);
+    const df q0 = df_mul(g0, g0), q1 = df_mul(g1, g1), q2 = df_mul(g2, g2);
+    const df P0 = df_add_fast(df_mul(grid_df(row, 0), d0), df_mul(grid_df(row, 1), d1));
+    const df P1 = df_add_fast(df_mul(grid_df(row, 2), d1), df_mul(grid_df(row, 3), d2));
+    const df P2 = df_add_fast(df_mul(grid_df(row, 4), d2), df_mul(grid_df(row, 5), d3));
+    const df wL0 = df_mul(grid_df(row, 12), q0), wL1 = df_mul(grid_df(row, 13), q1), wL2 = df_mul(grid_df(row, 14), q2);
+    const df numL = df_add_fast(df_add_fast(df_mul(wL0, P0), df_mul(wL1, P1)), df_mul(wL2, P2));
+    const df denL = df_add_fast(df_add_fast(wL0, wL1), wL2);
+    const df M0 = df_add_fast(df_mul(grid_df(row, 6), d0), df_mul(grid_df(row, 7), d1));
+    const df M1 = df_add_fast(df_mul(grid_df(row, 8), d1), df_mul(grid_df(row, 9), d2));
+    const df M2 = df_add_fast(df_mul(grid_df(row, 10), d2), df_mul(grid_df(row, 11), d3));
+    const df wR0 = df_mul(grid_df(row, 15), q0), wR1 = df_mul(grid_df(row, 16), q1), wR2 = df_mul(grid_df(row, 17), q2);
+    const df numR = df_add_fast(df_add_fast(df_mul(wR0, M0), df_mul(wR1, M1)), df_mul(wR2, M2));
+    const df denR = df_add_fast(df_add_fast(wR0, wR1), wR2);
+    eL = vc + df_to_double(df_div(numL, denL));
+    eR = vc + df_to_double(df_div(numR, denR));
+}
+
+__device__ __forceinline__ void weno5_edges_nu(float vc, const float D[4], float eps, const float* __restrict__ row,
+                                               float& eR, float& eL) {
+    auto T = [&](int k) { return __ldg(row + 2 * k); };
+    const float S0 = D[0] * D[0], S1 = D[1] * D[1], S2 = D[2] * D[2], S3 = D[3] * D[3];
+    const float b0 = fmaf(T(18), S0, fmaf(T(19), D[0] * D[1], T(20) * S1));
+    const float b1 = fmaf(T(21), S1, fmaf(T(22), D[1] * D[2], T(23) * S2));
+    const float b2 = fmaf(T(24), S2, fmaf(T(25), D[2] * D[3], T(26) * S3));
+    const float t0 = eps + b0, t1 = eps + b1, t2 = eps + b2;
+    const float m = fminf(t0, fminf(t1, t2));
+    float g0 = __fdividef(m, t0), g1 = __fdividef(m, t1), g2 = __fdividef(m, t2);
+    g0 *= g0;
+    g1 *= g1;
+    g2 *= g2;
+    const float P0 = fmaf(T(0), D[0], T(1) * D[1]), P1 = fmaf(T(2), D[1], T(3) * D[2]);
+    const float P2 = fmaf(T(4), D[2], T(5) * D[3]);
+    const float M0 = fmaf(T(6), D[0], T(7) * D[1]), M1 = fmaf(T(8), D[1], T(9) * D[2]);
+    const float M2 = fmaf(T(10), D[2], T(11) * D[3]);
+    const float wL0 = T(12) * g0, wL1 = T(13) * g1, wL2 = T(14) * g2;
+    const float wR0 = T(15) * g0, wR1 = T(16) * g1, wR2 = T(17) * g2;
+    eL = vc + __fdividef(fmaf(wL0, P0, fmaf(wL1, P1, wL2 * P2)), wL0 + wL1 + wL2);
+    eR = vc + __fdividef(fmaf(wR0, M0, fmaf(wR1, M1, wR2 * M2)), wR0 + wR1 + wR2);
+}
+
+// 1/dx of cell c of a non-uniform direction, in the path's precision.
+__device__ __forceinline__ double grid_inv_dx(const float* __restrict__ grid, int c, double) {
+    const float* row = grid + (long long)(c + 1) * kGridRowFloats;
+    return df_to_double(grid_df(row, kGridInvDx));
+}
+__device__ __forceinline__ float grid_inv_dx(const float* __restrict__ grid, int c, float) {
+    return __ldg(grid + (long long)(c + 1) * kGridRowFloats + 2 * kGridInvDx);
 }
 
 template <typename Real> struct EosR {
@@ -973,8 +1058,9 @@ __global__ void __launch_bounds__(128) sweep_kernel(const SweepArgs a) {
 // ---------------------------------------------------------------------------
 constexpr int kStreamThreads = 128;
 
-template <typename Real, int NF, int NDIM, bool LEARNED = false, int ORDER = 5>
+template <typename Real, int NF, int NDIM, bool LEARNED = false, int ORDER = 5, bool NONUNIF = false>
 __global__ void __launch_bounds__(kStreamThreads) sweep_x_stream_kernel(const SweepArgs a) {
+    static_assert(!NONUNIF || (!LEARNED && ORDER == 5), "non-uniform grids: WENO5, FP64 and mixed forms");
     static_assert(!LEARNED || sizeof(Real) == 4, "the learned form runs in FP32");
     static_assert(!LEARNED || ORDER == 5, "the learned form replaces the WENO5 weights");
     using Lay = Layout<NF, NDIM>;
@@ -1092,8 +1178,15 @@ __global__ void __launch_bounds__(kStreamThreads) sweep_x_stream_kernel(const Sw
             }
         }
         if (!LEARNED && live) {
+            if constexpr (NONUNIF) {
+                const float* row = a.grid[0] + (long long)(c + 1) * kGridRowFloats;
+                const Real epsn = sweep_epsw<Real, 3>(a);   // unscaled eps
 #pragma unroll
-            for (int q = 0; q < NS; ++q) weno_edges<ORDER>(vcv[q], Dv[q], eps34, eR[q], eL[q]);
+                for (int q = 0; q < NS; ++q) weno5_edges_nu(vcv[q], Dv[q], epsn, row, eR[q], eL[q]);
+            } else {
+#pragma unroll
+                for (int q = 0; q < NS; ++q) weno_edges<ORDER>(vcv[q], Dv[q], eps34, eR[q], eL[q]);
+            }
         }
         if constexpr (!LEARNED) {
 #pragma unroll
@@ -1131,7 +1224,8 @@ __global__ void __launch_bounds__(kStreamThreads) sweep_x_stream_kernel(const Sw
             Real Fm[NS];
 #pragma unroll
             for (int q = 0; q < NS; ++q) Fm[q] = sh_F[q][t];
-            finish_cell<Real, NF, NDIM>(a, rowoff + (c - 1), Fm, F, sh_F[NS][t], ut, cm1, inv_dx);
+            finish_cell<Real, NF, NDIM>(a, rowoff + (c - 1), Fm, F, sh_F[NS][t], ut, cm1,
+                                        NONUNIF ? grid_inv_dx(a.grid[0], c - 1, Real(0)) : inv_dx);
         }
         __syncthreads();
         // carry the last slot of the chunk into position 0
@@ -1165,8 +1259,9 @@ __global__ void __launch_bounds__(kStreamThreads) sweep_x_stream_kernel(const Sw
 // ---------------------------------------------------------------------------
 constexpr int kRowsPerChunk = 4;
 
-template <typename Real, int NF, int NDIM, int DIR, bool LEARNED, int ORDER>
+template <typename Real, int NF, int NDIM, int DIR, bool LEARNED, int ORDER, bool NONUNIF = false>
 __device__ __forceinline__ void sweep_yz_stream_body(const SweepArgs& a) {
+    static_assert(!NONUNIF || (!LEARNED && ORDER == 5), "non-uniform grids: WENO5, FP64 and mixed forms");
     static_assert(!LEARNED || ORDER == 5, "the learned form replaces the WENO5 weights");
     static_assert(DIR == 1 || DIR == 2, "y or z");
     static_assert(!LEARNED || sizeof(Real) == 4, "the learned form runs in FP32");
@@ -1270,8 +1365,15 @@ __device__ __forceinline__ void sweep_yz_stream_body(const SweepArgs& a) {
                     cell[q] = v2;
                     cm1[q] = v1;
                 }
+                if constexpr (NONUNIF) {
+                    const float* grow = a.grid[DIR] + (long long)(c + 1) * kGridRowFloats;
+                    const Real epsn = sweep_epsw<Real, 3>(a);   // unscaled eps
 #pragma unroll
-                for (int q = 0; q < NS; ++q) weno_edges<ORDER>(cell[q], Dv[q], eps34, eR[q], eL[q]);
+                    for (int q = 0; q < NS; ++q) weno5_edges_nu(cell[q], Dv[q], epsn, grow, eR[q], eL[q]);
+                } else {
+#pragma unroll
+                    for (int q = 0; q < NS; ++q) weno_edges<ORDER>(cell[q], Dv[q], eps34, eR[q], eL[q]);
+                }
             }
 #pragma unroll
             for (int q = 0; q < NS; ++q) {
@@ -1309,7 +1411,7 @@ __device__ __forceinline__ void sweep_yz_stream_body(const SweepArgs& a) {
 #pragma unroll
             for (int q = 0; q < NS; ++q) Fm[q] = sh_F[q][row][lane];
             finish_cell<Real, NF, NDIM>(a, basei + (long long)(c - 1) * sd, Fm, F, sh_F[NS][row][lane], ut, cm1,
-                                        inv_dx);
+                                        NONUNIF ? grid_inv_dx(a.grid[DIR], c - 1, Real(0)) : inv_dx);
         }
         __syncthreads();
         // carry the last row of the chunk into row 0
@@ -1333,9 +1435,9 @@ __device__ __forceinline__ void sweep_yz_stream_body(const SweepArgs& a) {
 // entry with a register bound (4 CTAs per SM for two fluids) so that enough
 // warps stay resident; the mixed form keeps the compiler's own allocation,
 // which schedules its loads better.
-template <typename Real, int NF, int NDIM, int DIR, int ORDER = 5>
+template <typename Real, int NF, int NDIM, int DIR, int ORDER = 5, bool NONUNIF = false>
 __global__ void __launch_bounds__(32 * kRowsPerChunk) sweep_yz_stream_kernel(const SweepArgs a) {
-    sweep_yz_stream_body<Real, NF, NDIM, DIR, false, ORDER>(a);
+    sweep_yz_stream_body<Real, NF, NDIM, DIR, false, ORDER, NONUNIF>(a);
 }
 
 template <int NF, int NDIM, int DIR>
@@ -1438,8 +1540,18 @@ __global__ void __launch_bounds__(256) prims_kernel(const PrimArgs a) {
             } else {
                 const Real cs = real_sqrt(c2);
                 Real r = 0;
+                int ci[3] = {0, 0, 0};
+                if (a.grid[0] || a.grid[1] || a.grid[2]) {   // non-uniform: this cell's widths
+                    const unsigned ii = (unsigned)i, nx = (unsigned)a.g.n[0], ny = (unsigned)a.g.n[1];
+                    ci[0] = (int)(ii % nx);
+                    ci[1] = (int)((ii / nx) % ny);
+                    ci[2] = (int)(ii / (nx * ny));
+                }
 #pragma unroll
-                for (int d = 0; d < NDIM; ++d) r = real_max(r, (fabs(wv[IM + d]) + cs) * (Real)a.g.inv_dx[d]);
+                for (int d = 0; d < NDIM; ++d) {
+                    const Real inv = a.grid[d] ? grid_inv_dx(a.grid[d], ci[d], Real(0)) : (Real)a.g.inv_dx[d];
+                    r = real_max(r, (fabs(wv[IM + d]) + cs) * inv);
+                }
                 rate = fmax(rate, (double)r);
             }
         }

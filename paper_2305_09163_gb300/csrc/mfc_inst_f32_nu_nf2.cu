@@ -1,0 +1,5 @@
+// Instantiates the non-uniform-grid sweeps for float arithmetic and 2 fluid(s).
+#include "mfc_launch.cuh"
+namespace mfc {
+template cudaError_t launch_sweep<float, 2, false, 5, true>(SweepArgs, int, int, cudaStream_t);
+}  // namespace mfc

@@ -13,22 +13,22 @@ constexpr int kElemThreads = 256;
 // so the two recomputed slots at its start cost about 0.1%.
 constexpr long long kStreamSlotsPerBlock = 16LL * kStreamThreads;
 
-template <typename Real, int NF, bool LEARNED = false, int ORDER = 5>
+template <typename Real, int NF, bool LEARNED = false, int ORDER = 5, bool NONUNIF = false>
 cudaError_t launch_sweep(SweepArgs a, int ndim, int dir, cudaStream_t s) {
     if (dir == 0) {
         const long long total = (long long)(a.g.n[0] + 2) * (a.g.ncell / a.g.n[0]);
         a.slots_per_block = kStreamSlotsPerBlock;
         const unsigned blocks = (unsigned)((total + kStreamSlotsPerBlock - 1) / kStreamSlotsPerBlock);
         switch (ndim) {
-            case 1: sweep_x_stream_kernel<Real, NF, 1, LEARNED, ORDER><<<blocks, kStreamThreads, 0, s>>>(a); break;
-            case 2: sweep_x_stream_kernel<Real, NF, 2, LEARNED, ORDER><<<blocks, kStreamThreads, 0, s>>>(a); break;
-            case 3: sweep_x_stream_kernel<Real, NF, 3, LEARNED, ORDER><<<blocks, kStreamThreads, 0, s>>>(a); break;
+            case 1: sweep_x_stream_kernel<Real, NF, 1, LEARNED, ORDER, NONUNIF><<<blocks, kStreamThreads, 0, s>>>(a); break;
+            case 2: sweep_x_stream_kernel<Real, NF, 2, LEARNED, ORDER, NONUNIF><<<blocks, kStreamThreads, 0, s>>>(a); break;
+            case 3: sweep_x_stream_kernel<Real, NF, 3, LEARNED, ORDER, NONUNIF><<<blocks, kStreamThreads, 0, s>>>(a); break;
             default: return cudaErrorInvalidValue;
         }
         return cudaGetLastError();
     }
     const int t1 = (dir == 0) ? 1 : 0, t2 = (dir == 2) ? 1 : 2;
-    if (a.yz_stream) {
+    if (NONUNIF || a.yz_stream) {   // non-uniform grids: the stream kernel only
         // y/z stream kernel, one CTA per 32 x-lanes of a segment
         const unsigned blocks = (unsigned)((long long)((a.g.n[t1] + 31) / 32) * a.nseg * a.g.n[t2]);
         if constexpr (LEARNED) {
@@ -40,14 +40,15 @@ cudaError_t launch_sweep(SweepArgs a, int ndim, int dir, cudaStream_t s) {
             }
         } else {
             switch (ndim * 4 + dir) {
-                case 9: sweep_yz_stream_kernel<Real, NF, 2, 1, ORDER><<<blocks, 32 * kRowsPerChunk, 0, s>>>(a); break;
-                case 13: sweep_yz_stream_kernel<Real, NF, 3, 1, ORDER><<<blocks, 32 * kRowsPerChunk, 0, s>>>(a); break;
-                case 14: sweep_yz_stream_kernel<Real, NF, 3, 2, ORDER><<<blocks, 32 * kRowsPerChunk, 0, s>>>(a); break;
+                case 9: sweep_yz_stream_kernel<Real, NF, 2, 1, ORDER, NONUNIF><<<blocks, 32 * kRowsPerChunk, 0, s>>>(a); break;
+                case 13: sweep_yz_stream_kernel<Real, NF, 3, 1, ORDER, NONUNIF><<<blocks, 32 * kRowsPerChunk, 0, s>>>(a); break;
+                case 14: sweep_yz_stream_kernel<Real, NF, 3, 2, ORDER, NONUNIF><<<blocks, 32 * kRowsPerChunk, 0, s>>>(a); break;
                 default: return cudaErrorInvalidValue;
             }
         }
         return cudaGetLastError();
     }
+    if constexpr (NONUNIF) return cudaErrorInvalidValue;
     const long long warps = (long long)((a.g.n[t1] + 31) / 32) * a.nseg * a.g.n[t2];
     const unsigned blocks = (unsigned)((warps * 32 + kSweepThreads - 1) / kSweepThreads);
     switch (ndim * 4 + dir) {
@@ -109,6 +110,13 @@ MFC_DECLARE_INSTANCES(float, 3)
 extern template cudaError_t launch_sweep<float, 1, true>(SweepArgs, int, int, cudaStream_t);
 extern template cudaError_t launch_sweep<float, 2, true>(SweepArgs, int, int, cudaStream_t);
 extern template cudaError_t launch_sweep<float, 3, true>(SweepArgs, int, int, cudaStream_t);
+// non-uniform grids (mfc_inst_*_nu_*.cu)
+extern template cudaError_t launch_sweep<double, 1, false, 5, true>(SweepArgs, int, int, cudaStream_t);
+extern template cudaError_t launch_sweep<double, 2, false, 5, true>(SweepArgs, int, int, cudaStream_t);
+extern template cudaError_t launch_sweep<double, 3, false, 5, true>(SweepArgs, int, int, cudaStream_t);
+extern template cudaError_t launch_sweep<float, 1, false, 5, true>(SweepArgs, int, int, cudaStream_t);
+extern template cudaError_t launch_sweep<float, 2, false, 5, true>(SweepArgs, int, int, cudaStream_t);
+extern template cudaError_t launch_sweep<float, 3, false, 5, true>(SweepArgs, int, int, cudaStream_t);
 // WENO3 (mfc_inst_*_w3_*.cu)
 extern template cudaError_t launch_sweep<double, 1, false, 3>(SweepArgs, int, int, cudaStream_t);
 extern template cudaError_t launch_sweep<double, 2, false, 3>(SweepArgs, int, int, cudaStream_t);
