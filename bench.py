@@ -51,14 +51,17 @@ FLOP_SWEEP_CELL_3D_2F_W3 = 31 * 7 + 87 + 18
 # The Kapila model adds K (two Z_k = gamma_k (p + pinf_k), the weighted sum,
 # one reciprocal, K = alpha (Z_2/D - 1)) and its source term: 13 per cell and sweep.
 FLOP_SWEEP_CELL_3D_2F_KAPILA = FLOP_SWEEP_CELL_3D_2F + 13
-# Forms the bench can time: name -> (precision, extra solver parameters).
+# Forms the bench can time: name -> (precision, extra solver parameters,
+# workload: the shock-bubble, or the same on the tanh-stretched grid).
 FORMS = {
-    "fp64": ("fp64", {}),
-    "mixed": ("mixed", {}),
-    "learned": ("learned", {}),
-    "fp64_weno3": ("fp64", {"weno_order": 3}),
-    "mixed_weno3": ("mixed", {"weno_order": 3}),
-    "fp64_kapila": ("fp64", {"model": 1}),
+    "fp64": ("fp64", {}, "uniform"),
+    "mixed": ("mixed", {}, "uniform"),
+    "learned": ("learned", {}, "uniform"),
+    "fp64_weno3": ("fp64", {"weno_order": 3}, "uniform"),
+    "mixed_weno3": ("mixed", {"weno_order": 3}, "uniform"),
+    "fp64_kapila": ("fp64", {"model": 1}, "uniform"),
+    "fp64_stretched": ("fp64", {}, "stretched"),
+    "mixed_stretched": ("mixed", {}, "stretched"),
 }
 # RK3 stage epilogue in the last sweep: 6 per variable (stages 2, 3), 4 in stage 1
 FLOP_RK_CELL_2F = 7 * (6 + 6 + 4) / 3.0
@@ -191,8 +194,11 @@ def time_form(m, torch, wl, w_dev, form, steps, warmup, dist_barrier, sampler_gp
     """Warm up, then time `steps` steps (CFL + SSP-RK3) of one form (FORMS) with
     CUDA events on the solver's stream.  Returns a dict of measurements."""
     stream = torch.cuda.current_stream()
-    precision, params = FORMS[form]
+    precision, params, _ = FORMS[form]
     s = m.Solver(wl.n, wl.lo, wl.hi, wl.bc, wl.gamma, wl.pi_inf, precision=precision, fallback=1, **params)
+    if wl.faces is not None:
+        for d in range(3):
+            s.set_grid(d, wl.faces[d])
     if mlp is not None:
         s.set_mlp(mlp)
     s.set_state_prim(w_dev)
@@ -420,7 +426,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
     ap.add_argument("--n", type=int, default=256, help="cells per direction of the shock-bubble cube")
-    ap.add_argument("--forms", default="fp64,mixed,learned,fp64_weno3,mixed_weno3,fp64_kapila",
+    ap.add_argument("--forms", default="fp64,mixed,learned,fp64_weno3,mixed_weno3,fp64_kapila,fp64_stretched,"
+                                       "mixed_stretched",
                     help="comma list of " + ",".join(FORMS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -464,12 +471,20 @@ def main():
     results = {}
     training = None
     head = "fp64" if "fp64" in forms else forms[0]
+    stretched = None
     for form in forms:
         mlp = None
         if form == "learned":
             mlp, training = train_learned(m, torch)
-        r = time_form(m, torch, wl, w_dev, form, args.steps, args.warmup, barrier,
+        fwl, fw = wl, w_dev
+        if FORMS[form][2] == "stretched":
+            if stretched is None:
+                swl = workloads.shock_bubble_stretched(args.n)
+                stretched = (swl, torch.from_numpy(swl.prims()).cuda())
+            fwl, fw = stretched
+        r = time_form(m, torch, fwl, fw, form, args.steps, args.warmup, barrier,
                       sampler_gpu=local if form == head else None, mlp=mlp)
+        r["workload"] = fwl.name
         r["ms_max"] = max_over_ranks(r["ms_per_step"], ws, "cuda")
         results[form] = r
 
@@ -517,15 +532,20 @@ def main():
         stages = r["sweep_launches"] / 3.0
         peaks = _measured_peaks()
         hbm = float(peaks.get("hbm_gbs", 6800.0))
-        if form in ("fp64_weno3", "fp64_kapila"):
-            fl = FLOP_SWEEP_CELL_3D_2F_W3 if form == "fp64_weno3" else FLOP_SWEEP_CELL_3D_2F_KAPILA
+        entry["workload"] = r["workload"]
+        if form in ("fp64_weno3", "fp64_kapila", "fp64_stretched"):
+            fl = {"fp64_weno3": FLOP_SWEEP_CELL_3D_2F_W3, "fp64_kapila": FLOP_SWEEP_CELL_3D_2F_KAPILA,
+                  "fp64_stretched": FLOP_SWEEP_CELL_3D_2F}[form]
             tf = (fl + FLOP_RK_CELL_2F / 3.0) * cells * r["sweep_launches"] / sweep_s / 1e12
-            entry["roofline"] = {"kernel": "sweep (x, y, z), " + ("WENO3" if form == "fp64_weno3" else "Kapila"),
+            entry["roofline"] = {"kernel": "sweep (x, y, z), " + {"fp64_weno3": "WENO3", "fp64_kapila": "Kapila",
+                                                                  "fp64_stretched": "non-uniform grid"}[form],
                                  "bound": "alu", "achieved": tf,
                                  "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": tf / FP64_PEAK_TFLOPS,
                                  "flop_per_cell_per_sweep": fl,
-                                 "note": "nominal FP64 peak as for the WENO5 form"}
-        elif form in ("mixed", "mixed_weno3"):
+                                 "note": "nominal FP64 peak as for the WENO5 form" + (
+                                     "; FLOPs counted as on a uniform grid (the per-cell coefficients add work)"
+                                     if form == "fp64_stretched" else "")}
+        elif form in ("mixed", "mixed_weno3", "mixed_stretched"):
             gbs = BYTES_MIXED_SWEEPS_STAGE * cells * stages / sweep_s / 1e9
             fl = FLOP_SWEEP_CELL_3D_2F if form == "mixed" else FLOP_SWEEP_CELL_3D_2F_W3
             tf = fl * cells * r["sweep_launches"] / sweep_s / 1e12

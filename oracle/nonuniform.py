@@ -3,8 +3,8 @@
 TEST INFRASTRUCTURE ONLY (see ``oracle/__init__.py``).
 
 Sec. 3.3 of arXiv 2305.09163 discretises on a structured mesh with
-non-uniform spacing (tanh stretching, Sec. 5's droplet case gives the
-mapping); Listing 1 (Sec. 4.2) reconstructs with per-index coefficient tables
+non-uniform spacing (tanh stretching; the face coordinates come from the
+input generators); Listing 1 (Sec. 4.2) reconstructs with per-index coefficient tables
 (candidate, smoothness-indicator and ideal-weight coefficients per cell).  The
 tables follow from the finite-volume WENO construction (Jiang & Shu; Shu's
 notes, which Sec. 3.2 cites for the details), written here directly:
@@ -29,16 +29,6 @@ from __future__ import annotations
 import numpy as np
 
 GHOST = 3
-
-
-def stretched_faces(n: int, lo: float, hi: float, a: float, xa: float, xb: float) -> np.ndarray:
-    """Face coordinates of n cells after the hyperbolic-tangent stretching of
-    Sec. 5 (droplet case): x_s = x + (x/a)[log cosh(a(x-xa)/L) + log cosh(a(x-xb)/L)
-    - 2 log cosh(a(xb-xa)/(2L))], applied to the uniform faces, L = hi - lo."""
-    x = np.linspace(lo, hi, n + 1)
-    L = hi - lo
-    lc = lambda z: np.log(np.cosh(z))
-    return x + (x / a) * (lc(a * (x - xa) / L) + lc(a * (x - xb) / L) - 2.0 * lc(a * (xb - xa) / (2.0 * L)))
 
 
 def ghost_widths(faces: np.ndarray, periodic: bool) -> np.ndarray:

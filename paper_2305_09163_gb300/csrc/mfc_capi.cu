@@ -17,6 +17,7 @@ using namespace mfc;
 // The learned form's device blob: MFC_MLP_PARAMS floats, then the packed
 // per-lane fragments the sweeps load (16-byte aligned).
 constexpr size_t kMlpFragOffset = 8192;
+static_assert(kGridRow == kGridRowValues, "host and device grid rows agree");
 static_assert(sizeof(float) * MFC_MLP_PARAMS <= kMlpFragOffset, "parameters fit before the fragments");
 
 cudaError_t mfc_launch_mlp_pack(const float* P, void* frag, cudaStream_t s);
@@ -224,7 +225,10 @@ mfc_status run_prims(mfc_ctx* c, const double* src, bool rate) {
     a.w = c->w;
     a.rate_max = rate ? c->d_rate : nullptr;
     a.bad = rate ? c->d_bad : nullptr;
-    for (int d = 0; d < 3; ++d) a.grid[d] = c->grid[d];
+    for (int d = 0; d < 3; ++d) {   // layouts as mfc_set_grid stores them
+        a.grid[d] = c->grid[d];
+        a.grid_stride[d] = c->n[d] + 2;
+    }
     return launch(c, rate ? P_CFL : P_PRIMS, [&] { return dispatch_prims(c, a, rate); });
 }
 
@@ -246,7 +250,10 @@ SweepArgs base_sweep(const mfc_ctx* c) {
     a.yz_stream = c->yz_stream >= 0 ? c->yz_stream : 1;
     a.bound = c->bound;
     a.kapila = c->kapila;
-    for (int d = 0; d < 3; ++d) a.grid[d] = c->grid[d];
+    for (int d = 0; d < 3; ++d) {   // layouts as mfc_set_grid stores them
+        a.grid[d] = c->grid[d];
+        a.grid_stride[d] = c->n[d] + 2;
+    }
     for (int k = 0; k < 3; ++k) {
         a.kgam[k] = k < c->nf ? c->gamma[k] : 1.0;
         a.kpinf[k] = k < c->nf ? c->pi_inf[k] : 0.0;
@@ -462,9 +469,19 @@ mfc_status mfc_set_grid(mfc_ctx* c, int dir, const double* faces, int nfaces) {
     if (c->precision == MFC_LEARNED) return fail(c, MFC_ERR_ARG, "non-uniform grids: FP64 and mixed forms only");
     if (c->weno_order != 5) return fail(c, MFC_ERR_ARG, "non-uniform grids need weno_order 5");
     const bool periodic = c->bc[2 * dir] == MFC_BC_PERIODIC;
-    std::vector<float> tab;
-    if (!grid_tables(faces, c->n[dir], periodic, tab))
+    std::vector<float> rows;
+    if (!grid_tables(faces, c->n[dir], periodic, rows))
         return fail(c, MFC_ERR_ARG, "faces must be finite and strictly increasing");
+    // device layout: x value-major (value k of cell c at pair k * (n+2) + c + 1,
+    // coalesced across the lanes of the x sweep), y and z row-major as built
+    const int nc = c->n[dir] + 2;
+    std::vector<float> tab(rows);
+    if (dir == 0)
+        for (int cell = 0; cell < nc; ++cell)
+            for (int k = 0; k < kGridRow; ++k) {
+                tab[2 * ((size_t)k * nc + cell)] = rows[((size_t)cell * kGridRow + k) * 2];
+                tab[2 * ((size_t)k * nc + cell) + 1] = rows[((size_t)cell * kGridRow + k) * 2 + 1];
+            }
     if (!c->grid[dir]) {
         cudaError_t e = cudaMalloc(&c->grid[dir], tab.size() * sizeof(float));
         if (e != cudaSuccess) {

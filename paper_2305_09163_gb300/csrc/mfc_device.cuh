@@ -79,7 +79,8 @@ struct SweepArgs {
     float tau;              // learned form: discontinuity-sensor threshold
     int yz_stream;          // y/z sweeps: 1 = stream kernel, 0 = pencil marching
     int bound;              // learned form: range safeguard on learned edge values
-    const float* grid[3];   // non-uniform directions: WENO5 rows per cell (mfc_grid.cu), else null
+    const float* grid[3];   // non-uniform directions: WENO5 table (GridCol layout), else null
+    int grid_stride[3];     // x: cells per table value (n + 2); see GridCol
     int kapila;             // 1: Kapila model, K div(u) in the volume-fraction rows
     double kgam[3], kpinf[3];   // Kapila: gamma_k and pi_inf_k of every fluid
     float kgamf[3], kpinff[3];
@@ -113,13 +114,32 @@ struct PrimArgs {
     void* w;                // primitives out [NS][ncell], Real
     unsigned long long* rate_max;  // optional: max (|u_d|+c)/dx_d as ordered bits
     int* bad;               // optional: count of non-physical cells
-    const float* grid[3];   // non-uniform directions: per-cell rows (1/dx at value 27), else null
+    const float* grid[3];   // non-uniform directions: WENO5 table (GridCol layout), else null
+    int grid_stride[3];
 };
 
-// Values per non-uniform grid row (28 values, each an FP32 pair hi, lo) and
-// the position of 1/dx in a row.
-constexpr int kGridRowFloats = 56;
+// Non-uniform grid table of one direction: 28 values per cell (mfc_grid.cu),
+// each an FP32 pair (hi, lo), for the cells c = -1..n.  Value k of cell c is the
+// pair at (c + 1) * step + k * stride: the x direction is stored value-major
+// (step 1, stride n + 2) so that the lanes of an x sweep, on consecutive cells,
+// read consecutive pairs; y and z row-major (step 28, stride 1), as all lanes
+// of a y/z sweep read the same cell.  Value 27 is 1/dx.
 constexpr int kGridInvDx = 27;
+constexpr int kGridRowValues = 28;   // values per cell (mfc_grid.h: kGridRow)
+
+// The values of one cell: value-major (x; runtime stride n + 2) or row-major
+// (y, z; consecutive, so the loads take constant offsets).
+template <bool VALUE_MAJOR>
+struct GridCol {
+    const float2* p;
+    int stride;
+    __device__ __forceinline__ GridCol(const float* grid, int stride_, int c)
+        : p(reinterpret_cast<const float2*>(grid) + (long long)(c + 1) * (VALUE_MAJOR ? 1 : kGridRowValues)),
+          stride(stride_) {}
+    __device__ __forceinline__ float2 operator[](int k) const {
+        return __ldg(p + (VALUE_MAJOR ? (long long)k * stride : (long long)k));
+    }
+};
 
 template <int NF, int NDIM> struct Layout {
     static constexpr int NS = 2 * NF + NDIM;
@@ -320,12 +340,15 @@ __device__ __forceinline__ void weno_edges(Real vc, const Real D[4], Real epsw, 
 // (no 4/3 scaling), so eps enters unscaled.  Weights normalised by
 // m = min_r (eps + beta_r) as in the uniform variants.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ df grid_df(const float* __restrict__ row, int k) {
-    return {__ldg(row + 2 * k), __ldg(row + 2 * k + 1)};
+template <class Col>
+__device__ __forceinline__ df grid_df(const Col& row, int k) {
+    const float2 v = row[k];
+    return {v.x, v.y};
 }
 
-__device__ __forceinline__ void weno5_edges_nu(double vc, const double D[4], double eps,
-                                               const float* __restrict__ row, double& eR, double& eL) {
+template <class Col>
+__device__ __forceinline__ void weno5_edges_nu(double vc, const double D[4], double eps, const Col& row,
+                                               double& eR, double& eL) {
     const df d0 = df_from_double(D[0]), d1 = df_from_double(D[1]);
     const df d2 = df_from_double(D[2]), d3 = df_from_double(D[3]);
     const df S0 = df_mul(d0, d0), S1 = df_mul(d1, d1), S2 = df_mul(d2, d2), S3 = df_mul(d3, d3);
@@ -357,9 +380,10 @@ __device__ __forceinline__ void weno5_edges_nu(double vc, const double D[4], dou
     eR = vc + df_to_double(df_div(numR, denR));
 }
 
-__device__ __forceinline__ void weno5_edges_nu(float vc, const float D[4], float eps, const float* __restrict__ row,
+template <class Col>
+__device__ __forceinline__ void weno5_edges_nu(float vc, const float D[4], float eps, const Col& row,
                                                float& eR, float& eL) {
-    auto T = [&](int k) { return __ldg(row + 2 * k); };
+    auto T = [&](int k) { return row[k].x; };
     const float S0 = D[0] * D[0], S1 = D[1] * D[1], S2 = D[2] * D[2], S3 = D[3] * D[3];
     const float b0 = fmaf(T(18), S0, fmaf(T(19), D[0] * D[1], T(20) * S1));
     const float b1 = fmaf(T(21), S1, fmaf(T(22), D[1] * D[2], T(23) * S2));
@@ -381,12 +405,13 @@ __device__ __forceinline__ void weno5_edges_nu(float vc, const float D[4], float
 }
 
 // 1/dx of cell c of a non-uniform direction, in the path's precision.
-__device__ __forceinline__ double grid_inv_dx(const float* __restrict__ grid, int c, double) {
-    const float* row = grid + (long long)(c + 1) * kGridRowFloats;
-    return df_to_double(grid_df(row, kGridInvDx));
+template <bool VALUE_MAJOR>
+__device__ __forceinline__ double grid_inv_dx(const float* grid, int stride, int c, double) {
+    return df_to_double(grid_df(GridCol<VALUE_MAJOR>(grid, stride, c), kGridInvDx));
 }
-__device__ __forceinline__ float grid_inv_dx(const float* __restrict__ grid, int c, float) {
-    return __ldg(grid + (long long)(c + 1) * kGridRowFloats + 2 * kGridInvDx);
+template <bool VALUE_MAJOR>
+__device__ __forceinline__ float grid_inv_dx(const float* grid, int stride, int c, float) {
+    return GridCol<VALUE_MAJOR>(grid, stride, c)[kGridInvDx].x;
 }
 
 template <typename Real> struct EosR {
@@ -1179,7 +1204,7 @@ __global__ void __launch_bounds__(kStreamThreads) sweep_x_stream_kernel(const Sw
         }
         if (!LEARNED && live) {
             if constexpr (NONUNIF) {
-                const float* row = a.grid[0] + (long long)(c + 1) * kGridRowFloats;
+                const GridCol<true> row(a.grid[0], a.grid_stride[0], c);
                 const Real epsn = sweep_epsw<Real, 3>(a);   // unscaled eps
 #pragma unroll
                 for (int q = 0; q < NS; ++q) weno5_edges_nu(vcv[q], Dv[q], epsn, row, eR[q], eL[q]);
@@ -1225,7 +1250,7 @@ __global__ void __launch_bounds__(kStreamThreads) sweep_x_stream_kernel(const Sw
 #pragma unroll
             for (int q = 0; q < NS; ++q) Fm[q] = sh_F[q][t];
             finish_cell<Real, NF, NDIM>(a, rowoff + (c - 1), Fm, F, sh_F[NS][t], ut, cm1,
-                                        NONUNIF ? grid_inv_dx(a.grid[0], c - 1, Real(0)) : inv_dx);
+                                        NONUNIF ? grid_inv_dx<true>(a.grid[0], a.grid_stride[0], c - 1, Real(0)) : inv_dx);
         }
         __syncthreads();
         // carry the last slot of the chunk into position 0
@@ -1366,7 +1391,7 @@ __device__ __forceinline__ void sweep_yz_stream_body(const SweepArgs& a) {
                     cm1[q] = v1;
                 }
                 if constexpr (NONUNIF) {
-                    const float* grow = a.grid[DIR] + (long long)(c + 1) * kGridRowFloats;
+                    const GridCol<false> grow(a.grid[DIR], a.grid_stride[DIR], c);
                     const Real epsn = sweep_epsw<Real, 3>(a);   // unscaled eps
 #pragma unroll
                     for (int q = 0; q < NS; ++q) weno5_edges_nu(cell[q], Dv[q], epsn, grow, eR[q], eL[q]);
@@ -1411,7 +1436,8 @@ __device__ __forceinline__ void sweep_yz_stream_body(const SweepArgs& a) {
 #pragma unroll
             for (int q = 0; q < NS; ++q) Fm[q] = sh_F[q][row][lane];
             finish_cell<Real, NF, NDIM>(a, basei + (long long)(c - 1) * sd, Fm, F, sh_F[NS][row][lane], ut, cm1,
-                                        NONUNIF ? grid_inv_dx(a.grid[DIR], c - 1, Real(0)) : inv_dx);
+                                        NONUNIF ? grid_inv_dx<false>(a.grid[DIR], a.grid_stride[DIR], c - 1, Real(0))
+                                                : inv_dx);
         }
         __syncthreads();
         // carry the last row of the chunk into row 0
@@ -1549,7 +1575,9 @@ __global__ void __launch_bounds__(256) prims_kernel(const PrimArgs a) {
                 }
 #pragma unroll
                 for (int d = 0; d < NDIM; ++d) {
-                    const Real inv = a.grid[d] ? grid_inv_dx(a.grid[d], ci[d], Real(0)) : (Real)a.g.inv_dx[d];
+                    const Real inv = !a.grid[d] ? (Real)a.g.inv_dx[d]
+                                     : d == 0 ? grid_inv_dx<true>(a.grid[d], a.grid_stride[d], ci[d], Real(0))
+                                              : grid_inv_dx<false>(a.grid[d], a.grid_stride[d], ci[d], Real(0));
                     r = real_max(r, (fabs(wv[IM + d]) + cs) * inv);
                 }
                 rate = fmax(rate, (double)r);

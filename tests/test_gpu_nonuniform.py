@@ -26,7 +26,7 @@ def mfc():
 
 def _faces(n, d, kind):
     if kind == "tanh":
-        return nu.stretched_faces(n, 0.0, 1.0, 3.0, 0.35 + 0.05 * d, 0.65 - 0.05 * d)
+        return workloads.stretched_faces(n, 0.0, 1.0, 3.0, 0.35 + 0.05 * d, 0.65 - 0.05 * d)
     xi = np.linspace(0.0, 1.0, n + 1)
     return xi + 0.5 * np.sin(2 * np.pi * xi) / (2 * np.pi)
 
@@ -85,7 +85,7 @@ def test_nonuniform_cfl_and_steps_match_oracle(mfc):
     """The paper's stretching on the small shock-bubble: CFL dt from the smallest
     cells and five SSP-RK3 steps."""
     wl = workloads.shock_bubble(24)
-    faces = [nu.stretched_faces(24, 0.0, 1.0, 4.0, 0.35, 0.65) for _ in range(3)]
+    faces = [workloads.stretched_faces(24, 0.0, 1.0, 4.0, 0.35, 0.65) for _ in range(3)]
     pb = oracle.Problem(wl.n, wl.lo, wl.hi, wl.bc, wl.gamma, wl.pi_inf, fallback=True, faces=faces)
     w = wl.prims()
     q = oracle.cons_from_prims(pb, w)

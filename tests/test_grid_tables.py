@@ -5,6 +5,7 @@ weights, smoothness indicators and 1/dx of every cell, ghost cells included."""
 import numpy as np
 import pytest
 
+import workloads
 from oracle import nonuniform as nu
 
 
@@ -20,7 +21,7 @@ def m():
 @pytest.mark.parametrize("kind", ["paper_stretching", "random"])
 def test_library_tables_match_the_oracle(m, periodic, kind):
     if kind == "paper_stretching":
-        faces = nu.stretched_faces(24, -10.0, 10.0, 4.0, -1.2, 1.2)
+        faces = workloads.stretched_faces(24, -10.0, 10.0, 4.0, -1.2, 1.2)
     else:
         faces = np.concatenate([[0.0], np.cumsum(np.random.default_rng(5).uniform(0.3, 2.0, 19))])
     lib = m.mfc_grid_table(faces, periodic)

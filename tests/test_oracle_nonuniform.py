@@ -91,7 +91,7 @@ def test_tables_scale_free_and_mirror_symmetric():
 def test_paper_stretching_refines_near_the_droplet():
     """Sec. 5's mapping with a = 4, x_a = -1.2 D, x_b = 1.2 D on [-10 D, 10 D]:
     monotone, finer between x_a and x_b than near the ends."""
-    f = nu.stretched_faces(400, -10.0, 10.0, 4.0, -1.2, 1.2)
+    f = workloads.stretched_faces(400, -10.0, 10.0, 4.0, -1.2, 1.2)
     h = np.diff(f)
     assert np.all(h > 0)
     mid = h[(f[:-1] > -1.0) & (f[1:] < 1.0)]
@@ -115,7 +115,7 @@ def test_stretched_grid_uniform_state_and_conservation():
     R = oracle.rhs(pb, oracle.cons_from_prims(pb, w))
     assert np.abs(R).max() <= 1e-12 * (1e5 + 1.3 * 400.0) / h.min()
     gam, pin = workloads.fluids(2)
-    f3 = [nu.stretched_faces(n, 0.0, 1.0, 3.0, 0.4, 0.6) for n in (10, 9, 8)]
+    f3 = [workloads.stretched_faces(n, 0.0, 1.0, 3.0, 0.4, 0.6) for n in (10, 9, 8)]
     pb3 = oracle.Problem((10, 9, 8), (0,) * 3, (1,) * 3, (0,) * 6, gam, pin, faces=f3)
     q = oracle.cons_from_prims(pb3, workloads.random_prims((10, 9, 8), 2, 11))
     R = oracle.rhs(pb3, q)

@@ -55,6 +55,7 @@ class Workload:
     seed: int | None = None
     notes: str = ""
     builder: object = field(default=None, repr=False)
+    faces: tuple | None = None   # non-uniform grid: face coordinates per direction (or None)
 
     @property
     def ndim(self) -> int:
@@ -76,8 +77,26 @@ class Workload:
         return self.builder(self)
 
 
-def _centers(n, lo, hi):
-    return [lo[d] + (np.arange(n[d]) + 0.5) * (hi[d] - lo[d]) / n[d] for d in range(3)]
+def _centers(n, lo, hi, faces=None):
+    out = []
+    for d in range(3):
+        if faces is not None and faces[d] is not None:
+            f = np.asarray(faces[d], dtype=np.float64)
+            out.append(0.5 * (f[1:] + f[:-1]))
+        else:
+            out.append(lo[d] + (np.arange(n[d]) + 0.5) * (hi[d] - lo[d]) / n[d])
+    return out
+
+
+def stretched_faces(n: int, lo: float, hi: float, a: float, xa: float, xb: float) -> np.ndarray:
+    """Face coordinates of n cells after the hyperbolic-tangent stretching the
+    paper gives for its droplet case (Sec. 5): x_s = x + (x/a)[log cosh(a(x-xa)/L)
+    + log cosh(a(x-xb)/L) - 2 log cosh(a(xb-xa)/(2L))] applied to the uniform
+    faces of [lo, hi], L = hi - lo; cells are finest between xa and xb."""
+    x = np.linspace(lo, hi, n + 1)
+    L = hi - lo
+    lc = lambda z: np.log(np.cosh(z))
+    return x + (x / a) * (lc(a * (x - xa) / L) + lc(a * (x - xb) / L) - 2.0 * lc(a * (xb - xa) / (2.0 * L)))
 
 
 def _pack(nf, ndim, rho_k, alpha, u, p):
@@ -125,19 +144,19 @@ def shock_tube(n: int = 1000) -> Workload:
 # --------------------------------------------------------------------------
 # 3D shock-bubble and shock-bubble-cloud workloads
 # --------------------------------------------------------------------------
-def _bubble_field(n, lo, hi, bubbles, width):
+def _bubble_field(n, lo, hi, bubbles, width, faces=None):
     """max over bubbles of the smeared indicator; each bubble only touches its
     bounding box so large grids stay cheap."""
-    xc, yc, zc = _centers(n, lo, hi)
+    cen = _centers(n, lo, hi, faces)
+    xc, yc, zc = cen
     ind = np.zeros((n[2], n[1], n[0]))
-    dxs = [(hi[d] - lo[d]) / n[d] for d in range(3)]
     for (cx, cy, cz, rad) in bubbles:
         reach = rad + 6.0 * width
         sl = []
         for d, c in enumerate((cx, cy, cz)):
-            a = max(0, int(math.floor((c - reach - lo[d]) / dxs[d])))
-            b = min(n[d], int(math.ceil((c + reach - lo[d]) / dxs[d])) + 1)
-            sl.append(slice(a, b))
+            a = int(np.searchsorted(cen[d], c - reach))
+            b = int(np.searchsorted(cen[d], c + reach)) + 1
+            sl.append(slice(max(0, a), min(n[d], b)))
         if any(s.start >= s.stop for s in sl):
             continue
         X = xc[sl[0]][None, None, :]
@@ -149,17 +168,17 @@ def _bubble_field(n, lo, hi, bubbles, width):
     return ind
 
 
-def _shock_region(n, lo, hi, x_shock):
-    xc = _centers(n, lo, hi)[0]
+def _shock_region(n, lo, hi, x_shock, faces=None):
+    xc = _centers(n, lo, hi, faces)[0]
     return np.broadcast_to((xc < x_shock)[None, None, :], (n[2], n[1], n[0]))
 
 
-def _two_fluid_bubbles(wl: Workload, bubbles) -> np.ndarray:
-    dx = (wl.hi[0] - wl.lo[0]) / wl.n[0]
-    air = _bubble_field(wl.n, wl.lo, wl.hi, bubbles, dx)
+def _two_fluid_bubbles(wl: Workload, bubbles, width=None) -> np.ndarray:
+    dx = (wl.hi[0] - wl.lo[0]) / wl.n[0] if width is None else width
+    air = _bubble_field(wl.n, wl.lo, wl.hi, bubbles, dx, wl.faces)
     a_air = ALPHA_MIN + (1.0 - 2.0 * ALPHA_MIN) * air
     a_w = 1.0 - a_air
-    shocked = _shock_region(wl.n, wl.lo, wl.hi, 0.05)
+    shocked = _shock_region(wl.n, wl.lo, wl.hi, wl.lo[0] + 0.05, wl.faces)
     rho_w = np.where(shocked, SHOCK_RHO, RHO_WATER)
     p = np.where(shocked, P_SHOCK, P_AMBIENT)
     ux = np.where(shocked, SHOCK_U, 0.0)
@@ -186,6 +205,30 @@ def shock_bubble(n: int = 256, steps: int = 1000) -> Workload:
         cfl=0.3, steps=steps,
         notes="air bubble R=0.1 at the centre of a water cube; 1e9 Pa shocked water for x<0.05",
         builder=_build_shock_bubble)
+
+
+def _build_shock_bubble_stretched(wl: Workload) -> np.ndarray:
+    c = [0.5 * (wl.lo[d] + wl.hi[d]) for d in range(3)]
+    # the interface is smeared over about two of the (smallest) cells around the bubble
+    width = float(min(np.diff(wl.faces[d]).min() for d in range(3)))
+    return _two_fluid_bubbles(wl, [(c[0], c[1], c[2], 0.1)], width)
+
+
+def shock_bubble_stretched(n: int = 256, a: float = 4.0, steps: int = 1000) -> Workload:
+    """The shock-bubble on a grid stretched as the paper's droplet case
+    (Sec. 5): the mapping of stretched_faces on [-0.5, 0.5] per direction with
+    x_a = -0.12, x_b = 0.12 (1.2 bubble diameters), shifted to start at 0; the
+    air bubble (R = 0.1) sits at the centre of the refined region, the shocked
+    water at x < 0.05."""
+    f = stretched_faces(n, -0.5, 0.5, a, -0.12, 0.12)
+    f = f - f[0]
+    faces = (f, f.copy(), f.copy())
+    return Workload(
+        name="shock_bubble_stretched_3d_%d" % n, n=(n, n, n), lo=(0.0,) * 3, hi=(float(f[-1]),) * 3,
+        bc=(BC_TRANSMISSIVE,) * 6, gamma=(WATER[0], AIR[0]), pi_inf=(WATER[1], AIR[1]),
+        cfl=0.3, steps=steps, faces=faces,
+        notes="shock-bubble on a tanh-stretched grid (a = %g), cells finest around the bubble" % a,
+        builder=_build_shock_bubble_stretched)
 
 
 def bubble_cloud_layout(count, seed, box_lo, box_hi, median_r, sigma, min_gap, max_tries=200000):
