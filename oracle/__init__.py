@@ -33,7 +33,7 @@ _LIB = os.path.join(_HERE, "libmfc_oracle.so")
 _lock = threading.Lock()
 _lib = None
 
-BC_PERIODIC, BC_TRANSMISSIVE, BC_REFLECTIVE = 0, 1, 2
+BC_PERIODIC, BC_TRANSMISSIVE, BC_REFLECTIVE, BC_CHARACTERISTIC = 0, 1, 2, 3
 
 
 def build(force: bool = False) -> str:
@@ -132,6 +132,8 @@ class Problem:
         if model not in self.MODELS:
             raise ValueError("model must be 'allaire' or 'kapila'")
         self.model = model
+        if model == "kapila" and BC_CHARACTERISTIC in self.bc[:2 * self.ndim]:
+            raise ValueError("characteristic boundaries are written for the Allaire model")
         self.sys_size = 2 * self.nf + self.ndim
         self.ncell = self.n[0] * self.n[1] * self.n[2]
         self.faces = [None, None, None]

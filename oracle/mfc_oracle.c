@@ -35,7 +35,11 @@
  *     oracle/nonuniform.py from the definitions.
  *   - Boundaries (Sec. 3.3): ghost cells three deep (WENO5 order); periodic,
  *     transmissive (copy of the nearest interior cell) and reflective (mirror,
- *     normal momentum negated).
+ *     normal momentum negated); and characteristic (bc 3, Sec. 3.3's
+ *     characteristic-based conditions after Thompson): stencils see
+ *     transmissive ghosts, and the boundary cell's normal contribution comes
+ *     from the characteristic amplitudes with the incoming ones set to zero
+ *     (oracle_cbc_normal).
  *
  * Optional first-order fallback (Sec. 3.2, first-order reconstruction): when a
  * reconstructed face state has a negative partial density, a volume fraction
@@ -388,12 +392,12 @@ static void fetch_cell(const oracle_params *P, const double *q, int idx[3], doub
         if (ii[d] < 0) {
             int bc = P->bc[2 * d];
             if (bc == 0) ii[d] += n;
-            else if (bc == 1) ii[d] = 0;
+            else if (bc == 1 || bc == 3) ii[d] = 0;
             else { ii[d] = -ii[d] - 1; flip = d; }
         } else if (ii[d] >= n) {
             int bc = P->bc[2 * d + 1];
             if (bc == 0) ii[d] -= n;
-            else if (bc == 1) ii[d] = n - 1;
+            else if (bc == 1 || bc == 3) ii[d] = n - 1;
             else { ii[d] = 2 * n - 1 - ii[d]; flip = d; }
         }
     }
@@ -415,6 +419,69 @@ static int face_state_ok(const oracle_params *P, const double *w) {
     mixture(P, w, &G, &Q);
     if (!((G + 1.0) * w[i_E(P)] + Q > 0.0)) return 0;
     return 1;
+}
+
+/* ---- characteristic boundary (Sec. 3.3, Thompson's characteristic-based
+ * conditions), non-reflecting ----
+ * Normal part of dq/dt at a boundary cell from the quasi-linear form of the
+ * model in primitive variables along d (Sec. 2.1, Allaire):
+ *   (a_k r_k)_t + u (a_k r_k)_x + a_k r_k u_x = 0,  u_t + u u_x + p_x / r = 0,
+ *   (u_tan)_t + u (u_tan)_x = 0,  p_t + u p_x + r c^2 u_x = 0,  a_t + u a_x = 0,
+ * c^2 = ((Gamma+1) p + Pi)/(Gamma r), written with the wave amplitudes
+ *   L1 = (u - c)(p_x - r c u_x),  L5 = (u + c)(p_x + r c u_x),
+ *   Lk = u ((a_k r_k)_x - a_k r_k p_x/(r c^2)),  Lt = u (u_tan)_x,  La = u a_x,
+ * as p_t = -(L5 + L1)/2, u_t = -(L5 - L1)/(2 r c), (a_k r_k)_t = -Lk - a_k r_k
+ * (L5 + L1)/(2 r c^2), (u_tan)_t = -Lt, a_t = -La.  Amplitudes of waves that
+ * enter the domain (speed > 0 at the low boundary, < 0 at the high one) are
+ * set to zero; the others use the one-sided difference between the boundary
+ * cell (qb) and its interior neighbour (qn), h the boundary cell's width.  The
+ * primitive rates are then turned into conserved ones. */
+void oracle_cbc_normal(const oracle_params *P, int d, int high, const double *qb, const double *qn, double h,
+                       double *out) {
+    int ns = sys_size(P), nf = P->nf, nd = P->ndim;
+    double wb[OR_MAXV], wn[OR_MAXV], wx[OR_MAXV], wt[OR_MAXV];
+    oracle_cons_to_prim(P, qb, wb);
+    oracle_cons_to_prim(P, qn, wn);
+    for (int v = 0; v < ns; ++v) wx[v] = high ? (wb[v] - wn[v]) / h : (wn[v] - wb[v]) / h;
+    double r = density(P, wb), c = sqrt(sound_speed_sq(P, wb));
+    double u = wb[i_mom(P, d)], p = wb[i_E(P)];
+    double ux = wx[i_mom(P, d)], px = wx[i_E(P)];
+    double lam1 = u - c, lam5 = u + c;
+    int in1 = high ? lam1 < 0.0 : lam1 > 0.0;
+    int in5 = high ? lam5 < 0.0 : lam5 > 0.0;
+    int inu = high ? u < 0.0 : u > 0.0;
+    double L1 = in1 ? 0.0 : lam1 * (px - r * c * ux);
+    double L5 = in5 ? 0.0 : lam5 * (px + r * c * ux);
+    for (int k = 0; k < nf; ++k) {
+        double Lk = inu ? 0.0 : u * (wx[k] - wb[k] * px / (r * c * c));
+        wt[k] = -Lk - wb[k] * (L5 + L1) / (2.0 * r * c * c);
+    }
+    for (int e = 0; e < nd; ++e) {
+        if (e == d) wt[i_mom(P, e)] = -(L5 - L1) / (2.0 * r * c);
+        else wt[i_mom(P, e)] = inu ? 0.0 : -u * wx[i_mom(P, e)];
+    }
+    wt[i_E(P)] = -0.5 * (L5 + L1);
+    for (int a = 0; a < nf - 1; ++a) wt[i_alpha(P, a)] = inu ? 0.0 : -u * wx[i_alpha(P, a)];
+    /* primitive rates -> conserved rates */
+    double rt = 0.0;
+    for (int k = 0; k < nf; ++k) { out[k] = wt[k]; rt += wt[k]; }
+    double ke = 0.0, kt = 0.0;
+    for (int e = 0; e < nd; ++e) {
+        double ue = wb[i_mom(P, e)];
+        out[i_mom(P, e)] = ue * rt + r * wt[i_mom(P, e)];
+        ke += 0.5 * ue * ue;
+        kt += ue * wt[i_mom(P, e)];
+    }
+    double G, Q, Gt = 0.0, Pt = 0.0;
+    mixture(P, wb, &G, &Q);
+    double GN = 1.0 / (P->gamma[nf - 1] - 1.0), PN = P->gamma[nf - 1] * P->pi_inf[nf - 1] / (P->gamma[nf - 1] - 1.0);
+    for (int a = 0; a < nf - 1; ++a) {
+        double Ga = 1.0 / (P->gamma[a] - 1.0), Pa = P->gamma[a] * P->pi_inf[a] / (P->gamma[a] - 1.0);
+        Gt += (Ga - GN) * wt[i_alpha(P, a)];
+        Pt += (Pa - PN) * wt[i_alpha(P, a)];
+        out[i_alpha(P, a)] = wt[i_alpha(P, a)];
+    }
+    out[i_E(P)] = G * wt[i_E(P)] + p * Gt + Pt + ke * rt + r * kt;
 }
 
 /* Flux through the face on the low side of cell (i,j,k) in direction d, i.e.
@@ -494,6 +561,18 @@ long oracle_rhs(const oracle_params *P, const double *q, double *rhs, double *fm
         for (long c = 0; c < ncell; ++c) {
             int ci[3] = {(int)(c % nx), (int)((c / nx) % ny), (int)(c / ((long)nx * ny))};
             const double inv = P->tab[d] ? tab_row(P, d, ci[d])[TAB_IDX] : inv_u;
+            int cb_high = (P->bc[2 * d + 1] == 3 && ci[d] == P->n[d] - 1);
+            int cb_low = (P->bc[2 * d] == 3 && ci[d] == 0);
+            if (cb_low || cb_high) {   /* characteristic boundary cell: normal part from the amplitudes */
+                int nb[3] = {ci[0], ci[1], ci[2]};
+                nb[d] += cb_low ? 1 : -1;
+                double qb[OR_MAXV], qn[OR_MAXV], o[OR_MAXV];
+                fetch_cell(P, q, ci, qb);
+                fetch_cell(P, q, nb, qn);
+                oracle_cbc_normal(P, d, cb_high, qb, qn, 1.0 / inv, o);
+                for (int v = 0; v < ns; ++v) rhs[(long)v * ncell + c] += o[v];
+                continue;
+            }
             int hi[3] = {ci[0], ci[1], ci[2]};
             hi[d] += 1;
             long flo = ((long)ci[2] * m[1] + ci[1]) * m[0] + ci[0];
@@ -536,6 +615,19 @@ void oracle_rhs_cells(const oracle_params *P, const double *q, long nsel, const 
         for (int v = 0; v < ns; ++v) o[v] = 0.0;
         for (int d = 0; d < P->ndim; ++d) {
             double Flo[OR_MAXV], Fhi[OR_MAXV], ulo, uhi;
+            int cb_high = (P->bc[2 * d + 1] == 3 && ci[d] == P->n[d] - 1);
+            int cb_low = (P->bc[2 * d] == 3 && ci[d] == 0);
+            if (cb_low || cb_high) {
+                int nb[3] = {ci[0], ci[1], ci[2]};
+                nb[d] += cb_low ? 1 : -1;
+                double qb[OR_MAXV], qn[OR_MAXV], ob[OR_MAXV];
+                fetch_cell(P, q, ci, qb);
+                fetch_cell(P, q, nb, qn);
+                double h = P->tab[d] ? 1.0 / tab_row(P, d, ci[d])[TAB_IDX] : P->dx[d];
+                oracle_cbc_normal(P, d, cb_high, qb, qn, h, ob);
+                for (int v = 0; v < ns; ++v) o[v] += ob[v];
+                continue;
+            }
             oracle_face(P, q, d, ci[0], ci[1], ci[2], Flo, &ulo);
             int hi[3] = {ci[0], ci[1], ci[2]};
             hi[d] += 1;
