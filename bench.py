@@ -62,6 +62,7 @@ FORMS = {
     "fp64_kapila": ("fp64", {"model": 1}, "uniform"),
     "fp64_stretched": ("fp64", {}, "stretched"),
     "mixed_stretched": ("mixed", {}, "stretched"),
+    "fp64_cbc": ("fp64", {}, "cbc"),
 }
 # RK3 stage epilogue in the last sweep: 6 per variable (stages 2, 3), 4 in stage 1
 FLOP_RK_CELL_2F = 7 * (6 + 6 + 4) / 3.0
@@ -427,7 +428,7 @@ def main():
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
     ap.add_argument("--n", type=int, default=256, help="cells per direction of the shock-bubble cube")
     ap.add_argument("--forms", default="fp64,mixed,learned,fp64_weno3,mixed_weno3,fp64_kapila,fp64_stretched,"
-                                       "mixed_stretched",
+                                       "mixed_stretched,fp64_cbc",
                     help="comma list of " + ",".join(FORMS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -477,6 +478,8 @@ def main():
         if form == "learned":
             mlp, training = train_learned(m, torch)
         fwl, fw = wl, w_dev
+        if FORMS[form][2] == "cbc":   # same cells and state, non-reflecting faces
+            fwl = workloads.shock_bubble_cbc(args.n)
         if FORMS[form][2] == "stretched":
             if stretched is None:
                 swl = workloads.shock_bubble_stretched(args.n)
@@ -533,12 +536,13 @@ def main():
         peaks = _measured_peaks()
         hbm = float(peaks.get("hbm_gbs", 6800.0))
         entry["workload"] = r["workload"]
-        if form in ("fp64_weno3", "fp64_kapila", "fp64_stretched"):
+        if form in ("fp64_weno3", "fp64_kapila", "fp64_stretched", "fp64_cbc"):
             fl = {"fp64_weno3": FLOP_SWEEP_CELL_3D_2F_W3, "fp64_kapila": FLOP_SWEEP_CELL_3D_2F_KAPILA,
-                  "fp64_stretched": FLOP_SWEEP_CELL_3D_2F}[form]
+                  "fp64_stretched": FLOP_SWEEP_CELL_3D_2F, "fp64_cbc": FLOP_SWEEP_CELL_3D_2F}[form]
             tf = (fl + FLOP_RK_CELL_2F / 3.0) * cells * r["sweep_launches"] / sweep_s / 1e12
             entry["roofline"] = {"kernel": "sweep (x, y, z), " + {"fp64_weno3": "WENO3", "fp64_kapila": "Kapila",
-                                                                  "fp64_stretched": "non-uniform grid"}[form],
+                                                                  "fp64_stretched": "non-uniform grid",
+                                                                  "fp64_cbc": "characteristic boundaries"}[form],
                                  "bound": "alu", "achieved": tf,
                                  "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": tf / FP64_PEAK_TFLOPS,
                                  "flop_per_cell_per_sweep": fl,

@@ -43,7 +43,12 @@ typedef enum {
     MFC_ERR_TIMEOUT = 6       /* reserved: a bounded device wait expired */
 } mfc_status;
 
-typedef enum { MFC_BC_PERIODIC = 0, MFC_BC_TRANSMISSIVE = 1, MFC_BC_REFLECTIVE = 2 } mfc_bc;
+typedef enum {
+    MFC_BC_PERIODIC = 0,
+    MFC_BC_TRANSMISSIVE = 1,
+    MFC_BC_REFLECTIVE = 2,
+    MFC_BC_CHARACTERISTIC = 3
+} mfc_bc;
 
 /* Arithmetic of the reconstruction and Riemann solver:
  *   MFC_FP64    everything in float64;
@@ -63,7 +68,14 @@ typedef enum { MFC_FP64 = 0, MFC_MIXED = 1, MFC_LEARNED = 2 } mfc_precision;
  *                active direction needs at least 3 cells.
  *   lo, hi       domain corners [3] (only active directions are used).
  *   bc           [6] boundary types for -x,+x,-y,+y,-z,+z (mfc_bc); periodic
- *                must be set on both faces of a direction.
+ *                must be set on both faces of a direction.  Characteristic
+ *                (non-reflecting, Sec. 3.3 after Thompson): ghost cells as
+ *                transmissive for the faces of interior cells, while the
+ *                boundary cell's normal rate comes from the wave amplitudes
+ *                of the quasi-linear primitive system (one-sided difference
+ *                to the interior neighbour over the boundary cell's width),
+ *                with the amplitudes of incoming waves set to zero.  FP64 and
+ *                mixed forms, Allaire model only (MFC_ERR_ARG otherwise).
  *   num_fluids   N in 1..3; gamma[N] > 1, pi_inf[N] >= 0 (Pa).
  *   precision    mfc_precision.
  *   cuda_stream  cudaStream_t to use, or NULL for the legacy default stream.

@@ -137,6 +137,12 @@ mfc_status launch(mfc_ctx* c, int cat, F&& fn) {
 
 bool nonuniform(const mfc_ctx* c) { return c->grid[0] || c->grid[1] || c->grid[2]; }
 
+bool has_cbc(const mfc_ctx* c) {
+    for (int i = 0; i < 2 * c->ndim; ++i)
+        if (c->bc[i] == MFC_BC_CHARACTERISTIC) return true;
+    return false;
+}
+
 cudaError_t dispatch_sweep(const mfc_ctx* c, const SweepArgs& a, int dir) {
     if (nonuniform(c)) {
         if (is_f32(c)) {
@@ -250,6 +256,7 @@ SweepArgs base_sweep(const mfc_ctx* c) {
     a.yz_stream = c->yz_stream >= 0 ? c->yz_stream : 1;
     a.bound = c->bound;
     a.kapila = c->kapila;
+    a.cbc = has_cbc(c);
     for (int d = 0; d < 3; ++d) {   // layouts as mfc_set_grid stores them
         a.grid[d] = c->grid[d];
         a.grid_stride[d] = c->n[d] + 2;
@@ -345,8 +352,13 @@ mfc_status mfc_init(mfc_ctx** out, int nx, int ny, int nz, const double lo[3], c
         if (d >= ndim && n[d] != 1) return MFC_ERR_ARG;
         if (d < ndim && !(hi[d] > lo[d]) ) return MFC_ERR_ARG;
     }
-    for (int i = 0; i < 6; ++i)
-        if (bc[i] < 0 || bc[i] > 2) return MFC_ERR_ARG;
+    bool any_cbc = false;
+    for (int i = 0; i < 6; ++i) {
+        if (bc[i] < MFC_BC_PERIODIC || bc[i] > MFC_BC_CHARACTERISTIC) return MFC_ERR_ARG;
+        any_cbc |= i < 2 * ndim && bc[i] == MFC_BC_CHARACTERISTIC;
+    }
+    // characteristic boundaries: FP64 and mixed forms
+    if (any_cbc && precision == MFC_LEARNED) return MFC_ERR_ARG;
     for (int d = 0; d < ndim; ++d)
         if ((bc[2 * d] == MFC_BC_PERIODIC) != (bc[2 * d + 1] == MFC_BC_PERIODIC)) return MFC_ERR_ARG;
     for (int k = 0; k < num_fluids; ++k)
@@ -451,6 +463,8 @@ mfc_status mfc_set_param(mfc_ctx* c, const char* name, double value) {
         c->rk_order = (int)value;
     } else if (!strcmp(name, "model")) {
         if (value != 0.0 && value != 1.0) return fail(c, MFC_ERR_ARG, "model must be 0 (Allaire) or 1 (Kapila)");
+        if (value == 1.0 && has_cbc(c))
+            return fail(c, MFC_ERR_ARG, "characteristic boundaries are defined for the Allaire model (model 0)");
         c->kapila = (int)value;
     } else if (!strcmp(name, "profile")) {
         if (value != 0.0 && value != 1.0) return fail(c, MFC_ERR_ARG, "profile must be 0 or 1");

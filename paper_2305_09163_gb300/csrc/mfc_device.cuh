@@ -30,7 +30,7 @@
 
 namespace mfc {
 
-enum { BC_PERIODIC = 0, BC_TRANSMISSIVE = 1, BC_REFLECTIVE = 2 };
+enum { BC_PERIODIC = 0, BC_TRANSMISSIVE = 1, BC_REFLECTIVE = 2, BC_CHARACTERISTIC = 3 };
 
 struct Geometry {
     int n[3];
@@ -81,6 +81,7 @@ struct SweepArgs {
     int bound;              // learned form: range safeguard on learned edge values
     const float* grid[3];   // non-uniform directions: WENO5 table (GridCol layout), else null
     int grid_stride[3];     // x: cells per table value (n + 2); see GridCol
+    int cbc;                // some boundary is characteristic (the stream kernels handle it)
     int kapila;             // 1: Kapila model, K div(u) in the volume-fraction rows
     double kgam[3], kpinf[3];   // Kapila: gamma_k and pi_inf_k of every fluid
     float kgamf[3], kpinff[3];
@@ -157,13 +158,13 @@ __host__ __device__ inline long long stride_of(const Geometry& g, int d) {
 __device__ __forceinline__ int ghost_map(int i, int n, int bclo, int bchi, bool* flip) {
     if (i < 0) {
         if (bclo == BC_PERIODIC) return i + n;
-        if (bclo == BC_TRANSMISSIVE) return 0;
+        if (bclo == BC_TRANSMISSIVE || bclo == BC_CHARACTERISTIC) return 0;
         *flip = true;
         return -i - 1;
     }
     if (i >= n) {
         if (bchi == BC_PERIODIC) return i - n;
-        if (bchi == BC_TRANSMISSIVE) return n - 1;
+        if (bchi == BC_TRANSMISSIVE || bchi == BC_CHARACTERISTIC) return n - 1;
         *flip = true;
         return 2 * n - 1 - i;
     }
@@ -805,6 +806,72 @@ __device__ __forceinline__ void face_flux_learned(const SweepArgs& a, const EosR
 
 // Finish one cell: flux difference + alpha div(u) source, then the epilogue
 // selected by a.mode.
+// Characteristic (non-reflecting) boundary (Sec. 3.3: characteristic-based
+// conditions after Thompson).  Normal part of dq/dt of a boundary cell from
+// the quasi-linear primitive equations along DIR, written with the wave
+// amplitudes L1 = (u - c)(p_x - r c u_x), L5 = (u + c)(p_x + r c u_x),
+// Lk = u ((a_k r_k)_x - a_k r_k p_x/(r c^2)) and u (.)_x for the tangential
+// velocities and volume fractions; the amplitudes of waves entering the domain
+// (speed > 0 at the low boundary, < 0 at the high one) are zero.  wb: the
+// cell's primitives, wx: their one-sided derivative towards the interior
+// neighbour.  Rates: p_t = -(L5 + L1)/2, u_t = -(L5 - L1)/(2 r c),
+// (a_k r_k)_t = -Lk - a_k r_k (L5 + L1)/(2 r c^2), others -L; then conserved.
+// Not inlined: only boundary cells run it.
+template <typename Real, int NF, int NDIM, int DIR>
+__device__ __noinline__ void cbc_rate(const EosR<Real>& e, const Real* wb, const Real* wx, bool high, Real* out) {
+    using Lay = Layout<NF, NDIM>;
+    constexpr int NS = Lay::NS, IM = Lay::IM, IE = Lay::IE, IA = Lay::IA;
+    Real r = 0, G = e.G_N, P = e.P_N;
+#pragma unroll
+    for (int k = 0; k < NF; ++k) r += wb[k];
+#pragma unroll
+    for (int k = 0; k < NF - 1; ++k) {
+        G = fma(e.dG[k], wb[IA + k], G);
+        P = fma(e.dP[k], wb[IA + k], P);
+    }
+    const Real p = wb[IE], u = wb[IM + DIR];
+    const Real rc2 = ((G + (Real)1) * p + P) / G;          // r c^2
+    const Real c = sqrt(rc2 / r);
+    const Real ux = wx[IM + DIR], px = wx[IE];
+    const Real lam1 = u - c, lam5 = u + c;
+    const bool in1 = high ? lam1 < (Real)0 : lam1 > (Real)0;
+    const bool in5 = high ? lam5 < (Real)0 : lam5 > (Real)0;
+    const bool inu = high ? u < (Real)0 : u > (Real)0;
+    const Real L1 = in1 ? (Real)0 : lam1 * (px - r * c * ux);
+    const Real L5 = in5 ? (Real)0 : lam5 * (px + r * c * ux);
+    const Real ac = (L5 + L1) / (2 * rc2);
+    Real wt[NS];
+#pragma unroll
+    for (int k = 0; k < NF; ++k) wt[k] = -(inu ? (Real)0 : u * (wx[k] - wb[k] * px / rc2)) - wb[k] * ac;
+#pragma unroll
+    for (int m = 0; m < NDIM; ++m) wt[IM + m] = m == DIR ? -(L5 - L1) / (2 * r * c) : (inu ? (Real)0 : -u * wx[IM + m]);
+    wt[IE] = -(L5 + L1) / 2;
+#pragma unroll
+    for (int k = 0; k < NF - 1; ++k) wt[IA + k] = inu ? (Real)0 : -u * wx[IA + k];
+    Real rt = 0;
+#pragma unroll
+    for (int k = 0; k < NF; ++k) {
+        out[k] = wt[k];
+        rt += wt[k];
+    }
+    Real ke = 0, kt = 0;
+#pragma unroll
+    for (int m = 0; m < NDIM; ++m) {
+        const Real um = wb[IM + m];
+        out[IM + m] = fma(um, rt, r * wt[IM + m]);
+        ke = fma((Real)0.5 * um, um, ke);
+        kt = fma(um, wt[IM + m], kt);
+    }
+    Real Gt = 0, Pt = 0;
+#pragma unroll
+    for (int k = 0; k < NF - 1; ++k) {
+        Gt = fma(e.dG[k], wt[IA + k], Gt);
+        Pt = fma(e.dP[k], wt[IA + k], Pt);
+        out[IA + k] = wt[IA + k];
+    }
+    out[IE] = G * wt[IE] + p * Gt + Pt + ke * rt + r * kt;
+}
+
 // Kapila coefficients (Sec. 2.1, 5-equation models): the volume-fraction rows
 // carry (alpha_k + K_k) div(u) instead of alpha_k div(u), with
 //   K_k = alpha_k (rho c_W^2 / Z_k - 1),  1/(rho c_W^2) = sum_j alpha_j / Z_j,
@@ -885,9 +952,33 @@ __device__ __forceinline__ void kapila_K_df(const SweepArgs& a, const double* w,
     for (int k = 0; k < NF - 1; ++k) K[k] = df_to_double(df_mul(al[k], df_add(df_div(pe[k], D), {-1.f, 0.f})));
 }
 
-template <typename Real, int NF, int NDIM>
+// Normal rate of a characteristic boundary cell (flat index idx, neighbours
+// sd apart along DIR; n cells along DIR) from its primitives and those of its
+// interior neighbour.
+template <typename Real, int NF, int NDIM, int DIR>
+__device__ __noinline__ void cbc_cell_rate(const SweepArgs& a, long long idx, long long sd, int n, bool high,
+                                           Real inv_dx, Real* out) {
+    using Lay = Layout<NF, NDIM>;
+    constexpr int NS = Lay::NS;
+    const Real* __restrict__ w = static_cast<const Real*>(a.w);
+    const long long nc = a.g.ncell;
+    const long long nb = n > 1 ? (high ? idx - sd : idx + sd) : idx;   // one cell: no gradient
+    Real wb[NS], wx[NS];
+#pragma unroll
+    for (int q = 0; q < NS; ++q) {
+        wb[q] = w[q * nc + idx];
+        const Real wn = w[q * nc + nb];
+        wx[q] = (high ? wb[q] - wn : wn - wb[q]) * inv_dx;
+    }
+    cbc_rate<Real, NF, NDIM, DIR>(sweep_eos<Real>(a), wb, wx, high, out);
+}
+
+// Finish cell idx (coordinate b along DIR, neighbours sd apart): flux
+// difference and alpha div(u) source, or, at a characteristic boundary, the
+// boundary rate; then store, accumulate or apply the RK stage.
+template <typename Real, int NF, int NDIM, int DIR>
 __device__ __forceinline__ void finish_cell(const SweepArgs& a, long long idx, const Real* Fm, const Real* Fp,
-                                            Real um, Real up, const Real* cell, Real inv_dx) {
+                                            Real um, Real up, const Real* cell, Real inv_dx, int b, long long sd) {
     using Lay = Layout<NF, NDIM>;
     constexpr int NS = Lay::NS, IA = Lay::IA;
     Real out[NS];
@@ -904,6 +995,17 @@ __device__ __forceinline__ void finish_cell(const SweepArgs& a, long long idx, c
         } else {
 #pragma unroll
             for (int k = 0; k < NF - 1; ++k) out[IA + k] = fma(cell[IA + k], du, out[IA + k]);
+        }
+    }
+    if (a.cbc) {
+        const int n = a.g.n[DIR];
+        const bool lo = b == 0 && a.g.bc_lo[DIR] == BC_CHARACTERISTIC;
+        const bool hi = b == n - 1 && a.g.bc_hi[DIR] == BC_CHARACTERISTIC;
+        if (lo || hi) {   // the boundary rate replaces the flux difference and the source
+            Real cb[NS];
+            cbc_cell_rate<Real, NF, NDIM, DIR>(a, idx, sd, n, !lo, inv_dx, cb);
+#pragma unroll
+            for (int v = 0; v < NS; ++v) out[v] = cb[v];
         }
     }
     const long long nc = a.g.ncell;
@@ -1037,7 +1139,8 @@ __global__ void __launch_bounds__(128) sweep_kernel(const SweepArgs a) {
             else
                 face_flux<Real, NF, NDIM, DIR>(a, e, eLprev, eR, cm1, vc, F, ut);
             if (c >= s0 + 1 && active)
-                finish_cell<Real, NF, NDIM>(a, base + (long long)(c - 1) * sd, Fprev, F, utprev, ut, cm1, inv_dx);
+                finish_cell<Real, NF, NDIM, DIR>(a, base + (long long)(c - 1) * sd, Fprev, F, utprev, ut, cm1, inv_dx,
+                                                 c - 1, sd);
 #pragma unroll
             for (int v = 0; v < NS; ++v) Fprev[v] = F[v];
             utprev = ut;
@@ -1249,8 +1352,9 @@ __global__ void __launch_bounds__(kStreamThreads) sweep_x_stream_kernel(const Sw
             Real Fm[NS];
 #pragma unroll
             for (int q = 0; q < NS; ++q) Fm[q] = sh_F[q][t];
-            finish_cell<Real, NF, NDIM>(a, rowoff + (c - 1), Fm, F, sh_F[NS][t], ut, cm1,
-                                        NONUNIF ? grid_inv_dx<true>(a.grid[0], a.grid_stride[0], c - 1, Real(0)) : inv_dx);
+            finish_cell<Real, NF, NDIM, 0>(a, rowoff + (c - 1), Fm, F, sh_F[NS][t], ut, cm1,
+                                           NONUNIF ? grid_inv_dx<true>(a.grid[0], a.grid_stride[0], c - 1, Real(0)) : inv_dx,
+                                           c - 1, 1);
         }
         __syncthreads();
         // carry the last slot of the chunk into position 0
@@ -1435,9 +1539,10 @@ __device__ __forceinline__ void sweep_yz_stream_body(const SweepArgs& a) {
             Real Fm[NS];
 #pragma unroll
             for (int q = 0; q < NS; ++q) Fm[q] = sh_F[q][row][lane];
-            finish_cell<Real, NF, NDIM>(a, basei + (long long)(c - 1) * sd, Fm, F, sh_F[NS][row][lane], ut, cm1,
-                                        NONUNIF ? grid_inv_dx<false>(a.grid[DIR], a.grid_stride[DIR], c - 1, Real(0))
-                                                : inv_dx);
+            finish_cell<Real, NF, NDIM, DIR>(a, basei + (long long)(c - 1) * sd, Fm, F, sh_F[NS][row][lane], ut, cm1,
+                                             NONUNIF ? grid_inv_dx<false>(a.grid[DIR], a.grid_stride[DIR], c - 1, Real(0))
+                                                     : inv_dx,
+                                             c - 1, sd);
         }
         __syncthreads();
         // carry the last row of the chunk into row 0

@@ -68,7 +68,7 @@ mfc_status scratch_for_current_device(double** out, char* err, int err_len) {
 
 template <int NF>
 cudaError_t run(const Geometry& g, const EosConst& e, int ndim, const double* q, double* rhs, double* w,
-                double eps, int fallback, cudaStream_t s) {
+                double eps, int fallback, int cbc, cudaStream_t s) {
     PrimArgs pa{};
     pa.g = g;
     pa.e = e;
@@ -88,6 +88,7 @@ cudaError_t run(const Geometry& g, const EosConst& e, int ndim, const double* q,
         a.eps = eps;
         a.fallback = fallback;
         a.fallback_count = nullptr;
+        a.cbc = cbc;
         sweep_set_f32_constants(a);
         const long long trans = g.ncell / g.n[d];
         int L = 64;
@@ -118,8 +119,12 @@ extern "C" mfc_status mfc_rhs_noalloc(const double* q, double* rhs, int nx, int 
         if (d >= ndim && n[d] != 1)
             return noalloc_fail(err, err_len, MFC_ERR_ARG, "inactive directions must have 1 cell");
     }
-    for (int i = 0; i < 6; ++i)
-        if (bc[i] < 0 || bc[i] > 2) return noalloc_fail(err, err_len, MFC_ERR_ARG, "unknown boundary type");
+    int cbc = 0;
+    for (int i = 0; i < 6; ++i) {
+        if (bc[i] < MFC_BC_PERIODIC || bc[i] > MFC_BC_CHARACTERISTIC)
+            return noalloc_fail(err, err_len, MFC_ERR_ARG, "unknown boundary type");
+        cbc |= i < 2 * ndim && bc[i] == MFC_BC_CHARACTERISTIC;
+    }
     for (int d = 0; d < ndim; ++d)
         if ((bc[2 * d] == MFC_BC_PERIODIC) != (bc[2 * d + 1] == MFC_BC_PERIODIC))
             return noalloc_fail(err, err_len, MFC_ERR_ARG, "periodic must be set on both faces of a direction");
@@ -167,9 +172,9 @@ extern "C" mfc_status mfc_rhs_noalloc(const double* q, double* rhs, int nx, int 
     cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
     cudaError_t rc;
     switch (N) {
-        case 1: rc = run<1>(g, e, ndim, q, rhs, w, weno_eps, fallback, s); break;
-        case 2: rc = run<2>(g, e, ndim, q, rhs, w, weno_eps, fallback, s); break;
-        default: rc = run<3>(g, e, ndim, q, rhs, w, weno_eps, fallback, s); break;
+        case 1: rc = run<1>(g, e, ndim, q, rhs, w, weno_eps, fallback, cbc, s); break;
+        case 2: rc = run<2>(g, e, ndim, q, rhs, w, weno_eps, fallback, cbc, s); break;
+        default: rc = run<3>(g, e, ndim, q, rhs, w, weno_eps, fallback, cbc, s); break;
     }
     if (rc != cudaSuccess) {
         char buf[256];

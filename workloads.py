@@ -35,7 +35,7 @@ SHOCK_RHO = 1230.377372836252
 SHOCK_U = 432.69216080845405
 SHOCK_SPEED = 2310.880784462928
 
-BC_PERIODIC, BC_TRANSMISSIVE, BC_REFLECTIVE = 0, 1, 2
+BC_PERIODIC, BC_TRANSMISSIVE, BC_REFLECTIVE, BC_CHARACTERISTIC = 0, 1, 2, 3
 
 
 @dataclass
@@ -204,6 +204,17 @@ def shock_bubble(n: int = 256, steps: int = 1000) -> Workload:
         bc=(BC_TRANSMISSIVE,) * 6, gamma=(WATER[0], AIR[0]), pi_inf=(WATER[1], AIR[1]),
         cfl=0.3, steps=steps,
         notes="air bubble R=0.1 at the centre of a water cube; 1e9 Pa shocked water for x<0.05",
+        builder=_build_shock_bubble)
+
+
+def shock_bubble_cbc(n: int = 256, steps: int = 1000) -> Workload:
+    """The shock-bubble with characteristic (non-reflecting) boundaries on all
+    six faces instead of transmissive ghost cells; same initial state."""
+    return Workload(
+        name="shock_bubble_cbc_3d_%d" % n, n=(n, n, n), lo=(0.0,) * 3, hi=(1.0,) * 3,
+        bc=(BC_CHARACTERISTIC,) * 6, gamma=(WATER[0], AIR[0]), pi_inf=(WATER[1], AIR[1]),
+        cfl=0.3, steps=steps,
+        notes="shock_bubble_3d with non-reflecting faces",
         builder=_build_shock_bubble)
 
 
