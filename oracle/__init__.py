@@ -7,11 +7,13 @@ package.
 
 Contents (each cites the passage of arXiv 2305.09163 it follows):
   * ``mfc_oracle.c`` (loaded with ctypes): EOS (Sec. 2.1, Eq. "soe"), the Allaire
-    and Kapila five-equation models (Sec. 2.1), WENO5-JS
+    and Kapila five-equation models (Sec. 2.1), the six-equation model and its
+    pressure relaxation (Sec. 2.3), WENO5-JS
     and WENO3-JS (Sec. 3.2), HLLC (Sec. 3.2.1), ghost cells (Sec. 3.3), the semi-discrete
     operator (Sec. 3.1, Eq. "fvmdis") and the CFL rate.
-  * this module: SSP-RK1/2/3 (Sec. 3.4, Gottlieb & Shu TVD Runge-Kutta) and the
-    CFL time step, in plain numpy on top of the C right-hand side.
+  * this module: SSP-RK1/2/3 (Sec. 3.4, Gottlieb & Shu TVD Runge-Kutta; for the
+    six-equation model every stage is followed by the pressure relaxation) and
+    the CFL time step, in plain numpy on top of the C right-hand side.
   * ``exact_riemann``: exact two-material stiffened-gas Riemann solution used to
     judge shock-tube runs.
   * ``mlp``: FP64 forward/backward of the learned-weight network.
@@ -95,6 +97,10 @@ def _load():
             lib.oracle_rhs_cells.argtypes = [P, dp, ctypes.c_long, lp, dp, dp]
             lib.oracle_max_rate.argtypes = [P, dp, lp]
             lib.oracle_max_rate.restype = ctypes.c_double
+            lib.oracle_relax6.argtypes = [P, dp]
+            lib.oracle_relax6.restype = ctypes.c_double
+            lib.oracle_relax6_array.argtypes = [P, dp, ctypes.c_long]
+            lib.oracle_relax6_array.restype = ctypes.c_long
             _lib = lib
     return _lib
 
@@ -106,7 +112,7 @@ def _dp(a: np.ndarray):
 class Problem:
     """Grid, boundary types and fluids of one problem (Sec. 3.1 uniform grid)."""
 
-    MODELS = {"allaire": 0, "kapila": 1}
+    MODELS = {"allaire": 0, "kapila": 1, "six": 2}
 
     def __init__(self, n, lo, hi, bc, gamma, pi_inf, eps=1e-6, fallback=False, weno_order=5, model="allaire",
                  faces=None):
@@ -130,11 +136,13 @@ class Problem:
             raise ValueError("weno_order must be 3 or 5")
         self.weno_order = int(weno_order)
         if model not in self.MODELS:
-            raise ValueError("model must be 'allaire' or 'kapila'")
+            raise ValueError("model must be 'allaire', 'kapila' or 'six'")
         self.model = model
-        if model == "kapila" and BC_CHARACTERISTIC in self.bc[:2 * self.ndim]:
+        if model != "allaire" and BC_CHARACTERISTIC in self.bc[:2 * self.ndim]:
             raise ValueError("characteristic boundaries are written for the Allaire model")
-        self.sys_size = 2 * self.nf + self.ndim
+        # six-equation model: the phase internal energies (conserved) or pressures
+        # (primitive) follow the volume fractions
+        self.sys_size = (3 if model == "six" else 2) * self.nf + self.ndim
         self.ncell = self.n[0] * self.n[1] * self.n[2]
         self.faces = [None, None, None]
         self._tabs = [None, None, None]
@@ -308,30 +316,60 @@ def cfl_dt(pb: Problem, q, cfl: float) -> float:
     return cfl / m
 
 
+def relax(pb: Problem, q) -> np.ndarray:
+    """Six-equation model: pressure relaxation with infinite stiffness of every
+    cell (Sec. 2.3; oracle_relax6), returning a new state."""
+    if pb.model != "six":
+        raise ValueError("relaxation belongs to the six-equation model")
+    q = np.array(_state(pb, q), dtype=np.float64)
+    bad = _load().oracle_relax6_array(ctypes.byref(pb.params()), _dp(q), pb.ncell)
+    if bad:
+        raise FloatingPointError("relaxation failed in %d cells" % bad)
+    return q.reshape(pb.shape())
+
+
+def relax_cell(pb: Problem, q):
+    """Relax one conserved cell state; returns (relaxed state, relaxed pressure p^)."""
+    q = np.array(q, dtype=np.float64)
+    ph = _load().oracle_relax6(ctypes.byref(pb.params()), _dp(q))
+    return q, ph
+
+
+def _stage_end(pb):
+    """What ends every Runge-Kutta stage: the relaxation for the six-equation
+    model, nothing otherwise (also for pb = None, a bare ODE)."""
+    return (lambda s: relax(pb, s)) if pb is not None and pb.model == "six" else (lambda s: s)
+
+
 def rk3_step(pb: Problem, q, dt: float, rhs_fn=None):
     """One SSP-RK3 step in Shu-Osher form (Gottlieb & Shu 1998; Sec. 3.4):
     q1 = q + dt R(q); q2 = 3/4 q + 1/4 (q1 + dt R(q1)); q' = 1/3 q + 2/3 (q2 + dt R(q2)).
+    Six-equation model: each of q1, q2 and q' is relaxed (Sec. 2.3: the
+    hyperbolic update first, then the relaxation).
     """
     f = rhs_fn if rhs_fn is not None else (lambda s: rhs(pb, s))
+    g = _stage_end(pb)
     q = np.asarray(q, dtype=np.float64)
-    q1 = q + dt * f(q)
-    q2 = 0.75 * q + 0.25 * (q1 + dt * f(q1))
-    return q / 3.0 + (2.0 / 3.0) * (q2 + dt * f(q2))
+    q1 = g(q + dt * f(q))
+    q2 = g(0.75 * q + 0.25 * (q1 + dt * f(q1)))
+    return g(q / 3.0 + (2.0 / 3.0) * (q2 + dt * f(q2)))
 
 
 def rk_step(pb: Problem, q, dt: float, order: int = 3, rhs_fn=None):
     """One step of the SSP Runge-Kutta scheme of the given order (Sec. 3.4,
     Gottlieb & Shu TVD Runge-Kutta family): 1 = forward Euler;
-    2 = q1 = q + dt R(q), q' = 1/2 q + 1/2 (q1 + dt R(q1)); 3 = rk3_step."""
+    2 = q1 = q + dt R(q), q' = 1/2 q + 1/2 (q1 + dt R(q1)); 3 = rk3_step.
+    Six-equation model: every stage is relaxed."""
     f = rhs_fn if rhs_fn is not None else (lambda s: rhs(pb, s))
+    g = _stage_end(pb)
     q = np.asarray(q, dtype=np.float64)
     if order == 3:
         return rk3_step(pb, q, dt, rhs_fn=f)
-    q1 = q + dt * f(q)
+    q1 = g(q + dt * f(q))
     if order == 1:
         return q1
     if order == 2:
-        return 0.5 * q + 0.5 * (q1 + dt * f(q1))
+        return g(0.5 * q + 0.5 * (q1 + dt * f(q1)))
     raise ValueError("order must be 1, 2 or 3")
 
 

@@ -41,6 +41,20 @@
  *     from the characteristic amplitudes with the incoming ones set to zero
  *     (oracle_cbc_normal).
  *
+ *   - With model = 2, the six-equation model with pressure relaxation (Sec. 2.3,
+ *     after Saurel, Petitpas & Berry 2009 and Schmidmayer et al. 2020): each
+ *     phase also carries its internal energy a_k r_k e_k, obeying
+ *     d(a_k r_k e_k)/dt + div(a_k r_k e_k u) + a_k p_k div(u) = 0, and waves
+ *     travel at the frozen sound speed, r c^2 = sum a_k g_k (p_k + pinf_k).
+ *     After every Runge-Kutta stage the state is relaxed to one pressure with
+ *     infinite stiffness (oracle_relax6), so the right-hand side always acts
+ *     on states with p_k = p: it takes p from the total energy and the mixture
+ *     law (as the five-equation model does), the phase energies at the faces
+ *     as a_k (p + g_k pinf_k)/(g_k - 1), and the work term as a_k p div(u).
+ *     The primitive vector carries, after the five-equation variables, the
+ *     phase pressures (g_k - 1) a_k r_k e_k / a_k - g_k pinf_k of the state
+ *     (informative; the right-hand side does not read them).
+ *
  * Optional first-order fallback (Sec. 3.2, first-order reconstruction): when a
  * reconstructed face state has a negative partial density, a volume fraction
  * outside [0,1] or (Gamma+1)p+Pi <= 0, both sides of that face use the cell
@@ -54,7 +68,7 @@
 #include <string.h>
 
 #define OR_MAXF 3             /* fluids */
-#define OR_MAXV (2 * OR_MAXF + 3) /* conserved variables */
+#define OR_MAXV (3 * OR_MAXF + 3) /* conserved variables (six-equation model) */
 
 typedef struct {
     int n[3];          /* cells per direction; 1 for an inactive direction */
@@ -67,7 +81,8 @@ typedef struct {
     double eps;        /* WENO epsilon */
     int fallback;      /* first-order fallback at non-physical faces */
     int weno_order;    /* 5 (default) or 3 */
-    int model;         /* 0: Allaire (K = 0); 1: Kapila (K div u in the alpha rows) */
+    int model;         /* 0: Allaire (K = 0); 1: Kapila (K div u in the alpha rows);
+                          2: six-equation (phase internal energies; relaxation between stages) */
     const double *tab[3]; /* non-uniform grid: per-direction WENO5 tables (NULL: uniform) */
 } oracle_params;
 
@@ -111,11 +126,15 @@ static double weno5_table(const double *row, int side, const double *st, double 
     return st[2] + (a[0] * p[0] + a[1] * p[1] + a[2] * p[2]) / s;
 }
 
-/* ---- variable indexing (conserved and primitive share positions) ---- */
-static int sys_size(const oracle_params *P) { return 2 * P->nf + P->ndim; }
+/* ---- variable indexing (conserved and primitive share positions) ----
+ * a_k r_k (N), r u or u (ndim), r E or p (1), a_k (N-1); the six-equation model
+ * appends a_k r_k e_k or p_k (N). */
+static int six(const oracle_params *P) { return P->model == 2; }
+static int sys_size(const oracle_params *P) { return (six(P) ? 3 : 2) * P->nf + P->ndim; }
 static int i_mom(const oracle_params *P, int d) { return P->nf + d; }
 static int i_E(const oracle_params *P) { return P->nf + P->ndim; }
 static int i_alpha(const oracle_params *P, int k) { return P->nf + P->ndim + 1 + k; }
+static int i_int(const oracle_params *P, int k) { return 2 * P->nf + P->ndim + k; }
 
 int oracle_sys_size(const oracle_params *P) { return sys_size(P); }
 
@@ -181,6 +200,12 @@ void oracle_cons_to_prim(const oracle_params *P, const double *q, double *w) {
     double G, Q;
     mixture(P, q, &G, &Q);
     w[i_E(P)] = (q[i_E(P)] - ke - Q) / G;
+    if (six(P)) {   /* phase pressures from the internal energies */
+        double a[OR_MAXF];
+        all_alphas(P, q, a);
+        for (int k = 0; k < P->nf; ++k)
+            w[i_int(P, k)] = (P->gamma[k] - 1.0) * q[i_int(P, k)] / a[k] - P->gamma[k] * P->pi_inf[k];
+    }
 }
 
 /* Primitive -> conserved for one cell. */
@@ -193,6 +218,16 @@ void oracle_prim_to_cons(const oracle_params *P, const double *w, double *q) {
         double u = w[i_mom(P, d)];
         q[i_mom(P, d)] = r * u;
         ke += 0.5 * r * u * u;
+    }
+    if (six(P)) {   /* a_k r_k e_k = a_k (p_k + g_k pinf_k)/(g_k - 1); r E = sum + kinetic */
+        double a[OR_MAXF], e = 0.0;
+        all_alphas(P, w, a);
+        for (int k = 0; k < P->nf; ++k) {
+            q[i_int(P, k)] = a[k] * (w[i_int(P, k)] + P->gamma[k] * P->pi_inf[k]) / (P->gamma[k] - 1.0);
+            e += q[i_int(P, k)];
+        }
+        q[i_E(P)] = e + ke;
+        return;
     }
     double G, Q;
     mixture(P, w, &G, &Q);
@@ -221,8 +256,16 @@ void oracle_cons_to_prim_array(const oracle_params *P, const double *q, double *
     }
 }
 
-/* Squared sound speed ((Gamma+1)p + Pi)/(Gamma rho) of a primitive state. */
+/* Squared sound speed ((Gamma+1)p + Pi)/(Gamma rho) of a primitive state;
+ * six-equation model: the frozen sound speed sum a_k g_k (p + pinf_k) / rho of
+ * the phases at the mixture pressure. */
 static double sound_speed_sq(const oracle_params *P, const double *w) {
+    if (six(P)) {
+        double a[OR_MAXF], s = 0.0;
+        all_alphas(P, w, a);
+        for (int k = 0; k < P->nf; ++k) s += a[k] * P->gamma[k] * (w[i_E(P)] + P->pi_inf[k]);
+        return s / density(P, w);
+    }
     double G, Q;
     mixture(P, w, &G, &Q);
     return ((G + 1.0) * w[i_E(P)] + Q) / (G * density(P, w));
@@ -307,16 +350,16 @@ static void physical_flux(const oracle_params *P, int d, const double *w, double
     double r = density(P, w);
     double un = w[i_mom(P, d)];
     double p = w[i_E(P)];
-    double G, Q;
-    mixture(P, w, &G, &Q);
-    double ke = 0.0;
-    for (int e = 0; e < P->ndim; ++e) ke += 0.5 * r * w[i_mom(P, e)] * w[i_mom(P, e)];
-    double rE = G * p + Q + ke;
+    double q[OR_MAXV];
+    oracle_prim_to_cons(P, w, q);
+    double rE = q[i_E(P)];
     for (int k = 0; k < P->nf; ++k) F[k] = w[k] * un;
     for (int e = 0; e < P->ndim; ++e) F[i_mom(P, e)] = r * w[i_mom(P, e)] * un;
     F[i_mom(P, d)] += p;
     F[i_E(P)] = (rE + p) * un;
     for (int k = 0; k < P->nf - 1; ++k) F[i_alpha(P, k)] = w[i_alpha(P, k)] * un;
+    if (six(P))
+        for (int k = 0; k < P->nf; ++k) F[i_int(P, k)] = q[i_int(P, k)] * un;
     (void)ns;
 }
 
@@ -340,6 +383,8 @@ static void star_state(const oracle_params *P, int d, const double *w, double sK
     qs[i_mom(P, d)] = xi * r * ss;
     qs[i_E(P)] = xi * (q[i_E(P)] + (ss - un) * (r * ss + p / (sK - un)));
     for (int k = 0; k < P->nf - 1; ++k) qs[i_alpha(P, k)] = xi * w[i_alpha(P, k)];
+    if (six(P))   /* internal energies: advected with the mass, as the partial densities */
+        for (int k = 0; k < P->nf; ++k) qs[i_int(P, k)] = xi * q[i_int(P, k)];
     (void)ns;
 }
 
@@ -415,6 +460,7 @@ static int face_state_ok(const oracle_params *P, const double *w) {
     for (int k = 0; k < P->nf; ++k)
         if (!(a[k] >= 0.0 && a[k] <= 1.0)) return 0;
     if (!(density(P, w) > 0.0)) return 0;
+    if (six(P)) return sound_speed_sq(P, w) > 0.0;
     double G, Q;
     mixture(P, w, &G, &Q);
     if (!((G + 1.0) * w[i_E(P)] + Q > 0.0)) return 0;
@@ -484,6 +530,111 @@ void oracle_cbc_normal(const oracle_params *P, int d, int high, const double *qb
     out[i_E(P)] = G * wt[i_E(P)] + p * Gt + Pt + ke * rt + r * kt;
 }
 
+/* ---- six-equation model (Sec. 2.3) ---- */
+/* a_k p of cell c (the coefficient of div(u) in the internal-energy rows). */
+static void six_work(const oracle_params *P, const double *q, long ncell, long c, double *src) {
+    double qc[OR_MAXV], wc[OR_MAXV], a[OR_MAXF];
+    for (int v = 0; v < sys_size(P); ++v) qc[v] = q[(long)v * ncell + c];
+    oracle_cons_to_prim(P, qc, wc);
+    all_alphas(P, wc, a);
+    for (int k = 0; k < P->nf; ++k) src[k] = a[k] * wc[i_E(P)];
+}
+
+/* Volume fraction of phase k after relaxing to pressure p with infinite
+ * stiffness: at fixed mass the phase energy follows de_k = -p dv_k with the
+ * interfacial pressure taken as the final p, which for a stiffened gas,
+ * a_k r_k e_k = a_k (p + g_k pinf_k)/(g_k - 1), integrates to
+ *   a_k (p + g_k pinf_k)/(g_k - 1) - E_k0 = -p (a_k - a_k0),
+ *   a_k(p) = (g_k - 1)(E_k0 + a_k0 p) / (g_k (p + pinf_k)),
+ * E_k0 = a_k r_k e_k before the relaxation. */
+static double relaxed_alpha(const oracle_params *P, int k, double a0, double E0, double p) {
+    double g = P->gamma[k], pi = P->pi_inf[k];
+    return (g - 1.0) * (E0 + a0 * p) / (g * (p + pi));
+}
+
+/* Pressure relaxation of one conserved cell state, in place (Sec. 2.3: the
+ * hyperbolic step is followed by relaxation to pressure equilibrium with
+ * infinite stiffness; Saurel, Petitpas & Berry 2009, Schmidmayer et al. 2020).
+ *  1. the phases that take part are those with a_k0 > 0 and a positive
+ *     p_k0 + pinf_k (E_k0 > a_k0 pinf_k); the others (traces that transport
+ *     has driven to or below zero) keep their volume fraction;
+ *  2. the relaxed pressure p^ solves sum_{taking part} a_k(p^) = 1 - sum_{others}
+ *     a_k0 (relaxed_alpha).  Each a_k(p) of a phase taking part falls strictly
+ *     on p > -min pinf (over those phases), so the left side falls from +inf
+ *     to below the right side; the root is unique and is found by bisection
+ *     to the last bit;
+ *  3. the volume fractions of the phases taking part become a_k(p^);
+ *  4. the pressure is recomputed from the conserved total energy with the
+ *     mixture law of the new fractions, p = (r E - r|u|^2/2 - Pi)/Gamma, and
+ *     every phase's internal energy is reset to that pressure.
+ * Returns p^ (NaN if no phase can take part). */
+double oracle_relax6(const oracle_params *P, double *q) {
+    int nf = P->nf;
+    double a0[OR_MAXF], E0[OR_MAXF];
+    int in[OR_MAXF], nin = 0;
+    all_alphas(P, q, a0);
+    double pimin = 0.0, pmax = 0.0, target = 1.0;
+    for (int k = 0; k < nf; ++k) {
+        E0[k] = q[i_int(P, k)];
+        in[k] = a0[k] > 0.0 && E0[k] > a0[k] * P->pi_inf[k];
+        if (!in[k]) {
+            target -= a0[k];
+            continue;
+        }
+        if (nin == 0 || P->pi_inf[k] < pimin) pimin = P->pi_inf[k];
+        double pk = (P->gamma[k] - 1.0) * E0[k] / a0[k] - P->gamma[k] * P->pi_inf[k];
+        if (pk > pmax) pmax = pk;
+        nin += 1;
+    }
+    if (nin == 0) return NAN;
+    double lo = -pimin, hi = pmax + 1.0;
+    for (int it = 0; it < 2100; ++it) {   /* upper end of the bracket */
+        double s = 0.0;
+        for (int k = 0; k < nf; ++k)
+            if (in[k]) s += relaxed_alpha(P, k, a0[k], E0[k], hi);
+        if (s < target) break;
+        hi = 2.0 * hi + 1.0;
+    }
+    for (int it = 0; it < 2100; ++it) {
+        double mid = 0.5 * (lo + hi);
+        if (!(mid > lo && mid < hi)) break;
+        double s = 0.0;
+        for (int k = 0; k < nf; ++k)
+            if (in[k]) s += relaxed_alpha(P, k, a0[k], E0[k], mid);
+        if (s > target) lo = mid;
+        else hi = mid;
+    }
+    double ph = 0.5 * (lo + hi);
+    for (int k = 0; k < nf - 1; ++k)
+        if (in[k]) q[i_alpha(P, k)] = relaxed_alpha(P, k, a0[k], E0[k], ph);
+    double a[OR_MAXF], G = 0.0, Q = 0.0;
+    all_alphas(P, q, a);
+    for (int k = 0; k < nf; ++k) {
+        G += a[k] / (P->gamma[k] - 1.0);
+        Q += a[k] * P->gamma[k] * P->pi_inf[k] / (P->gamma[k] - 1.0);
+    }
+    double r = density(P, q), ke = 0.0;
+    for (int d = 0; d < P->ndim; ++d) ke += 0.5 * q[i_mom(P, d)] * q[i_mom(P, d)] / r;
+    double p = (q[i_E(P)] - ke - Q) / G;
+    for (int k = 0; k < nf; ++k)
+        q[i_int(P, k)] = a[k] * (p + P->gamma[k] * P->pi_inf[k]) / (P->gamma[k] - 1.0);
+    return ph;
+}
+
+/* oracle_relax6 on every cell; returns the number of cells that could not be relaxed. */
+long oracle_relax6_array(const oracle_params *P, double *q, long ncell) {
+    int ns = sys_size(P);
+    long bad = 0;
+#pragma omp parallel for schedule(static) reduction(+ : bad)
+    for (long c = 0; c < ncell; ++c) {
+        double qc[OR_MAXV];
+        for (int v = 0; v < ns; ++v) qc[v] = q[(long)v * ncell + c];
+        if (isnan(oracle_relax6(P, qc))) { bad += 1; continue; }
+        for (int v = 0; v < ns; ++v) q[(long)v * ncell + c] = qc[v];
+    }
+    return bad;
+}
+
 /* Flux through the face on the low side of cell (i,j,k) in direction d, i.e.
  * between cells idx - e_d and idx.  Returns 1 if the first-order fallback was
  * used at this face. */
@@ -519,9 +670,19 @@ int oracle_face(const oracle_params *P, const double *q, int d, int i, int j, in
             wR[v] = oracle_weno5(st, P->eps);
         }
     }
+    if (six(P))   /* phases at the face pressure: the state is relaxed */
+        for (int k = 0; k < P->nf; ++k) {
+            wL[i_int(P, k)] = wL[i_E(P)];
+            wR[i_int(P, k)] = wR[i_E(P)];
+        }
     int fb = 0;
     if (P->fallback && !(face_state_ok(P, wL) && face_state_ok(P, wR))) {
         for (int v = 0; v < ns; ++v) { wL[v] = w[2][v]; wR[v] = w[3][v]; }
+        if (six(P))
+            for (int k = 0; k < P->nf; ++k) {
+                wL[i_int(P, k)] = wL[i_E(P)];
+                wR[i_int(P, k)] = wR[i_E(P)];
+            }
         fb = 1;
     }
     oracle_hllc(P, d, wL, wR, F, ut);
@@ -591,6 +752,11 @@ long oracle_rhs(const oracle_params *P, const double *q, double *rhs, double *fm
                 long o = (long)i_alpha(P, a) * ncell + c;
                 rhs[o] += (q[o] + K[a]) * divu;
             }
+            if (six(P)) {
+                double src[OR_MAXF];
+                six_work(P, q, ncell, c, src);
+                for (int a = 0; a < P->nf; ++a) rhs[(long)i_int(P, a) * ncell + c] -= src[a] * divu;
+            }
         }
         free(Ff);
     }
@@ -648,6 +814,11 @@ void oracle_rhs_cells(const oracle_params *P, const double *q, long nsel, const 
             }
             for (int a = 0; a < P->nf - 1; ++a)
                 o[i_alpha(P, a)] += (q[(long)i_alpha(P, a) * ncell + c] + K[a]) * divu;
+            if (six(P)) {
+                double src[OR_MAXF];
+                six_work(P, q, ncell, c, src);
+                for (int a = 0; a < P->nf; ++a) o[i_int(P, a)] -= src[a] * divu;
+            }
         }
     }
     if (fmax)

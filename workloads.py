@@ -207,6 +207,20 @@ def shock_bubble(n: int = 256, steps: int = 1000) -> Workload:
         builder=_build_shock_bubble)
 
 
+def six_equation_prims(w: np.ndarray, nf: int, spread: float = 0.0, seed: int = 0) -> np.ndarray:
+    """Primitive state of the six-equation model from a five-equation one:
+    the same rows (the pressure row stands for the mixture pressure) followed
+    by N phase pressures, equal to the mixture pressure times
+    (1 + spread * N(0,1) noise) per phase and cell (spread = 0: pressure
+    equilibrium)."""
+    w = np.asarray(w, dtype=np.float64)
+    ndim = w.shape[0] - 2 * nf
+    p = w[nf + ndim]
+    rng = np.random.default_rng(seed)
+    pk = [p * (1.0 + spread * rng.standard_normal(p.shape)) if spread else p.copy() for _ in range(nf)]
+    return np.concatenate([w, np.stack(pk)], axis=0)
+
+
 def shock_bubble_cbc(n: int = 256, steps: int = 1000) -> Workload:
     """The shock-bubble with characteristic (non-reflecting) boundaries on all
     six faces instead of transmissive ghost cells; same initial state."""
