@@ -63,6 +63,8 @@ FORMS = {
     "fp64_stretched": ("fp64", {}, "stretched"),
     "mixed_stretched": ("mixed", {}, "stretched"),
     "fp64_cbc": ("fp64", {}, "cbc"),
+    "fp64_six": ("fp64", {"model": 2}, "six"),
+    "mixed_six": ("mixed", {"model": 2}, "six"),
 }
 # RK3 stage epilogue in the last sweep: 6 per variable (stages 2, 3), 4 in stage 1
 FLOP_RK_CELL_2F = 7 * (6 + 6 + 4) / 3.0
@@ -428,7 +430,7 @@ def main():
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
     ap.add_argument("--n", type=int, default=256, help="cells per direction of the shock-bubble cube")
     ap.add_argument("--forms", default="fp64,mixed,learned,fp64_weno3,mixed_weno3,fp64_kapila,fp64_stretched,"
-                                       "mixed_stretched,fp64_cbc",
+                                       "mixed_stretched,fp64_cbc,fp64_six,mixed_six",
                     help="comma list of " + ",".join(FORMS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -473,6 +475,7 @@ def main():
     training = None
     head = "fp64" if "fp64" in forms else forms[0]
     stretched = None
+    six_w = None
     for form in forms:
         mlp = None
         if form == "learned":
@@ -480,6 +483,10 @@ def main():
         fwl, fw = wl, w_dev
         if FORMS[form][2] == "cbc":   # same cells and state, non-reflecting faces
             fwl = workloads.shock_bubble_cbc(args.n)
+        if FORMS[form][2] == "six":   # same cells and state, phases in pressure equilibrium
+            if six_w is None:
+                six_w = torch.from_numpy(workloads.six_equation_prims(w_host, wl.nf)).cuda()
+            fw = six_w
         if FORMS[form][2] == "stretched":
             if stretched is None:
                 swl = workloads.shock_bubble_stretched(args.n)
@@ -526,7 +533,9 @@ def main():
         if r is None:
             line["forms"][form] = None
             continue
-        g = grind_ns(r["ms_max"], ws, cells, ns)
+        # equations per cell: the six-equation model adds the N phase energies
+        neq = ns + wl.nf if FORMS[form][2] == "six" else ns
+        g = grind_ns(r["ms_max"], ws, cells, neq)
         entry = {"grind": g, "unit": UNIT, "ms_per_step": r["ms_max"],
                  "cell_updates_per_s": ws * cells / (r["ms_max"] * 1e-3),
                  "speedup_vs_fp64": ms / r["ms_max"], "gpu_launches": r["launches"],
@@ -536,22 +545,27 @@ def main():
         peaks = _measured_peaks()
         hbm = float(peaks.get("hbm_gbs", 6800.0))
         entry["workload"] = r["workload"]
-        if form in ("fp64_weno3", "fp64_kapila", "fp64_stretched", "fp64_cbc"):
+        entry["equations"] = neq
+        if form in ("fp64_weno3", "fp64_kapila", "fp64_stretched", "fp64_cbc", "fp64_six"):
             fl = {"fp64_weno3": FLOP_SWEEP_CELL_3D_2F_W3, "fp64_kapila": FLOP_SWEEP_CELL_3D_2F_KAPILA,
-                  "fp64_stretched": FLOP_SWEEP_CELL_3D_2F, "fp64_cbc": FLOP_SWEEP_CELL_3D_2F}[form]
+                  "fp64_stretched": FLOP_SWEEP_CELL_3D_2F, "fp64_cbc": FLOP_SWEEP_CELL_3D_2F,
+                  "fp64_six": FLOP_SWEEP_CELL_3D_2F}[form]
             tf = (fl + FLOP_RK_CELL_2F / 3.0) * cells * r["sweep_launches"] / sweep_s / 1e12
             entry["roofline"] = {"kernel": "sweep (x, y, z), " + {"fp64_weno3": "WENO3", "fp64_kapila": "Kapila",
                                                                   "fp64_stretched": "non-uniform grid",
-                                                                  "fp64_cbc": "characteristic boundaries"}[form],
+                                                                  "fp64_cbc": "characteristic boundaries",
+                                                                  "fp64_six": "six-equation model"}[form],
                                  "bound": "alu", "achieved": tf,
                                  "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": tf / FP64_PEAK_TFLOPS,
                                  "flop_per_cell_per_sweep": fl,
                                  "note": "nominal FP64 peak as for the WENO5 form" + (
                                      "; FLOPs counted as on a uniform grid (the per-cell coefficients add work)"
-                                     if form == "fp64_stretched" else "")}
-        elif form in ("mixed", "mixed_weno3", "mixed_stretched"):
+                                     if form == "fp64_stretched" else
+                                     "; FLOPs counted as the five-equation sweep (the phase-energy rows and the "
+                                     "relaxation add work)" if form == "fp64_six" else "")}
+        elif form in ("mixed", "mixed_weno3", "mixed_stretched", "mixed_six"):
             gbs = BYTES_MIXED_SWEEPS_STAGE * cells * stages / sweep_s / 1e9
-            fl = FLOP_SWEEP_CELL_3D_2F if form == "mixed" else FLOP_SWEEP_CELL_3D_2F_W3
+            fl = FLOP_SWEEP_CELL_3D_2F_W3 if form == "mixed_weno3" else FLOP_SWEEP_CELL_3D_2F
             tf = fl * cells * r["sweep_launches"] / sweep_s / 1e12
             entry["roofline"] = {"kernel": "sweep (x, y, z)", "hbm_gbs": gbs, "hbm_peak": hbm,
                                  "hbm_frac": gbs / hbm, "fp32_tflops": tf, "fp32_peak": FP32_PEAK_TFLOPS,

@@ -17,6 +17,11 @@
  *     primitive w: a_1 r_1 .. a_N r_N,   u_x [,   u_y,   u_z],   p, a_1 .. a_{N-1}
  * where a_k are volume fractions (a_N = 1 - sum of the others), r_k phase
  * densities, u the mixture velocity, E the total energy and p the pressure.
+ * The six-equation model ("model" 2) appends N rows, sys_size = 3*N + d:
+ *     conserved q: ..., a_1 r_1 e_1 .. a_N r_N e_N   (phase internal energies)
+ *     primitive w: ..., p_1 .. p_N                   (phase pressures)
+ * with a_k r_k e_k = a_k (p_k + g_k pinf_k)/(g_k - 1); there the primitive p
+ * is the pressure of the mixture law for the total energy.
  *
  * Pointers: "on_device" = 1 means a device pointer on the context's GPU
  * (e.g. a contiguous float64 torch tensor's data_ptr), used in stream order;
@@ -96,6 +101,22 @@ mfc_status mfc_init(mfc_ctx** out, int nx, int ny, int nz, const double lo[3], c
  *                (Sec. 2.1), the volume-fraction rows gain K_k div(u) with
  *                K_k = alpha_k (rho c_W^2/(rho_k c_k^2) - 1), c_W Wood's mixture
  *                sound speed (two fluids: the formula of Sec. 2.1);
+ *                2: six-equation model with pressure relaxation (Sec. 2.3;
+ *                2 or 3 fluids, FP64 and mixed forms, WENO5, uniform grid,
+ *                no characteristic boundaries): the state gains the phase
+ *                internal energies (layout above), waves travel at the frozen
+ *                sound speed r c^2 = sum_k a_k g_k (p + pinf_k), the phase
+ *                energies are carried with the face velocity and lose
+ *                a_k p div(u), and every Runge-Kutta stage of mfc_step ends
+ *                with the relaxation to one pressure with infinite stiffness
+ *                (each phase's energy follows de_k = -p dv_k at the final
+ *                pressure p; sum_k a_k = 1 fixes p; then p is recomputed from
+ *                the total energy and the phase energies reset to it; phases
+ *                with a_k <= 0 or p_k + pinf_k <= 0 keep their a_k).  mfc_rhs
+ *                returns the hyperbolic part; it takes the phases at the
+ *                mixture pressure (the states it acts on are relaxed).  The
+ *                state layout changes, so set the model before the state
+ *                (MFC_ERR_ARG otherwise);
  *   "rk_order"   order of the SSP Runge-Kutta step of mfc_step (Sec. 3.4):
  *                3 (default), 2 (q1 = q + dt R(q), q' = 1/2 q + 1/2 (q1 + dt R(q1)))
  *                or 1 (forward Euler);
@@ -145,7 +166,9 @@ mfc_status mfc_set_state(mfc_ctx* ctx, const double* q, int on_device);
 
 /* Set the state from primitive variables w (layout above); the conversion
  * rho E = Gamma p + Pi + rho|u|^2/2 (Sec. 2.1, Eq. "soe" with the mixture
- * rules) runs on the GPU. */
+ * rules) runs on the GPU.  Six-equation model: the phase pressures give the
+ * phase energies and r E = sum_k a_k r_k e_k + r|u|^2/2; the row p is not
+ * read. */
 mfc_status mfc_set_state_prim(mfc_ctx* ctx, const double* w, int on_device);
 
 /* Copy the current conserved state out. */

@@ -355,10 +355,13 @@ class Solver:
         prec = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
         self.ctx = mfc_init(self.n, lo, hi, bc, gamma, pi_inf, prec, stream)
         for k, v in params.items():
-            mfc_set_param(self.ctx, k, v)
+            self.set_param(k, v)
 
     def set_param(self, name, value):
         mfc_set_param(self.ctx, name, value)
+        if name == "model":   # the six-equation model adds the phase internal energies
+            self.sys_size = mfc_sys_size(self.ctx)
+            self.shape = (self.sys_size, self.n[2], self.n[1], self.n[0])
 
     def set_state(self, q):
         mfc_set_state(self.ctx, q)

@@ -22,7 +22,7 @@ static_assert(sizeof(float) * MFC_MLP_PARAMS <= kMlpFragOffset, "parameters fit 
 
 cudaError_t mfc_launch_mlp_pack(const float* P, void* frag, cudaStream_t s);
 cudaError_t mfc_launch_prims_out(const double* q, double* w, long long nc, int nf, int ndim, const EosConst& e,
-                                 cudaStream_t s);
+                                 int six, cudaStream_t s);
 
 namespace {
 
@@ -54,6 +54,8 @@ struct mfc_ctx {
     int weno_order = 5;       // reconstruction: WENO5-JS or WENO3-JS
     int rk_order = 3;         // SSP Runge-Kutta order of mfc_step: 1, 2 or 3
     int kapila = 0;           // model: 0 Allaire, 1 Kapila (K div u source)
+    int six = 0;              // model 2: six-equation model with pressure relaxation
+    int nw = 3;               // primitive rows (2N + d); ns = state rows (+N for the six-equation model)
     float* grid[3] = {nullptr, nullptr, nullptr};   // non-uniform directions: WENO5 rows (mfc_grid.cu)
 
     Geometry g{};
@@ -144,6 +146,12 @@ bool has_cbc(const mfc_ctx* c) {
 }
 
 cudaError_t dispatch_sweep(const mfc_ctx* c, const SweepArgs& a, int dir) {
+    if (c->six) {
+        if (is_f32(c)) return c->nf == 2 ? launch_sweep<float, 2, false, 5, false, true>(a, c->ndim, dir, c->stream)
+                                         : launch_sweep<float, 3, false, 5, false, true>(a, c->ndim, dir, c->stream);
+        return c->nf == 2 ? launch_sweep<double, 2, false, 5, false, true>(a, c->ndim, dir, c->stream)
+                          : launch_sweep<double, 3, false, 5, false, true>(a, c->ndim, dir, c->stream);
+    }
     if (nonuniform(c)) {
         if (is_f32(c)) {
             switch (c->nf) {
@@ -194,6 +202,12 @@ cudaError_t dispatch_sweep(const mfc_ctx* c, const SweepArgs& a, int dir) {
 }
 
 cudaError_t dispatch_prims(const mfc_ctx* c, const PrimArgs& a, bool rate) {
+    if (c->six) {
+        if (is_f32(c)) return c->nf == 2 ? launch_prims<float, 2, true>(a, c->ndim, rate, c->stream)
+                                         : launch_prims<float, 3, true>(a, c->ndim, rate, c->stream);
+        return c->nf == 2 ? launch_prims<double, 2, true>(a, c->ndim, rate, c->stream)
+                          : launch_prims<double, 3, true>(a, c->ndim, rate, c->stream);
+    }
     if (is_f32(c)) {
         switch (c->nf) {
             case 1: return launch_prims<float, 1>(a, c->ndim, rate, c->stream);
@@ -209,6 +223,9 @@ cudaError_t dispatch_prims(const mfc_ctx* c, const PrimArgs& a, bool rate) {
 }
 
 cudaError_t dispatch_cons(const mfc_ctx* c, const double* w, double* q) {
+    if (c->six)
+        return c->nf == 2 ? launch_cons6<2>(c->g, c->e, w, q, c->ndim, c->stream)
+                          : launch_cons6<3>(c->g, c->e, w, q, c->ndim, c->stream);
     switch (c->nf) {
         case 1: return launch_cons<1>(c->g, c->e, w, q, c->ndim, c->stream);
         case 2: return launch_cons<2>(c->g, c->e, w, q, c->ndim, c->stream);
@@ -264,6 +281,7 @@ SweepArgs base_sweep(const mfc_ctx* c) {
     for (int k = 0; k < 3; ++k) {
         a.kgam[k] = k < c->nf ? c->gamma[k] : 1.0;
         a.kpinf[k] = k < c->nf ? c->pi_inf[k] : 0.0;
+        a.rc1[k] = k < c->nf ? (c->gamma[k] - 1.0) / c->gamma[k] : 0.0;
     }
     sweep_set_f32_constants(a);
     return a;
@@ -335,6 +353,31 @@ void free_all(mfc_ctx* c) {
     if (c->h_pin) cudaFreeHost(c->h_pin);
 }
 
+// (Re)allocate the state, stage and accumulator buffers for ns rows.
+mfc_status alloc_state(mfc_ctx* c, int ns) {
+    cudaFree(c->q);
+    cudaFree(c->q1);
+    cudaFree(c->R);
+    c->q = c->q1 = nullptr;
+    c->R = nullptr;
+    const size_t bytes = sizeof(double) * (size_t)ns * (size_t)c->ncell;
+    const size_t rbytes = real_size(c) * (size_t)ns * (size_t)c->ncell;
+    cudaError_t e = cudaSuccess;
+    if ((e = cudaMalloc(&c->q, bytes)) != cudaSuccess || (e = cudaMalloc(&c->q1, bytes)) != cudaSuccess ||
+        (e = cudaMalloc(&c->R, rbytes)) != cudaSuccess) {
+        cudaGetLastError();
+        cudaFree(c->q);
+        cudaFree(c->q1);
+        cudaFree(c->R);
+        c->q = c->q1 = nullptr;
+        c->R = nullptr;
+        return fail(c, e == cudaErrorMemoryAllocation ? MFC_ERR_OOM : MFC_ERR_CUDA, "cudaMalloc: %s",
+                    cudaGetErrorString(e));
+    }
+    c->ns = ns;
+    return MFC_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -376,6 +419,7 @@ mfc_status mfc_init(mfc_ctx** out, int nx, int ny, int nz, const double lo[3], c
     c->ndim = ndim;
     c->nf = num_fluids;
     c->ns = 2 * num_fluids + ndim;
+    c->nw = c->ns;
     c->ncell = ncell;
     for (int i = 0; i < 6; ++i) c->bc[i] = bc[i];
     for (int k = 0; k < num_fluids; ++k) {
@@ -404,6 +448,13 @@ mfc_status mfc_init(mfc_ctx** out, int nx, int ny, int nz, const double lo[3], c
     for (int k = 0; k < 2; ++k) {
         c->e.dG[k] = k < N - 1 ? G[k] - G[N - 1] : 0.0;
         c->e.dP[k] = k < N - 1 ? P[k] - P[N - 1] : 0.0;
+    }
+    // six-equation model: frozen r c^2 = sum a_k g_k (p + pinf_k) = A p + B
+    c->e.A_N = gamma[N - 1];
+    c->e.B_N = gamma[N - 1] * pi_inf[N - 1];
+    for (int k = 0; k < 2; ++k) {
+        c->e.dA[k] = k < N - 1 ? gamma[k] - gamma[N - 1] : 0.0;
+        c->e.dB[k] = k < N - 1 ? gamma[k] * pi_inf[k] - gamma[N - 1] * pi_inf[N - 1] : 0.0;
     }
 
     const size_t bytes = sizeof(double) * (size_t)c->ns * (size_t)ncell;
@@ -457,15 +508,30 @@ mfc_status mfc_set_param(mfc_ctx* c, const char* name, double value) {
         if (value == 3.0 && c->precision == MFC_LEARNED)
             return fail(c, MFC_ERR_ARG, "the learned form replaces the WENO5 weights (weno_order 5)");
         if (value == 3.0 && nonuniform(c)) return fail(c, MFC_ERR_ARG, "non-uniform grids need weno_order 5");
+        if (value == 3.0 && c->six) return fail(c, MFC_ERR_ARG, "the six-equation model needs weno_order 5");
         c->weno_order = (int)value;
     } else if (!strcmp(name, "rk_order")) {
         if (value != 1.0 && value != 2.0 && value != 3.0) return fail(c, MFC_ERR_ARG, "rk_order must be 1, 2 or 3");
         c->rk_order = (int)value;
     } else if (!strcmp(name, "model")) {
-        if (value != 0.0 && value != 1.0) return fail(c, MFC_ERR_ARG, "model must be 0 (Allaire) or 1 (Kapila)");
-        if (value == 1.0 && has_cbc(c))
+        if (value != 0.0 && value != 1.0 && value != 2.0)
+            return fail(c, MFC_ERR_ARG, "model must be 0 (Allaire), 1 (Kapila) or 2 (six-equation)");
+        if (value != 0.0 && has_cbc(c))
             return fail(c, MFC_ERR_ARG, "characteristic boundaries are defined for the Allaire model (model 0)");
-        c->kapila = (int)value;
+        const int six = value == 2.0;
+        if (six) {
+            if (c->precision == MFC_LEARNED) return fail(c, MFC_ERR_ARG, "six-equation model: FP64 and mixed forms");
+            if (c->nf < 2) return fail(c, MFC_ERR_ARG, "six-equation model: 2 or 3 fluids");
+            if (c->weno_order != 5 || nonuniform(c))
+                return fail(c, MFC_ERR_ARG, "six-equation model: WENO5 on a uniform grid");
+        }
+        if (six != c->six) {   // the state layout changes: set the model before the state
+            if (c->state_set) return fail(c, MFC_ERR_ARG, "set the model before the state");
+            mfc_status st = alloc_state(c, c->nw + (six ? c->nf : 0));
+            if (st != MFC_OK) return st;
+            c->six = six;
+        }
+        c->kapila = value == 1.0;
     } else if (!strcmp(name, "profile")) {
         if (value != 0.0 && value != 1.0) return fail(c, MFC_ERR_ARG, "profile must be 0 or 1");
         c->profile = value != 0.0;
@@ -482,6 +548,7 @@ mfc_status mfc_set_grid(mfc_ctx* c, int dir, const double* faces, int nfaces) {
     if (!faces || nfaces != c->n[dir] + 1) return fail(c, MFC_ERR_ARG, "need n+1 = %d face coordinates", c->n[dir] + 1);
     if (c->precision == MFC_LEARNED) return fail(c, MFC_ERR_ARG, "non-uniform grids: FP64 and mixed forms only");
     if (c->weno_order != 5) return fail(c, MFC_ERR_ARG, "non-uniform grids need weno_order 5");
+    if (c->six) return fail(c, MFC_ERR_ARG, "non-uniform grids: five-equation models only");
     const bool periodic = c->bc[2 * dir] == MFC_BC_PERIODIC;
     std::vector<float> rows;
     if (!grid_tables(faces, c->n[dir], periodic, rows))
@@ -671,7 +738,8 @@ mfc_status mfc_get_prims(mfc_ctx* c, double* w, int on_device) {
     if (!w) return fail(c, MFC_ERR_ARG, "NULL buffer");
     if (!c->state_set) return fail(c, MFC_ERR_STATE_UNSET, "no state set");
     double* dst = on_device ? w : c->q1;
-    s = launch(c, P_CONVERT, [&] { return mfc_launch_prims_out(c->q, dst, c->ncell, c->nf, c->ndim, c->e, c->stream); });
+    s = launch(c, P_CONVERT,
+               [&] { return mfc_launch_prims_out(c->q, dst, c->ncell, c->nf, c->ndim, c->e, c->six, c->stream); });
     if (s != MFC_OK) return s;
     if (!on_device) {
         const size_t bytes = sizeof(double) * (size_t)c->ns * (size_t)c->ncell;

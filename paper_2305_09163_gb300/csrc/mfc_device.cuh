@@ -42,9 +42,14 @@ struct Geometry {
 // Mixture closure written as Gamma = G_N + sum_{k<N} alpha_k dG_k, with
 // G_k = 1/(gamma_k - 1) and P_k = gamma_k pinf_k/(gamma_k - 1); this is
 // sum_k alpha_k G_k with alpha_N = 1 - sum_{k<N} alpha_k (Sec. 2.1).
+// The six-equation model's frozen sound speed (Sec. 2.3), r c^2 =
+// sum_k alpha_k g_k (p + pinf_k) = A p + B, is written the same way:
+// A = A_N + sum_{k<N} alpha_k dA_k (A_k = g_k), B likewise (B_k = g_k pinf_k).
 struct EosConst {
     double G_N, P_N;
     double dG[2], dP[2];
+    double A_N, B_N;
+    double dA[2], dB[2];
 };
 
 // FP32 copies of the constants the FP32 kernels use, converted once on the
@@ -53,6 +58,8 @@ struct EosConst {
 struct EosConstF {
     float G_N, P_N;
     float dG[2], dP[2];
+    float A_N, B_N;
+    float dA[2], dB[2];
 };
 
 // Arguments of one directional sweep.
@@ -83,7 +90,8 @@ struct SweepArgs {
     int grid_stride[3];     // x: cells per table value (n + 2); see GridCol
     int cbc;                // some boundary is characteristic (the stream kernels handle it)
     int kapila;             // 1: Kapila model, K div(u) in the volume-fraction rows
-    double kgam[3], kpinf[3];   // Kapila: gamma_k and pi_inf_k of every fluid
+    double kgam[3], kpinf[3];   // Kapila, six-equation model: gamma_k and pi_inf_k of every fluid
+    double rc1[3];              // six-equation relaxation: (gamma_k - 1)/gamma_k
     float kgamf[3], kpinff[3];
     EosConstF ef;           // FP32 kernels: e, eps * 3/4 and g.inv_dx in FP32
     float eps34f;
@@ -95,9 +103,13 @@ struct SweepArgs {
 inline void sweep_set_f32_constants(SweepArgs& a) {
     a.ef.G_N = (float)a.e.G_N;
     a.ef.P_N = (float)a.e.P_N;
+    a.ef.A_N = (float)a.e.A_N;
+    a.ef.B_N = (float)a.e.B_N;
     for (int k = 0; k < 2; ++k) {
         a.ef.dG[k] = (float)a.e.dG[k];
         a.ef.dP[k] = (float)a.e.dP[k];
+        a.ef.dA[k] = (float)a.e.dA[k];
+        a.ef.dB[k] = (float)a.e.dB[k];
     }
     a.eps34f = (float)(0.75 * a.eps);
     a.epsf = (float)a.eps;
@@ -142,11 +154,16 @@ struct GridCol {
     }
 };
 
-template <int NF, int NDIM> struct Layout {
+// Variables of a cell.  The reconstructed (primitive) ones, NS of them, are
+// the same for every model; the six-equation model's state appends the N
+// phase internal energies a_k r_k e_k (rows NS .. NQ-1).
+template <int NF, int NDIM, bool SIX = false> struct Layout {
     static constexpr int NS = 2 * NF + NDIM;
+    static constexpr int NQ = NS + (SIX ? NF : 0);
     static constexpr int IM = NF;              // first momentum / velocity
     static constexpr int IE = NF + NDIM;       // energy / pressure
     static constexpr int IA = NF + NDIM + 1;   // first transported volume fraction
+    static constexpr int II = NS;              // six-equation model: first phase internal energy
 };
 
 __host__ __device__ inline long long stride_of(const Geometry& g, int d) {
@@ -417,14 +434,19 @@ __device__ __forceinline__ float grid_inv_dx(const float* grid, int stride, int 
 
 template <typename Real> struct EosR {
     Real G_N, P_N, dG[2], dP[2];
+    Real A_N, B_N, dA[2], dB[2];
     __device__ __forceinline__ explicit EosR(const EosConst& e)
-        : G_N((Real)e.G_N), P_N((Real)e.P_N) {
+        : G_N((Real)e.G_N), P_N((Real)e.P_N), A_N((Real)e.A_N), B_N((Real)e.B_N) {
         dG[0] = (Real)e.dG[0]; dG[1] = (Real)e.dG[1];
         dP[0] = (Real)e.dP[0]; dP[1] = (Real)e.dP[1];
+        dA[0] = (Real)e.dA[0]; dA[1] = (Real)e.dA[1];
+        dB[0] = (Real)e.dB[0]; dB[1] = (Real)e.dB[1];
     }
-    __device__ __forceinline__ explicit EosR(const EosConstF& e) : G_N(e.G_N), P_N(e.P_N) {
+    __device__ __forceinline__ explicit EosR(const EosConstF& e) : G_N(e.G_N), P_N(e.P_N), A_N(e.A_N), B_N(e.B_N) {
         dG[0] = e.dG[0]; dG[1] = e.dG[1];
         dP[0] = e.dP[0]; dP[1] = e.dP[1];
+        dA[0] = e.dA[0]; dA[1] = e.dA[1];
+        dB[0] = e.dB[0]; dB[1] = e.dB[1];
     }
 };
 
@@ -483,7 +505,9 @@ template <typename Real> struct Mix {
     Real r, G, P, n;
 };
 
-template <typename Real, int NF, int NDIM>
+// Six-equation model (SIX): n = Gamma r c^2 with the frozen sound speed,
+// r c^2 = A p + B, so that c^2 = n/(Gamma r) holds for both models.
+template <typename Real, int NF, int NDIM, bool SIX = false>
 __device__ __forceinline__ Mix<Real> mixture(const Real* s, const EosR<Real>& e) {
     using Lay = Layout<NF, NDIM>;
     Mix<Real> m;
@@ -497,13 +521,24 @@ __device__ __forceinline__ Mix<Real> mixture(const Real* s, const EosR<Real>& e)
         m.G = fma(s[Lay::IA + k], e.dG[k], m.G);
         m.P = fma(s[Lay::IA + k], e.dP[k], m.P);
     }
-    m.n = fma(m.G + (Real)1, s[Lay::IE], m.P);
+    if constexpr (SIX) {
+        Real A = e.A_N, B = e.B_N;
+#pragma unroll
+        for (int k = 0; k < NF - 1; ++k) {
+            A = fma(s[Lay::IA + k], e.dA[k], A);
+            B = fma(s[Lay::IA + k], e.dB[k], B);
+        }
+        m.n = m.G * fma(A, s[Lay::IE], B);
+    } else {
+        m.n = fma(m.G + (Real)1, s[Lay::IE], m.P);
+    }
     return m;
 }
 
 // A reconstructed face state is physical when every partial density is
 // non-negative, every volume fraction (including alpha_N) lies in [0,1], the
-// density is positive and (Gamma+1)p + Pi > 0.
+// density is positive and (Gamma+1)p + Pi > 0 (six-equation model: the frozen
+// r c^2 > 0; m.n carries either).
 template <typename Real, int NF, int NDIM>
 __device__ __forceinline__ bool face_state_ok(const Real* s, const Mix<Real>& m) {
     using Lay = Layout<NF, NDIM>;
@@ -525,9 +560,14 @@ __device__ __forceinline__ bool face_state_ok(const Real* s, const Mix<Real>& m)
 // HLLC flux and face velocity (Sec. 3.2.1) between primitive states L | R with
 // normal direction DIR; Davis wave-speed estimates.  The branch order matches
 // the four cases of the paper: 0<=sL; sL<0<=s*; s*<0<sR; sR<=0.
-template <typename Real, int NF, int NDIM, int DIR>
+//
+// Six-equation model (SIX): the phase internal energies are carried with the
+// mass like the volume fractions, their face values being those of the
+// phases at the face pressure, a_k (p + g_k pinf_k)/(g_k - 1) =
+// a_k (G_k p + P_k); their flux is the upwind value times the face velocity.
+template <typename Real, int NF, int NDIM, int DIR, bool SIX = false>
 __device__ __forceinline__ void hllc(const Real* L, const Real* R, const Mix<Real>& mL, const Mix<Real>& mR,
-                                     Real* F, Real& ut) {
+                                     Real* F, Real& ut, const EosR<Real>* e6 = nullptr) {
     using Lay = Layout<NF, NDIM>;
     constexpr int IM = Lay::IM, IE = Lay::IE, IA = Lay::IA;
     const Real uL = L[IM + DIR], uR = R[IM + DIR], pL = L[IE], pR = R[IE];
@@ -570,6 +610,15 @@ __device__ __forceinline__ void hllc(const Real* L, const Real* R, const Mix<Rea
     F[IE] = fma(rE, ut, pK * uK) + sKe * (sS - uK) * fma(xi * rK, sS, pK * rr);
 #pragma unroll
     for (int k = 0; k < NF - 1; ++k) F[IA + k] = K[IA + k] * ut;
+    if constexpr (SIX) {
+        Real aN = 1;
+#pragma unroll
+        for (int k = 0; k < NF - 1; ++k) {
+            aN -= K[IA + k];
+            F[Lay::NS + k] = K[IA + k] * fma(e6->G_N + e6->dG[k], pK, e6->P_N + e6->dP[k]) * ut;
+        }
+        F[Lay::NS + NF - 1] = aN * fma(e6->G_N, pK, e6->P_N) * ut;
+    }
 }
 
 // Count one fallback face per calling lane with one atomic per converged
@@ -582,12 +631,12 @@ __device__ __forceinline__ void count_fallback(unsigned long long* counter) {
 
 // Face flux between reconstructed states (with the optional first-order
 // fallback to the two cell values cl | cr).
-template <typename Real, int NF, int NDIM, int DIR>
+template <typename Real, int NF, int NDIM, int DIR, bool SIX = false>
 __device__ __forceinline__ void face_flux(const SweepArgs& a, const EosR<Real>& e, const Real* eLs, const Real* eRs,
                                           const Real* cl, const Real* cr, Real* F, Real& ut) {
     constexpr int NS = Layout<NF, NDIM>::NS;
-    Mix<Real> mL = mixture<Real, NF, NDIM>(eLs, e);
-    Mix<Real> mR = mixture<Real, NF, NDIM>(eRs, e);
+    Mix<Real> mL = mixture<Real, NF, NDIM, SIX>(eLs, e);
+    Mix<Real> mR = mixture<Real, NF, NDIM, SIX>(eRs, e);
     bool first = false;
     if (a.fallback) {
         first = !(face_state_ok<Real, NF, NDIM>(eLs, mL) && face_state_ok<Real, NF, NDIM>(eRs, mR));
@@ -599,16 +648,16 @@ __device__ __forceinline__ void face_flux(const SweepArgs& a, const EosR<Real>& 
             Real fl[NS], fr[NS];
 #pragma unroll
             for (int v = 0; v < NS; ++v) { fl[v] = cl[v]; fr[v] = cr[v]; }
-            mL = mixture<Real, NF, NDIM>(fl, e);
-            mR = mixture<Real, NF, NDIM>(fr, e);
-            hllc<Real, NF, NDIM, DIR>(fl, fr, mL, mR, F, ut);
+            mL = mixture<Real, NF, NDIM, SIX>(fl, e);
+            mR = mixture<Real, NF, NDIM, SIX>(fr, e);
+            hllc<Real, NF, NDIM, DIR, SIX>(fl, fr, mL, mR, F, ut, &e);
         } else {
-            hllc<Real, NF, NDIM, DIR>(eLs, eRs, mL, mR, F, ut);
+            hllc<Real, NF, NDIM, DIR, SIX>(eLs, eRs, mL, mR, F, ut, &e);
         }
         return;
     }
     if (!__any_sync(__activemask(), first)) {
-        hllc<Real, NF, NDIM, DIR>(eLs, eRs, mL, mR, F, ut);
+        hllc<Real, NF, NDIM, DIR, SIX>(eLs, eRs, mL, mR, F, ut, &e);
         return;
     }
     // FP64: some lane of the warp falls back; select the states first so
@@ -621,10 +670,10 @@ __device__ __forceinline__ void face_flux(const SweepArgs& a, const EosR<Real>& 
     }
     if (first) {
         count_fallback(a.fallback_count);
-        mL = mixture<Real, NF, NDIM>(sl, e);
-        mR = mixture<Real, NF, NDIM>(sr, e);
+        mL = mixture<Real, NF, NDIM, SIX>(sl, e);
+        mR = mixture<Real, NF, NDIM, SIX>(sr, e);
     }
-    hllc<Real, NF, NDIM, DIR>(sl, sr, mL, mR, F, ut);
+    hllc<Real, NF, NDIM, DIR, SIX>(sl, sr, mL, mR, F, ut, &e);
 }
 
 // ---------------------------------------------------------------------------
@@ -952,6 +1001,160 @@ __device__ __forceinline__ void kapila_K_df(const SweepArgs& a, const double* w,
     for (int k = 0; k < NF - 1; ++k) K[k] = df_to_double(df_mul(al[k], df_add(df_div(pe[k], D), {-1.f, 0.f})));
 }
 
+// Six-equation model (Sec. 2.3): pressure relaxation of one cell's conserved
+// state q[NQ] with infinite stiffness, in place, after a Runge-Kutta stage
+// (Saurel, Petitpas & Berry 2009; Schmidmayer et al. 2020).  At fixed mass
+// each phase's energy follows de_k = -p dv_k at the final pressure p, which for
+// a stiffened gas gives the relaxed volume fraction
+//     a_k(p) = (g_k - 1)(E_k0 + a_k0 p) / (g_k (p + pinf_k)),  E_k0 = a_k r_k e_k.
+// The phases taking part are those with a_k0 > 0 and p_k0 + pinf_k > 0
+// (E_k0 > a_k0 pinf_k); the others keep a_k0.  The relaxed pressure solves
+// f(p) = sum_{taking part} a_k(p) - (1 - sum_{others} a_k0) = 0; on
+// p > lo = -min pinf (over the phases taking part) f is convex and falls
+// strictly from +inf to below zero, so the root is unique.
+//  1. FP32 Newton from the pressure the mixture law gives for the total energy
+//     with the old fractions (the root itself for a relaxed state): from the
+//     left of the root Newton rises monotonically to it, from the right it
+//     lands left of it unless it would leave the domain, when the step bisects
+//     [lo, p] instead; at most 60 iterations, ending at a relative step of 2^-20;
+//  2. two Newton steps with f in float-float arithmetic (f' in FP32 suffices:
+//     its error only slows the quadratic convergence to a linear one with
+//     factor ~1e-7), which bring p to ~1e-14 relative;
+//  3. one FP64 Newton step, p1 = p0 - f(p0)/f'(p0), and the new fractions
+//     a_k(p1) = a_k(p0) + a_k'(p0)(p1 - p0) (the second-order remainder is
+//     below FP64 rounding): a fraction near 1 must be right to ~1e-16
+//     absolute, since a trace phase's fraction is 1 minus it;
+//  4. in FP64 the pressure of the total energy with the mixture law of the
+//     new fractions and every phase's energy reset to it.
+// On GB300 an FP64 instruction costs the issue time of ~60 FP32 ones; the
+// iteration is the costly part, hence steps 1-2 (see mfc_df.cuh).
+template <int NF, int NDIM>
+__device__ __noinline__ void relax6(const SweepArgs& a, double* q) {
+    using Lay = Layout<NF, NDIM, true>;
+    constexpr int IM = Lay::IM, IE = Lay::IE, IA = Lay::IA, II = Lay::II;
+    double a0[NF], E0[NF];
+    bool in[NF];
+    double asum = 0.0;
+#pragma unroll
+    for (int k = 0; k < NF - 1; ++k) {
+        a0[k] = q[IA + k];
+        asum += a0[k];
+    }
+    a0[NF - 1] = 1.0 - asum;
+    double target = 1.0;
+    float lo = 0.f;
+    bool any = false;
+#pragma unroll
+    for (int k = 0; k < NF; ++k) {
+        E0[k] = q[II + k];
+        in[k] = a0[k] > 0.0 && E0[k] > a0[k] * a.kpinf[k];
+        if (!in[k]) {
+            target -= a0[k];
+            continue;
+        }
+        lo = any ? fmaxf(lo, -a.kpinff[k]) : -a.kpinff[k];
+        any = true;
+    }
+    if (!any) return;   // no phase can relax: left as is (the CFL check flags it)
+    // mixture-law pressure of the total energy (old fractions, then new ones)
+    double r = q[0], m2 = 0.0;
+#pragma unroll
+    for (int k = 1; k < NF; ++k) r += q[k];
+#pragma unroll
+    for (int d = 0; d < NDIM; ++d) m2 = fma(q[IM + d], q[IM + d], m2);
+    const double eint = q[IE] - 0.5 * m2 / r;
+    auto mixture_p = [&]() {
+        double G = a.e.G_N, P = a.e.P_N;
+#pragma unroll
+        for (int k = 0; k < NF - 1; ++k) {
+            G = fma(q[IA + k], a.e.dG[k], G);
+            P = fma(q[IA + k], a.e.dP[k], P);
+        }
+        return (eint - P) / G;
+    };
+    // the phases in float-float (integer splits) and FP32
+    df a0d[NF], E0d[NF], pid[NF], c1d[NF];
+    float a0f[NF], E0f[NF], pif[NF], c1f[NF];
+#pragma unroll
+    for (int k = 0; k < NF; ++k) {
+        a0d[k] = df_from_double(a0[k]);
+        E0d[k] = df_from_double(E0[k]);
+        pid[k] = df_from_double(a.kpinf[k]);
+        c1d[k] = df_from_double(a.rc1[k]);
+        a0f[k] = a0d[k].hi;
+        E0f[k] = E0d[k].hi;
+        pif[k] = a.kpinff[k];
+        c1f[k] = c1d[k].hi;
+    }
+    const df targetd = df_from_double(target);
+    // 1. FP32 Newton
+    float p = (float)mixture_p();
+    if (!(p > lo)) p = lo + fmaxf(fabsf(lo), 1.f);
+    float hi = INFINITY;
+    for (int it = 0; it < 60; ++it) {
+        float f = -targetd.hi, fp = 0.f;
+#pragma unroll
+        for (int k = 0; k < NF; ++k) {
+            if (!in[k]) continue;
+            const float t = 1.f / (p + pif[k]);
+            f = fmaf(c1f[k] * fmaf(a0f[k], p, E0f[k]), t, f);
+            fp = fmaf(c1f[k] * fmaf(a0f[k], pif[k], -E0f[k]), t * t, fp);
+        }
+        if (f > 0.f) lo = p;
+        else hi = p;
+        float pn = p - f / fp;
+        if (!(pn > lo && pn < hi)) pn = 0.5f * (lo + (hi < INFINITY ? hi : p));
+        const bool done = fabsf(pn - p) <= 0x1p-20f * fabsf(pn) || !(pn > lo && pn < hi);
+        p = pn;
+        if (done) break;
+    }
+    // 2. float-float Newton steps
+    df pd = {p, 0.f};
+#pragma unroll
+    for (int s = 0; s < 2; ++s) {
+        df f = df_neg(targetd);
+        float fp = 0.f;
+#pragma unroll
+        for (int k = 0; k < NF; ++k) {
+            if (!in[k]) continue;
+            const df num = df_add(E0d[k], df_mul(a0d[k], pd));
+            const df den = df_add(pd, pid[k]);
+            f = df_add(f, df_mul(c1d[k], df_div(num, den)));
+            const float t = 1.f / den.hi;
+            fp = fmaf(c1f[k] * fmaf(a0f[k], pif[k], -E0f[k]), t * t, fp);
+        }
+        pd = df_add(pd, {-(f.hi + f.lo) / fp, 0.f});
+    }
+    // 3. one FP64 Newton step and the fractions at its end (first order)
+    const double p0 = df_to_double(pd);
+    double ak[NF], dak[NF], f64 = -target, fp64 = 0.0;
+#pragma unroll
+    for (int k = 0; k < NF; ++k) {
+        ak[k] = a0[k];
+        dak[k] = 0.0;
+        if (!in[k]) continue;
+        const double pi = a.kpinf[k];
+        const double t = 1.0 / (p0 + pi);
+        ak[k] = a.rc1[k] * fma(a0[k], p0, E0[k]) * t;
+        dak[k] = a.rc1[k] * fma(a0[k], pi, -E0[k]) * t * t;
+        f64 += ak[k];
+        fp64 += dak[k];
+    }
+    const double dp = df_widen(-(float)f64 / (float)fp64);
+    // 4. new fractions, the pressure of the total energy, the phase energies
+    double an = 1.0;
+#pragma unroll
+    for (int k = 0; k < NF - 1; ++k) {
+        if (in[k]) q[IA + k] = fma(dak[k], dp, ak[k]);
+        an -= q[IA + k];
+    }
+    const double pe = mixture_p();
+#pragma unroll
+    for (int k = 0; k < NF - 1; ++k)
+        q[II + k] = q[IA + k] * fma(a.e.G_N + a.e.dG[k], pe, a.e.P_N + a.e.dP[k]);
+    q[II + NF - 1] = an * fma(a.e.G_N, pe, a.e.P_N);
+}
+
 // Normal rate of a characteristic boundary cell (flat index idx, neighbours
 // sd apart along DIR; n cells along DIR) from its primitives and those of its
 // interior neighbour.
@@ -976,15 +1179,29 @@ __device__ __noinline__ void cbc_cell_rate(const SweepArgs& a, long long idx, lo
 // Finish cell idx (coordinate b along DIR, neighbours sd apart): flux
 // difference and alpha div(u) source, or, at a characteristic boundary, the
 // boundary rate; then store, accumulate or apply the RK stage.
-template <typename Real, int NF, int NDIM, int DIR>
+//
+// Six-equation model (SIX): NQ rows; the phase energies lose a_k p div(u)
+// (cell values), and an RK stage update ends with the pressure relaxation
+// (relax6) before it is stored.
+template <typename Real, int NF, int NDIM, int DIR, bool SIX = false>
 __device__ __forceinline__ void finish_cell(const SweepArgs& a, long long idx, const Real* Fm, const Real* Fp,
                                             Real um, Real up, const Real* cell, Real inv_dx, int b, long long sd) {
-    using Lay = Layout<NF, NDIM>;
-    constexpr int NS = Lay::NS, IA = Lay::IA;
-    Real out[NS];
+    using Lay = Layout<NF, NDIM, SIX>;
+    constexpr int NS = Lay::NS, NQ = Lay::NQ, IA = Lay::IA;
+    Real out[NQ];
 #pragma unroll
-    for (int v = 0; v < NS; ++v) out[v] = (Fm[v] - Fp[v]) * inv_dx;
+    for (int v = 0; v < NQ; ++v) out[v] = (Fm[v] - Fp[v]) * inv_dx;
     const Real du = (up - um) * inv_dx;
+    if constexpr (SIX) {
+        const Real pdu = cell[Lay::IE] * du;
+        Real aN = 1;
+#pragma unroll
+        for (int k = 0; k < NF - 1; ++k) {
+            aN -= cell[IA + k];
+            out[Lay::II + k] -= cell[IA + k] * pdu;
+        }
+        out[Lay::II + NF - 1] -= aN * pdu;
+    }
     if constexpr (NF > 1) {
         if (a.kapila) {
             Real K[NF - 1];
@@ -1012,13 +1229,14 @@ __device__ __forceinline__ void finish_cell(const SweepArgs& a, long long idx, c
     Real* R = static_cast<Real*>(a.R);
     if (a.mode == 0) {
 #pragma unroll
-        for (int v = 0; v < NS; ++v) R[v * nc + idx] = out[v];
+        for (int v = 0; v < NQ; ++v) R[v * nc + idx] = out[v];
     } else if (a.mode == 1) {
 #pragma unroll
-        for (int v = 0; v < NS; ++v) R[v * nc + idx] += out[v];
+        for (int v = 0; v < NQ; ++v) R[v * nc + idx] += out[v];
     } else if (a.mode == 2) {
+        double qn[SIX ? NQ : 1];
 #pragma unroll
-        for (int v = 0; v < NS; ++v) {
+        for (int v = 0; v < NQ; ++v) {
             const Real rv = a.acc_in ? R[v * nc + idx] + out[v] : out[v];
             // FP32 accumulator widened by integer operations (a conversion
             // instruction would take an FP64-pipe slot)
@@ -1028,11 +1246,17 @@ __device__ __forceinline__ void finish_cell(const SweepArgs& a, long long idx, c
             const double s = fma(a.dt, rd, a.qs[v * nc + idx]);
             double o = a.c1 * s;
             if (a.c0 != 0.0) o = fma(a.c0, a.q0[v * nc + idx], o);
-            a.qout[v * nc + idx] = o;
+            if constexpr (SIX) qn[v] = o;
+            else a.qout[v * nc + idx] = o;
+        }
+        if constexpr (SIX) {
+            relax6<NF, NDIM>(a, qn);
+#pragma unroll
+            for (int v = 0; v < NQ; ++v) a.qout[v * nc + idx] = qn[v];
         }
     } else {
 #pragma unroll
-        for (int v = 0; v < NS; ++v) {
+        for (int v = 0; v < NQ; ++v) {
             const Real rv = a.acc_in ? R[v * nc + idx] + out[v] : out[v];
             a.out[v * nc + idx] = (double)rv;
         }
@@ -1186,17 +1410,19 @@ __global__ void __launch_bounds__(128) sweep_kernel(const SweepArgs a) {
 // ---------------------------------------------------------------------------
 constexpr int kStreamThreads = 128;
 
-template <typename Real, int NF, int NDIM, bool LEARNED = false, int ORDER = 5, bool NONUNIF = false>
+template <typename Real, int NF, int NDIM, bool LEARNED = false, int ORDER = 5, bool NONUNIF = false, bool SIX = false>
 __global__ void __launch_bounds__(kStreamThreads) sweep_x_stream_kernel(const SweepArgs a) {
+    static_assert(!SIX || (!LEARNED && ORDER == 5 && !NONUNIF), "six-equation model: WENO5 on uniform grids");
     static_assert(!NONUNIF || (!LEARNED && ORDER == 5), "non-uniform grids: WENO5, FP64 and mixed forms");
     static_assert(!LEARNED || sizeof(Real) == 4, "the learned form runs in FP32");
     static_assert(!LEARNED || ORDER == 5, "the learned form replaces the WENO5 weights");
     using Lay = Layout<NF, NDIM>;
     constexpr int NS = Lay::NS, IM = Lay::IM;
+    constexpr int NQ = Layout<NF, NDIM, SIX>::NQ;   // flux rows
     constexpr int NJ = LEARNED ? NS : 1;
     __shared__ Real sh_eL[NS][kStreamThreads + 1];
     __shared__ Real sh_eLJ[NJ][kStreamThreads + 1];
-    __shared__ Real sh_F[NS + 1][kStreamThreads + 1];
+    __shared__ Real sh_F[NQ + 1][kStreamThreads + 1];
     const Real* __restrict__ w = static_cast<const Real*>(a.w);
     const int n = a.g.n[0];
     const long long rowlen = (long long)n + 2;
@@ -1329,7 +1555,7 @@ __global__ void __launch_bounds__(kStreamThreads) sweep_x_stream_kernel(const Sw
             }
         }
         __syncthreads();
-        Real F[NS], ut = 0;
+        Real F[NQ], ut = 0;
         const bool has_face = live && c >= 0 && s >= own0 - 1;
         if (has_face) {
             Real lft[NS];
@@ -1341,18 +1567,18 @@ __global__ void __launch_bounds__(kStreamThreads) sweep_x_stream_kernel(const Sw
                 for (int q = 0; q < NS; ++q) lftJ[q] = sh_eLJ[q][t];
                 face_flux_learned<NF, NDIM, 0>(a, e, lft, eR, lftJ, eRJ, cm1, cell, F, ut);
             } else {
-                face_flux<Real, NF, NDIM, 0>(a, e, lft, eR, cm1, cell, F, ut);
+                face_flux<Real, NF, NDIM, 0, SIX>(a, e, lft, eR, cm1, cell, F, ut);
             }
 #pragma unroll
-            for (int q = 0; q < NS; ++q) sh_F[q][t + 1] = F[q];
-            sh_F[NS][t + 1] = ut;
+            for (int q = 0; q < NQ; ++q) sh_F[q][t + 1] = F[q];
+            sh_F[NQ][t + 1] = ut;
         }
         __syncthreads();
         if (has_face && s >= own0 && c >= 1) {
-            Real Fm[NS];
+            Real Fm[NQ];
 #pragma unroll
-            for (int q = 0; q < NS; ++q) Fm[q] = sh_F[q][t];
-            finish_cell<Real, NF, NDIM, 0>(a, rowoff + (c - 1), Fm, F, sh_F[NS][t], ut, cm1,
+            for (int q = 0; q < NQ; ++q) Fm[q] = sh_F[q][t];
+            finish_cell<Real, NF, NDIM, 0, SIX>(a, rowoff + (c - 1), Fm, F, sh_F[NQ][t], ut, cm1,
                                            NONUNIF ? grid_inv_dx<true>(a.grid[0], a.grid_stride[0], c - 1, Real(0)) : inv_dx,
                                            c - 1, 1);
         }
@@ -1363,9 +1589,9 @@ __global__ void __launch_bounds__(kStreamThreads) sweep_x_stream_kernel(const Sw
             for (int q = 0; q < NS; ++q) {
                 sh_eL[q][0] = sh_eL[q][kStreamThreads];
                 if constexpr (LEARNED) sh_eLJ[q][0] = sh_eLJ[q][kStreamThreads];
-                sh_F[q][0] = sh_F[q][kStreamThreads];
             }
-            sh_F[NS][0] = sh_F[NS][kStreamThreads];
+#pragma unroll
+            for (int q = 0; q <= NQ; ++q) sh_F[q][0] = sh_F[q][kStreamThreads];
         }
         __syncthreads();
     }
@@ -1388,14 +1614,16 @@ __global__ void __launch_bounds__(kStreamThreads) sweep_x_stream_kernel(const Sw
 // ---------------------------------------------------------------------------
 constexpr int kRowsPerChunk = 4;
 
-template <typename Real, int NF, int NDIM, int DIR, bool LEARNED, int ORDER, bool NONUNIF = false>
+template <typename Real, int NF, int NDIM, int DIR, bool LEARNED, int ORDER, bool NONUNIF = false, bool SIX = false>
 __device__ __forceinline__ void sweep_yz_stream_body(const SweepArgs& a) {
+    static_assert(!SIX || (!LEARNED && ORDER == 5 && !NONUNIF), "six-equation model: WENO5 on uniform grids");
     static_assert(!NONUNIF || (!LEARNED && ORDER == 5), "non-uniform grids: WENO5, FP64 and mixed forms");
     static_assert(!LEARNED || ORDER == 5, "the learned form replaces the WENO5 weights");
     static_assert(DIR == 1 || DIR == 2, "y or z");
     static_assert(!LEARNED || sizeof(Real) == 4, "the learned form runs in FP32");
     using Lay = Layout<NF, NDIM>;
     constexpr int NS = Lay::NS, IM = Lay::IM;
+    constexpr int NQ = Layout<NF, NDIM, SIX>::NQ;   // flux rows
     constexpr int NJ = LEARNED ? NS : 1;
     constexpr int T1 = 0;
     constexpr int T2 = (DIR == 2) ? 1 : 2;
@@ -1403,7 +1631,7 @@ __device__ __forceinline__ void sweep_yz_stream_body(const SweepArgs& a) {
     __shared__ Real ring[RING][NS][32];
     __shared__ Real sh_eL[NS][kRowsPerChunk + 1][32];
     __shared__ Real sh_eLJ[NJ][kRowsPerChunk + 1][32];
-    __shared__ Real sh_F[NS + 1][kRowsPerChunk + 1][32];
+    __shared__ Real sh_F[NQ + 1][kRowsPerChunk + 1][32];
     const Real* __restrict__ w = static_cast<const Real*>(a.w);
     const int lane = threadIdx.x & 31, row = threadIdx.x >> 5;
     const int n1 = a.g.n[T1], n2 = a.g.n[T2], nd = a.g.n[DIR];
@@ -1516,7 +1744,7 @@ __device__ __forceinline__ void sweep_yz_stream_body(const SweepArgs& a) {
 #pragma unroll
             for (int q = 0; q < NS; ++q) ring[slot(inext)][q][lane] = nxt[q];
         }
-        Real F[NS], ut = 0;
+        Real F[NQ], ut = 0;
         const bool has_face = live && c >= s0;
         if (has_face) {
             Real lft[NS];
@@ -1528,18 +1756,18 @@ __device__ __forceinline__ void sweep_yz_stream_body(const SweepArgs& a) {
                 for (int q = 0; q < NS; ++q) lftJ[q] = sh_eLJ[q][row][lane];
                 face_flux_learned<NF, NDIM, DIR>(a, e, lft, eR, lftJ, eRJ, cm1, cell, F, ut);
             } else {
-                face_flux<Real, NF, NDIM, DIR>(a, e, lft, eR, cm1, cell, F, ut);
+                face_flux<Real, NF, NDIM, DIR, SIX>(a, e, lft, eR, cm1, cell, F, ut);
             }
 #pragma unroll
-            for (int q = 0; q < NS; ++q) sh_F[q][row + 1][lane] = F[q];
-            sh_F[NS][row + 1][lane] = ut;
+            for (int q = 0; q < NQ; ++q) sh_F[q][row + 1][lane] = F[q];
+            sh_F[NQ][row + 1][lane] = ut;
         }
         __syncthreads();
         if (has_face && c >= s0 + 1 && active) {
-            Real Fm[NS];
+            Real Fm[NQ];
 #pragma unroll
-            for (int q = 0; q < NS; ++q) Fm[q] = sh_F[q][row][lane];
-            finish_cell<Real, NF, NDIM, DIR>(a, basei + (long long)(c - 1) * sd, Fm, F, sh_F[NS][row][lane], ut, cm1,
+            for (int q = 0; q < NQ; ++q) Fm[q] = sh_F[q][row][lane];
+            finish_cell<Real, NF, NDIM, DIR, SIX>(a, basei + (long long)(c - 1) * sd, Fm, F, sh_F[NQ][row][lane], ut, cm1,
                                              NONUNIF ? grid_inv_dx<false>(a.grid[DIR], a.grid_stride[DIR], c - 1, Real(0))
                                                      : inv_dx,
                                              c - 1, sd);
@@ -1551,9 +1779,9 @@ __device__ __forceinline__ void sweep_yz_stream_body(const SweepArgs& a) {
             for (int q = 0; q < NS; ++q) {
                 sh_eL[q][0][lane] = sh_eL[q][kRowsPerChunk][lane];
                 if constexpr (LEARNED) sh_eLJ[q][0][lane] = sh_eLJ[q][kRowsPerChunk][lane];
-                sh_F[q][0][lane] = sh_F[q][kRowsPerChunk][lane];
             }
-            sh_F[NS][0][lane] = sh_F[NS][kRowsPerChunk][lane];
+#pragma unroll
+            for (int q = 0; q <= NQ; ++q) sh_F[q][0][lane] = sh_F[q][kRowsPerChunk][lane];
         }
         __syncthreads();
     }
@@ -1566,9 +1794,9 @@ __device__ __forceinline__ void sweep_yz_stream_body(const SweepArgs& a) {
 // entry with a register bound (4 CTAs per SM for two fluids) so that enough
 // warps stay resident; the mixed form keeps the compiler's own allocation,
 // which schedules its loads better.
-template <typename Real, int NF, int NDIM, int DIR, int ORDER = 5, bool NONUNIF = false>
+template <typename Real, int NF, int NDIM, int DIR, int ORDER = 5, bool NONUNIF = false, bool SIX = false>
 __global__ void __launch_bounds__(32 * kRowsPerChunk) sweep_yz_stream_kernel(const SweepArgs a) {
-    sweep_yz_stream_body<Real, NF, NDIM, DIR, false, ORDER, NONUNIF>(a);
+    sweep_yz_stream_body<Real, NF, NDIM, DIR, false, ORDER, NONUNIF, SIX>(a);
 }
 
 template <int NF, int NDIM, int DIR>
@@ -1583,9 +1811,10 @@ __global__ void __launch_bounds__(32 * kRowsPerChunk, NF <= 2 ? 4 : 3) sweep_yz_
 // energy subtraction stay FP64, the rest is FP32.  Optionally the CFL rate
 // max_d (|u_d| + c)/dx_d with c^2 = ((Gamma+1)p + Pi)/(Gamma rho), reduced to one
 // max per launch with an order-preserving integer atomic (non-negative
-// doubles), so it is exact and independent of scheduling.
+// doubles), so it is exact and independent of scheduling.  Six-equation model
+// (SIX): the frozen sound speed, r c^2 = A p + B (Sec. 2.3).
 // ---------------------------------------------------------------------------
-template <int NF, int NDIM>
+template <int NF, int NDIM, bool SIX = false>
 __device__ __forceinline__ void prims_cell(const double* q, const EosConst& e, double* wv, double& c2) {
     using Lay = Layout<NF, NDIM>;
     constexpr int IM = Lay::IM, IE = Lay::IE, IA = Lay::IA;
@@ -1609,10 +1838,20 @@ __device__ __forceinline__ void prims_cell(const double* q, const EosConst& e, d
     wv[IE] = p;
 #pragma unroll
     for (int k = 0; k < NF - 1; ++k) wv[IA + k] = q[IA + k];
-    c2 = fma(G + 1.0, p, P) * iG * irho;
+    if constexpr (SIX) {
+        double A = e.A_N, B = e.B_N;
+#pragma unroll
+        for (int k = 0; k < NF - 1; ++k) {
+            A = fma(q[IA + k], e.dA[k], A);
+            B = fma(q[IA + k], e.dB[k], B);
+        }
+        c2 = fma(A, p, B) * irho;
+    } else {
+        c2 = fma(G + 1.0, p, P) * iG * irho;
+    }
 }
 
-template <int NF, int NDIM>
+template <int NF, int NDIM, bool SIX = false>
 __device__ __forceinline__ void prims_cell(const double* q, const EosConst& e, float* wv, float& c2) {
     using Lay = Layout<NF, NDIM>;
     constexpr int IM = Lay::IM, IE = Lay::IE, IA = Lay::IA;
@@ -1641,10 +1880,20 @@ __device__ __forceinline__ void prims_cell(const double* q, const EosConst& e, f
     wv[IE] = p;
 #pragma unroll
     for (int k = 0; k < NF - 1; ++k) wv[IA + k] = (float)q[IA + k];
-    c2 = __fdividef(fmaf(G + 1.0f, p, (float)P), G * rho);
+    if constexpr (SIX) {
+        float A = (float)e.A_N, B = (float)e.B_N;
+#pragma unroll
+        for (int k = 0; k < NF - 1; ++k) {
+            A = fmaf((float)q[IA + k], (float)e.dA[k], A);
+            B = fmaf((float)q[IA + k], (float)e.dB[k], B);
+        }
+        c2 = __fdividef(fmaf(A, p, B), rho);
+    } else {
+        c2 = __fdividef(fmaf(G + 1.0f, p, (float)P), G * rho);
+    }
 }
 
-template <typename Real, int NF, int NDIM, bool RATE>
+template <typename Real, int NF, int NDIM, bool RATE, bool SIX = false>
 __global__ void __launch_bounds__(256) prims_kernel(const PrimArgs a) {
     using Lay = Layout<NF, NDIM>;
     constexpr int NS = Lay::NS, IM = Lay::IM;
@@ -1658,7 +1907,7 @@ __global__ void __launch_bounds__(256) prims_kernel(const PrimArgs a) {
 #pragma unroll
         for (int v = 0; v < NS; ++v) q[v] = __ldg(a.q + v * nc + i);
         Real wv[NS], c2;
-        prims_cell<NF, NDIM>(q, a.e, wv, c2);
+        prims_cell<NF, NDIM, SIX>(q, a.e, wv, c2);
 #pragma unroll
         for (int v = 0; v < NS; ++v) w[v * nc + i] = wv[v];
         if (RATE) {
@@ -1743,6 +1992,44 @@ __global__ void __launch_bounds__(256) cons_kernel(Geometry g, EosConst e, const
         q[IE * nc + i] = fma(G, s[IE], P) + 0.5 * rho * ke;
 #pragma unroll
         for (int k = 0; k < NF - 1; ++k) q[(IA + k) * nc + i] = s[IA + k];
+    }
+}
+
+// Six-equation model: primitive (the five-equation variables, then the phase
+// pressures p_k) -> conserved.  a_k r_k e_k = a_k (p_k + g_k pinf_k)/(g_k - 1)
+// = a_k (G_k p_k + P_k), r E = sum_k a_k r_k e_k + r|u|^2/2; the primitive
+// mixture-pressure row is not read.
+template <int NF, int NDIM>
+__global__ void __launch_bounds__(256) cons6_kernel(Geometry g, EosConst e, const double* __restrict__ w,
+                                                    double* __restrict__ q) {
+    using Lay = Layout<NF, NDIM, true>;
+    constexpr int NQ = Lay::NQ, IM = Lay::IM, IE = Lay::IE, IA = Lay::IA, II = Lay::II;
+    const long long nc = g.ncell;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < nc;
+         i += (long long)gridDim.x * blockDim.x) {
+        double s[NQ];
+#pragma unroll
+        for (int v = 0; v < NQ; ++v) s[v] = w[v * nc + i];
+        double rho = s[0];
+#pragma unroll
+        for (int k = 1; k < NF; ++k) rho += s[k];
+        double ke = 0.0;
+#pragma unroll
+        for (int d = 0; d < NDIM; ++d) { ke = fma(s[IM + d], s[IM + d], ke); q[(IM + d) * nc + i] = rho * s[IM + d]; }
+#pragma unroll
+        for (int k = 0; k < NF; ++k) q[k * nc + i] = s[k];
+        double aN = 1.0, esum = 0.0;
+#pragma unroll
+        for (int k = 0; k < NF - 1; ++k) {
+            q[(IA + k) * nc + i] = s[IA + k];
+            aN -= s[IA + k];
+            const double E = s[IA + k] * fma(e.G_N + e.dG[k], s[II + k], e.P_N + e.dP[k]);
+            q[(II + k) * nc + i] = E;
+            esum += E;
+        }
+        const double EN = aN * fma(e.G_N, s[II + NF - 1], e.P_N);
+        q[(II + NF - 1) * nc + i] = EN;
+        q[IE * nc + i] = esum + EN + 0.5 * rho * ke;
     }
 }
 

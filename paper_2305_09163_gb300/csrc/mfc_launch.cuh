@@ -13,22 +13,23 @@ constexpr int kElemThreads = 256;
 // so the two recomputed slots at its start cost about 0.1%.
 constexpr long long kStreamSlotsPerBlock = 16LL * kStreamThreads;
 
-template <typename Real, int NF, bool LEARNED = false, int ORDER = 5, bool NONUNIF = false>
+// SIX: the six-equation model (stream kernels, WENO5, uniform grids).
+template <typename Real, int NF, bool LEARNED = false, int ORDER = 5, bool NONUNIF = false, bool SIX = false>
 cudaError_t launch_sweep(SweepArgs a, int ndim, int dir, cudaStream_t s) {
     if (dir == 0) {
         const long long total = (long long)(a.g.n[0] + 2) * (a.g.ncell / a.g.n[0]);
         a.slots_per_block = kStreamSlotsPerBlock;
         const unsigned blocks = (unsigned)((total + kStreamSlotsPerBlock - 1) / kStreamSlotsPerBlock);
         switch (ndim) {
-            case 1: sweep_x_stream_kernel<Real, NF, 1, LEARNED, ORDER, NONUNIF><<<blocks, kStreamThreads, 0, s>>>(a); break;
-            case 2: sweep_x_stream_kernel<Real, NF, 2, LEARNED, ORDER, NONUNIF><<<blocks, kStreamThreads, 0, s>>>(a); break;
-            case 3: sweep_x_stream_kernel<Real, NF, 3, LEARNED, ORDER, NONUNIF><<<blocks, kStreamThreads, 0, s>>>(a); break;
+            case 1: sweep_x_stream_kernel<Real, NF, 1, LEARNED, ORDER, NONUNIF, SIX><<<blocks, kStreamThreads, 0, s>>>(a); break;
+            case 2: sweep_x_stream_kernel<Real, NF, 2, LEARNED, ORDER, NONUNIF, SIX><<<blocks, kStreamThreads, 0, s>>>(a); break;
+            case 3: sweep_x_stream_kernel<Real, NF, 3, LEARNED, ORDER, NONUNIF, SIX><<<blocks, kStreamThreads, 0, s>>>(a); break;
             default: return cudaErrorInvalidValue;
         }
         return cudaGetLastError();
     }
     const int t1 = (dir == 0) ? 1 : 0, t2 = (dir == 2) ? 1 : 2;
-    if (NONUNIF || a.yz_stream) {   // non-uniform grids: the stream kernel only
+    if (NONUNIF || SIX || a.yz_stream) {   // non-uniform grids, six-equation model: the stream kernel only
         // y/z stream kernel, one CTA per 32 x-lanes of a segment
         const unsigned blocks = (unsigned)((long long)((a.g.n[t1] + 31) / 32) * a.nseg * a.g.n[t2]);
         if constexpr (LEARNED) {
@@ -40,15 +41,15 @@ cudaError_t launch_sweep(SweepArgs a, int ndim, int dir, cudaStream_t s) {
             }
         } else {
             switch (ndim * 4 + dir) {
-                case 9: sweep_yz_stream_kernel<Real, NF, 2, 1, ORDER, NONUNIF><<<blocks, 32 * kRowsPerChunk, 0, s>>>(a); break;
-                case 13: sweep_yz_stream_kernel<Real, NF, 3, 1, ORDER, NONUNIF><<<blocks, 32 * kRowsPerChunk, 0, s>>>(a); break;
-                case 14: sweep_yz_stream_kernel<Real, NF, 3, 2, ORDER, NONUNIF><<<blocks, 32 * kRowsPerChunk, 0, s>>>(a); break;
+                case 9: sweep_yz_stream_kernel<Real, NF, 2, 1, ORDER, NONUNIF, SIX><<<blocks, 32 * kRowsPerChunk, 0, s>>>(a); break;
+                case 13: sweep_yz_stream_kernel<Real, NF, 3, 1, ORDER, NONUNIF, SIX><<<blocks, 32 * kRowsPerChunk, 0, s>>>(a); break;
+                case 14: sweep_yz_stream_kernel<Real, NF, 3, 2, ORDER, NONUNIF, SIX><<<blocks, 32 * kRowsPerChunk, 0, s>>>(a); break;
                 default: return cudaErrorInvalidValue;
             }
         }
         return cudaGetLastError();
     }
-    if constexpr (NONUNIF) return cudaErrorInvalidValue;
+    if constexpr (NONUNIF || SIX) return cudaErrorInvalidValue;
     const long long warps = (long long)((a.g.n[t1] + 31) / 32) * a.nseg * a.g.n[t2];
     const unsigned blocks = (unsigned)((warps * 32 + kSweepThreads - 1) / kSweepThreads);
     switch (ndim * 4 + dir) {
@@ -68,16 +69,29 @@ inline unsigned elem_blocks(long long n) {
     return (unsigned)b;
 }
 
-template <typename Real, int NF>
+template <typename Real, int NF, bool SIX = false>
 cudaError_t launch_prims(const PrimArgs& a, int ndim, bool rate, cudaStream_t s) {
     const unsigned blocks = elem_blocks(a.g.ncell);
     switch (ndim * 2 + (rate ? 1 : 0)) {
-        case 2: prims_kernel<Real, NF, 1, false><<<blocks, kElemThreads, 0, s>>>(a); break;
-        case 3: prims_kernel<Real, NF, 1, true><<<blocks, kElemThreads, 0, s>>>(a); break;
-        case 4: prims_kernel<Real, NF, 2, false><<<blocks, kElemThreads, 0, s>>>(a); break;
-        case 5: prims_kernel<Real, NF, 2, true><<<blocks, kElemThreads, 0, s>>>(a); break;
-        case 6: prims_kernel<Real, NF, 3, false><<<blocks, kElemThreads, 0, s>>>(a); break;
-        case 7: prims_kernel<Real, NF, 3, true><<<blocks, kElemThreads, 0, s>>>(a); break;
+        case 2: prims_kernel<Real, NF, 1, false, SIX><<<blocks, kElemThreads, 0, s>>>(a); break;
+        case 3: prims_kernel<Real, NF, 1, true, SIX><<<blocks, kElemThreads, 0, s>>>(a); break;
+        case 4: prims_kernel<Real, NF, 2, false, SIX><<<blocks, kElemThreads, 0, s>>>(a); break;
+        case 5: prims_kernel<Real, NF, 2, true, SIX><<<blocks, kElemThreads, 0, s>>>(a); break;
+        case 6: prims_kernel<Real, NF, 3, false, SIX><<<blocks, kElemThreads, 0, s>>>(a); break;
+        case 7: prims_kernel<Real, NF, 3, true, SIX><<<blocks, kElemThreads, 0, s>>>(a); break;
+        default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+template <int NF>
+cudaError_t launch_cons6(const Geometry& g, const EosConst& e, const double* w, double* q, int ndim,
+                         cudaStream_t s) {
+    const unsigned blocks = elem_blocks(g.ncell);
+    switch (ndim) {
+        case 1: cons6_kernel<NF, 1><<<blocks, kElemThreads, 0, s>>>(g, e, w, q); break;
+        case 2: cons6_kernel<NF, 2><<<blocks, kElemThreads, 0, s>>>(g, e, w, q); break;
+        case 3: cons6_kernel<NF, 3><<<blocks, kElemThreads, 0, s>>>(g, e, w, q); break;
         default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();
@@ -124,6 +138,17 @@ extern template cudaError_t launch_sweep<double, 3, false, 3>(SweepArgs, int, in
 extern template cudaError_t launch_sweep<float, 1, false, 3>(SweepArgs, int, int, cudaStream_t);
 extern template cudaError_t launch_sweep<float, 2, false, 3>(SweepArgs, int, int, cudaStream_t);
 extern template cudaError_t launch_sweep<float, 3, false, 3>(SweepArgs, int, int, cudaStream_t);
+// six-equation model (mfc_inst_*_six_*.cu)
+extern template cudaError_t launch_sweep<double, 2, false, 5, false, true>(SweepArgs, int, int, cudaStream_t);
+extern template cudaError_t launch_sweep<double, 3, false, 5, false, true>(SweepArgs, int, int, cudaStream_t);
+extern template cudaError_t launch_sweep<float, 2, false, 5, false, true>(SweepArgs, int, int, cudaStream_t);
+extern template cudaError_t launch_sweep<float, 3, false, 5, false, true>(SweepArgs, int, int, cudaStream_t);
+extern template cudaError_t launch_prims<double, 2, true>(const PrimArgs&, int, bool, cudaStream_t);
+extern template cudaError_t launch_prims<double, 3, true>(const PrimArgs&, int, bool, cudaStream_t);
+extern template cudaError_t launch_prims<float, 2, true>(const PrimArgs&, int, bool, cudaStream_t);
+extern template cudaError_t launch_prims<float, 3, true>(const PrimArgs&, int, bool, cudaStream_t);
+extern template cudaError_t launch_cons6<2>(const Geometry&, const EosConst&, const double*, double*, int, cudaStream_t);
+extern template cudaError_t launch_cons6<3>(const Geometry&, const EosConst&, const double*, double*, int, cudaStream_t);
 extern template cudaError_t launch_cons<1>(const Geometry&, const EosConst&, const double*, double*, int, cudaStream_t);
 extern template cudaError_t launch_cons<2>(const Geometry&, const EosConst&, const double*, double*, int, cudaStream_t);
 extern template cudaError_t launch_cons<3>(const Geometry&, const EosConst&, const double*, double*, int, cudaStream_t);

@@ -493,8 +493,10 @@ __global__ void harvest_kernel(const double* __restrict__ wf, int nxf, int nyf, 
 }
 
 __global__ void __launch_bounds__(256) prims_out_kernel(const double* __restrict__ q, double* __restrict__ w,
-                                                        long long nc, int nf, int ndim, EosConst e) {
-    // generic (runtime NF, NDIM) FP64 primitive recovery for output
+                                                        long long nc, int nf, int ndim, EosConst e, int six) {
+    // generic (runtime NF, NDIM) FP64 primitive recovery for output; the
+    // six-equation model (six) appends the phase pressures
+    // p_k = (a_k r_k e_k / a_k - P_k)/G_k
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < nc;
          i += (long long)gridDim.x * blockDim.x) {
         const int ns = 2 * nf + ndim, IM = nf, IE = nf + ndim, IA = nf + ndim + 1;
@@ -514,6 +516,16 @@ __global__ void __launch_bounds__(256) prims_out_kernel(const double* __restrict
         for (int k2 = 0; k2 < nf; ++k2) w[k2 * nc + i] = q[k2 * nc + i];
         w[IE * nc + i] = (q[IE * nc + i] - 0.5 * ke - Pm) / G;
         for (int k2 = IA; k2 < ns; ++k2) w[k2 * nc + i] = q[k2 * nc + i];
+        if (six) {
+            double aN = 1.0;
+            for (int k2 = 0; k2 < nf; ++k2) {
+                const double ak = k2 < nf - 1 ? q[(IA + k2) * nc + i] : aN;
+                if (k2 < nf - 1) aN -= ak;
+                const double Gk = k2 < nf - 1 ? e.G_N + e.dG[k2] : e.G_N;
+                const double Pk = k2 < nf - 1 ? e.P_N + e.dP[k2] : e.P_N;
+                w[(ns + k2) * nc + i] = (q[(ns + k2) * nc + i] / ak - Pk) / Gk;
+            }
+        }
     }
 }
 
@@ -534,10 +546,10 @@ cudaError_t mfc_launch_mlp_pack(const float* P, void* frag, cudaStream_t s) {
 
 // Host launcher used by mfc_get_prims in the context code.
 cudaError_t mfc_launch_prims_out(const double* q, double* w, long long nc, int nf, int ndim, const EosConst& e,
-                                 cudaStream_t s) {
+                                 int six, cudaStream_t s) {
     long long b = (nc + 255) / 256;
     if (b > 152 * 16) b = 152 * 16;
-    prims_out_kernel<<<(unsigned)b, 256, 0, s>>>(q, w, nc, nf, ndim, e);
+    prims_out_kernel<<<(unsigned)b, 256, 0, s>>>(q, w, nc, nf, ndim, e, six);
     return cudaGetLastError();
 }
 

@@ -43,7 +43,8 @@ def sampled_rhs_error(pb, q, R_gpu_flat, cells, Rc, fmax):
 def state_error(pb, qa, qb):
     """Per-component max difference of two conserved states, relative to the
     component's magnitude (momentum components share the momentum magnitude,
-    volume fractions use 1)."""
+    volume fractions use 1; the six-equation model's phase energies their own
+    magnitude)."""
     ns = pb.sys_size
     nf, nd = pb.nf, pb.ndim
     qa = np.asarray(qa).reshape(ns, -1)
@@ -53,7 +54,7 @@ def state_error(pb, qa, qb):
     for v in range(ns):
         if nf <= v < nf + nd:
             scale = mom
-        elif v > nf + nd:
+        elif nf + nd < v < 2 * nf + nd:
             scale = 1.0
         else:
             scale = np.abs(qb[v]).max()
