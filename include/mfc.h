@@ -274,8 +274,9 @@ long long mfc_network_rows(mfc_ctx* ctx);
 
 /* Per-kernel timing collected while "profile" is on: for category i in
  * [0, n) (0 prims, 1 sweep_x, 2 sweep_y, 3 sweep_z, 4 prims+cfl, 5 convert,
- * 6 mlp), total milliseconds and launch counts.  Synchronises the stream.
- * Returns the number of categories (7). */
+ * 6 mlp, 7 characteristic-boundary rates), total milliseconds and launch
+ * counts.  Synchronises the stream.
+ * Returns the number of categories (8). */
 int mfc_profile_read(mfc_ctx* ctx, double* total_ms, long long* launches, int n);
 
 /* Largest grid (in cells) that mfc_rhs_noalloc accepts. */

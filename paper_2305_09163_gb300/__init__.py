@@ -23,7 +23,7 @@ MFC_ERR_ARG, MFC_ERR_STATE_UNSET, MFC_ERR_OOM, MFC_ERR_CUDA, MFC_ERR_NONPHYSICAL
 MFC_BC_PERIODIC, MFC_BC_TRANSMISSIVE, MFC_BC_REFLECTIVE, MFC_BC_CHARACTERISTIC = 0, 1, 2, 3
 MFC_FP64, MFC_MIXED, MFC_LEARNED = 0, 1, 2
 PRECISIONS = {"fp64": MFC_FP64, "mixed": MFC_MIXED, "learned": MFC_LEARNED}
-PROFILE_CATEGORIES = ("prims", "sweep_x", "sweep_y", "sweep_z", "prims_cfl", "convert", "mlp")
+PROFILE_CATEGORIES = ("prims", "sweep_x", "sweep_y", "sweep_z", "prims_cfl", "convert", "mlp", "boundary")
 MLP_PARAMS = 32 * 5 + 32 + 32 * 32 + 32 + 3 * 32 + 3
 
 _lib = None

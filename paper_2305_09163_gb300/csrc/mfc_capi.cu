@@ -26,7 +26,7 @@ cudaError_t mfc_launch_prims_out(const double* q, double* w, long long nc, int n
 
 namespace {
 
-enum ProfCat { P_PRIMS = 0, P_SWEEP_X, P_SWEEP_Y, P_SWEEP_Z, P_CFL, P_CONVERT, P_MLP, P_NCAT };
+enum ProfCat { P_PRIMS = 0, P_SWEEP_X, P_SWEEP_Y, P_SWEEP_Z, P_CFL, P_CONVERT, P_MLP, P_BOUNDARY, P_NCAT };
 
 struct ProfRec {
     int cat;
@@ -57,6 +57,8 @@ struct mfc_ctx {
     int six = 0;              // model 2: six-equation model with pressure relaxation
     int nw = 3;               // primitive rows (2N + d); ns = state rows (+N for the six-equation model)
     float* grid[3] = {nullptr, nullptr, nullptr};   // non-uniform directions: WENO5 rows (mfc_grid.cu)
+    void* cbc_rates = nullptr;    // characteristic boundaries: rates of the boundary cells
+    size_t cbc_bytes = 0;
 
     Geometry g{};
     EosConst e{};
@@ -298,9 +300,62 @@ struct RkStage {
     double c0, c1, dt;
 };
 
+// Characteristic boundaries: the boundary cells' rates for this stage, ahead
+// of the sweeps (cbc_rates_kernel); fills a's side-buffer fields.
+mfc_status run_cbc(mfc_ctx* c, SweepArgs& a) {
+    long long cells = 0;
+    for (int d = 0; d < 3; ++d)
+        for (int s = 0; s < 2; ++s) {
+            a.cbc_off[d][s] = -1;
+            if (d < c->ndim && c->bc[2 * d + s] == MFC_BC_CHARACTERISTIC) {
+                a.cbc_off[d][s] = cells * c->nw;
+                cells += c->ncell / c->n[d];
+            }
+        }
+    const size_t bytes = (size_t)cells * (size_t)c->nw * real_size(c);
+    if (bytes > c->cbc_bytes) {
+        cudaFree(c->cbc_rates);
+        c->cbc_rates = nullptr;
+        c->cbc_bytes = 0;
+        cudaError_t e = cudaMalloc(&c->cbc_rates, bytes);
+        if (e != cudaSuccess) {
+            c->cbc_rates = nullptr;
+            return fail(c, e == cudaErrorMemoryAllocation ? MFC_ERR_OOM : MFC_ERR_CUDA, "cudaMalloc: %s",
+                        cudaGetErrorString(e));
+        }
+        c->cbc_bytes = bytes;
+    }
+    a.cbc_rates = c->cbc_rates;
+    return launch(c, P_BOUNDARY, [&]() -> cudaError_t {
+        if (is_f32(c)) {
+            switch (c->nf) {
+                case 1: return launch_cbc<float, 1>(a, c->ndim, cells, c->stream);
+                case 2: return launch_cbc<float, 2>(a, c->ndim, cells, c->stream);
+                default: return launch_cbc<float, 3>(a, c->ndim, cells, c->stream);
+            }
+        }
+        switch (c->nf) {
+            case 1: return launch_cbc<double, 1>(a, c->ndim, cells, c->stream);
+            case 2: return launch_cbc<double, 2>(a, c->ndim, cells, c->stream);
+            default: return launch_cbc<double, 3>(a, c->ndim, cells, c->stream);
+        }
+    });
+}
+
 mfc_status run_sweeps(mfc_ctx* c, double* out, const RkStage* rk) {
+    SweepArgs cb{};
+    if (has_cbc(c)) {
+        cb = base_sweep(c);
+        mfc_status s = run_cbc(c, cb);
+        if (s != MFC_OK) return s;
+    }
     for (int d = 0; d < c->ndim; ++d) {
         SweepArgs a = base_sweep(c);
+        if (cb.cbc_rates) {
+            a.cbc_rates = cb.cbc_rates;
+            for (int k = 0; k < 3; ++k)
+                for (int s = 0; s < 2; ++s) a.cbc_off[k][s] = cb.cbc_off[k][s];
+        }
         a.seg = auto_segment(c, d);
         a.nseg = (c->n[d] + a.seg - 1) / a.seg;
         a.R = c->R;
@@ -350,6 +405,7 @@ void free_all(mfc_ctx* c) {
     cudaFree(c->d_fallback);
     cudaFree(c->mlp);
     for (int d = 0; d < 3; ++d) cudaFree(c->grid[d]);
+    cudaFree(c->cbc_rates);
     if (c->h_pin) cudaFreeHost(c->h_pin);
 }
 

@@ -88,7 +88,9 @@ struct SweepArgs {
     int bound;              // learned form: range safeguard on learned edge values
     const float* grid[3];   // non-uniform directions: WENO5 table (GridCol layout), else null
     int grid_stride[3];     // x: cells per table value (n + 2); see GridCol
-    int cbc;                // some boundary is characteristic (the stream kernels handle it)
+    int cbc;                // some boundary is characteristic
+    const void* cbc_rates;  // their cells' normal rates (cbc_rates_kernel), Real, or null
+    long long cbc_off[3][2];    // start of direction d, side s in cbc_rates (-1: not characteristic)
     int kapila;             // 1: Kapila model, K div(u) in the volume-fraction rows
     double kgam[3], kpinf[3];   // Kapila, six-equation model: gamma_k and pi_inf_k of every fluid
     double rc1[3];              // six-equation relaxation: (gamma_k - 1)/gamma_k
@@ -1176,16 +1178,71 @@ __device__ __noinline__ void cbc_cell_rate(const SweepArgs& a, long long idx, lo
     cbc_rate<Real, NF, NDIM, DIR>(sweep_eos<Real>(a), wb, wx, high, out);
 }
 
-// Finish cell idx (coordinate b along DIR, neighbours sd apart): flux
-// difference and alpha div(u) source, or, at a characteristic boundary, the
-// boundary rate; then store, accumulate or apply the RK stage.
+// Characteristic boundary rates of every boundary cell, ahead of the sweeps:
+// one lane per cell, so no sweep warp waits on the FP64 boundary arithmetic.
+// cbc_rates holds, for direction d and side s (0 low, 1 high) from
+// cbc_off[d][s], NS rows of the plane's cells, indexed by the transverse flat
+// index tr (x fastest among the two other directions).
+template <typename Real, int NF, int NDIM>
+__global__ void __launch_bounds__(256) cbc_rates_kernel(const SweepArgs a, long long total) {
+    using Lay = Layout<NF, NDIM>;
+    constexpr int NS = Lay::NS;
+    Real* out = static_cast<Real*>(const_cast<void*>(a.cbc_rates));
+    const int nx = a.g.n[0], ny = a.g.n[1];
+    for (long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x; g < total;
+         g += (long long)gridDim.x * blockDim.x) {
+        int dir = -1, side = 0;
+        long long tr = 0, nt = 0, base = 0;
+        for (int dd = 0; dd < NDIM && dir < 0; ++dd)
+            for (int s = 0; s < 2 && dir < 0; ++s) {
+                const long long o = a.cbc_off[dd][s];
+                if (o < 0) continue;
+                const long long cnt = a.g.ncell / a.g.n[dd];
+                const long long first = o / NS;   // cells before this plane
+                if (g < first + cnt) {
+                    dir = dd;
+                    side = s;
+                    tr = g - first;
+                    nt = cnt;
+                    base = o;
+                }
+            }
+        if (dir < 0) continue;
+        const int n = a.g.n[dir];
+        const int b = side ? n - 1 : 0;
+        long long idx;
+        if (dir == 0) idx = (long long)b + (long long)nx * tr;
+        else if (dir == 1) idx = (tr % nx) + (long long)nx * (b + (long long)ny * (tr / nx));
+        else idx = tr + (long long)nx * ny * b;
+        const long long sd = stride_of(a.g, dir);
+        Real inv = (Real)a.g.inv_dx[dir];
+        if (a.grid[dir])
+            inv = dir == 0 ? grid_inv_dx<true>(a.grid[0], a.grid_stride[0], b, Real(0))
+                           : grid_inv_dx<false>(a.grid[dir], a.grid_stride[dir], b, Real(0));
+        Real r[NS];
+        if (dir == 0) cbc_cell_rate<Real, NF, NDIM, 0>(a, idx, sd, n, side == 1, inv, r);
+        else if (dir == 1) {
+            if constexpr (NDIM > 1) cbc_cell_rate<Real, NF, NDIM, 1>(a, idx, sd, n, side == 1, inv, r);
+        } else {
+            if constexpr (NDIM > 2) cbc_cell_rate<Real, NF, NDIM, 2>(a, idx, sd, n, side == 1, inv, r);
+        }
+#pragma unroll
+        for (int v = 0; v < NS; ++v) out[base + v * nt + tr] = r[v];
+    }
+}
+
+// Finish cell idx (coordinate b along DIR, neighbours sd apart, transverse
+// flat index tr or -1): flux difference and alpha div(u) source, or, at a
+// characteristic boundary, the boundary rate (from cbc_rates when the caller
+// gives tr, else computed here); then store, accumulate or apply the RK stage.
 //
 // Six-equation model (SIX): NQ rows; the phase energies lose a_k p div(u)
 // (cell values), and an RK stage update ends with the pressure relaxation
 // (relax6) before it is stored.
 template <typename Real, int NF, int NDIM, int DIR, bool SIX = false>
 __device__ __forceinline__ void finish_cell(const SweepArgs& a, long long idx, const Real* Fm, const Real* Fp,
-                                            Real um, Real up, const Real* cell, Real inv_dx, int b, long long sd) {
+                                            Real um, Real up, const Real* cell, Real inv_dx, int b, long long sd,
+                                            long long tr = -1) {
     using Lay = Layout<NF, NDIM, SIX>;
     constexpr int NS = Lay::NS, NQ = Lay::NQ, IA = Lay::IA;
     Real out[NQ];
@@ -1219,10 +1276,17 @@ __device__ __forceinline__ void finish_cell(const SweepArgs& a, long long idx, c
         const bool lo = b == 0 && a.g.bc_lo[DIR] == BC_CHARACTERISTIC;
         const bool hi = b == n - 1 && a.g.bc_hi[DIR] == BC_CHARACTERISTIC;
         if (lo || hi) {   // the boundary rate replaces the flux difference and the source
-            Real cb[NS];
-            cbc_cell_rate<Real, NF, NDIM, DIR>(a, idx, sd, n, !lo, inv_dx, cb);
+            if (a.cbc_rates && tr >= 0) {
+                const Real* rb = static_cast<const Real*>(a.cbc_rates) + a.cbc_off[DIR][lo ? 0 : 1] + tr;
+                const long long nt = a.g.ncell / n;
 #pragma unroll
-            for (int v = 0; v < NS; ++v) out[v] = cb[v];
+                for (int v = 0; v < NS; ++v) out[v] = rb[v * nt];
+            } else {
+                Real cb[NS];
+                cbc_cell_rate<Real, NF, NDIM, DIR>(a, idx, sd, n, !lo, inv_dx, cb);
+#pragma unroll
+                for (int v = 0; v < NS; ++v) out[v] = cb[v];
+            }
         }
     }
     const long long nc = a.g.ncell;
@@ -1580,7 +1644,7 @@ __global__ void __launch_bounds__(kStreamThreads) sweep_x_stream_kernel(const Sw
             for (int q = 0; q < NQ; ++q) Fm[q] = sh_F[q][t];
             finish_cell<Real, NF, NDIM, 0, SIX>(a, rowoff + (c - 1), Fm, F, sh_F[NQ][t], ut, cm1,
                                            NONUNIF ? grid_inv_dx<true>(a.grid[0], a.grid_stride[0], c - 1, Real(0)) : inv_dx,
-                                           c - 1, 1);
+                                           c - 1, 1, row);
         }
         __syncthreads();
         // carry the last slot of the chunk into position 0
@@ -1770,7 +1834,7 @@ __device__ __forceinline__ void sweep_yz_stream_body(const SweepArgs& a) {
             finish_cell<Real, NF, NDIM, DIR, SIX>(a, basei + (long long)(c - 1) * sd, Fm, F, sh_F[NQ][row][lane], ut, cm1,
                                              NONUNIF ? grid_inv_dx<false>(a.grid[DIR], a.grid_stride[DIR], c - 1, Real(0))
                                                      : inv_dx,
-                                             c - 1, sd);
+                                             c - 1, sd, (long long)t1 + (long long)n1 * t2);
         }
         __syncthreads();
         // carry the last row of the chunk into row 0

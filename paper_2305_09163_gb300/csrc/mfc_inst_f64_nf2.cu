@@ -4,5 +4,6 @@
 namespace mfc {
 template cudaError_t launch_sweep<double, 2>(SweepArgs, int, int, cudaStream_t);
 template cudaError_t launch_prims<double, 2>(const PrimArgs&, int, bool, cudaStream_t);
+template cudaError_t launch_cbc<double, 2>(const SweepArgs&, int, long long, cudaStream_t);
 template cudaError_t launch_cons<2>(const Geometry&, const EosConst&, const double*, double*, int, cudaStream_t);
 }  // namespace mfc

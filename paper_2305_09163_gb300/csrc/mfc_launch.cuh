@@ -84,6 +84,19 @@ cudaError_t launch_prims(const PrimArgs& a, int ndim, bool rate, cudaStream_t s)
     return cudaGetLastError();
 }
 
+// Characteristic boundary rates (cbc_rates_kernel): total = boundary cells.
+template <typename Real, int NF>
+cudaError_t launch_cbc(const SweepArgs& a, int ndim, long long total, cudaStream_t s) {
+    const unsigned blocks = elem_blocks(total);
+    switch (ndim) {
+        case 1: cbc_rates_kernel<Real, NF, 1><<<blocks, kElemThreads, 0, s>>>(a, total); break;
+        case 2: cbc_rates_kernel<Real, NF, 2><<<blocks, kElemThreads, 0, s>>>(a, total); break;
+        case 3: cbc_rates_kernel<Real, NF, 3><<<blocks, kElemThreads, 0, s>>>(a, total); break;
+        default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
 template <int NF>
 cudaError_t launch_cons6(const Geometry& g, const EosConst& e, const double* w, double* q, int ndim,
                          cudaStream_t s) {
@@ -113,7 +126,8 @@ cudaError_t launch_cons(const Geometry& g, const EosConst& e, const double* w, d
 // Explicitly instantiated in the mfc_inst_*.cu units.
 #define MFC_DECLARE_INSTANCES(Real, NF)                                                         \
     extern template cudaError_t launch_sweep<Real, NF>(SweepArgs, int, int, cudaStream_t); \
-    extern template cudaError_t launch_prims<Real, NF>(const PrimArgs&, int, bool, cudaStream_t);
+    extern template cudaError_t launch_prims<Real, NF>(const PrimArgs&, int, bool, cudaStream_t); \
+    extern template cudaError_t launch_cbc<Real, NF>(const SweepArgs&, int, long long, cudaStream_t);
 
 MFC_DECLARE_INSTANCES(double, 1)
 MFC_DECLARE_INSTANCES(double, 2)
