@@ -1863,6 +1863,15 @@ __global__ void __launch_bounds__(32 * kRowsPerChunk) sweep_yz_stream_kernel(con
     sweep_yz_stream_body<Real, NF, NDIM, DIR, false, ORDER, NONUNIF, SIX>(a);
 }
 
+// The mixed form's six-equation y/z sweep: bounded to 5 CTAs per SM (96
+// registers; unbounded it took 107 and ran 45 instead of 37 ms over the 256^3
+// bench).  A bound of one CTA per SM is not the same as none: it slowed the
+// five-equation kernels by half, hence a separate entry.
+template <int NF, int NDIM, int DIR>
+__global__ void __launch_bounds__(32 * kRowsPerChunk, 5) sweep_yz_stream_six32_kernel(const SweepArgs a) {
+    sweep_yz_stream_body<float, NF, NDIM, DIR, false, 5, false, true>(a);
+}
+
 template <int NF, int NDIM, int DIR>
 __global__ void __launch_bounds__(32 * kRowsPerChunk, NF <= 2 ? 4 : 3) sweep_yz_stream_learned_kernel(const SweepArgs a) {
     sweep_yz_stream_body<float, NF, NDIM, DIR, true, 5>(a);

@@ -39,6 +39,13 @@ cudaError_t launch_sweep(SweepArgs a, int ndim, int dir, cudaStream_t s) {
                 case 14: sweep_yz_stream_learned_kernel<NF, 3, 2><<<blocks, 32 * kRowsPerChunk, 0, s>>>(a); break;
                 default: return cudaErrorInvalidValue;
             }
+        } else if constexpr (SIX && sizeof(Real) == 4) {
+            switch (ndim * 4 + dir) {
+                case 9: sweep_yz_stream_six32_kernel<NF, 2, 1><<<blocks, 32 * kRowsPerChunk, 0, s>>>(a); break;
+                case 13: sweep_yz_stream_six32_kernel<NF, 3, 1><<<blocks, 32 * kRowsPerChunk, 0, s>>>(a); break;
+                case 14: sweep_yz_stream_six32_kernel<NF, 3, 2><<<blocks, 32 * kRowsPerChunk, 0, s>>>(a); break;
+                default: return cudaErrorInvalidValue;
+            }
         } else {
             switch (ndim * 4 + dir) {
                 case 9: sweep_yz_stream_kernel<Real, NF, 2, 1, ORDER, NONUNIF, SIX><<<blocks, 32 * kRowsPerChunk, 0, s>>>(a); break;
