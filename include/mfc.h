@@ -102,8 +102,8 @@ mfc_status mfc_init(mfc_ctx** out, int nx, int ny, int nz, const double lo[3], c
  *                K_k = alpha_k (rho c_W^2/(rho_k c_k^2) - 1), c_W Wood's mixture
  *                sound speed (two fluids: the formula of Sec. 2.1);
  *                2: six-equation model with pressure relaxation (Sec. 2.3;
- *                2 or 3 fluids, FP64 and mixed forms, WENO5, uniform grid,
- *                no characteristic boundaries): the state gains the phase
+ *                2 or 3 fluids, FP64 and mixed forms, no characteristic
+ *                boundaries): the state gains the phase
  *                internal energies (layout above), waves travel at the frozen
  *                sound speed r c^2 = sum_k a_k g_k (p + pinf_k), the phase
  *                energies are carried with the face velocity and lose

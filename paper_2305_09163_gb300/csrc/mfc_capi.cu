@@ -149,10 +149,23 @@ bool has_cbc(const mfc_ctx* c) {
 
 cudaError_t dispatch_sweep(const mfc_ctx* c, const SweepArgs& a, int dir) {
     if (c->six) {
-        if (is_f32(c)) return c->nf == 2 ? launch_sweep<float, 2, false, 5, false, true>(a, c->ndim, dir, c->stream)
-                                         : launch_sweep<float, 3, false, 5, false, true>(a, c->ndim, dir, c->stream);
-        return c->nf == 2 ? launch_sweep<double, 2, false, 5, false, true>(a, c->ndim, dir, c->stream)
-                          : launch_sweep<double, 3, false, 5, false, true>(a, c->ndim, dir, c->stream);
+        const bool two = c->nf == 2;
+        if (nonuniform(c)) {
+            if (is_f32(c)) return two ? launch_sweep<float, 2, false, 5, true, true>(a, c->ndim, dir, c->stream)
+                                      : launch_sweep<float, 3, false, 5, true, true>(a, c->ndim, dir, c->stream);
+            return two ? launch_sweep<double, 2, false, 5, true, true>(a, c->ndim, dir, c->stream)
+                       : launch_sweep<double, 3, false, 5, true, true>(a, c->ndim, dir, c->stream);
+        }
+        if (c->weno_order == 3) {
+            if (is_f32(c)) return two ? launch_sweep<float, 2, false, 3, false, true>(a, c->ndim, dir, c->stream)
+                                      : launch_sweep<float, 3, false, 3, false, true>(a, c->ndim, dir, c->stream);
+            return two ? launch_sweep<double, 2, false, 3, false, true>(a, c->ndim, dir, c->stream)
+                       : launch_sweep<double, 3, false, 3, false, true>(a, c->ndim, dir, c->stream);
+        }
+        if (is_f32(c)) return two ? launch_sweep<float, 2, false, 5, false, true>(a, c->ndim, dir, c->stream)
+                                  : launch_sweep<float, 3, false, 5, false, true>(a, c->ndim, dir, c->stream);
+        return two ? launch_sweep<double, 2, false, 5, false, true>(a, c->ndim, dir, c->stream)
+                   : launch_sweep<double, 3, false, 5, false, true>(a, c->ndim, dir, c->stream);
     }
     if (nonuniform(c)) {
         if (is_f32(c)) {
@@ -564,7 +577,6 @@ mfc_status mfc_set_param(mfc_ctx* c, const char* name, double value) {
         if (value == 3.0 && c->precision == MFC_LEARNED)
             return fail(c, MFC_ERR_ARG, "the learned form replaces the WENO5 weights (weno_order 5)");
         if (value == 3.0 && nonuniform(c)) return fail(c, MFC_ERR_ARG, "non-uniform grids need weno_order 5");
-        if (value == 3.0 && c->six) return fail(c, MFC_ERR_ARG, "the six-equation model needs weno_order 5");
         c->weno_order = (int)value;
     } else if (!strcmp(name, "rk_order")) {
         if (value != 1.0 && value != 2.0 && value != 3.0) return fail(c, MFC_ERR_ARG, "rk_order must be 1, 2 or 3");
@@ -578,8 +590,6 @@ mfc_status mfc_set_param(mfc_ctx* c, const char* name, double value) {
         if (six) {
             if (c->precision == MFC_LEARNED) return fail(c, MFC_ERR_ARG, "six-equation model: FP64 and mixed forms");
             if (c->nf < 2) return fail(c, MFC_ERR_ARG, "six-equation model: 2 or 3 fluids");
-            if (c->weno_order != 5 || nonuniform(c))
-                return fail(c, MFC_ERR_ARG, "six-equation model: WENO5 on a uniform grid");
         }
         if (six != c->six) {   // the state layout changes: set the model before the state
             if (c->state_set) return fail(c, MFC_ERR_ARG, "set the model before the state");
@@ -604,7 +614,6 @@ mfc_status mfc_set_grid(mfc_ctx* c, int dir, const double* faces, int nfaces) {
     if (!faces || nfaces != c->n[dir] + 1) return fail(c, MFC_ERR_ARG, "need n+1 = %d face coordinates", c->n[dir] + 1);
     if (c->precision == MFC_LEARNED) return fail(c, MFC_ERR_ARG, "non-uniform grids: FP64 and mixed forms only");
     if (c->weno_order != 5) return fail(c, MFC_ERR_ARG, "non-uniform grids need weno_order 5");
-    if (c->six) return fail(c, MFC_ERR_ARG, "non-uniform grids: five-equation models only");
     const bool periodic = c->bc[2 * dir] == MFC_BC_PERIODIC;
     std::vector<float> rows;
     if (!grid_tables(faces, c->n[dir], periodic, rows))

@@ -1476,7 +1476,7 @@ constexpr int kStreamThreads = 128;
 
 template <typename Real, int NF, int NDIM, bool LEARNED = false, int ORDER = 5, bool NONUNIF = false, bool SIX = false>
 __global__ void __launch_bounds__(kStreamThreads) sweep_x_stream_kernel(const SweepArgs a) {
-    static_assert(!SIX || (!LEARNED && ORDER == 5 && !NONUNIF), "six-equation model: WENO5 on uniform grids");
+    static_assert(!SIX || !LEARNED, "six-equation model: FP64 and mixed forms");
     static_assert(!NONUNIF || (!LEARNED && ORDER == 5), "non-uniform grids: WENO5, FP64 and mixed forms");
     static_assert(!LEARNED || sizeof(Real) == 4, "the learned form runs in FP32");
     static_assert(!LEARNED || ORDER == 5, "the learned form replaces the WENO5 weights");
@@ -1680,7 +1680,7 @@ constexpr int kRowsPerChunk = 4;
 
 template <typename Real, int NF, int NDIM, int DIR, bool LEARNED, int ORDER, bool NONUNIF = false, bool SIX = false>
 __device__ __forceinline__ void sweep_yz_stream_body(const SweepArgs& a) {
-    static_assert(!SIX || (!LEARNED && ORDER == 5 && !NONUNIF), "six-equation model: WENO5 on uniform grids");
+    static_assert(!SIX || !LEARNED, "six-equation model: FP64 and mixed forms");
     static_assert(!NONUNIF || (!LEARNED && ORDER == 5), "non-uniform grids: WENO5, FP64 and mixed forms");
     static_assert(!LEARNED || ORDER == 5, "the learned form replaces the WENO5 weights");
     static_assert(DIR == 1 || DIR == 2, "y or z");
@@ -1867,9 +1867,9 @@ __global__ void __launch_bounds__(32 * kRowsPerChunk) sweep_yz_stream_kernel(con
 // registers; unbounded it took 107 and ran 45 instead of 37 ms over the 256^3
 // bench).  A bound of one CTA per SM is not the same as none: it slowed the
 // five-equation kernels by half, hence a separate entry.
-template <int NF, int NDIM, int DIR>
+template <int NF, int NDIM, int DIR, int ORDER = 5, bool NONUNIF = false>
 __global__ void __launch_bounds__(32 * kRowsPerChunk, 5) sweep_yz_stream_six32_kernel(const SweepArgs a) {
-    sweep_yz_stream_body<float, NF, NDIM, DIR, false, 5, false, true>(a);
+    sweep_yz_stream_body<float, NF, NDIM, DIR, false, ORDER, NONUNIF, true>(a);
 }
 
 template <int NF, int NDIM, int DIR>

@@ -1,0 +1,5 @@
+// Instantiates the six-equation-model sweeps on non-uniform grids for float arithmetic and 3 fluids.
+#include "mfc_launch.cuh"
+namespace mfc {
+template cudaError_t launch_sweep<float, 3, false, 5, true, true>(SweepArgs, int, int, cudaStream_t);
+}  // namespace mfc

@@ -41,9 +41,9 @@ cudaError_t launch_sweep(SweepArgs a, int ndim, int dir, cudaStream_t s) {
             }
         } else if constexpr (SIX && sizeof(Real) == 4) {
             switch (ndim * 4 + dir) {
-                case 9: sweep_yz_stream_six32_kernel<NF, 2, 1><<<blocks, 32 * kRowsPerChunk, 0, s>>>(a); break;
-                case 13: sweep_yz_stream_six32_kernel<NF, 3, 1><<<blocks, 32 * kRowsPerChunk, 0, s>>>(a); break;
-                case 14: sweep_yz_stream_six32_kernel<NF, 3, 2><<<blocks, 32 * kRowsPerChunk, 0, s>>>(a); break;
+                case 9: sweep_yz_stream_six32_kernel<NF, 2, 1, ORDER, NONUNIF><<<blocks, 32 * kRowsPerChunk, 0, s>>>(a); break;
+                case 13: sweep_yz_stream_six32_kernel<NF, 3, 1, ORDER, NONUNIF><<<blocks, 32 * kRowsPerChunk, 0, s>>>(a); break;
+                case 14: sweep_yz_stream_six32_kernel<NF, 3, 2, ORDER, NONUNIF><<<blocks, 32 * kRowsPerChunk, 0, s>>>(a); break;
                 default: return cudaErrorInvalidValue;
             }
         } else {
@@ -159,7 +159,15 @@ extern template cudaError_t launch_sweep<double, 3, false, 3>(SweepArgs, int, in
 extern template cudaError_t launch_sweep<float, 1, false, 3>(SweepArgs, int, int, cudaStream_t);
 extern template cudaError_t launch_sweep<float, 2, false, 3>(SweepArgs, int, int, cudaStream_t);
 extern template cudaError_t launch_sweep<float, 3, false, 3>(SweepArgs, int, int, cudaStream_t);
-// six-equation model (mfc_inst_*_six_*.cu)
+// six-equation model (mfc_inst_*_six_*.cu; with a stretched grid or WENO3: mfc_inst_*_six_nu_*, *_six_w3_*)
+extern template cudaError_t launch_sweep<double, 2, false, 5, true, true>(SweepArgs, int, int, cudaStream_t);
+extern template cudaError_t launch_sweep<double, 3, false, 5, true, true>(SweepArgs, int, int, cudaStream_t);
+extern template cudaError_t launch_sweep<float, 2, false, 5, true, true>(SweepArgs, int, int, cudaStream_t);
+extern template cudaError_t launch_sweep<float, 3, false, 5, true, true>(SweepArgs, int, int, cudaStream_t);
+extern template cudaError_t launch_sweep<double, 2, false, 3, false, true>(SweepArgs, int, int, cudaStream_t);
+extern template cudaError_t launch_sweep<double, 3, false, 3, false, true>(SweepArgs, int, int, cudaStream_t);
+extern template cudaError_t launch_sweep<float, 2, false, 3, false, true>(SweepArgs, int, int, cudaStream_t);
+extern template cudaError_t launch_sweep<float, 3, false, 3, false, true>(SweepArgs, int, int, cudaStream_t);
 extern template cudaError_t launch_sweep<double, 2, false, 5, false, true>(SweepArgs, int, int, cudaStream_t);
 extern template cudaError_t launch_sweep<double, 3, false, 5, false, true>(SweepArgs, int, int, cudaStream_t);
 extern template cudaError_t launch_sweep<float, 2, false, 5, false, true>(SweepArgs, int, int, cudaStream_t);
