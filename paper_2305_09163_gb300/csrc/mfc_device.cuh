@@ -623,6 +623,82 @@ __device__ __forceinline__ void hllc(const Real* L, const Real* R, const Mix<Rea
     }
 }
 
+// The FP64 path's HLLC in float-float arithmetic (mfc_df.cuh): the same
+// steps, branch order and xi - 1 form as hllc, on float-float copies of the
+// FP64 face states (integer splits); only the mixture sums before it and the
+// widening of each flux after it use the FP64 pipe.  On GB300 an FP64
+// instruction costs the issue time of ~60 FP32 ones, and the FP64 solver's
+// two square roots, three reciprocals and ~60 further FP64 operations per face
+// were half of the sweeps' FP64 work.  Differences that can cancel (p_R - p_L,
+// s - u) use the exact float-float addition; the error of the flux stays near
+// 2^-44 of its terms, far below the FP64 path's 1e-11 parity requirement.
+template <int NF, int NDIM, int DIR, bool SIX = false>
+__device__ __forceinline__ void hllc_df(const double* L, const double* R, const Mix<double>& mL,
+                                        const Mix<double>& mR, double* F, double& ut,
+                                        const EosR<double>* e6 = nullptr) {
+    using Lay = Layout<NF, NDIM>;
+    constexpr int NS = Lay::NS, IM = Lay::IM, IE = Lay::IE, IA = Lay::IA;
+    const df uL = df_from_double(L[IM + DIR]), uR = df_from_double(R[IM + DIR]);
+    const df pL = df_from_double(L[IE]), pR = df_from_double(R[IE]);
+    const df rL = df_from_double(mL.r), rR = df_from_double(mR.r);
+    // c^2 = n/(Gamma rho)
+    const df cL = df_sqrt(df_div(df_from_double(mL.n), df_mul(df_from_double(mL.G), rL)));
+    const df cR = df_sqrt(df_div(df_from_double(mR.n), df_mul(df_from_double(mR.G), rR)));
+    const df sL = df_min(df_add(uL, df_neg(cL)), df_add(uR, df_neg(cR)));
+    const df sR = df_max(df_add(uL, cL), df_add(uR, cR));
+    const df aL = df_mul(rL, df_add(sL, df_neg(uL))), aR = df_mul(rR, df_add(sR, df_neg(uR)));
+    const df num = df_add(df_add(pR, df_neg(pL)), df_add(df_mul(aL, uL), df_neg(df_mul(aR, uR))));
+    const df sS = df_div(num, df_add(aL, df_neg(aR)));
+    const bool useL = sL.hi >= 0.f || sS.hi >= 0.f;
+    const bool star = useL ? !(sL.hi >= 0.f) : (sR.hi > 0.f);
+    const double* K = useL ? L : R;
+    const df rK = useL ? rL : rR, uK = useL ? uL : uR, pK = useL ? pL : pR, sK = useL ? sL : sR;
+    const double GK = useL ? mL.G : mR.G, PK = useL ? mL.P : mR.P;
+    // xi - 1 = (s* - u_K)/(s_K - s*), exact face velocity u_K at a contact
+    df rr = {0.f, 0.f}, xm1 = {0.f, 0.f}, sKe = {0.f, 0.f};
+    const df dsu = df_add(sS, df_neg(uK));
+    if (star) {
+        rr = df_div({1.f, 0.f}, df_add(sK, df_neg(sS)));
+        xm1 = df_mul(dsu, rr);
+        sKe = sK;
+    }
+    const df xi = df_add_fast({1.f, 0.f}, xm1);
+    const df utd = df_add(uK, df_mul(sKe, xm1));
+    df Kd[NS];
+#pragma unroll
+    for (int v = 0; v < NS; ++v) Kd[v] = df_from_double(K[v]);
+    df u2 = df_mul(Kd[IM], Kd[IM]);
+#pragma unroll
+    for (int dd = 1; dd < NDIM; ++dd) u2 = df_add_fast(u2, df_mul(Kd[IM + dd], Kd[IM + dd]));
+    const df rE = df_add_fast(df_add_fast(df_mul(df_from_double(GK), pK), df_from_double(PK)),
+                              df_mul_pow2(df_mul(rK, u2), 0.5f));
+#pragma unroll
+    for (int k = 0; k < NF; ++k) F[k] = df_to_double(df_mul(Kd[k], utd));
+    const df sKds = df_mul(sKe, dsu);   // s_K (s* - u_K)
+#pragma unroll
+    for (int dd = 0; dd < NDIM; ++dd) {
+        if (dd == DIR)
+            F[IM + dd] = df_to_double(df_add(df_add(df_mul(df_mul(rK, uK), utd), pK), df_mul(df_mul(sKds, xi), rK)));
+        else
+            F[IM + dd] = df_to_double(df_mul(df_mul(rK, Kd[IM + dd]), utd));
+    }
+    F[IE] = df_to_double(df_add(df_add(df_mul(rE, utd), df_mul(pK, uK)),
+                                df_mul(sKds, df_add(df_mul(df_mul(xi, rK), sS), df_mul(pK, rr)))));
+#pragma unroll
+    for (int k = 0; k < NF - 1; ++k) F[IA + k] = df_to_double(df_mul(Kd[IA + k], utd));
+    ut = df_to_double(utd);
+    if constexpr (SIX) {
+        double aN = 1.0;
+        const double pKd = K[IE];
+#pragma unroll
+        for (int k = 0; k < NF - 1; ++k) {
+            aN -= K[IA + k];
+            F[NS + k] = K[IA + k] * fma(e6->G_N + e6->dG[k], pKd, e6->P_N + e6->dP[k]) * ut;
+        }
+        F[NS + NF - 1] = aN * fma(e6->G_N, pKd, e6->P_N) * ut;
+    }
+}
+
 // Count one fallback face per calling lane with one atomic per converged
 // group of lanes (a single global counter takes every fallback of the grid).
 __device__ __forceinline__ void count_fallback(unsigned long long* counter) {
@@ -658,24 +734,22 @@ __device__ __forceinline__ void face_flux(const SweepArgs& a, const EosR<Real>& 
         }
         return;
     }
-    if (!__any_sync(__activemask(), first)) {
-        hllc<Real, NF, NDIM, DIR, SIX>(eLs, eRs, mL, mR, F, ut, &e);
-        return;
-    }
-    // FP64: some lane of the warp falls back; select the states first so
-    // that the warp runs the (costly) solver once rather than once per branch
-    Real sl[NS], sr[NS];
+    if constexpr (sizeof(Real) == 8) {
+        // FP64: select the states first so that the solver (float-float, large)
+        // is inlined once and a warp with falling-back lanes runs it once
+        Real sl[NS], sr[NS];
 #pragma unroll
-    for (int v = 0; v < NS; ++v) {
-        sl[v] = first ? cl[v] : eLs[v];
-        sr[v] = first ? cr[v] : eRs[v];
+        for (int v = 0; v < NS; ++v) {
+            sl[v] = first ? cl[v] : eLs[v];
+            sr[v] = first ? cr[v] : eRs[v];
+        }
+        if (first) {
+            count_fallback(a.fallback_count);
+            mL = mixture<Real, NF, NDIM, SIX>(sl, e);
+            mR = mixture<Real, NF, NDIM, SIX>(sr, e);
+        }
+        hllc_df<NF, NDIM, DIR, SIX>(sl, sr, mL, mR, F, ut, &e);
     }
-    if (first) {
-        count_fallback(a.fallback_count);
-        mL = mixture<Real, NF, NDIM, SIX>(sl, e);
-        mR = mixture<Real, NF, NDIM, SIX>(sr, e);
-    }
-    hllc<Real, NF, NDIM, DIR, SIX>(sl, sr, mL, mR, F, ut, &e);
 }
 
 // ---------------------------------------------------------------------------

@@ -93,6 +93,22 @@ __device__ __forceinline__ df df_div(df a, df b) {
     return df_fast_two_sum(q1, __fmul_rn(r.hi, y));
 }
 
+// sqrt(x) for x > 0: the correctly rounded FP32 root s of x.hi, then one
+// Newton correction on the exact residual, sqrt(x) = s + (x - s^2)/(2 s)
+// (Dekker 1971; Hida, Li and Bailey's double-double sqrt); ~2^-46 relative.
+// x <= 0 gives 0.
+__device__ __forceinline__ df df_sqrt(df x) {
+    if (!(x.hi > 0.f)) return {0.f, 0.f};
+    const float s = __fsqrt_rn(x.hi);
+    const df r = df_add(x, df_neg(df_two_prod(s, s)));
+    return df_fast_two_sum(s, __fmul_rn(r.hi, __fmul_rn(0.5f, __frcp_rn(s))));
+}
+
+// x < y (parts normalised: |lo| <= ulp(hi)/2).
+__device__ __forceinline__ bool df_lt(df x, df y) { return x.hi < y.hi || (x.hi == y.hi && x.lo < y.lo); }
+__device__ __forceinline__ df df_min(df x, df y) { return df_lt(y, x) ? y : x; }
+__device__ __forceinline__ df df_max(df x, df y) { return df_lt(x, y) ? y : x; }
+
 // FP64 -> float-float by integer operations on the bit pattern (FP64<->FP32
 // conversion instructions run on the FP64 pipe, the scarce one on GB300): hi
 // takes the sign, the rebiased exponent and the top 23 stored significand bits
