@@ -1549,7 +1549,7 @@ __global__ void __launch_bounds__(128) sweep_kernel(const SweepArgs a) {
 constexpr int kStreamThreads = 128;
 
 template <typename Real, int NF, int NDIM, bool LEARNED = false, int ORDER = 5, bool NONUNIF = false, bool SIX = false>
-__global__ void __launch_bounds__(kStreamThreads) sweep_x_stream_kernel(const SweepArgs a) {
+__device__ __forceinline__ void sweep_x_stream_body(const SweepArgs& a) {
     static_assert(!SIX || !LEARNED, "six-equation model: FP64 and mixed forms");
     static_assert(!NONUNIF || (!LEARNED && ORDER == 5), "non-uniform grids: WENO5, FP64 and mixed forms");
     static_assert(!LEARNED || sizeof(Real) == 4, "the learned form runs in FP32");
@@ -1736,6 +1736,18 @@ __global__ void __launch_bounds__(kStreamThreads) sweep_x_stream_kernel(const Sw
     if constexpr (LEARNED) {
         if ((threadIdx.x & 31) == 0 && net_rows && a.net_rows) atomicAdd(a.net_rows, net_rows);
     }
+}
+
+template <typename Real, int NF, int NDIM, bool LEARNED = false, int ORDER = 5, bool NONUNIF = false, bool SIX = false>
+__global__ void __launch_bounds__(kStreamThreads) sweep_x_stream_kernel(const SweepArgs a) {
+    sweep_x_stream_body<Real, NF, NDIM, LEARNED, ORDER, NONUNIF, SIX>(a);
+}
+
+// FP64 sweeps bounded to 4 CTAs (16 warps) per SM, for the variants where
+// the extra warps outweigh the spills (launch_sweep chooses).
+template <int NF, int NDIM, int ORDER = 5, bool NONUNIF = false, bool SIX = false>
+__global__ void __launch_bounds__(kStreamThreads, 4) sweep_x_stream_f64_kernel(const SweepArgs a) {
+    sweep_x_stream_body<double, NF, NDIM, false, ORDER, NONUNIF, SIX>(a);
 }
 
 // ---------------------------------------------------------------------------
@@ -1944,6 +1956,11 @@ __global__ void __launch_bounds__(32 * kRowsPerChunk) sweep_yz_stream_kernel(con
 template <int NF, int NDIM, int DIR, int ORDER = 5, bool NONUNIF = false>
 __global__ void __launch_bounds__(32 * kRowsPerChunk, 5) sweep_yz_stream_six32_kernel(const SweepArgs a) {
     sweep_yz_stream_body<float, NF, NDIM, DIR, false, ORDER, NONUNIF, true>(a);
+}
+
+template <int NF, int NDIM, int DIR, int ORDER = 5, bool NONUNIF = false, bool SIX = false>
+__global__ void __launch_bounds__(32 * kRowsPerChunk, 4) sweep_yz_stream_f64_kernel(const SweepArgs a) {
+    sweep_yz_stream_body<double, NF, NDIM, DIR, false, ORDER, NONUNIF, SIX>(a);
 }
 
 template <int NF, int NDIM, int DIR>

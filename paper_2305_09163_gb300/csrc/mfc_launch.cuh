@@ -16,15 +16,29 @@ constexpr long long kStreamSlotsPerBlock = 16LL * kStreamThreads;
 // SIX: the six-equation model (stream kernels, WENO5, uniform grids).
 template <typename Real, int NF, bool LEARNED = false, int ORDER = 5, bool NONUNIF = false, bool SIX = false>
 cudaError_t launch_sweep(SweepArgs a, int ndim, int dir, cudaStream_t s) {
+    // FP64 sweeps bounded to 4 CTAs per SM (128 registers, small spills):
+    // faster for the stretched-grid (83.7 -> 71.1 ms per step at 256^3),
+    // six-equation (83.4 -> 80.7) and WENO3 (42.1 -> 41.5) variants, slower
+    // for the uniform WENO5 ones (61.0 -> 63.8, Kapila 65.3 -> 67.2)
+    constexpr bool kBoundFp64 = NONUNIF || SIX || ORDER == 3;
     if (dir == 0) {
         const long long total = (long long)(a.g.n[0] + 2) * (a.g.ncell / a.g.n[0]);
         a.slots_per_block = kStreamSlotsPerBlock;
         const unsigned blocks = (unsigned)((total + kStreamSlotsPerBlock - 1) / kStreamSlotsPerBlock);
-        switch (ndim) {
-            case 1: sweep_x_stream_kernel<Real, NF, 1, LEARNED, ORDER, NONUNIF, SIX><<<blocks, kStreamThreads, 0, s>>>(a); break;
-            case 2: sweep_x_stream_kernel<Real, NF, 2, LEARNED, ORDER, NONUNIF, SIX><<<blocks, kStreamThreads, 0, s>>>(a); break;
-            case 3: sweep_x_stream_kernel<Real, NF, 3, LEARNED, ORDER, NONUNIF, SIX><<<blocks, kStreamThreads, 0, s>>>(a); break;
-            default: return cudaErrorInvalidValue;
+        if constexpr (sizeof(Real) == 8 && kBoundFp64) {
+            switch (ndim) {
+                case 1: sweep_x_stream_f64_kernel<NF, 1, ORDER, NONUNIF, SIX><<<blocks, kStreamThreads, 0, s>>>(a); break;
+                case 2: sweep_x_stream_f64_kernel<NF, 2, ORDER, NONUNIF, SIX><<<blocks, kStreamThreads, 0, s>>>(a); break;
+                case 3: sweep_x_stream_f64_kernel<NF, 3, ORDER, NONUNIF, SIX><<<blocks, kStreamThreads, 0, s>>>(a); break;
+                default: return cudaErrorInvalidValue;
+            }
+        } else {
+            switch (ndim) {
+                case 1: sweep_x_stream_kernel<Real, NF, 1, LEARNED, ORDER, NONUNIF, SIX><<<blocks, kStreamThreads, 0, s>>>(a); break;
+                case 2: sweep_x_stream_kernel<Real, NF, 2, LEARNED, ORDER, NONUNIF, SIX><<<blocks, kStreamThreads, 0, s>>>(a); break;
+                case 3: sweep_x_stream_kernel<Real, NF, 3, LEARNED, ORDER, NONUNIF, SIX><<<blocks, kStreamThreads, 0, s>>>(a); break;
+                default: return cudaErrorInvalidValue;
+            }
         }
         return cudaGetLastError();
     }
@@ -37,6 +51,13 @@ cudaError_t launch_sweep(SweepArgs a, int ndim, int dir, cudaStream_t s) {
                 case 9: sweep_yz_stream_learned_kernel<NF, 2, 1><<<blocks, 32 * kRowsPerChunk, 0, s>>>(a); break;
                 case 13: sweep_yz_stream_learned_kernel<NF, 3, 1><<<blocks, 32 * kRowsPerChunk, 0, s>>>(a); break;
                 case 14: sweep_yz_stream_learned_kernel<NF, 3, 2><<<blocks, 32 * kRowsPerChunk, 0, s>>>(a); break;
+                default: return cudaErrorInvalidValue;
+            }
+        } else if constexpr (sizeof(Real) == 8 && kBoundFp64) {
+            switch (ndim * 4 + dir) {
+                case 9: sweep_yz_stream_f64_kernel<NF, 2, 1, ORDER, NONUNIF, SIX><<<blocks, 32 * kRowsPerChunk, 0, s>>>(a); break;
+                case 13: sweep_yz_stream_f64_kernel<NF, 3, 1, ORDER, NONUNIF, SIX><<<blocks, 32 * kRowsPerChunk, 0, s>>>(a); break;
+                case 14: sweep_yz_stream_f64_kernel<NF, 3, 2, ORDER, NONUNIF, SIX><<<blocks, 32 * kRowsPerChunk, 0, s>>>(a); break;
                 default: return cudaErrorInvalidValue;
             }
         } else if constexpr (SIX && sizeof(Real) == 4) {
