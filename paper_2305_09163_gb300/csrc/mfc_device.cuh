@@ -2015,45 +2015,50 @@ __device__ __forceinline__ void prims_cell(const double* q, const EosConst& e, d
     }
 }
 
+// FP32 form: the per-cell FP64 -> FP32 conversions by integer operations
+// (narrow_rn, df_widen), since conversion instructions run on the FP64 pipe.
 template <int NF, int NDIM, bool SIX = false>
 __device__ __forceinline__ void prims_cell(const double* q, const EosConst& e, float* wv, float& c2) {
     using Lay = Layout<NF, NDIM>;
     constexpr int IM = Lay::IM, IE = Lay::IE, IA = Lay::IA;
-    float rho = (float)q[0];
+    float qf[Lay::NS];
 #pragma unroll
-    for (int k = 1; k < NF; ++k) rho += (float)q[k];
+    for (int v = 0; v < Lay::NS; ++v) qf[v] = v == IE ? 0.f : narrow_rn(q[v]);
+    float rho = qf[0];
+#pragma unroll
+    for (int k = 1; k < NF; ++k) rho += qf[k];
     float G = (float)e.G_N;
     double P = e.P_N;
 #pragma unroll
     for (int k = 0; k < NF - 1; ++k) {
-        G = fmaf((float)q[IA + k], (float)e.dG[k], G);
+        G = fmaf(qf[IA + k], (float)e.dG[k], G);
         P = fma(q[IA + k], e.dP[k], P);
     }
     const float irho = __fdividef(1.0f, rho);
     float ke = 0.f;
 #pragma unroll
     for (int d = 0; d < NDIM; ++d) {
-        const float m = (float)q[IM + d];
+        const float m = qf[IM + d];
         wv[IM + d] = m * irho;
         ke = fmaf(m, wv[IM + d], ke);
     }
-    const double eint = fma(-0.5, (double)ke, q[IE] - P);
-    const float p = __fdividef((float)eint, G);
+    const double eint = fma(-0.5, df_widen(ke), q[IE] - P);
+    const float p = __fdividef(narrow_rn(eint), G);
 #pragma unroll
-    for (int k = 0; k < NF; ++k) wv[k] = (float)q[k];
+    for (int k = 0; k < NF; ++k) wv[k] = qf[k];
     wv[IE] = p;
 #pragma unroll
-    for (int k = 0; k < NF - 1; ++k) wv[IA + k] = (float)q[IA + k];
+    for (int k = 0; k < NF - 1; ++k) wv[IA + k] = qf[IA + k];
     if constexpr (SIX) {
         float A = (float)e.A_N, B = (float)e.B_N;
 #pragma unroll
         for (int k = 0; k < NF - 1; ++k) {
-            A = fmaf((float)q[IA + k], (float)e.dA[k], A);
-            B = fmaf((float)q[IA + k], (float)e.dB[k], B);
+            A = fmaf(qf[IA + k], (float)e.dA[k], A);
+            B = fmaf(qf[IA + k], (float)e.dB[k], B);
         }
         c2 = __fdividef(fmaf(A, p, B), rho);
     } else {
-        c2 = __fdividef(fmaf(G + 1.0f, p, (float)P), G * rho);
+        c2 = __fdividef(fmaf(G + 1.0f, p, narrow_rn(P)), G * rho);
     }
 }
 

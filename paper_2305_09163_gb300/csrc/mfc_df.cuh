@@ -137,4 +137,21 @@ __device__ __forceinline__ double df_widen(float f) {
 
 __device__ __forceinline__ double df_to_double(df x) { return df_widen(x.hi) + df_widen(x.lo); }
 
+// FP64 -> FP32 rounded to nearest (ties to even) by integer operations on the
+// bit pattern: the same result as the conversion instruction for every value
+// in the normal FP32 range; |d| < 2^-126 gives a signed zero and |d| >= 2^128
+// (after rounding) infinity.
+__device__ __forceinline__ float narrow_rn(double d) {
+    const unsigned hw = (unsigned)__double2hiint(d), lw = (unsigned)__double2loint(d);
+    const unsigned sign = hw & 0x80000000u;
+    const int e = (int)((hw >> 20) & 0x7FFu) - 1023 + 127;
+    if (e <= 0) return __int_as_float((int)sign);
+    if (e >= 255) return __int_as_float((int)(sign | 0x7F800000u));
+    const unsigned m23 = ((hw & 0xFFFFFu) << 3) | (lw >> 29);   // top 23 stored bits
+    const unsigned rem = lw & 0x1FFFFFFFu;                       // the 29 bits below
+    const unsigned up = (rem > 0x10000000u || (rem == 0x10000000u && (m23 & 1u))) ? 1u : 0u;
+    // a carry out of the significand moves into the exponent, as rounding does
+    return __int_as_float((int)(sign | (((unsigned)e << 23) + m23 + up)));
+}
+
 }  // namespace mfc

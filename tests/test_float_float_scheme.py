@@ -181,3 +181,38 @@ def test_float_float_weno5_matches_the_oracle(kind):
     scale = np.abs(v).max(axis=1)
     assert np.all(np.abs(eL - rL) <= 1e-13 * scale)
     assert np.all(np.abs(eR - rR) <= 1e-13 * scale)
+
+
+def narrow(d):
+    """FP64 -> FP32 round-to-nearest-even by integer operations on the bit
+    pattern, as the FP32 primitive recovery does (normal FP32 range)."""
+    u = np.asarray(d, dtype=np.float64).view(np.uint64)
+    hw = (u >> np.uint64(32)).astype(np.uint64)
+    lw = (u & np.uint64(0xFFFFFFFF)).astype(np.uint64)
+    sign = hw & np.uint64(0x80000000)
+    e = ((hw >> np.uint64(20)) & np.uint64(0x7FF)).astype(np.int64) - 1023 + 127
+    m23 = ((hw & np.uint64(0xFFFFF)) << np.uint64(3)) | (lw >> np.uint64(29))
+    rem = lw & np.uint64(0x1FFFFFFF)
+    half = np.uint64(0x10000000)
+    up = ((rem > half) | ((rem == half) & ((m23 & np.uint64(1)) == 1))).astype(np.uint64)
+    bits = sign | ((np.clip(e, 0, 255).astype(np.uint64) << np.uint64(23)) + m23 + up)
+    out = (bits & np.uint64(0xFFFFFFFF)).astype(np.uint32).view(np.float32)
+    out = np.where(e <= 0, np.where(sign > 0, np.float32(-0.0), np.float32(0.0)), out)
+    return np.where(e >= 255, np.where(sign > 0, -np.inf, np.inf).astype(np.float32), out)
+
+
+def test_integer_narrowing_rounds_to_nearest_even():
+    """Equal to IEEE conversion (numpy) for every double whose result is a
+    normal float, ties and carries into the exponent included."""
+    rng = np.random.default_rng(3)
+    d = rng.standard_normal(1_000_000) * 10.0 ** rng.uniform(-37, 38, 1_000_000)
+    f = d.astype(np.float32)
+    keep = np.isfinite(f) & (np.abs(f) >= np.float32(2.0 ** -126))
+    assert np.array_equal(narrow(d[keep]), f[keep])
+    # exact ties: a float plus half an FP32 ulp rounds to the even neighbour
+    x = rng.uniform(1, 2, 10000).astype(np.float32).astype(np.float64)
+    tie = x + 2.0 ** -24
+    assert np.array_equal(narrow(tie), tie.astype(np.float32))
+    # the largest significand rounds up into the next binade
+    y = np.nextafter(np.float64(2.0), 0.0)
+    assert narrow(np.array([y]))[0] == np.float32(2.0)
