@@ -1743,6 +1743,13 @@ __global__ void __launch_bounds__(kStreamThreads) sweep_x_stream_kernel(const Sw
     sweep_x_stream_body<Real, NF, NDIM, LEARNED, ORDER, NONUNIF, SIX>(a);
 }
 
+// The learned form's x sweep bounded to 4 CTAs per SM (128 registers, 32
+// bytes of spills; unbounded it took 168 and kept 12 warps per SM).
+template <int NF, int NDIM>
+__global__ void __launch_bounds__(kStreamThreads, 4) sweep_x_stream_learned_kernel(const SweepArgs a) {
+    sweep_x_stream_body<float, NF, NDIM, true, 5, false, false>(a);
+}
+
 // FP64 sweeps bounded to 4 CTAs (16 warps) per SM, for the variants where
 // the extra warps outweigh the spills (launch_sweep chooses).
 template <int NF, int NDIM, int ORDER = 5, bool NONUNIF = false, bool SIX = false>

@@ -25,7 +25,14 @@ cudaError_t launch_sweep(SweepArgs a, int ndim, int dir, cudaStream_t s) {
         const long long total = (long long)(a.g.n[0] + 2) * (a.g.ncell / a.g.n[0]);
         a.slots_per_block = kStreamSlotsPerBlock;
         const unsigned blocks = (unsigned)((total + kStreamSlotsPerBlock - 1) / kStreamSlotsPerBlock);
-        if constexpr (sizeof(Real) == 8 && kBoundFp64) {
+        if constexpr (LEARNED) {
+            switch (ndim) {
+                case 1: sweep_x_stream_learned_kernel<NF, 1><<<blocks, kStreamThreads, 0, s>>>(a); break;
+                case 2: sweep_x_stream_learned_kernel<NF, 2><<<blocks, kStreamThreads, 0, s>>>(a); break;
+                case 3: sweep_x_stream_learned_kernel<NF, 3><<<blocks, kStreamThreads, 0, s>>>(a); break;
+                default: return cudaErrorInvalidValue;
+            }
+        } else if constexpr (sizeof(Real) == 8 && kBoundFp64) {
             switch (ndim) {
                 case 1: sweep_x_stream_f64_kernel<NF, 1, ORDER, NONUNIF, SIX><<<blocks, kStreamThreads, 0, s>>>(a); break;
                 case 2: sweep_x_stream_f64_kernel<NF, 2, ORDER, NONUNIF, SIX><<<blocks, kStreamThreads, 0, s>>>(a); break;
