@@ -1,0 +1,72 @@
+"""Parity at the bench's full size for every FP64 form it times besides the
+headline (which test_gpu_parity covers): the 256^3 shock-bubble workloads in
+the bench's launch configuration, the whole right-hand side on the GPU, the
+oracle at sampled cells (random cells, domain faces and edges, the shock front,
+the bubble interface).  The same FP64 gate as everywhere else."""
+import numpy as np
+import pytest
+
+import oracle
+import workloads
+from parity_util import sampled_rhs_error
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+TOL_FP64 = 1e-11
+N = 256
+
+# form: (workload builder, solver parameters, oracle options, six-equation state)
+FORMS = {
+    "fp64_weno3": (workloads.shock_bubble, {"weno_order": 3}, {"weno_order": 3}, False),
+    "fp64_kapila": (workloads.shock_bubble, {"model": 1}, {"model": "kapila"}, False),
+    "fp64_stretched": (workloads.shock_bubble_stretched, {}, {}, False),
+    "fp64_cbc": (workloads.shock_bubble_cbc, {}, {}, False),
+    "fp64_six": (workloads.shock_bubble, {"model": 2}, {"model": "six"}, True),
+}
+
+
+@pytest.fixture(scope="module")
+def mfc():
+    import paper_2305_09163_gb300 as m
+    m.build()
+    m.load()
+    return m
+
+
+def _cells(pb, shock_x):
+    rng = np.random.default_rng(13)
+    n = N
+    pick = [rng.integers(0, pb.ncell, 1200)]
+    for (x, y, z) in [(0, 0, 0), (n - 1, n - 1, n - 1), (0, 128, 128), (n - 1, 128, 128), (128, 0, 128),
+                      (128, n - 1, 128), (128, 128, 0), (128, 128, n - 1), (128, 128, 128 + 25),
+                      (128 + 26, 128, 128), (128, 102, 128)]:
+        pick.append(np.array([(z * n + y) * n + x]))
+    xs = rng.integers(max(0, shock_x - 5), shock_x + 6, 300)
+    ys = rng.integers(0, n, 300)
+    zs = rng.integers(0, n, 300)
+    pick.append((zs * n + ys) * n + xs)
+    return np.unique(np.concatenate(pick))
+
+
+@pytest.mark.parametrize("form", list(FORMS))
+def test_full_size_sampled_parity_of_each_form(mfc, form):
+    build, params, opts, six = FORMS[form]
+    wl = build(N)
+    pb = oracle.Problem(wl.n, wl.lo, wl.hi, wl.bc, wl.gamma, wl.pi_inf, fallback=True, faces=wl.faces, **opts)
+    w = wl.prims()
+    if six:
+        w = workloads.six_equation_prims(w, wl.nf)
+    q = oracle.cons_from_prims(pb, w)
+    s = mfc.Solver(wl.n, wl.lo, wl.hi, wl.bc, wl.gamma, wl.pi_inf, precision="fp64", fallback=1, **params)
+    if wl.faces is not None:
+        for d in range(3):
+            s.set_grid(d, wl.faces[d])
+    s.set_state_prim(torch.from_numpy(w).cuda())
+    R = s.rhs().cpu().numpy().reshape(pb.sys_size, -1)
+    # the shock front: the first x cell whose centre lies beyond 0.05
+    centers = 0.5 * (wl.faces[0][1:] + wl.faces[0][:-1]) if wl.faces is not None else (np.arange(N) + 0.5) / N
+    cells = _cells(pb, int(np.searchsorted(centers, 0.05)))
+    Rc, fmax = oracle.rhs_cells(pb, q, cells, return_fmax=True)
+    err = sampled_rhs_error(pb, q, R, cells, Rc, fmax)
+    assert err.max() <= TOL_FP64, (form, err)
