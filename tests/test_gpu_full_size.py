@@ -1,8 +1,10 @@
-"""Parity at the bench's full size for every FP64 form it times besides the
-headline (which test_gpu_parity covers): the 256^3 shock-bubble workloads in
-the bench's launch configuration, the whole right-hand side on the GPU, the
-oracle at sampled cells (random cells, domain faces and edges, the shock front,
-the bubble interface).  The same FP64 gate as everywhere else."""
+"""Parity at full size: every FP64 form the bench times besides the headline
+(which test_gpu_parity covers) on the 256^3 shock-bubble workloads in the
+bench's launch configuration, and the FP64 and mixed forms on the 384^3 bubble
+cloud and the 512^3 three-fluid workload.  The whole right-hand side runs on
+the GPU; the oracle evaluates sampled cells (random cells, domain faces and
+edges, the shock front, the interfaces).  The FP64 gate, and the mixed gate for
+the mixed form."""
 import numpy as np
 import pytest
 
@@ -70,3 +72,45 @@ def test_full_size_sampled_parity_of_each_form(mfc, form):
     Rc, fmax = oracle.rhs_cells(pb, q, cells, return_fmax=True)
     err = sampled_rhs_error(pb, q, R, cells, Rc, fmax)
     assert err.max() <= TOL_FP64, (form, err)
+
+
+def _sampled_check(mfc, wl, precision, tol, seed):
+    pb = oracle.Problem(wl.n, wl.lo, wl.hi, wl.bc, wl.gamma, wl.pi_inf, fallback=True)
+    w = wl.prims()
+    q = oracle.cons_from_prims(pb, w)
+    s = mfc.Solver(wl.n, wl.lo, wl.hi, wl.bc, wl.gamma, wl.pi_inf, precision=precision, fallback=1)
+    s.set_state_prim(torch.from_numpy(w).cuda())
+    R = s.rhs().cpu().numpy().reshape(pb.sys_size, -1)
+    del s
+    torch.cuda.empty_cache()
+    n = wl.n[0]
+    rng = np.random.default_rng(seed)
+    # random cells, the domain's corners, and cells near the shock front (x < 0.05)
+    pick = [rng.integers(0, pb.ncell, 1500), np.array([0, pb.ncell - 1, n - 1, pb.ncell - n])]
+    xs = rng.integers(0, int(0.05 * n) + 6, 400)
+    ys = rng.integers(0, n, 400)
+    zs = rng.integers(0, n, 400)
+    pick.append((zs * n + ys) * n + xs)
+    # cells where the volume fractions vary (bubble interfaces, the solid slab's faces)
+    a = w[pb.nf + pb.ndim + 1].reshape(-1)
+    inter = np.flatnonzero((a > 0.01) & (a < 0.99))
+    if inter.size:
+        pick.append(rng.choice(inter, min(400, inter.size), replace=False))
+    cells = np.unique(np.concatenate(pick))
+    Rc, fmax = oracle.rhs_cells(pb, q, cells, return_fmax=True)
+    err = sampled_rhs_error(pb, q, R, cells, Rc, fmax)
+    assert err.max() <= tol, (wl.name, precision, err)
+
+
+@pytest.mark.parametrize("precision,tol", [("fp64", TOL_FP64), ("mixed", 2e-4)])
+def test_full_size_bubble_cloud(mfc, precision, tol):
+    """The 384^3 shock-bubble-cloud workload (64 air bubbles with lognormal
+    radii in water, planar shock)."""
+    _sampled_check(mfc, workloads.bubble_cloud(384), precision, tol, 17)
+
+
+@pytest.mark.parametrize("precision,tol", [("fp64", TOL_FP64), ("mixed", 2e-4)])
+def test_full_size_three_fluid(mfc, precision, tol):
+    """The 512^3 three-fluid workload (water, an air bubble cloud and a stiff
+    solid slab; ~10 GB per state array)."""
+    _sampled_check(mfc, workloads.three_fluid(512), precision, tol, 19)
