@@ -644,8 +644,8 @@ __device__ __forceinline__ void hllc_df(const double* L, const double* R, const 
     // c^2 = n/(Gamma rho)
     const df cL = df_sqrt(df_div(df_from_double(mL.n), df_mul(df_from_double(mL.G), rL)));
     const df cR = df_sqrt(df_div(df_from_double(mR.n), df_mul(df_from_double(mR.G), rR)));
-    const df sL = df_min(df_add(uL, df_neg(cL)), df_add(uR, df_neg(cR)));
-    const df sR = df_max(df_add(uL, cL), df_add(uR, cR));
+    const df sL = df_min(df_add_fast(uL, df_neg(cL)), df_add_fast(uR, df_neg(cR)));
+    const df sR = df_max(df_add_fast(uL, cL), df_add_fast(uR, cR));
     const df aL = df_mul(rL, df_add(sL, df_neg(uL))), aR = df_mul(rR, df_add(sR, df_neg(uR)));
     const df num = df_add(df_add(pR, df_neg(pL)), df_add(df_mul(aL, uL), df_neg(df_mul(aR, uR))));
     const df sS = df_div(num, df_add(aL, df_neg(aR)));
@@ -663,7 +663,7 @@ __device__ __forceinline__ void hllc_df(const double* L, const double* R, const 
         sKe = sK;
     }
     const df xi = df_add_fast({1.f, 0.f}, xm1);
-    const df utd = df_add(uK, df_mul(sKe, xm1));
+    const df utd = df_add_fast(uK, df_mul(sKe, xm1));
     df Kd[NS];
 #pragma unroll
     for (int v = 0; v < NS; ++v) Kd[v] = df_from_double(K[v]);
@@ -678,12 +678,12 @@ __device__ __forceinline__ void hllc_df(const double* L, const double* R, const 
 #pragma unroll
     for (int dd = 0; dd < NDIM; ++dd) {
         if (dd == DIR)
-            F[IM + dd] = df_to_double(df_add(df_add(df_mul(df_mul(rK, uK), utd), pK), df_mul(df_mul(sKds, xi), rK)));
+            F[IM + dd] = df_to_double(df_add_fast(df_add_fast(df_mul(df_mul(rK, uK), utd), pK), df_mul(df_mul(sKds, xi), rK)));
         else
             F[IM + dd] = df_to_double(df_mul(df_mul(rK, Kd[IM + dd]), utd));
     }
-    F[IE] = df_to_double(df_add(df_add(df_mul(rE, utd), df_mul(pK, uK)),
-                                df_mul(sKds, df_add(df_mul(df_mul(xi, rK), sS), df_mul(pK, rr)))));
+    F[IE] = df_to_double(df_add_fast(df_add_fast(df_mul(rE, utd), df_mul(pK, uK)),
+                                     df_mul(sKds, df_add_fast(df_mul(df_mul(xi, rK), sS), df_mul(pK, rr)))));
 #pragma unroll
     for (int k = 0; k < NF - 1; ++k) F[IA + k] = df_to_double(df_mul(Kd[IA + k], utd));
     ut = df_to_double(utd);
