@@ -1998,7 +1998,7 @@ __device__ __forceinline__ void prims_cell(const double* q, const EosConst& e, d
         G = fma(q[IA + k], e.dG[k], G);
         P = fma(q[IA + k], e.dP[k], P);
     }
-    const double x = 1.0 / (rho * G);
+    const double x = rcp_nr(rho * G);   // FP32 seed + cubic Newton step: 3 FP64 instructions
     const double irho = G * x, iG = rho * x;
     double ke = 0.0;
 #pragma unroll
@@ -2094,7 +2094,10 @@ __global__ void __launch_bounds__(256) prims_kernel(const PrimArgs a) {
             if (!(c2 > (Real)0) || !(c2 - c2 == (Real)0) || !(us - us == (Real)0)) {
                 bad += 1;
             } else {
-                const Real cs = real_sqrt(c2);
+                // FP64: the root in float-float (~2^-46 relative), off the FP64 pipe
+                Real cs;
+                if constexpr (sizeof(Real) == 8) cs = df_to_double(df_sqrt(df_from_double(c2)));
+                else cs = real_sqrt(c2);
                 Real r = 0;
                 int ci[3] = {0, 0, 0};
                 if (a.grid[0] || a.grid[1] || a.grid[2]) {   // non-uniform: this cell's widths
