@@ -1,0 +1,582 @@
+// The directional sweeps: pencil-marching y/z kernel, x stream kernel, y/z
+// stream kernels, and their bounded entries.
+#pragma once
+#include "mfc_cell.cuh"
+
+namespace mfc {
+
+// ---------------------------------------------------------------------------
+// Directional sweep for y and z.  One thread marches along one pencil segment
+// of `seg` cells in direction DIR: it reconstructs the edges of cells
+// s0-1..s1, forms faces s0-1/2..s1-1/2 and finishes cells s0..s1-1.  A warp
+// covers 32 consecutive x of one segment (lanes past the end of a row work on
+// a clamped copy and store nothing), so loads and stores are coalesced and all
+// lanes of a warp run the same number of iterations, which the tensor-core
+// network of the learned form (LEARNED) requires.
+// ---------------------------------------------------------------------------
+template <typename Real, int NF, int NDIM, int DIR, bool LEARNED = false, int ORDER = 5>
+__global__ void __launch_bounds__(128) sweep_kernel(const SweepArgs a) {
+    static_assert(!LEARNED || sizeof(Real) == 4, "the learned form runs in FP32");
+    static_assert(!LEARNED || ORDER == 5, "the learned form replaces the WENO5 weights");
+    using Lay = Layout<NF, NDIM>;
+    constexpr int NS = Lay::NS, IM = Lay::IM;
+    constexpr int T1 = (DIR == 0) ? 1 : 0;
+    constexpr int T2 = (DIR == 2) ? 1 : 2;
+    const Real* __restrict__ w = static_cast<const Real*>(a.w);
+    const int lane = threadIdx.x & 31;
+    const long long wid = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int n1 = a.g.n[T1], n2 = a.g.n[T2], nd = a.g.n[DIR];
+    const int nxc = (n1 + 31) >> 5;
+    if (wid >= (long long)nxc * a.nseg * n2) return;  // whole warps only
+    const int xc = (int)(wid % nxc);
+    const long long rest = wid / nxc;
+    const int sg = (int)(rest % a.nseg);
+    const int t2 = (int)(rest / a.nseg);
+    const bool active = xc * 32 + lane < n1;
+    if (!LEARNED && !active) return;
+    const int t1 = active ? xc * 32 + lane : n1 - 1;
+    const long long sd = stride_of(a.g, DIR);
+    const long long base = (long long)t1 * stride_of(a.g, T1) + (long long)t2 * stride_of(a.g, T2);
+    const long long nc = a.g.ncell;
+    const int s0 = sg * a.seg;
+    const int s1 = min(s0 + a.seg, nd);
+    const int bclo = a.g.bc_lo[DIR], bchi = a.g.bc_hi[DIR];
+    const Real eps34 = sweep_epsw<Real, ORDER>(a);  // 3/4 eps (WENO5) or eps (WENO3)
+    const EosR<Real> e = sweep_eos<Real>(a);
+    const Real inv_dx = sweep_inv_dx<Real>(a, DIR);
+    LearnSmem<NS>* lsm = nullptr;
+    if constexpr (LEARNED) {
+        __shared__ LearnSmem<NS> lbuf[4];
+        lsm = &lbuf[threadIdx.x >> 5];
+    }
+    unsigned long long net_rows = 0;  // learned form: network rows of this warp
+
+    auto load = [&](int i, Real* out) {
+        bool flip = false;
+        const int m = ghost_map(i, nd, bclo, bchi, &flip);
+        const long long idx = base + (long long)m * sd;
+#pragma unroll
+        for (int v = 0; v < NS; ++v) out[v] = __ldg(w + v * nc + idx);
+        if (flip) out[IM + DIR] = -out[IM + DIR];
+    };
+
+    // Window around the cell c being reconstructed: vc = c, vp1 = c+1,
+    // vp2 = c+2, the four differences across c-2..c+2, and cm1 = c-1.
+    Real vc[NS], vp1[NS], vp2[NS], D[NS][4], cm1[NS];
+    {
+        Real t[NS];
+        load(s0 - 3, t);
+        load(s0 - 2, cm1);
+        load(s0 - 1, vc);
+        load(s0, vp1);
+        load(s0 + 1, vp2);
+#pragma unroll
+        for (int v = 0; v < NS; ++v) {
+            D[v][0] = cm1[v] - t[v];
+            D[v][1] = vc[v] - cm1[v];
+            D[v][2] = vp1[v] - vc[v];
+            D[v][3] = vp2[v] - vp1[v];
+        }
+    }
+    Real eLprev[NS], eLprevJ[NS], Fprev[NS], utprev = 0;
+#pragma unroll
+    for (int v = 0; v < NS; ++v) { eLprev[v] = 0; eLprevJ[v] = 0; Fprev[v] = 0; }
+
+    for (int c = s0 - 1; c <= s1; ++c) {
+        Real eR[NS], eL[NS], eRJ[NS], eLJ[NS];
+        if constexpr (LEARNED) {
+            auto stencil = [&](int v, float (&dd)[4]) -> float {
+                dd[0] = D[v][0];
+                dd[1] = D[v][1];
+                dd[2] = D[v][2];
+                dd[3] = D[v][3];
+                return vc[v];
+            };
+            net_rows += learned_cell_edges<NS>(stencil, eps34, a.tau, a.bound != 0, a.mlp_frag, *lsm, lane, eRJ, eLJ, eR,
+                                                  eL);
+        } else {
+#pragma unroll
+            for (int v = 0; v < NS; ++v) weno_edges<ORDER>(vc[v], D[v], eps34, eR[v], eL[v]);
+        }
+        if (c >= s0) {
+            Real F[NS], ut;
+            if constexpr (LEARNED)
+                face_flux_learned<NF, NDIM, DIR>(a, e, eLprev, eR, eLprevJ, eRJ, cm1, vc, F, ut);
+            else
+                face_flux<Real, NF, NDIM, DIR>(a, e, eLprev, eR, cm1, vc, F, ut);
+            if (c >= s0 + 1 && active)
+                finish_cell<Real, NF, NDIM, DIR>(a, base + (long long)(c - 1) * sd, Fprev, F, utprev, ut, cm1, inv_dx,
+                                                 c - 1, sd);
+#pragma unroll
+            for (int v = 0; v < NS; ++v) Fprev[v] = F[v];
+            utprev = ut;
+        }
+        // advance the window by one cell
+#pragma unroll
+        for (int v = 0; v < NS; ++v) {
+            eLprev[v] = eL[v];
+            if constexpr (LEARNED) eLprevJ[v] = eLJ[v];
+            cm1[v] = vc[v];
+        }
+        if (c < s1) {
+            Real nw[NS];
+            load(c + 3, nw);
+#pragma unroll
+            for (int v = 0; v < NS; ++v) {
+                D[v][0] = D[v][1];
+                D[v][1] = D[v][2];
+                D[v][2] = D[v][3];
+                D[v][3] = nw[v] - vp2[v];
+                vc[v] = vp1[v];
+                vp1[v] = vp2[v];
+                vp2[v] = nw[v];
+            }
+        }
+    }
+    if constexpr (LEARNED) {
+        if ((threadIdx.x & 31) == 0 && net_rows && a.net_rows) atomicAdd(a.net_rows, net_rows);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// x sweep as a coalesced stream.  Every x-row of n cells is laid out as n+2
+// "slots" for edge cells c = -1..n; the rows are concatenated and each CTA
+// owns `slots_per_block` consecutive slots.  A chunk of 128 slots is one slot
+// per lane: lane s reconstructs the edges of its cell c (five-cell stencil read
+// straight from global memory, consecutive lanes = consecutive x), forms the
+// face c-1/2 from its own right-side value and the left-side value of slot s-1
+// (shared memory), and finishes cell c-1 from faces c-3/2 and c-1/2.  The last
+// slot's left-side value and flux carry to the next chunk, and each CTA starts
+// two slots early so that its first cell has both faces.  Every lane takes part
+// in every chunk, as the learned form's warp-level network needs.
+// ---------------------------------------------------------------------------
+constexpr int kStreamThreads = 128;
+
+template <typename Real, int NF, int NDIM, bool LEARNED = false, int ORDER = 5, bool NONUNIF = false, bool SIX = false>
+__device__ __forceinline__ void sweep_x_stream_body(const SweepArgs& a) {
+    static_assert(!SIX || !LEARNED, "six-equation model: FP64 and mixed forms");
+    static_assert(!NONUNIF || (!LEARNED && ORDER == 5), "non-uniform grids: WENO5, FP64 and mixed forms");
+    static_assert(!LEARNED || sizeof(Real) == 4, "the learned form runs in FP32");
+    static_assert(!LEARNED || ORDER == 5, "the learned form replaces the WENO5 weights");
+    using Lay = Layout<NF, NDIM>;
+    constexpr int NS = Lay::NS, IM = Lay::IM;
+    constexpr int NQ = Layout<NF, NDIM, SIX>::NQ;   // flux rows
+    constexpr int NJ = LEARNED ? NS : 1;
+    __shared__ Real sh_eL[NS][kStreamThreads + 1];
+    __shared__ Real sh_eLJ[NJ][kStreamThreads + 1];
+    __shared__ Real sh_F[NQ + 1][kStreamThreads + 1];
+    const Real* __restrict__ w = static_cast<const Real*>(a.w);
+    const int n = a.g.n[0];
+    const long long rowlen = (long long)n + 2;
+    const long long nrows = a.g.ncell / n;
+    const long long total = rowlen * nrows;
+    const long long own0 = (long long)blockIdx.x * a.slots_per_block;
+    const long long own1 = min(own0 + a.slots_per_block, total);
+    const long long nc = a.g.ncell;
+    const int bclo = a.g.bc_lo[0], bchi = a.g.bc_hi[0];
+    const Real eps34 = sweep_epsw<Real, ORDER>(a);  // 3/4 eps (WENO5) or eps (WENO3)
+    const EosR<Real> e = sweep_eos<Real>(a);
+    const Real inv_dx = sweep_inv_dx<Real>(a, 0);
+    const int t = threadIdx.x;
+    LearnSmem<NS>* lsm = nullptr;
+    if constexpr (LEARNED) {
+        __shared__ LearnSmem<NS> lbuf[kStreamThreads / 32];
+        lsm = &lbuf[t >> 5];
+    }
+    unsigned long long net_rows = 0;  // learned form: network rows of this warp
+
+    // (row, column) of this lane's slot: one 64-bit division when the slot first
+    // becomes valid, then advanced by 128 slots per chunk with additions (a
+    // 64-bit division per chunk would run on the FP64 pipe)
+    long long srow = 0;
+    int scol = 0;  // slot index within its row, 0..n+1
+    bool placed = false;
+    for (long long base = own0 - 2; base < own1; base += kStreamThreads) {
+        const long long s = base + t;
+        if (s >= 0 && !placed) {
+            srow = s / rowlen;
+            scol = (int)(s - srow * rowlen);
+            placed = true;
+        }
+        const bool live = (s >= 0) && (s < own1);
+        const long long row = srow;
+        const int c = live ? scol - 1 : -1;
+        const long long rowoff = row * n;
+        if (placed) {
+            scol += kStreamThreads;
+            while (scol >= rowlen) {
+                scol -= (int)rowlen;
+                ++srow;
+            }
+        }
+        Real cell[NS], cm1[NS], eL[NS], eR[NS], eLJ[NS], eRJ[NS];
+        if constexpr (LEARNED) {
+            // the five cells of this lane's stencil, re-read (L1) per variable
+            int mk[5];
+            bool fk[5];
+#pragma unroll
+            for (int k = 0; k < 5; ++k) {
+                fk[k] = false;
+                mk[k] = live ? ghost_map(c + k - 2, n, bclo, bchi, &fk[k]) : 0;
+            }
+            const Real* wr = w + rowoff;
+            auto stencil = [&](int q, float (&dd)[4]) -> float {
+                float v5[5];
+#pragma unroll
+                for (int k = 0; k < 5; ++k) {
+                    float x = live ? __ldg(wr + q * nc + mk[k]) : 0.f;
+                    if (q == IM && fk[k]) x = -x;
+                    v5[k] = x;
+                }
+#pragma unroll
+                for (int k = 0; k < 4; ++k) dd[k] = v5[k + 1] - v5[k];
+                return v5[2];
+            };
+            net_rows += learned_cell_edges<NS>(stencil, eps34, a.tau, a.bound != 0, a.mlp_frag, *lsm, t & 31, eRJ, eLJ,
+                                                  eR, eL);
+#pragma unroll
+            for (int q = 0; q < NS; ++q) {
+                float x1 = live ? __ldg(wr + q * nc + mk[1]) : 0.f;
+                float x2 = live ? __ldg(wr + q * nc + mk[2]) : 0.f;
+                if (q == IM && fk[1]) x1 = -x1;
+                if (q == IM && fk[2]) x2 = -x2;
+                cm1[q] = x1;
+                cell[q] = x2;
+            }
+        }
+        Real vcv[NS], Dv[NS][4];
+        if constexpr (!LEARNED) {
+#pragma unroll
+            for (int q = 0; q < NS; ++q) {
+                vcv[q] = 0;
+                cm1[q] = 0;
+                Dv[q][0] = Dv[q][1] = Dv[q][2] = Dv[q][3] = 0;
+            }
+        }
+        if (!LEARNED && live) {
+            Real v[5][NS];
+#pragma unroll
+            for (int k = 0; k < 5; ++k) {
+                bool flip = false;
+                const int m = ghost_map(c + k - 2, n, bclo, bchi, &flip);
+#pragma unroll
+                for (int q = 0; q < NS; ++q) v[k][q] = __ldg(w + q * nc + rowoff + m);
+                if (flip) v[k][IM] = -v[k][IM];
+            }
+#pragma unroll
+            for (int q = 0; q < NS; ++q) {
+                Dv[q][0] = v[1][q] - v[0][q];
+                Dv[q][1] = v[2][q] - v[1][q];
+                Dv[q][2] = v[3][q] - v[2][q];
+                Dv[q][3] = v[4][q] - v[3][q];
+                vcv[q] = v[2][q];
+                cm1[q] = v[1][q];
+            }
+        }
+        if (!LEARNED && live) {
+            if constexpr (NONUNIF) {
+                const GridCol<true> row(a.grid[0], a.grid_stride[0], c);
+                const Real epsn = sweep_epsw<Real, 3>(a);   // unscaled eps
+#pragma unroll
+                for (int q = 0; q < NS; ++q) weno5_edges_nu(vcv[q], Dv[q], epsn, row, eR[q], eL[q]);
+            } else {
+#pragma unroll
+                for (int q = 0; q < NS; ++q) weno_edges<ORDER>(vcv[q], Dv[q], eps34, eR[q], eL[q]);
+            }
+        }
+        if constexpr (!LEARNED) {
+#pragma unroll
+            for (int q = 0; q < NS; ++q) cell[q] = vcv[q];
+        }
+        // left-side values of this chunk; slot 0 holds the carry from the last chunk
+        if (live) {
+#pragma unroll
+            for (int q = 0; q < NS; ++q) {
+                sh_eL[q][t + 1] = eL[q];
+                if constexpr (LEARNED) sh_eLJ[q][t + 1] = eLJ[q];
+            }
+        }
+        __syncthreads();
+        Real F[NQ], ut = 0;
+        const bool has_face = live && c >= 0 && s >= own0 - 1;
+        if (has_face) {
+            Real lft[NS];
+#pragma unroll
+            for (int q = 0; q < NS; ++q) lft[q] = sh_eL[q][t];
+            if constexpr (LEARNED) {
+                Real lftJ[NS];
+#pragma unroll
+                for (int q = 0; q < NS; ++q) lftJ[q] = sh_eLJ[q][t];
+                face_flux_learned<NF, NDIM, 0>(a, e, lft, eR, lftJ, eRJ, cm1, cell, F, ut);
+            } else {
+                face_flux<Real, NF, NDIM, 0, SIX>(a, e, lft, eR, cm1, cell, F, ut);
+            }
+#pragma unroll
+            for (int q = 0; q < NQ; ++q) sh_F[q][t + 1] = F[q];
+            sh_F[NQ][t + 1] = ut;
+        }
+        __syncthreads();
+        if (has_face && s >= own0 && c >= 1) {
+            Real Fm[NQ];
+#pragma unroll
+            for (int q = 0; q < NQ; ++q) Fm[q] = sh_F[q][t];
+            finish_cell<Real, NF, NDIM, 0, SIX>(a, rowoff + (c - 1), Fm, F, sh_F[NQ][t], ut, cm1,
+                                           NONUNIF ? grid_inv_dx<true>(a.grid[0], a.grid_stride[0], c - 1, Real(0)) : inv_dx,
+                                           c - 1, 1, row);
+        }
+        __syncthreads();
+        // carry the last slot of the chunk into position 0
+        if (t == kStreamThreads - 1) {
+#pragma unroll
+            for (int q = 0; q < NS; ++q) {
+                sh_eL[q][0] = sh_eL[q][kStreamThreads];
+                if constexpr (LEARNED) sh_eLJ[q][0] = sh_eLJ[q][kStreamThreads];
+            }
+#pragma unroll
+            for (int q = 0; q <= NQ; ++q) sh_F[q][0] = sh_F[q][kStreamThreads];
+        }
+        __syncthreads();
+    }
+    if constexpr (LEARNED) {
+        if ((threadIdx.x & 31) == 0 && net_rows && a.net_rows) atomicAdd(a.net_rows, net_rows);
+    }
+}
+
+template <typename Real, int NF, int NDIM, bool LEARNED = false, int ORDER = 5, bool NONUNIF = false, bool SIX = false>
+__global__ void __launch_bounds__(kStreamThreads) sweep_x_stream_kernel(const SweepArgs a) {
+    sweep_x_stream_body<Real, NF, NDIM, LEARNED, ORDER, NONUNIF, SIX>(a);
+}
+
+// The learned form's x sweep bounded to 4 CTAs per SM (128 registers, 32
+// bytes of spills; unbounded it took 168 and kept 12 warps per SM).
+template <int NF, int NDIM>
+__global__ void __launch_bounds__(kStreamThreads, 4) sweep_x_stream_learned_kernel(const SweepArgs a) {
+    sweep_x_stream_body<float, NF, NDIM, true, 5, false, false>(a);
+}
+
+// FP64 sweeps bounded to 4 CTAs (16 warps) per SM, for the variants where
+// the extra warps outweigh the spills (launch_sweep chooses).
+template <int NF, int NDIM, int ORDER = 5, bool NONUNIF = false, bool SIX = false>
+__global__ void __launch_bounds__(kStreamThreads, 4) sweep_x_stream_f64_kernel(const SweepArgs a) {
+    sweep_x_stream_body<double, NF, NDIM, false, ORDER, NONUNIF, SIX>(a);
+}
+
+// ---------------------------------------------------------------------------
+// y or z sweep as a coalesced stream (FP32 paths).  A CTA of 4 warps covers 32
+// consecutive x (lanes) of one pencil segment s0..s1-1 along DIR and walks it
+// in chunks of 4 edge cells, one per warp: warp r of a chunk reconstructs the
+// edges of cell c = base + r from its five-cell stencil, read from a shared
+// ring of the 8 rows base-2..base+5 (each warp loads one new row per chunk,
+// prefetched into registers during the previous chunk's arithmetic), forms the
+// face c-1/2 with the left-side value of the previous row (shared memory, or
+// the carry from the previous chunk) and finishes cell c-1.  Unlike the
+// marching kernel no per-thread window is kept, so more warps stay resident to
+// hide load and tensor-core latency.
+// ---------------------------------------------------------------------------
+constexpr int kRowsPerChunk = 4;
+
+template <typename Real, int NF, int NDIM, int DIR, bool LEARNED, int ORDER, bool NONUNIF = false, bool SIX = false>
+__device__ __forceinline__ void sweep_yz_stream_body(const SweepArgs& a) {
+    static_assert(!SIX || !LEARNED, "six-equation model: FP64 and mixed forms");
+    static_assert(!NONUNIF || (!LEARNED && ORDER == 5), "non-uniform grids: WENO5, FP64 and mixed forms");
+    static_assert(!LEARNED || ORDER == 5, "the learned form replaces the WENO5 weights");
+    static_assert(DIR == 1 || DIR == 2, "y or z");
+    static_assert(!LEARNED || sizeof(Real) == 4, "the learned form runs in FP32");
+    using Lay = Layout<NF, NDIM>;
+    constexpr int NS = Lay::NS, IM = Lay::IM;
+    constexpr int NQ = Layout<NF, NDIM, SIX>::NQ;   // flux rows
+    constexpr int NJ = LEARNED ? NS : 1;
+    constexpr int T1 = 0;
+    constexpr int T2 = (DIR == 2) ? 1 : 2;
+    constexpr int RING = 2 * kRowsPerChunk;  // rows base-2 .. base+5 of a chunk
+    __shared__ Real ring[RING][NS][32];
+    __shared__ Real sh_eL[NS][kRowsPerChunk + 1][32];
+    __shared__ Real sh_eLJ[NJ][kRowsPerChunk + 1][32];
+    __shared__ Real sh_F[NQ + 1][kRowsPerChunk + 1][32];
+    const Real* __restrict__ w = static_cast<const Real*>(a.w);
+    const int lane = threadIdx.x & 31, row = threadIdx.x >> 5;
+    const int n1 = a.g.n[T1], n2 = a.g.n[T2], nd = a.g.n[DIR];
+    const int nxc = (n1 + 31) >> 5;
+    const long long bid = blockIdx.x;
+    const int xc = (int)(bid % nxc);
+    const long long rest = bid / nxc;
+    const int sg = (int)(rest % a.nseg);
+    const int t2 = (int)(rest / a.nseg);
+    if (t2 >= n2) return;  // whole CTA
+    const bool active = xc * 32 + lane < n1;
+    const int t1 = active ? xc * 32 + lane : n1 - 1;
+    const long long sd = stride_of(a.g, DIR);
+    const long long basei = (long long)t1 * stride_of(a.g, T1) + (long long)t2 * stride_of(a.g, T2);
+    const long long nc = a.g.ncell;
+    const int s0 = sg * a.seg;
+    const int s1 = min(s0 + a.seg, nd);
+    const int bclo = a.g.bc_lo[DIR], bchi = a.g.bc_hi[DIR];
+    const Real eps34 = sweep_epsw<Real, ORDER>(a);  // 3/4 eps (WENO5) or eps (WENO3)
+    const EosR<Real> e = sweep_eos<Real>(a);
+    const Real inv_dx = sweep_inv_dx<Real>(a, DIR);
+    LearnSmem<NS>* lsm = nullptr;
+    if constexpr (LEARNED) {
+        __shared__ LearnSmem<NS> lbuf[kRowsPerChunk];
+        lsm = &lbuf[row];
+    }
+    unsigned long long net_rows = 0;  // learned form: network rows of this warp
+    // cell i along DIR (ghost-mapped) of this lane's column
+    auto load = [&](int i, Real* out) {
+        bool flip = false;
+        const int m = ghost_map(i, nd, bclo, bchi, &flip);
+        const long long idx = basei + (long long)m * sd;
+#pragma unroll
+        for (int q = 0; q < NS; ++q) out[q] = __ldg(w + q * nc + idx);
+        if (flip) out[IM + DIR] = -out[IM + DIR];
+    };
+    auto slot = [](int i) { return ((i % RING) + RING) % RING; };
+    // prologue: rows s0-3 .. s0+4 (cells base-2 .. base+5 of the first chunk)
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        const int i = s0 - 3 + row + kRowsPerChunk * h;
+        if (i <= s1 + 2) {
+            Real v[NS];
+            load(i, v);
+#pragma unroll
+            for (int q = 0; q < NS; ++q) ring[slot(i)][q][lane] = v[q];
+        }
+    }
+    __syncthreads();
+
+    for (int base = s0 - 1; base <= s1; base += kRowsPerChunk) {
+        // prefetch the row the next chunk adds (cell base+6+row) while this one computes
+        const int inext = base + RING - 2 + row;
+        const bool pf = inext <= s1 + 2;
+        Real nxt[NS];
+        if (pf) load(inext, nxt);
+        const int c = base + row;       // edge cell of this warp (warp-uniform)
+        const bool live = c <= s1;
+        Real cell[NS], cm1[NS], eL[NS], eR[NS], eLJ[NS], eRJ[NS];
+        if (live) {
+            if constexpr (LEARNED) {
+                auto stencil = [&](int q, float (&dd)[4]) -> float {
+                    float v5[5];
+#pragma unroll
+                    for (int k = 0; k < 5; ++k) v5[k] = ring[slot(c - 2 + k)][q][lane];
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) dd[k] = v5[k + 1] - v5[k];
+                    return v5[2];
+                };
+                net_rows += learned_cell_edges<NS>(stencil, eps34, a.tau, a.bound != 0, a.mlp_frag, *lsm, lane, eRJ,
+                                                   eLJ, eR, eL);
+#pragma unroll
+                for (int q = 0; q < NS; ++q) {
+                    cell[q] = ring[slot(c)][q][lane];
+                    cm1[q] = ring[slot(c - 1)][q][lane];
+                }
+            } else {
+                Real Dv[NS][4];
+#pragma unroll
+                for (int q = 0; q < NS; ++q) {
+                    const Real v0 = ring[slot(c - 2)][q][lane], v1 = ring[slot(c - 1)][q][lane];
+                    const Real v2 = ring[slot(c)][q][lane], v3 = ring[slot(c + 1)][q][lane];
+                    const Real v4 = ring[slot(c + 2)][q][lane];
+                    Dv[q][0] = v1 - v0;
+                    Dv[q][1] = v2 - v1;
+                    Dv[q][2] = v3 - v2;
+                    Dv[q][3] = v4 - v3;
+                    cell[q] = v2;
+                    cm1[q] = v1;
+                }
+                if constexpr (NONUNIF) {
+                    const GridCol<false> grow(a.grid[DIR], a.grid_stride[DIR], c);
+                    const Real epsn = sweep_epsw<Real, 3>(a);   // unscaled eps
+#pragma unroll
+                    for (int q = 0; q < NS; ++q) weno5_edges_nu(cell[q], Dv[q], epsn, grow, eR[q], eL[q]);
+                } else {
+#pragma unroll
+                    for (int q = 0; q < NS; ++q) weno_edges<ORDER>(cell[q], Dv[q], eps34, eR[q], eL[q]);
+                }
+            }
+#pragma unroll
+            for (int q = 0; q < NS; ++q) {
+                sh_eL[q][row + 1][lane] = eL[q];
+                if constexpr (LEARNED) sh_eLJ[q][row + 1][lane] = eLJ[q];
+            }
+        }
+        __syncthreads();
+        // rows base-2 .. base+1 are no longer needed: the prefetched rows replace them
+        if (pf) {
+#pragma unroll
+            for (int q = 0; q < NS; ++q) ring[slot(inext)][q][lane] = nxt[q];
+        }
+        Real F[NQ], ut = 0;
+        const bool has_face = live && c >= s0;
+        if (has_face) {
+            Real lft[NS];
+#pragma unroll
+            for (int q = 0; q < NS; ++q) lft[q] = sh_eL[q][row][lane];
+            if constexpr (LEARNED) {
+                Real lftJ[NS];
+#pragma unroll
+                for (int q = 0; q < NS; ++q) lftJ[q] = sh_eLJ[q][row][lane];
+                face_flux_learned<NF, NDIM, DIR>(a, e, lft, eR, lftJ, eRJ, cm1, cell, F, ut);
+            } else {
+                face_flux<Real, NF, NDIM, DIR, SIX>(a, e, lft, eR, cm1, cell, F, ut);
+            }
+#pragma unroll
+            for (int q = 0; q < NQ; ++q) sh_F[q][row + 1][lane] = F[q];
+            sh_F[NQ][row + 1][lane] = ut;
+        }
+        __syncthreads();
+        if (has_face && c >= s0 + 1 && active) {
+            Real Fm[NQ];
+#pragma unroll
+            for (int q = 0; q < NQ; ++q) Fm[q] = sh_F[q][row][lane];
+            finish_cell<Real, NF, NDIM, DIR, SIX>(a, basei + (long long)(c - 1) * sd, Fm, F, sh_F[NQ][row][lane], ut, cm1,
+                                             NONUNIF ? grid_inv_dx<false>(a.grid[DIR], a.grid_stride[DIR], c - 1, Real(0))
+                                                     : inv_dx,
+                                             c - 1, sd, (long long)t1 + (long long)n1 * t2);
+        }
+        __syncthreads();
+        // carry the last row of the chunk into row 0
+        if (row == kRowsPerChunk - 1) {
+#pragma unroll
+            for (int q = 0; q < NS; ++q) {
+                sh_eL[q][0][lane] = sh_eL[q][kRowsPerChunk][lane];
+                if constexpr (LEARNED) sh_eLJ[q][0][lane] = sh_eLJ[q][kRowsPerChunk][lane];
+            }
+#pragma unroll
+            for (int q = 0; q <= NQ; ++q) sh_F[q][0][lane] = sh_F[q][kRowsPerChunk][lane];
+        }
+        __syncthreads();
+    }
+    if constexpr (LEARNED) {
+        if ((threadIdx.x & 31) == 0 && net_rows && a.net_rows) atomicAdd(a.net_rows, net_rows);
+    }
+}
+
+// The y/z stream kernel of the FP32 forms.  The learned form gets its own
+// entry with a register bound (4 CTAs per SM for two fluids) so that enough
+// warps stay resident; the mixed form keeps the compiler's own allocation,
+// which schedules its loads better.
+template <typename Real, int NF, int NDIM, int DIR, int ORDER = 5, bool NONUNIF = false, bool SIX = false>
+__global__ void __launch_bounds__(32 * kRowsPerChunk) sweep_yz_stream_kernel(const SweepArgs a) {
+    sweep_yz_stream_body<Real, NF, NDIM, DIR, false, ORDER, NONUNIF, SIX>(a);
+}
+
+// The mixed form's six-equation y/z sweep: bounded to 5 CTAs per SM (96
+// registers; unbounded it took 107 and ran 45 instead of 37 ms over the 256^3
+// bench).  A bound of one CTA per SM is not the same as none: it slowed the
+// five-equation kernels by half, hence a separate entry.
+template <int NF, int NDIM, int DIR, int ORDER = 5, bool NONUNIF = false>
+__global__ void __launch_bounds__(32 * kRowsPerChunk, 5) sweep_yz_stream_six32_kernel(const SweepArgs a) {
+    sweep_yz_stream_body<float, NF, NDIM, DIR, false, ORDER, NONUNIF, true>(a);
+}
+
+template <int NF, int NDIM, int DIR, int ORDER = 5, bool NONUNIF = false, bool SIX = false>
+__global__ void __launch_bounds__(32 * kRowsPerChunk, 4) sweep_yz_stream_f64_kernel(const SweepArgs a) {
+    sweep_yz_stream_body<double, NF, NDIM, DIR, false, ORDER, NONUNIF, SIX>(a);
+}
+
+template <int NF, int NDIM, int DIR>
+__global__ void __launch_bounds__(32 * kRowsPerChunk, NF <= 2 ? 4 : 3) sweep_yz_stream_learned_kernel(const SweepArgs a) {
+    sweep_yz_stream_body<float, NF, NDIM, DIR, true, 5>(a);
+}
+
+}  // namespace mfc

@@ -1,0 +1,227 @@
+// Reconstruction (Sec. 3.2, 3.3): WENO5-JS and WENO3-JS edge values in FP64
+// (float-float weights) and FP32, and WENO5 on non-uniform grids from the
+// per-cell coefficient tables.
+#pragma once
+#include "mfc_common.cuh"
+
+namespace mfc {
+
+// ---------------------------------------------------------------------------
+// WENO5-JS edge values of one cell (Sec. 3.2).  D[k] = v_{c+k-1} - v_{c+k-2},
+// k = 0..3, i.e. the four differences across the five-cell stencil c-2..c+2.
+// Returns eR (value at c-1/2) and eL (value at c+1/2).
+//
+// The Jiang-Shu smoothness indicators as quadratic forms of the differences,
+//   b0 = 4/3 [ 5/2 D1^2 - 11/4 D1 D0 + D0^2 ]   (stencil c-2..c)
+//   b1 = 4/3 [ D1^2 + D2^2 - 5/4 D1 D2 ]        (stencil c-1..c+1)
+//   b2 = 4/3 [ 5/2 D2^2 - 11/4 D2 D3 + D3^2 ]   (stencil c..c+2),
+// are evaluated without the common factor 4/3, with eps scaled by 3/4 so every
+// (eps + b_r) carries the same factor and the weights are unchanged.  The
+// candidates are increments over v_c (constant data reconstructs exactly).
+// eps34 = 3/4 eps.
+//
+// FP64 path: the differences D come in as FP64 and the edge values go out as
+// FP64, but the smoothness indicators, weights and weighted increments are
+// evaluated in float-float arithmetic (mfc_df.cuh, ~48 bits): on GB300 this
+// costs 8 FP64 instructions per variable instead of ~50.  The weights are
+// normalised by m = min_r (eps + b_r), g_r = m/(eps + b_r) <= 1, so that
+// (eps + b)^2 (up to ~1e40 for a 1e9 Pa pressure jump) never meets the FP32
+// range; with ideal weights 1 : 6 : 3 (times 10) and candidates times 6
+// (integer coefficients, exact in FP32):
+//   eL - v_c = (g0^2 (5 D1 - 2 D0) + 6 g1^2 (D1 + 2 D2) + 3 g2^2 (4 D2 - D3))
+//              / (6 (g0^2 + 6 g1^2 + 3 g2^2)),
+//   eR - v_c = (g2^2 (2 D3 - 5 D2) - 6 g1^2 (2 D1 + D2) + 3 g0^2 (D0 - 4 D1))
+//              / (6 (g2^2 + 6 g1^2 + 3 g0^2)).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void weno5_edges(double vc, const double D[4], double eps34,
+                                            double& eR, double& eL) {
+    // sums use the fast float-float addition: its error, ~2^-44 of the
+    // operands, is relative to the stencil's differences, far inside the
+    // path's parity tolerance; scalings by 2 and 4 are exact
+    const df d0 = df_from_double(D[0]), d1 = df_from_double(D[1]);
+    const df d2 = df_from_double(D[2]), d3 = df_from_double(D[3]);
+    const df S1 = df_mul(d1, d1), S2 = df_mul(d2, d2);
+    const df b0 = df_add_fast(df_add_fast(df_mul(d0, d0), df_mul_f(df_mul(d1, d0), -2.75f)), df_mul_f(S1, 2.5f));
+    const df b1 = df_add_fast(df_add_fast(S1, S2), df_mul_f(df_mul(d1, d2), -1.25f));
+    const df b2 = df_add_fast(df_add_fast(df_mul(d3, d3), df_mul_f(df_mul(d2, d3), -2.75f)), df_mul_f(S2, 2.5f));
+    const df e = df_from_double(eps34);
+    const df t0 = df_add_fast(e, b0), t1 = df_add_fast(e, b1), t2 = df_add_fast(e, b2);
+    const float m = fminf(t0.hi, fminf(t1.hi, t2.hi));
+    const df g0 = df_div_f(m, t0), g1 = df_div_f(m, t1), g2 = df_div_f(m, t2);
+    const df q0 = df_mul(g0, g0), q1 = df_mul_f(df_mul(g1, g1), 6.f), q2 = df_mul(g2, g2);
+    // edge at c+1/2: weights q0, q1, 3 q2
+    const df wL2 = df_mul_f(q2, 3.f);
+    const df P0 = df_add_fast(df_mul_f(d1, 5.f), df_mul_pow2(d0, -2.f));
+    const df P1 = df_add_fast(d1, df_mul_pow2(d2, 2.f));
+    const df P2 = df_add_fast(df_mul_pow2(d2, 4.f), df_neg(d3));
+    const df numL = df_add_fast(df_add_fast(df_mul(q0, P0), df_mul(q1, P1)), df_mul(wL2, P2));
+    const df denL = df_mul_f(df_add_fast(df_add_fast(q0, q1), wL2), 6.f);
+    // edge at c-1/2: weights q2, q1, 3 q0
+    const df wR2 = df_mul_f(q0, 3.f);
+    const df M0 = df_add_fast(df_mul_pow2(d3, 2.f), df_mul_f(d2, -5.f));
+    const df M1 = df_neg(df_add_fast(df_mul_pow2(d1, 2.f), d2));
+    const df M2 = df_add_fast(d0, df_mul_pow2(d1, -4.f));
+    const df numR = df_add_fast(df_add_fast(df_mul(q2, M0), df_mul(q1, M1)), df_mul(wR2, M2));
+    const df denR = df_mul_f(df_add_fast(df_add_fast(q2, q1), wR2), 6.f);
+    eL = vc + df_to_double(df_div(numL, denL));
+    eR = vc + df_to_double(df_div(numR, denR));
+}
+
+// FP32 variant for the mixed path.  The weights are normalised by the smallest
+// eps+beta, so no intermediate overflows FP32 (beta of a 1e9 Pa jump is ~1e19).
+__device__ __forceinline__ void weno5_edges(float vc, const float D[4], float eps34,
+                                            float& eR, float& eL) {
+    const float S0 = D[0] * D[0], S1 = D[1] * D[1], S2 = D[2] * D[2], S3 = D[3] * D[3];
+    const float b0 = fmaf(2.5f, S1, fmaf(-2.75f, D[1] * D[0], S0));
+    const float b1 = fmaf(-1.25f, D[1] * D[2], S1 + S2);
+    const float b2 = fmaf(2.5f, S2, fmaf(-2.75f, D[2] * D[3], S3));
+    const float t0 = eps34 + b0, t1 = eps34 + b1, t2 = eps34 + b2;
+    const float m = fminf(t0, fminf(t1, t2));
+    float g0 = __fdividef(m, t0), g1 = __fdividef(m, t1), g2 = __fdividef(m, t2);
+    g0 *= g0; g1 *= g1; g2 *= g2;
+    const float p0 = fmaf(5.f / 6.f, D[1], (-1.f / 3.f) * D[0]);
+    const float p1 = fmaf(1.f / 6.f, D[1], (1.f / 3.f) * D[2]);
+    const float p2 = fmaf(2.f / 3.f, D[2], (-1.f / 6.f) * D[3]);
+    const float m0 = fmaf(-5.f / 6.f, D[2], (1.f / 3.f) * D[3]);
+    const float m1 = fmaf(-1.f / 6.f, D[2], (-1.f / 3.f) * D[1]);
+    const float m2 = fmaf(-2.f / 3.f, D[1], (1.f / 6.f) * D[0]);
+    const float wl0 = 0.1f * g0, wl1 = 0.6f * g1, wl2 = 0.3f * g2;
+    const float wr0 = 0.1f * g2, wr2 = 0.3f * g0;
+    eL = vc + __fdividef(fmaf(wl0, p0, fmaf(wl1, p1, wl2 * p2)), wl0 + wl1 + wl2);
+    eR = vc + __fdividef(fmaf(wr0, m0, fmaf(wl1, m1, wr2 * m2)), wr0 + wl1 + wr2);
+}
+
+// ---------------------------------------------------------------------------
+// WENO3-JS (the third-order variant of Sec. 3.2: k = 2 candidates) for the
+// edges at c+1/2 (eL) and c-1/2 (eR) from a = v_c - v_{c-1}, b = v_{c+1} - v_c.
+// With t0 = eps + a^2, t1 = eps + b^2 the weights of the candidates
+// v_c + a/2 (cells c-1, c; ideal 1/3) and v_c + b/2 (cells c, c+1; ideal 2/3)
+// are proportional to t1^2 and 2 t0^2, so
+//   eL = v_c + (t1^2 a + 2 t0^2 b) / (2 (t1^2 + 2 t0^2))
+// and, mirrored, eR = v_c - (t0^2 b + 2 t1^2 a) / (2 (t0^2 + 2 t1^2)).
+// FP64 path: a and b come in as FP64, the weights and weighted increments are
+// float-float (mfc_df.cuh), scaled as the FP32 variant below so nothing leaves
+// the FP32 range: g_r = min(t0, t1)/t_r <= 1, weights g0^2 and 2 g1^2 at
+// c+1/2, g1^2 and 2 g0^2 at c-1/2.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void weno3_edges(double vc, double a, double b, double eps, double& eR, double& eL) {
+    const df A = df_from_double(a), Bd = df_from_double(b), E = df_from_double(eps);
+    const df t0 = df_add_fast(E, df_mul(A, A)), t1 = df_add_fast(E, df_mul(Bd, Bd));
+    const float m = fminf(t0.hi, t1.hi);
+    const df g0 = df_div_f(m, t0), g1 = df_div_f(m, t1);
+    const df s0 = df_mul(g0, g0), s1 = df_mul(g1, g1);
+    const df s0x2 = df_mul_pow2(s0, 2.f), s1x2 = df_mul_pow2(s1, 2.f);
+    const df numL = df_add_fast(df_mul(s0, A), df_mul(s1x2, Bd));
+    const df numR = df_add_fast(df_mul(s1, Bd), df_mul(s0x2, A));
+    const df denL = df_mul_pow2(df_add_fast(s0, s1x2), 2.f), denR = df_mul_pow2(df_add_fast(s1, s0x2), 2.f);
+    eL = vc + df_to_double(df_div(numL, denL));
+    eR = vc - df_to_double(df_div(numR, denR));
+}
+
+// FP32: t^2 can overflow FP32 (a pressure jump of 1e9 Pa gives t ~ 1e18), so
+// both t are scaled by their minimum first: g_r = min(t0, t1)/t_r <= 1.
+__device__ __forceinline__ void weno3_edges(float vc, float a, float b, float eps, float& eR, float& eL) {
+    const float t0 = fmaf(a, a, eps), t1 = fmaf(b, b, eps);
+    const float m = fminf(t0, t1);
+    float g0 = __fdividef(m, t0), g1 = __fdividef(m, t1);
+    g0 *= g0;
+    g1 *= g1;
+    // weights proportional to g0/3 and 2 g1/3 at c+1/2, g1/3 and 2 g0/3 at c-1/2
+    eL = vc + 0.5f * __fdividef(fmaf(2.f * g1, b, g0 * a), fmaf(2.f, g1, g0));
+    eR = vc - 0.5f * __fdividef(fmaf(2.f * g0, a, g1 * b), fmaf(2.f, g0, g1));
+}
+
+// Edge values of the reconstruction of order ORDER (3 or 5) from the four
+// differences D across cells c-2..c+2; epsw is the epsilon as the order's
+// edge function takes it (3/4 eps for WENO5, eps for WENO3).
+template <int ORDER, typename Real>
+__device__ __forceinline__ void weno_edges(Real vc, const Real D[4], Real epsw, Real& eR, Real& eL) {
+    static_assert(ORDER == 3 || ORDER == 5, "WENO3 or WENO5");
+    if constexpr (ORDER == 3) weno3_edges(vc, D[1], D[2], epsw, eR, eL);
+    else weno5_edges(vc, D, epsw, eR, eL);
+}
+
+// ---------------------------------------------------------------------------
+// WENO5-JS on a non-uniform grid (Sec. 3.3, with per-cell coefficients as in
+// Listing 1): row = the cell's table row (mfc_grid.cu): candidate increments
+// ea_r Da_r + eb_r Db_r for both edges (values 0..11), ideal weights (12..17),
+// beta_r = qa Da^2 + qab Da Db + qb Db^2 (18..26), with (Da, Db) = (D0, D1),
+// (D1, D2), (D2, D3) for r = 0, 1, 2.  The indicators are the exact integrals
+// (no 4/3 scaling), so eps enters unscaled.  Weights normalised by
+// m = min_r (eps + beta_r) as in the uniform variants.
+// ---------------------------------------------------------------------------
+template <class Col>
+__device__ __forceinline__ df grid_df(const Col& row, int k) {
+    const float2 v = row[k];
+    return {v.x, v.y};
+}
+
+template <class Col>
+__device__ __forceinline__ void weno5_edges_nu(double vc, const double D[4], double eps, const Col& row,
+                                               double& eR, double& eL) {
+    const df d0 = df_from_double(D[0]), d1 = df_from_double(D[1]);
+    const df d2 = df_from_double(D[2]), d3 = df_from_double(D[3]);
+    const df S0 = df_mul(d0, d0), S1 = df_mul(d1, d1), S2 = df_mul(d2, d2), S3 = df_mul(d3, d3);
+    const df X01 = df_mul(d0, d1), X12 = df_mul(d1, d2), X23 = df_mul(d2, d3);
+    const df b0 = df_add_fast(df_add_fast(df_mul(grid_df(row, 18), S0), df_mul(grid_df(row, 19), X01)),
+                              df_mul(grid_df(row, 20), S1));
+    const df b1 = df_add_fast(df_add_fast(df_mul(grid_df(row, 21), S1), df_mul(grid_df(row, 22), X12)),
+                              df_mul(grid_df(row, 23), S2));
+    const df b2 = df_add_fast(df_add_fast(df_mul(grid_df(row, 24), S2), df_mul(grid_df(row, 25), X23)),
+                              df_mul(grid_df(row, 26), S3));
+    const df e = df_from_double(eps);
+    const df t0 = df_add_fast(e, b0), t1 = df_add_fast(e, b1), t2 = df_add_fast(e, b2);
+    const float m = fminf(t0.hi, fminf(t1.hi, t2.hi));
+    const df g0 = df_div_f(m, t0), g1 = df_div_f(m, t1), g2 = df_div_f(m, t2);
+    const df q0 = df_mul(g0, g0), q1 = df_mul(g1, g1), q2 = df_mul(g2, g2);
+    const df P0 = df_add_fast(df_mul(grid_df(row, 0), d0), df_mul(grid_df(row, 1), d1));
+    const df P1 = df_add_fast(df_mul(grid_df(row, 2), d1), df_mul(grid_df(row, 3), d2));
+    const df P2 = df_add_fast(df_mul(grid_df(row, 4), d2), df_mul(grid_df(row, 5), d3));
+    const df wL0 = df_mul(grid_df(row, 12), q0), wL1 = df_mul(grid_df(row, 13), q1), wL2 = df_mul(grid_df(row, 14), q2);
+    const df numL = df_add_fast(df_add_fast(df_mul(wL0, P0), df_mul(wL1, P1)), df_mul(wL2, P2));
+    const df denL = df_add_fast(df_add_fast(wL0, wL1), wL2);
+    const df M0 = df_add_fast(df_mul(grid_df(row, 6), d0), df_mul(grid_df(row, 7), d1));
+    const df M1 = df_add_fast(df_mul(grid_df(row, 8), d1), df_mul(grid_df(row, 9), d2));
+    const df M2 = df_add_fast(df_mul(grid_df(row, 10), d2), df_mul(grid_df(row, 11), d3));
+    const df wR0 = df_mul(grid_df(row, 15), q0), wR1 = df_mul(grid_df(row, 16), q1), wR2 = df_mul(grid_df(row, 17), q2);
+    const df numR = df_add_fast(df_add_fast(df_mul(wR0, M0), df_mul(wR1, M1)), df_mul(wR2, M2));
+    const df denR = df_add_fast(df_add_fast(wR0, wR1), wR2);
+    eL = vc + df_to_double(df_div(numL, denL));
+    eR = vc + df_to_double(df_div(numR, denR));
+}
+
+template <class Col>
+__device__ __forceinline__ void weno5_edges_nu(float vc, const float D[4], float eps, const Col& row,
+                                               float& eR, float& eL) {
+    auto T = [&](int k) { return row[k].x; };
+    const float S0 = D[0] * D[0], S1 = D[1] * D[1], S2 = D[2] * D[2], S3 = D[3] * D[3];
+    const float b0 = fmaf(T(18), S0, fmaf(T(19), D[0] * D[1], T(20) * S1));
+    const float b1 = fmaf(T(21), S1, fmaf(T(22), D[1] * D[2], T(23) * S2));
+    const float b2 = fmaf(T(24), S2, fmaf(T(25), D[2] * D[3], T(26) * S3));
+    const float t0 = eps + b0, t1 = eps + b1, t2 = eps + b2;
+    const float m = fminf(t0, fminf(t1, t2));
+    float g0 = __fdividef(m, t0), g1 = __fdividef(m, t1), g2 = __fdividef(m, t2);
+    g0 *= g0;
+    g1 *= g1;
+    g2 *= g2;
+    const float P0 = fmaf(T(0), D[0], T(1) * D[1]), P1 = fmaf(T(2), D[1], T(3) * D[2]);
+    const float P2 = fmaf(T(4), D[2], T(5) * D[3]);
+    const float M0 = fmaf(T(6), D[0], T(7) * D[1]), M1 = fmaf(T(8), D[1], T(9) * D[2]);
+    const float M2 = fmaf(T(10), D[2], T(11) * D[3]);
+    const float wL0 = T(12) * g0, wL1 = T(13) * g1, wL2 = T(14) * g2;
+    const float wR0 = T(15) * g0, wR1 = T(16) * g1, wR2 = T(17) * g2;
+    eL = vc + __fdividef(fmaf(wL0, P0, fmaf(wL1, P1, wL2 * P2)), wL0 + wL1 + wL2);
+    eR = vc + __fdividef(fmaf(wR0, M0, fmaf(wR1, M1, wR2 * M2)), wR0 + wR1 + wR2);
+}
+
+// 1/dx of cell c of a non-uniform direction, in the path's precision.
+template <bool VALUE_MAJOR>
+__device__ __forceinline__ double grid_inv_dx(const float* grid, int stride, int c, double) {
+    return df_to_double(grid_df(GridCol<VALUE_MAJOR>(grid, stride, c), kGridInvDx));
+}
+template <bool VALUE_MAJOR>
+__device__ __forceinline__ float grid_inv_dx(const float* grid, int stride, int c, float) {
+    return GridCol<VALUE_MAJOR>(grid, stride, c)[kGridInvDx].x;
+}
+
+}  // namespace mfc
