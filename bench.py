@@ -79,10 +79,10 @@ FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 BYTES_MIXED_SWEEPS_STAGE = (56 + 84 + (168 + 224 + 224) / 3.0)
 # DRAM bytes per cell of one FP64 sweep launch, averaged over the x, y and z
 # sweeps of a stage: dram__bytes_read.sum + dram__bytes_write.sum of one ncu
-# capture of the 160^3 shock-bubble (x 101.5, y 157.6, z 277.3 B/cell; the
+# capture of the 160^3 shock-bubble (x 102.6, y 158.6, z 279.0 B/cell; the
 # algorithmic w + R (+ RK states) bytes are 112, 168 and 280), scaled to the
 # bench size by the cell count.  Must be re-measured when the FP64 sweeps change.
-FP64_SWEEP_DRAM_BYTES_PER_CELL = (102.7 + 158.6 + 278.7) / 3.0
+FP64_SWEEP_DRAM_BYTES_PER_CELL = (102.6 + 158.6 + 279.0) / 3.0
 # Useful tensor-core FLOPs of the learned network per stencil
 # (5x32 + 32x32 + 32x3 multiply-adds) and stencils per cell and sweep (2 edges x 7 variables).
 FLOP_MLP_STENCIL = 2 * (5 * 32 + 32 * 32 + 32 * 3)
@@ -518,10 +518,10 @@ def main():
                      "flop_per_cell_per_sweep": FLOP_SWEEP_CELL_3D_2F,
                      "traffic": FP64_SWEEP_DRAM_BYTES_PER_CELL * cells if head == "fp64" else None,
                      "traffic_note": "DRAM bytes per sweep launch (ncu at 160^3, scaled by cells)",
-                     "ncu_issue_active": 0.46,
+                     "ncu_issue_active": 0.48,
                      "note": "FLOPs at FP64 accuracy; the WENO weights and HLLC run in float-float on the FP32 "
                              "pipes, so the rate can pass the FP64 pipe's nominal peak.  ncu (160^3): FP64 pipe "
-                             "42-46% busy, issue 43-49% active (ncu_issue_active: their mean), ~12 warps per SM: "
+                             "44-51% busy, issue 48-49% active (ncu_issue_active: their mean), ~12 warps per SM: "
                              "latency-bound"},
         "gpu_launches": fp["launches"],
         "kernels_ms": {k: v[0] for k, v in fp["kernels"].items() if v[1]},

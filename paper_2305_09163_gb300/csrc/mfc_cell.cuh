@@ -380,6 +380,59 @@ __global__ void __launch_bounds__(256) cbc_rates_kernel(const SweepArgs a, long 
     }
 }
 
+// Finish-operand staging of the y/z stream kernels.  The R accumulator, qs and
+// q0 values of the cell a lane finishes in a chunk are copied to shared memory
+// by cp.async when the chunk starts, so their DRAM latency overlaps the
+// chunk's reconstruction and Riemann arithmetic instead of stalling the
+// finish.  Layout: [R: NQ x kStageSlots Real][qs: NQ x kStageSlots double]
+// [q0: NQ x kStageSlots double], only the parts a.stage selects, slot = the
+// thread's index in its CTA.  Each lane reads back only what it staged itself.
+constexpr int kStageSlots = 128;
+
+template <int B>
+__device__ __forceinline__ void cp_async_ca(void* sdst, const void* gsrc) {
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(sdst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], %2;\n" ::"r"(sa), "l"(gsrc), "n"(B) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
+
+template <typename Real, int NQ>
+__host__ __device__ constexpr size_t stage_offset_qs(int mask) {
+    return (mask & 1) ? (size_t)NQ * kStageSlots * sizeof(Real) : 0;
+}
+template <typename Real, int NQ>
+__host__ __device__ constexpr size_t stage_offset_q0(int mask) {
+    return stage_offset_qs<Real, NQ>(mask) + ((mask & 2) ? (size_t)NQ * kStageSlots * sizeof(double) : 0);
+}
+template <typename Real, int NQ>
+__host__ __device__ constexpr size_t stage_bytes(int mask) {
+    return stage_offset_q0<Real, NQ>(mask) + ((mask & 4) ? (size_t)NQ * kStageSlots * sizeof(double) : 0);
+}
+
+template <typename Real, int NQ>
+__device__ __forceinline__ void stage_finish_operands(const SweepArgs& a, long long idx, unsigned char* stg, int slot) {
+    const long long nc = a.g.ncell;
+    const int m = a.stage;
+    if (m & 1) {
+        Real* d = reinterpret_cast<Real*>(stg) + slot;
+        const Real* R = static_cast<const Real*>(a.R);
+#pragma unroll
+        for (int v = 0; v < NQ; ++v) cp_async_ca<sizeof(Real)>(d + v * kStageSlots, R + v * nc + idx);
+    }
+    if (m & 2) {
+        double* d = reinterpret_cast<double*>(stg + stage_offset_qs<Real, NQ>(m)) + slot;
+#pragma unroll
+        for (int v = 0; v < NQ; ++v) cp_async_ca<8>(d + v * kStageSlots, a.qs + v * nc + idx);
+    }
+    if (m & 4) {
+        double* d = reinterpret_cast<double*>(stg + stage_offset_q0<Real, NQ>(m)) + slot;
+#pragma unroll
+        for (int v = 0; v < NQ; ++v) cp_async_ca<8>(d + v * kStageSlots, a.q0 + v * nc + idx);
+    }
+    cp_async_commit();
+}
+
 // Finish cell idx (coordinate b along DIR, neighbours sd apart, transverse
 // flat index tr or -1): flux difference and alpha div(u) source, or, at a
 // characteristic boundary, the boundary rate (from cbc_rates when the caller
@@ -388,10 +441,13 @@ __global__ void __launch_bounds__(256) cbc_rates_kernel(const SweepArgs a, long 
 // Six-equation model (SIX): NQ rows; the phase energies lose a_k p div(u)
 // (cell values), and an RK stage update ends with the pressure relaxation
 // (relax6) before it is stored.
+//
+// stg (y/z stream kernels, or null): this lane's operands staged by
+// stage_finish_operands, complete (cp_async_wait_all) before the call.
 template <typename Real, int NF, int NDIM, int DIR, bool SIX = false>
 __device__ __forceinline__ void finish_cell(const SweepArgs& a, long long idx, const Real* Fm, const Real* Fp,
                                             Real um, Real up, const Real* cell, Real inv_dx, int b, long long sd,
-                                            long long tr = -1) {
+                                            long long tr = -1, const unsigned char* stg = nullptr, int slot = 0) {
     using Lay = Layout<NF, NDIM, SIX>;
     constexpr int NS = Lay::NS, NQ = Lay::NQ, IA = Lay::IA;
     Real out[NQ];
@@ -440,25 +496,45 @@ __device__ __forceinline__ void finish_cell(const SweepArgs& a, long long idx, c
     }
     const long long nc = a.g.ncell;
     Real* R = static_cast<Real*>(a.R);
+    // operand rows: staged (stride kStageSlots) or in global memory (stride nc)
+    const Real* pR = R + idx;
+    const double *pQs = a.qs + idx, *pQ0 = a.q0 + idx;
+    long long sRv = nc, sQsv = nc, sQ0v = nc;
+    if (stg) {
+        const int m = a.stage;
+        if (m & 1) { pR = reinterpret_cast<const Real*>(stg) + slot; sRv = kStageSlots; }
+        if (m & 2) { pQs = reinterpret_cast<const double*>(stg + stage_offset_qs<Real, NQ>(m)) + slot; sQsv = kStageSlots; }
+        if (m & 4) { pQ0 = reinterpret_cast<const double*>(stg + stage_offset_q0<Real, NQ>(m)) + slot; sQ0v = kStageSlots; }
+    }
+    auto Rv = [&](int v) -> Real { return pR[v * sRv]; };
+    auto qsv = [&](int v) -> double { return pQs[v * sQsv]; };
+    auto q0v = [&](int v) -> double { return pQ0[v * sQ0v]; };
     if (a.mode == 0) {
 #pragma unroll
         for (int v = 0; v < NQ; ++v) R[v * nc + idx] = out[v];
     } else if (a.mode == 1) {
 #pragma unroll
-        for (int v = 0; v < NQ; ++v) R[v * nc + idx] += out[v];
+        for (int v = 0; v < NQ; ++v) R[v * nc + idx] = Rv(v) + out[v];
     } else if (a.mode == 2) {
         double qn[SIX ? NQ : 1];
+        // FP32 forms: the increment c1 dt R is formed in FP32 (R is an FP32
+        // quantity there) and widened by integer operations, so the FP64
+        // accumulation takes one FP64 operation per value, two with the q0
+        // term.  FP64 form: c1 (qs + dt R), the product skipped when c1 = 1.
+        [[maybe_unused]] float c1dt = 0.f;
+        if constexpr (sizeof(Real) == 4) c1dt = narrow_rn(a.c1 * a.dt);
+        const bool unit = a.c1 == 1.0;
 #pragma unroll
         for (int v = 0; v < NQ; ++v) {
-            const Real rv = a.acc_in ? R[v * nc + idx] + out[v] : out[v];
-            // FP32 accumulator widened by integer operations (a conversion
-            // instruction would take an FP64-pipe slot)
-            double rd;
-            if constexpr (sizeof(Real) == 4) rd = df_widen(rv);
-            else rd = rv;
-            const double s = fma(a.dt, rd, a.qs[v * nc + idx]);
-            double o = a.c1 * s;
-            if (a.c0 != 0.0) o = fma(a.c0, a.q0[v * nc + idx], o);
+            const Real rv = a.acc_in ? Rv(v) + out[v] : out[v];
+            double o;
+            if constexpr (sizeof(Real) == 4) {
+                o = fma(a.c1, qsv(v), widen_all(c1dt * rv));
+            } else {
+                o = fma(a.dt, rv, qsv(v));
+                if (!unit) o *= a.c1;
+            }
+            if (a.c0 != 0.0) o = fma(a.c0, q0v(v), o);
             if constexpr (SIX) qn[v] = o;
             else a.qout[v * nc + idx] = o;
         }
@@ -470,7 +546,7 @@ __device__ __forceinline__ void finish_cell(const SweepArgs& a, long long idx, c
     } else {
 #pragma unroll
         for (int v = 0; v < NQ; ++v) {
-            const Real rv = a.acc_in ? R[v * nc + idx] + out[v] : out[v];
+            const Real rv = a.acc_in ? Rv(v) + out[v] : out[v];
             a.out[v * nc + idx] = (double)rv;
         }
     }

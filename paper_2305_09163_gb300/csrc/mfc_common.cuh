@@ -65,6 +65,8 @@ struct SweepArgs {
     const uint4* mlp_frag;  // learned form: packed per-lane network fragments (device)
     float tau;              // learned form: discontinuity-sensor threshold
     int yz_stream;          // y/z sweeps: 1 = stream kernel, 0 = pencil marching
+    int stage;              // y/z stream kernels: finish operands staged in dynamic shared
+                            // memory by cp.async (bit 0: R, bit 1: qs, bit 2: q0; 0: none)
     int bound;              // learned form: range safeguard on learned edge values
     const float* grid[3];   // non-uniform directions: WENO5 table (GridCol layout), else null
     int grid_stride[3];     // x: cells per table value (n + 2); see GridCol

@@ -127,11 +127,22 @@ __device__ __forceinline__ df df_from_double(double d) {
 }
 
 // FP32 -> FP64 by integer operations (exact for normal numbers; zero and FP32
-// subnormals give 0).
+// subnormals give 0; infinities and NaNs are not mapped: the float-float
+// arithmetic of the FP64 path never forms them).
 __device__ __forceinline__ double df_widen(float f) {
     const unsigned b = (unsigned)__float_as_int(f);
     const unsigned ef = (b >> 23) & 0xFFu;
     const unsigned hw = (b & 0x80000000u) | ((ef + (1023u - 127u)) << 20) | ((b & 0x7FFFFFu) >> 3);
+    return ef ? __hiloint2double((int)hw, (int)(b << 29)) : 0.0;
+}
+
+// df_widen that also keeps infinities and NaNs (the FP32 forms' RK update,
+// where a non-finite right-hand side must reach the state and the CFL check).
+__device__ __forceinline__ double widen_all(float f) {
+    const unsigned b = (unsigned)__float_as_int(f);
+    const unsigned ef = (b >> 23) & 0xFFu;
+    const unsigned ed = ef == 0xFFu ? 0x7FFu : ef + (1023u - 127u);
+    const unsigned hw = (b & 0x80000000u) | (ed << 20) | ((b & 0x7FFFFFu) >> 3);
     return ef ? __hiloint2double((int)hw, (int)(b << 29)) : 0.0;
 }
 

@@ -13,6 +13,52 @@ constexpr int kElemThreads = 256;
 // so the two recomputed slots at its start cost about 0.1%.
 constexpr long long kStreamSlotsPerBlock = 16LL * kStreamThreads;
 
+// Finish operands a y/z stream launch stages in shared memory (SweepArgs::stage):
+// the R accumulator where the finish reads it, qs in an RK stage, q0 where the
+// stage has a q0 term.
+inline int stage_mask(const SweepArgs& a) {
+    switch (a.mode) {
+        case 1: return 1;
+        case 2: return (a.acc_in ? 1 : 0) | 2 | (a.c0 != 0.0 ? 4 : 0);
+        case 3: return a.acc_in ? 1 : 0;
+        default: return 0;
+    }
+}
+
+inline size_t stage_bytes_rt(int mask, int nq, size_t real_size) {
+    return (size_t)nq * kStageSlots *
+           (((mask & 1) ? real_size : 0) + ((mask & 2) ? sizeof(double) : 0) + ((mask & 4) ? sizeof(double) : 0));
+}
+
+// Launch one y/z stream kernel.  An entry built with staging (STAGE) gets its
+// finish operands staged, dropping q0, then qs, then R from the staging while
+// its shared memory would lower the number of CTAs resident per SM (the
+// kernels are latency-bound: residency comes first).
+template <typename Real, bool STAGE = false, typename Kernel>
+cudaError_t launch_yz_stream(Kernel kernel, unsigned blocks, SweepArgs a, int nq, cudaStream_t s) {
+    constexpr int threads = 32 * kRowsPerChunk;
+    int mask = STAGE ? stage_mask(a) : 0;
+    size_t dyn = 0;
+    if (mask) {
+        int occ0 = 0;
+        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ0, kernel, threads, 0);
+        if (e != cudaSuccess) return e;
+        for (; mask; mask &= ~(mask & 4 ? 4 : mask & 2 ? 2 : 1)) {
+            dyn = stage_bytes_rt(mask, nq, sizeof(Real));
+            e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
+            if (e != cudaSuccess) return e;
+            int occ = 0;
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kernel, threads, dyn);
+            if (e != cudaSuccess) return e;
+            if (occ >= occ0) break;
+        }
+        if (!mask) dyn = 0;
+    }
+    a.stage = mask;
+    kernel<<<blocks, threads, dyn, s>>>(a);
+    return cudaGetLastError();
+}
+
 // SIX: the six-equation model (stream kernels, WENO5, uniform grids).
 template <typename Real, int NF, bool LEARNED = false, int ORDER = 5, bool NONUNIF = false, bool SIX = false>
 cudaError_t launch_sweep(SweepArgs a, int ndim, int dir, cudaStream_t s) {
@@ -53,36 +99,43 @@ cudaError_t launch_sweep(SweepArgs a, int ndim, int dir, cudaStream_t s) {
     if (NONUNIF || SIX || a.yz_stream) {   // non-uniform grids, six-equation model: the stream kernel only
         // y/z stream kernel, one CTA per 32 x-lanes of a segment
         const unsigned blocks = (unsigned)((long long)((a.g.n[t1] + 31) / 32) * a.nseg * a.g.n[t2]);
+        auto nq = [](int nd) { return 2 * NF + nd + (SIX ? NF : 0); };
         if constexpr (LEARNED) {
             switch (ndim * 4 + dir) {
-                case 9: sweep_yz_stream_learned_kernel<NF, 2, 1><<<blocks, 32 * kRowsPerChunk, 0, s>>>(a); break;
-                case 13: sweep_yz_stream_learned_kernel<NF, 3, 1><<<blocks, 32 * kRowsPerChunk, 0, s>>>(a); break;
-                case 14: sweep_yz_stream_learned_kernel<NF, 3, 2><<<blocks, 32 * kRowsPerChunk, 0, s>>>(a); break;
+                case 9: return launch_yz_stream<Real, true>(sweep_yz_stream_learned_kernel<NF, 2, 1>, blocks, a, nq(2), s);
+                case 13: return launch_yz_stream<Real, true>(sweep_yz_stream_learned_kernel<NF, 3, 1>, blocks, a, nq(3), s);
+                case 14: return launch_yz_stream<Real, true>(sweep_yz_stream_learned_kernel<NF, 3, 2>, blocks, a, nq(3), s);
                 default: return cudaErrorInvalidValue;
             }
         } else if constexpr (sizeof(Real) == 8 && kBoundFp64) {
             switch (ndim * 4 + dir) {
-                case 9: sweep_yz_stream_f64_kernel<NF, 2, 1, ORDER, NONUNIF, SIX><<<blocks, 32 * kRowsPerChunk, 0, s>>>(a); break;
-                case 13: sweep_yz_stream_f64_kernel<NF, 3, 1, ORDER, NONUNIF, SIX><<<blocks, 32 * kRowsPerChunk, 0, s>>>(a); break;
-                case 14: sweep_yz_stream_f64_kernel<NF, 3, 2, ORDER, NONUNIF, SIX><<<blocks, 32 * kRowsPerChunk, 0, s>>>(a); break;
+                case 9: return launch_yz_stream<Real, !NONUNIF>(sweep_yz_stream_f64_kernel<NF, 2, 1, ORDER, NONUNIF, SIX>, blocks, a, nq(2), s);
+                case 13: return launch_yz_stream<Real, !NONUNIF>(sweep_yz_stream_f64_kernel<NF, 3, 1, ORDER, NONUNIF, SIX>, blocks, a, nq(3), s);
+                case 14: return launch_yz_stream<Real, !NONUNIF>(sweep_yz_stream_f64_kernel<NF, 3, 2, ORDER, NONUNIF, SIX>, blocks, a, nq(3), s);
                 default: return cudaErrorInvalidValue;
             }
         } else if constexpr (SIX && sizeof(Real) == 4) {
             switch (ndim * 4 + dir) {
-                case 9: sweep_yz_stream_six32_kernel<NF, 2, 1, ORDER, NONUNIF><<<blocks, 32 * kRowsPerChunk, 0, s>>>(a); break;
-                case 13: sweep_yz_stream_six32_kernel<NF, 3, 1, ORDER, NONUNIF><<<blocks, 32 * kRowsPerChunk, 0, s>>>(a); break;
-                case 14: sweep_yz_stream_six32_kernel<NF, 3, 2, ORDER, NONUNIF><<<blocks, 32 * kRowsPerChunk, 0, s>>>(a); break;
+                case 9: return launch_yz_stream<Real, true>(sweep_yz_stream_six32_kernel<NF, 2, 1, ORDER, NONUNIF>, blocks, a, nq(2), s);
+                case 13: return launch_yz_stream<Real, true>(sweep_yz_stream_six32_kernel<NF, 3, 1, ORDER, NONUNIF>, blocks, a, nq(3), s);
+                case 14: return launch_yz_stream<Real, true>(sweep_yz_stream_six32_kernel<NF, 3, 2, ORDER, NONUNIF>, blocks, a, nq(3), s);
+                default: return cudaErrorInvalidValue;
+            }
+        } else if constexpr (sizeof(Real) == 4 && !NONUNIF) {
+            switch (ndim * 4 + dir) {
+                case 9: return launch_yz_stream<Real, true>(sweep_yz_stream_f32_kernel<NF, 2, 1, ORDER>, blocks, a, nq(2), s);
+                case 13: return launch_yz_stream<Real, true>(sweep_yz_stream_f32_kernel<NF, 3, 1, ORDER>, blocks, a, nq(3), s);
+                case 14: return launch_yz_stream<Real, true>(sweep_yz_stream_f32_kernel<NF, 3, 2, ORDER>, blocks, a, nq(3), s);
                 default: return cudaErrorInvalidValue;
             }
         } else {
             switch (ndim * 4 + dir) {
-                case 9: sweep_yz_stream_kernel<Real, NF, 2, 1, ORDER, NONUNIF, SIX><<<blocks, 32 * kRowsPerChunk, 0, s>>>(a); break;
-                case 13: sweep_yz_stream_kernel<Real, NF, 3, 1, ORDER, NONUNIF, SIX><<<blocks, 32 * kRowsPerChunk, 0, s>>>(a); break;
-                case 14: sweep_yz_stream_kernel<Real, NF, 3, 2, ORDER, NONUNIF, SIX><<<blocks, 32 * kRowsPerChunk, 0, s>>>(a); break;
+                case 9: return launch_yz_stream<Real, sizeof(Real) == 8>(sweep_yz_stream_kernel<Real, NF, 2, 1, ORDER, NONUNIF, SIX>, blocks, a, nq(2), s);
+                case 13: return launch_yz_stream<Real, sizeof(Real) == 8>(sweep_yz_stream_kernel<Real, NF, 3, 1, ORDER, NONUNIF, SIX>, blocks, a, nq(3), s);
+                case 14: return launch_yz_stream<Real, sizeof(Real) == 8>(sweep_yz_stream_kernel<Real, NF, 3, 2, ORDER, NONUNIF, SIX>, blocks, a, nq(3), s);
                 default: return cudaErrorInvalidValue;
             }
         }
-        return cudaGetLastError();
     }
     if constexpr (NONUNIF || SIX) return cudaErrorInvalidValue;
     const long long warps = (long long)((a.g.n[t1] + 31) / 32) * a.nseg * a.g.n[t2];

@@ -375,7 +375,10 @@ __global__ void __launch_bounds__(kStreamThreads, 4) sweep_x_stream_f64_kernel(c
 // ---------------------------------------------------------------------------
 constexpr int kRowsPerChunk = 4;
 
-template <typename Real, int NF, int NDIM, int DIR, bool LEARNED, int ORDER, bool NONUNIF = false, bool SIX = false>
+// STAGE: the kernel stages its finish operands (a.stage) in dynamic shared
+// memory; entries without it keep the plain loads (and their registers).
+template <typename Real, int NF, int NDIM, int DIR, bool LEARNED, int ORDER, bool NONUNIF = false, bool SIX = false,
+          bool STAGE = false>
 __device__ __forceinline__ void sweep_yz_stream_body(const SweepArgs& a) {
     static_assert(!SIX || !LEARNED, "six-equation model: FP64 and mixed forms");
     static_assert(!NONUNIF || (!LEARNED && ORDER == 5), "non-uniform grids: WENO5, FP64 and mixed forms");
@@ -393,6 +396,8 @@ __device__ __forceinline__ void sweep_yz_stream_body(const SweepArgs& a) {
     __shared__ Real sh_eL[NS][kRowsPerChunk + 1][32];
     __shared__ Real sh_eLJ[NJ][kRowsPerChunk + 1][32];
     __shared__ Real sh_F[NQ + 1][kRowsPerChunk + 1][32];
+    extern __shared__ __align__(16) unsigned char stage_smem[];   // a.stage operands
+    static_assert(32 * kRowsPerChunk == kStageSlots, "one staging slot per thread");
     const Real* __restrict__ w = static_cast<const Real*>(a.w);
     const int lane = threadIdx.x & 31, row = threadIdx.x >> 5;
     const int n1 = a.g.n[T1], n2 = a.g.n[T2], nd = a.g.n[DIR];
@@ -451,6 +456,11 @@ __device__ __forceinline__ void sweep_yz_stream_body(const SweepArgs& a) {
         if (pf) load(inext, nxt);
         const int c = base + row;       // edge cell of this warp (warp-uniform)
         const bool live = c <= s1;
+        const bool fin = live && c >= s0 + 1 && active;   // this lane finishes cell c-1 in this chunk
+        if constexpr (STAGE) {
+            if (a.stage && fin)
+                stage_finish_operands<Real, NQ>(a, basei + (long long)(c - 1) * sd, stage_smem, threadIdx.x);
+        }
         Real cell[NS], cm1[NS], eL[NS], eR[NS], eLJ[NS], eRJ[NS];
         if (live) {
             if constexpr (LEARNED) {
@@ -524,14 +534,21 @@ __device__ __forceinline__ void sweep_yz_stream_body(const SweepArgs& a) {
             sh_F[NQ][row + 1][lane] = ut;
         }
         __syncthreads();
-        if (has_face && c >= s0 + 1 && active) {
+        if (fin) {
             Real Fm[NQ];
 #pragma unroll
             for (int q = 0; q < NQ; ++q) Fm[q] = sh_F[q][row][lane];
+            const unsigned char* stg = nullptr;
+            if constexpr (STAGE) {
+                if (a.stage) {
+                    cp_async_wait_all();
+                    stg = stage_smem;
+                }
+            }
             finish_cell<Real, NF, NDIM, DIR, SIX>(a, basei + (long long)(c - 1) * sd, Fm, F, sh_F[NQ][row][lane], ut, cm1,
                                              NONUNIF ? grid_inv_dx<false>(a.grid[DIR], a.grid_stride[DIR], c - 1, Real(0))
                                                      : inv_dx,
-                                             c - 1, sd, (long long)t1 + (long long)n1 * t2);
+                                             c - 1, sd, (long long)t1 + (long long)n1 * t2, stg, threadIdx.x);
         }
         __syncthreads();
         // carry the last row of the chunk into row 0
@@ -551,13 +568,22 @@ __device__ __forceinline__ void sweep_yz_stream_body(const SweepArgs& a) {
     }
 }
 
-// The y/z stream kernel of the FP32 forms.  The learned form gets its own
-// entry with a register bound (4 CTAs per SM for two fluids) so that enough
-// warps stay resident; the mixed form keeps the compiler's own allocation,
-// which schedules its loads better.
+// The y/z stream kernel (FP64 uniform WENO5 forms, with staged finish
+// operands, and the mixed form on non-uniform grids, without: staging took
+// it from 96 to 123 registers): the compiler's own register allocation.
 template <typename Real, int NF, int NDIM, int DIR, int ORDER = 5, bool NONUNIF = false, bool SIX = false>
 __global__ void __launch_bounds__(32 * kRowsPerChunk) sweep_yz_stream_kernel(const SweepArgs a) {
-    sweep_yz_stream_body<Real, NF, NDIM, DIR, false, ORDER, NONUNIF, SIX>(a);
+    sweep_yz_stream_body<Real, NF, NDIM, DIR, false, ORDER, NONUNIF, SIX, sizeof(Real) == 8>(a);
+}
+
+// The mixed form's five-equation y/z stream kernel on uniform grids, with
+// staged finish operands: bounded to 8 CTAs per SM for up to two fluids (64
+// registers, no spills), 5 for three, so that the registers allow the
+// residency the staging's shared memory does.  The learned form gets its own
+// entry below.
+template <int NF, int NDIM, int DIR, int ORDER = 5>
+__global__ void __launch_bounds__(32 * kRowsPerChunk, NF <= 2 ? 8 : 5) sweep_yz_stream_f32_kernel(const SweepArgs a) {
+    sweep_yz_stream_body<float, NF, NDIM, DIR, false, ORDER, false, false, true>(a);
 }
 
 // The mixed form's six-equation y/z sweep: bounded to 5 CTAs per SM (96
@@ -566,17 +592,20 @@ __global__ void __launch_bounds__(32 * kRowsPerChunk) sweep_yz_stream_kernel(con
 // five-equation kernels by half, hence a separate entry.
 template <int NF, int NDIM, int DIR, int ORDER = 5, bool NONUNIF = false>
 __global__ void __launch_bounds__(32 * kRowsPerChunk, 5) sweep_yz_stream_six32_kernel(const SweepArgs a) {
-    sweep_yz_stream_body<float, NF, NDIM, DIR, false, ORDER, NONUNIF, true>(a);
+    sweep_yz_stream_body<float, NF, NDIM, DIR, false, ORDER, NONUNIF, true, true>(a);
 }
 
+// The bounded FP64 y/z stream kernel (stretched-grid, six-equation and WENO3
+// forms, 4 CTAs per SM).  Staging pays for WENO3 (40.7 -> 39.2 ms per step at
+// 256^3), not on stretched grids (70.0 -> 71.8 ms, more spills at the bound).
 template <int NF, int NDIM, int DIR, int ORDER = 5, bool NONUNIF = false, bool SIX = false>
 __global__ void __launch_bounds__(32 * kRowsPerChunk, 4) sweep_yz_stream_f64_kernel(const SweepArgs a) {
-    sweep_yz_stream_body<double, NF, NDIM, DIR, false, ORDER, NONUNIF, SIX>(a);
+    sweep_yz_stream_body<double, NF, NDIM, DIR, false, ORDER, NONUNIF, SIX, !NONUNIF>(a);
 }
 
 template <int NF, int NDIM, int DIR>
 __global__ void __launch_bounds__(32 * kRowsPerChunk, NF <= 2 ? 4 : 3) sweep_yz_stream_learned_kernel(const SweepArgs a) {
-    sweep_yz_stream_body<float, NF, NDIM, DIR, true, 5>(a);
+    sweep_yz_stream_body<float, NF, NDIM, DIR, true, 5, false, false, true>(a);
 }
 
 }  // namespace mfc

@@ -216,3 +216,32 @@ def test_integer_narrowing_rounds_to_nearest_even():
     # the largest significand rounds up into the next binade
     y = np.nextafter(np.float64(2.0), 0.0)
     assert narrow(np.array([y]))[0] == np.float32(2.0)
+
+
+def widen_all(f):
+    """float -> double by integer operations on the bit pattern, infinities
+    and NaNs included (the FP32 forms' RK update widens c1 dt R this way)."""
+    b = np.asarray(f, dtype=np.float32).view(np.uint32).astype(np.uint64)
+    ef = (b >> np.uint64(23)) & np.uint64(0xFF)
+    ed = np.where(ef == 0xFF, np.uint64(0x7FF), ef + np.uint64(1023 - 127))
+    hw = (b & np.uint64(0x80000000)) | (ed << np.uint64(20)) | ((b & np.uint64(0x7FFFFF)) >> np.uint64(3))
+    lw = (b << np.uint64(29)) & np.uint64(0xFFFFFFFF)
+    d = ((hw << np.uint64(32)) | lw).view(np.float64)
+    return np.where(ef == 0, 0.0, d)
+
+
+def test_integer_widening_is_the_exact_conversion():
+    """Equal to IEEE widening for every normal float, keeps infinities and
+    NaNs (so a non-finite right-hand side reaches the state and the CFL
+    check), and flushes FP32 subnormals to zero like the FTZ arithmetic."""
+    rng = np.random.default_rng(5)
+    bits = rng.integers(0, 2 ** 32, 1_000_000, dtype=np.uint64).astype(np.uint32)
+    f = bits.view(np.float32)
+    normal = np.isfinite(f) & (np.abs(f) >= np.float32(2.0 ** -126))
+    assert np.array_equal(widen_all(f[normal]), f[normal].astype(np.float64))
+    special = np.array([np.inf, -np.inf, np.nan, np.float32(2.0 ** -130), -np.float32(2.0 ** -140), 0.0],
+                       dtype=np.float32)
+    w = widen_all(special)
+    assert w[0] == np.inf and w[1] == -np.inf and np.isnan(w[2])
+    assert np.all(w[3:] == 0.0)
+    assert np.isnan(widen_all(f[np.isnan(f)])).all()
