@@ -85,6 +85,13 @@ cudaError_t launch_sweep(SweepArgs a, int ndim, int dir, cudaStream_t s) {
                 case 3: sweep_x_stream_f64_kernel<NF, 3, ORDER, NONUNIF, SIX><<<blocks, kStreamThreads, 0, s>>>(a); break;
                 default: return cudaErrorInvalidValue;
             }
+        } else if constexpr (sizeof(Real) == 4 && !NONUNIF && !SIX) {
+            switch (ndim) {
+                case 1: sweep_x_stream_f32_kernel<NF, 1, ORDER><<<blocks, kStreamThreads, 0, s>>>(a); break;
+                case 2: sweep_x_stream_f32_kernel<NF, 2, ORDER><<<blocks, kStreamThreads, 0, s>>>(a); break;
+                case 3: sweep_x_stream_f32_kernel<NF, 3, ORDER><<<blocks, kStreamThreads, 0, s>>>(a); break;
+                default: return cudaErrorInvalidValue;
+            }
         } else {
             switch (ndim) {
                 case 1: sweep_x_stream_kernel<Real, NF, 1, LEARNED, ORDER, NONUNIF, SIX><<<blocks, kStreamThreads, 0, s>>>(a); break;

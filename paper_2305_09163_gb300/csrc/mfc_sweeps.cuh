@@ -162,9 +162,15 @@ __device__ __forceinline__ void sweep_x_stream_body(const SweepArgs& a) {
     constexpr int NS = Lay::NS, IM = Lay::IM;
     constexpr int NQ = Layout<NF, NDIM, SIX>::NQ;   // flux rows
     constexpr int NJ = LEARNED ? NS : 1;
-    __shared__ Real sh_eL[NS][kStreamThreads + 1];
-    __shared__ Real sh_eLJ[NJ][kStreamThreads + 1];
-    __shared__ Real sh_F[NQ + 1][kStreamThreads + 1];
+    // Edge values and face fluxes of slot s sit at position s mod ER of a ring
+    // of ER = kStreamThreads + 1: a chunk writes its 128 slots and reads their
+    // left neighbours, the first of which the previous chunk wrote; the next
+    // chunk overwrites it (s + 128 = s - 1 mod ER) only after the barriers that
+    // order it.
+    constexpr int ER = kStreamThreads + 1;
+    __shared__ Real sh_eL[NS][ER];
+    __shared__ Real sh_eLJ[NJ][ER];
+    __shared__ Real sh_F[NQ + 1][ER];
     const Real* __restrict__ w = static_cast<const Real*>(a.w);
     const int n = a.g.n[0];
     const long long rowlen = (long long)n + 2;
@@ -191,7 +197,11 @@ __device__ __forceinline__ void sweep_x_stream_body(const SweepArgs& a) {
     long long srow = 0;
     int scol = 0;  // slot index within its row, 0..n+1
     bool placed = false;
+    // ring position of this lane's slot (own0 - 2 + t) mod ER, then one step
+    // back per chunk
+    int pos = (int)(((own0 - 2 + t) % ER + ER) % ER);
     for (long long base = own0 - 2; base < own1; base += kStreamThreads) {
+        const int pl = pos == 0 ? ER - 1 : pos - 1;   // left neighbour's position
         const long long s = base + t;
         if (s >= 0 && !placed) {
             srow = s / rowlen;
@@ -292,8 +302,8 @@ __device__ __forceinline__ void sweep_x_stream_body(const SweepArgs& a) {
         if (live) {
 #pragma unroll
             for (int q = 0; q < NS; ++q) {
-                sh_eL[q][t + 1] = eL[q];
-                if constexpr (LEARNED) sh_eLJ[q][t + 1] = eLJ[q];
+                sh_eL[q][pos] = eL[q];
+                if constexpr (LEARNED) sh_eLJ[q][pos] = eLJ[q];
             }
         }
         __syncthreads();
@@ -302,40 +312,36 @@ __device__ __forceinline__ void sweep_x_stream_body(const SweepArgs& a) {
         if (has_face) {
             Real lft[NS];
 #pragma unroll
-            for (int q = 0; q < NS; ++q) lft[q] = sh_eL[q][t];
+            for (int q = 0; q < NS; ++q) lft[q] = sh_eL[q][pl];
             if constexpr (LEARNED) {
                 Real lftJ[NS];
 #pragma unroll
-                for (int q = 0; q < NS; ++q) lftJ[q] = sh_eLJ[q][t];
+                for (int q = 0; q < NS; ++q) lftJ[q] = sh_eLJ[q][pl];
                 face_flux_learned<NF, NDIM, 0>(a, e, lft, eR, lftJ, eRJ, cm1, cell, F, ut);
             } else {
                 face_flux<Real, NF, NDIM, 0, SIX>(a, e, lft, eR, cm1, cell, F, ut);
             }
 #pragma unroll
-            for (int q = 0; q < NQ; ++q) sh_F[q][t + 1] = F[q];
-            sh_F[NQ][t + 1] = ut;
+            for (int q = 0; q < NQ; ++q) sh_F[q][pos] = F[q];
+            sh_F[NQ][pos] = ut;
         }
         __syncthreads();
         if (has_face && s >= own0 && c >= 1) {
             Real Fm[NQ];
 #pragma unroll
-            for (int q = 0; q < NQ; ++q) Fm[q] = sh_F[q][t];
-            finish_cell<Real, NF, NDIM, 0, SIX>(a, rowoff + (c - 1), Fm, F, sh_F[NQ][t], ut, cm1,
+            for (int q = 0; q < NQ; ++q) Fm[q] = sh_F[q][pl];
+            finish_cell<Real, NF, NDIM, 0, SIX>(a, rowoff + (c - 1), Fm, F, sh_F[NQ][pl], ut, cm1,
                                            NONUNIF ? grid_inv_dx<true>(a.grid[0], a.grid_stride[0], c - 1, Real(0)) : inv_dx,
                                            c - 1, 1, row);
         }
-        __syncthreads();
-        // carry the last slot of the chunk into position 0
-        if (t == kStreamThreads - 1) {
-#pragma unroll
-            for (int q = 0; q < NS; ++q) {
-                sh_eL[q][0] = sh_eL[q][kStreamThreads];
-                if constexpr (LEARNED) sh_eLJ[q][0] = sh_eLJ[q][kStreamThreads];
-            }
-#pragma unroll
-            for (int q = 0; q <= NQ; ++q) sh_F[q][0] = sh_F[q][kStreamThreads];
-        }
-        __syncthreads();
+        // No barrier is needed here: the next chunk writes edge values
+        // (position pl of this chunk) after this chunk's second barrier, which
+        // follows every read of them, and fluxes after its own first barrier,
+        // which follows every finish of this chunk.  The FP64 kernels keep one
+        // (measured: their warps in step ran the 256^3 step 58.6 instead of
+        // 60.1 ms).
+        if constexpr (sizeof(Real) == 8) __syncthreads();
+        pos = pl;
     }
     if constexpr (LEARNED) {
         if ((threadIdx.x & 31) == 0 && net_rows && a.net_rows) atomicAdd(a.net_rows, net_rows);
@@ -345,6 +351,13 @@ __device__ __forceinline__ void sweep_x_stream_body(const SweepArgs& a) {
 template <typename Real, int NF, int NDIM, bool LEARNED = false, int ORDER = 5, bool NONUNIF = false, bool SIX = false>
 __global__ void __launch_bounds__(kStreamThreads) sweep_x_stream_kernel(const SweepArgs a) {
     sweep_x_stream_body<Real, NF, NDIM, LEARNED, ORDER, NONUNIF, SIX>(a);
+}
+
+// The mixed form's five-equation x stream kernel on uniform grids, bounded to
+// 7 CTAs per SM for up to two fluids (72 registers), 5 for three.
+template <int NF, int NDIM, int ORDER = 5>
+__global__ void __launch_bounds__(kStreamThreads, NF <= 2 ? 7 : 5) sweep_x_stream_f32_kernel(const SweepArgs a) {
+    sweep_x_stream_body<float, NF, NDIM, false, ORDER, false, false>(a);
 }
 
 // The learned form's x sweep bounded to 4 CTAs per SM (128 registers, 32
@@ -392,10 +405,15 @@ __device__ __forceinline__ void sweep_yz_stream_body(const SweepArgs& a) {
     constexpr int T1 = 0;
     constexpr int T2 = (DIR == 2) ? 1 : 2;
     constexpr int RING = 2 * kRowsPerChunk;  // rows base-2 .. base+5 of a chunk
+    // Edge values and face fluxes of cell c sit in row c mod ER of a ring of
+    // ER = kRowsPerChunk + 1 rows: a chunk writes its four cells and reads
+    // their left neighbours, the last of which the previous chunk wrote, and the
+    // next chunk overwrites that row only after the barriers that order it.
+    constexpr int ER = kRowsPerChunk + 1;
     __shared__ Real ring[RING][NS][32];
-    __shared__ Real sh_eL[NS][kRowsPerChunk + 1][32];
-    __shared__ Real sh_eLJ[NJ][kRowsPerChunk + 1][32];
-    __shared__ Real sh_F[NQ + 1][kRowsPerChunk + 1][32];
+    __shared__ Real sh_eL[NS][ER][32];
+    __shared__ Real sh_eLJ[NJ][ER][32];
+    __shared__ Real sh_F[NQ + 1][ER][32];
     extern __shared__ __align__(16) unsigned char stage_smem[];   // a.stage operands
     static_assert(32 * kRowsPerChunk == kStageSlots, "one staging slot per thread");
     const Real* __restrict__ w = static_cast<const Real*>(a.w);
@@ -435,6 +453,7 @@ __device__ __forceinline__ void sweep_yz_stream_body(const SweepArgs& a) {
         if (flip) out[IM + DIR] = -out[IM + DIR];
     };
     auto slot = [](int i) { return ((i % RING) + RING) % RING; };
+    auto eslot = [](int i) { return (i + 2 * ER) % ER; };   // i >= -2
     // prologue: rows s0-3 .. s0+4 (cells base-2 .. base+5 of the first chunk)
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
@@ -505,8 +524,8 @@ __device__ __forceinline__ void sweep_yz_stream_body(const SweepArgs& a) {
             }
 #pragma unroll
             for (int q = 0; q < NS; ++q) {
-                sh_eL[q][row + 1][lane] = eL[q];
-                if constexpr (LEARNED) sh_eLJ[q][row + 1][lane] = eLJ[q];
+                sh_eL[q][eslot(c)][lane] = eL[q];
+                if constexpr (LEARNED) sh_eLJ[q][eslot(c)][lane] = eLJ[q];
             }
         }
         __syncthreads();
@@ -520,24 +539,24 @@ __device__ __forceinline__ void sweep_yz_stream_body(const SweepArgs& a) {
         if (has_face) {
             Real lft[NS];
 #pragma unroll
-            for (int q = 0; q < NS; ++q) lft[q] = sh_eL[q][row][lane];
+            for (int q = 0; q < NS; ++q) lft[q] = sh_eL[q][eslot(c - 1)][lane];
             if constexpr (LEARNED) {
                 Real lftJ[NS];
 #pragma unroll
-                for (int q = 0; q < NS; ++q) lftJ[q] = sh_eLJ[q][row][lane];
+                for (int q = 0; q < NS; ++q) lftJ[q] = sh_eLJ[q][eslot(c - 1)][lane];
                 face_flux_learned<NF, NDIM, DIR>(a, e, lft, eR, lftJ, eRJ, cm1, cell, F, ut);
             } else {
                 face_flux<Real, NF, NDIM, DIR, SIX>(a, e, lft, eR, cm1, cell, F, ut);
             }
 #pragma unroll
-            for (int q = 0; q < NQ; ++q) sh_F[q][row + 1][lane] = F[q];
-            sh_F[NQ][row + 1][lane] = ut;
+            for (int q = 0; q < NQ; ++q) sh_F[q][eslot(c)][lane] = F[q];
+            sh_F[NQ][eslot(c)][lane] = ut;
         }
         __syncthreads();
         if (fin) {
             Real Fm[NQ];
 #pragma unroll
-            for (int q = 0; q < NQ; ++q) Fm[q] = sh_F[q][row][lane];
+            for (int q = 0; q < NQ; ++q) Fm[q] = sh_F[q][eslot(c - 1)][lane];
             const unsigned char* stg = nullptr;
             if constexpr (STAGE) {
                 if (a.stage) {
@@ -545,23 +564,19 @@ __device__ __forceinline__ void sweep_yz_stream_body(const SweepArgs& a) {
                     stg = stage_smem;
                 }
             }
-            finish_cell<Real, NF, NDIM, DIR, SIX>(a, basei + (long long)(c - 1) * sd, Fm, F, sh_F[NQ][row][lane], ut, cm1,
+            finish_cell<Real, NF, NDIM, DIR, SIX>(a, basei + (long long)(c - 1) * sd, Fm, F,
+                                             sh_F[NQ][eslot(c - 1)][lane], ut, cm1,
                                              NONUNIF ? grid_inv_dx<false>(a.grid[DIR], a.grid_stride[DIR], c - 1, Real(0))
                                                      : inv_dx,
                                              c - 1, sd, (long long)t1 + (long long)n1 * t2, stg, threadIdx.x);
         }
-        __syncthreads();
-        // carry the last row of the chunk into row 0
-        if (row == kRowsPerChunk - 1) {
-#pragma unroll
-            for (int q = 0; q < NS; ++q) {
-                sh_eL[q][0][lane] = sh_eL[q][kRowsPerChunk][lane];
-                if constexpr (LEARNED) sh_eLJ[q][0][lane] = sh_eLJ[q][kRowsPerChunk][lane];
-            }
-#pragma unroll
-            for (int q = 0; q <= NQ; ++q) sh_F[q][0][lane] = sh_F[q][kRowsPerChunk][lane];
-        }
-        __syncthreads();
+        // No barrier is needed here: the next chunk writes edge values (row
+        // c+4 = c-1 mod ER) after this chunk's second barrier, which follows
+        // every read of them, and fluxes after its own first barrier, which
+        // follows every finish of this chunk.  The FP64 kernels keep one
+        // (measured: their warps in step ran the 256^3 step 58.6 instead of
+        // 60.1 ms).
+        if constexpr (sizeof(Real) == 8) __syncthreads();
     }
     if constexpr (LEARNED) {
         if ((threadIdx.x & 31) == 0 && net_rows && a.net_rows) atomicAdd(a.net_rows, net_rows);
