@@ -79,10 +79,10 @@ FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 BYTES_MIXED_SWEEPS_STAGE = (56 + 84 + (168 + 224 + 224) / 3.0)
 # DRAM bytes per cell of one FP64 sweep launch, averaged over the x, y and z
 # sweeps of a stage: dram__bytes_read.sum + dram__bytes_write.sum of one ncu
-# capture of the 160^3 shock-bubble (x 102.6, y 158.6, z 279.0 B/cell; the
+# capture of the 160^3 shock-bubble (x 102.7, y 158.7, z 279.0 B/cell; the
 # algorithmic w + R (+ RK states) bytes are 112, 168 and 280), scaled to the
 # bench size by the cell count.  Must be re-measured when the FP64 sweeps change.
-FP64_SWEEP_DRAM_BYTES_PER_CELL = (102.6 + 158.6 + 279.0) / 3.0
+FP64_SWEEP_DRAM_BYTES_PER_CELL = (102.7 + 158.7 + 279.0) / 3.0
 # Useful tensor-core FLOPs of the learned network per stencil
 # (5x32 + 32x32 + 32x3 multiply-adds) and stencils per cell and sweep (2 edges x 7 variables).
 FLOP_MLP_STENCIL = 2 * (5 * 32 + 32 * 32 + 32 * 3)
