@@ -410,6 +410,38 @@ __host__ __device__ constexpr size_t stage_bytes(int mask) {
     return stage_offset_q0<Real, NQ>(mask) + ((mask & 4) ? (size_t)NQ * kStageSlots * sizeof(double) : 0);
 }
 
+// Finish operands of a sweep launch, as a staging mask: the R accumulator
+// where the finish reads it, qs in an RK stage, q0 where the stage has a q0
+// term.
+__host__ __device__ inline int stage_mask(const SweepArgs& a) {
+    switch (a.mode) {
+        case 1: return 1;
+        case 2: return (a.acc_in ? 1 : 0) | 2 | (a.c0 != 0.0 ? 4 : 0);
+        case 3: return a.acc_in ? 1 : 0;
+        default: return 0;
+    }
+}
+
+// The finish operands in mask m that are not staged: an L2 prefetch when the
+// chunk starts, so that the finish's own loads meet L2 rather than DRAM.
+template <typename Real, int NQ>
+__device__ __forceinline__ void prefetch_finish_operands(const SweepArgs& a, long long idx, int m) {
+    const long long nc = a.g.ncell;
+    if (m & 1) {
+        const Real* R = static_cast<const Real*>(a.R);
+#pragma unroll
+        for (int v = 0; v < NQ; ++v) asm volatile("prefetch.global.L2 [%0];" ::"l"(R + v * nc + idx));
+    }
+    if (m & 2) {
+#pragma unroll
+        for (int v = 0; v < NQ; ++v) asm volatile("prefetch.global.L2 [%0];" ::"l"(a.qs + v * nc + idx));
+    }
+    if (m & 4) {
+#pragma unroll
+        for (int v = 0; v < NQ; ++v) asm volatile("prefetch.global.L2 [%0];" ::"l"(a.q0 + v * nc + idx));
+    }
+}
+
 template <typename Real, int NQ>
 __device__ __forceinline__ void stage_finish_operands(const SweepArgs& a, long long idx, unsigned char* stg, int slot) {
     const long long nc = a.g.ncell;

@@ -13,18 +13,6 @@ constexpr int kElemThreads = 256;
 // so the two recomputed slots at its start cost about 0.1%.
 constexpr long long kStreamSlotsPerBlock = 16LL * kStreamThreads;
 
-// Finish operands a y/z stream launch stages in shared memory (SweepArgs::stage):
-// the R accumulator where the finish reads it, qs in an RK stage, q0 where the
-// stage has a q0 term.
-inline int stage_mask(const SweepArgs& a) {
-    switch (a.mode) {
-        case 1: return 1;
-        case 2: return (a.acc_in ? 1 : 0) | 2 | (a.c0 != 0.0 ? 4 : 0);
-        case 3: return a.acc_in ? 1 : 0;
-        default: return 0;
-    }
-}
-
 inline size_t stage_bytes_rt(int mask, int nq, size_t real_size) {
     return (size_t)nq * kStageSlots *
            (((mask & 1) ? real_size : 0) + ((mask & 2) ? sizeof(double) : 0) + ((mask & 4) ? sizeof(double) : 0));

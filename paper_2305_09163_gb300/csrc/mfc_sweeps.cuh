@@ -219,6 +219,15 @@ __device__ __forceinline__ void sweep_x_stream_body(const SweepArgs& a) {
                 ++srow;
             }
         }
+        if constexpr (LEARNED) {
+            // the learned sweep keeps 16 warps per SM: pull the next chunk's
+            // cells into L1 while this chunk computes
+            if (placed && base + kStreamThreads + t < own1 && srow < nrows) {
+                const float* nx = w + srow * n + min(max(scol - 1, 0), n - 1);
+#pragma unroll
+                for (int q = 0; q < NS; ++q) asm volatile("prefetch.global.L1 [%0];" ::"l"(nx + q * nc));
+            }
+        }
         Real cell[NS], cm1[NS], eL[NS], eR[NS], eLJ[NS], eRJ[NS];
         if constexpr (LEARNED) {
             // the five cells of this lane's stencil, re-read (L1) per variable
@@ -476,9 +485,19 @@ __device__ __forceinline__ void sweep_yz_stream_body(const SweepArgs& a) {
         const int c = base + row;       // edge cell of this warp (warp-uniform)
         const bool live = c <= s1;
         const bool fin = live && c >= s0 + 1 && active;   // this lane finishes cell c-1 in this chunk
-        if constexpr (STAGE) {
-            if (a.stage && fin)
-                stage_finish_operands<Real, NQ>(a, basei + (long long)(c - 1) * sd, stage_smem, threadIdx.x);
+        if (fin) {
+            const long long fidx = basei + (long long)(c - 1) * sd;
+            int staged = 0;
+            if constexpr (STAGE) {
+                staged = a.stage;
+                if (staged) stage_finish_operands<Real, NQ>(a, fidx, stage_smem, threadIdx.x);
+            }
+            // FP32 five-equation forms only: measured faster there (mixed 6.46 ->
+            // 6.27, learned 14.2 -> 12.8, mixed stretched 10.3 -> 8.7 ms per step
+            // at 256^3), not for the FP64 stretched-grid (70.3 -> 70.6) or the
+            // six-equation sweeps (mixed 16.9 -> 17.2)
+            if constexpr (sizeof(Real) == 4 && !SIX)
+                prefetch_finish_operands<Real, NQ>(a, fidx, stage_mask(a) & ~staged);
         }
         Real cell[NS], cm1[NS], eL[NS], eR[NS], eLJ[NS], eRJ[NS];
         if (live) {
