@@ -145,10 +145,11 @@ __global__ void __launch_bounds__(128) sweep_kernel(const SweepArgs a) {
 // per lane: lane s reconstructs the edges of its cell c (five-cell stencil read
 // straight from global memory, consecutive lanes = consecutive x), forms the
 // face c-1/2 from its own right-side value and the left-side value of slot s-1
-// (shared memory), and finishes cell c-1 from faces c-3/2 and c-1/2.  The last
-// slot's left-side value and flux carry to the next chunk, and each CTA starts
-// two slots early so that its first cell has both faces.  Every lane takes part
-// in every chunk, as the learned form's warp-level network needs.
+// (shared memory), and finishes cell c-1 from faces c-3/2 and c-1/2.  The
+// left-side values and fluxes sit in rings indexed by slot, so the next chunk
+// reads the last slot's ones where this chunk wrote them; each CTA starts two
+// slots early so that its first cell has both faces.  Every lane takes part in
+// every chunk, as the learned form's warp-level network needs.
 // ---------------------------------------------------------------------------
 constexpr int kStreamThreads = 128;
 
@@ -307,7 +308,8 @@ __device__ __forceinline__ void sweep_x_stream_body(const SweepArgs& a) {
 #pragma unroll
             for (int q = 0; q < NS; ++q) cell[q] = vcv[q];
         }
-        // left-side values of this chunk; slot 0 holds the carry from the last chunk
+        // left-side values of this chunk (the last chunk's last slot stays at
+        // the position before this chunk's first)
         if (live) {
 #pragma unroll
             for (int q = 0; q < NS; ++q) {
@@ -384,14 +386,15 @@ __global__ void __launch_bounds__(kStreamThreads, 4) sweep_x_stream_f64_kernel(c
 }
 
 // ---------------------------------------------------------------------------
-// y or z sweep as a coalesced stream (FP32 paths).  A CTA of 4 warps covers 32
+// y or z sweep as a coalesced stream.  A CTA of 4 warps covers 32
 // consecutive x (lanes) of one pencil segment s0..s1-1 along DIR and walks it
 // in chunks of 4 edge cells, one per warp: warp r of a chunk reconstructs the
 // edges of cell c = base + r from its five-cell stencil, read from a shared
 // ring of the 8 rows base-2..base+5 (each warp loads one new row per chunk,
 // prefetched into registers during the previous chunk's arithmetic), forms the
-// face c-1/2 with the left-side value of the previous row (shared memory, or
-// the carry from the previous chunk) and finishes cell c-1.  Unlike the
+// face c-1/2 with the left-side value of the previous row (a shared ring of
+// 5 rows, which holds the previous chunk's last row too) and finishes cell
+// c-1 (its operands staged or prefetched when the chunk starts).  Unlike the
 // marching kernel no per-thread window is kept, so more warps stay resident to
 // hide load and tensor-core latency.
 // ---------------------------------------------------------------------------
