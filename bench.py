@@ -290,7 +290,50 @@ def cpu_baseline_sample(wl, w_host, min_seconds=10.0, min_calls=2):
     cores = os.environ.get("OMP_NUM_THREADS") or str(os.cpu_count())
     return {"value": grind, "unit": UNIT, "cores": int(cores), "kind": "oracle",
             "sample": "%d oracle RHS calls on a %dx%dx%d slab (z planes %d..%d) of the %s initial state, %.1f s"
-                      % (calls, wl.n[0], wl.n[1], nz, z0, z0 + nz - 1, wl.name, el)}
+                      % (calls, wl.n[0], wl.n[1], nz, z0, z0 + nz - 1, wl.name, el),
+            "one_core": cpu_one_core_sample(wl.n[0])}
+
+
+# The same oracle RHS on one host core: a child process with OMP_NUM_THREADS=1
+# (OpenMP fixes its team size at first use, so the parent cannot shrink it).
+_ONE_CORE_CHILD = r"""
+import json, sys, time
+sys.path.insert(0, sys.argv[1])
+import numpy as np
+import oracle, workloads
+n, nz, min_seconds = int(sys.argv[2]), 4, float(sys.argv[3])
+wl = workloads.shock_bubble(n)
+w = wl.prims()
+z0 = n // 2 - nz // 2
+sub = np.ascontiguousarray(w[:, z0:z0 + nz])
+h = (wl.hi[2] - wl.lo[2]) / n
+pb = oracle.Problem((n, n, nz), wl.lo, (wl.hi[0], wl.hi[1], wl.lo[2] + nz * h), wl.bc, wl.gamma, wl.pi_inf,
+                    fallback=True)
+q = oracle.cons_from_prims(pb, sub)
+oracle.rhs(pb, q)
+calls, t0 = 0, time.perf_counter()
+while calls < 2 or time.perf_counter() - t0 < min_seconds:
+    oracle.rhs(pb, q)
+    calls += 1
+el = time.perf_counter() - t0
+print(json.dumps({"value": el / calls / (pb.ncell * pb.sys_size) * 1e9, "cores": 1,
+                  "sample": "%d oracle RHS calls on a %dx%dx%d slab (z planes %d..%d), one thread, %.1f s"
+                            % (calls, n, n, nz, z0, z0 + nz - 1, el)}))
+"""
+
+
+def cpu_one_core_sample(n, min_seconds=5.0):
+    env = dict(os.environ, OMP_NUM_THREADS="1")
+    try:
+        res = subprocess.run([sys.executable, "-c", _ONE_CORE_CHILD, ROOT, str(n), str(min_seconds)], env=env,
+                             capture_output=True, text=True, timeout=300)
+        if res.returncode != 0:
+            return {"error": (res.stderr.strip().splitlines() or ["exit %d" % res.returncode])[-1]}
+        out = json.loads(res.stdout.strip().splitlines()[-1])
+        out["unit"] = UNIT
+        return out
+    except (OSError, ValueError, subprocess.SubprocessError) as e:
+        return {"error": str(e)}
 
 
 def run_reference(args, wl):

@@ -50,3 +50,12 @@ def test_max_over_two_gloo_ranks():
 def test_single_rank_is_a_no_op():
     import bench
     assert bench.max_over_ranks(3.5, 1) == 3.5
+
+
+def test_one_core_oracle_sample_runs_in_a_child_with_one_thread():
+    """bench.py's single-core CPU figure: the oracle's RHS timed in a child
+    process with OMP_NUM_THREADS=1 on a small slab of the shock-bubble."""
+    import bench
+    out = bench.cpu_one_core_sample(16, min_seconds=0.2)
+    assert "error" not in out, out
+    assert out["cores"] == 1 and out["value"] > 0 and out["unit"] == bench.UNIT
