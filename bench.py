@@ -332,8 +332,8 @@ def cpu_one_core_sample(n, min_seconds=5.0):
         out = json.loads(res.stdout.strip().splitlines()[-1])
         out["unit"] = UNIT
         return out
-    except (OSError, ValueError, subprocess.SubprocessError) as e:
-        return {"error": str(e)}
+    except (OSError, ValueError, IndexError, subprocess.SubprocessError) as e:
+        return {"error": str(e) or type(e).__name__}
 
 
 def run_reference(args, wl):
