@@ -56,7 +56,21 @@ typedef enum {
 } mfc_bc;
 
 /* Arithmetic of the reconstruction and Riemann solver:
- *   MFC_FP64    everything in float64;
+ *   MFC_FP64    float64 state, primitive recovery, stencil differences, edge
+ *               sums, mixture rules, fluxes, divergence and Runge-Kutta
+ *               update; the WENO nonlinear weights and the HLLC solver are
+ *               evaluated in float-float arithmetic (a value is the unevaluated
+ *               sum of two float32 numbers, about 48 significant bits) with the
+ *               float32 exponent range, and their results are widened back to
+ *               float64.  The right-hand side matches a plain float64
+ *               evaluation to 1e-11 relative to each component's flux scale.
+ *               Supported range (SI units): every primitive value, stencil
+ *               difference and pressure jump below 1e18 in magnitude (the
+ *               smoothness indicators square the differences in float32
+ *               range), every product of three state values such as
+ *               (rho E + p) u below 1e37; a magnitude below 2^-126 (1.2e-38)
+ *               inside these solvers counts as zero, an absolute error far
+ *               below any flux scale;
  *   MFC_MIXED   WENO5 and HLLC in float32; pressure recovery from total energy
  *               and the Runge-Kutta accumulation stay float64;
  *   MFC_LEARNED as MFC_MIXED, with WENO5 nonlinear weights from a small MLP
@@ -136,8 +150,8 @@ mfc_status mfc_init(mfc_ctx** out, int nx, int ny, int nz, const double lo[3], c
  * Errors: MFC_ERR_ARG for an unknown name or out-of-range value. */
 mfc_status mfc_set_param(mfc_ctx* ctx, const char* name, double value);
 
-/* Non-uniform grid (Sec. 3.3: a structured mesh with non-uniform spacing,
- * e.g. the tanh stretching of Sec. 5): faces[0..n_dir] are the strictly
+/* Non-uniform grid (Sec. 4.1: a structured mesh with non-uniform spacing,
+ * e.g. the tanh stretching of Sec. 6.3): faces[0..n_dir] are the strictly
  * increasing face coordinates of the n_dir cells of direction dir (0 x, 1 y,
  * 2 z; an active direction).  The library builds, on the host, the per-cell
  * WENO5 coefficients of the finite-volume reconstruction on each five-cell
@@ -161,7 +175,11 @@ mfc_status mfc_set_grid(mfc_ctx* ctx, int dir, const double* faces, int nfaces);
  * NULL or out_len is too small; -1 for bad faces. */
 int mfc_grid_table(const double* faces, int n, int periodic, float* out, long long out_len);
 
-/* Copy a conserved state q (layout above) into the context. */
+/* Copy a conserved state q (layout above) into the context: the cell
+ * averages q_{i,j,k} of the conserved variables of Eq. "fvm" (Sec. 3.1; the
+ * variables of Sec. 2.1's five-equation model), which mfc_step advances.
+ * No check of physical validity is made here (mfc_cfl_dt does it).
+ * Errors: MFC_ERR_ARG (NULL q), MFC_ERR_CUDA. */
 mfc_status mfc_set_state(mfc_ctx* ctx, const double* q, int on_device);
 
 /* Set the state from primitive variables w (layout above); the conversion
@@ -171,7 +189,10 @@ mfc_status mfc_set_state(mfc_ctx* ctx, const double* q, int on_device);
  * read. */
 mfc_status mfc_set_state_prim(mfc_ctx* ctx, const double* w, int on_device);
 
-/* Copy the current conserved state out. */
+/* Copy the current conserved state out: the cell averages q_{i,j,k} of
+ * Eq. "fvm" (Sec. 3.1), layout above.  With a host pointer the call waits for
+ * the stream; with a device pointer the copy is enqueued on it.
+ * Errors: MFC_ERR_STATE_UNSET, MFC_ERR_ARG (NULL q), MFC_ERR_CUDA. */
 mfc_status mfc_get_state(mfc_ctx* ctx, double* q, int on_device);
 
 /* R(q) of Eq. "fvmdis" (Sec. 3.1) for the current state: WENO5 reconstruction
@@ -188,8 +209,10 @@ mfc_status mfc_rhs(mfc_ctx* ctx, double* rhs, int on_device);
  * Errors: MFC_ERR_STATE_UNSET, MFC_ERR_ARG (dt not finite or <= 0), MFC_ERR_CUDA. */
 mfc_status mfc_step(mfc_ctx* ctx, double dt);
 
-/* CFL time step of the current state: dt = cfl / max over cells and
- * directions of (|u_d| + c)/dx_d, with c^2 = ((Gamma+1)p + Pi)/(Gamma rho).
+/* CFL time step of the current state (Sec. 1: the Courant-Friedrichs-Lewy
+ * constraint restricts the explicit time step; the paper gives no formula, so
+ * this is the usual one): dt = cfl / max over cells and directions of
+ * (|u_d| + c)/dx_d, with c^2 = ((Gamma+1)p + Pi)/(Gamma rho).
  * Synchronises the stream (8-byte readback).  Errors: MFC_ERR_NONPHYSICAL if
  * any cell has a non-finite state or c^2 <= 0 (*dt_out = 0),
  * MFC_ERR_STATE_UNSET, MFC_ERR_ARG. */
@@ -300,8 +323,10 @@ int mfc_profile_read(mfc_ctx* ctx, double* total_ms, long long* launches, int n)
  * doubles = 18.9 MB) is a static device array of the library, held by every GPU
  * that loads the library until the process exits.  The first call on a device,
  * with that device current, looks up the array's device address once; make that
- * first call before any stream capture.  All calls share the array: calls that
- * overlap on the GPU race on it and must be serialised by the caller.
+ * first call before any stream capture.  The address is cached for the life of
+ * the process, so do not use this entry point across a cudaDeviceReset (which
+ * reloads the library's device code elsewhere).  All calls share the array:
+ * calls that overlap on the GPU race on it and must be serialised by the caller.
  * Errors: MFC_ERR_ARG (bad arguments, or a grid larger than
  * MFC_NOALLOC_MAX_CELLS, with the reason in err), MFC_ERR_CUDA. */
 mfc_status mfc_rhs_noalloc(const double* q, double* rhs, int nx, int ny, int nz, const double lo[3],

@@ -17,8 +17,8 @@ Contents (each cites the passage of arXiv 2305.09163 it follows):
   * ``exact_riemann``: exact two-material stiffened-gas Riemann solution used to
     judge shock-tube runs.
   * ``mlp``: FP64 forward/backward of the learned-weight network.
-  * ``nonuniform``: WENO5 coefficient tables of a non-uniform grid (Sec. 3.3,
-    Listing 1) from their definitions, and the tanh stretching of Sec. 5.
+  * ``nonuniform``: WENO5 coefficient tables of a non-uniform grid (Sec. 4.1,
+    Listing 1) from their definitions, and the tanh stretching of Sec. 6.3.
 """
 from __future__ import annotations
 

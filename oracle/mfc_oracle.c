@@ -29,7 +29,7 @@
  *   - Riemann solver (Sec. 3.2.1): HLLC, Davis wave-speed estimates, star states
  *     with continuity of normal velocity and pressure, four-branch flux.
  *     Face velocity = HLLC flux of a volume fraction divided by that fraction.
- *   - Grid (Sec. 3.3): uniform, or non-uniform per direction with WENO5
+ *   - Grid (Sec. 4.1): uniform, or non-uniform per direction with WENO5
  *     coefficient tables (candidates, ideal weights, smoothness-indicator
  *     quadratic forms per cell, as Listing 1's per-index tables) built by
  *     oracle/nonuniform.py from the definitions.

@@ -2,7 +2,7 @@
 
 TEST INFRASTRUCTURE ONLY (see ``oracle/__init__.py``).
 
-Sec. 3.3 of arXiv 2305.09163 discretises on a structured mesh with
+Sec. 4.1 of arXiv 2305.09163 discretises on a structured mesh with
 non-uniform spacing (tanh stretching; the face coordinates come from the
 input generators); Listing 1 (Sec. 4.2) reconstructs with per-index coefficient tables
 (candidate, smoothness-indicator and ideal-weight coefficients per cell).  The

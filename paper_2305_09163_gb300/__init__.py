@@ -311,13 +311,24 @@ NOALLOC_MAX_CELLS = 262144
 
 def mfc_rhs_noalloc(q, rhs, n, lo, hi, bc, gamma, pi_inf, weno_eps=1e-6, fallback=1, stream=None):
     """Allocation-free R(q) for callers that cannot let the library allocate
-    device memory; q and rhs are device tensors (float64, contiguous)."""
+    device memory; q and rhs are device tensors (float64, contiguous) on the
+    current CUDA device, each holding (2 N + d) * nx * ny * nz values (the C
+    side trusts the pointers, so the sizes and the device are checked here)."""
+    import torch
     lib = load()
     qa, qdev = _ptr(q)
     ra, rdev = _ptr(rhs)
     if not (qdev and rdev):
         raise TypeError("mfc_rhs_noalloc takes device buffers")
     n = list(n) + [1] * (3 - len(n))
+    ndim = 3 if n[2] > 1 else (2 if n[1] > 1 else 1)
+    need = (2 * len(gamma) + ndim) * int(n[0]) * int(n[1]) * int(n[2])
+    if q.numel() != need or rhs.numel() != need:
+        raise ValueError("mfc_rhs_noalloc: q and rhs must hold (2N + d) * cells = %d values (got %d and %d)"
+                         % (need, q.numel(), rhs.numel()))
+    cur = torch.cuda.current_device()
+    if q.device.index != cur or rhs.device.index != cur:
+        raise ValueError("mfc_rhs_noalloc: q and rhs must be on the current CUDA device (cuda:%d)" % cur)
     lo3 = (ctypes.c_double * 3)(*(list(lo) + [0.0] * (3 - len(lo))))
     hi3 = (ctypes.c_double * 3)(*(list(hi) + [1.0] * (3 - len(hi))))
     bc6 = (ctypes.c_int * 6)(*(list(bc) + [1] * (6 - len(bc))))

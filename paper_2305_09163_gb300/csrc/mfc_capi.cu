@@ -111,14 +111,7 @@ size_t real_size(const mfc_ctx* c) { return is_f32(c) ? sizeof(float) : sizeof(d
 
 int auto_segment(const mfc_ctx* c, int dir) {
     if (c->seg_override > 0) return c->seg_override;
-    const int nd = c->n[dir];
-    const long long trans = c->ncell / nd;
-    // the FP64 stream sweeps do more work per cell: longer segments halve the
-    // recomputed edge cells (256^3 shock-bubble: 104.4 vs 105.5 ms per step)
-    int L = (!is_f32(c) && c->yz_stream != 0) ? 128 : 64;
-    // keep at least ~8 warps per SM resident while limiting edge recomputation
-    while (L > 8 && trans * ((nd + L - 1) / L) < 152LL * 4 * kSweepThreads) L /= 2;
-    return L;
+    return sweep_segment(c->ncell, c->n[dir], !is_f32(c) && c->yz_stream != 0);
 }
 
 template <typename F>
@@ -506,25 +499,7 @@ mfc_status mfc_init(mfc_ctx** out, int nx, int ny, int nz, const double lo[3], c
         g.inv_dx[d] = d < ndim ? n[d] / (hi[d] - lo[d]) : 0.0;
     }
     g.ncell = ncell;
-    const int N = num_fluids;
-    double G[3], P[3];
-    for (int k = 0; k < N; ++k) {
-        G[k] = 1.0 / (gamma[k] - 1.0);
-        P[k] = gamma[k] * pi_inf[k] / (gamma[k] - 1.0);
-    }
-    c->e.G_N = G[N - 1];
-    c->e.P_N = P[N - 1];
-    for (int k = 0; k < 2; ++k) {
-        c->e.dG[k] = k < N - 1 ? G[k] - G[N - 1] : 0.0;
-        c->e.dP[k] = k < N - 1 ? P[k] - P[N - 1] : 0.0;
-    }
-    // six-equation model: frozen r c^2 = sum a_k g_k (p + pinf_k) = A p + B
-    c->e.A_N = gamma[N - 1];
-    c->e.B_N = gamma[N - 1] * pi_inf[N - 1];
-    for (int k = 0; k < 2; ++k) {
-        c->e.dA[k] = k < N - 1 ? gamma[k] - gamma[N - 1] : 0.0;
-        c->e.dB[k] = k < N - 1 ? gamma[k] * pi_inf[k] - gamma[N - 1] * pi_inf[N - 1] : 0.0;
-    }
+    c->e = make_eos_const(num_fluids, gamma, pi_inf);
 
     const size_t bytes = sizeof(double) * (size_t)c->ns * (size_t)ncell;
     const size_t wbytes = real_size(c) * (size_t)c->ns * (size_t)ncell;

@@ -1,4 +1,4 @@
-// Non-uniform grids (Sec. 3.3: a structured mesh with non-uniform spacing;
+// Non-uniform grids (Sec. 4.1: a structured mesh with non-uniform spacing;
 // Listing 1 of Sec. 4.2 reconstructs with per-index coefficient tables).  Host
 // code: for every cell of a direction the WENO5 coefficients of the
 // finite-volume reconstruction on its five-cell stencil, in the form the

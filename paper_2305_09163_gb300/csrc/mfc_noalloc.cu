@@ -12,7 +12,11 @@
 // Host code must not use the array's name as a device address (in host code it
 // is a host-side stand-in).  The device address is obtained once per device with
 // cudaGetSymbolAddress, on the first call made with that device current, and
-// cached; that first call should therefore come before any stream capture.
+// cached; that first call should therefore come before any stream capture.  The
+// cached address belongs to the device's primary context as it was then: after
+// cudaDeviceReset (or anything else that re-creates that context) the module is
+// loaded anew and the cached address is stale, so this entry point must not be
+// used across a device reset.
 // All calls share the array, so calls that overlap on the GPU (different
 // streams, or different host threads on one device) race on it and must be
 // serialised by the caller.  Nothing in it needs clearing: every call overwrites
@@ -90,11 +94,8 @@ cudaError_t run(const Geometry& g, const EosConst& e, int ndim, const double* q,
         a.fallback_count = nullptr;
         a.cbc = cbc;
         sweep_set_f32_constants(a);
-        const long long trans = g.ncell / g.n[d];
-        int L = 64;
-        while (L > 8 && trans * ((g.n[d] + L - 1) / L) < 152LL * 4 * kSweepThreads) L /= 2;
-        a.seg = L;
-        a.nseg = (g.n[d] + L - 1) / L;
+        a.seg = sweep_segment(g.ncell, g.n[d], true);
+        a.nseg = (g.n[d] + a.seg - 1) / a.seg;
         rc = launch_sweep<double, NF>(a, ndim, d, s);
         if (rc != cudaSuccess) return rc;
     }
@@ -157,18 +158,7 @@ extern "C" mfc_status mfc_rhs_noalloc(const double* q, double* rhs, int nx, int 
     }
     g.ncell = ncell;
     const int N = num_fluids;
-    double G[3], P[3];
-    for (int k = 0; k < N; ++k) {
-        G[k] = 1.0 / (gamma[k] - 1.0);
-        P[k] = gamma[k] * pi_inf[k] / (gamma[k] - 1.0);
-    }
-    EosConst e{};
-    e.G_N = G[N - 1];
-    e.P_N = P[N - 1];
-    for (int k = 0; k < 2; ++k) {
-        e.dG[k] = k < N - 1 ? G[k] - G[N - 1] : 0.0;
-        e.dP[k] = k < N - 1 ? P[k] - P[N - 1] : 0.0;
-    }
+    const EosConst e = make_eos_const(N, gamma, pi_inf);
     cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
     cudaError_t rc;
     switch (N) {

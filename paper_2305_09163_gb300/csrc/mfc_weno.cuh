@@ -142,7 +142,7 @@ __device__ __forceinline__ void weno_edges(Real vc, const Real D[4], Real epsw, 
 }
 
 // ---------------------------------------------------------------------------
-// WENO5-JS on a non-uniform grid (Sec. 3.3, with per-cell coefficients as in
+// WENO5-JS on a non-uniform grid (Sec. 4.1, with per-cell coefficients as in
 // Listing 1): row = the cell's table row (mfc_grid.cu): candidate increments
 // ea_r Da_r + eb_r Db_r for both edges (values 0..11), ideal weights (12..17),
 // beta_r = qa Da^2 + qab Da Db + qb Db^2 (18..26), with (Da, Db) = (D0, D1),

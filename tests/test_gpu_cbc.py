@@ -9,7 +9,7 @@ import pytest
 
 import oracle
 import workloads
-from parity_util import rhs_error, state_error
+from parity_util import FP32_UNIT, rhs_error, rhs_error_raw, state_error
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -105,8 +105,10 @@ def test_cbc_mixed_rhs_close_to_oracle(mfc):
     q = oracle.cons_from_prims(pb, w)
     R_cpu, fmax, _ = oracle.rhs(pb, q, return_info=True)
     s.set_state_prim(torch.from_numpy(w).cuda())
-    err = rhs_error(pb, q, s.rhs().cpu().numpy(), R_cpu, fmax)
-    assert 1e-12 < err.max() <= TOL_MIXED_RHS, err
+    R = s.rhs().cpu().numpy()
+    err = rhs_error(pb, q, R, R_cpu, fmax, unit=FP32_UNIT)
+    assert err.max() <= TOL_MIXED_RHS, err
+    assert rhs_error_raw(pb, q, R, R_cpu, fmax).max() > 1e-12  # FP32 arithmetic in use
 
 
 def test_cbc_noalloc_matches_oracle(mfc):

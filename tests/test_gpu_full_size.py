@@ -10,7 +10,7 @@ import pytest
 
 import oracle
 import workloads
-from parity_util import sampled_rhs_error
+from parity_util import FP32_UNIT, FP64_UNIT, rhs_table, sampled_rhs_error
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -52,7 +52,7 @@ def _cells(pb, shock_x):
 
 
 @pytest.mark.parametrize("form", list(FORMS))
-def test_full_size_sampled_parity_of_each_form(mfc, form):
+def test_full_size_sampled_parity_of_each_form(mfc, form, capsys):
     build, params, opts, six = FORMS[form]
     wl = build(N)
     pb = oracle.Problem(wl.n, wl.lo, wl.hi, wl.bc, wl.gamma, wl.pi_inf, fallback=True, faces=wl.faces, **opts)
@@ -71,10 +71,13 @@ def test_full_size_sampled_parity_of_each_form(mfc, form):
     cells = _cells(pb, int(np.searchsorted(centers, 0.05)))
     Rc, fmax = oracle.rhs_cells(pb, q, cells, return_fmax=True)
     err = sampled_rhs_error(pb, q, R, cells, Rc, fmax)
+    with capsys.disabled():
+        print("\n%s 256^3 FP64 RHS at %d sampled cells:\n" % (form, cells.size)
+              + rhs_table(pb, q, R, Rc, fmax, cells=cells))
     assert err.max() <= TOL_FP64, (form, err)
 
 
-def _sampled_check(mfc, wl, precision, tol, seed):
+def _sampled_check(mfc, wl, precision, tol, seed, capsys=None):
     pb = oracle.Problem(wl.n, wl.lo, wl.hi, wl.bc, wl.gamma, wl.pi_inf, fallback=True)
     w = wl.prims()
     q = oracle.cons_from_prims(pb, w)
@@ -98,19 +101,24 @@ def _sampled_check(mfc, wl, precision, tol, seed):
         pick.append(rng.choice(inter, min(400, inter.size), replace=False))
     cells = np.unique(np.concatenate(pick))
     Rc, fmax = oracle.rhs_cells(pb, q, cells, return_fmax=True)
-    err = sampled_rhs_error(pb, q, R, cells, Rc, fmax)
+    unit = FP64_UNIT if precision == "fp64" else FP32_UNIT
+    err = sampled_rhs_error(pb, q, R, cells, Rc, fmax, unit=unit)
+    if capsys is not None:
+        with capsys.disabled():
+            print("\n%s %s RHS at %d sampled cells:\n" % (wl.name, precision, cells.size)
+                  + rhs_table(pb, q, R, Rc, fmax, cells=cells, unit=unit))
     assert err.max() <= tol, (wl.name, precision, err)
 
 
 @pytest.mark.parametrize("precision,tol", [("fp64", TOL_FP64), ("mixed", 2e-4)])
-def test_full_size_bubble_cloud(mfc, precision, tol):
+def test_full_size_bubble_cloud(mfc, precision, tol, capsys):
     """The 384^3 shock-bubble-cloud workload (64 air bubbles with lognormal
     radii in water, planar shock)."""
-    _sampled_check(mfc, workloads.bubble_cloud(384), precision, tol, 17)
+    _sampled_check(mfc, workloads.bubble_cloud(384), precision, tol, 17, capsys)
 
 
 @pytest.mark.parametrize("precision,tol", [("fp64", TOL_FP64), ("mixed", 2e-4)])
-def test_full_size_three_fluid(mfc, precision, tol):
+def test_full_size_three_fluid(mfc, precision, tol, capsys):
     """The 512^3 three-fluid workload (water, an air bubble cloud and a stiff
     solid slab; ~10 GB per state array)."""
-    _sampled_check(mfc, workloads.three_fluid(512), precision, tol, 19)
+    _sampled_check(mfc, workloads.three_fluid(512), precision, tol, 19, capsys)

@@ -5,7 +5,7 @@ import pytest
 
 import oracle
 import workloads
-from parity_util import rhs_error
+from parity_util import FP32_UNIT, rhs_error
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -44,7 +44,7 @@ def test_ideal_weight_network_reproduces_linear_weno5(m, n, nf, bc):
     s.set_mlp(_ideal_params())
     s.set_state_prim(torch.from_numpy(w).cuda())
     R = s.rhs().cpu().numpy()
-    err = rhs_error(pb, q, R, R_cpu, fmax)
+    err = rhs_error(pb, q, R, R_cpu, fmax, unit=FP32_UNIT)
     assert err.max() <= 2e-5, err
 
 
@@ -86,8 +86,8 @@ def test_fused_network_matches_reference_edge_by_edge(m, n, nf, capsys):
     s.set_state(torch.from_numpy(q).cuda())
     R = s.rhs().cpu().numpy()
     rows = s.network_rows()
-    err = rhs_error(pb, q, R, R_ref, fmax)
-    err_bad = rhs_error(pb, q, R_bad, R_ref, fmax)
+    err = rhs_error(pb, q, R, R_ref, fmax, unit=FP32_UNIT)
+    err_bad = rhs_error(pb, q, R_bad, R_ref, fmax, unit=FP32_UNIT)
     with capsys.disabled():
         print("\nfused network vs reference: err %.3g (planted off-by-one %.3g), network rows %d"
               % (err.max(), err_bad.max(), rows))

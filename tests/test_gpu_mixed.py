@@ -6,7 +6,7 @@ import pytest
 
 import oracle
 import workloads
-from parity_util import rhs_error, state_error
+from parity_util import FP32_UNIT, rhs_error, rhs_error_raw, state_error
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -32,10 +32,10 @@ def test_mixed_rhs_close_to_fp64_oracle(mfc, n, nf):
     s = mfc.Solver(pb.n, pb.lo, pb.hi, pb.bc, gam, pin, precision="mixed", fallback=1)
     s.set_state_prim(torch.from_numpy(w).cuda())
     R = s.rhs().cpu().numpy()
-    err = rhs_error(pb, q, R, R_cpu, fmax)
+    err = rhs_error(pb, q, R, R_cpu, fmax, unit=FP32_UNIT)
     print("mixed rhs err", n, nf, err)
     assert err.max() <= TOL_MIXED_RHS, err
-    assert err.max() > 1e-12  # really computed in FP32
+    assert rhs_error_raw(pb, q, R, R_cpu, fmax).max() > 1e-12  # really computed in FP32
 
 
 def test_mixed_steps_track_fp64_on_shock_bubble(mfc):

@@ -1,5 +1,5 @@
-"""Parity of the non-uniform-grid sweeps (mfc_set_grid; Sec. 3.3 and Listing 1's
-per-cell coefficients; Sec. 5's tanh stretching) with the CPU FP64 oracle,
+"""Parity of the non-uniform-grid sweeps (mfc_set_grid; Sec. 4.1 and Listing 1's
+per-cell coefficients; Sec. 6.3's tanh stretching) with the CPU FP64 oracle,
 through the C ABI; the same metric and FP64 gate as on uniform grids."""
 import numpy as np
 import pytest
@@ -7,7 +7,7 @@ import pytest
 import oracle
 import workloads
 from oracle import nonuniform as nu
-from parity_util import rhs_error, state_error
+from parity_util import FP32_UNIT, rhs_error, rhs_error_raw, state_error
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -77,8 +77,10 @@ def test_nonuniform_mixed_rhs_close_to_oracle(mfc):
     q = oracle.cons_from_prims(pb, w)
     R_cpu, fmax, _ = oracle.rhs(pb, q, return_info=True)
     s.set_state_prim(torch.from_numpy(w).cuda())
-    err = rhs_error(pb, q, s.rhs().cpu().numpy(), R_cpu, fmax)
-    assert 1e-12 < err.max() <= TOL_MIXED_RHS, err
+    R = s.rhs().cpu().numpy()
+    err = rhs_error(pb, q, R, R_cpu, fmax, unit=FP32_UNIT)
+    assert err.max() <= TOL_MIXED_RHS, err
+    assert rhs_error_raw(pb, q, R, R_cpu, fmax).max() > 1e-12  # FP32 arithmetic in use
 
 
 def test_nonuniform_cfl_and_steps_match_oracle(mfc):

@@ -10,7 +10,7 @@ import pytest
 
 import oracle
 import workloads
-from parity_util import rhs_error, sampled_rhs_error, state_error
+from parity_util import rhs_error, rhs_table, sampled_rhs_error, state_error
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -99,7 +99,7 @@ def test_rhs_parity_independent_of_segment_length(mfc, seg, yz):
     assert rhs_error(pb, q, R_gpu, R_cpu, fmax).max() <= TOL_FP64
 
 
-def test_rhs_parity_shock_bubble_small(mfc):
+def test_rhs_parity_shock_bubble_small(mfc, capsys):
     """The shock-bubble geometry at 48^3: shocked water (1e9 Pa), tanh air bubble."""
     wl = workloads.shock_bubble(48)
     pb = oracle.Problem(wl.n, wl.lo, wl.hi, wl.bc, wl.gamma, wl.pi_inf, fallback=True)
@@ -109,6 +109,46 @@ def test_rhs_parity_shock_bubble_small(mfc):
     s = _solver(mfc, pb)
     s.set_state_prim(torch.from_numpy(w).cuda())
     R_gpu = s.rhs().cpu().numpy()
+    with capsys.disabled():
+        print("\nshock-bubble 48^3, FP64 RHS per component:\n" + rhs_table(pb, q, R_gpu, R_cpu, fmax))
+    assert rhs_error(pb, q, R_gpu, R_cpu, fmax).max() <= TOL_FP64
+
+
+@pytest.mark.parametrize("p_high,solid", [(1e12, True), (1e16, False)], ids=["stiff_solid_1e12", "jump_1e16"])
+def test_rhs_parity_at_range_extremes(mfc, p_high, solid, capsys):
+    """The FP64 path's WENO weights and HLLC run in float-float (float32 exponent
+    range): three fluids with the stiff solid phase (gamma 3, pi_inf 1e10 Pa),
+    either dominant (volume fraction ~0.98) beside a 1e5 -> 1e12 Pa pressure
+    jump, or mixed with water and air across a 1e5 -> 1e16 Pa jump, near the top
+    of the documented range.  Gate: the FP64 1e-11."""
+    n = (29, 17, 13)
+    gam, pin = workloads.fluids(3)
+    assert pin[2] == 1e10
+    pb = _problem(n, (1,) * 6, gam, pin, True)
+    w = workloads.random_prims(n, 3, seed=404)
+    nf, nd = 3, 3
+    ip = nf + nd
+    x = (np.arange(n[0]) + 0.5) / n[0]
+    high = np.broadcast_to(x > 0.45, w[ip].shape)
+    w[ip] = np.where(high, p_high, 1e5) * (1.0 + 0.05 * np.sin(7.0 * w[nf]))
+    if solid:
+        a = np.empty((nf,) + w[0].shape)
+        a[0] = 0.01 * (1.0 + 0.5 * np.sin(3.0 * w[nf]))
+        a[1] = 0.01 * (1.0 + 0.5 * np.cos(5.0 * w[nf + 1]))
+        a[2] = 1.0 - a[0] - a[1]
+        rho = (1000.0, 1.0, 2000.0)
+        for k in range(nf):
+            w[k] = a[k] * rho[k]
+        for k in range(nf - 1):
+            w[ip + 1 + k] = a[k]
+    q = oracle.cons_from_prims(pb, w)
+    R_cpu, fmax, _ = oracle.rhs(pb, q, return_info=True)
+    s = _solver(mfc, pb)
+    s.set_state_prim(torch.from_numpy(np.ascontiguousarray(w)).cuda())
+    R_gpu = s.rhs().cpu().numpy()
+    with capsys.disabled():
+        print("\nrange extremes (p_high %.0e, solid-dominant %s), FP64 RHS per component:\n"
+              % (p_high, solid) + rhs_table(pb, q, R_gpu, R_cpu, fmax))
     assert rhs_error(pb, q, R_gpu, R_cpu, fmax).max() <= TOL_FP64
 
 
@@ -255,7 +295,7 @@ def test_rhs_to_host_buffer(mfc):
 
 
 @pytest.mark.parametrize("wl_name", ["shock_bubble"])
-def test_full_size_sampled_parity(mfc, wl_name):
+def test_full_size_sampled_parity(mfc, wl_name, capsys):
     """The 256^3 shock-bubble workload in the bench's launch configuration:
     full GPU RHS, oracle at sampled cells (random, boundaries, interface, shock)."""
     wl = workloads.shock_bubble(256)
@@ -279,4 +319,7 @@ def test_full_size_sampled_parity(mfc, wl_name):
     cells = np.unique(np.concatenate(pick))
     Rc, fmax = oracle.rhs_cells(pb, q, cells, return_fmax=True)
     err = sampled_rhs_error(pb, q, R, cells, Rc, fmax)
+    with capsys.disabled():
+        print("\nshock-bubble 256^3, FP64 RHS at %d sampled cells:\n" % cells.size
+              + rhs_table(pb, q, R, Rc, fmax, cells=cells))
     assert err.max() <= TOL_FP64, err

@@ -8,7 +8,7 @@ import pytest
 
 import oracle
 import workloads
-from parity_util import rhs_error, state_error
+from parity_util import FP32_UNIT, rhs_error, rhs_error_raw, state_error
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -120,8 +120,10 @@ def test_six_mixed_rhs_close_to_oracle(mfc):
     q = oracle.cons_from_prims(pb, w)
     R_cpu, fmax, _ = oracle.rhs(pb, q, return_info=True)
     s.set_state(torch.from_numpy(np.ascontiguousarray(q)).cuda())
-    err = rhs_error(pb, q, s.rhs().cpu().numpy(), R_cpu, fmax)
-    assert 1e-12 < err.max() <= TOL_MIXED_RHS, err
+    R = s.rhs().cpu().numpy()
+    err = rhs_error(pb, q, R, R_cpu, fmax, unit=FP32_UNIT)
+    assert err.max() <= TOL_MIXED_RHS, err
+    assert rhs_error_raw(pb, q, R, R_cpu, fmax).max() > 1e-12  # FP32 arithmetic in use
 
 
 def test_six_mixed_steps_close_to_oracle(mfc):
@@ -173,7 +175,7 @@ def test_six_mixed_shock_bubble_stays_close_in_l1(mfc):
 
 @pytest.mark.parametrize("n,nf", [((33,), 2), ((27, 19), 3), ((29, 17, 13), 2)])
 def test_six_rhs_parity_stretched_grid(mfc, n, nf):
-    """The six-equation model on tanh-stretched grids (Sec. 3.3's per-cell
+    """The six-equation model on tanh-stretched grids (Sec. 4.1's non-uniform mesh, per-cell
     WENO5 coefficients): the FP64 gate."""
     gam, pin = workloads.fluids(nf)
     faces = [workloads.stretched_faces(m, 0.0, 1.0, 3.0, 0.3, 0.7) for m in n]

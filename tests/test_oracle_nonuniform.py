@@ -1,5 +1,5 @@
-"""CPU pins of the oracle's non-uniform-grid WENO5 (Sec. 3.3; Listing 1's
-per-index coefficient tables; Sec. 5's tanh stretching).  Each pin comes from
+"""CPU pins of the oracle's non-uniform-grid WENO5 (Sec. 4.1; Listing 1's
+per-index coefficient tables; Sec. 6.3's tanh stretching).  Each pin comes from
 outside the generator: closed forms on a uniform grid, exactness for
 polynomials on random non-uniform cells, the smoothness indicators against
 Gauss quadrature of an independently built interpolant, symmetries, and the
@@ -89,7 +89,7 @@ def test_tables_scale_free_and_mirror_symmetric():
 
 
 def test_paper_stretching_refines_near_the_droplet():
-    """Sec. 5's mapping with a = 4, x_a = -1.2 D, x_b = 1.2 D on [-10 D, 10 D]:
+    """Sec. 6.3's mapping with a = 4, x_a = -1.2 D, x_b = 1.2 D on [-10 D, 10 D]:
     monotone, finer between x_a and x_b than near the ends."""
     f = workloads.stretched_faces(400, -10.0, 10.0, 4.0, -1.2, 1.2)
     h = np.diff(f)

@@ -90,7 +90,7 @@ def _centers(n, lo, hi, faces=None):
 
 def stretched_faces(n: int, lo: float, hi: float, a: float, xa: float, xb: float) -> np.ndarray:
     """Face coordinates of n cells after the hyperbolic-tangent stretching the
-    paper gives for its droplet case (Sec. 5): x_s = x + (x/a)[log cosh(a(x-xa)/L)
+    paper gives for its droplet case (Sec. 6.3): x_s = x + (x/a)[log cosh(a(x-xa)/L)
     + log cosh(a(x-xb)/L) - 2 log cosh(a(xb-xa)/(2L))] applied to the uniform
     faces of [lo, hi], L = hi - lo; cells are finest between xa and xb."""
     x = np.linspace(lo, hi, n + 1)
@@ -241,7 +241,7 @@ def _build_shock_bubble_stretched(wl: Workload) -> np.ndarray:
 
 def shock_bubble_stretched(n: int = 256, a: float = 4.0, steps: int = 1000) -> Workload:
     """The shock-bubble on a grid stretched as the paper's droplet case
-    (Sec. 5): the mapping of stretched_faces on [-0.5, 0.5] per direction with
+    (Sec. 6.3): the mapping of stretched_faces on [-0.5, 0.5] per direction with
     x_a = -0.12, x_b = 0.12 (1.2 bubble diameters), shifted to start at 0; the
     air bubble (R = 0.1) sits at the centre of the refined region, the shocked
     water at x < 0.05."""
