@@ -1,10 +1,16 @@
 """Throughput of the five-equation RHS / SSP-RK3 step on GB300.
 
-Default workload: the 256^3 two-fluid water/air shock-bubble in FP64 (a step =
+Headline workload: the 256^3 two-fluid water/air shock-bubble in FP64 (a step =
 one CFL reduction + three RHS evaluations + three RK stage updates).  The metric
 is the grind time t_RHS / (cells * equations) in ns/(cell*eqn*RHS) (lower is
-better), with cell-updates/s beside it; the mixed-precision (and, when built,
-learned-weight) forms are timed on the same workload and reported under "forms".
+better), with cell-updates/s beside it.  The other forms (mixed precision,
+learned weights, WENO3, Kapila, stretched grid, characteristic boundaries,
+six-equation model) are timed on the same workload under "forms", and every
+form on the configuration it is defined on (the 384^3 bubble cloud in FP64,
+mixed and learned; the 512^3 three-fluid workload in FP64 and mixed) under
+"configs".  Every timed run starts from the initial state developed by
+--develop steps (so shock and interfaces are present), then --warmup untimed
+steps, then the timed steps.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
@@ -38,51 +44,71 @@ METRIC = "grind time ns/(cell·eqn·RHS) & cell-updates/s, FP64 vs mixed vs lear
 UNIT = "ns/(cell*eqn*RHS)"
 CFL = 0.3
 
-# Algorithmic FP64 operations of one directional sweep per cell (3D, two fluids,
-# seven equations), counted from the formulation the kernels evaluate with
-# FMA = 2 and every add, multiply, divide, square root, min and max = 1:
-#   WENO5 edges (both sides of a cell) 70 per variable x 7, HLLC 87 per face,
-#   flux difference + alpha div(u) source 18 per cell.
-FLOP_SWEEP_CELL_3D_2F = 70 * 7 + 87 + 18
-# The same with the third-order reconstruction: WENO3 edges (both sides) 31 per
-# variable (two differences, t = eps + d^2, t^2, the two weight denominators
-# and their product, one reciprocal, the two numerators and the two edges).
-FLOP_SWEEP_CELL_3D_2F_W3 = 31 * 7 + 87 + 18
-# The Kapila model adds K (two Z_k = gamma_k (p + pinf_k), the weighted sum,
-# one reciprocal, K = alpha (Z_2/D - 1)) and its source term: 13 per cell and sweep.
-FLOP_SWEEP_CELL_3D_2F_KAPILA = FLOP_SWEEP_CELL_3D_2F + 13
-# Forms the bench can time: name -> (precision, extra solver parameters,
-# workload: the shock-bubble, or the same on the tanh-stretched grid).
-FORMS = {
-    "fp64": ("fp64", {}, "uniform"),
-    "mixed": ("mixed", {}, "uniform"),
-    "learned": ("learned", {}, "uniform"),
-    "fp64_weno3": ("fp64", {"weno_order": 3}, "uniform"),
-    "mixed_weno3": ("mixed", {"weno_order": 3}, "uniform"),
-    "fp64_kapila": ("fp64", {"model": 1}, "uniform"),
-    "fp64_stretched": ("fp64", {}, "stretched"),
-    "mixed_stretched": ("mixed", {}, "stretched"),
-    "fp64_cbc": ("fp64", {}, "cbc"),
-    "fp64_six": ("fp64", {"model": 2}, "six"),
-    "mixed_six": ("mixed", {"model": 2}, "six"),
+# Algorithmic floating-point work of one directional sweep per cell (3D), as
+# the oracle's plain formulation spends it: + - * / and sqrt one each, counted
+# by the oracle's counting build (oracle.rhs_flop_breakdown; recounted by
+# tests/test_oracle_flops.py): WENO edges of every variable on both sides of a
+# face plus HLLC per face, the flux difference and volume-fraction source per
+# cell, primitive recovery once per cell (a third per sweep).  Keyed by
+# (reconstruction or model, fluids).
+ORACLE_FLOP_PER_CELL_SWEEP = {
+    ("weno5", 2): 3860 / 3, ("weno5", 3): 4941 / 3, ("weno3", 2): 1970 / 3, ("weno3", 3): 2511 / 3,
+    ("kapila", 2): 4016 / 3, ("kapila", 3): 5151 / 3,
 }
-# RK3 stage epilogue in the last sweep: 6 per variable (stages 2, 3), 4 in stage 1
-FLOP_RK_CELL_2F = 7 * (6 + 6 + 4) / 3.0
-# Nominal FP64 peak: 152 SMs x 4 FP64 FLOP/clk/SM (2 DFMA) x 2.07 GHz
-FP64_PEAK_TFLOPS = 152 * 4 * 2.07e9 / 1e12
+# SSP-RK3 update per conserved variable, by its definition: stage 1
+# q + dt R (2), stages 2 and 3 a q + b (q_s + dt R) (5): 4 per stage on average.
+RK_FLOP_PER_VAR_STAGE = 4.0
+# Forms the bench can time on the 256^3 shock-bubble: name -> (precision, extra
+# solver parameters, workload variant, work variant for the FLOP count).
+FORMS = {
+    "fp64": ("fp64", {}, "uniform", "weno5"),
+    "mixed": ("mixed", {}, "uniform", "weno5"),
+    "learned": ("learned", {}, "uniform", "weno5"),
+    "fp64_weno3": ("fp64", {"weno_order": 3}, "uniform", "weno3"),
+    "mixed_weno3": ("mixed", {"weno_order": 3}, "uniform", "weno3"),
+    "fp64_kapila": ("fp64", {"model": 1}, "uniform", "kapila"),
+    "fp64_stretched": ("fp64", {}, "stretched", "weno5"),
+    "mixed_stretched": ("mixed", {}, "stretched", "weno5"),
+    "fp64_cbc": ("fp64", {}, "cbc", "weno5"),
+    "fp64_six": ("fp64", {"model": 2}, "six", "weno5"),
+    "mixed_six": ("mixed", {"model": 2}, "six", "weno5"),
+}
+# Every form on the configuration it is defined on: name -> (workload, precision).
+CONFIG_RUNS = {
+    "bubble_cloud_384_fp64": ("bubble_cloud", "fp64"),
+    "bubble_cloud_384_mixed": ("bubble_cloud", "mixed"),
+    "bubble_cloud_384_learned": ("bubble_cloud", "learned"),
+    "three_fluid_512_fp64": ("three_fluid", "fp64"),
+    "three_fluid_512_mixed": ("three_fluid", "mixed"),
+}
+# Issue-slot peak: 152 SMs x 4 schedulers x one warp instruction per clock.
+SCHEDULERS = 152 * 4
+# Warp instructions per cell of the FP64 WENO5 sweeps (x, y, z; 3D, two
+# fluids, smsp__inst_executed.sum / cells of one ncu capture).  Re-measured
+# whenever the FP64 sweeps change: NCU_FP64_SWEEPS says which capture.
+FP64_SWEEP_WARP_INST_PER_CELL = (240.9, 236.2, 246.3)
+# From the same capture: FP64-pipe and FP32 (fma) pipe activity of the sweeps
+# (mean over x, y, z) and DRAM bytes per cell per launch (the z sweep of an RK
+# stage also writes the next stage's primitives).
+FP64_SWEEP_PIPE_FP64 = 0.618
+FP64_SWEEP_PIPE_FMA = 0.379
+FP64_SWEEP_DRAM_BYTES_PER_CELL = (103.5 + 160.0 + 337.1) / 3.0
+NCU_FP64_SWEEPS = "profiles/sweep_fp64_shock_bubble_160.md"
 # Nominal FP32 peak: 152 SMs x 128 FMA/clk x 2 FLOP x 2.07 GHz
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 # Algorithmic DRAM bytes per cell of the three mixed-form sweeps of one stage
-# (FP32 primitives and accumulator, FP64 state): x reads w and writes R (56 B),
-# y reads w and updates R (84 B), z reads w and R and the FP64 stage states and
-# writes the new state (224 B; 168 B in stage 1, which has no q^n term).
-BYTES_MIXED_SWEEPS_STAGE = (56 + 84 + (168 + 224 + 224) / 3.0)
-# DRAM bytes per cell of one FP64 sweep launch, averaged over the x, y and z
-# sweeps of a stage: dram__bytes_read.sum + dram__bytes_write.sum of one ncu
-# capture of the 160^3 shock-bubble (x 102.7, y 158.7, z 279.0 B/cell; the
-# algorithmic w + R (+ RK states) bytes are 112, 168 and 280), scaled to the
-# bench size by the cell count.  Must be re-measured when the FP64 sweeps change.
-FP64_SWEEP_DRAM_BYTES_PER_CELL = (102.7 + 158.7 + 279.0) / 3.0
+# (FP32 primitives and accumulator, FP64 state), for ns state rows and nw
+# reconstructed rows (nw = ns except in the six-equation model): x reads w and
+# writes R, y reads w and updates R, z reads w and R and the FP64 stage states
+# and writes the new state (stage 1 has no q^n term).
+def bytes_mixed_sweeps_stage(ns, nw):
+    x = 4 * nw + 4 * ns
+    y = 4 * nw + 8 * ns
+    z1 = 4 * nw + 4 * ns + 8 * ns + 8 * ns
+    z23 = z1 + 8 * ns
+    return x + y + (z1 + 2 * z23) / 3.0
+
+
 # Useful tensor-core FLOPs of the learned network per stencil
 # (5x32 + 32x32 + 32x3 multiply-adds) and stencils per cell and sweep (2 edges x 7 variables).
 FLOP_MLP_STENCIL = 2 * (5 * 32 + 32 * 32 + 32 * 3)
@@ -173,18 +199,36 @@ def _measured_peaks():
         return {}
 
 
-def train_learned(m, torch, log=None):
-    """Train the learned weights on stencils of 128^3 shock-bubble and
-    bubble-cloud runs (done before, and outside, the timed region)."""
+# Training data of the learned weights: runs of the plain method (mixed form)
+# on the 256^3 shock-bubble and the 384^3 bubble cloud, harvested at five
+# snapshots each (the coarse stencils are the runs restricted by 2 per axis,
+# 128^3 and 192^3, with the fine face values as targets), 1e6 stencils per
+# snapshot: 1e7 in all.
+TRAIN_RUNS = (("shock_bubble", 256, 200, (0, 50, 100, 150, 200), 1_000_000, 1),
+              ("bubble_cloud", 384, 200, (0, 50, 100, 150, 200), 1_000_000, 2))
+
+
+def train_learned(m, torch, log=None, runs=TRAIN_RUNS):
+    """Train the learned weights on stencils harvested from runs of the
+    shock-bubble and bubble-cloud workloads (done before, and outside, every
+    timed region)."""
     from paper_2305_09163_gb300 import learned
     t0 = time.perf_counter()
-    parts = [learned.harvest_run(workloads.shock_bubble(128, steps=80), 80, {20, 40, 60, 80}, 1_000_000, 1),
-             learned.harvest_run(workloads.bubble_cloud(128, steps=80, seed=230509163), 80, {20, 40, 60, 80},
-                                 1_000_000, 2)]
+    parts = []
+    for name, n, steps, snaps, per, seed in runs:
+        wl = getattr(workloads, name)(n)
+        parts.append(learned.harvest_run(wl, steps, set(snaps), per, seed))
+        torch.cuda.empty_cache()
+    th = time.perf_counter()
     P, hist = learned.train(learned.Samples.cat(parts))
     torch.cuda.synchronize()
-    return P.cpu().numpy(), {"samples": sum(len(p) for p in parts), "final_loss": hist[-1],
-                             "seconds": time.perf_counter() - t0}
+    info = {"samples": sum(len(p) for p in parts),
+            "runs": ["%s %d^3, steps %s, %d per snapshot" % (name, n, list(snaps), per)
+                     for name, n, _, snaps, per, _ in runs],
+            "final_loss": hist[-1], "harvest_seconds": th - t0, "train_seconds": time.perf_counter() - th}
+    del parts
+    torch.cuda.empty_cache()
+    return P.cpu().numpy(), info
 
 
 def _sweep_profile(prof):
@@ -193,11 +237,12 @@ def _sweep_profile(prof):
     return ms, n
 
 
-def time_form(m, torch, wl, w_dev, form, steps, warmup, dist_barrier, sampler_gpu=None, mlp=None):
-    """Warm up, then time `steps` steps (CFL + SSP-RK3) of one form (FORMS) with
-    CUDA events on the solver's stream.  Returns a dict of measurements."""
+def time_form(m, torch, wl, w_dev, precision, params, steps, warmup, develop, dist_barrier, sampler_gpu=None,
+              mlp=None):
+    """Develop the initial state by `develop` steps, warm up by `warmup` more,
+    then time `steps` steps (CFL + SSP-RK3) with CUDA events on the solver's
+    stream.  Returns a dict of measurements."""
     stream = torch.cuda.current_stream()
-    precision, params, _ = FORMS[form]
     s = m.Solver(wl.n, wl.lo, wl.hi, wl.bc, wl.gamma, wl.pi_inf, precision=precision, fallback=1, **params)
     if wl.faces is not None:
         for d in range(3):
@@ -205,7 +250,7 @@ def time_form(m, torch, wl, w_dev, form, steps, warmup, dist_barrier, sampler_gp
     if mlp is not None:
         s.set_mlp(mlp)
     s.set_state_prim(w_dev)
-    for _ in range(warmup):
+    for _ in range(develop + warmup):
         s.step(s.cfl_dt(CFL))
     torch.cuda.synchronize()
     dist_barrier()
@@ -241,7 +286,7 @@ def time_form(m, torch, wl, w_dev, form, steps, warmup, dist_barrier, sampler_gp
     s.close()
     return {"ms_per_step": ms, "launches": launches, "sweep_ms": sweep_ms, "sweep_launches": sweep_n,
             "kernels": kern, "clocks": sampler.summary() if sampler else None, "fallback_faces": fb,
-            "network_rows": rows}
+            "network_rows": rows, "steps": steps, "warmup": warmup, "develop": develop}
 
 
 def e2e_form(m, torch, wl, w_host, precision, steps, warmup):
@@ -432,49 +477,129 @@ def _accuracy_case(m, torch, wl, key, mlp, t0):
     print(json.dumps(res), flush=True)
 
 
-def _accuracy_learned_2x(m, torch, mlp, training):
-    # learned vs WENO5-JS at 128^3 against FP64 at 256^3 (the 768^3 reference of the
-    # 384^3 cloud is out of reach of a bench run), same physical time
-    n = 128
-    fine = workloads.bubble_cloud(2 * n)
-    coarse = workloads.bubble_cloud(n)
+def _accuracy_learned_2x(m, torch, mlp, training, n=192, t_end=1.0e-4):
+    """Learned weights against WENO5-JS at the bubble cloud's own cell size
+    (1/384): a 192^3 box of the cloud ([0, 0.5] x [0.25, 0.75]^2, the shock and
+    the first bubbles), judged against the FP64 run of the same box at 2x
+    resolution (384^3) restricted to the coarse grid, same physical time; the
+    coarse runs start from the restricted fine initial state."""
+    fine = workloads.bubble_cloud_box(2 * n)
+    coarse = workloads.bubble_cloud_box(n)
     fw = fine.prims()
-    init = fw.reshape(fw.shape[0], n, 2, n, 2, n, 2).mean(axis=(2, 4, 6))
+    init = np.ascontiguousarray(fw.reshape(fw.shape[0], n, 2, n, 2, n, 2).mean(axis=(2, 4, 6)))
     del fw
-    t_end = 1.0e-4
+
     def run_to(wl, precision, mlp=None, init=None):
         s = m.Solver(wl.n, wl.lo, wl.hi, wl.bc, wl.gamma, wl.pi_inf, precision=precision, fallback=1)
         if mlp is not None:
             s.set_mlp(mlp)
         s.set_state_prim(torch.from_numpy(init if init is not None else wl.prims()).cuda())
-        t = 0.0
+        t, k = 0.0, 0
         while t < t_end:
             dt = min(s.cfl_dt(CFL), t_end - t)
             s.step(dt)
             t += dt
+            k += 1
         w = s.get_prims().cpu().numpy()
         s.close()
-        return w
-    ref = run_to(fine, "fp64")
+        torch.cuda.empty_cache()
+        return w, k
+    t0 = time.perf_counter()
+    ref, kf = run_to(fine, "fp64")
     ref = ref.reshape(ref.shape[0], n, 2, n, 2, n, 2).mean(axis=(2, 4, 6))
-    res = {"config": "3", "workload": "bubble_cloud 128^3 vs restricted FP64 256^3", "t_end": t_end,
-           "learned_vs_2x": _l1_fields(run_to(coarse, "learned", mlp, init), ref, 2),
-           "mixed_js_vs_2x": _l1_fields(run_to(coarse, "mixed", None, init), ref, 2),
-           "fp64_js_vs_2x": _l1_fields(run_to(coarse, "fp64", None, init), ref, 2),
-           "training": training}
+    wl_, kc = run_to(coarse, "learned", mlp, init)
+    res = {"config": "3", "workload": "bubble-cloud box %d^3 (cell 1/384) vs restricted FP64 %d^3" % (n, 2 * n),
+           "t_end": t_end, "steps_coarse": kc, "steps_fine": kf,
+           "learned_vs_2x": _l1_fields(wl_, ref, 2),
+           "mixed_js_vs_2x": _l1_fields(run_to(coarse, "mixed", None, init)[0], ref, 2),
+           "fp64_js_vs_2x": _l1_fields(run_to(coarse, "fp64", None, init)[0], ref, 2),
+           "training": training, "seconds": time.perf_counter() - t0}
+    res["learned_gain"] = {k: 1.0 - res["learned_vs_2x"][k] / res["mixed_js_vs_2x"][k] for k in ("rho", "p", "alpha")}
     print(json.dumps(res), flush=True)
+
+
+def _sweep_roofline_fp64(r, cells, ns, variant, nf, clocks):
+    """Roofline of the FP64 sweeps.  Their work runs mostly on the FP32 pipes
+    (the WENO weights and HLLC in float-float), and neither the FP64 pipe nor
+    DRAM is saturated: the binding resource is issue slots (latency-bound
+    dependency chains).  frac = warp instructions issued per second (the
+    stored per-cell count x cells x launches / the library's own launch times)
+    over 152 SMs x 4 schedulers x the SM clock sampled during the run; the
+    FP64-accurate algorithmic FLOP rate (oracle-counted work) is reported
+    beside it."""
+    sweep_s = r["sweep_ms"] * 1e-3
+    launches = r["sweep_launches"]
+    stages = launches / 3.0
+    flop = ORACLE_FLOP_PER_CELL_SWEEP[(variant, nf)] * cells * launches + RK_FLOP_PER_VAR_STAGE * ns * cells * stages
+    mhz = (clocks or {}).get("sm_mhz") or 2070.0
+    inst = sum(FP64_SWEEP_WARP_INST_PER_CELL) / 3.0 * cells * launches
+    achieved = inst / sweep_s / 1e9
+    peak = SCHEDULERS * mhz * 1e6 / 1e9
+    return {"bound": "alu", "resource": "issue slots", "kernel": "sweep (x, y, z)", "achieved": achieved,
+            "peak": peak, "unit": "Gwarp-inst/s", "frac": achieved / peak, "issue_frac": achieved / peak,
+            "peak_note": "152 SMs x 4 schedulers x 1 warp instruction per clock x the sampled SM clock (%.0f MHz)"
+                         % mhz,
+            "warp_inst_per_cell_per_sweep": sum(FP64_SWEEP_WARP_INST_PER_CELL) / 3.0,
+            "flop_tflops": flop / sweep_s / 1e12,
+            "flop_per_cell_per_sweep": ORACLE_FLOP_PER_CELL_SWEEP[(variant, nf)],
+            "flop_note": "FP64-accurate work of the oracle's plain formulation (counted), + RK update",
+            "fp64_pipe_frac_ncu": FP64_SWEEP_PIPE_FP64, "fma_pipe_frac_ncu": FP64_SWEEP_PIPE_FMA,
+            "traffic": FP64_SWEEP_DRAM_BYTES_PER_CELL * cells if FP64_SWEEP_DRAM_BYTES_PER_CELL else None,
+            "traffic_note": "DRAM bytes per sweep launch, per-cell counts of one ncu capture scaled by cells",
+            "ncu": NCU_FP64_SWEEPS}
+
+
+def _sweep_roofline_hbm(r, cells, ns, nw, variant, nf, peaks, learned=False):
+    """Mixed and learned forms: algorithmic DRAM bytes of the three sweeps of a
+    stage over the measured copy bandwidth, and the oracle-counted FLOPs (run in
+    FP32) over the nominal FP32 peak."""
+    sweep_s = r["sweep_ms"] * 1e-3
+    stages = r["sweep_launches"] / 3.0
+    hbm = float(peaks.get("hbm_gbs", 6800.0))
+    gbs = bytes_mixed_sweeps_stage(ns, nw) * cells * stages / sweep_s / 1e9
+    tf = ORACLE_FLOP_PER_CELL_SWEEP[(variant, nf)] * cells * r["sweep_launches"] / sweep_s / 1e12
+    out = {"bound": "hbm", "kernel": "sweep (x, y, z)", "achieved": gbs, "peak": hbm, "unit": "GB/s",
+           "frac": gbs / hbm, "hbm_gbs": gbs, "hbm_frac": gbs / hbm,
+           "bytes_per_cell_stage": bytes_mixed_sweeps_stage(ns, nw),
+           "fp32_tflops": tf, "fp32_peak": FP32_PEAK_TFLOPS, "fp32_frac": tf / FP32_PEAK_TFLOPS,
+           "note": "peaks: HBM of measured copy, FP32 nominal; FLOPs: the oracle's count, run in FP32"}
+    if learned:
+        edges = STENCILS_PER_CELL_SWEEP * cells * r["sweep_launches"]
+        tfl = FLOP_MLP_STENCIL * r["network_rows"] / sweep_s / 1e12
+        bf = float(peaks.get("bf16_tflops_sustained", 1700.0))
+        out.update({"kernel": "sweep (x, y, z) with the network", "network_edges": r["network_rows"],
+                    "network_fraction": r["network_rows"] / edges, "tensor_tflops": tfl, "tensor_peak": bf,
+                    "tensor_frac": tfl / bf})
+    return out
+
+
+def _form_entry(r, ws, cells, neq, head_ms=None):
+    g = grind_ns(r["ms_max"], ws, cells, neq)
+    e = {"grind": g, "unit": UNIT, "ms_per_step": r["ms_max"], "cell_updates_per_s": ws * cells / (r["ms_max"] * 1e-3),
+         "gpu_launches": r["launches"], "steps": r["steps"], "warmup": r["warmup"], "develop": r["develop"],
+         "kernels_ms": {k: v[0] for k, v in r["kernels"].items() if v[1]}, "workload": r["workload"],
+         "equations": neq, "fallback_faces": r["fallback_faces"]}
+    if head_ms is not None:
+        e["speedup_vs_fp64"] = head_ms / r["ms_max"]
+    if r.get("clocks"):
+        e["clocks"] = r["clocks"]
+    return e
 
 
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--develop", type=int, default=20,
+                    help="steps from the initial state before the warm-up (shock and interfaces developed)")
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
     ap.add_argument("--n", type=int, default=256, help="cells per direction of the shock-bubble cube")
     ap.add_argument("--forms", default="fp64,mixed,learned,fp64_weno3,mixed_weno3,fp64_kapila,fp64_stretched,"
                                        "mixed_stretched,fp64_cbc,fp64_six,mixed_six",
                     help="comma list of " + ",".join(FORMS))
+    ap.add_argument("--config-runs", default=",".join(CONFIG_RUNS),
+                    help="comma list of " + ",".join(CONFIG_RUNS) + " (or 'none'); each times at least 20 steps")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--accuracy", action="store_true",
@@ -514,126 +639,105 @@ def main():
     for f in forms:
         if f not in FORMS:
             raise SystemExit("unknown form %r (known: %s)" % (f, ", ".join(FORMS)))
+    runs = [c.strip() for c in args.config_runs.split(",") if c.strip() and c.strip() != "none"]
+    for c in runs:
+        if c not in CONFIG_RUNS:
+            raise SystemExit("unknown config run %r (known: %s)" % (c, ", ".join(CONFIG_RUNS)))
     results = {}
     training = None
+    mlp = None
+    if "learned" in forms or any(CONFIG_RUNS[c][1] == "learned" for c in runs):
+        mlp, training = train_learned(m, torch)
     head = "fp64" if "fp64" in forms else forms[0]
     stretched = None
     six_w = None
     for form in forms:
-        mlp = None
-        if form == "learned":
-            mlp, training = train_learned(m, torch)
+        precision, params, variant, _ = FORMS[form]
         fwl, fw = wl, w_dev
-        if FORMS[form][2] == "cbc":   # same cells and state, non-reflecting faces
+        if variant == "cbc":   # same cells and state, non-reflecting faces
             fwl = workloads.shock_bubble_cbc(args.n)
-        if FORMS[form][2] == "six":   # same cells and state, phases in pressure equilibrium
+        if variant == "six":   # same cells and state, phases in pressure equilibrium
             if six_w is None:
                 six_w = torch.from_numpy(workloads.six_equation_prims(w_host, wl.nf)).cuda()
             fw = six_w
-        if FORMS[form][2] == "stretched":
+        if variant == "stretched":
             if stretched is None:
                 swl = workloads.shock_bubble_stretched(args.n)
                 stretched = (swl, torch.from_numpy(swl.prims()).cuda())
             fwl, fw = stretched
-        r = time_form(m, torch, fwl, fw, form, args.steps, args.warmup, barrier,
-                      sampler_gpu=local if form == head else None, mlp=mlp)
+        r = time_form(m, torch, fwl, fw, precision, params, args.steps, args.warmup, args.develop, barrier,
+                      sampler_gpu=local if form == head else None, mlp=mlp if precision == "learned" else None)
         r["workload"] = fwl.name
         r["ms_max"] = max_over_ranks(r["ms_per_step"], ws, "cuda")
         results[form] = r
+    del six_w, stretched
+    torch.cuda.empty_cache()
 
     fp = results[head]
     ms = fp["ms_max"]
     grind = grind_ns(ms, ws, cells, ns)
-    flops_per_sweep_launch = (FLOP_SWEEP_CELL_3D_2F + FLOP_RK_CELL_2F / 3.0) * cells
-    achieved = flops_per_sweep_launch * fp["sweep_launches"] / (fp["sweep_ms"] * 1e-3) / 1e12
-
+    peaks = _measured_peaks()
     line = {
         "metric": METRIC, "value": grind, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": False, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": wl.name + " (FP64, 2 fluids, 7 equations)", "cells": cells, "sys_size": ns,
-                   "rhs_per_step": 3, "cfl": CFL, "parallelism": "replicas" if ws > 1 else "single-gpu",
-                   "l2": "inputs larger than L2 (state %.2f GB per array)" % (cells * ns * 8 / 1e9)},
+                   "rhs_per_step": 3, "cfl": CFL, "develop_steps": args.develop,
+                   "parallelism": "replicas" if ws > 1 else "single-gpu",
+                   "l2": "inputs larger than L2 (state %.2f GB per array)" % (cells * ns * 8 / 1e9),
+                   "arithmetic": "FP64 state, primitives, differences, fluxes, RK; WENO weights and HLLC in "
+                                 "float-float (~48 bits, FP32 exponent range); parity <= 1e-11 vs the FP64 oracle"},
         "cell_updates_per_s": ws * cells / (ms * 1e-3),
-        "roofline": {"bound": "alu", "kernel": "sweep (x, y, z)", "achieved": achieved,
-                     "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS,
-                     "peak_note": "nominal FP64: 152 SMs x 4 FLOP/clk x 2.07 GHz",
-                     "flop_per_cell_per_sweep": FLOP_SWEEP_CELL_3D_2F,
-                     "traffic": FP64_SWEEP_DRAM_BYTES_PER_CELL * cells if head == "fp64" else None,
-                     "traffic_note": "DRAM bytes per sweep launch (ncu at 160^3, scaled by cells)",
-                     "ncu_issue_active": 0.48,
-                     "note": "FLOPs at FP64 accuracy; the WENO weights and HLLC run in float-float on the FP32 "
-                             "pipes, so the rate can pass the FP64 pipe's nominal peak.  ncu (160^3): FP64 pipe "
-                             "44-51% busy, issue 48-49% active (ncu_issue_active: their mean), ~12 warps per SM: "
-                             "latency-bound"},
+        "roofline": _sweep_roofline_fp64(fp, cells, ns, "weno5", wl.nf, fp["clocks"]) if head == "fp64" else None,
         "gpu_launches": fp["launches"],
         "kernels_ms": {k: v[0] for k, v in fp["kernels"].items() if v[1]},
         "fallback_faces": fp["fallback_faces"],
         "clocks": fp["clocks"],
         "forms": {},
+        "configs": {},
     }
     for form, r in results.items():
         if form == head:
             continue
-        if r is None:
-            line["forms"][form] = None
-            continue
+        precision, params, variant, work = FORMS[form]
+        six = variant == "six"
         # equations per cell: the six-equation model adds the N phase energies
-        neq = ns + wl.nf if FORMS[form][2] == "six" else ns
-        g = grind_ns(r["ms_max"], ws, cells, neq)
-        entry = {"grind": g, "unit": UNIT, "ms_per_step": r["ms_max"],
-                 "cell_updates_per_s": ws * cells / (r["ms_max"] * 1e-3),
-                 "speedup_vs_fp64": ms / r["ms_max"], "gpu_launches": r["launches"],
-                 "kernels_ms": {k: v[0] for k, v in r["kernels"].items() if v[1]}}
-        sweep_s = r["sweep_ms"] * 1e-3
-        stages = r["sweep_launches"] / 3.0
-        peaks = _measured_peaks()
-        hbm = float(peaks.get("hbm_gbs", 6800.0))
-        entry["workload"] = r["workload"]
-        entry["equations"] = neq
-        if form in ("fp64_weno3", "fp64_kapila", "fp64_stretched", "fp64_cbc", "fp64_six"):
-            fl = {"fp64_weno3": FLOP_SWEEP_CELL_3D_2F_W3, "fp64_kapila": FLOP_SWEEP_CELL_3D_2F_KAPILA,
-                  "fp64_stretched": FLOP_SWEEP_CELL_3D_2F, "fp64_cbc": FLOP_SWEEP_CELL_3D_2F,
-                  "fp64_six": FLOP_SWEEP_CELL_3D_2F}[form]
-            tf = (fl + FLOP_RK_CELL_2F / 3.0) * cells * r["sweep_launches"] / sweep_s / 1e12
-            entry["roofline"] = {"kernel": "sweep (x, y, z), " + {"fp64_weno3": "WENO3", "fp64_kapila": "Kapila",
-                                                                  "fp64_stretched": "non-uniform grid",
-                                                                  "fp64_cbc": "characteristic boundaries",
-                                                                  "fp64_six": "six-equation model"}[form],
-                                 "bound": "alu", "achieved": tf,
-                                 "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": tf / FP64_PEAK_TFLOPS,
-                                 "flop_per_cell_per_sweep": fl,
-                                 "note": "nominal FP64 peak as for the WENO5 form" + (
-                                     "; FLOPs counted as on a uniform grid (the per-cell coefficients add work)"
-                                     if form == "fp64_stretched" else
-                                     "; FLOPs counted as the five-equation sweep (the phase-energy rows and the "
-                                     "relaxation add work)" if form == "fp64_six" else "")}
-        elif form in ("mixed", "mixed_weno3", "mixed_stretched", "mixed_six"):
-            gbs = BYTES_MIXED_SWEEPS_STAGE * cells * stages / sweep_s / 1e9
-            fl = FLOP_SWEEP_CELL_3D_2F_W3 if form == "mixed_weno3" else FLOP_SWEEP_CELL_3D_2F
-            tf = fl * cells * r["sweep_launches"] / sweep_s / 1e12
-            entry["roofline"] = {"kernel": "sweep (x, y, z)", "hbm_gbs": gbs, "hbm_peak": hbm,
-                                 "hbm_frac": gbs / hbm, "fp32_tflops": tf, "fp32_peak": FP32_PEAK_TFLOPS,
-                                 "fp32_frac": tf / FP32_PEAK_TFLOPS,
-                                 "note": "peaks: HBM of measured copy, FP32 nominal"}
-        elif form == "learned":
-            # the sweeps do the mixed form's work plus the sensor and, on the
-            # edges it does not trip, the network (counted on the device)
-            gbs = BYTES_MIXED_SWEEPS_STAGE * cells * stages / sweep_s / 1e9
-            tf = FLOP_SWEEP_CELL_3D_2F * cells * r["sweep_launches"] / sweep_s / 1e12
-            edges = STENCILS_PER_CELL_SWEEP * cells * r["sweep_launches"]
-            tfl = FLOP_MLP_STENCIL * r["network_rows"] / sweep_s / 1e12
-            bf = float(peaks.get("bf16_tflops_sustained", 1700.0))
-            entry["roofline"] = {"kernel": "sweep (x, y, z) with the network", "hbm_gbs": gbs, "hbm_peak": hbm,
-                                 "hbm_frac": gbs / hbm, "fp32_tflops": tf, "fp32_peak": FP32_PEAK_TFLOPS,
-                                 "fp32_frac": tf / FP32_PEAK_TFLOPS,
-                                 "network_edges": r["network_rows"], "network_fraction": r["network_rows"] / edges,
-                                 "tensor_tflops": tfl, "tensor_peak": bf, "tensor_frac": tfl / bf,
-                                 "note": "HBM/FP32 as the mixed form (its algorithmic bytes and FLOPs); network "
-                                         "FLOPs of the edges evaluated, averaged over the sweep time; peaks: HBM "
-                                         "of measured copy, FP32 nominal, BF16 measured sustained"}
-            entry["training"] = training
+        neq = ns + wl.nf if six else ns
+        entry = _form_entry(r, ws, cells, neq, ms)
+        if precision == "fp64":
+            entry["roofline"] = _sweep_roofline_fp64(r, cells, neq, work, wl.nf, fp["clocks"])
+            entry["roofline"]["note"] = ("instruction count per cell of the FP64 WENO5 sweeps (not re-measured "
+                                         "for this form); FLOPs of the oracle's %s formulation%s"
+                                         % (work, "; the per-cell tables of the stretched grid and the "
+                                            "six-equation rows and relaxation add work" if variant in
+                                            ("stretched", "six") else ""))
+        else:
+            entry["roofline"] = _sweep_roofline_hbm(r, cells, neq, ns, work, wl.nf, peaks,
+                                                    learned=precision == "learned")
+            if precision == "learned":
+                entry["training"] = training
         line["forms"][form] = entry
+    for name in runs:
+        wname, precision = CONFIG_RUNS[name]
+        cwl = getattr(workloads, wname)()
+        cw = torch.from_numpy(cwl.prims()).cuda()
+        r = time_form(m, torch, cwl, cw, precision, {}, max(args.steps, 20), args.warmup, args.develop, barrier,
+                      sampler_gpu=local, mlp=mlp if precision == "learned" else None)
+        del cw
+        torch.cuda.empty_cache()
+        r["workload"] = cwl.name
+        r["ms_max"] = max_over_ranks(r["ms_per_step"], ws, "cuda")
+        entry = _form_entry(r, ws, cwl.ncell, cwl.sys_size)
+        entry["config"] = {"workload": cwl.name, "cells": cwl.ncell, "fluids": cwl.nf, "form": precision,
+                           "notes": cwl.notes}
+        if precision == "fp64":
+            entry["roofline"] = _sweep_roofline_fp64(r, cwl.ncell, cwl.sys_size, "weno5", cwl.nf, r["clocks"])
+            if cwl.nf != 2:
+                entry["roofline"]["note"] = "instruction count per cell of the two-fluid FP64 sweeps"
+        else:
+            entry["roofline"] = _sweep_roofline_hbm(r, cwl.ncell, cwl.sys_size, cwl.sys_size, "weno5", cwl.nf, peaks,
+                                                    learned=precision == "learned")
+        line["configs"][name] = entry
     if not args.no_e2e:
         k = max(2, min(args.steps, 5))
         dt, nbytes = e2e_form(m, torch, wl, w_host, "fp64", k, 1)

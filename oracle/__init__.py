@@ -221,6 +221,93 @@ def rhs(pb: Problem, q, return_info: bool = False):
     return out
 
 
+_COUNTED_SRC = os.path.join(_HERE, "mfc_oracle_counted.cpp")
+_COUNTED_LIB = os.path.join(_HERE, "libmfc_oracle_counted.so")
+_counted = None
+
+
+def _load_counted():
+    """The operation-counting build (mfc_oracle_counted.cpp + flop_count.h):
+    the same C source compiled as C++ with every double a counting type, one
+    thread, no OpenMP."""
+    global _counted
+    with _lock:
+        if _counted is None:
+            deps = [_SRC, _COUNTED_SRC, os.path.join(_HERE, "flop_count.h")]
+            if not os.path.exists(_COUNTED_LIB) or any(os.path.getmtime(_COUNTED_LIB) < os.path.getmtime(d)
+                                                       for d in deps):
+                tmp = _COUNTED_LIB + ".tmp%d" % os.getpid()
+                subprocess.check_call(["g++", "-std=c++17", "-O1", "-ffp-contract=off", "-fPIC", "-shared",
+                                       "-o", tmp, _COUNTED_SRC, "-lm"])
+                os.replace(tmp, _COUNTED_LIB)
+            lib = ctypes.CDLL(_COUNTED_LIB)
+            dp = ctypes.POINTER(ctypes.c_double)
+            lib.oracle_rhs.argtypes = [ctypes.POINTER(Params), dp, dp, dp]
+            lib.oracle_rhs.restype = ctypes.c_long
+            lib.oracle_face.argtypes = [ctypes.POINTER(Params), dp, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                        ctypes.c_int, dp, dp]
+            lib.oracle_face.restype = ctypes.c_int
+            lib.oracle_cons_to_prim_array.argtypes = [ctypes.POINTER(Params), dp, dp, ctypes.c_long]
+            lib.oracle_flop_reset.argtypes = []
+            lib.oracle_flop_read.restype = ctypes.c_ulonglong
+            _counted = lib
+    return _counted
+
+
+def rhs_flops(pb: Problem, q):
+    """Floating-point operations (+ - * / and sqrt, one each) that the oracle's
+    plain formulation spends on one R(q), counted by the counting build; and
+    R(q) itself (equal to ``rhs``)."""
+    q = _state(pb, q)
+    out = np.empty_like(q)
+    fmax = np.zeros(pb.sys_size)
+    lib = _load_counted()
+    lib.oracle_flop_reset()
+    lib.oracle_rhs(ctypes.byref(pb.params()), _dp(q), _dp(out), _dp(fmax))
+    return int(lib.oracle_flop_read()), out.reshape(pb.shape())
+
+
+def rhs_flop_breakdown(pb: Problem, q) -> dict:
+    """The algorithmic work of one R(q), from the counting build, per unit of
+    the method (Sec. 3.1-3.2): ``prims`` per cell (conserved -> primitive, once
+    per cell), ``face`` per face and direction (WENO edges of every variable on
+    both sides plus HLLC, averaged over the faces: HLLC's branch decides part of
+    the count), ``div`` per cell and direction (flux difference and
+    volume-fraction source), and ``per_cell_sweep`` = prims/ndim + face + div,
+    the work of one directional sweep per cell with one face per cell.  The
+    oracle itself recomputes the primitives of the six cells around every face
+    and visits n + 1 faces per row; those repeats are taken out here."""
+    q = _state(pb, q)
+    lib = _load_counted()
+    P = pb.params()
+    w = np.empty_like(q)
+    lib.oracle_flop_reset()
+    lib.oracle_cons_to_prim_array(ctypes.byref(P), _dp(q), _dp(w), pb.ncell)
+    c_prim = lib.oracle_flop_read() / pb.ncell
+    total, _ = rhs_flops(pb, q)
+    F = np.empty(pb.sys_size)
+    ut = np.empty(1)
+    face_work = 0.0        # WENO + HLLC over all faces (one face per cell and direction)
+    face_calls = 0.0       # everything oracle_face counted, per direction
+    for d in range(pb.ndim):
+        m = list(pb.n)
+        m[d] += 1
+        cnt = 0
+        for k in range(m[2]):
+            for j in range(m[1]):
+                for i in range(m[0]):
+                    lib.oracle_flop_reset()
+                    lib.oracle_face(ctypes.byref(P), _dp(q), d, i, j, k, _dp(F), _dp(ut))
+                    cnt += lib.oracle_flop_read()
+        nface = m[0] * m[1] * m[2]
+        face_calls += cnt
+        face_work += (cnt / nface - 6 * c_prim) * pb.ncell
+    c_div = (total - face_calls) / (pb.ncell * pb.ndim)
+    c_face = face_work / (pb.ncell * pb.ndim)
+    return {"prims": c_prim, "face": c_face, "div": c_div, "rhs_total": total,
+            "per_cell_sweep": c_prim / pb.ndim + c_face + c_div}
+
+
 def rhs_cells(pb: Problem, q, cells, return_fmax: bool = False):
     """R at the given flat cell indices; result [len(cells)][sys_size]
     (and, with return_fmax, the per-variable max |F| over the faces visited)."""

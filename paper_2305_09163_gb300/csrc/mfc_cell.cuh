@@ -465,6 +465,164 @@ __device__ __forceinline__ void stage_finish_operands(const SweepArgs& a, long l
     cp_async_commit();
 }
 
+// ---------------------------------------------------------------------------
+// Conserved -> primitive (Sec. 2.1): rho = sum a_k r_k, u = (rho u)/rho,
+// p = (rho E - rho|u|^2/2 - Pi)/Gamma.  FP64 path: all in FP64.  Mixed path:
+// rho E - Pi (the water Pi ~ 7.8e8 Pa cancels against rho E) and the kinetic
+// energy subtraction stay FP64, the rest is FP32.  Optionally the CFL rate
+// max_d (|u_d| + c)/dx_d with c^2 = ((Gamma+1)p + Pi)/(Gamma rho), reduced to one
+// max per launch with an order-preserving integer atomic (non-negative
+// doubles), so it is exact and independent of scheduling.  Six-equation model
+// (SIX): the frozen sound speed, r c^2 = A p + B (Sec. 2.3).
+// ---------------------------------------------------------------------------
+template <int NF, int NDIM, bool SIX = false>
+__device__ __forceinline__ void prims_cell(const double* q, const EosConst& e, double* wv, double& c2) {
+    using Lay = Layout<NF, NDIM>;
+    constexpr int IM = Lay::IM, IE = Lay::IE, IA = Lay::IA;
+    double rho = q[0];
+#pragma unroll
+    for (int k = 1; k < NF; ++k) rho += q[k];
+    double G = e.G_N, P = e.P_N;
+#pragma unroll
+    for (int k = 0; k < NF - 1; ++k) {
+        G = fma(q[IA + k], e.dG[k], G);
+        P = fma(q[IA + k], e.dP[k], P);
+    }
+    const double x = rcp_nr(rho * G);   // FP32 seed + cubic Newton step: 3 FP64 instructions
+    const double irho = G * x, iG = rho * x;
+    double ke = 0.0;
+#pragma unroll
+    for (int d = 0; d < NDIM; ++d) { wv[IM + d] = q[IM + d] * irho; ke = fma(q[IM + d], wv[IM + d], ke); }
+    const double p = (q[IE] - 0.5 * ke - P) * iG;
+#pragma unroll
+    for (int k = 0; k < NF; ++k) wv[k] = q[k];
+    wv[IE] = p;
+#pragma unroll
+    for (int k = 0; k < NF - 1; ++k) wv[IA + k] = q[IA + k];
+    if constexpr (SIX) {
+        double A = e.A_N, B = e.B_N;
+#pragma unroll
+        for (int k = 0; k < NF - 1; ++k) {
+            A = fma(q[IA + k], e.dA[k], A);
+            B = fma(q[IA + k], e.dB[k], B);
+        }
+        c2 = fma(A, p, B) * irho;
+    } else {
+        c2 = fma(G + 1.0, p, P) * iG * irho;
+    }
+}
+
+// FP32 form: the per-cell FP64 -> FP32 conversions by integer operations
+// (narrow_rn, df_widen), since conversion instructions run on the FP64 pipe.
+template <int NF, int NDIM, bool SIX = false>
+__device__ __forceinline__ void prims_cell(const double* q, const EosConst& e, float* wv, float& c2) {
+    using Lay = Layout<NF, NDIM>;
+    constexpr int IM = Lay::IM, IE = Lay::IE, IA = Lay::IA;
+    float qf[Lay::NS];
+#pragma unroll
+    for (int v = 0; v < Lay::NS; ++v) qf[v] = v == IE ? 0.f : narrow_rn(q[v]);
+    float rho = qf[0];
+#pragma unroll
+    for (int k = 1; k < NF; ++k) rho += qf[k];
+    float G = (float)e.G_N;
+    double P = e.P_N;
+#pragma unroll
+    for (int k = 0; k < NF - 1; ++k) {
+        G = fmaf(qf[IA + k], (float)e.dG[k], G);
+        P = fma(q[IA + k], e.dP[k], P);
+    }
+    const float irho = __fdividef(1.0f, rho);
+    float ke = 0.f;
+#pragma unroll
+    for (int d = 0; d < NDIM; ++d) {
+        const float m = qf[IM + d];
+        wv[IM + d] = m * irho;
+        ke = fmaf(m, wv[IM + d], ke);
+    }
+    const double eint = fma(-0.5, df_widen(ke), q[IE] - P);
+    const float p = __fdividef(narrow_rn(eint), G);
+#pragma unroll
+    for (int k = 0; k < NF; ++k) wv[k] = qf[k];
+    wv[IE] = p;
+#pragma unroll
+    for (int k = 0; k < NF - 1; ++k) wv[IA + k] = qf[IA + k];
+    if constexpr (SIX) {
+        float A = (float)e.A_N, B = (float)e.B_N;
+#pragma unroll
+        for (int k = 0; k < NF - 1; ++k) {
+            A = fmaf(qf[IA + k], (float)e.dA[k], A);
+            B = fmaf(qf[IA + k], (float)e.dB[k], B);
+        }
+        c2 = __fdividef(fmaf(A, p, B), rho);
+    } else {
+        c2 = __fdividef(fmaf(G + 1.0f, p, narrow_rn(P)), G * rho);
+    }
+}
+
+// CFL rate of one cell from its primitives (Sec. 1: the CFL restriction),
+// max_d (|u_d| + c)/dx_d, in the arithmetic of the path (FP64: the root in
+// float-float, ~2^-46 relative, off the FP64 pipe; FP32 forms: FP32), or -1
+// for a non-physical cell (c^2 <= 0 or a non-finite value).  i: the cell's
+// index (non-uniform grids take its widths from the tables).  Shared by the
+// primitive-recovery kernel and the fused RK epilogue, so both give the same
+// bits.
+template <typename Real, int NF, int NDIM>
+__device__ __forceinline__ double cell_cfl_rate(const Real* wv, Real c2, const Geometry& g, const float* const* grid,
+                                                const int* grid_stride, long long i) {
+    constexpr int IM = Layout<NF, NDIM>::IM;
+    Real us = 0;
+#pragma unroll
+    for (int d = 0; d < NDIM; ++d) us += wv[IM + d];
+    if (!(c2 > (Real)0) || !(c2 - c2 == (Real)0) || !(us - us == (Real)0)) return -1.0;
+    Real cs;
+    if constexpr (sizeof(Real) == 8) cs = df_to_double(df_sqrt(df_from_double(c2)));
+    else cs = real_sqrt(c2);
+    Real r = 0;
+    int ci[3] = {0, 0, 0};
+    if (grid[0] || grid[1] || grid[2]) {   // non-uniform: this cell's widths
+        const unsigned ii = (unsigned)i, nx = (unsigned)g.n[0], ny = (unsigned)g.n[1];
+        ci[0] = (int)(ii % nx);
+        ci[1] = (int)((ii / nx) % ny);
+        ci[2] = (int)(ii / (nx * ny));
+    }
+#pragma unroll
+    for (int d = 0; d < NDIM; ++d) {
+        const Real inv = !grid[d] ? (Real)g.inv_dx[d]
+                         : d == 0 ? grid_inv_dx<true>(grid[d], grid_stride[d], ci[d], Real(0))
+                                  : grid_inv_dx<false>(grid[d], grid_stride[d], ci[d], Real(0));
+        r = real_max(r, (fabs(wv[IM + d]) + cs) * inv);
+    }
+    return (double)r;
+}
+
+// Running CFL maximum and non-physical count of the cells a thread finished
+// (fused RK epilogue), published once per kernel: the converged lanes reduce
+// the ordered bits of the non-negative rate (high word, then the low word among
+// the lanes holding the largest high word) and one lane does the atomics.
+struct RateAcc {
+    double rate = 0.0;
+    int bad = 0;
+    __device__ __forceinline__ void add(double r) {
+        if (r < 0.0) bad += 1;
+        else rate = fmax(rate, r);
+    }
+};
+
+__device__ __forceinline__ void publish_rate(const SweepArgs& a, const RateAcc& acc) {
+    if (!a.rate_max) return;
+    const unsigned mask = __activemask();
+    const unsigned long long bits = (unsigned long long)__double_as_longlong(acc.rate);
+    const unsigned hi = (unsigned)(bits >> 32);
+    const unsigned mhi = __reduce_max_sync(mask, hi);
+    const unsigned mlo = __reduce_max_sync(mask, hi == mhi ? (unsigned)bits : 0u);
+    const unsigned nbad = __reduce_add_sync(mask, (unsigned)acc.bad);
+    if ((int)(threadIdx.x & 31) == __ffs((int)mask) - 1) {
+        atomicMax(a.rate_max, ((unsigned long long)mhi << 32) | mlo);
+        if (nbad) atomicAdd(a.bad, (int)nbad);
+    }
+}
+
+
 // Finish cell idx (coordinate b along DIR, neighbours sd apart, transverse
 // flat index tr or -1): flux difference and alpha div(u) source, or, at a
 // characteristic boundary, the boundary rate (from cbc_rates when the caller
@@ -476,10 +634,16 @@ __device__ __forceinline__ void stage_finish_operands(const SweepArgs& a, long l
 //
 // stg (y/z stream kernels, or null): this lane's operands staged by
 // stage_finish_operands, complete (cp_async_wait_all) before the call.
+//
+// Fused primitive recovery (FP64 form, five-equation models, RK stage update
+// with a.w_next set): the new state of the cell is in registers, so its primitives
+// are written to a.w_next (the next stage's sweeps read them there instead of
+// a separate recovery pass over q) and, with a.rate_max, its CFL rate is
+// returned for the caller's RateAcc (-1: non-physical); otherwise 0.
 template <typename Real, int NF, int NDIM, int DIR, bool SIX = false>
-__device__ __forceinline__ void finish_cell(const SweepArgs& a, long long idx, const Real* Fm, const Real* Fp,
-                                            Real um, Real up, const Real* cell, Real inv_dx, int b, long long sd,
-                                            long long tr = -1, const unsigned char* stg = nullptr, int slot = 0) {
+__device__ __forceinline__ double finish_cell(const SweepArgs& a, long long idx, const Real* Fm, const Real* Fp,
+                                              Real um, Real up, const Real* cell, Real inv_dx, int b, long long sd,
+                                              long long tr = -1, const unsigned char* stg = nullptr, int slot = 0) {
     using Lay = Layout<NF, NDIM, SIX>;
     constexpr int NS = Lay::NS, NQ = Lay::NQ, IA = Lay::IA;
     Real out[NQ];
@@ -548,7 +712,7 @@ __device__ __forceinline__ void finish_cell(const SweepArgs& a, long long idx, c
 #pragma unroll
         for (int v = 0; v < NQ; ++v) R[v * nc + idx] = Rv(v) + out[v];
     } else if (a.mode == 2) {
-        double qn[SIX ? NQ : 1];
+        double qn[NQ];
         // FP32 forms: the increment c1 dt R is formed in FP32 (R is an FP32
         // quantity there) and widened by integer operations, so the FP64
         // accumulation takes one FP64 operation per value, two with the q0
@@ -567,13 +731,25 @@ __device__ __forceinline__ void finish_cell(const SweepArgs& a, long long idx, c
                 if (!unit) o *= a.c1;
             }
             if (a.c0 != 0.0) o = fma(a.c0, q0v(v), o);
-            if constexpr (SIX) qn[v] = o;
-            else a.qout[v * nc + idx] = o;
+            qn[v] = o;
+            if constexpr (!SIX) a.qout[v * nc + idx] = o;
         }
         if constexpr (SIX) {
             relax6<NF, NDIM>(a, qn);
 #pragma unroll
             for (int v = 0; v < NQ; ++v) a.qout[v * nc + idx] = qn[v];
+        } else if constexpr (sizeof(Real) == 8) {
+            // FP64 form only: in the FP32 forms' z sweep (memory-bound, 64
+            // registers) the fused recovery spilled and cost more than the
+            // separate pass it replaced (mixed 6.27 -> 6.52 ms per step at 256^3)
+            if (a.w_next) {
+                Real wv[NS], c2;
+                prims_cell<NF, NDIM>(qn, a.e, wv, c2);
+                Real* wn = static_cast<Real*>(a.w_next);
+#pragma unroll
+                for (int v = 0; v < NS; ++v) wn[v * nc + idx] = wv[v];
+                if (a.rate_max) return cell_cfl_rate<Real, NF, NDIM>(wv, c2, a.g, a.grid, a.grid_stride, idx);
+            }
         }
     } else {
 #pragma unroll
@@ -582,6 +758,7 @@ __device__ __forceinline__ void finish_cell(const SweepArgs& a, long long idx, c
             a.out[v * nc + idx] = (double)rv;
         }
     }
+    return 0.0;
 }
 
 }  // namespace mfc

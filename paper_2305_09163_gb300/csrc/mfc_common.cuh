@@ -54,6 +54,9 @@ struct SweepArgs {
     const double* qs;       // RK: current stage state
     double* qout;           // RK: output stage state (may alias qs or q0)
     double* out;            // mode 3: float64 right-hand side output
+    void* w_next;           // mode 2, optional: primitives of qout [NS][ncell], Real (five-equation models)
+    unsigned long long* rate_max;  // with w_next, optional: CFL rate of qout, max as ordered bits
+    int* bad;               // with rate_max: count of non-physical cells of qout
     double c0, c1, dt;      // RK: qout = c0 q0 + c1 (qs + dt (R + s))
     double eps;             // WENO epsilon
     int fallback;           // first-order fallback at non-physical faces

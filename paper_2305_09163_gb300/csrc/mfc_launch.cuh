@@ -109,6 +109,13 @@ cudaError_t launch_sweep(SweepArgs a, int ndim, int dir, cudaStream_t s) {
                 case 14: return launch_yz_stream<Real, !NONUNIF>(sweep_yz_stream_f64_kernel<NF, 3, 2, ORDER, NONUNIF, SIX>, blocks, a, nq(3), s);
                 default: return cudaErrorInvalidValue;
             }
+        } else if constexpr (sizeof(Real) == 8 && NF == 3 && ORDER == 5) {
+            switch (ndim * 4 + dir) {
+                case 9: return launch_yz_stream<Real, true>(sweep_yz_stream_f64b3_kernel<NF, 2, 1>, blocks, a, nq(2), s);
+                case 13: return launch_yz_stream<Real, true>(sweep_yz_stream_f64b3_kernel<NF, 3, 1>, blocks, a, nq(3), s);
+                case 14: return launch_yz_stream<Real, true>(sweep_yz_stream_f64b3_kernel<NF, 3, 2>, blocks, a, nq(3), s);
+                default: return cudaErrorInvalidValue;
+            }
         } else if constexpr (SIX && sizeof(Real) == 4) {
             switch (ndim * 4 + dir) {
                 case 9: return launch_yz_stream<Real, true>(sweep_yz_stream_six32_kernel<NF, 2, 1, ORDER, NONUNIF>, blocks, a, nq(2), s);

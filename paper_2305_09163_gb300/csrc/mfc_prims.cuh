@@ -5,104 +5,13 @@
 
 namespace mfc {
 
-// ---------------------------------------------------------------------------
-// Conserved -> primitive (Sec. 2.1): rho = sum a_k r_k, u = (rho u)/rho,
-// p = (rho E - rho|u|^2/2 - Pi)/Gamma.  FP64 path: all in FP64.  Mixed path:
-// rho E - Pi (the water Pi ~ 7.8e8 Pa cancels against rho E) and the kinetic
-// energy subtraction stay FP64, the rest is FP32.  Optionally the CFL rate
-// max_d (|u_d| + c)/dx_d with c^2 = ((Gamma+1)p + Pi)/(Gamma rho), reduced to one
-// max per launch with an order-preserving integer atomic (non-negative
-// doubles), so it is exact and independent of scheduling.  Six-equation model
-// (SIX): the frozen sound speed, r c^2 = A p + B (Sec. 2.3).
-// ---------------------------------------------------------------------------
-template <int NF, int NDIM, bool SIX = false>
-__device__ __forceinline__ void prims_cell(const double* q, const EosConst& e, double* wv, double& c2) {
-    using Lay = Layout<NF, NDIM>;
-    constexpr int IM = Lay::IM, IE = Lay::IE, IA = Lay::IA;
-    double rho = q[0];
-#pragma unroll
-    for (int k = 1; k < NF; ++k) rho += q[k];
-    double G = e.G_N, P = e.P_N;
-#pragma unroll
-    for (int k = 0; k < NF - 1; ++k) {
-        G = fma(q[IA + k], e.dG[k], G);
-        P = fma(q[IA + k], e.dP[k], P);
-    }
-    const double x = rcp_nr(rho * G);   // FP32 seed + cubic Newton step: 3 FP64 instructions
-    const double irho = G * x, iG = rho * x;
-    double ke = 0.0;
-#pragma unroll
-    for (int d = 0; d < NDIM; ++d) { wv[IM + d] = q[IM + d] * irho; ke = fma(q[IM + d], wv[IM + d], ke); }
-    const double p = (q[IE] - 0.5 * ke - P) * iG;
-#pragma unroll
-    for (int k = 0; k < NF; ++k) wv[k] = q[k];
-    wv[IE] = p;
-#pragma unroll
-    for (int k = 0; k < NF - 1; ++k) wv[IA + k] = q[IA + k];
-    if constexpr (SIX) {
-        double A = e.A_N, B = e.B_N;
-#pragma unroll
-        for (int k = 0; k < NF - 1; ++k) {
-            A = fma(q[IA + k], e.dA[k], A);
-            B = fma(q[IA + k], e.dB[k], B);
-        }
-        c2 = fma(A, p, B) * irho;
-    } else {
-        c2 = fma(G + 1.0, p, P) * iG * irho;
-    }
-}
-
-// FP32 form: the per-cell FP64 -> FP32 conversions by integer operations
-// (narrow_rn, df_widen), since conversion instructions run on the FP64 pipe.
-template <int NF, int NDIM, bool SIX = false>
-__device__ __forceinline__ void prims_cell(const double* q, const EosConst& e, float* wv, float& c2) {
-    using Lay = Layout<NF, NDIM>;
-    constexpr int IM = Lay::IM, IE = Lay::IE, IA = Lay::IA;
-    float qf[Lay::NS];
-#pragma unroll
-    for (int v = 0; v < Lay::NS; ++v) qf[v] = v == IE ? 0.f : narrow_rn(q[v]);
-    float rho = qf[0];
-#pragma unroll
-    for (int k = 1; k < NF; ++k) rho += qf[k];
-    float G = (float)e.G_N;
-    double P = e.P_N;
-#pragma unroll
-    for (int k = 0; k < NF - 1; ++k) {
-        G = fmaf(qf[IA + k], (float)e.dG[k], G);
-        P = fma(q[IA + k], e.dP[k], P);
-    }
-    const float irho = __fdividef(1.0f, rho);
-    float ke = 0.f;
-#pragma unroll
-    for (int d = 0; d < NDIM; ++d) {
-        const float m = qf[IM + d];
-        wv[IM + d] = m * irho;
-        ke = fmaf(m, wv[IM + d], ke);
-    }
-    const double eint = fma(-0.5, df_widen(ke), q[IE] - P);
-    const float p = __fdividef(narrow_rn(eint), G);
-#pragma unroll
-    for (int k = 0; k < NF; ++k) wv[k] = qf[k];
-    wv[IE] = p;
-#pragma unroll
-    for (int k = 0; k < NF - 1; ++k) wv[IA + k] = qf[IA + k];
-    if constexpr (SIX) {
-        float A = (float)e.A_N, B = (float)e.B_N;
-#pragma unroll
-        for (int k = 0; k < NF - 1; ++k) {
-            A = fmaf(qf[IA + k], (float)e.dA[k], A);
-            B = fmaf(qf[IA + k], (float)e.dB[k], B);
-        }
-        c2 = __fdividef(fmaf(A, p, B), rho);
-    } else {
-        c2 = __fdividef(fmaf(G + 1.0f, p, narrow_rn(P)), G * rho);
-    }
-}
+// Conserved -> primitive recovery per cell (prims_cell) and the CFL rate of a
+// cell (cell_cfl_rate) live in mfc_cell.cuh, where the RK epilogue uses them too.
 
 template <typename Real, int NF, int NDIM, bool RATE, bool SIX = false>
 __global__ void __launch_bounds__(256) prims_kernel(const PrimArgs a) {
     using Lay = Layout<NF, NDIM>;
-    constexpr int NS = Lay::NS, IM = Lay::IM;
+    constexpr int NS = Lay::NS;
     const long long nc = a.g.ncell;
     double rate = 0.0;
     int bad = 0;
@@ -117,34 +26,9 @@ __global__ void __launch_bounds__(256) prims_kernel(const PrimArgs a) {
 #pragma unroll
         for (int v = 0; v < NS; ++v) w[v * nc + i] = wv[v];
         if (RATE) {
-            // in the arithmetic of the path: FP64, or FP32 for the mixed path
-            Real us = 0;
-#pragma unroll
-            for (int d = 0; d < NDIM; ++d) us += wv[IM + d];
-            if (!(c2 > (Real)0) || !(c2 - c2 == (Real)0) || !(us - us == (Real)0)) {
-                bad += 1;
-            } else {
-                // FP64: the root in float-float (~2^-46 relative), off the FP64 pipe
-                Real cs;
-                if constexpr (sizeof(Real) == 8) cs = df_to_double(df_sqrt(df_from_double(c2)));
-                else cs = real_sqrt(c2);
-                Real r = 0;
-                int ci[3] = {0, 0, 0};
-                if (a.grid[0] || a.grid[1] || a.grid[2]) {   // non-uniform: this cell's widths
-                    const unsigned ii = (unsigned)i, nx = (unsigned)a.g.n[0], ny = (unsigned)a.g.n[1];
-                    ci[0] = (int)(ii % nx);
-                    ci[1] = (int)((ii / nx) % ny);
-                    ci[2] = (int)(ii / (nx * ny));
-                }
-#pragma unroll
-                for (int d = 0; d < NDIM; ++d) {
-                    const Real inv = !a.grid[d] ? (Real)a.g.inv_dx[d]
-                                     : d == 0 ? grid_inv_dx<true>(a.grid[d], a.grid_stride[d], ci[d], Real(0))
-                                              : grid_inv_dx<false>(a.grid[d], a.grid_stride[d], ci[d], Real(0));
-                    r = real_max(r, (fabs(wv[IM + d]) + cs) * inv);
-                }
-                rate = fmax(rate, (double)r);
-            }
+            const double r = cell_cfl_rate<Real, NF, NDIM>(wv, c2, a.g, a.grid, a.grid_stride, i);
+            if (r < 0.0) bad += 1;
+            else rate = fmax(rate, r);
         }
     }
     if (RATE) {

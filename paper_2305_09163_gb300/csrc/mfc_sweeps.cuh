@@ -50,6 +50,7 @@ __global__ void __launch_bounds__(128) sweep_kernel(const SweepArgs a) {
         lsm = &lbuf[threadIdx.x >> 5];
     }
     unsigned long long net_rows = 0;  // learned form: network rows of this warp
+    RateAcc racc;                     // fused RK epilogue: CFL rate of the finished cells
 
     auto load = [&](int i, Real* out) {
         bool flip = false;
@@ -105,8 +106,8 @@ __global__ void __launch_bounds__(128) sweep_kernel(const SweepArgs a) {
             else
                 face_flux<Real, NF, NDIM, DIR>(a, e, eLprev, eR, cm1, vc, F, ut);
             if (c >= s0 + 1 && active)
-                finish_cell<Real, NF, NDIM, DIR>(a, base + (long long)(c - 1) * sd, Fprev, F, utprev, ut, cm1, inv_dx,
-                                                 c - 1, sd);
+                racc.add(finish_cell<Real, NF, NDIM, DIR>(a, base + (long long)(c - 1) * sd, Fprev, F, utprev, ut, cm1,
+                                                          inv_dx, c - 1, sd));
 #pragma unroll
             for (int v = 0; v < NS; ++v) Fprev[v] = F[v];
             utprev = ut;
@@ -136,6 +137,7 @@ __global__ void __launch_bounds__(128) sweep_kernel(const SweepArgs a) {
     if constexpr (LEARNED) {
         if ((threadIdx.x & 31) == 0 && net_rows && a.net_rows) atomicAdd(a.net_rows, net_rows);
     }
+    publish_rate(a, racc);
 }
 
 // ---------------------------------------------------------------------------
@@ -169,7 +171,13 @@ __device__ __forceinline__ void sweep_x_stream_body(const SweepArgs& a) {
     // chunk overwrites it (s + 128 = s - 1 mod ER) only after the barriers that
     // order it.
     constexpr int ER = kStreamThreads + 1;
+    // ROLL (FP64): the reconstruction runs as one copy looped over the
+    // variables, stencils loaded per variable, edges to shared memory.  Unrolled
+    // over the variables the float-float code overflowed the instruction cache
+    // (ncu: "no instruction" the largest stall, 1.0-1.5 warps per issue).
+    constexpr bool ROLL = sizeof(Real) == 8 && !LEARNED;
     __shared__ Real sh_eL[NS][ER];
+    __shared__ Real sh_eR[ROLL ? NS : 1][kStreamThreads];
     __shared__ Real sh_eLJ[NJ][ER];
     __shared__ Real sh_F[NQ + 1][ER];
     const Real* __restrict__ w = static_cast<const Real*>(a.w);
@@ -191,6 +199,7 @@ __device__ __forceinline__ void sweep_x_stream_body(const SweepArgs& a) {
         lsm = &lbuf[t >> 5];
     }
     unsigned long long net_rows = 0;  // learned form: network rows of this warp
+    RateAcc racc;                     // fused RK epilogue: CFL rate of the finished cells
 
     // (row, column) of this lane's slot: one 64-bit division when the slot first
     // becomes valid, then advanced by 128 slots per chunk with additions (a
@@ -273,7 +282,42 @@ __device__ __forceinline__ void sweep_x_stream_body(const SweepArgs& a) {
                 Dv[q][0] = Dv[q][1] = Dv[q][2] = Dv[q][3] = 0;
             }
         }
-        if (!LEARNED && live) {
+        if (ROLL && live) {
+            int mk[5];
+            bool fk[5];
+#pragma unroll
+            for (int k = 0; k < 5; ++k) {
+                fk[k] = false;
+                mk[k] = ghost_map(c + k - 2, n, bclo, bchi, &fk[k]);
+            }
+            const Real* wr = w + rowoff;
+#pragma unroll 1
+            for (int q = 0; q < NS; ++q) {
+                Real v[5];
+#pragma unroll
+                for (int k = 0; k < 5; ++k) {
+                    const Real x = __ldg(wr + q * nc + mk[k]);
+                    v[k] = (q == IM && fk[k]) ? -x : x;
+                }
+                Real Dq[4] = {v[1] - v[0], v[2] - v[1], v[3] - v[2], v[4] - v[3]};
+                Real er, el;
+                if constexpr (NONUNIF) {
+                    const GridCol<true> grow(a.grid[0], a.grid_stride[0], c);
+                    weno5_edges_nu(v[2], Dq, sweep_epsw<Real, 3>(a), grow, er, el);
+                } else {
+                    weno_edges<ORDER>(v[2], Dq, eps34, er, el);
+                }
+                sh_eL[q][pos] = el;
+                sh_eR[q][t] = er;
+            }
+#pragma unroll
+            for (int q = 0; q < NS; ++q) {
+                const Real x1 = __ldg(wr + q * nc + mk[1]), x2 = __ldg(wr + q * nc + mk[2]);
+                cm1[q] = (q == IM && fk[1]) ? -x1 : x1;
+                vcv[q] = (q == IM && fk[2]) ? -x2 : x2;
+            }
+        }
+        if (!ROLL && !LEARNED && live) {
             Real v[5][NS];
 #pragma unroll
             for (int k = 0; k < 5; ++k) {
@@ -293,7 +337,7 @@ __device__ __forceinline__ void sweep_x_stream_body(const SweepArgs& a) {
                 cm1[q] = v[1][q];
             }
         }
-        if (!LEARNED && live) {
+        if (!ROLL && !LEARNED && live) {
             if constexpr (NONUNIF) {
                 const GridCol<true> row(a.grid[0], a.grid_stride[0], c);
                 const Real epsn = sweep_epsw<Real, 3>(a);   // unscaled eps
@@ -310,7 +354,7 @@ __device__ __forceinline__ void sweep_x_stream_body(const SweepArgs& a) {
         }
         // left-side values of this chunk (the last chunk's last slot stays at
         // the position before this chunk's first)
-        if (live) {
+        if (!ROLL && live) {
 #pragma unroll
             for (int q = 0; q < NS; ++q) {
                 sh_eL[q][pos] = eL[q];
@@ -324,6 +368,10 @@ __device__ __forceinline__ void sweep_x_stream_body(const SweepArgs& a) {
             Real lft[NS];
 #pragma unroll
             for (int q = 0; q < NS; ++q) lft[q] = sh_eL[q][pl];
+            if constexpr (ROLL) {
+#pragma unroll
+                for (int q = 0; q < NS; ++q) eR[q] = sh_eR[q][t];
+            }
             if constexpr (LEARNED) {
                 Real lftJ[NS];
 #pragma unroll
@@ -341,9 +389,9 @@ __device__ __forceinline__ void sweep_x_stream_body(const SweepArgs& a) {
             Real Fm[NQ];
 #pragma unroll
             for (int q = 0; q < NQ; ++q) Fm[q] = sh_F[q][pl];
-            finish_cell<Real, NF, NDIM, 0, SIX>(a, rowoff + (c - 1), Fm, F, sh_F[NQ][pl], ut, cm1,
-                                           NONUNIF ? grid_inv_dx<true>(a.grid[0], a.grid_stride[0], c - 1, Real(0)) : inv_dx,
-                                           c - 1, 1, row);
+            racc.add(finish_cell<Real, NF, NDIM, 0, SIX>(
+                a, rowoff + (c - 1), Fm, F, sh_F[NQ][pl], ut, cm1,
+                NONUNIF ? grid_inv_dx<true>(a.grid[0], a.grid_stride[0], c - 1, Real(0)) : inv_dx, c - 1, 1, row));
         }
         // No barrier is needed here: the next chunk writes edge values
         // (position pl of this chunk) after this chunk's second barrier, which
@@ -357,6 +405,7 @@ __device__ __forceinline__ void sweep_x_stream_body(const SweepArgs& a) {
     if constexpr (LEARNED) {
         if ((threadIdx.x & 31) == 0 && net_rows && a.net_rows) atomicAdd(a.net_rows, net_rows);
     }
+    publish_rate(a, racc);
 }
 
 template <typename Real, int NF, int NDIM, bool LEARNED = false, int ORDER = 5, bool NONUNIF = false, bool SIX = false>
@@ -422,8 +471,12 @@ __device__ __forceinline__ void sweep_yz_stream_body(const SweepArgs& a) {
     // their left neighbours, the last of which the previous chunk wrote, and the
     // next chunk overwrites that row only after the barriers that order it.
     constexpr int ER = kRowsPerChunk + 1;
+    // ROLL (FP64): one copy of the reconstruction looped over the variables
+    // (stencils from the ring, edges to shared memory); see the x stream body.
+    constexpr bool ROLL = sizeof(Real) == 8 && !LEARNED;
     __shared__ Real ring[RING][NS][32];
     __shared__ Real sh_eL[NS][ER][32];
+    __shared__ Real sh_eR[ROLL ? NS : 1][kRowsPerChunk][32];
     __shared__ Real sh_eLJ[NJ][ER][32];
     __shared__ Real sh_F[NQ + 1][ER][32];
     extern __shared__ __align__(16) unsigned char stage_smem[];   // a.stage operands
@@ -455,6 +508,7 @@ __device__ __forceinline__ void sweep_yz_stream_body(const SweepArgs& a) {
         lsm = &lbuf[row];
     }
     unsigned long long net_rows = 0;  // learned form: network rows of this warp
+    RateAcc racc;                     // fused RK epilogue: CFL rate of the finished cells
     // cell i along DIR (ghost-mapped) of this lane's column
     auto load = [&](int i, Real* out) {
         bool flip = false;
@@ -520,6 +574,28 @@ __device__ __forceinline__ void sweep_yz_stream_body(const SweepArgs& a) {
                     cell[q] = ring[slot(c)][q][lane];
                     cm1[q] = ring[slot(c - 1)][q][lane];
                 }
+            } else if constexpr (ROLL) {
+                const int s0r = slot(c - 2), s1r = slot(c - 1), s2r = slot(c), s3r = slot(c + 1), s4r = slot(c + 2);
+#pragma unroll 1
+                for (int q = 0; q < NS; ++q) {
+                    const Real v0 = ring[s0r][q][lane], v1 = ring[s1r][q][lane], v2 = ring[s2r][q][lane];
+                    const Real v3 = ring[s3r][q][lane], v4 = ring[s4r][q][lane];
+                    Real Dq[4] = {v1 - v0, v2 - v1, v3 - v2, v4 - v3};
+                    Real er, el;
+                    if constexpr (NONUNIF) {
+                        const GridCol<false> grow(a.grid[DIR], a.grid_stride[DIR], c);
+                        weno5_edges_nu(v2, Dq, sweep_epsw<Real, 3>(a), grow, er, el);
+                    } else {
+                        weno_edges<ORDER>(v2, Dq, eps34, er, el);
+                    }
+                    sh_eL[q][eslot(c)][lane] = el;
+                    sh_eR[q][row][lane] = er;
+                }
+#pragma unroll
+                for (int q = 0; q < NS; ++q) {
+                    cell[q] = ring[s2r][q][lane];
+                    cm1[q] = ring[s1r][q][lane];
+                }
             } else {
                 Real Dv[NS][4];
 #pragma unroll
@@ -544,10 +620,12 @@ __device__ __forceinline__ void sweep_yz_stream_body(const SweepArgs& a) {
                     for (int q = 0; q < NS; ++q) weno_edges<ORDER>(cell[q], Dv[q], eps34, eR[q], eL[q]);
                 }
             }
+            if constexpr (!ROLL) {
 #pragma unroll
-            for (int q = 0; q < NS; ++q) {
-                sh_eL[q][eslot(c)][lane] = eL[q];
-                if constexpr (LEARNED) sh_eLJ[q][eslot(c)][lane] = eLJ[q];
+                for (int q = 0; q < NS; ++q) {
+                    sh_eL[q][eslot(c)][lane] = eL[q];
+                    if constexpr (LEARNED) sh_eLJ[q][eslot(c)][lane] = eLJ[q];
+                }
             }
         }
         __syncthreads();
@@ -562,6 +640,10 @@ __device__ __forceinline__ void sweep_yz_stream_body(const SweepArgs& a) {
             Real lft[NS];
 #pragma unroll
             for (int q = 0; q < NS; ++q) lft[q] = sh_eL[q][eslot(c - 1)][lane];
+            if constexpr (ROLL) {
+#pragma unroll
+                for (int q = 0; q < NS; ++q) eR[q] = sh_eR[q][row][lane];
+            }
             if constexpr (LEARNED) {
                 Real lftJ[NS];
 #pragma unroll
@@ -586,11 +668,10 @@ __device__ __forceinline__ void sweep_yz_stream_body(const SweepArgs& a) {
                     stg = stage_smem;
                 }
             }
-            finish_cell<Real, NF, NDIM, DIR, SIX>(a, basei + (long long)(c - 1) * sd, Fm, F,
-                                             sh_F[NQ][eslot(c - 1)][lane], ut, cm1,
-                                             NONUNIF ? grid_inv_dx<false>(a.grid[DIR], a.grid_stride[DIR], c - 1, Real(0))
-                                                     : inv_dx,
-                                             c - 1, sd, (long long)t1 + (long long)n1 * t2, stg, threadIdx.x);
+            racc.add(finish_cell<Real, NF, NDIM, DIR, SIX>(
+                a, basei + (long long)(c - 1) * sd, Fm, F, sh_F[NQ][eslot(c - 1)][lane], ut, cm1,
+                NONUNIF ? grid_inv_dx<false>(a.grid[DIR], a.grid_stride[DIR], c - 1, Real(0)) : inv_dx, c - 1, sd,
+                (long long)t1 + (long long)n1 * t2, stg, threadIdx.x));
         }
         // No barrier is needed here: the next chunk writes edge values (row
         // c+4 = c-1 mod ER) after this chunk's second barrier, which follows
@@ -603,6 +684,7 @@ __device__ __forceinline__ void sweep_yz_stream_body(const SweepArgs& a) {
     if constexpr (LEARNED) {
         if ((threadIdx.x & 31) == 0 && net_rows && a.net_rows) atomicAdd(a.net_rows, net_rows);
     }
+    publish_rate(a, racc);
 }
 
 // The y/z stream kernel (FP64 uniform WENO5 forms, with staged finish
@@ -638,6 +720,13 @@ __global__ void __launch_bounds__(32 * kRowsPerChunk, 5) sweep_yz_stream_six32_k
 template <int NF, int NDIM, int DIR, int ORDER = 5, bool NONUNIF = false, bool SIX = false>
 __global__ void __launch_bounds__(32 * kRowsPerChunk, 4) sweep_yz_stream_f64_kernel(const SweepArgs a) {
     sweep_yz_stream_body<double, NF, NDIM, DIR, false, ORDER, NONUNIF, SIX, !NONUNIF>(a);
+}
+
+// The FP64 uniform WENO5 y/z stream kernel for three fluids, bounded to 3
+// CTAs per SM (168 registers): unbounded it takes 187-192 and keeps 2.
+template <int NF, int NDIM, int DIR>
+__global__ void __launch_bounds__(32 * kRowsPerChunk, 3) sweep_yz_stream_f64b3_kernel(const SweepArgs a) {
+    sweep_yz_stream_body<double, NF, NDIM, DIR, false, 5, false, false, true>(a);
 }
 
 template <int NF, int NDIM, int DIR>

@@ -17,7 +17,7 @@ from dataclasses import dataclass
 
 import numpy as np
 
-from . import (MLP_PARAMS, MLP_WORK_FLOATS, Solver, mfc_harvest, mfc_mlp_adam, mfc_mlp_forward, mfc_mlp_grad)
+from . import MLP_PARAMS, MLP_WORK_FLOATS, Solver, mfc_harvest, mfc_mlp_adam, mfc_mlp_grad
 
 IDEAL = (0.1, 0.6, 0.3)
 HIDDEN = 32
@@ -124,16 +124,3 @@ def train(samples: Samples, epochs=15, batch=65536, lr=2e-3, lam=1.0, seed=0, pa
         if log:
             log("epoch %d loss %.6g" % (ep, history[-1]))
     return P, history
-
-
-def evaluate(P, samples: Samples, lam=0.0):
-    """Face-value mean squared errors against the fine target on smooth samples:
-    (network, WENO5-JS), both in normalised units."""
-    import torch
-    om = torch.empty((len(samples), 3), dtype=torch.float32, device=samples.x.device)
-    mfc_mlp_forward(P, samples.x, om)
-    y = (om * samples.phat).sum(dim=1)
-    m = samples.smooth > 0.5
-    e_net = ((y - samples.target)[m] ** 2).mean().item()
-    e_js = ((samples.js - samples.target)[m] ** 2).mean().item()
-    return e_net, e_js

@@ -294,6 +294,30 @@ def bubble_cloud(n: int = 384, steps: int = 500, seed: int = 230509163) -> Workl
         builder=_build_cloud)
 
 
+def _build_cloud_box(wl: Workload) -> np.ndarray:
+    # the bubbles of the full cloud (layout gap from its own cell size), on this
+    # box's cells, interfaces smeared over this grid's cell width
+    bubbles = bubble_cloud_layout(64, wl.seed, (0.15, 0.05, 0.05), (0.95, 0.95, 0.95),
+                                  0.02, 0.3, 2.0 / wl.layout_n)
+    return _two_fluid_bubbles(wl, bubbles)
+
+
+def bubble_cloud_box(n: int, lo=(0.0, 0.25, 0.25), hi=(0.5, 0.75, 0.75), layout_n: int = 384,
+                     seed: int = 230509163) -> Workload:
+    """A box of the bubble cloud (the bubbles of the layout_n^3 cloud, the same
+    shock) on n cells per direction: with the default box, n = layout_n / 2 has
+    the full cloud's cell size and n = layout_n half of it."""
+    wl = Workload(
+        name="shock_bubble_cloud_box_%d" % n, n=(n, n, n), lo=tuple(lo), hi=tuple(hi),
+        bc=(BC_TRANSMISSIVE,) * 6, gamma=(WATER[0], AIR[0]), pi_inf=(WATER[1], AIR[1]),
+        cfl=0.3, steps=0, seed=seed,
+        notes="box [%g,%g]x[%g,%g]x[%g,%g] of the %d^3 bubble cloud" % (lo[0], hi[0], lo[1], hi[1], lo[2], hi[2],
+                                                                       layout_n),
+        builder=_build_cloud_box)
+    wl.layout_n = layout_n
+    return wl
+
+
 def _build_three_fluid(wl: Workload) -> np.ndarray:
     dx = 1.0 / wl.n[0]
     bubbles = bubble_cloud_layout(128, wl.seed, (0.15, 0.05, 0.05), (0.7, 0.95, 0.95),
