@@ -477,7 +477,7 @@ def _accuracy_case(m, torch, wl, key, mlp, t0):
     print(json.dumps(res), flush=True)
 
 
-def _accuracy_learned_2x(m, torch, mlp, training, n=192, t_end=1.0e-4):
+def _accuracy_learned_2x(m, torch, mlp, training, n=192, t_end=1.0e-4, taus=(10.0, 30.0)):
     """Learned weights against WENO5-JS at the bubble cloud's own cell size
     (1/384): a 192^3 box of the cloud ([0, 0.5] x [0.25, 0.75]^2, the shock and
     the first bubbles), judged against the FP64 run of the same box at 2x
@@ -489,32 +489,41 @@ def _accuracy_learned_2x(m, torch, mlp, training, n=192, t_end=1.0e-4):
     init = np.ascontiguousarray(fw.reshape(fw.shape[0], n, 2, n, 2, n, 2).mean(axis=(2, 4, 6)))
     del fw
 
-    def run_to(wl, precision, mlp=None, init=None):
-        s = m.Solver(wl.n, wl.lo, wl.hi, wl.bc, wl.gamma, wl.pi_inf, precision=precision, fallback=1)
+    def run_to(wl, precision, mlp=None, init=None, **params):
+        s = m.Solver(wl.n, wl.lo, wl.hi, wl.bc, wl.gamma, wl.pi_inf, precision=precision, fallback=1, **params)
         if mlp is not None:
             s.set_mlp(mlp)
         s.set_state_prim(torch.from_numpy(init if init is not None else wl.prims()).cuda())
         t, k = 0.0, 0
-        while t < t_end:
-            dt = min(s.cfl_dt(CFL), t_end - t)
-            s.step(dt)
-            t += dt
-            k += 1
-        w = s.get_prims().cpu().numpy()
+        try:
+            while t < t_end:
+                dt = min(s.cfl_dt(CFL), t_end - t)
+                s.step(dt)
+                t += dt
+                k += 1
+            w = s.get_prims().cpu().numpy()
+        except m.MFCError as exc:   # a non-physical state: reported, not timed
+            w = "failed at step %d (t = %.3g s): %s" % (k, t, exc)
         s.close()
         torch.cuda.empty_cache()
         return w, k
     t0 = time.perf_counter()
     ref, kf = run_to(fine, "fp64")
     ref = ref.reshape(ref.shape[0], n, 2, n, 2, n, 2).mean(axis=(2, 4, 6))
-    wl_, kc = run_to(coarse, "learned", mlp, init)
+    js = _l1_fields(run_to(coarse, "mixed", None, init)[0], ref, 2)
     res = {"config": "3", "workload": "bubble-cloud box %d^3 (cell 1/384) vs restricted FP64 %d^3" % (n, 2 * n),
-           "t_end": t_end, "steps_coarse": kc, "steps_fine": kf,
-           "learned_vs_2x": _l1_fields(wl_, ref, 2),
-           "mixed_js_vs_2x": _l1_fields(run_to(coarse, "mixed", None, init)[0], ref, 2),
+           "t_end": t_end, "steps_fine": kf, "mixed_js_vs_2x": js,
            "fp64_js_vs_2x": _l1_fields(run_to(coarse, "fp64", None, init)[0], ref, 2),
-           "training": training, "seconds": time.perf_counter() - t0}
-    res["learned_gain"] = {k: 1.0 - res["learned_vs_2x"][k] / res["mixed_js_vs_2x"][k] for k in ("rho", "p", "alpha")}
+           "training": training}
+    for tau in taus:
+        wl_, kc = run_to(coarse, "learned", mlp, init, sensor_tau=tau)
+        key = "learned_tau%g" % tau
+        if isinstance(wl_, str):
+            res[key] = {"error": wl_}
+            continue
+        e = _l1_fields(wl_, ref, 2)
+        res[key] = {"vs_2x": e, "steps": kc, "gain_vs_js": {k: 1.0 - e[k] / js[k] for k in ("rho", "p", "alpha")}}
+    res["seconds"] = time.perf_counter() - t0
     print(json.dumps(res), flush=True)
 
 

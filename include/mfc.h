@@ -142,7 +142,7 @@ mfc_status mfc_init(mfc_ctx** out, int nx, int ny, int nz, const double lo[3], c
  *   "sensor_tau" learned form: the discontinuity sensor trips (WENO5-JS
  *                weights are used) where max_r b_r > tau (min_r b_r + 1e-6 s^2),
  *                b the smoothness indicators without their 4/3 factor and s the
- *                stencil scale; default 30, range [1, 1e30];
+ *                stencil scale; default 10, range [1, 1e30];
  *   "learned_bound" learned form: 1 (default) / 0: keep a learned edge value
  *                only inside the range of the cell and its two neighbours
  *                (WENO5-JS value otherwise);
@@ -259,6 +259,27 @@ mfc_status mfc_mlp_forward(const float* params, const float* x, long long batch,
 mfc_status mfc_mlp_grad(const float* params, const float* x, const float* phat, const float* target,
                         const float* mask, long long batch, float lam, float* grad, float* loss, float* work,
                         void* stream);
+
+/* mfc_mlp_grad runs on the fifth-generation tensor cores (tcgen05: one CTA
+ * per 128 samples, BF16 operands in shared memory, FP32 accumulators in tensor
+ * memory, the weight gradients as one MMA chain over the batch); its waits on
+ * the tensor core are bounded, and a wait that gives up sets a flag that
+ * mfc_mlp_tc_status reports.  mfc_mlp_grad_mma computes the same loss and
+ * gradient on warp-level mma.sync tiles of 16 samples (same arguments and
+ * workspace); the two agree to BF16 rounding. */
+mfc_status mfc_mlp_grad_mma(const float* params, const float* x, const float* phat, const float* target,
+                            const float* mask, long long batch, float lam, float* grad, float* loss, float* work,
+                            void* stream);
+
+/* omega[batch][3] as mfc_mlp_forward computes it, on the tcgen05 tensor cores
+ * (M = 128 samples per MMA, FP32 accumulators in tensor memory). */
+mfc_status mfc_mlp_forward_tc(const float* params, const float* x, long long batch, float* omega, void* stream);
+
+/* Synchronises the device and reports whether a bounded tensor-core wait of
+ * mfc_mlp_grad or mfc_mlp_forward_tc gave up since the last call (1; the
+ * flag is then cleared), 0 if none did, -1 on a CUDA error.  The kernels that
+ * gave up leave their outputs incomplete. */
+int mfc_mlp_tc_status(void);
 
 /* One Adam step (bias-corrected, step >= 1) on params[n] with moments m[n], v[n]. */
 mfc_status mfc_mlp_adam(float* params, const float* grad, float* m, float* v, int n, float lr, float beta1,

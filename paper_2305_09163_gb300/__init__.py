@@ -87,6 +87,12 @@ def _declare(lib):
     lib.mfc_mlp_grad.argtypes = [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_ll, ctypes.c_float,
                                  c_void_p, c_void_p, c_void_p, c_void_p]
     lib.mfc_mlp_grad.restype = c_int
+    lib.mfc_mlp_grad_mma.argtypes = lib.mfc_mlp_grad.argtypes
+    lib.mfc_mlp_grad_mma.restype = c_int
+    lib.mfc_mlp_forward_tc.argtypes = [c_void_p, c_void_p, c_ll, c_void_p, c_void_p]
+    lib.mfc_mlp_forward_tc.restype = c_int
+    lib.mfc_mlp_tc_status.argtypes = []
+    lib.mfc_mlp_tc_status.restype = c_int
     lib.mfc_mlp_adam.argtypes = [c_void_p, c_void_p, c_void_p, c_void_p, c_int, ctypes.c_float, ctypes.c_float,
                                  ctypes.c_float, ctypes.c_float, c_int, c_void_p]
     lib.mfc_mlp_adam.restype = c_int
@@ -273,13 +279,40 @@ def mfc_mlp_forward(params, x, omega, stream=None):
         raise MFCError(st, "mfc_mlp_forward")
 
 
-def mfc_mlp_grad(params, x, phat, target, mask, lam, grad, loss, work, stream=None):
+def mfc_mlp_forward_tc(params, x, omega, stream=None):
+    """As mfc_mlp_forward, on the tcgen05 tensor cores."""
     lib = load()
-    st = lib.mfc_mlp_grad(_dev32(params, "params"), _dev32(x, "x"), _dev32(phat, "phat"), _dev32(target, "target"),
-                          _dev32(mask, "mask"), x.shape[0], float(lam), _dev32(grad, "grad"),
-                          _dev32(loss, "loss") if loss is not None else None, _dev32(work, "work"), _stream(stream))
+    st = lib.mfc_mlp_forward_tc(_dev32(params, "params"), _dev32(x, "x"), x.shape[0], _dev32(omega, "omega"),
+                                _stream(stream))
     if st != MFC_OK:
-        raise MFCError(st, "mfc_mlp_grad")
+        raise MFCError(st, "mfc_mlp_forward_tc")
+
+
+def _grad_call(fn, name, params, x, phat, target, mask, lam, grad, loss, work, stream):
+    st = fn(_dev32(params, "params"), _dev32(x, "x"), _dev32(phat, "phat"), _dev32(target, "target"),
+            _dev32(mask, "mask"), x.shape[0], float(lam), _dev32(grad, "grad"),
+            _dev32(loss, "loss") if loss is not None else None, _dev32(work, "work"), _stream(stream))
+    if st != MFC_OK:
+        raise MFCError(st, name)
+
+
+def mfc_mlp_grad(params, x, phat, target, mask, lam, grad, loss, work, stream=None):
+    """Loss and gradient of a batch on the tcgen05 tensor cores."""
+    _grad_call(load().mfc_mlp_grad, "mfc_mlp_grad", params, x, phat, target, mask, lam, grad, loss, work, stream)
+
+
+def mfc_mlp_grad_mma(params, x, phat, target, mask, lam, grad, loss, work, stream=None):
+    """The same on warp-level mma.sync tiles."""
+    _grad_call(load().mfc_mlp_grad_mma, "mfc_mlp_grad_mma", params, x, phat, target, mask, lam, grad, loss, work,
+               stream)
+
+
+def mfc_mlp_tc_status():
+    """1 if a bounded tensor-core wait gave up since the last call (then cleared), else 0 (synchronises)."""
+    st = load().mfc_mlp_tc_status()
+    if st < 0:
+        raise MFCError(MFC_ERR_CUDA, "mfc_mlp_tc_status")
+    return st
 
 
 def mfc_mlp_adam(params, grad, m, v, lr, beta1, beta2, eps, step, stream=None):

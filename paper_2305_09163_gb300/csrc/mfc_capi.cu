@@ -49,7 +49,7 @@ struct mfc_ctx {
     int fallback = 1;
     int seg_override = 0;
     bool profile = false;
-    double tau = 30.0;        // learned form: sensor threshold
+    double tau = 10.0;        // learned form: sensor threshold
     int yz_stream = -1;       // y/z sweep kernel: -1 automatic, 0 marching, 1 stream
     int bound = 1;            // learned form: range safeguard
     int weno_order = 5;       // reconstruction: WENO5-JS or WENO3-JS

@@ -1,7 +1,9 @@
 // Learned WENO weights: training kernels and their C ABI (include/mfc.h).
 //
 //   mfc_mlp_forward  weights omega for a batch of normalised stencils
-//   mfc_mlp_grad     loss and gradient of a batch (forward + backpropagation)
+//   mfc_mlp_grad_mma loss and gradient of a batch (forward + backpropagation)
+//                    on warp-level mma.sync; mfc_mlp_grad (mfc_mlp_tc.cu) is
+//                    the same on the fifth-generation tensor cores
 //   mfc_mlp_adam     Adam update of the parameter blob
 //   mfc_harvest      training samples from a fine primitive field: coarse
 //                    (2x restricted) stencils, WENO5 candidates, the fine-grid
@@ -564,9 +566,9 @@ mfc_status mfc_mlp_forward(const float* params, const float* x, long long batch,
     return cudaGetLastError() == cudaSuccess ? MFC_OK : MFC_ERR_CUDA;
 }
 
-mfc_status mfc_mlp_grad(const float* params, const float* x, const float* phat, const float* target,
-                        const float* mask, long long batch, float lam, float* grad, float* loss, float* work,
-                        void* stream) {
+mfc_status mfc_mlp_grad_mma(const float* params, const float* x, const float* phat, const float* target,
+                            const float* mask, long long batch, float lam, float* grad, float* loss, float* work,
+                            void* stream) {
     if (!params || !x || !phat || !target || !mask || !grad || !work || batch <= 0 || !(lam >= 0.f))
         return MFC_ERR_ARG;
     cudaStream_t s = static_cast<cudaStream_t>(stream);

