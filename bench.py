@@ -86,13 +86,13 @@ SCHEDULERS = 152 * 4
 # Warp instructions per cell of the FP64 WENO5 sweeps (x, y, z; 3D, two
 # fluids, smsp__inst_executed.sum / cells of one ncu capture).  Re-measured
 # whenever the FP64 sweeps change: NCU_FP64_SWEEPS says which capture.
-FP64_SWEEP_WARP_INST_PER_CELL = (240.9, 236.2, 246.3)
+FP64_SWEEP_WARP_INST_PER_CELL = (229.0, 231.1, 241.8)
 # From the same capture: FP64-pipe and FP32 (fma) pipe activity of the sweeps
 # (mean over x, y, z) and DRAM bytes per cell per launch (the z sweep of an RK
 # stage also writes the next stage's primitives).
-FP64_SWEEP_PIPE_FP64 = 0.618
-FP64_SWEEP_PIPE_FMA = 0.379
-FP64_SWEEP_DRAM_BYTES_PER_CELL = (103.5 + 160.0 + 337.1) / 3.0
+FP64_SWEEP_PIPE_FP64 = 0.630
+FP64_SWEEP_PIPE_FMA = 0.413
+FP64_SWEEP_DRAM_BYTES_PER_CELL = (103.5 + 159.9 + 337.2) / 3.0
 NCU_FP64_SWEEPS = "profiles/sweep_fp64_shock_bubble_160.md"
 # Nominal FP32 peak: 152 SMs x 128 FMA/clk x 2 FLOP x 2.07 GHz
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
@@ -208,10 +208,51 @@ TRAIN_RUNS = (("shock_bubble", 256, 200, (0, 50, 100, 150, 200), 1_000_000, 1),
               ("bubble_cloud", 384, 200, (0, 50, 100, 150, 200), 1_000_000, 2))
 
 
-def train_learned(m, torch, log=None, runs=TRAIN_RUNS):
+# Useful FLOPs of one sample's loss gradient: the forward layers (5x32, 32x32,
+# 32x3 multiply-adds), the backward data products (3x32, 32x32) and the
+# weight-gradient products (32x5, 32x32, 3x32), two FLOPs per multiply-add.
+FLOP_MLP_GRAD_SAMPLE = 2 * ((5 * 32 + 32 * 32 + 32 * 3) + (3 * 32 + 32 * 32) + (32 * 5 + 32 * 32 + 3 * 32))
+
+
+def time_mlp_grad(m, torch, P, samples, batch=65536, passes=3):
+    """Milliseconds per pass over the training samples of the loss gradient on
+    the tcgen05 tensor cores (mfc_mlp_grad) and on warp-level mma.sync
+    (mfc_mlp_grad_mma), timed with CUDA events on the current stream."""
+    n = len(samples) - len(samples) % batch
+    G = torch.empty_like(P)
+    L = torch.empty(1, dtype=torch.float32, device=P.device)
+    work = torch.empty(m.MLP_WORK_FLOATS, dtype=torch.float32, device=P.device)
+    out = {"samples_per_pass": n, "batch": batch}
+    peaks = _measured_peaks()
+    bf = float(peaks.get("bf16_tflops", 1900.0))
+    for name, fn in (("tcgen05", m.mfc_mlp_grad), ("mma_sync", m.mfc_mlp_grad_mma)):
+        def one_pass():
+            for a in range(0, n, batch):
+                sb = samples.slice(a, a + batch)
+                fn(P, sb.x, sb.phat, sb.target, sb.smooth, 1.0, G, L, work)
+        one_pass()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(passes):
+            one_pass()
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / passes
+        tf = FLOP_MLP_GRAD_SAMPLE * n / (ms * 1e-3) / 1e12
+        out[name] = {"ms_per_pass": ms, "samples_per_s": n / (ms * 1e-3), "tensor_tflops": tf,
+                     "tensor_frac": tf / bf}
+    if m.mfc_mlp_tc_status():
+        out["tcgen05"]["error"] = "a bounded tensor-core wait gave up"
+    out["note"] = ("useful FLOPs %d per sample; tensor_frac against the measured bf16 burst peak: the 5-32-32-3 "
+                   "network is far too small to load the tensor cores (one 128-sample tile per CTA and MMA "
+                   "round trip)" % FLOP_MLP_GRAD_SAMPLE)
+    return out
+
+
+def train_learned(m, torch, log=None, runs=TRAIN_RUNS, time_grad=False):
     """Train the learned weights on stencils harvested from runs of the
     shock-bubble and bubble-cloud workloads (done before, and outside, every
-    timed region)."""
+    timed region); with time_grad also time the two gradient kernels."""
     from paper_2305_09163_gb300 import learned
     t0 = time.perf_counter()
     parts = []
@@ -220,13 +261,17 @@ def train_learned(m, torch, log=None, runs=TRAIN_RUNS):
         parts.append(learned.harvest_run(wl, steps, set(snaps), per, seed))
         torch.cuda.empty_cache()
     th = time.perf_counter()
-    P, hist = learned.train(learned.Samples.cat(parts))
+    samples = learned.Samples.cat(parts)
+    del parts
+    P, hist = learned.train(samples)
     torch.cuda.synchronize()
-    info = {"samples": sum(len(p) for p in parts),
+    info = {"samples": len(samples),
             "runs": ["%s %d^3, steps %s, %d per snapshot" % (name, n, list(snaps), per)
                      for name, n, _, snaps, per, _ in runs],
             "final_loss": hist[-1], "harvest_seconds": th - t0, "train_seconds": time.perf_counter() - th}
-    del parts
+    if time_grad:
+        info["grad_kernels"] = time_mlp_grad(m, torch, P, learned.smooth_part(samples))
+    del samples
     torch.cuda.empty_cache()
     return P.cpu().numpy(), info
 
@@ -656,7 +701,7 @@ def main():
     training = None
     mlp = None
     if "learned" in forms or any(CONFIG_RUNS[c][1] == "learned" for c in runs):
-        mlp, training = train_learned(m, torch)
+        mlp, training = train_learned(m, torch, time_grad=True)
     head = "fp64" if "fp64" in forms else forms[0]
     stretched = None
     six_w = None
