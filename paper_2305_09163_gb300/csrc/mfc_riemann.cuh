@@ -197,26 +197,41 @@ __device__ __forceinline__ void hllc(const Real* L, const Real* R, const Mix<Rea
 }
 
 // The FP64 path's HLLC in float-float arithmetic (mfc_df.cuh): the same
-// steps, branch order and xi - 1 form as hllc, on float-float copies of the
-// FP64 face states (integer splits); only the mixture sums before it and the
-// widening of each flux after it use the FP64 pipe.  On GB300 an FP64
-// instruction costs the issue time of ~60 FP32 ones, and the FP64 solver's
-// two square roots, three reciprocals and ~60 further FP64 operations per face
-// were half of the sweeps' FP64 work.  Differences that can cancel (p_R - p_L,
-// s - u) use the exact float-float addition; the error of the flux stays near
-// 2^-44 of its terms, far below the FP64 path's 1e-11 parity requirement.
-template <int NF, int NDIM, int DIR, bool SIX = false>
-__device__ __forceinline__ void hllc_df(const double* L, const double* R, const Mix<double>& mL,
-                                        const Mix<double>& mR, double* F, double& ut,
-                                        const EosR<double>* e6 = nullptr) {
+// steps, branch order and xi - 1 form as hllc, on float-float face states;
+// only the widening of each flux after it uses the FP64 pipe.  On GB300 an
+// FP64 instruction costs the issue time of ~60 FP32 ones, and the FP64
+// solver's two square roots, three reciprocals and ~60 further FP64 operations
+// per face were half of the sweeps' FP64 work.  Differences that can cancel
+// (p_R - p_L, s - u) use the exact float-float addition; the error of the flux
+// stays near 2^-44 of its terms, far below the FP64 path's 1e-11 parity
+// requirement.  The states come either as FP64 values (split by integer
+// operations when read) or already in float-float; `at(v)` reads variable v.
+struct F64States {
+    const double* p;
+    __device__ __forceinline__ df at(int v) const { return df_from_double(p[v]); }
+};
+struct DfStates {
+    const df* p;
+    __device__ __forceinline__ df at(int v) const { return p[v]; }
+};
+
+// Mixture quantities of a float-float face state (see Mix).
+struct MixDf {
+    df r, G, P, n;
+};
+
+// Returns whether the flux took the left state (useL).
+template <int NF, int NDIM, int DIR, typename States>
+__device__ __forceinline__ bool hllc_df_core(const States& L, const States& R, const MixDf& mL, const MixDf& mR,
+                                             double* F, double& ut) {
     using Lay = Layout<NF, NDIM>;
     constexpr int NS = Lay::NS, IM = Lay::IM, IE = Lay::IE, IA = Lay::IA;
-    const df uL = df_from_double(L[IM + DIR]), uR = df_from_double(R[IM + DIR]);
-    const df pL = df_from_double(L[IE]), pR = df_from_double(R[IE]);
-    const df rL = df_from_double(mL.r), rR = df_from_double(mR.r);
+    const df uL = L.at(IM + DIR), uR = R.at(IM + DIR);
+    const df pL = L.at(IE), pR = R.at(IE);
+    const df rL = mL.r, rR = mR.r;
     // c^2 = n/(Gamma rho)
-    const df cL = df_sqrt(df_div(df_from_double(mL.n), df_mul(df_from_double(mL.G), rL)));
-    const df cR = df_sqrt(df_div(df_from_double(mR.n), df_mul(df_from_double(mR.G), rR)));
+    const df cL = df_sqrt(df_div(mL.n, df_mul(mL.G, rL)));
+    const df cR = df_sqrt(df_div(mR.n, df_mul(mR.G, rR)));
     const df sL = df_min(df_add_fast(uL, df_neg(cL)), df_add_fast(uR, df_neg(cR)));
     const df sR = df_max(df_add_fast(uL, cL), df_add_fast(uR, cR));
     const df aL = df_mul(rL, df_add(sL, df_neg(uL))), aR = df_mul(rR, df_add(sR, df_neg(uR)));
@@ -224,9 +239,9 @@ __device__ __forceinline__ void hllc_df(const double* L, const double* R, const 
     const df sS = df_div(num, df_add(aL, df_neg(aR)));
     const bool useL = sL.hi >= 0.f || sS.hi >= 0.f;
     const bool star = useL ? !(sL.hi >= 0.f) : (sR.hi > 0.f);
-    const double* K = useL ? L : R;
+    const States& K = useL ? L : R;
     const df rK = useL ? rL : rR, uK = useL ? uL : uR, pK = useL ? pL : pR, sK = useL ? sL : sR;
-    const double GK = useL ? mL.G : mR.G, PK = useL ? mL.P : mR.P;
+    const df GK = useL ? mL.G : mR.G, PK = useL ? mL.P : mR.P;
     // xi - 1 = (s* - u_K)/(s_K - s*), exact face velocity u_K at a contact
     df rr = {0.f, 0.f}, xm1 = {0.f, 0.f}, sKe = {0.f, 0.f};
     const df dsu = df_add(sS, df_neg(uK));
@@ -239,12 +254,11 @@ __device__ __forceinline__ void hllc_df(const double* L, const double* R, const 
     const df utd = df_add_fast(uK, df_mul(sKe, xm1));
     df Kd[NS];
 #pragma unroll
-    for (int v = 0; v < NS; ++v) Kd[v] = df_from_double(K[v]);
+    for (int v = 0; v < NS; ++v) Kd[v] = K.at(v);
     df u2 = df_mul(Kd[IM], Kd[IM]);
 #pragma unroll
     for (int dd = 1; dd < NDIM; ++dd) u2 = df_add_fast(u2, df_mul(Kd[IM + dd], Kd[IM + dd]));
-    const df rE = df_add_fast(df_add_fast(df_mul(df_from_double(GK), pK), df_from_double(PK)),
-                              df_mul_pow2(df_mul(rK, u2), 0.5f));
+    const df rE = df_add_fast(df_add_fast(df_mul(GK, pK), PK), df_mul_pow2(df_mul(rK, u2), 0.5f));
 #pragma unroll
     for (int k = 0; k < NF; ++k) F[k] = df_to_double(df_mul(Kd[k], utd));
     const df sKds = df_mul(sKe, dsu);   // s_K (s* - u_K)
@@ -260,7 +274,21 @@ __device__ __forceinline__ void hllc_df(const double* L, const double* R, const 
 #pragma unroll
     for (int k = 0; k < NF - 1; ++k) F[IA + k] = df_to_double(df_mul(Kd[IA + k], utd));
     ut = df_to_double(utd);
+    return useL;
+}
+
+// HLLC of FP64 face states with their FP64 mixture quantities.
+template <int NF, int NDIM, int DIR, bool SIX = false>
+__device__ __forceinline__ void hllc_df(const double* L, const double* R, const Mix<double>& mL,
+                                        const Mix<double>& mR, double* F, double& ut,
+                                        const EosR<double>* e6 = nullptr) {
+    using Lay = Layout<NF, NDIM>;
+    constexpr int NS = Lay::NS, IE = Lay::IE, IA = Lay::IA;
+    const MixDf xL{df_from_double(mL.r), df_from_double(mL.G), df_from_double(mL.P), df_from_double(mL.n)};
+    const MixDf xR{df_from_double(mR.r), df_from_double(mR.G), df_from_double(mR.P), df_from_double(mR.n)};
+    const bool useL = hllc_df_core<NF, NDIM, DIR>(F64States{L}, F64States{R}, xL, xR, F, ut);
     if constexpr (SIX) {
+        const double* K = useL ? L : R;
         double aN = 1.0;
         const double pKd = K[IE];
 #pragma unroll
@@ -270,6 +298,62 @@ __device__ __forceinline__ void hllc_df(const double* L, const double* R, const 
         }
         F[NS + NF - 1] = aN * fma(e6->G_N, pKd, e6->P_N) * ut;
     }
+}
+
+// The EOS constants as float-float values (split once per kernel).
+struct EosDf {
+    df G_N, P_N, dG[2], dP[2];
+    template <typename E>
+    __device__ __forceinline__ explicit EosDf(const E& e)
+        : G_N(df_from_double((double)e.G_N)), P_N(df_from_double((double)e.P_N)) {
+        dG[0] = df_from_double((double)e.dG[0]);
+        dG[1] = df_from_double((double)e.dG[1]);
+        dP[0] = df_from_double((double)e.dP[0]);
+        dP[1] = df_from_double((double)e.dP[1]);
+    }
+};
+
+// Mixture quantities of a float-float face state, in float-float.
+template <int NF, int NDIM>
+__device__ __forceinline__ MixDf mixture_df(const df* s, const EosDf& e) {
+    using Lay = Layout<NF, NDIM>;
+    MixDf m;
+    m.r = s[0];
+#pragma unroll
+    for (int k = 1; k < NF; ++k) m.r = df_add(m.r, s[k]);
+    m.G = e.G_N;
+    m.P = e.P_N;
+#pragma unroll
+    for (int k = 0; k < NF - 1; ++k) {
+        m.G = df_add(m.G, df_mul(s[Lay::IA + k], e.dG[k]));
+        m.P = df_add(m.P, df_mul(s[Lay::IA + k], e.dP[k]));
+    }
+    m.n = df_add(df_mul(df_add_fast(m.G, {1.f, 0.f}), s[Lay::IE]), m.P);
+    return m;
+}
+
+// face_state_ok for float-float states (normalised: the sign and the order
+// against 0 and 1 follow from hi, then lo).
+__device__ __forceinline__ bool df_nonneg(df x) { return x.hi >= 0.f; }
+__device__ __forceinline__ bool df_positive(df x) { return x.hi > 0.f; }
+__device__ __forceinline__ bool df_unit(df x) { return x.hi >= 0.f && (x.hi < 1.f || (x.hi == 1.f && x.lo <= 0.f)); }
+
+template <int NF, int NDIM>
+__device__ __forceinline__ bool face_state_ok_df(const df* s, const MixDf& m) {
+    using Lay = Layout<NF, NDIM>;
+    bool ok = df_positive(m.r) && df_positive(m.n);
+#pragma unroll
+    for (int k = 0; k < NF; ++k) ok = ok && df_nonneg(s[k]);
+    if (NF > 1) {
+        df asum = s[Lay::IA];
+#pragma unroll
+        for (int k = 0; k < NF - 1; ++k) {
+            ok = ok && df_unit(s[Lay::IA + k]);
+            if (k > 0) asum = df_add(asum, s[Lay::IA + k]);
+        }
+        ok = ok && df_unit(df_add({1.f, 0.f}, df_neg(asum)));
+    }
+    return ok;
 }
 
 // Count one fallback face per calling lane with one atomic per converged
@@ -323,6 +407,36 @@ __device__ __forceinline__ void face_flux(const SweepArgs& a, const EosR<Real>& 
         }
         hllc_df<NF, NDIM, DIR, SIX>(sl, sr, mL, mR, F, ut, &e);
     }
+}
+
+// FP64 path, face states already in float-float (the reconstruction's cell
+// value plus its float-float increment): mixture and positivity test in
+// float-float, the first-order fallback splitting the two FP64 cell values;
+// no FP64 operation before the widened fluxes.
+template <int NF, int NDIM, int DIR>
+__device__ __forceinline__ void face_flux_df(const SweepArgs& a, const EosDf& e, const df* eLs, const df* eRs,
+                                             const double* cl, const double* cr, double* F, double& ut) {
+    constexpr int NS = Layout<NF, NDIM>::NS;
+    MixDf mL = mixture_df<NF, NDIM>(eLs, e);
+    MixDf mR = mixture_df<NF, NDIM>(eRs, e);
+    const bool first = a.fallback && !(face_state_ok_df<NF, NDIM>(eLs, mL) && face_state_ok_df<NF, NDIM>(eRs, mR));
+    df sl[NS], sr[NS];
+#pragma unroll
+    for (int v = 0; v < NS; ++v) {
+        sl[v] = eLs[v];
+        sr[v] = eRs[v];
+    }
+    if (first) {
+        count_fallback(a.fallback_count);
+#pragma unroll
+        for (int v = 0; v < NS; ++v) {
+            sl[v] = df_from_double(cl[v]);
+            sr[v] = df_from_double(cr[v]);
+        }
+        mL = mixture_df<NF, NDIM>(sl, e);
+        mR = mixture_df<NF, NDIM>(sr, e);
+    }
+    hllc_df_core<NF, NDIM, DIR>(DfStates{sl}, DfStates{sr}, mL, mR, F, ut);
 }
 
 }  // namespace mfc

@@ -176,8 +176,14 @@ __device__ __forceinline__ void sweep_x_stream_body(const SweepArgs& a) {
     // over the variables the float-float code overflowed the instruction cache
     // (ncu: "no instruction" the largest stall, 1.0-1.5 warps per issue).
     constexpr bool ROLL = sizeof(Real) == 8 && !LEARNED;
+    // DFS (FP64 uniform WENO5, five-equation): the edge values stay float-float
+    // (cell value + increment, in the same 8 bytes) from the reconstruction into
+    // the Riemann solver: no FP64 edge sums and mixtures (256^3: see DESIGN)
+    constexpr bool DFS = ROLL && ORDER == 5 && !NONUNIF && !SIX;
     __shared__ Real sh_eL[NS][ER];
     __shared__ Real sh_eR[ROLL ? NS : 1][kStreamThreads];
+    df(*dsh_eL)[ER] = reinterpret_cast<df(*)[ER]>(sh_eL);
+    df(*dsh_eR)[kStreamThreads] = reinterpret_cast<df(*)[kStreamThreads]>(sh_eR);
     __shared__ Real sh_eLJ[NJ][ER];
     __shared__ Real sh_F[NQ + 1][ER];
     const Real* __restrict__ w = static_cast<const Real*>(a.w);
@@ -191,6 +197,7 @@ __device__ __forceinline__ void sweep_x_stream_body(const SweepArgs& a) {
     const int bclo = a.g.bc_lo[0], bchi = a.g.bc_hi[0];
     const Real eps34 = sweep_epsw<Real, ORDER>(a);  // 3/4 eps (WENO5) or eps (WENO3)
     const EosR<Real> e = sweep_eos<Real>(a);
+    [[maybe_unused]] const EosDf edf(e);   // DFS: the EOS constants as float-float
     const Real inv_dx = sweep_inv_dx<Real>(a, 0);
     const int t = threadIdx.x;
     LearnSmem<NS>* lsm = nullptr;
@@ -306,15 +313,22 @@ __device__ __forceinline__ void sweep_x_stream_body(const SweepArgs& a) {
                     for (int k = 0; k < 5; ++k) vn[k] = __ldg(wr + (q + 1) * nc + mk[k]);
                 }
                 Real Dq[4] = {v[1] - v[0], v[2] - v[1], v[3] - v[2], v[4] - v[3]};
-                Real er, el;
-                if constexpr (NONUNIF) {
-                    const GridCol<true> grow(a.grid[0], a.grid_stride[0], c);
-                    weno5_edges_nu(v[2], Dq, sweep_epsw<Real, 3>(a), grow, er, el);
+                if constexpr (DFS) {
+                    df er, el;
+                    weno5_edges_df(v[2], Dq, eps34, er, el);
+                    dsh_eL[q][pos] = el;
+                    dsh_eR[q][t] = er;
                 } else {
-                    weno_edges<ORDER>(v[2], Dq, eps34, er, el);
+                    Real er, el;
+                    if constexpr (NONUNIF) {
+                        const GridCol<true> grow(a.grid[0], a.grid_stride[0], c);
+                        weno5_edges_nu(v[2], Dq, sweep_epsw<Real, 3>(a), grow, er, el);
+                    } else {
+                        weno_edges<ORDER>(v[2], Dq, eps34, er, el);
+                    }
+                    sh_eL[q][pos] = el;
+                    sh_eR[q][t] = er;
                 }
-                sh_eL[q][pos] = el;
-                sh_eR[q][t] = er;
             }
 #pragma unroll
             for (int q = 0; q < NS; ++q) {
@@ -370,7 +384,20 @@ __device__ __forceinline__ void sweep_x_stream_body(const SweepArgs& a) {
         __syncthreads();
         Real F[NQ], ut = 0;
         const bool has_face = live && c >= 0 && s >= own0 - 1;
-        if (has_face) {
+        if constexpr (DFS) {
+          if (has_face) {
+            df lftd[NS], erd[NS];
+#pragma unroll
+            for (int q = 0; q < NS; ++q) {
+                lftd[q] = dsh_eL[q][pl];
+                erd[q] = dsh_eR[q][t];
+            }
+            face_flux_df<NF, NDIM, 0>(a, edf, lftd, erd, cm1, cell, F, ut);
+#pragma unroll
+            for (int q = 0; q < NQ; ++q) sh_F[q][pos] = F[q];
+            sh_F[NQ][pos] = ut;
+          }
+        } else if (has_face) {
             Real lft[NS];
 #pragma unroll
             for (int q = 0; q < NS; ++q) lft[q] = sh_eL[q][pl];
@@ -482,6 +509,10 @@ __device__ __forceinline__ void sweep_yz_stream_body(const SweepArgs& a) {
     __shared__ Real ring[RING][NS][32];
     __shared__ Real sh_eL[NS][ER][32];
     __shared__ Real sh_eR[ROLL ? NS : 1][kRowsPerChunk][32];
+    // DFS: edge values kept in float-float into the Riemann solver (x stream body)
+    constexpr bool DFS = ROLL && ORDER == 5 && !NONUNIF && !SIX;
+    df(*dsh_eL)[ER][32] = reinterpret_cast<df(*)[ER][32]>(sh_eL);
+    df(*dsh_eR)[kRowsPerChunk][32] = reinterpret_cast<df(*)[kRowsPerChunk][32]>(sh_eR);
     __shared__ Real sh_eLJ[NJ][ER][32];
     __shared__ Real sh_F[NQ + 1][ER][32];
     extern __shared__ __align__(16) unsigned char stage_smem[];   // a.stage operands
@@ -506,6 +537,7 @@ __device__ __forceinline__ void sweep_yz_stream_body(const SweepArgs& a) {
     const int bclo = a.g.bc_lo[DIR], bchi = a.g.bc_hi[DIR];
     const Real eps34 = sweep_epsw<Real, ORDER>(a);  // 3/4 eps (WENO5) or eps (WENO3)
     const EosR<Real> e = sweep_eos<Real>(a);
+    [[maybe_unused]] const EosDf edf(e);   // DFS: the EOS constants as float-float
     const Real inv_dx = sweep_inv_dx<Real>(a, DIR);
     LearnSmem<NS>* lsm = nullptr;
     if constexpr (LEARNED) {
@@ -586,15 +618,22 @@ __device__ __forceinline__ void sweep_yz_stream_body(const SweepArgs& a) {
                     const Real v0 = ring[s0r][q][lane], v1 = ring[s1r][q][lane], v2 = ring[s2r][q][lane];
                     const Real v3 = ring[s3r][q][lane], v4 = ring[s4r][q][lane];
                     Real Dq[4] = {v1 - v0, v2 - v1, v3 - v2, v4 - v3};
-                    Real er, el;
-                    if constexpr (NONUNIF) {
-                        const GridCol<false> grow(a.grid[DIR], a.grid_stride[DIR], c);
-                        weno5_edges_nu(v2, Dq, sweep_epsw<Real, 3>(a), grow, er, el);
+                    if constexpr (DFS) {
+                        df er, el;
+                        weno5_edges_df(v2, Dq, eps34, er, el);
+                        dsh_eL[q][eslot(c)][lane] = el;
+                        dsh_eR[q][row][lane] = er;
                     } else {
-                        weno_edges<ORDER>(v2, Dq, eps34, er, el);
+                        Real er, el;
+                        if constexpr (NONUNIF) {
+                            const GridCol<false> grow(a.grid[DIR], a.grid_stride[DIR], c);
+                            weno5_edges_nu(v2, Dq, sweep_epsw<Real, 3>(a), grow, er, el);
+                        } else {
+                            weno_edges<ORDER>(v2, Dq, eps34, er, el);
+                        }
+                        sh_eL[q][eslot(c)][lane] = el;
+                        sh_eR[q][row][lane] = er;
                     }
-                    sh_eL[q][eslot(c)][lane] = el;
-                    sh_eR[q][row][lane] = er;
                 }
 #pragma unroll
                 for (int q = 0; q < NS; ++q) {
@@ -641,7 +680,20 @@ __device__ __forceinline__ void sweep_yz_stream_body(const SweepArgs& a) {
         }
         Real F[NQ], ut = 0;
         const bool has_face = live && c >= s0;
-        if (has_face) {
+        if constexpr (DFS) {
+          if (has_face) {
+            df lftd[NS], erd[NS];
+#pragma unroll
+            for (int q = 0; q < NS; ++q) {
+                lftd[q] = dsh_eL[q][eslot(c - 1)][lane];
+                erd[q] = dsh_eR[q][row][lane];
+            }
+            face_flux_df<NF, NDIM, DIR>(a, edf, lftd, erd, cm1, cell, F, ut);
+#pragma unroll
+            for (int q = 0; q < NQ; ++q) sh_F[q][eslot(c)][lane] = F[q];
+            sh_F[NQ][eslot(c)][lane] = ut;
+          }
+        } else if (has_face) {
             Real lft[NS];
 #pragma unroll
             for (int q = 0; q < NS; ++q) lft[q] = sh_eL[q][eslot(c - 1)][lane];

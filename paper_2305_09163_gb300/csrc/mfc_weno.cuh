@@ -33,8 +33,7 @@ namespace mfc {
 //   eR - v_c = (g2^2 (2 D3 - 5 D2) - 6 g1^2 (2 D1 + D2) + 3 g0^2 (D0 - 4 D1))
 //              / (6 (g2^2 + 6 g1^2 + 3 g0^2)).
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ void weno5_edges(double vc, const double D[4], double eps34,
-                                            double& eR, double& eL) {
+__device__ __forceinline__ void weno5_increments(const double D[4], double eps34, df& iR, df& iL) {
     // sums use the fast float-float addition: its error, ~2^-44 of the
     // operands, is relative to the stencil's differences, far inside the
     // path's parity tolerance; scalings by 2 and 4 are exact
@@ -63,8 +62,29 @@ __device__ __forceinline__ void weno5_edges(double vc, const double D[4], double
     const df M2 = df_add_fast(d0, df_mul_pow2(d1, -4.f));
     const df numR = df_add_fast(df_add_fast(df_mul(q2, M0), df_mul(q1, M1)), df_mul(wR2, M2));
     const df denR = df_mul_f(df_add_fast(df_add_fast(q2, q1), wR2), 6.f);
-    eL = vc + df_to_double(df_div(numL, denL));
-    eR = vc + df_to_double(df_div(numR, denR));
+    iL = df_div(numL, denL);
+    iR = df_div(numR, denR);
+}
+
+// The two edge values in FP64 (the increments widened and added to v_c).
+__device__ __forceinline__ void weno5_edges(double vc, const double D[4], double eps34,
+                                            double& eR, double& eL) {
+    df iR, iL;
+    weno5_increments(D, eps34, iR, iL);
+    eL = vc + df_to_double(iL);
+    eR = vc + df_to_double(iR);
+}
+
+// The two edge values as float-float numbers: the cell value split (integer
+// operations) plus the increment, with the accurate float-float addition (the
+// face state then carries ~2^-48 of its magnitude, as an FP64 edge split for
+// the float-float Riemann solver does), and no FP64 operation.
+__device__ __forceinline__ void weno5_edges_df(double vc, const double D[4], double eps34, df& eR, df& eL) {
+    df iR, iL;
+    weno5_increments(D, eps34, iR, iL);
+    const df c = df_from_double(vc);
+    eL = df_add(c, iL);
+    eR = df_add(c, iR);
 }
 
 // FP32 variant for the mixed path.  The weights are normalised by the smallest
