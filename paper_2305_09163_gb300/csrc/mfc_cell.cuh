@@ -640,16 +640,17 @@ __device__ __forceinline__ void publish_rate(const SweepArgs& a, const RateAcc& 
 // are written to a.w_next (the next stage's sweeps read them there instead of
 // a separate recovery pass over q) and, with a.rate_max, its CFL rate is
 // returned for the caller's RateAcc (-1: non-physical); otherwise 0.
+//
+// finish_cell takes the two face fluxes and face velocities; finish_cell_df the
+// same in float-float (FP64 path: the flux differences are formed before one
+// widening each); both call finish_cell_rates with (F_- - F_+)/dx and the
+// face-velocity divergence.
 template <typename Real, int NF, int NDIM, int DIR, bool SIX = false>
-__device__ __forceinline__ double finish_cell(const SweepArgs& a, long long idx, const Real* Fm, const Real* Fp,
-                                              Real um, Real up, const Real* cell, Real inv_dx, int b, long long sd,
-                                              long long tr = -1, const unsigned char* stg = nullptr, int slot = 0) {
+__device__ __forceinline__ double finish_cell_rates(const SweepArgs& a, long long idx, Real* out, const Real du,
+                                                    const Real* cell, Real inv_dx, int b, long long sd, long long tr,
+                                                    const unsigned char* stg, int slot) {
     using Lay = Layout<NF, NDIM, SIX>;
     constexpr int NS = Lay::NS, NQ = Lay::NQ, IA = Lay::IA;
-    Real out[NQ];
-#pragma unroll
-    for (int v = 0; v < NQ; ++v) out[v] = (Fm[v] - Fp[v]) * inv_dx;
-    const Real du = (up - um) * inv_dx;
     if constexpr (SIX) {
         const Real pdu = cell[Lay::IE] * du;
         Real aN = 1;
@@ -759,6 +760,34 @@ __device__ __forceinline__ double finish_cell(const SweepArgs& a, long long idx,
         }
     }
     return 0.0;
+}
+
+template <typename Real, int NF, int NDIM, int DIR, bool SIX = false>
+__device__ __forceinline__ double finish_cell(const SweepArgs& a, long long idx, const Real* Fm, const Real* Fp,
+                                              Real um, Real up, const Real* cell, Real inv_dx, int b, long long sd,
+                                              long long tr = -1, const unsigned char* stg = nullptr, int slot = 0) {
+    constexpr int NQ = Layout<NF, NDIM, SIX>::NQ;
+    Real out[NQ];
+#pragma unroll
+    for (int v = 0; v < NQ; ++v) out[v] = (Fm[v] - Fp[v]) * inv_dx;
+    const Real du = (up - um) * inv_dx;
+    return finish_cell_rates<Real, NF, NDIM, DIR, SIX>(a, idx, out, du, cell, inv_dx, b, sd, tr, stg, slot);
+}
+
+// Five-equation FP64 path with float-float fluxes: the differences and the
+// division by dx in float-float (accurate addition: relative error ~2^-47 of
+// the difference), one widening per value.
+template <int NF, int NDIM, int DIR>
+__device__ __forceinline__ double finish_cell_df(const SweepArgs& a, long long idx, const df* Fm, const df* Fp,
+                                                 df um, df up, const double* cell, double inv_dx, df inv_df, int b,
+                                                 long long sd, long long tr = -1, const unsigned char* stg = nullptr,
+                                                 int slot = 0) {
+    constexpr int NQ = Layout<NF, NDIM>::NQ;
+    double out[NQ];
+#pragma unroll
+    for (int v = 0; v < NQ; ++v) out[v] = df_to_double(df_mul(df_add(Fm[v], df_neg(Fp[v])), inv_df));
+    const double du = df_to_double(df_mul(df_add(up, df_neg(um)), inv_df));
+    return finish_cell_rates<double, NF, NDIM, DIR>(a, idx, out, du, cell, inv_dx, b, sd, tr, stg, slot);
 }
 
 }  // namespace mfc

@@ -220,10 +220,11 @@ struct MixDf {
     df r, G, P, n;
 };
 
-// Returns whether the flux took the left state (useL).
+// Fluxes and face velocity in float-float; returns whether the flux took the
+// left state (useL).
 template <int NF, int NDIM, int DIR, typename States>
 __device__ __forceinline__ bool hllc_df_core(const States& L, const States& R, const MixDf& mL, const MixDf& mR,
-                                             double* F, double& ut) {
+                                             df* F, df& ut) {
     using Lay = Layout<NF, NDIM>;
     constexpr int NS = Lay::NS, IM = Lay::IM, IE = Lay::IE, IA = Lay::IA;
     const df uL = L.at(IM + DIR), uR = R.at(IM + DIR);
@@ -260,20 +261,20 @@ __device__ __forceinline__ bool hllc_df_core(const States& L, const States& R, c
     for (int dd = 1; dd < NDIM; ++dd) u2 = df_add_fast(u2, df_mul(Kd[IM + dd], Kd[IM + dd]));
     const df rE = df_add_fast(df_add_fast(df_mul(GK, pK), PK), df_mul_pow2(df_mul(rK, u2), 0.5f));
 #pragma unroll
-    for (int k = 0; k < NF; ++k) F[k] = df_to_double(df_mul(Kd[k], utd));
+    for (int k = 0; k < NF; ++k) F[k] = df_mul(Kd[k], utd);
     const df sKds = df_mul(sKe, dsu);   // s_K (s* - u_K)
 #pragma unroll
     for (int dd = 0; dd < NDIM; ++dd) {
         if (dd == DIR)
-            F[IM + dd] = df_to_double(df_add_fast(df_add_fast(df_mul(df_mul(rK, uK), utd), pK), df_mul(df_mul(sKds, xi), rK)));
+            F[IM + dd] = df_add_fast(df_add_fast(df_mul(df_mul(rK, uK), utd), pK), df_mul(df_mul(sKds, xi), rK));
         else
-            F[IM + dd] = df_to_double(df_mul(df_mul(rK, Kd[IM + dd]), utd));
+            F[IM + dd] = df_mul(df_mul(rK, Kd[IM + dd]), utd);
     }
-    F[IE] = df_to_double(df_add_fast(df_add_fast(df_mul(rE, utd), df_mul(pK, uK)),
-                                     df_mul(sKds, df_add_fast(df_mul(df_mul(xi, rK), sS), df_mul(pK, rr)))));
+    F[IE] = df_add_fast(df_add_fast(df_mul(rE, utd), df_mul(pK, uK)),
+                        df_mul(sKds, df_add_fast(df_mul(df_mul(xi, rK), sS), df_mul(pK, rr))));
 #pragma unroll
-    for (int k = 0; k < NF - 1; ++k) F[IA + k] = df_to_double(df_mul(Kd[IA + k], utd));
-    ut = df_to_double(utd);
+    for (int k = 0; k < NF - 1; ++k) F[IA + k] = df_mul(Kd[IA + k], utd);
+    ut = utd;
     return useL;
 }
 
@@ -286,7 +287,11 @@ __device__ __forceinline__ void hllc_df(const double* L, const double* R, const 
     constexpr int NS = Lay::NS, IE = Lay::IE, IA = Lay::IA;
     const MixDf xL{df_from_double(mL.r), df_from_double(mL.G), df_from_double(mL.P), df_from_double(mL.n)};
     const MixDf xR{df_from_double(mR.r), df_from_double(mR.G), df_from_double(mR.P), df_from_double(mR.n)};
-    const bool useL = hllc_df_core<NF, NDIM, DIR>(F64States{L}, F64States{R}, xL, xR, F, ut);
+    df Fd[NS], utd;
+    const bool useL = hllc_df_core<NF, NDIM, DIR>(F64States{L}, F64States{R}, xL, xR, Fd, utd);
+#pragma unroll
+    for (int v = 0; v < NS; ++v) F[v] = df_to_double(Fd[v]);
+    ut = df_to_double(utd);
     if constexpr (SIX) {
         const double* K = useL ? L : R;
         double aN = 1.0;
@@ -415,7 +420,7 @@ __device__ __forceinline__ void face_flux(const SweepArgs& a, const EosR<Real>& 
 // no FP64 operation before the widened fluxes.
 template <int NF, int NDIM, int DIR>
 __device__ __forceinline__ void face_flux_df(const SweepArgs& a, const EosDf& e, const df* eLs, const df* eRs,
-                                             const double* cl, const double* cr, double* F, double& ut) {
+                                             const double* cl, const double* cr, df* F, df& ut) {
     constexpr int NS = Layout<NF, NDIM>::NS;
     MixDf mL = mixture_df<NF, NDIM>(eLs, e);
     MixDf mR = mixture_df<NF, NDIM>(eRs, e);

@@ -186,6 +186,7 @@ __device__ __forceinline__ void sweep_x_stream_body(const SweepArgs& a) {
     df(*dsh_eR)[kStreamThreads] = reinterpret_cast<df(*)[kStreamThreads]>(sh_eR);
     __shared__ Real sh_eLJ[NJ][ER];
     __shared__ Real sh_F[NQ + 1][ER];
+    df(*dsh_F)[ER] = reinterpret_cast<df(*)[ER]>(sh_F);   // DFS: float-float fluxes
     const Real* __restrict__ w = static_cast<const Real*>(a.w);
     const int n = a.g.n[0];
     const long long rowlen = (long long)n + 2;
@@ -199,6 +200,7 @@ __device__ __forceinline__ void sweep_x_stream_body(const SweepArgs& a) {
     const EosR<Real> e = sweep_eos<Real>(a);
     [[maybe_unused]] const EosDf edf(e);   // DFS: the EOS constants as float-float
     const Real inv_dx = sweep_inv_dx<Real>(a, 0);
+    [[maybe_unused]] const df inv_df = df_from_double((double)inv_dx);
     const int t = threadIdx.x;
     LearnSmem<NS>* lsm = nullptr;
     if constexpr (LEARNED) {
@@ -383,6 +385,7 @@ __device__ __forceinline__ void sweep_x_stream_body(const SweepArgs& a) {
         }
         __syncthreads();
         Real F[NQ], ut = 0;
+        [[maybe_unused]] df Fd[DFS ? NQ : 1], utd = {0.f, 0.f};
         const bool has_face = live && c >= 0 && s >= own0 - 1;
         if constexpr (DFS) {
           if (has_face) {
@@ -392,10 +395,10 @@ __device__ __forceinline__ void sweep_x_stream_body(const SweepArgs& a) {
                 lftd[q] = dsh_eL[q][pl];
                 erd[q] = dsh_eR[q][t];
             }
-            face_flux_df<NF, NDIM, 0>(a, edf, lftd, erd, cm1, cell, F, ut);
+            face_flux_df<NF, NDIM, 0>(a, edf, lftd, erd, cm1, cell, Fd, utd);
 #pragma unroll
-            for (int q = 0; q < NQ; ++q) sh_F[q][pos] = F[q];
-            sh_F[NQ][pos] = ut;
+            for (int q = 0; q < NQ; ++q) dsh_F[q][pos] = Fd[q];
+            dsh_F[NQ][pos] = utd;
           }
         } else if (has_face) {
             Real lft[NS];
@@ -418,7 +421,15 @@ __device__ __forceinline__ void sweep_x_stream_body(const SweepArgs& a) {
             sh_F[NQ][pos] = ut;
         }
         __syncthreads();
-        if (has_face && s >= own0 && c >= 1) {
+        if (DFS && has_face && s >= own0 && c >= 1) {
+            if constexpr (DFS) {
+                df Fm[NQ];
+#pragma unroll
+                for (int q = 0; q < NQ; ++q) Fm[q] = dsh_F[q][pl];
+                racc.add(finish_cell_df<NF, NDIM, 0>(a, rowoff + (c - 1), Fm, Fd, dsh_F[NQ][pl], utd, cm1, inv_dx,
+                                                     inv_df, c - 1, 1, row));
+            }
+        } else if (has_face && s >= own0 && c >= 1) {
             Real Fm[NQ];
 #pragma unroll
             for (int q = 0; q < NQ; ++q) Fm[q] = sh_F[q][pl];
@@ -515,6 +526,7 @@ __device__ __forceinline__ void sweep_yz_stream_body(const SweepArgs& a) {
     df(*dsh_eR)[kRowsPerChunk][32] = reinterpret_cast<df(*)[kRowsPerChunk][32]>(sh_eR);
     __shared__ Real sh_eLJ[NJ][ER][32];
     __shared__ Real sh_F[NQ + 1][ER][32];
+    df(*dsh_F)[ER][32] = reinterpret_cast<df(*)[ER][32]>(sh_F);   // DFS: float-float fluxes
     extern __shared__ __align__(16) unsigned char stage_smem[];   // a.stage operands
     static_assert(32 * kRowsPerChunk == kStageSlots, "one staging slot per thread");
     const Real* __restrict__ w = static_cast<const Real*>(a.w);
@@ -539,6 +551,7 @@ __device__ __forceinline__ void sweep_yz_stream_body(const SweepArgs& a) {
     const EosR<Real> e = sweep_eos<Real>(a);
     [[maybe_unused]] const EosDf edf(e);   // DFS: the EOS constants as float-float
     const Real inv_dx = sweep_inv_dx<Real>(a, DIR);
+    [[maybe_unused]] const df inv_df = df_from_double((double)inv_dx);
     LearnSmem<NS>* lsm = nullptr;
     if constexpr (LEARNED) {
         __shared__ LearnSmem<NS> lbuf[kRowsPerChunk];
@@ -679,6 +692,7 @@ __device__ __forceinline__ void sweep_yz_stream_body(const SweepArgs& a) {
             for (int q = 0; q < NS; ++q) ring[slot(inext)][q][lane] = nxt[q];
         }
         Real F[NQ], ut = 0;
+        [[maybe_unused]] df Fd[DFS ? NQ : 1], utd = {0.f, 0.f};
         const bool has_face = live && c >= s0;
         if constexpr (DFS) {
           if (has_face) {
@@ -688,10 +702,10 @@ __device__ __forceinline__ void sweep_yz_stream_body(const SweepArgs& a) {
                 lftd[q] = dsh_eL[q][eslot(c - 1)][lane];
                 erd[q] = dsh_eR[q][row][lane];
             }
-            face_flux_df<NF, NDIM, DIR>(a, edf, lftd, erd, cm1, cell, F, ut);
+            face_flux_df<NF, NDIM, DIR>(a, edf, lftd, erd, cm1, cell, Fd, utd);
 #pragma unroll
-            for (int q = 0; q < NQ; ++q) sh_F[q][eslot(c)][lane] = F[q];
-            sh_F[NQ][eslot(c)][lane] = ut;
+            for (int q = 0; q < NQ; ++q) dsh_F[q][eslot(c)][lane] = Fd[q];
+            dsh_F[NQ][eslot(c)][lane] = utd;
           }
         } else if (has_face) {
             Real lft[NS];
@@ -715,9 +729,6 @@ __device__ __forceinline__ void sweep_yz_stream_body(const SweepArgs& a) {
         }
         __syncthreads();
         if (fin) {
-            Real Fm[NQ];
-#pragma unroll
-            for (int q = 0; q < NQ; ++q) Fm[q] = sh_F[q][eslot(c - 1)][lane];
             const unsigned char* stg = nullptr;
             if constexpr (STAGE) {
                 if (a.stage) {
@@ -725,10 +736,22 @@ __device__ __forceinline__ void sweep_yz_stream_body(const SweepArgs& a) {
                     stg = stage_smem;
                 }
             }
-            racc.add(finish_cell<Real, NF, NDIM, DIR, SIX>(
-                a, basei + (long long)(c - 1) * sd, Fm, F, sh_F[NQ][eslot(c - 1)][lane], ut, cm1,
-                NONUNIF ? grid_inv_dx<false>(a.grid[DIR], a.grid_stride[DIR], c - 1, Real(0)) : inv_dx, c - 1, sd,
-                (long long)t1 + (long long)n1 * t2, stg, threadIdx.x));
+            if constexpr (DFS) {
+                df Fm[NQ];
+#pragma unroll
+                for (int q = 0; q < NQ; ++q) Fm[q] = dsh_F[q][eslot(c - 1)][lane];
+                racc.add(finish_cell_df<NF, NDIM, DIR>(a, basei + (long long)(c - 1) * sd, Fm, Fd,
+                                                       dsh_F[NQ][eslot(c - 1)][lane], utd, cm1, inv_dx, inv_df, c - 1,
+                                                       sd, (long long)t1 + (long long)n1 * t2, stg, threadIdx.x));
+            } else {
+                Real Fm[NQ];
+#pragma unroll
+                for (int q = 0; q < NQ; ++q) Fm[q] = sh_F[q][eslot(c - 1)][lane];
+                racc.add(finish_cell<Real, NF, NDIM, DIR, SIX>(
+                    a, basei + (long long)(c - 1) * sd, Fm, F, sh_F[NQ][eslot(c - 1)][lane], ut, cm1,
+                    NONUNIF ? grid_inv_dx<false>(a.grid[DIR], a.grid_stride[DIR], c - 1, Real(0)) : inv_dx, c - 1, sd,
+                    (long long)t1 + (long long)n1 * t2, stg, threadIdx.x));
+            }
         }
         // No barrier is needed here: the next chunk writes edge values (row
         // c+4 = c-1 mod ER) after this chunk's second barrier, which follows
