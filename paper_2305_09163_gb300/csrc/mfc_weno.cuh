@@ -33,12 +33,11 @@ namespace mfc {
 //   eR - v_c = (g2^2 (2 D3 - 5 D2) - 6 g1^2 (2 D1 + D2) + 3 g0^2 (D0 - 4 D1))
 //              / (6 (g2^2 + 6 g1^2 + 3 g0^2)).
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ void weno5_increments(const double D[4], double eps34, df& iR, df& iL) {
+__device__ __forceinline__ void weno5_increments_df(const df (&D)[4], double eps34, df& iR, df& iL) {
     // sums use the fast float-float addition: its error, ~2^-44 of the
     // operands, is relative to the stencil's differences, far inside the
     // path's parity tolerance; scalings by 2 and 4 are exact
-    const df d0 = df_from_double(D[0]), d1 = df_from_double(D[1]);
-    const df d2 = df_from_double(D[2]), d3 = df_from_double(D[3]);
+    const df d0 = D[0], d1 = D[1], d2 = D[2], d3 = D[3];
     const df S1 = df_mul(d1, d1), S2 = df_mul(d2, d2);
     const df b0 = df_add_fast(df_add_fast(df_mul(d0, d0), df_mul_f(df_mul(d1, d0), -2.75f)), df_mul_f(S1, 2.5f));
     const df b1 = df_add_fast(df_add_fast(S1, S2), df_mul_f(df_mul(d1, d2), -1.25f));
@@ -64,6 +63,11 @@ __device__ __forceinline__ void weno5_increments(const double D[4], double eps34
     const df denR = df_mul_f(df_add_fast(df_add_fast(q2, q1), wR2), 6.f);
     iL = df_div(numL, denL);
     iR = df_div(numR, denR);
+}
+
+__device__ __forceinline__ void weno5_increments(const double D[4], double eps34, df& iR, df& iL) {
+    const df d[4] = {df_from_double(D[0]), df_from_double(D[1]), df_from_double(D[2]), df_from_double(D[3])};
+    weno5_increments_df(d, eps34, iR, iL);
 }
 
 // The two edge values in FP64 (the increments widened and added to v_c).
