@@ -86,13 +86,13 @@ SCHEDULERS = 152 * 4
 # Warp instructions per cell of the FP64 WENO5 sweeps (x, y, z; 3D, two
 # fluids, smsp__inst_executed.sum / cells of one ncu capture).  Re-measured
 # whenever the FP64 sweeps change: NCU_FP64_SWEEPS says which capture.
-FP64_SWEEP_WARP_INST_PER_CELL = (229.0, 231.1, 241.8)
+FP64_SWEEP_WARP_INST_PER_CELL = (230.3, 231.6, 243.6)
 # From the same capture: FP64-pipe and FP32 (fma) pipe activity of the sweeps
 # (mean over x, y, z) and DRAM bytes per cell per launch (the z sweep of an RK
 # stage also writes the next stage's primitives).
-FP64_SWEEP_PIPE_FP64 = 0.630
-FP64_SWEEP_PIPE_FMA = 0.413
-FP64_SWEEP_DRAM_BYTES_PER_CELL = (103.5 + 159.9 + 337.2) / 3.0
+FP64_SWEEP_PIPE_FP64 = 0.359
+FP64_SWEEP_PIPE_FMA = 0.526
+FP64_SWEEP_DRAM_BYTES_PER_CELL = (103.8 + 159.0 + 334.8) / 3.0
 NCU_FP64_SWEEPS = "profiles/sweep_fp64_shock_bubble_160.md"
 # Nominal FP32 peak: 152 SMs x 128 FMA/clk x 2 FLOP x 2.07 GHz
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
