@@ -13,10 +13,12 @@ namespace mfc {
 // b the smoothness indicators without their 4/3 factor), where the stencil is
 // flat to FP32 resolution (s <= 1e-7 |v_c|), and where the learned edge value
 // would leave the range of cells c-1, c, c+1.  Only the stencils whose learned
-// value can be used go to the network: the warp packs them (ballot and prefix
-// count) into shared memory as BF16 rows of the five normalised differences,
-// one row per edge, evaluates the network on the tensor cores 16 rows per
-// tile, and each lane turns its rows' logits into weights and edge values.
+// value can be used go to the network: per variable the warp packs them
+// (ballot and prefix count) into shared memory as BF16 rows of the five
+// normalised differences, one row per edge, evaluates the network on the
+// tensor cores 16 rows per tile, and each lane turns its rows' logits into
+// weights and edge values while its stencil is still in registers.  A warp
+// whose 32 stencils of a variable all keep the JS weights skips the network.
 // All 32 lanes must call these functions.
 // ---------------------------------------------------------------------------
 #ifndef MFC_LEARN_TILES
@@ -24,17 +26,15 @@ namespace mfc {
 #endif
 constexpr int kLearnTiles = MFC_LEARN_TILES;
 
-template <int NS> struct LearnSmem {
-    // one row per network evaluation (both edges of up to 32 cells x NS
-    // variables): BF16 inputs in columns 0..4, then overwritten by the logits
-    uint4 row[2 * NS * 32];
+struct LearnRows {
+    // one row per network evaluation (both edges of up to 32 cells of one
+    // variable): BF16 inputs in columns 0..4, then overwritten by the logits
+    uint4 row[64];
 };
 
 // Network over rows 0..nrows-1 of sm; each row's inputs are replaced by its
 // three logits (FP32, words 0..2).
-template <int NS>
-__device__ __forceinline__ void learned_logits(const uint4* __restrict__ frag, LearnSmem<NS>& sm, int nrows,
-                                               int lane) {
+__device__ __forceinline__ void learned_logits(const uint4* __restrict__ frag, LearnRows& sm, int nrows, int lane) {
     const int g = lane >> 2, t = lane & 3;
     const int nt = (nrows + 15) >> 4;
     const uint32_t* rw = reinterpret_cast<const uint32_t*>(sm.row);
@@ -76,108 +76,107 @@ __device__ __forceinline__ float learned_increment(const uint4& row, float d0, f
     return __fdividef(fmaf(e0, d0, fmaf(e1, d1, e2 * d2)), e0 + e1 + e2);
 }
 
-// Edge values of one cell for all NS variables: WENO5-JS (eRjs, eLjs) and the
-// learned form (eR, eL; equal to the JS values where the sensor trips).
-// stencil(v, d) returns the cell value of variable v and fills d with the four
-// differences across cells c-2..c+2; it is called once per variable, and again
-// for the variables whose stencils went to the network, so that the stencils
-// need not stay in registers across the network.  Returns the number of
-// network rows (edges) the warp evaluated.
+// Edge values of one variable of one cell: WENO5-JS (eRjs, eLjs) and the
+// learned form (eR, eL; equal to the JS values where the sensor trips).  vc is
+// the cell value and d the four differences across cells c-2..c+2.  Returns
+// the number of network rows (edges) the warp evaluated (warp-uniform).
+__device__ __forceinline__ int learned_var_edges(float vc, const float (&d)[4], float eps34, float tau, bool bound,
+                                                 const uint4* __restrict__ frag, LearnRows& sm, int lane,
+                                                 float& eRjs, float& eLjs, float& eR, float& eL) {
+    weno5_edges(vc, d, eps34, eRjs, eLjs);
+    eR = eRjs;
+    eL = eLjs;
+    const float S0 = d[0] * d[0], S1 = d[1] * d[1], S2 = d[2] * d[2], S3 = d[3] * d[3];
+    const float b0 = fmaf(2.5f, S1, fmaf(-2.75f, d[1] * d[0], S0));
+    const float b1 = fmaf(-1.25f, d[1] * d[2], S1 + S2);
+    const float b2 = fmaf(2.5f, S2, fmaf(-2.75f, d[2] * d[3], S3));
+    const float xm2 = -(d[0] + d[1]), xm1 = -d[1], xp1 = d[2], xp2 = d[2] + d[3];
+    const float sc = fmaxf(fmaxf(fabsf(xm2), fabsf(xm1)), fmaxf(fabsf(xp1), fabsf(xp2)));
+    const float bmax = fmaxf(b0, fmaxf(b1, b2)), bmin = fminf(b0, fminf(b1, b2));
+    const bool usejs = !(sc > 1e-7f * fabsf(vc)) || (bmax > tau * fmaf(1e-6f * sc, sc, bmin));
+    const unsigned need = __ballot_sync(0xffffffffu, !usejs);
+    if (need == 0u) return 0;
+    const int nrows = 2 * __popc(need);
+    const int r = 2 * __popc(need & ((1u << lane) - 1u));
+    __syncwarp();   // the previous evaluation's logits are read before rows are rewritten
+    if (!usejs) {
+        const float is = __fdividef(1.0f, sc + 1e-30f);
+        // edge at c+1/2: stencil c-2..c+2; edge at c-1/2: the mirrored stencil
+        sm.row[r] = make_uint4(pack_bf16(xm2 * is, xm1 * is), pack_bf16(0.f, xp1 * is), pack_bf16(xp2 * is, 0.f), 0u);
+        sm.row[r + 1] =
+            make_uint4(pack_bf16(xp2 * is, xp1 * is), pack_bf16(0.f, xm1 * is), pack_bf16(xm2 * is, 0.f), 0u);
+    }
+    learned_logits(frag, sm, nrows, lane);
+    if (!usejs) {
+        // increments at c+1/2 of the stencils c-2..c, c-1..c+1, c..c+2
+        const float p0 = fmaf(5.f / 6.f, d[1], (-1.f / 3.f) * d[0]);
+        const float p1 = fmaf(1.f / 6.f, d[1], (1.f / 3.f) * d[2]);
+        const float p2 = fmaf(2.f / 3.f, d[2], (-1.f / 6.f) * d[3]);
+        // increments at c-1/2 of the stencils c..c+2, c-1..c+1, c-2..c
+        const float m0 = fmaf(-5.f / 6.f, d[2], (1.f / 3.f) * d[3]);
+        const float m1 = fmaf(-1.f / 6.f, d[2], (-1.f / 3.f) * d[1]);
+        const float m2 = fmaf(-2.f / 3.f, d[1], (1.f / 6.f) * d[0]);
+        const float il = learned_increment(sm.row[r], p0, p1, p2);
+        const float ir = learned_increment(sm.row[r + 1], m0, m1, m2);
+        // accept a learned value only inside the range of cells c-1, c, c+1
+        const float lo = fminf(0.f, fminf(-d[1], d[2])), hi = fmaxf(0.f, fmaxf(-d[1], d[2]));
+        if (!(bound && (il < lo || il > hi))) eL = vc + il;
+        if (!(bound && (ir < lo || ir > hi))) eR = vc + ir;
+    }
+    return nrows;
+}
+
+// The same for all NS variables of a cell, unrolled over the variables (the
+// pencil-marching sweep, which keeps its stencils in registers): stencil(v, d)
+// returns the cell value of variable v and fills d with its four differences.
 template <int NS, typename Stencil>
 __device__ __forceinline__ int learned_cell_edges(const Stencil& stencil, float eps34, float tau, bool bound,
-                                                   const uint4* __restrict__ frag, LearnSmem<NS>& sm, int lane,
+                                                   const uint4* __restrict__ frag, LearnRows& sm, int lane,
                                                    float (&eRjs)[NS], float (&eLjs)[NS], float (&eR)[NS],
                                                    float (&eL)[NS]) {
-    const unsigned below = (1u << lane) - 1u;
-    unsigned need[NS];
     int nrows = 0;
-    __syncwarp();   // the previous call's logits are read before rows are rewritten
 #pragma unroll
     for (int v = 0; v < NS; ++v) {
         float d[4];
         const float vc = stencil(v, d);
-        weno5_edges(vc, d, eps34, eRjs[v], eLjs[v]);
-        const float S0 = d[0] * d[0], S1 = d[1] * d[1], S2 = d[2] * d[2], S3 = d[3] * d[3];
-        const float b0 = fmaf(2.5f, S1, fmaf(-2.75f, d[1] * d[0], S0));
-        const float b1 = fmaf(-1.25f, d[1] * d[2], S1 + S2);
-        const float b2 = fmaf(2.5f, S2, fmaf(-2.75f, d[2] * d[3], S3));
-        const float xm2 = -(d[0] + d[1]), xm1 = -d[1], xp1 = d[2], xp2 = d[2] + d[3];
-        const float sc = fmaxf(fmaxf(fabsf(xm2), fabsf(xm1)), fmaxf(fabsf(xp1), fabsf(xp2)));
-        const float bmax = fmaxf(b0, fmaxf(b1, b2)), bmin = fminf(b0, fminf(b1, b2));
-        const bool usejs = !(sc > 1e-7f * fabsf(vc)) || (bmax > tau * fmaf(1e-6f * sc, sc, bmin));
-        need[v] = __ballot_sync(0xffffffffu, !usejs);
-        if (!usejs) {
-            const float is = __fdividef(1.0f, sc + 1e-30f);
-            const int r = nrows + 2 * __popc(need[v] & below);
-            // edge at c+1/2: stencil c-2..c+2; edge at c-1/2: the mirrored stencil
-            sm.row[r] = make_uint4(pack_bf16(xm2 * is, xm1 * is), pack_bf16(0.f, xp1 * is),
-                                   pack_bf16(xp2 * is, 0.f), 0u);
-            sm.row[r + 1] = make_uint4(pack_bf16(xp2 * is, xp1 * is), pack_bf16(0.f, xm1 * is),
-                                       pack_bf16(xm2 * is, 0.f), 0u);
-        }
-        nrows += 2 * __popc(need[v]);
-    }
-    learned_logits<NS>(frag, sm, nrows, lane);
-    int r = 0;
-#pragma unroll
-    for (int v = 0; v < NS; ++v) {
-        eL[v] = eLjs[v];
-        eR[v] = eRjs[v];
-        if (need[v] & (1u << lane)) {
-            float d[4];
-            const float vc = stencil(v, d);
-            const int rr = r + 2 * __popc(need[v] & below);
-            // increments at c+1/2 of the stencils c-2..c, c-1..c+1, c..c+2
-            const float p0 = fmaf(5.f / 6.f, d[1], (-1.f / 3.f) * d[0]);
-            const float p1 = fmaf(1.f / 6.f, d[1], (1.f / 3.f) * d[2]);
-            const float p2 = fmaf(2.f / 3.f, d[2], (-1.f / 6.f) * d[3]);
-            // increments at c-1/2 of the stencils c..c+2, c-1..c+1, c-2..c
-            const float m0 = fmaf(-5.f / 6.f, d[2], (1.f / 3.f) * d[3]);
-            const float m1 = fmaf(-1.f / 6.f, d[2], (-1.f / 3.f) * d[1]);
-            const float m2 = fmaf(-2.f / 3.f, d[1], (1.f / 6.f) * d[0]);
-            const float il = learned_increment(sm.row[rr], p0, p1, p2);
-            const float ir = learned_increment(sm.row[rr + 1], m0, m1, m2);
-            // accept a learned value only inside the range of cells c-1, c, c+1
-            const float lo = fminf(0.f, fminf(-d[1], d[2])), hi = fmaxf(0.f, fmaxf(-d[1], d[2]));
-            if (!(bound && (il < lo || il > hi))) eL[v] = vc + il;
-            if (!(bound && (ir < lo || ir > hi))) eR[v] = vc + ir;
-        }
-        r += 2 * __popc(need[v]);
+        nrows += learned_var_edges(vc, d, eps34, tau, bound, frag, sm, lane, eRjs[v], eLjs[v], eR[v], eL[v]);
     }
     return nrows;
 }
 
 // Face flux of the learned form: the learned face states, else (non-physical)
-// the WENO5-JS states, else the first-order cell values.
-template <int NF, int NDIM, int DIR>
+// the WENO5-JS states, else the first-order cell values.  loadJ(Lj, Rj) fills
+// the JS states; it is called only where the learned ones fail, so that they
+// need not be held beside them.
+template <int NF, int NDIM, int DIR, typename LoadJ>
 __device__ __forceinline__ void face_flux_learned(const SweepArgs& a, const EosR<float>& e, const float* Ll,
-                                                  const float* Rl, const float* Lj, const float* Rj, const float* cl,
+                                                  const float* Rl, const LoadJ& loadJ, const float* cl,
                                                   const float* cr, float* F, float& ut) {
     constexpr int NS = Layout<NF, NDIM>::NS;
-    Mix<float> mL = mixture<float, NF, NDIM>(Ll, e);
-    Mix<float> mR = mixture<float, NF, NDIM>(Rl, e);
-    int choice = 0;
-    if (a.fallback) {
-        if (!(face_state_ok<float, NF, NDIM>(Ll, mL) && face_state_ok<float, NF, NDIM>(Rl, mR))) {
-            const Mix<float> jL = mixture<float, NF, NDIM>(Lj, e);
-            const Mix<float> jR = mixture<float, NF, NDIM>(Rj, e);
-            if (face_state_ok<float, NF, NDIM>(Lj, jL) && face_state_ok<float, NF, NDIM>(Rj, jR)) {
-                choice = 1;
-                mL = jL;
-                mR = jR;
-            } else {
-                choice = 2;
-                mL = mixture<float, NF, NDIM>(cl, e);
-                mR = mixture<float, NF, NDIM>(cr, e);
-                count_fallback(a.fallback_count);
-            }
-        }
-    }
     float fl[NS], fr[NS];
 #pragma unroll
     for (int v = 0; v < NS; ++v) {
-        fl[v] = choice == 0 ? Ll[v] : (choice == 1 ? Lj[v] : cl[v]);
-        fr[v] = choice == 0 ? Rl[v] : (choice == 1 ? Rj[v] : cr[v]);
+        fl[v] = Ll[v];
+        fr[v] = Rl[v];
+    }
+    Mix<float> mL = mixture<float, NF, NDIM>(fl, e);
+    Mix<float> mR = mixture<float, NF, NDIM>(fr, e);
+    if (a.fallback) {
+        if (!(face_state_ok<float, NF, NDIM>(fl, mL) && face_state_ok<float, NF, NDIM>(fr, mR))) {
+            loadJ(fl, fr);
+            mL = mixture<float, NF, NDIM>(fl, e);
+            mR = mixture<float, NF, NDIM>(fr, e);
+            if (!(face_state_ok<float, NF, NDIM>(fl, mL) && face_state_ok<float, NF, NDIM>(fr, mR))) {
+#pragma unroll
+                for (int v = 0; v < NS; ++v) {
+                    fl[v] = cl[v];
+                    fr[v] = cr[v];
+                }
+                mL = mixture<float, NF, NDIM>(fl, e);
+                mR = mixture<float, NF, NDIM>(fr, e);
+                count_fallback(a.fallback_count);
+            }
+        }
     }
     hllc<float, NF, NDIM, DIR>(fl, fr, mL, mR, F, ut);
 }

@@ -44,9 +44,9 @@ __global__ void __launch_bounds__(128) sweep_kernel(const SweepArgs a) {
     const Real eps34 = sweep_epsw<Real, ORDER>(a);  // 3/4 eps (WENO5) or eps (WENO3)
     const EosR<Real> e = sweep_eos<Real>(a);
     const Real inv_dx = sweep_inv_dx<Real>(a, DIR);
-    LearnSmem<NS>* lsm = nullptr;
+    LearnRows* lsm = nullptr;
     if constexpr (LEARNED) {
-        __shared__ LearnSmem<NS> lbuf[4];
+        __shared__ LearnRows lbuf[4];
         lsm = &lbuf[threadIdx.x >> 5];
     }
     unsigned long long net_rows = 0;  // learned form: network rows of this warp
@@ -102,7 +102,16 @@ __global__ void __launch_bounds__(128) sweep_kernel(const SweepArgs a) {
         if (c >= s0) {
             Real F[NS], ut;
             if constexpr (LEARNED)
-                face_flux_learned<NF, NDIM, DIR>(a, e, eLprev, eR, eLprevJ, eRJ, cm1, vc, F, ut);
+                face_flux_learned<NF, NDIM, DIR>(
+                    a, e, eLprev, eR,
+                    [&](float* Lj, float* Rj) {
+#pragma unroll
+                        for (int v = 0; v < NS; ++v) {
+                            Lj[v] = eLprevJ[v];
+                            Rj[v] = eRJ[v];
+                        }
+                    },
+                    cm1, vc, F, ut);
             else
                 face_flux<Real, NF, NDIM, DIR>(a, e, eLprev, eR, cm1, vc, F, ut);
             if (c >= s0 + 1 && active)
@@ -181,10 +190,11 @@ __device__ __forceinline__ void sweep_x_stream_body(const SweepArgs& a) {
     // the Riemann solver: no FP64 edge sums and mixtures (256^3: see DESIGN)
     constexpr bool DFS = ROLL && ORDER == 5 && !NONUNIF && !SIX;
     __shared__ Real sh_eL[NS][ER];
-    __shared__ Real sh_eR[ROLL ? NS : 1][kStreamThreads];
+    __shared__ Real sh_eR[(ROLL || LEARNED) ? NS : 1][kStreamThreads];
     df(*dsh_eL)[ER] = reinterpret_cast<df(*)[ER]>(sh_eL);
     df(*dsh_eR)[kStreamThreads] = reinterpret_cast<df(*)[kStreamThreads]>(sh_eR);
     __shared__ Real sh_eLJ[NJ][ER];
+    __shared__ Real sh_eRJ[NJ][kStreamThreads];
     __shared__ Real sh_F[NQ + 1][ER];
     df(*dsh_F)[ER] = reinterpret_cast<df(*)[ER]>(sh_F);   // DFS: float-float fluxes
     const Real* __restrict__ w = static_cast<const Real*>(a.w);
@@ -202,9 +212,9 @@ __device__ __forceinline__ void sweep_x_stream_body(const SweepArgs& a) {
     const Real inv_dx = sweep_inv_dx<Real>(a, 0);
     [[maybe_unused]] const df inv_df = df_from_double((double)inv_dx);
     const int t = threadIdx.x;
-    LearnSmem<NS>* lsm = nullptr;
+    LearnRows* lsm = nullptr;
     if constexpr (LEARNED) {
-        __shared__ LearnSmem<NS> lbuf[kStreamThreads / 32];
+        __shared__ LearnRows lbuf[kStreamThreads / 32];
         lsm = &lbuf[t >> 5];
     }
     unsigned long long net_rows = 0;  // learned form: network rows of this warp
@@ -247,9 +257,11 @@ __device__ __forceinline__ void sweep_x_stream_body(const SweepArgs& a) {
                 for (int q = 0; q < NS; ++q) asm volatile("prefetch.global.L1 [%0];" ::"l"(nx + q * nc));
             }
         }
-        Real cell[NS], cm1[NS], eL[NS], eR[NS], eLJ[NS], eRJ[NS];
+        Real cell[NS], cm1[NS], eL[NS], eR[NS];
         if constexpr (LEARNED) {
-            // the five cells of this lane's stencil, re-read (L1) per variable
+            // one copy of the reconstruction looped over the variables (the
+            // network's code once), the next variable's stencil loaded while
+            // this one computes, edge values to shared memory
             int mk[5];
             bool fk[5];
 #pragma unroll
@@ -258,20 +270,29 @@ __device__ __forceinline__ void sweep_x_stream_body(const SweepArgs& a) {
                 mk[k] = live ? ghost_map(c + k - 2, n, bclo, bchi, &fk[k]) : 0;
             }
             const Real* wr = w + rowoff;
-            auto stencil = [&](int q, float (&dd)[4]) -> float {
-                float v5[5];
+            float vn[5];
 #pragma unroll
-                for (int k = 0; k < 5; ++k) {
-                    float x = live ? __ldg(wr + q * nc + mk[k]) : 0.f;
-                    if (q == IM && fk[k]) x = -x;
-                    v5[k] = x;
+            for (int k = 0; k < 5; ++k) vn[k] = live ? __ldg(wr + mk[k]) : 0.f;
+#pragma unroll 1
+            for (int q = 0; q < NS; ++q) {
+                float v[5];
+#pragma unroll
+                for (int k = 0; k < 5; ++k) v[k] = (q == IM && fk[k]) ? -vn[k] : vn[k];
+                if (q + 1 < NS) {
+#pragma unroll
+                    for (int k = 0; k < 5; ++k) vn[k] = live ? __ldg(wr + (q + 1) * nc + mk[k]) : 0.f;
                 }
-#pragma unroll
-                for (int k = 0; k < 4; ++k) dd[k] = v5[k + 1] - v5[k];
-                return v5[2];
-            };
-            net_rows += learned_cell_edges<NS>(stencil, eps34, a.tau, a.bound != 0, a.mlp_frag, *lsm, t & 31, eRJ, eLJ,
-                                                  eR, eL);
+                const float dq[4] = {v[1] - v[0], v[2] - v[1], v[3] - v[2], v[4] - v[3]};
+                float ejR, ejL, elR, elL;
+                net_rows += learned_var_edges(v[2], dq, eps34, a.tau, a.bound != 0, a.mlp_frag, *lsm, t & 31, ejR,
+                                              ejL, elR, elL);
+                if (live) {
+                    sh_eL[q][pos] = elL;
+                    sh_eLJ[q][pos] = ejL;
+                    sh_eR[q][t] = elR;
+                    sh_eRJ[q][t] = ejR;
+                }
+            }
 #pragma unroll
             for (int q = 0; q < NS; ++q) {
                 float x1 = live ? __ldg(wr + q * nc + mk[1]) : 0.f;
@@ -376,12 +397,9 @@ __device__ __forceinline__ void sweep_x_stream_body(const SweepArgs& a) {
         }
         // left-side values of this chunk (the last chunk's last slot stays at
         // the position before this chunk's first)
-        if (!ROLL && live) {
+        if (!ROLL && !LEARNED && live) {
 #pragma unroll
-            for (int q = 0; q < NS; ++q) {
-                sh_eL[q][pos] = eL[q];
-                if constexpr (LEARNED) sh_eLJ[q][pos] = eLJ[q];
-            }
+            for (int q = 0; q < NS; ++q) sh_eL[q][pos] = eL[q];
         }
         __syncthreads();
         Real F[NQ], ut = 0;
@@ -404,15 +422,21 @@ __device__ __forceinline__ void sweep_x_stream_body(const SweepArgs& a) {
             Real lft[NS];
 #pragma unroll
             for (int q = 0; q < NS; ++q) lft[q] = sh_eL[q][pl];
-            if constexpr (ROLL) {
+            if constexpr (ROLL || LEARNED) {
 #pragma unroll
                 for (int q = 0; q < NS; ++q) eR[q] = sh_eR[q][t];
             }
             if constexpr (LEARNED) {
-                Real lftJ[NS];
+                face_flux_learned<NF, NDIM, 0>(
+                    a, e, lft, eR,
+                    [&](float* Lj, float* Rj) {
 #pragma unroll
-                for (int q = 0; q < NS; ++q) lftJ[q] = sh_eLJ[q][pl];
-                face_flux_learned<NF, NDIM, 0>(a, e, lft, eR, lftJ, eRJ, cm1, cell, F, ut);
+                        for (int q = 0; q < NS; ++q) {
+                            Lj[q] = sh_eLJ[q][pl];
+                            Rj[q] = sh_eRJ[q][t];
+                        }
+                    },
+                    cm1, cell, F, ut);
             } else {
                 face_flux<Real, NF, NDIM, 0, SIX>(a, e, lft, eR, cm1, cell, F, ut);
             }
@@ -463,10 +487,18 @@ __global__ void __launch_bounds__(kStreamThreads, NF <= 2 ? 7 : 5) sweep_x_strea
     sweep_x_stream_body<float, NF, NDIM, false, ORDER, false, false>(a);
 }
 
-// The learned form's x sweep bounded to 4 CTAs per SM (128 registers, 32
-// bytes of spills; unbounded it took 168 and kept 12 warps per SM).
+// The learned form's sweeps bounded to 4 CTAs per SM (128 registers, at most
+// 12 bytes of spills; unbounded the x sweep took 168 and kept 12 warps per
+// SM).  At 5 CTAs (96 registers, ~300 bytes of spills in x) the 256^3 step
+// took 14.2 instead of 13.8 ms; y/z at 6 CTAs (80 registers), 15.2.
+#ifndef MFC_LEARN_X_CTAS
+#define MFC_LEARN_X_CTAS 4
+#endif
+#ifndef MFC_LEARN_YZ_CTAS
+#define MFC_LEARN_YZ_CTAS 4
+#endif
 template <int NF, int NDIM>
-__global__ void __launch_bounds__(kStreamThreads, 4) sweep_x_stream_learned_kernel(const SweepArgs a) {
+__global__ void __launch_bounds__(kStreamThreads, MFC_LEARN_X_CTAS) sweep_x_stream_learned_kernel(const SweepArgs a) {
     sweep_x_stream_body<float, NF, NDIM, true, 5, false, false>(a);
 }
 
@@ -519,12 +551,13 @@ __device__ __forceinline__ void sweep_yz_stream_body(const SweepArgs& a) {
     constexpr bool ROLL = sizeof(Real) == 8 && !LEARNED;
     __shared__ Real ring[RING][NS][32];
     __shared__ Real sh_eL[NS][ER][32];
-    __shared__ Real sh_eR[ROLL ? NS : 1][kRowsPerChunk][32];
+    __shared__ Real sh_eR[(ROLL || LEARNED) ? NS : 1][kRowsPerChunk][32];
     // DFS: edge values kept in float-float into the Riemann solver (x stream body)
     constexpr bool DFS = ROLL && ORDER == 5 && !NONUNIF && !SIX;
     df(*dsh_eL)[ER][32] = reinterpret_cast<df(*)[ER][32]>(sh_eL);
     df(*dsh_eR)[kRowsPerChunk][32] = reinterpret_cast<df(*)[kRowsPerChunk][32]>(sh_eR);
     __shared__ Real sh_eLJ[NJ][ER][32];
+    __shared__ Real sh_eRJ[NJ][kRowsPerChunk][32];
     __shared__ Real sh_F[NQ + 1][ER][32];
     df(*dsh_F)[ER][32] = reinterpret_cast<df(*)[ER][32]>(sh_F);   // DFS: float-float fluxes
     extern __shared__ __align__(16) unsigned char stage_smem[];   // a.stage operands
@@ -552,9 +585,9 @@ __device__ __forceinline__ void sweep_yz_stream_body(const SweepArgs& a) {
     [[maybe_unused]] const EosDf edf(e);   // DFS: the EOS constants as float-float
     const Real inv_dx = sweep_inv_dx<Real>(a, DIR);
     [[maybe_unused]] const df inv_df = df_from_double((double)inv_dx);
-    LearnSmem<NS>* lsm = nullptr;
+    LearnRows* lsm = nullptr;
     if constexpr (LEARNED) {
-        __shared__ LearnSmem<NS> lbuf[kRowsPerChunk];
+        __shared__ LearnRows lbuf[kRowsPerChunk];
         lsm = &lbuf[row];
     }
     unsigned long long net_rows = 0;  // learned form: network rows of this warp
@@ -606,23 +639,29 @@ __device__ __forceinline__ void sweep_yz_stream_body(const SweepArgs& a) {
             if constexpr (sizeof(Real) == 4 && !SIX)
                 prefetch_finish_operands<Real, NQ>(a, fidx, stage_mask(a) & ~staged);
         }
-        Real cell[NS], cm1[NS], eL[NS], eR[NS], eLJ[NS], eRJ[NS];
+        Real cell[NS], cm1[NS], eL[NS], eR[NS];
         if (live) {
             if constexpr (LEARNED) {
-                auto stencil = [&](int q, float (&dd)[4]) -> float {
-                    float v5[5];
-#pragma unroll
-                    for (int k = 0; k < 5; ++k) v5[k] = ring[slot(c - 2 + k)][q][lane];
-#pragma unroll
-                    for (int k = 0; k < 4; ++k) dd[k] = v5[k + 1] - v5[k];
-                    return v5[2];
-                };
-                net_rows += learned_cell_edges<NS>(stencil, eps34, a.tau, a.bound != 0, a.mlp_frag, *lsm, lane, eRJ,
-                                                   eLJ, eR, eL);
+                // one copy of the reconstruction looped over the variables
+                // (stencils from the ring, edge values to shared memory)
+                const int s0r = slot(c - 2), s1r = slot(c - 1), s2r = slot(c), s3r = slot(c + 1), s4r = slot(c + 2);
+#pragma unroll 1
+                for (int q = 0; q < NS; ++q) {
+                    const float v0 = ring[s0r][q][lane], v1 = ring[s1r][q][lane], v2 = ring[s2r][q][lane];
+                    const float v3 = ring[s3r][q][lane], v4 = ring[s4r][q][lane];
+                    const float dq[4] = {v1 - v0, v2 - v1, v3 - v2, v4 - v3};
+                    float ejR, ejL, elR, elL;
+                    net_rows += learned_var_edges(v2, dq, eps34, a.tau, a.bound != 0, a.mlp_frag, *lsm, lane, ejR,
+                                                  ejL, elR, elL);
+                    sh_eL[q][eslot(c)][lane] = elL;
+                    sh_eLJ[q][eslot(c)][lane] = ejL;
+                    sh_eR[q][row][lane] = elR;
+                    sh_eRJ[q][row][lane] = ejR;
+                }
 #pragma unroll
                 for (int q = 0; q < NS; ++q) {
-                    cell[q] = ring[slot(c)][q][lane];
-                    cm1[q] = ring[slot(c - 1)][q][lane];
+                    cell[q] = ring[s2r][q][lane];
+                    cm1[q] = ring[s1r][q][lane];
                 }
             } else if constexpr (ROLL) {
                 const int s0r = slot(c - 2), s1r = slot(c - 1), s2r = slot(c), s3r = slot(c + 1), s4r = slot(c + 2);
@@ -677,12 +716,9 @@ __device__ __forceinline__ void sweep_yz_stream_body(const SweepArgs& a) {
                     for (int q = 0; q < NS; ++q) weno_edges<ORDER>(cell[q], Dv[q], eps34, eR[q], eL[q]);
                 }
             }
-            if constexpr (!ROLL) {
+            if constexpr (!ROLL && !LEARNED) {
 #pragma unroll
-                for (int q = 0; q < NS; ++q) {
-                    sh_eL[q][eslot(c)][lane] = eL[q];
-                    if constexpr (LEARNED) sh_eLJ[q][eslot(c)][lane] = eLJ[q];
-                }
+                for (int q = 0; q < NS; ++q) sh_eL[q][eslot(c)][lane] = eL[q];
             }
         }
         __syncthreads();
@@ -711,15 +747,21 @@ __device__ __forceinline__ void sweep_yz_stream_body(const SweepArgs& a) {
             Real lft[NS];
 #pragma unroll
             for (int q = 0; q < NS; ++q) lft[q] = sh_eL[q][eslot(c - 1)][lane];
-            if constexpr (ROLL) {
+            if constexpr (ROLL || LEARNED) {
 #pragma unroll
                 for (int q = 0; q < NS; ++q) eR[q] = sh_eR[q][row][lane];
             }
             if constexpr (LEARNED) {
-                Real lftJ[NS];
+                face_flux_learned<NF, NDIM, DIR>(
+                    a, e, lft, eR,
+                    [&](float* Lj, float* Rj) {
 #pragma unroll
-                for (int q = 0; q < NS; ++q) lftJ[q] = sh_eLJ[q][eslot(c - 1)][lane];
-                face_flux_learned<NF, NDIM, DIR>(a, e, lft, eR, lftJ, eRJ, cm1, cell, F, ut);
+                        for (int q = 0; q < NS; ++q) {
+                            Lj[q] = sh_eLJ[q][eslot(c - 1)][lane];
+                            Rj[q] = sh_eRJ[q][row][lane];
+                        }
+                    },
+                    cm1, cell, F, ut);
             } else {
                 face_flux<Real, NF, NDIM, DIR, SIX>(a, e, lft, eR, cm1, cell, F, ut);
             }
@@ -807,7 +849,8 @@ __global__ void __launch_bounds__(32 * kRowsPerChunk, 3) sweep_yz_stream_f64b3_k
 }
 
 template <int NF, int NDIM, int DIR>
-__global__ void __launch_bounds__(32 * kRowsPerChunk, NF <= 2 ? 4 : 3) sweep_yz_stream_learned_kernel(const SweepArgs a) {
+__global__ void __launch_bounds__(32 * kRowsPerChunk, NF <= 2 ? MFC_LEARN_YZ_CTAS : 3)
+    sweep_yz_stream_learned_kernel(const SweepArgs a) {
     sweep_yz_stream_body<float, NF, NDIM, DIR, true, 5, false, false, true>(a);
 }
 
