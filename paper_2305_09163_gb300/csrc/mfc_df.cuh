@@ -114,6 +114,91 @@ __device__ __forceinline__ df df_sqrt(df x) {
     return df_fast_two_sum(s, __fmul_rn(r.hi, __fmul_rn(0.5f, __frcp_rn(s))));
 }
 
+// ---------------------------------------------------------------------------
+// Two float-float values side by side: the same operation sequence as the
+// scalar functions above, applied to both lanes of packed FP32 instructions
+// (add/mul/fma .f32x2 of the sm_100 family: one issue slot per pair).  A
+// difference a - b is formed as one rounding of a + (-1) b, the same value.
+// ---------------------------------------------------------------------------
+struct df2 {
+    float2 hi, lo;
+};
+
+__device__ __forceinline__ float2 f2(float x) { return make_float2(x, x); }
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __ffma2_rn(b, make_float2(-1.f, -1.f), a); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 swap2(float2 a) { return make_float2(a.y, a.x); }
+
+__device__ __forceinline__ df2 df2_make(df x, df y) { return {make_float2(x.hi, y.hi), make_float2(x.lo, y.lo)}; }
+__device__ __forceinline__ df df2_x(df2 a) { return {a.hi.x, a.lo.x}; }
+__device__ __forceinline__ df df2_y(df2 a) { return {a.hi.y, a.lo.y}; }
+__device__ __forceinline__ df2 df2_swap(df2 a) { return {swap2(a.hi), swap2(a.lo)}; }
+
+__device__ __forceinline__ df2 df2_two_sum(float2 a, float2 b) {
+    const float2 s = add2(a, b);
+    const float2 bb = sub2(s, a);
+    return {s, add2(sub2(a, sub2(s, bb)), sub2(b, bb))};
+}
+
+__device__ __forceinline__ df2 df2_fast_two_sum(float2 a, float2 b) {
+    const float2 s = add2(a, b);
+    return {s, sub2(b, sub2(s, a))};
+}
+
+// the product's error as fma(a, b, -p)
+__device__ __forceinline__ df2 df2_two_prod(float2 a, float2 b) {
+    const float2 p = mul2(a, b);
+    return {p, fma2(a, b, make_float2(-p.x, -p.y))};
+}
+
+__device__ __forceinline__ df2 df2_add(df2 x, df2 y) {
+    df2 s = df2_two_sum(x.hi, y.hi);
+    const df2 t = df2_two_sum(x.lo, y.lo);
+    s = df2_fast_two_sum(s.hi, add2(s.lo, t.hi));
+    return df2_fast_two_sum(s.hi, add2(s.lo, t.lo));
+}
+
+__device__ __forceinline__ df2 df2_add_fast(df2 x, df2 y) {
+    const df2 s = df2_two_sum(x.hi, y.hi);
+    return df2_fast_two_sum(s.hi, add2(add2(s.lo, x.lo), y.lo));
+}
+
+__device__ __forceinline__ df2 df2_neg(df2 x) {
+    return {make_float2(-x.hi.x, -x.hi.y), make_float2(-x.lo.x, -x.lo.y)};
+}
+
+__device__ __forceinline__ df2 df2_mul_pow2(df2 x, float2 f) { return {mul2(x.hi, f), mul2(x.lo, f)}; }
+
+__device__ __forceinline__ df2 df2_mul(df2 x, df2 y) {
+    const df2 p = df2_two_prod(x.hi, y.hi);
+    float2 e = fma2(x.hi, y.lo, p.lo);
+    e = fma2(x.lo, y.hi, e);
+    return df2_fast_two_sum(p.hi, e);
+}
+
+__device__ __forceinline__ df2 df2_mul_f(df2 x, float2 f) {
+    const df2 p = df2_two_prod(x.hi, f);
+    return df2_fast_two_sum(p.hi, fma2(x.lo, f, p.lo));
+}
+
+__device__ __forceinline__ df2 df2_div_f(float2 a, df2 b) {
+    const float2 y = make_float2(rcp_approx(b.hi.x), rcp_approx(b.hi.y));
+    const float2 q1 = mul2(a, y);
+    const df2 p = df2_two_prod(q1, b.hi);
+    float2 r = sub2(sub2(a, p.hi), p.lo);
+    r = fma2(make_float2(-q1.x, -q1.y), b.lo, r);
+    return df2_fast_two_sum(q1, mul2(r, y));
+}
+
+__device__ __forceinline__ df2 df2_div(df2 a, df2 b) {
+    const float2 y = make_float2(rcp_approx(b.hi.x), rcp_approx(b.hi.y));
+    const float2 q1 = mul2(a.hi, y);
+    const df2 r = df2_add(a, df2_neg(df2_mul_f(b, q1)));
+    return df2_fast_two_sum(q1, mul2(r.hi, y));
+}
+
 // x < y (parts normalised: |lo| <= ulp(hi)/2).
 __device__ __forceinline__ bool df_lt(df x, df y) { return x.hi < y.hi || (x.hi == y.hi && x.lo < y.lo); }
 __device__ __forceinline__ df df_min(df x, df y) { return df_lt(y, x) ? y : x; }

@@ -33,36 +33,44 @@ namespace mfc {
 //   eR - v_c = (g2^2 (2 D3 - 5 D2) - 6 g1^2 (2 D1 + D2) + 3 g0^2 (D0 - 4 D1))
 //              / (6 (g2^2 + 6 g1^2 + 3 g0^2)).
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ void weno5_increments_df(const df (&D)[4], double eps34, df& iR, df& iL) {
-    // sums use the fast float-float addition: its error, ~2^-44 of the
-    // operands, is relative to the stencil's differences, far inside the
-    // path's parity tolerance; scalings by 2 and 4 are exact
-    const df d0 = D[0], d1 = D[1], d2 = D[2], d3 = D[3];
-    const df S1 = df_mul(d1, d1), S2 = df_mul(d2, d2);
-    const df b0 = df_add_fast(df_add_fast(df_mul(d0, d0), df_mul_f(df_mul(d1, d0), -2.75f)), df_mul_f(S1, 2.5f));
-    const df b1 = df_add_fast(df_add_fast(S1, S2), df_mul_f(df_mul(d1, d2), -1.25f));
-    const df b2 = df_add_fast(df_add_fast(df_mul(d3, d3), df_mul_f(df_mul(d2, d3), -2.75f)), df_mul_f(S2, 2.5f));
+// Both edges run in the two lanes of packed FP32 instructions (df2): lane x
+// evaluates the c+1/2 formula on the stencil, lane y the same formula on the
+// mirrored stencil (-D3, -D2, -D1, -D0), which is the edge at c-1/2 (b0 and b2
+// trade places, the candidates above become the eR ones).  b1, its weight and
+// m are common to both edges and are formed once.  Sums use the fast
+// float-float addition: its error, ~2^-44 of the operands, is relative to the
+// stencil's differences, far inside the path's parity tolerance; scalings by
+// powers of two are exact.  (256^3 FP64 step: 39.0 -> 35.9 ms against the same
+// arithmetic in scalar FP32 instructions.)
+__device__ __forceinline__ df2 weno5_increments_pair(const df (&D)[4], double eps34) {
+    const df2 X0 = df2_make(D[0], df_neg(D[3])), X1 = df2_make(D[1], df_neg(D[2]));
+    const df2 X2 = df2_swap(df2_neg(X1)), X3 = df2_swap(df2_neg(X0));   // (D2, -D1), (D3, -D0)
+    const df2 SX1 = df2_mul(X1, X1);                                     // (D1^2, D2^2)
+    const df2 B = df2_add_fast(df2_add_fast(df2_mul(X0, X0), df2_mul_f(df2_mul(X1, X0), f2(-2.75f))),
+                               df2_mul_f(SX1, f2(2.5f)));                // (b0, b2)
+    const df b1 = df_add_fast(df_add_fast(df2_x(SX1), df2_y(SX1)), df_mul_f(df_mul(D[1], D[2]), -1.25f));
     const df e = df_from_double(eps34);
-    const df t0 = df_add_fast(e, b0), t1 = df_add_fast(e, b1), t2 = df_add_fast(e, b2);
-    const float m = fminf(t0.hi, fminf(t1.hi, t2.hi));
-    const df g0 = df_div_f(m, t0), g1 = df_div_f(m, t1), g2 = df_div_f(m, t2);
-    const df q0 = df_mul(g0, g0), q1 = df_mul_f(df_mul(g1, g1), 6.f), q2 = df_mul(g2, g2);
-    // edge at c+1/2: weights q0, q1, 3 q2
-    const df wL2 = df_mul_f(q2, 3.f);
-    const df P0 = df_add_fast(df_mul_f(d1, 5.f), df_mul_pow2(d0, -2.f));
-    const df P1 = df_add_fast(d1, df_mul_pow2(d2, 2.f));
-    const df P2 = df_add_fast(df_mul_pow2(d2, 4.f), df_neg(d3));
-    const df numL = df_add_fast(df_add_fast(df_mul(q0, P0), df_mul(q1, P1)), df_mul(wL2, P2));
-    const df denL = df_mul_f(df_add_fast(df_add_fast(q0, q1), wL2), 6.f);
-    // edge at c-1/2: weights q2, q1, 3 q0
-    const df wR2 = df_mul_f(q0, 3.f);
-    const df M0 = df_add_fast(df_mul_pow2(d3, 2.f), df_mul_f(d2, -5.f));
-    const df M1 = df_neg(df_add_fast(df_mul_pow2(d1, 2.f), d2));
-    const df M2 = df_add_fast(d0, df_mul_pow2(d1, -4.f));
-    const df numR = df_add_fast(df_add_fast(df_mul(q2, M0), df_mul(q1, M1)), df_mul(wR2, M2));
-    const df denR = df_mul_f(df_add_fast(df_add_fast(q2, q1), wR2), 6.f);
-    iL = df_div(numL, denL);
-    iR = df_div(numR, denR);
+    const df2 T = df2_add_fast(df2_make(e, e), B);                       // (t0, t2)
+    const df t1 = df_add_fast(e, b1);
+    const float m = fminf(T.hi.x, fminf(t1.hi, T.hi.y));
+    const df2 G = df2_div_f(f2(m), T);                                   // (g0, g2)
+    const df g1 = df_div_f(m, t1);
+    const df2 Q = df2_mul(G, G);                                         // (q0, q2)
+    const df q1 = df_mul_f(df_mul(g1, g1), 6.f);
+    const df2 Q1 = df2_make(q1, q1);
+    const df2 W2 = df2_mul_f(df2_swap(Q), f2(3.f));                      // (3 q2, 3 q0)
+    const df2 P0 = df2_add_fast(df2_mul_f(X1, f2(5.f)), df2_mul_pow2(X0, f2(-2.f)));
+    const df2 P1 = df2_add_fast(X1, df2_mul_pow2(X2, f2(2.f)));
+    const df2 P2 = df2_add_fast(df2_mul_pow2(X2, f2(4.f)), df2_neg(X3));
+    const df2 num = df2_add_fast(df2_add_fast(df2_mul(Q, P0), df2_mul(Q1, P1)), df2_mul(W2, P2));
+    const df2 den = df2_mul_f(df2_add_fast(df2_add_fast(Q, Q1), W2), f2(6.f));
+    return df2_div(num, den);   // (increment at c+1/2, increment at c-1/2)
+}
+
+__device__ __forceinline__ void weno5_increments_df(const df (&D)[4], double eps34, df& iR, df& iL) {
+    const df2 I = weno5_increments_pair(D, eps34);
+    iL = df2_x(I);
+    iR = df2_y(I);
 }
 
 __device__ __forceinline__ void weno5_increments(const double D[4], double eps34, df& iR, df& iL) {
@@ -84,11 +92,11 @@ __device__ __forceinline__ void weno5_edges(double vc, const double D[4], double
 // face state then carries ~2^-48 of its magnitude, as an FP64 edge split for
 // the float-float Riemann solver does), and no FP64 operation.
 __device__ __forceinline__ void weno5_edges_df(double vc, const double D[4], double eps34, df& eR, df& eL) {
-    df iR, iL;
-    weno5_increments(D, eps34, iR, iL);
+    const df d[4] = {df_from_double(D[0]), df_from_double(D[1]), df_from_double(D[2]), df_from_double(D[3])};
     const df c = df_from_double(vc);
-    eL = df_add(c, iL);
-    eR = df_add(c, iR);
+    const df2 E = df2_add(df2_make(c, c), weno5_increments_pair(d, eps34));
+    eL = df2_x(E);
+    eR = df2_y(E);
 }
 
 // FP32 variant for the mixed path.  The weights are normalised by the smallest

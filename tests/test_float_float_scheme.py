@@ -115,29 +115,40 @@ def to_double(x):
 
 
 def weno5_float_float(vc, D, eps34):
-    """Edge values (eR at c-1/2, eL at c+1/2) as the FP64 path forms them."""
-    d0, d1, d2, d3 = (split(D[:, j]) for j in range(4))
-    S1, S2 = mul(d1, d1), mul(d2, d2)
-    b0 = add_fast(add_fast(mul(d0, d0), mul_f(mul(d1, d0), -2.75)), mul_f(S1, 2.5))
-    b1 = add_fast(add_fast(S1, S2), mul_f(mul(d1, d2), -1.25))
-    b2 = add_fast(add_fast(mul(d3, d3), mul_f(mul(d2, d3), -2.75)), mul_f(S2, 2.5))
+    """Edge values (eR at c-1/2, eL at c+1/2) as the FP64 path forms them: the
+    c+1/2 formula on the stencil and, for eR, on the mirrored stencil
+    (-D3, -D2, -D1, -D0), with b1, its weight and the normaliser m shared."""
+    d = [split(D[:, j]) for j in range(4)]
     e = split(np.full(len(vc), eps34))
-    t0, t1, t2 = add_fast(e, b0), add_fast(e, b1), add_fast(e, b2)
-    m = np.minimum(np.minimum(t0[0], t1[0]), t2[0])
-    g0, g1, g2 = div_f(m, t0), div_f(m, t1), div_f(m, t2)
-    q0, q1, q2 = mul(g0, g0), mul_f(mul(g1, g1), 6), mul(g2, g2)
-    wL2, wR2 = mul_f(q2, 3), mul_f(q0, 3)
-    P0 = add_fast(mul_f(d1, 5), mul_pow2(d0, -2))
-    P1 = add_fast(d1, mul_pow2(d2, 2))
-    P2 = add_fast(mul_pow2(d2, 4), neg(d3))
-    numL = add_fast(add_fast(mul(q0, P0), mul(q1, P1)), mul(wL2, P2))
-    denL = mul_f(add_fast(add_fast(q0, q1), wL2), 6)
-    M0 = add_fast(mul_pow2(d3, 2), mul_f(d2, -5))
-    M1 = neg(add_fast(mul_pow2(d1, 2), d2))
-    M2 = add_fast(d0, mul_pow2(d1, -4))
-    numR = add_fast(add_fast(mul(q2, M0), mul(q1, M1)), mul(wR2, M2))
-    denR = mul_f(add_fast(add_fast(q2, q1), wR2), 6)
-    return vc + to_double(div(numR, denR)), vc + to_double(div(numL, denL))
+    S1, S2 = mul(d[1], d[1]), mul(d[2], d[2])
+    b1 = add_fast(add_fast(S1, S2), mul_f(mul(d[1], d[2]), -1.25))
+    t1 = add_fast(e, b1)
+
+    def side(x0, x1, x2, x3):
+        b0 = add_fast(add_fast(mul(x0, x0), mul_f(mul(x1, x0), -2.75)), mul_f(mul(x1, x1), 2.5))
+        return x0, x1, x2, x3, add_fast(e, b0)
+
+    L = side(d[0], d[1], d[2], d[3])
+    R = side(neg(d[3]), neg(d[2]), neg(d[1]), neg(d[0]))
+    m = np.minimum(np.minimum(L[4][0], t1[0]), R[4][0])
+    g1 = div_f(m, t1)
+    q1 = mul_f(mul(g1, g1), 6)
+    gL, gR = div_f(m, L[4]), div_f(m, R[4])
+    qL, qR = mul(gL, gL), mul(gR, gR)
+
+    def increment(x, q0, q2):
+        x0, x1, x2, x3 = x[:4]
+        w2 = mul_f(q2, 3)
+        P0 = add_fast(mul_f(x1, 5), mul_pow2(x0, -2))
+        P1 = add_fast(x1, mul_pow2(x2, 2))
+        P2 = add_fast(mul_pow2(x2, 4), neg(x3))
+        num = add_fast(add_fast(mul(q0, P0), mul(q1, P1)), mul(w2, P2))
+        den = mul_f(add_fast(add_fast(q0, q1), w2), 6)
+        return div(num, den)
+
+    iL = increment(L, qL, qR)
+    iR = increment(R, qR, qL)
+    return vc + to_double(iR), vc + to_double(iL)
 
 
 def test_error_free_transformations_are_exact():
