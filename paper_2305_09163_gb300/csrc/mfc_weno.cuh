@@ -101,26 +101,33 @@ __device__ __forceinline__ void weno5_edges_df(double vc, const double D[4], dou
 
 // FP32 variant for the mixed path.  The weights are normalised by the smallest
 // eps+beta, so no intermediate overflows FP32 (beta of a 1e9 Pa jump is ~1e19).
+// FP32: both edges in the two lanes of packed FP32 instructions, lane y
+// evaluating the c+1/2 formula on the mirrored stencil (-D3, -D2, -D1, -D0)
+// (as weno5_increments_pair); b1, its weight and m are formed once (256^3
+// mixed step 6.29 -> 6.06 ms against scalar FP32 instructions).
 __device__ __forceinline__ void weno5_edges(float vc, const float D[4], float eps34,
                                             float& eR, float& eL) {
-    const float S0 = D[0] * D[0], S1 = D[1] * D[1], S2 = D[2] * D[2], S3 = D[3] * D[3];
-    const float b0 = fmaf(2.5f, S1, fmaf(-2.75f, D[1] * D[0], S0));
-    const float b1 = fmaf(-1.25f, D[1] * D[2], S1 + S2);
-    const float b2 = fmaf(2.5f, S2, fmaf(-2.75f, D[2] * D[3], S3));
-    const float t0 = eps34 + b0, t1 = eps34 + b1, t2 = eps34 + b2;
-    const float m = fminf(t0, fminf(t1, t2));
-    float g0 = __fdividef(m, t0), g1 = __fdividef(m, t1), g2 = __fdividef(m, t2);
-    g0 *= g0; g1 *= g1; g2 *= g2;
-    const float p0 = fmaf(5.f / 6.f, D[1], (-1.f / 3.f) * D[0]);
-    const float p1 = fmaf(1.f / 6.f, D[1], (1.f / 3.f) * D[2]);
-    const float p2 = fmaf(2.f / 3.f, D[2], (-1.f / 6.f) * D[3]);
-    const float m0 = fmaf(-5.f / 6.f, D[2], (1.f / 3.f) * D[3]);
-    const float m1 = fmaf(-1.f / 6.f, D[2], (-1.f / 3.f) * D[1]);
-    const float m2 = fmaf(-2.f / 3.f, D[1], (1.f / 6.f) * D[0]);
-    const float wl0 = 0.1f * g0, wl1 = 0.6f * g1, wl2 = 0.3f * g2;
-    const float wr0 = 0.1f * g2, wr2 = 0.3f * g0;
-    eL = vc + __fdividef(fmaf(wl0, p0, fmaf(wl1, p1, wl2 * p2)), wl0 + wl1 + wl2);
-    eR = vc + __fdividef(fmaf(wr0, m0, fmaf(wl1, m1, wr2 * m2)), wr0 + wl1 + wr2);
+    const float2 X0 = make_float2(D[0], -D[3]), X1 = make_float2(D[1], -D[2]);
+    const float2 X2 = make_float2(D[2], -D[1]), X3 = make_float2(D[3], -D[0]);
+    const float2 S = mul2(X1, X1);                                                     // (D1^2, D2^2)
+    const float2 B = fma2(f2(2.5f), S, fma2(f2(-2.75f), mul2(X1, X0), mul2(X0, X0)));  // (b0, b2)
+    const float b1 = fmaf(-1.25f, D[1] * D[2], S.x + S.y);
+    const float2 T = add2(f2(eps34), B);
+    const float t1 = eps34 + b1;
+    const float m = fminf(T.x, fminf(t1, T.y));
+    float2 G = make_float2(__fdividef(m, T.x), __fdividef(m, T.y));
+    G = mul2(G, G);
+    float g1 = __fdividef(m, t1);
+    g1 *= g1;
+    const float2 P0 = fma2(f2(5.f / 6.f), X1, mul2(f2(-1.f / 3.f), X0));
+    const float2 P1 = fma2(f2(1.f / 6.f), X1, mul2(f2(1.f / 3.f), X2));
+    const float2 P2 = fma2(f2(2.f / 3.f), X2, mul2(f2(-1.f / 6.f), X3));
+    const float2 W0 = mul2(f2(0.1f), G), W1 = f2(0.6f * g1), W2 = mul2(f2(0.3f), swap2(G));
+    const float2 num = fma2(W0, P0, fma2(W1, P1, mul2(W2, P2)));
+    const float2 den = add2(add2(W0, W1), W2);
+    const float2 E = add2(f2(vc), make_float2(__fdividef(num.x, den.x), __fdividef(num.y, den.y)));
+    eL = E.x;
+    eR = E.y;
 }
 
 // ---------------------------------------------------------------------------
