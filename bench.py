@@ -86,13 +86,13 @@ SCHEDULERS = 152 * 4
 # Warp instructions per cell of the FP64 WENO5 sweeps (x, y, z; 3D, two
 # fluids, smsp__inst_executed.sum / cells of one ncu capture).  Re-measured
 # whenever the FP64 sweeps change: NCU_FP64_SWEEPS says which capture.
-FP64_SWEEP_WARP_INST_PER_CELL = (230.3, 231.6, 243.6)
+FP64_SWEEP_WARP_INST_PER_CELL = (173.4, 176.9, 187.1)
 # From the same capture: FP64-pipe and FP32 (fma) pipe activity of the sweeps
 # (mean over x, y, z) and DRAM bytes per cell per launch (the z sweep of an RK
 # stage also writes the next stage's primitives).
-FP64_SWEEP_PIPE_FP64 = 0.359
-FP64_SWEEP_PIPE_FMA = 0.526
-FP64_SWEEP_DRAM_BYTES_PER_CELL = (103.8 + 159.0 + 334.8) / 3.0
+FP64_SWEEP_PIPE_FP64 = 0.404
+FP64_SWEEP_PIPE_FMA = 0.588
+FP64_SWEEP_DRAM_BYTES_PER_CELL = (101.7 + 158.1 + 334.9) / 3.0
 NCU_FP64_SWEEPS = "profiles/sweep_fp64_shock_bubble_160.md"
 # Nominal FP32 peak: 152 SMs x 128 FMA/clk x 2 FLOP x 2.07 GHz
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
@@ -574,13 +574,15 @@ def _accuracy_learned_2x(m, torch, mlp, training, n=192, t_end=1.0e-4, taus=(10.
 
 def _sweep_roofline_fp64(r, cells, ns, variant, nf, clocks):
     """Roofline of the FP64 sweeps.  Their work runs mostly on the FP32 pipes
-    (the WENO weights and HLLC in float-float), and neither the FP64 pipe nor
-    DRAM is saturated: the binding resource is issue slots (latency-bound
-    dependency chains).  frac = warp instructions issued per second (the
-    stored per-cell count x cells x launches / the library's own launch times)
-    over 152 SMs x 4 schedulers x the SM clock sampled during the run; the
-    FP64-accurate algorithmic FLOP rate (oracle-counted work) is reported
-    beside it."""
+    (the WENO weights and HLLC in float-float, the weights in packed FP32x2
+    instructions: one issue slot, two FMA-pipe cycles each), and neither the
+    FP64 pipe nor DRAM is saturated: the binding resources are issue slots and
+    the FMA pipe, with latency-bound dependency chains at 16 warps per SM.
+    frac = warp instructions issued per second (the stored per-cell count x
+    cells x launches / the library's own launch times) over 152 SMs x 4
+    schedulers x the SM clock sampled during the run; the FMA- and FP64-pipe
+    activity of the same capture and the FP64-accurate algorithmic FLOP rate
+    (oracle-counted work) are reported beside it."""
     sweep_s = r["sweep_ms"] * 1e-3
     launches = r["sweep_launches"]
     stages = launches / 3.0
@@ -589,7 +591,7 @@ def _sweep_roofline_fp64(r, cells, ns, variant, nf, clocks):
     inst = sum(FP64_SWEEP_WARP_INST_PER_CELL) / 3.0 * cells * launches
     achieved = inst / sweep_s / 1e9
     peak = SCHEDULERS * mhz * 1e6 / 1e9
-    return {"bound": "alu", "resource": "issue slots", "kernel": "sweep (x, y, z)", "achieved": achieved,
+    return {"bound": "alu", "resource": "issue slots (and FMA pipe)", "kernel": "sweep (x, y, z)", "achieved": achieved,
             "peak": peak, "unit": "Gwarp-inst/s", "frac": achieved / peak, "issue_frac": achieved / peak,
             "peak_note": "152 SMs x 4 schedulers x 1 warp instruction per clock x the sampled SM clock (%.0f MHz)"
                          % mhz,
