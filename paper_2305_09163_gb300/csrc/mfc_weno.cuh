@@ -144,17 +144,20 @@ __device__ __forceinline__ void weno5_edges(float vc, const float D[4], float ep
 // c+1/2, g1^2 and 2 g0^2 at c-1/2.
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ void weno3_edges(double vc, double a, double b, double eps, double& eR, double& eL) {
+    // lane x: the c+1/2 edge of the differences (a, b); lane y: the same formula
+    // on the mirrored differences (-b, -a), which is the c-1/2 edge
     const df A = df_from_double(a), Bd = df_from_double(b), E = df_from_double(eps);
-    const df t0 = df_add_fast(E, df_mul(A, A)), t1 = df_add_fast(E, df_mul(Bd, Bd));
-    const float m = fminf(t0.hi, t1.hi);
-    const df g0 = df_div_f(m, t0), g1 = df_div_f(m, t1);
-    const df s0 = df_mul(g0, g0), s1 = df_mul(g1, g1);
-    const df s0x2 = df_mul_pow2(s0, 2.f), s1x2 = df_mul_pow2(s1, 2.f);
-    const df numL = df_add_fast(df_mul(s0, A), df_mul(s1x2, Bd));
-    const df numR = df_add_fast(df_mul(s1, Bd), df_mul(s0x2, A));
-    const df denL = df_mul_pow2(df_add_fast(s0, s1x2), 2.f), denR = df_mul_pow2(df_add_fast(s1, s0x2), 2.f);
-    eL = vc + df_to_double(df_div(numL, denL));
-    eR = vc - df_to_double(df_div(numR, denR));
+    const df2 X = df2_make(A, df_neg(Bd)), Y = df2_make(Bd, df_neg(A));
+    const df2 T = df2_add_fast(df2_make(E, E), df2_mul(df2_make(A, Bd), df2_make(A, Bd)));   // (t0, t1)
+    const float m = fminf(T.hi.x, T.hi.y);
+    const df2 G = df2_div_f(f2(m), T);
+    const df2 S = df2_mul(G, G);                                     // (s0, s1)
+    const df2 S2 = df2_mul_pow2(df2_swap(S), f2(2.f));               // (2 s1, 2 s0)
+    const df2 num = df2_add_fast(df2_mul(S, X), df2_mul(S2, Y));
+    const df2 den = df2_mul_pow2(df2_add_fast(S, S2), f2(2.f));
+    const df2 I = df2_div(num, den);
+    eL = vc + df_to_double(df2_x(I));
+    eR = vc + df_to_double(df2_y(I));
 }
 
 // FP32: t^2 can overflow FP32 (a pressure jump of 1e9 Pa gives t ~ 1e18), so
