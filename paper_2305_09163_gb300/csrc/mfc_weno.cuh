@@ -201,35 +201,38 @@ __device__ __forceinline__ df grid_df(const Col& row, int k) {
 template <class Col>
 __device__ __forceinline__ void weno5_edges_nu(double vc, const double D[4], double eps, const Col& row,
                                                double& eR, double& eL) {
+    // the two edges side by side in packed FP32 instructions: lane x the c+1/2
+    // edge (coefficients 0-5, 12-14), lane y the c-1/2 edge (6-11, 15-17); the
+    // smoothness indicators b0 and b2 side by side, b1 alone
     const df d0 = df_from_double(D[0]), d1 = df_from_double(D[1]);
     const df d2 = df_from_double(D[2]), d3 = df_from_double(D[3]);
-    const df S0 = df_mul(d0, d0), S1 = df_mul(d1, d1), S2 = df_mul(d2, d2), S3 = df_mul(d3, d3);
-    const df X01 = df_mul(d0, d1), X12 = df_mul(d1, d2), X23 = df_mul(d2, d3);
-    const df b0 = df_add_fast(df_add_fast(df_mul(grid_df(row, 18), S0), df_mul(grid_df(row, 19), X01)),
-                              df_mul(grid_df(row, 20), S1));
-    const df b1 = df_add_fast(df_add_fast(df_mul(grid_df(row, 21), S1), df_mul(grid_df(row, 22), X12)),
-                              df_mul(grid_df(row, 23), S2));
-    const df b2 = df_add_fast(df_add_fast(df_mul(grid_df(row, 24), S2), df_mul(grid_df(row, 25), X23)),
-                              df_mul(grid_df(row, 26), S3));
+    auto C = [&](int kx, int ky) { return df2_make(grid_df(row, kx), grid_df(row, ky)); };
+    const df2 Dlo = df2_make(d0, d2), Dhi = df2_make(d1, d3);
+    const df2 Slo = df2_mul(Dlo, Dlo), Shi = df2_mul(Dhi, Dhi);   // (S0, S2), (S1, S3)
+    const df2 X = df2_mul(Dlo, Dhi);                               // (D0 D1, D2 D3)
+    const df2 B = df2_add_fast(df2_add_fast(df2_mul(C(18, 24), Slo), df2_mul(C(19, 25), X)),
+                               df2_mul(C(20, 26), Shi));           // (b0, b2)
+    const df b1 = df_add_fast(df_add_fast(df_mul(grid_df(row, 21), df2_x(Shi)), df_mul(grid_df(row, 22), df_mul(d1, d2))),
+                              df_mul(grid_df(row, 23), df2_y(Slo)));
     const df e = df_from_double(eps);
-    const df t0 = df_add_fast(e, b0), t1 = df_add_fast(e, b1), t2 = df_add_fast(e, b2);
-    const float m = fminf(t0.hi, fminf(t1.hi, t2.hi));
-    const df g0 = df_div_f(m, t0), g1 = df_div_f(m, t1), g2 = df_div_f(m, t2);
-    const df q0 = df_mul(g0, g0), q1 = df_mul(g1, g1), q2 = df_mul(g2, g2);
-    const df P0 = df_add_fast(df_mul(grid_df(row, 0), d0), df_mul(grid_df(row, 1), d1));
-    const df P1 = df_add_fast(df_mul(grid_df(row, 2), d1), df_mul(grid_df(row, 3), d2));
-    const df P2 = df_add_fast(df_mul(grid_df(row, 4), d2), df_mul(grid_df(row, 5), d3));
-    const df wL0 = df_mul(grid_df(row, 12), q0), wL1 = df_mul(grid_df(row, 13), q1), wL2 = df_mul(grid_df(row, 14), q2);
-    const df numL = df_add_fast(df_add_fast(df_mul(wL0, P0), df_mul(wL1, P1)), df_mul(wL2, P2));
-    const df denL = df_add_fast(df_add_fast(wL0, wL1), wL2);
-    const df M0 = df_add_fast(df_mul(grid_df(row, 6), d0), df_mul(grid_df(row, 7), d1));
-    const df M1 = df_add_fast(df_mul(grid_df(row, 8), d1), df_mul(grid_df(row, 9), d2));
-    const df M2 = df_add_fast(df_mul(grid_df(row, 10), d2), df_mul(grid_df(row, 11), d3));
-    const df wR0 = df_mul(grid_df(row, 15), q0), wR1 = df_mul(grid_df(row, 16), q1), wR2 = df_mul(grid_df(row, 17), q2);
-    const df numR = df_add_fast(df_add_fast(df_mul(wR0, M0), df_mul(wR1, M1)), df_mul(wR2, M2));
-    const df denR = df_add_fast(df_add_fast(wR0, wR1), wR2);
-    eL = vc + df_to_double(df_div(numL, denL));
-    eR = vc + df_to_double(df_div(numR, denR));
+    const df2 T = df2_add_fast(df2_make(e, e), B);                 // (t0, t2)
+    const df t1 = df_add_fast(e, b1);
+    const float m = fminf(T.hi.x, fminf(t1.hi, T.hi.y));
+    const df2 G = df2_div_f(f2(m), T);
+    const df2 Q = df2_mul(G, G);                                   // (q0, q2)
+    const df g1 = df_div_f(m, t1);
+    const df q1 = df_mul(g1, g1);
+    const df2 P0 = df2_add_fast(df2_mul(C(0, 6), df2_make(d0, d0)), df2_mul(C(1, 7), df2_make(d1, d1)));
+    const df2 P1 = df2_add_fast(df2_mul(C(2, 8), df2_make(d1, d1)), df2_mul(C(3, 9), df2_make(d2, d2)));
+    const df2 P2 = df2_add_fast(df2_mul(C(4, 10), df2_make(d2, d2)), df2_mul(C(5, 11), df2_make(d3, d3)));
+    const df2 W0 = df2_mul(C(12, 15), df2_make(df2_x(Q), df2_x(Q)));
+    const df2 W1 = df2_mul(C(13, 16), df2_make(q1, q1));
+    const df2 W2 = df2_mul(C(14, 17), df2_make(df2_y(Q), df2_y(Q)));
+    const df2 num = df2_add_fast(df2_add_fast(df2_mul(W0, P0), df2_mul(W1, P1)), df2_mul(W2, P2));
+    const df2 den = df2_add_fast(df2_add_fast(W0, W1), W2);
+    const df2 I = df2_div(num, den);
+    eL = vc + df_to_double(df2_x(I));
+    eR = vc + df_to_double(df2_y(I));
 }
 
 template <class Col>
