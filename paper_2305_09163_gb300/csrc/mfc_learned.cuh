@@ -83,13 +83,10 @@ __device__ __forceinline__ float learned_increment(const uint4& row, float d0, f
 __device__ __forceinline__ int learned_var_edges(float vc, const float (&d)[4], float eps34, float tau, bool bound,
                                                  const uint4* __restrict__ frag, LearnRows& sm, int lane,
                                                  float& eRjs, float& eLjs, float& eR, float& eL) {
-    weno5_edges(vc, d, eps34, eRjs, eLjs);
+    float b0, b1, b2;   // the JS smoothness indicators, reused by the sensor
+    weno5_edges(vc, d, eps34, eRjs, eLjs, b0, b1, b2);
     eR = eRjs;
     eL = eLjs;
-    const float S0 = d[0] * d[0], S1 = d[1] * d[1], S2 = d[2] * d[2], S3 = d[3] * d[3];
-    const float b0 = fmaf(2.5f, S1, fmaf(-2.75f, d[1] * d[0], S0));
-    const float b1 = fmaf(-1.25f, d[1] * d[2], S1 + S2);
-    const float b2 = fmaf(2.5f, S2, fmaf(-2.75f, d[2] * d[3], S3));
     const float xm2 = -(d[0] + d[1]), xm1 = -d[1], xp1 = d[2], xp2 = d[2] + d[3];
     const float sc = fmaxf(fmaxf(fabsf(xm2), fabsf(xm1)), fmaxf(fabsf(xp1), fabsf(xp2)));
     const float bmax = fmaxf(b0, fmaxf(b1, b2)), bmin = fminf(b0, fminf(b1, b2));

@@ -105,13 +105,15 @@ __device__ __forceinline__ void weno5_edges_df(double vc, const double D[4], dou
 // evaluating the c+1/2 formula on the mirrored stencil (-D3, -D2, -D1, -D0)
 // (as weno5_increments_pair); b1, its weight and m are formed once (256^3
 // mixed step 6.29 -> 6.06 ms against scalar FP32 instructions).
-__device__ __forceinline__ void weno5_edges(float vc, const float D[4], float eps34,
-                                            float& eR, float& eL) {
+__device__ __forceinline__ void weno5_edges(float vc, const float D[4], float eps34, float& eR, float& eL,
+                                            float& b0, float& b1, float& b2) {
     const float2 X0 = make_float2(D[0], -D[3]), X1 = make_float2(D[1], -D[2]);
     const float2 X2 = make_float2(D[2], -D[1]), X3 = make_float2(D[3], -D[0]);
     const float2 S = mul2(X1, X1);                                                     // (D1^2, D2^2)
     const float2 B = fma2(f2(2.5f), S, fma2(f2(-2.75f), mul2(X1, X0), mul2(X0, X0)));  // (b0, b2)
-    const float b1 = fmaf(-1.25f, D[1] * D[2], S.x + S.y);
+    b0 = B.x;
+    b2 = B.y;
+    b1 = fmaf(-1.25f, D[1] * D[2], S.x + S.y);
     const float2 T = add2(f2(eps34), B);
     const float t1 = eps34 + b1;
     const float m = fminf(T.x, fminf(t1, T.y));
@@ -128,6 +130,12 @@ __device__ __forceinline__ void weno5_edges(float vc, const float D[4], float ep
     const float2 E = add2(f2(vc), make_float2(__fdividef(num.x, den.x), __fdividef(num.y, den.y)));
     eL = E.x;
     eR = E.y;
+}
+// The same without the smoothness indicators (b0, b1, b2: without their 4/3
+// factor, as above).
+__device__ __forceinline__ void weno5_edges(float vc, const float D[4], float eps34, float& eR, float& eL) {
+    float b0, b1, b2;
+    weno5_edges(vc, D, eps34, eR, eL, b0, b1, b2);
 }
 
 // ---------------------------------------------------------------------------
