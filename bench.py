@@ -795,8 +795,8 @@ def main():
                                                     learned=precision == "learned")
         line["configs"][name] = entry
     if not args.no_e2e:
-        k = max(2, min(args.steps, 5))
-        dt, nbytes = e2e_form(m, torch, wl, w_host, "fp64", k, 1)
+        k = max(5, min(args.steps, 10))
+        dt, nbytes = e2e_form(m, torch, wl, w_host, "fp64", k, max(3, args.warmup))
         dt = max_over_ranks(dt, ws, "cuda")
         line["e2e"] = {"value": grind_ns(dt * 1e3, ws, cells, ns), "unit": UNIT,
                        "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes, "steps": k,
