@@ -185,10 +185,12 @@ __device__ __forceinline__ void sweep_x_stream_body(const SweepArgs& a) {
     // over the variables the float-float code overflowed the instruction cache
     // (ncu: "no instruction" the largest stall, 1.0-1.5 warps per issue).
     constexpr bool ROLL = sizeof(Real) == 8 && !LEARNED;
-    // DFS (FP64 uniform WENO5, five-equation): the edge values stay float-float
-    // (cell value + increment, in the same 8 bytes) from the reconstruction into
-    // the Riemann solver: no FP64 edge sums and mixtures (256^3: see DESIGN)
-    constexpr bool DFS = ROLL && ORDER == 5 && !NONUNIF && !SIX;
+    // DFS (FP64 WENO5 and WENO3, uniform and stretched grids, five-equation
+    // models): the edge values stay
+    // float-float (cell value + increment, in the same 8 bytes) from the
+    // reconstruction into the Riemann solver: no FP64 edge sums and mixtures
+    // (256^3 step: WENO5 44.3 -> 39.0 ms, WENO3 33.4 -> 24.7 ms)
+    constexpr bool DFS = ROLL && !SIX;
     __shared__ Real sh_eL[NS][ER];
     __shared__ Real sh_eR[(ROLL || LEARNED) ? NS : 1][kStreamThreads];
     df(*dsh_eL)[ER] = reinterpret_cast<df(*)[ER]>(sh_eL);
@@ -338,7 +340,14 @@ __device__ __forceinline__ void sweep_x_stream_body(const SweepArgs& a) {
                 Real Dq[4] = {v[1] - v[0], v[2] - v[1], v[3] - v[2], v[4] - v[3]};
                 if constexpr (DFS) {
                     df er, el;
-                    weno5_edges_df(v[2], Dq, eps34, er, el);
+                    if constexpr (NONUNIF) {
+                        const GridCol<true> grow(a.grid[0], a.grid_stride[0], c);
+                        weno5_edges_nu_df(v[2], Dq, sweep_epsw<Real, 3>(a), grow, er, el);
+                    } else if constexpr (ORDER == 5) {
+                        weno5_edges_df(v[2], Dq, eps34, er, el);
+                    } else {
+                        weno3_edges_df(v[2], Dq[1], Dq[2], eps34, er, el);
+                    }
                     dsh_eL[q][pos] = el;
                     dsh_eR[q][t] = er;
                 } else {
@@ -450,8 +459,14 @@ __device__ __forceinline__ void sweep_x_stream_body(const SweepArgs& a) {
                 df Fm[NQ];
 #pragma unroll
                 for (int q = 0; q < NQ; ++q) Fm[q] = dsh_F[q][pl];
-                racc.add(finish_cell_df<NF, NDIM, 0>(a, rowoff + (c - 1), Fm, Fd, dsh_F[NQ][pl], utd, cm1, inv_dx,
-                                                     inv_df, c - 1, 1, row));
+                double idx_d = inv_dx;
+                df idx_df = inv_df;
+                if constexpr (NONUNIF) {   // this cell's width
+                    idx_df = grid_df(GridCol<true>(a.grid[0], a.grid_stride[0], c - 1), kGridInvDx);
+                    idx_d = df_to_double(idx_df);
+                }
+                racc.add(finish_cell_df<NF, NDIM, 0>(a, rowoff + (c - 1), Fm, Fd, dsh_F[NQ][pl], utd, cm1, idx_d,
+                                                     idx_df, c - 1, 1, row));
             }
         } else if (has_face && s >= own0 && c >= 1) {
             Real Fm[NQ];
@@ -553,7 +568,7 @@ __device__ __forceinline__ void sweep_yz_stream_body(const SweepArgs& a) {
     __shared__ Real sh_eL[NS][ER][32];
     __shared__ Real sh_eR[(ROLL || LEARNED) ? NS : 1][kRowsPerChunk][32];
     // DFS: edge values kept in float-float into the Riemann solver (x stream body)
-    constexpr bool DFS = ROLL && ORDER == 5 && !NONUNIF && !SIX;
+    constexpr bool DFS = ROLL && !SIX;
     df(*dsh_eL)[ER][32] = reinterpret_cast<df(*)[ER][32]>(sh_eL);
     df(*dsh_eR)[kRowsPerChunk][32] = reinterpret_cast<df(*)[kRowsPerChunk][32]>(sh_eR);
     __shared__ Real sh_eLJ[NJ][ER][32];
@@ -672,7 +687,14 @@ __device__ __forceinline__ void sweep_yz_stream_body(const SweepArgs& a) {
                     Real Dq[4] = {v1 - v0, v2 - v1, v3 - v2, v4 - v3};
                     if constexpr (DFS) {
                         df er, el;
-                        weno5_edges_df(v2, Dq, eps34, er, el);
+                        if constexpr (NONUNIF) {
+                            const GridCol<false> grow(a.grid[DIR], a.grid_stride[DIR], c);
+                            weno5_edges_nu_df(v2, Dq, sweep_epsw<Real, 3>(a), grow, er, el);
+                        } else if constexpr (ORDER == 5) {
+                            weno5_edges_df(v2, Dq, eps34, er, el);
+                        } else {
+                            weno3_edges_df(v2, Dq[1], Dq[2], eps34, er, el);
+                        }
                         dsh_eL[q][eslot(c)][lane] = el;
                         dsh_eR[q][row][lane] = er;
                     } else {
@@ -782,8 +804,14 @@ __device__ __forceinline__ void sweep_yz_stream_body(const SweepArgs& a) {
                 df Fm[NQ];
 #pragma unroll
                 for (int q = 0; q < NQ; ++q) Fm[q] = dsh_F[q][eslot(c - 1)][lane];
+                double idx_d = inv_dx;
+                df idx_df = inv_df;
+                if constexpr (NONUNIF) {   // this cell's width
+                    idx_df = grid_df(GridCol<false>(a.grid[DIR], a.grid_stride[DIR], c - 1), kGridInvDx);
+                    idx_d = df_to_double(idx_df);
+                }
                 racc.add(finish_cell_df<NF, NDIM, DIR>(a, basei + (long long)(c - 1) * sd, Fm, Fd,
-                                                       dsh_F[NQ][eslot(c - 1)][lane], utd, cm1, inv_dx, inv_df, c - 1,
+                                                       dsh_F[NQ][eslot(c - 1)][lane], utd, cm1, idx_d, idx_df, c - 1,
                                                        sd, (long long)t1 + (long long)n1 * t2, stg, threadIdx.x));
             } else {
                 Real Fm[NQ];
@@ -842,9 +870,11 @@ __global__ void __launch_bounds__(32 * kRowsPerChunk, 4) sweep_yz_stream_f64_ker
 }
 
 // The FP64 uniform WENO5 y/z stream kernel for three fluids, bounded to 3
-// CTAs per SM (168 registers): unbounded it takes 187-192 and keeps 2.
+// CTAs per SM (168 registers; unbounded it takes 187-192 and keeps 2), the z
+// sweep (RK epilogue) to 4 (128 registers, 76 bytes of spills): 512^3 step
+// 356.2 -> 346.7 ms with both at 4, the y sweep alone slower at 4.
 template <int NF, int NDIM, int DIR>
-__global__ void __launch_bounds__(32 * kRowsPerChunk, 3) sweep_yz_stream_f64b3_kernel(const SweepArgs a) {
+__global__ void __launch_bounds__(32 * kRowsPerChunk, DIR == 2 ? 4 : 3) sweep_yz_stream_f64b3_kernel(const SweepArgs a) {
     sweep_yz_stream_body<double, NF, NDIM, DIR, false, 5, false, false, true>(a);
 }
 

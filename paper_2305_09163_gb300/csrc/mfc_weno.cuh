@@ -151,9 +151,9 @@ __device__ __forceinline__ void weno5_edges(float vc, const float D[4], float ep
 // the FP32 range: g_r = min(t0, t1)/t_r <= 1, weights g0^2 and 2 g1^2 at
 // c+1/2, g1^2 and 2 g0^2 at c-1/2.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ void weno3_edges(double vc, double a, double b, double eps, double& eR, double& eL) {
-    // lane x: the c+1/2 edge of the differences (a, b); lane y: the same formula
-    // on the mirrored differences (-b, -a), which is the c-1/2 edge
+// The two WENO3 increments (c+1/2 in lane x, c-1/2 in lane y): lane y evaluates
+// the c+1/2 formula on the mirrored differences (-b, -a).
+__device__ __forceinline__ df2 weno3_increments_pair(double a, double b, double eps) {
     const df A = df_from_double(a), Bd = df_from_double(b), E = df_from_double(eps);
     const df2 X = df2_make(A, df_neg(Bd)), Y = df2_make(Bd, df_neg(A));
     const df2 T = df2_add_fast(df2_make(E, E), df2_mul(df2_make(A, Bd), df2_make(A, Bd)));   // (t0, t1)
@@ -163,9 +163,20 @@ __device__ __forceinline__ void weno3_edges(double vc, double a, double b, doubl
     const df2 S2 = df2_mul_pow2(df2_swap(S), f2(2.f));               // (2 s1, 2 s0)
     const df2 num = df2_add_fast(df2_mul(S, X), df2_mul(S2, Y));
     const df2 den = df2_mul_pow2(df2_add_fast(S, S2), f2(2.f));
-    const df2 I = df2_div(num, den);
+    return df2_div(num, den);
+}
+__device__ __forceinline__ void weno3_edges(double vc, double a, double b, double eps, double& eR, double& eL) {
+    const df2 I = weno3_increments_pair(a, b, eps);
     eL = vc + df_to_double(df2_x(I));
     eR = vc + df_to_double(df2_y(I));
+}
+// The edge values in float-float (split cell value + increment), for the
+// Riemann solver on float-float face states.
+__device__ __forceinline__ void weno3_edges_df(double vc, double a, double b, double eps, df& eR, df& eL) {
+    const df c = df_from_double(vc);
+    const df2 E = df2_add(df2_make(c, c), weno3_increments_pair(a, b, eps));
+    eL = df2_x(E);
+    eR = df2_y(E);
 }
 
 // FP32: t^2 can overflow FP32 (a pressure jump of 1e9 Pa gives t ~ 1e18), so
@@ -207,8 +218,7 @@ __device__ __forceinline__ df grid_df(const Col& row, int k) {
 }
 
 template <class Col>
-__device__ __forceinline__ void weno5_edges_nu(double vc, const double D[4], double eps, const Col& row,
-                                               double& eR, double& eL) {
+__device__ __forceinline__ df2 weno5_increments_nu_pair(const double D[4], double eps, const Col& row) {
     // the two edges side by side in packed FP32 instructions: lane x the c+1/2
     // edge (coefficients 0-5, 12-14), lane y the c-1/2 edge (6-11, 15-17); the
     // smoothness indicators b0 and b2 side by side, b1 alone
@@ -238,9 +248,23 @@ __device__ __forceinline__ void weno5_edges_nu(double vc, const double D[4], dou
     const df2 W2 = df2_mul(C(14, 17), df2_make(df2_y(Q), df2_y(Q)));
     const df2 num = df2_add_fast(df2_add_fast(df2_mul(W0, P0), df2_mul(W1, P1)), df2_mul(W2, P2));
     const df2 den = df2_add_fast(df2_add_fast(W0, W1), W2);
-    const df2 I = df2_div(num, den);
+    return df2_div(num, den);   // (increment at c+1/2, increment at c-1/2)
+}
+template <class Col>
+__device__ __forceinline__ void weno5_edges_nu(double vc, const double D[4], double eps, const Col& row,
+                                               double& eR, double& eL) {
+    const df2 I = weno5_increments_nu_pair(D, eps, row);
     eL = vc + df_to_double(df2_x(I));
     eR = vc + df_to_double(df2_y(I));
+}
+// The edge values in float-float (split cell value + increment).
+template <class Col>
+__device__ __forceinline__ void weno5_edges_nu_df(double vc, const double D[4], double eps, const Col& row,
+                                                  df& eR, df& eL) {
+    const df c = df_from_double(vc);
+    const df2 E = df2_add(df2_make(c, c), weno5_increments_nu_pair(D, eps, row));
+    eL = df2_x(E);
+    eR = df2_y(E);
 }
 
 template <class Col>
