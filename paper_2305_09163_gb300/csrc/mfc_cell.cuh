@@ -777,17 +777,17 @@ __device__ __forceinline__ double finish_cell(const SweepArgs& a, long long idx,
 // Five-equation FP64 path with float-float fluxes: the differences and the
 // division by dx in float-float (accurate addition: relative error ~2^-47 of
 // the difference), one widening per value.
-template <int NF, int NDIM, int DIR>
+template <int NF, int NDIM, int DIR, bool SIX = false>
 __device__ __forceinline__ double finish_cell_df(const SweepArgs& a, long long idx, const df* Fm, const df* Fp,
                                                  df um, df up, const double* cell, double inv_dx, df inv_df, int b,
                                                  long long sd, long long tr = -1, const unsigned char* stg = nullptr,
                                                  int slot = 0) {
-    constexpr int NQ = Layout<NF, NDIM>::NQ;
+    constexpr int NQ = Layout<NF, NDIM, SIX>::NQ;
     double out[NQ];
 #pragma unroll
     for (int v = 0; v < NQ; ++v) out[v] = df_to_double(df_mul(df_add(Fm[v], df_neg(Fp[v])), inv_df));
     const double du = df_to_double(df_mul(df_add(up, df_neg(um)), inv_df));
-    return finish_cell_rates<double, NF, NDIM, DIR>(a, idx, out, du, cell, inv_dx, b, sd, tr, stg, slot);
+    return finish_cell_rates<double, NF, NDIM, DIR, SIX>(a, idx, out, du, cell, inv_dx, b, sd, tr, stg, slot);
 }
 
 }  // namespace mfc

@@ -309,18 +309,28 @@ __device__ __forceinline__ void hllc_df(const double* L, const double* R, const 
 // The EOS constants as float-float values (split once per kernel).
 struct EosDf {
     df G_N, P_N, dG[2], dP[2];
+    // six-equation model: the frozen-sound-speed coefficients and the phase
+    // constants G_k = G_N + dG_k, P_k = P_N + dP_k
+    df A_N, B_N, dA[2], dB[2], Gk[2], Pk[2];
     template <typename E>
     __device__ __forceinline__ explicit EosDf(const E& e)
-        : G_N(df_from_double((double)e.G_N)), P_N(df_from_double((double)e.P_N)) {
-        dG[0] = df_from_double((double)e.dG[0]);
-        dG[1] = df_from_double((double)e.dG[1]);
-        dP[0] = df_from_double((double)e.dP[0]);
-        dP[1] = df_from_double((double)e.dP[1]);
+        : G_N(df_from_double((double)e.G_N)), P_N(df_from_double((double)e.P_N)),
+          A_N(df_from_double((double)e.A_N)), B_N(df_from_double((double)e.B_N)) {
+#pragma unroll
+        for (int k = 0; k < 2; ++k) {
+            dG[k] = df_from_double((double)e.dG[k]);
+            dP[k] = df_from_double((double)e.dP[k]);
+            dA[k] = df_from_double((double)e.dA[k]);
+            dB[k] = df_from_double((double)e.dB[k]);
+            Gk[k] = df_from_double((double)e.G_N + (double)e.dG[k]);
+            Pk[k] = df_from_double((double)e.P_N + (double)e.dP[k]);
+        }
     }
 };
 
-// Mixture quantities of a float-float face state, in float-float.
-template <int NF, int NDIM>
+// Mixture quantities of a float-float face state, in float-float (SIX: n =
+// Gamma r c^2 with the frozen sound speed, r c^2 = A p + B, as in mixture).
+template <int NF, int NDIM, bool SIX = false>
 __device__ __forceinline__ MixDf mixture_df(const df* s, const EosDf& e) {
     using Lay = Layout<NF, NDIM>;
     MixDf m;
@@ -334,7 +344,17 @@ __device__ __forceinline__ MixDf mixture_df(const df* s, const EosDf& e) {
         m.G = df_add(m.G, df_mul(s[Lay::IA + k], e.dG[k]));
         m.P = df_add(m.P, df_mul(s[Lay::IA + k], e.dP[k]));
     }
-    m.n = df_add(df_mul(df_add_fast(m.G, {1.f, 0.f}), s[Lay::IE]), m.P);
+    if constexpr (SIX) {
+        df A = e.A_N, B = e.B_N;
+#pragma unroll
+        for (int k = 0; k < NF - 1; ++k) {
+            A = df_add(A, df_mul(s[Lay::IA + k], e.dA[k]));
+            B = df_add(B, df_mul(s[Lay::IA + k], e.dB[k]));
+        }
+        m.n = df_mul(m.G, df_add(df_mul(A, s[Lay::IE]), B));
+    } else {
+        m.n = df_add(df_mul(df_add_fast(m.G, {1.f, 0.f}), s[Lay::IE]), m.P);
+    }
     return m;
 }
 
@@ -419,12 +439,17 @@ __device__ __forceinline__ void face_flux(const SweepArgs& a, const EosR<Real>& 
 // value plus its float-float increment): mixture and positivity test in
 // float-float, the first-order fallback splitting the two FP64 cell values;
 // no FP64 operation before the widened fluxes.
-template <int NF, int NDIM, int DIR>
+//
+// Six-equation model (SIX): the phase internal energies are carried with the
+// upwind state at the face pressure, a_k (G_k p_K + P_k) times the face
+// velocity (as in hllc).
+template <int NF, int NDIM, int DIR, bool SIX = false>
 __device__ __forceinline__ void face_flux_df(const SweepArgs& a, const EosDf& e, const df* eLs, const df* eRs,
                                              const double* cl, const double* cr, df* F, df& ut) {
-    constexpr int NS = Layout<NF, NDIM>::NS;
-    MixDf mL = mixture_df<NF, NDIM>(eLs, e);
-    MixDf mR = mixture_df<NF, NDIM>(eRs, e);
+    using Lay = Layout<NF, NDIM>;
+    constexpr int NS = Lay::NS;
+    MixDf mL = mixture_df<NF, NDIM, SIX>(eLs, e);
+    MixDf mR = mixture_df<NF, NDIM, SIX>(eRs, e);
     const bool first = a.fallback && !(face_state_ok_df<NF, NDIM>(eLs, mL) && face_state_ok_df<NF, NDIM>(eRs, mR));
     df sl[NS], sr[NS];
 #pragma unroll
@@ -439,10 +464,21 @@ __device__ __forceinline__ void face_flux_df(const SweepArgs& a, const EosDf& e,
             sl[v] = df_from_double(cl[v]);
             sr[v] = df_from_double(cr[v]);
         }
-        mL = mixture_df<NF, NDIM>(sl, e);
-        mR = mixture_df<NF, NDIM>(sr, e);
+        mL = mixture_df<NF, NDIM, SIX>(sl, e);
+        mR = mixture_df<NF, NDIM, SIX>(sr, e);
     }
-    hllc_df_core<NF, NDIM, DIR>(DfStates{sl}, DfStates{sr}, mL, mR, F, ut);
+    const bool useL = hllc_df_core<NF, NDIM, DIR>(DfStates{sl}, DfStates{sr}, mL, mR, F, ut);
+    if constexpr (SIX) {
+        const df pK = useL ? sl[Lay::IE] : sr[Lay::IE];
+        df aN = {1.f, 0.f};
+#pragma unroll
+        for (int k = 0; k < NF - 1; ++k) {
+            const df aK = useL ? sl[Lay::IA + k] : sr[Lay::IA + k];
+            aN = df_add(aN, df_neg(aK));
+            F[NS + k] = df_mul(df_mul(aK, df_add(df_mul(e.Gk[k], pK), e.Pk[k])), ut);
+        }
+        F[NS + NF - 1] = df_mul(df_mul(aN, df_add(df_mul(e.G_N, pK), e.P_N)), ut);
+    }
 }
 
 }  // namespace mfc

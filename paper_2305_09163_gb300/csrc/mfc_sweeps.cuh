@@ -185,12 +185,12 @@ __device__ __forceinline__ void sweep_x_stream_body(const SweepArgs& a) {
     // over the variables the float-float code overflowed the instruction cache
     // (ncu: "no instruction" the largest stall, 1.0-1.5 warps per issue).
     constexpr bool ROLL = sizeof(Real) == 8 && !LEARNED;
-    // DFS (FP64 WENO5 and WENO3, uniform and stretched grids, five-equation
-    // models): the edge values stay
+    // DFS (FP64 WENO5 and WENO3, uniform and stretched grids, five- and
+    // six-equation models): the edge values stay
     // float-float (cell value + increment, in the same 8 bytes) from the
     // reconstruction into the Riemann solver: no FP64 edge sums and mixtures
     // (256^3 step: WENO5 44.3 -> 39.0 ms, WENO3 33.4 -> 24.7 ms)
-    constexpr bool DFS = ROLL && !SIX;
+    constexpr bool DFS = ROLL;
     __shared__ Real sh_eL[NS][ER];
     __shared__ Real sh_eR[(ROLL || LEARNED) ? NS : 1][kStreamThreads];
     df(*dsh_eL)[ER] = reinterpret_cast<df(*)[ER]>(sh_eL);
@@ -422,7 +422,7 @@ __device__ __forceinline__ void sweep_x_stream_body(const SweepArgs& a) {
                 lftd[q] = dsh_eL[q][pl];
                 erd[q] = dsh_eR[q][t];
             }
-            face_flux_df<NF, NDIM, 0>(a, edf, lftd, erd, cm1, cell, Fd, utd);
+            face_flux_df<NF, NDIM, 0, SIX>(a, edf, lftd, erd, cm1, cell, Fd, utd);
 #pragma unroll
             for (int q = 0; q < NQ; ++q) dsh_F[q][pos] = Fd[q];
             dsh_F[NQ][pos] = utd;
@@ -465,7 +465,7 @@ __device__ __forceinline__ void sweep_x_stream_body(const SweepArgs& a) {
                     idx_df = grid_df(GridCol<true>(a.grid[0], a.grid_stride[0], c - 1), kGridInvDx);
                     idx_d = df_to_double(idx_df);
                 }
-                racc.add(finish_cell_df<NF, NDIM, 0>(a, rowoff + (c - 1), Fm, Fd, dsh_F[NQ][pl], utd, cm1, idx_d,
+                racc.add(finish_cell_df<NF, NDIM, 0, SIX>(a, rowoff + (c - 1), Fm, Fd, dsh_F[NQ][pl], utd, cm1, idx_d,
                                                      idx_df, c - 1, 1, row));
             }
         } else if (has_face && s >= own0 && c >= 1) {
@@ -568,7 +568,7 @@ __device__ __forceinline__ void sweep_yz_stream_body(const SweepArgs& a) {
     __shared__ Real sh_eL[NS][ER][32];
     __shared__ Real sh_eR[(ROLL || LEARNED) ? NS : 1][kRowsPerChunk][32];
     // DFS: edge values kept in float-float into the Riemann solver (x stream body)
-    constexpr bool DFS = ROLL && !SIX;
+    constexpr bool DFS = ROLL;
     df(*dsh_eL)[ER][32] = reinterpret_cast<df(*)[ER][32]>(sh_eL);
     df(*dsh_eR)[kRowsPerChunk][32] = reinterpret_cast<df(*)[kRowsPerChunk][32]>(sh_eR);
     __shared__ Real sh_eLJ[NJ][ER][32];
@@ -760,7 +760,7 @@ __device__ __forceinline__ void sweep_yz_stream_body(const SweepArgs& a) {
                 lftd[q] = dsh_eL[q][eslot(c - 1)][lane];
                 erd[q] = dsh_eR[q][row][lane];
             }
-            face_flux_df<NF, NDIM, DIR>(a, edf, lftd, erd, cm1, cell, Fd, utd);
+            face_flux_df<NF, NDIM, DIR, SIX>(a, edf, lftd, erd, cm1, cell, Fd, utd);
 #pragma unroll
             for (int q = 0; q < NQ; ++q) dsh_F[q][eslot(c)][lane] = Fd[q];
             dsh_F[NQ][eslot(c)][lane] = utd;
@@ -810,7 +810,7 @@ __device__ __forceinline__ void sweep_yz_stream_body(const SweepArgs& a) {
                     idx_df = grid_df(GridCol<false>(a.grid[DIR], a.grid_stride[DIR], c - 1), kGridInvDx);
                     idx_d = df_to_double(idx_df);
                 }
-                racc.add(finish_cell_df<NF, NDIM, DIR>(a, basei + (long long)(c - 1) * sd, Fm, Fd,
+                racc.add(finish_cell_df<NF, NDIM, DIR, SIX>(a, basei + (long long)(c - 1) * sd, Fm, Fd,
                                                        dsh_F[NQ][eslot(c - 1)][lane], utd, cm1, idx_d, idx_df, c - 1,
                                                        sd, (long long)t1 + (long long)n1 * t2, stg, threadIdx.x));
             } else {
