@@ -213,7 +213,7 @@ __device__ __noinline__ void relax6(const SweepArgs& a, double* q) {
     for (int k = 1; k < NF; ++k) r += q[k];
 #pragma unroll
     for (int d = 0; d < NDIM; ++d) m2 = fma(q[IM + d], q[IM + d], m2);
-    const double eint = q[IE] - 0.5 * m2 / r;
+    const double eint = q[IE] - 0.5 * m2 * rcp_nr(r);
     auto mixture_p = [&]() {
         double G = a.e.G_N, P = a.e.P_N;
 #pragma unroll
@@ -221,7 +221,7 @@ __device__ __noinline__ void relax6(const SweepArgs& a, double* q) {
             G = fma(q[IA + k], a.e.dG[k], G);
             P = fma(q[IA + k], a.e.dP[k], P);
         }
-        return (eint - P) / G;
+        return (eint - P) * rcp_nr(G);
     };
     // the phases in float-float (integer splits) and FP32
     df a0d[NF], E0d[NF], pid[NF], c1d[NF];
@@ -247,13 +247,13 @@ __device__ __noinline__ void relax6(const SweepArgs& a, double* q) {
 #pragma unroll
         for (int k = 0; k < NF; ++k) {
             if (!in[k]) continue;
-            const float t = 1.f / (p + pif[k]);
+            const float t = rcp_approx(p + pif[k]);
             f = fmaf(c1f[k] * fmaf(a0f[k], p, E0f[k]), t, f);
             fp = fmaf(c1f[k] * fmaf(a0f[k], pif[k], -E0f[k]), t * t, fp);
         }
         if (f > 0.f) lo = p;
         else hi = p;
-        float pn = p - f / fp;
+        float pn = p - f * rcp_approx(fp);
         if (!(pn > lo && pn < hi)) pn = 0.5f * (lo + (hi < INFINITY ? hi : p));
         const bool done = fabsf(pn - p) <= 0x1p-20f * fabsf(pn) || !(pn > lo && pn < hi);
         p = pn;
@@ -271,10 +271,10 @@ __device__ __noinline__ void relax6(const SweepArgs& a, double* q) {
             const df num = df_add(E0d[k], df_mul(a0d[k], pd));
             const df den = df_add(pd, pid[k]);
             f = df_add(f, df_mul(c1d[k], df_div(num, den)));
-            const float t = 1.f / den.hi;
+            const float t = rcp_approx(den.hi);
             fp = fmaf(c1f[k] * fmaf(a0f[k], pif[k], -E0f[k]), t * t, fp);
         }
-        pd = df_add(pd, {-(f.hi + f.lo) / fp, 0.f});
+        pd = df_add(pd, {-(f.hi + f.lo) * rcp_approx(fp), 0.f});
     }
     // 3. one FP64 Newton step and the fractions at its end (first order)
     const double p0 = df_to_double(pd);
@@ -285,13 +285,13 @@ __device__ __noinline__ void relax6(const SweepArgs& a, double* q) {
         dak[k] = 0.0;
         if (!in[k]) continue;
         const double pi = a.kpinf[k];
-        const double t = 1.0 / (p0 + pi);
+        const double t = rcp_nr(p0 + pi);
         ak[k] = a.rc1[k] * fma(a0[k], p0, E0[k]) * t;
         dak[k] = a.rc1[k] * fma(a0[k], pi, -E0[k]) * t * t;
         f64 += ak[k];
         fp64 += dak[k];
     }
-    const double dp = df_widen(-(float)f64 / (float)fp64);
+    const double dp = df_widen(-(float)f64 * rcp_approx((float)fp64));
     // 4. new fractions, the pressure of the total energy, the phase energies
     double an = 1.0;
 #pragma unroll
