@@ -114,6 +114,15 @@ __device__ __forceinline__ df df_sqrt(df x) {
     return df_fast_two_sum(s, __fmul_rn(r.hi, __fmul_rn(0.5f, __frcp_rn(s))));
 }
 
+// An FP64 value carried bit for bit in a float-float slot (the same 8 bytes):
+// the six-equation sweeps keep their volume-fraction edges in FP64.
+__device__ __forceinline__ df df_pack(double d) {
+    return {__int_as_float(__double2loint(d)), __int_as_float(__double2hiint(d))};
+}
+__device__ __forceinline__ double df_unpack(df x) {
+    return __hiloint2double(__float_as_int(x.lo), __float_as_int(x.hi));
+}
+
 // ---------------------------------------------------------------------------
 // Two float-float values side by side: the same operation sequence as the
 // scalar functions above, applied to both lanes of packed FP32 instructions

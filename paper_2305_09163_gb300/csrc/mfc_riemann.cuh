@@ -442,21 +442,34 @@ __device__ __forceinline__ void face_flux(const SweepArgs& a, const EosR<Real>& 
 //
 // Six-equation model (SIX): the phase internal energies are carried with the
 // upwind state at the face pressure, a_k (G_k p_K + P_k) times the face
-// velocity (as in hllc).
+// velocity (as in hllc).  The volume-fraction slots of eLs and eRs hold FP64
+// edges (df_pack): alpha_N = 1 - sum_k alpha_k is formed in FP64, since where
+// phase N is a trace (alpha_N ~ 1e-6) the subtraction cancels and a
+// float-float alpha_k (~2^-48 of 1) would leave alpha_N ~3e-9 relative error.
 template <int NF, int NDIM, int DIR, bool SIX = false>
 __device__ __forceinline__ void face_flux_df(const SweepArgs& a, const EosDf& e, const df* eLs, const df* eRs,
                                              const double* cl, const double* cr, df* F, df& ut) {
     using Lay = Layout<NF, NDIM>;
     constexpr int NS = Lay::NS;
-    MixDf mL = mixture_df<NF, NDIM, SIX>(eLs, e);
-    MixDf mR = mixture_df<NF, NDIM, SIX>(eRs, e);
-    const bool first = a.fallback && !(face_state_ok_df<NF, NDIM>(eLs, mL) && face_state_ok_df<NF, NDIM>(eRs, mR));
     df sl[NS], sr[NS];
+    [[maybe_unused]] double aL[SIX ? NF - 1 : 1], aR[SIX ? NF - 1 : 1];
 #pragma unroll
     for (int v = 0; v < NS; ++v) {
         sl[v] = eLs[v];
         sr[v] = eRs[v];
     }
+    if constexpr (SIX) {
+#pragma unroll
+        for (int k = 0; k < NF - 1; ++k) {
+            aL[k] = df_unpack(eLs[Lay::IA + k]);
+            aR[k] = df_unpack(eRs[Lay::IA + k]);
+            sl[Lay::IA + k] = df_from_double(aL[k]);
+            sr[Lay::IA + k] = df_from_double(aR[k]);
+        }
+    }
+    MixDf mL = mixture_df<NF, NDIM, SIX>(sl, e);
+    MixDf mR = mixture_df<NF, NDIM, SIX>(sr, e);
+    const bool first = a.fallback && !(face_state_ok_df<NF, NDIM>(sl, mL) && face_state_ok_df<NF, NDIM>(sr, mR));
     if (first) {
         count_fallback(a.fallback_count);
 #pragma unroll
@@ -464,20 +477,27 @@ __device__ __forceinline__ void face_flux_df(const SweepArgs& a, const EosDf& e,
             sl[v] = df_from_double(cl[v]);
             sr[v] = df_from_double(cr[v]);
         }
+        if constexpr (SIX) {
+#pragma unroll
+            for (int k = 0; k < NF - 1; ++k) {
+                aL[k] = cl[Lay::IA + k];
+                aR[k] = cr[Lay::IA + k];
+            }
+        }
         mL = mixture_df<NF, NDIM, SIX>(sl, e);
         mR = mixture_df<NF, NDIM, SIX>(sr, e);
     }
     const bool useL = hllc_df_core<NF, NDIM, DIR>(DfStates{sl}, DfStates{sr}, mL, mR, F, ut);
     if constexpr (SIX) {
         const df pK = useL ? sl[Lay::IE] : sr[Lay::IE];
-        df aN = {1.f, 0.f};
+        double aN = 1.0;
 #pragma unroll
         for (int k = 0; k < NF - 1; ++k) {
-            const df aK = useL ? sl[Lay::IA + k] : sr[Lay::IA + k];
-            aN = df_add(aN, df_neg(aK));
-            F[NS + k] = df_mul(df_mul(aK, df_add(df_mul(e.Gk[k], pK), e.Pk[k])), ut);
+            const double aK = useL ? aL[k] : aR[k];
+            aN -= aK;
+            F[NS + k] = df_mul(df_mul(df_from_double(aK), df_add(df_mul(e.Gk[k], pK), e.Pk[k])), ut);
         }
-        F[NS + NF - 1] = df_mul(df_mul(aN, df_add(df_mul(e.G_N, pK), e.P_N)), ut);
+        F[NS + NF - 1] = df_mul(df_mul(df_from_double(aN), df_add(df_mul(e.G_N, pK), e.P_N)), ut);
     }
 }
 

@@ -162,6 +162,41 @@ __global__ void __launch_bounds__(128) sweep_kernel(const SweepArgs a) {
 // slots early so that its first cell has both faces.  Every lane takes part in
 // every chunk, as the learned form's warp-level network needs.
 // ---------------------------------------------------------------------------
+// The FP64 path's edge values of variable q of cell c along direction dir in
+// float-float (DFS): the increment pair of the reconstruction (WENO5 or WENO3
+// on uniform grids, WENO5 from the cell's tables on stretched ones) added to
+// the split cell value with the accurate float-float addition (the face state
+// carries ~2^-48 of its magnitude).  In the six-equation model the volume
+// fractions keep
+// FP64 edges instead (vc + the widened increment, carried in the same 8 bytes
+// by df_pack), since their complement alpha_N enters a flux (face_flux_df).
+// VALUE_MAJOR: the grid-table layout of the direction (x sweep: true).
+// ---------------------------------------------------------------------------
+template <typename Real, int NF, int NDIM, int ORDER, bool NONUNIF, bool SIX, bool VALUE_MAJOR>
+__device__ __forceinline__ void dfs_edges(const SweepArgs& a, int dir, int c, int q, double vc, const double (&D)[4],
+                                          double eps34, df& eR, df& eL) {
+    df2 I;
+    if constexpr (NONUNIF) {
+        const GridCol<VALUE_MAJOR> grow(a.grid[dir], a.grid_stride[dir], c);
+        I = weno5_increments_nu_pair(D, sweep_epsw<double, 3>(a), grow);
+    } else if constexpr (ORDER == 5) {
+        const df d[4] = {df_from_double(D[0]), df_from_double(D[1]), df_from_double(D[2]), df_from_double(D[3])};
+        I = weno5_increments_pair(d, eps34);
+    } else {
+        I = weno3_increments_pair(D[1], D[2], eps34);
+    }
+    if (SIX && q >= Layout<NF, NDIM>::IA && q < Layout<NF, NDIM>::IA + NF - 1) {
+        eL = df_pack(vc + df_to_double(df2_x(I)));
+        eR = df_pack(vc + df_to_double(df2_y(I)));
+    } else {
+        const df cc = df_from_double(vc);
+        const df2 E = df2_add(df2_make(cc, cc), I);
+        eL = df2_x(E);
+        eR = df2_y(E);
+    }
+}
+
+// ---------------------------------------------------------------------------
 constexpr int kStreamThreads = 128;
 
 template <typename Real, int NF, int NDIM, bool LEARNED = false, int ORDER = 5, bool NONUNIF = false, bool SIX = false>
@@ -340,14 +375,7 @@ __device__ __forceinline__ void sweep_x_stream_body(const SweepArgs& a) {
                 Real Dq[4] = {v[1] - v[0], v[2] - v[1], v[3] - v[2], v[4] - v[3]};
                 if constexpr (DFS) {
                     df er, el;
-                    if constexpr (NONUNIF) {
-                        const GridCol<true> grow(a.grid[0], a.grid_stride[0], c);
-                        weno5_edges_nu_df(v[2], Dq, sweep_epsw<Real, 3>(a), grow, er, el);
-                    } else if constexpr (ORDER == 5) {
-                        weno5_edges_df(v[2], Dq, eps34, er, el);
-                    } else {
-                        weno3_edges_df(v[2], Dq[1], Dq[2], eps34, er, el);
-                    }
+                    dfs_edges<Real, NF, NDIM, ORDER, NONUNIF, SIX, true>(a, 0, c, q, v[2], Dq, eps34, er, el);
                     dsh_eL[q][pos] = el;
                     dsh_eR[q][t] = er;
                 } else {
@@ -687,14 +715,7 @@ __device__ __forceinline__ void sweep_yz_stream_body(const SweepArgs& a) {
                     Real Dq[4] = {v1 - v0, v2 - v1, v3 - v2, v4 - v3};
                     if constexpr (DFS) {
                         df er, el;
-                        if constexpr (NONUNIF) {
-                            const GridCol<false> grow(a.grid[DIR], a.grid_stride[DIR], c);
-                            weno5_edges_nu_df(v2, Dq, sweep_epsw<Real, 3>(a), grow, er, el);
-                        } else if constexpr (ORDER == 5) {
-                            weno5_edges_df(v2, Dq, eps34, er, el);
-                        } else {
-                            weno3_edges_df(v2, Dq[1], Dq[2], eps34, er, el);
-                        }
+                        dfs_edges<Real, NF, NDIM, ORDER, NONUNIF, SIX, false>(a, DIR, c, q, v2, Dq, eps34, er, el);
                         dsh_eL[q][eslot(c)][lane] = el;
                         dsh_eR[q][row][lane] = er;
                     } else {

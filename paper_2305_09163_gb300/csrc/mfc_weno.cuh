@@ -87,18 +87,6 @@ __device__ __forceinline__ void weno5_edges(double vc, const double D[4], double
     eR = vc + df_to_double(iR);
 }
 
-// The two edge values as float-float numbers: the cell value split (integer
-// operations) plus the increment, with the accurate float-float addition (the
-// face state then carries ~2^-48 of its magnitude, as an FP64 edge split for
-// the float-float Riemann solver does), and no FP64 operation.
-__device__ __forceinline__ void weno5_edges_df(double vc, const double D[4], double eps34, df& eR, df& eL) {
-    const df d[4] = {df_from_double(D[0]), df_from_double(D[1]), df_from_double(D[2]), df_from_double(D[3])};
-    const df c = df_from_double(vc);
-    const df2 E = df2_add(df2_make(c, c), weno5_increments_pair(d, eps34));
-    eL = df2_x(E);
-    eR = df2_y(E);
-}
-
 // FP32 variant for the mixed path.  The weights are normalised by the smallest
 // eps+beta, so no intermediate overflows FP32 (beta of a 1e9 Pa jump is ~1e19).
 // FP32: both edges in the two lanes of packed FP32 instructions, lane y
@@ -170,15 +158,6 @@ __device__ __forceinline__ void weno3_edges(double vc, double a, double b, doubl
     eL = vc + df_to_double(df2_x(I));
     eR = vc + df_to_double(df2_y(I));
 }
-// The edge values in float-float (split cell value + increment), for the
-// Riemann solver on float-float face states.
-__device__ __forceinline__ void weno3_edges_df(double vc, double a, double b, double eps, df& eR, df& eL) {
-    const df c = df_from_double(vc);
-    const df2 E = df2_add(df2_make(c, c), weno3_increments_pair(a, b, eps));
-    eL = df2_x(E);
-    eR = df2_y(E);
-}
-
 // FP32: t^2 can overflow FP32 (a pressure jump of 1e9 Pa gives t ~ 1e18), so
 // both t are scaled by their minimum first: g_r = min(t0, t1)/t_r <= 1.
 __device__ __forceinline__ void weno3_edges(float vc, float a, float b, float eps, float& eR, float& eL) {
@@ -257,16 +236,6 @@ __device__ __forceinline__ void weno5_edges_nu(double vc, const double D[4], dou
     eL = vc + df_to_double(df2_x(I));
     eR = vc + df_to_double(df2_y(I));
 }
-// The edge values in float-float (split cell value + increment).
-template <class Col>
-__device__ __forceinline__ void weno5_edges_nu_df(double vc, const double D[4], double eps, const Col& row,
-                                                  df& eR, df& eL) {
-    const df c = df_from_double(vc);
-    const df2 E = df2_add(df2_make(c, c), weno5_increments_nu_pair(D, eps, row));
-    eL = df2_x(E);
-    eR = df2_y(E);
-}
-
 template <class Col>
 __device__ __forceinline__ void weno5_edges_nu(float vc, const float D[4], float eps, const Col& row,
                                                float& eR, float& eL) {
