@@ -94,6 +94,16 @@ FP64_SWEEP_PIPE_FP64 = 0.404
 FP64_SWEEP_PIPE_FMA = 0.588
 FP64_SWEEP_DRAM_BYTES_PER_CELL = (101.7 + 158.1 + 334.9) / 3.0
 NCU_FP64_SWEEPS = "profiles/sweep_fp64_shock_bubble_160.md"
+# The same count for the other FP64 forms (x, y, z; 160^3 shock-bubble, RK
+# stage 2; profiles/sweep_fp64_forms_shock_bubble_160.md).
+FP64_SWEEP_WARP_INST_PER_CELL_FORM = {
+    "fp64_weno3": (114.7, 117.0, 127.6),
+    "fp64_kapila": (187.2, 189.8, 200.1),
+    "fp64_stretched": (221.4, 206.6, 217.6),
+    "fp64_cbc": (174.1, 177.2, 187.5),
+    "fp64_six": (188.6, 191.7, 261.2),
+}
+NCU_FP64_FORMS = "profiles/sweep_fp64_forms_shock_bubble_160.md"
 # Nominal FP32 peak: 152 SMs x 128 FMA/clk x 2 FLOP x 2.07 GHz
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 # Algorithmic DRAM bytes per cell of the three mixed-form sweeps of one stage
@@ -572,7 +582,8 @@ def _accuracy_learned_2x(m, torch, mlp, training, n=192, t_end=1.0e-4, taus=(10.
     print(json.dumps(res), flush=True)
 
 
-def _sweep_roofline_fp64(r, cells, ns, variant, nf, clocks):
+def _sweep_roofline_fp64(r, cells, ns, variant, nf, clocks, inst_per_cell=FP64_SWEEP_WARP_INST_PER_CELL,
+                         ncu=NCU_FP64_SWEEPS):
     """Roofline of the FP64 sweeps.  Their work runs mostly on the FP32 pipes
     (the WENO weights and HLLC in float-float, the weights in packed FP32x2
     instructions: one issue slot, two FMA-pipe cycles each), and neither the
@@ -588,21 +599,21 @@ def _sweep_roofline_fp64(r, cells, ns, variant, nf, clocks):
     stages = launches / 3.0
     flop = ORACLE_FLOP_PER_CELL_SWEEP[(variant, nf)] * cells * launches + RK_FLOP_PER_VAR_STAGE * ns * cells * stages
     mhz = (clocks or {}).get("sm_mhz") or 2070.0
-    inst = sum(FP64_SWEEP_WARP_INST_PER_CELL) / 3.0 * cells * launches
+    inst = sum(inst_per_cell) / 3.0 * cells * launches
     achieved = inst / sweep_s / 1e9
     peak = SCHEDULERS * mhz * 1e6 / 1e9
     return {"bound": "alu", "resource": "issue slots (and FMA pipe)", "kernel": "sweep (x, y, z)", "achieved": achieved,
             "peak": peak, "unit": "Gwarp-inst/s", "frac": achieved / peak, "issue_frac": achieved / peak,
             "peak_note": "152 SMs x 4 schedulers x 1 warp instruction per clock x the sampled SM clock (%.0f MHz)"
                          % mhz,
-            "warp_inst_per_cell_per_sweep": sum(FP64_SWEEP_WARP_INST_PER_CELL) / 3.0,
+            "warp_inst_per_cell_per_sweep": sum(inst_per_cell) / 3.0,
             "flop_tflops": flop / sweep_s / 1e12,
             "flop_per_cell_per_sweep": ORACLE_FLOP_PER_CELL_SWEEP[(variant, nf)],
             "flop_note": "FP64-accurate work of the oracle's plain formulation (counted), + RK update",
             "fp64_pipe_frac_ncu": FP64_SWEEP_PIPE_FP64, "fma_pipe_frac_ncu": FP64_SWEEP_PIPE_FMA,
             "traffic": FP64_SWEEP_DRAM_BYTES_PER_CELL * cells if FP64_SWEEP_DRAM_BYTES_PER_CELL else None,
             "traffic_note": "DRAM bytes per sweep launch, per-cell counts of one ncu capture scaled by cells",
-            "ncu": NCU_FP64_SWEEPS}
+            "ncu": ncu}
 
 
 def _sweep_roofline_hbm(r, cells, ns, nw, variant, nf, peaks, learned=False):
@@ -761,9 +772,10 @@ def main():
         neq = ns + wl.nf if six else ns
         entry = _form_entry(r, ws, cells, neq, ms)
         if precision == "fp64":
-            entry["roofline"] = _sweep_roofline_fp64(r, cells, neq, work, wl.nf, fp["clocks"])
-            entry["roofline"]["note"] = ("instruction count per cell of the FP64 WENO5 sweeps (not re-measured "
-                                         "for this form); FLOPs of the oracle's %s formulation%s"
+            entry["roofline"] = _sweep_roofline_fp64(r, cells, neq, work, wl.nf, fp["clocks"],
+                                                     FP64_SWEEP_WARP_INST_PER_CELL_FORM[form], NCU_FP64_FORMS)
+            entry["roofline"]["note"] = ("instruction count per cell of this form's sweeps (ncu); FLOPs of the "
+                                         "oracle's %s formulation%s"
                                          % (work, "; the per-cell tables of the stretched grid and the "
                                             "six-equation rows and relaxation add work" if variant in
                                             ("stretched", "six") else ""))
